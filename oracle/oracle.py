@@ -1,0 +1,257 @@
+"""ctypes front end of the FP64 CPU oracle (test infrastructure only).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg use this module.
+Every function forwards to a routine of cqr_oracle.c, which cites the passage of the
+paper (arXiv 2311.11943) it follows.  Arrays are numpy float64, Fortran (column-major)
+order.  Nothing here imports the CUDA package.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+EBREAKDOWN = 6
+EUNRECOVERABLE = 5
+
+
+class Geom(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("p_r", C.c_int32), ("p_c", C.c_int32),
+                ("f", C.c_int32), ("protect_r", C.c_int32), ("mb", C.c_int64),
+                ("nb", C.c_int64), ("m_pad", C.c_int64), ("c", C.c_int64), ("d", C.c_int64),
+                ("M", C.c_int64), ("N", C.c_int64), ("grid_rows", C.c_int32),
+                ("grid_cols", C.c_int32)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(_build.build())
+        d = C.POINTER(C.c_double)
+        i64 = C.c_int64
+        L = _lib
+        L.cqro_geom_init.argtypes = [C.POINTER(Geom), i64, i64, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.cqro_generator.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_int, d, d]
+        L.cqro_splitmix64.argtypes = [C.c_uint64, C.c_int, C.POINTER(C.c_uint64)]
+        L.cqro_encode.argtypes = [C.POINTER(Geom), d, d, d, i64, d, i64]
+        L.cqro_icgs_panel.argtypes = [i64, i64, i64, C.c_double, d, i64, d, i64, C.POINTER(i64)]
+        L.cqro_factor.argtypes = [i64, i64, i64, i64, C.c_int, C.c_int, C.c_double, d, i64, d,
+                                  i64, C.POINTER(i64)]
+        L.cqro_inject.argtypes = [C.POINTER(Geom), C.POINTER(C.c_int), C.c_int,
+                                  C.POINTER(C.c_uint8), d, i64, d, i64]
+        L.cqro_invert_small.argtypes = [C.c_int, d, d]
+        L.cqro_recover.argtypes = [C.POINTER(Geom), d, d, C.POINTER(C.c_uint8), d, i64, d, i64,
+                                   C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int)]
+        L.cqro_build_G0.argtypes = [C.POINTER(Geom), d, d, i64]
+        L.cqro_post_orth_dense.argtypes = [C.POINTER(Geom), d, d, i64, i64, d, i64]
+        L.cqro_post_orth_block.argtypes = [C.POINTER(Geom), d, d, i64, i64, d, i64]
+        L.cqro_back_substitute.argtypes = [i64, d, i64, d, i64, i64]
+        L.cqro_solve_square.argtypes = [i64, i64, d, i64, d, i64, d, i64, i64, d, i64]
+        L.cqro_solve_ls.argtypes = [i64, i64, d, i64, d, i64, d, i64, i64, d, i64]
+    return _lib
+
+
+def _p(a):
+    assert a.dtype == np.float64 and (a.flags.f_contiguous or a.ndim == 1)
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ld(a):
+    return a.shape[0]
+
+
+class OracleError(RuntimeError):
+    def __init__(self, rc, what):
+        super().__init__("%s failed with status %d" % (what, rc))
+        self.rc = rc
+
+
+def _chk(rc, what):
+    if rc != 0:
+        raise OracleError(rc, what)
+
+
+def geom(m, n, p_r, p_c, f, protect_r=True):
+    g = Geom()
+    _chk(lib().cqro_geom_init(C.byref(g), m, n, p_r, p_c, f, int(bool(protect_r))), "geom")
+    return g
+
+
+def splitmix64(seed, count):
+    out = (C.c_uint64 * count)()
+    lib().cqro_splitmix64(seed, count, out)
+    return [int(v) for v in out]
+
+
+def generator(f, p_r, p_c, seed, gdist=0, gh_ones=False):
+    """a1: (G~ f x p_r, G~_h p_c x f), both returned as 2-D float64 arrays."""
+    Gt = np.zeros(max(f * p_r, 1))
+    Gh = np.zeros(max(p_c * f, 1))
+    _chk(lib().cqro_generator(f, p_r, p_c, seed, gdist, int(gh_ones), _p(Gt), _p(Gh)), "generator")
+    return Gt[: f * p_r].reshape(f, p_r).copy(), Gh[: p_c * f].reshape(p_c, f).copy()
+
+
+def _rowmajor(G):
+    G = np.ascontiguousarray(G, dtype=np.float64).ravel()
+    return G if G.size else np.zeros(1)
+
+
+def encode(g, Gt, Gh, A):
+    """a2: the encoded matrix At (M x N) from A (m x n)."""
+    A = np.asfortranarray(A, dtype=np.float64)
+    At = np.zeros((g.M, g.N), order="F")
+    _chk(lib().cqro_encode(C.byref(g), _p(_rowmajor(Gt)), _p(_rowmajor(Gh)), _p(A), _ld(A),
+                           _p(At), _ld(At)), "encode")
+    return At
+
+
+def icgs_panel(Q, R, kb, bk, tau=0.7071067811865476):
+    nre = C.c_int64(0)
+    rc = lib().cqro_icgs_panel(Q.shape[0], kb, bk, tau, _p(Q), _ld(Q), _p(R), _ld(R), C.byref(nre))
+    _chk(rc, "icgs_panel")
+    return nre.value
+
+
+def factor(Q, R, n, b, t0=0, t1=-1, tau=0.7071067811865476):
+    """a3-a5: PBMGS panels t0..t1-1 in place on Q (M x N) and R (N x N). Returns #reorth."""
+    nre = C.c_int64(0)
+    rc = lib().cqro_factor(Q.shape[0], Q.shape[1], n, b, t0, t1, tau, _p(Q), _ld(Q), _p(R),
+                           _ld(R), C.byref(nre))
+    _chk(rc, "factor")
+    return nre.value
+
+
+def inject(g, tiles, mask, Q, R):
+    """a6: erase node tiles (list of (i, j)); mask is a uint8 (grid_rows x grid_cols) array."""
+    flat = (C.c_int * max(2 * len(tiles), 1))(*[v for t in tiles for v in t])
+    _chk(lib().cqro_inject(C.byref(g), flat, len(tiles),
+                           mask.ctypes.data_as(C.POINTER(C.c_uint8)), _p(Q), _ld(Q), _p(R),
+                           _ld(R)), "inject")
+
+
+def recover(g, Gt, Gh, mask, Q, R, cap=4096):
+    """a7: decode every erased tile; returns (decode-set list, #tiles recovered)."""
+    sets = (C.c_int * cap)()
+    ln = C.c_int(0)
+    nrec = C.c_int(0)
+    rc = lib().cqro_recover(C.byref(g), _p(_rowmajor(Gt)), _p(_rowmajor(Gh)),
+                            mask.ctypes.data_as(C.POINTER(C.c_uint8)), _p(Q), _ld(Q), _p(R),
+                            _ld(R), sets, cap, C.byref(ln), C.byref(nrec))
+    _chk(rc, "recover")
+    return [int(sets[i]) for i in range(ln.value)], nrec.value
+
+
+def invert_small(G):
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    k = G.shape[0]
+    out = np.zeros_like(G)
+    _chk(lib().cqro_invert_small(k, _p(G.ravel()), out.ctypes.data_as(C.POINTER(C.c_double))),
+         "invert")
+    return out
+
+
+def build_G0(g, Gt):
+    G0 = np.zeros((g.m_pad, g.m_pad), order="F")
+    lib().cqro_build_G0(C.byref(g), _p(_rowmajor(Gt)), _p(G0), _ld(G0))
+    return G0
+
+
+def post_orth(g, Gt, Z, dense=False):
+    """a8: W = G_0 Z for Z m_pad x k (dense: explicit G_0; else the block formula)."""
+    Z = np.asfortranarray(Z, dtype=np.float64)
+    if Z.ndim == 1:
+        Z = Z.reshape(-1, 1, order="F")
+    W = np.zeros_like(Z, order="F")
+    fn = lib().cqro_post_orth_dense if dense else lib().cqro_post_orth_block
+    _chk(fn(C.byref(g), _p(_rowmajor(Gt)), _p(Z), _ld(Z), Z.shape[1], _p(W), _ld(W)), "post_orth")
+    return W
+
+
+def back_substitute(R, rhs):
+    x = np.asfortranarray(rhs, dtype=np.float64).copy(order="F")
+    if x.ndim == 1:
+        x = x.reshape(-1, 1, order="F")
+    R = np.asfortranarray(R)
+    lib().cqro_back_substitute(x.shape[0], _p(R), _ld(R), _p(x), _ld(x), x.shape[1])
+    return x
+
+
+def solve_square(Qo, R, yo):
+    """a9 (square): x from R x = Qo^T yo, Qo = G_0 Q_1, yo = G_0 y."""
+    Qo = np.asfortranarray(Qo)
+    yo = np.asfortranarray(yo if yo.ndim == 2 else yo.reshape(-1, 1), dtype=np.float64)
+    n = Qo.shape[1]
+    R = np.asfortranarray(R)
+    x = np.zeros((n, yo.shape[1]), order="F")
+    _chk(lib().cqro_solve_square(Qo.shape[0], n, _p(Qo), _ld(Qo), _p(R), _ld(R), _p(yo),
+                                 _ld(yo), yo.shape[1], _p(x), _ld(x)), "solve_square")
+    return x
+
+
+def solve_ls(Q1, R, y):
+    """a9 (tall): least squares through A = Q_1 R."""
+    Q1 = np.asfortranarray(Q1)
+    y = np.asfortranarray(y if y.ndim == 2 else y.reshape(-1, 1), dtype=np.float64)
+    n = Q1.shape[1]
+    R = np.asfortranarray(R)
+    x = np.zeros((n, y.shape[1]), order="F")
+    _chk(lib().cqro_solve_ls(Q1.shape[0], n, _p(Q1), _ld(Q1), _p(R), _ld(R), _p(y), _ld(y),
+                             y.shape[1], _p(x), _ld(x)), "solve_ls")
+    return x
+
+
+def run(A, p_r, p_c, f, b, seed=1, erasures=None, protect_r=True, gdist=0, tau=0.7071067811865476,
+        y=None, Gt=None, Gh=None, keep_states=False):
+    """The whole hot path on the CPU: generator, encode, PBMGS with erasures injected at the
+    start of the listed panels (dict panel -> list of (i, j)) and recovered, post-orth, solve.
+
+    Returns a dict with the generator, the encoded matrix, the final coded Q and R, the
+    post-orthogonalised Q, the decode sets, the reorth count and, when y is given, x.
+    """
+    A = np.asfortranarray(A, dtype=np.float64)
+    m, n = A.shape
+    g = geom(m, n, p_r, p_c, f, protect_r)
+    if Gt is None:
+        Gt, Gh = generator(f, p_r, p_c, seed, gdist)
+    At = encode(g, Gt, Gh, A)
+    Q = At.copy(order="F")
+    R = np.zeros((g.N, g.N), order="F")
+    T = (n + b - 1) // b
+    mask = np.zeros((g.grid_rows, g.grid_cols), dtype=np.uint8)
+    sets = []
+    nrec = 0
+    nre = 0
+    states = []
+    erasures = erasures or {}
+    for t in range(T):
+        if t in erasures and erasures[t]:
+            inject(g, erasures[t], mask, Q, R)
+            s, k = recover(g, Gt, Gh, mask, Q, R)
+            sets += s
+            nrec += k
+        nre += factor(Q, R, n, b, t, t + 1, tau)
+        if keep_states:
+            states.append((Q.copy(order="F"), R.copy(order="F")))
+    out = dict(geom=g, Gt=Gt, Gh=Gh, At=At, Q=Q, R=R, sets=sets, n_recovered=nrec,
+               n_reorth=nre, states=states)
+    if f > 0:
+        Qo = post_orth(g, Gt, Q[: g.m_pad, :n])
+    else:
+        Qo = Q[: g.m_pad, :n].copy(order="F")
+    out["Qo"] = Qo
+    if y is not None:
+        y = np.asarray(y, dtype=np.float64)
+        y2 = y.reshape(m, -1)
+        yp = np.zeros((g.m_pad, y2.shape[1]), order="F")
+        yp[:m] = y2
+        if m == n and g.m_pad == m:
+            yo = post_orth(g, Gt, yp) if f > 0 else yp
+            out["yo"] = yo
+            out["x"] = solve_square(Qo, R[:n, :n], yo)
+        else:
+            out["x"] = solve_ls(Q[: g.m_pad, :n], R[:n, :n], yp)
+    return out
