@@ -1,0 +1,198 @@
+/*
+ * coded_qr.h -- C ABI of the GB300 coded block Gram-Schmidt QR library.
+ *
+ * The library computes the fault-tolerant QR of "Coded Computing for Fault-Tolerant
+ * Parallel QR Decomposition" (arXiv 2311.11943) on one GPU.  The paper's p_r x p_c
+ * processor grid becomes virtual nodes: tiles of one matrix in device memory; a node
+ * failure becomes an injected erasure of that node's tiles.
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are column-major.  `ld*` arguments are leading dimensions in elements.
+ *  - Element type: double when cfg.dtype == CQR_F64, float when CQR_F32.  The generator
+ *    arrays of coded_qr_get_generator are always double.
+ *  - Pointers are DEVICE pointers unless the argument is marked "host".
+ *  - Ownership: the caller owns A, y, x, Q, R and every output buffer it passes.  The
+ *    handle owns the encoded matrix, the coded R, the generator, the erasure mask and its
+ *    workspace (allocated by coded_qr_create, or carved from caller memory by
+ *    coded_qr_create_in, in which case the caller keeps ownership of that memory and must
+ *    keep it alive until coded_qr_destroy).
+ *  - Ordering: all GPU work is enqueued on cfg.stream (NULL = the legacy default stream)
+ *    in call order.  Argument and state errors are returned synchronously and nothing is
+ *    enqueued.  Errors detected on the device (pivot breakdown, a barrier wait that ran
+ *    out) are recorded in a device status word and returned by coded_qr_sync_status and
+ *    by coded_qr_run, which synchronise the stream.
+ *  - State machine: create -> encode -> factor* -> [inject_erasure -> recover]* ->
+ *    post_orth / solve.  factor runs panels in order and may be split into ranges
+ *    (resume from any panel boundary).  Calls out of order return CQR_ESTATE.
+ *  - Geometry (Section 2 "Distributed computing model", Eq. (tildeG_eq)): tile height
+ *    mb = ceil(m / p_r) (A is zero-padded to m_pad = p_r * mb rows), tile width
+ *    nb = n / p_c (p_c must divide n), c = f * mb checksum rows, d = f * nb checksum
+ *    columns (0 without R protection), encoded matrix M x N = (m_pad + c) x (n + d).
+ *    Node (i, j), i < p_r + f, j < p_c + f (checksum grid columns only with R protection),
+ *    owns Q tile (i, j) = rows [i mb, (i+1) mb) x columns [j nb, (j+1) nb) of the coded Q
+ *    and, when i < p_c + f, R tile (i, j) = rows [i nb, (i+1) nb) x columns
+ *    [j nb, (j+1) nb) of the coded R.  f <= min(p_r, p_c) / 2 (Section 2 "Failure model").
+ */
+#ifndef CODED_QR_H
+#define CODED_QR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cqr_handle_s* cqr_handle;
+
+typedef enum {
+  CQR_OK = 0,
+  CQR_EINVAL = 1,          /* bad argument or geometry */
+  CQR_ENOMEM = 2,          /* device or pinned host allocation failed, or workspace too small */
+  CQR_ECUDA = 3,           /* a CUDA runtime call failed (launch, copy, missing device) */
+  CQR_ESTATE = 4,          /* call out of order, or erasures pending */
+  CQR_EUNRECOVERABLE = 5,  /* more than f erasures in a grid row/column, or singular G^ */
+  CQR_EBREAKDOWN = 6,      /* zero or non-finite pivot r_jj in the panel factorisation */
+  CQR_ETIMEOUT = 7,        /* a device-side wait exceeded its limit; the kernel gave up */
+  CQR_ENOTSUP = 8          /* configuration not supported by this build */
+} cqr_status;
+
+enum { CQR_F64 = 0, CQR_F32 = 1 };
+
+/* Arithmetic of the trailing-update GEMMs (Algorithm PBMGS, Rbar and Q -= Qbar Rbar). */
+enum {
+  CQR_MMA_SIMT = 0,   /* CUDA-core FMA in the storage precision (the only choice for F64) */
+  CQR_MMA_TF32 = 1,   /* F32 storage: tcgen05 kind::tf32 tensor cores, FP32 accumulation */
+  CQR_MMA_3XTF32 = 2  /* F32 storage: split operands hi + lo, three tcgen05 tf32 products */
+};
+
+enum { CQR_G_UNIF01 = 0, CQR_G_NORMAL = 1 };
+
+typedef struct {
+  int64_t m, n;        /* A is m x n, m >= n */
+  int32_t p_r, p_c;    /* virtual node grid */
+  int32_t f;           /* tolerated failures per grid row and column; 0 = uncoded QR */
+  int32_t b;           /* PBMGS panel width (columns per iteration) */
+  int32_t dtype;       /* CQR_F64 | CQR_F32 */
+  int32_t mma;         /* CQR_MMA_* */
+  int32_t protect_r;   /* 1: horizontal checksums protect R (Eq. (encoding)); 0: Q only */
+  int32_t gdist;       /* distribution of V~ and G~_h: CQR_G_UNIF01 (paper) | CQR_G_NORMAL */
+  int32_t nrhs_max;    /* largest right-hand-side count for post_orth / solve (>= 1) */
+  int32_t reserved;
+  uint64_t seed;       /* seed of the generator's SplitMix64 stream */
+  double tau;          /* ICGS criterion: reorthogonalise column j when its norm fell below
+                          tau times its norm at the panel start.  0 selects 1/sqrt(2);
+                          a negative value disables reorthogonalisation. */
+  void* stream;        /* cudaStream_t */
+} cqr_config;
+
+/* Geometry record filled by coded_qr_geometry (all int64). */
+enum {
+  CQR_GEO_M = 0, CQR_GEO_N, CQR_GEO_MB, CQR_GEO_NB, CQR_GEO_MPAD, CQR_GEO_C, CQR_GEO_D,
+  CQR_GEO_MROWS, CQR_GEO_NCOLS, CQR_GEO_LDQ, CQR_GEO_LDR, CQR_GEO_GRID_ROWS,
+  CQR_GEO_GRID_COLS, CQR_GEO_PANELS, CQR_GEO_COUNT
+};
+
+/* Bytes of device workspace a handle with this configuration needs (for coded_qr_create_in). */
+cqr_status coded_qr_workspace_size(const cqr_config* cfg, size_t* bytes);
+
+/* Create a handle; allocates the encoded matrix, the coded R and the workspace with
+ * cudaMalloc on the current device.  *out receives the handle. */
+cqr_status coded_qr_create(const cqr_config* cfg, cqr_handle* out);
+
+/* Same, but every device buffer is carved from `workspace` (device memory of at least
+ * coded_qr_workspace_size bytes, 256-byte aligned, owned by the caller). */
+cqr_status coded_qr_create_in(const cqr_config* cfg, void* workspace, size_t bytes,
+                              cqr_handle* out);
+
+/* Release the handle (synchronises its stream first).  NULL is accepted. */
+cqr_status coded_qr_destroy(cqr_handle h);
+
+/* Fill dims[CQR_GEO_COUNT] (host) with the handle's geometry. */
+cqr_status coded_qr_geometry(cqr_handle h, int64_t* dims);
+
+/* a1 + a2.  Generator (Construction "Q-factor checksum-generator matrix", Section 4.2:
+ * V~ i.i.d. Unif(0,1) from SplitMix64(seed), G~_1 = -1/2 V~ V~^T, G~ = [G~_1 V~]; G~_h
+ * p_c x f from the same stream) computed on the device, then the checksum encode
+ * At = [[A, A G_h], [G_v A, G_v A G_h]] (Eq. (encoding)), each checksum tile
+ * C_{i,j} = sum_t g~_{i,t} A_{t,j} (Section 4.2).  A: m x n, lda >= m.  Resets the
+ * factorisation (next panel = 0, R = 0, no pending erasures). */
+cqr_status coded_qr_encode(cqr_handle h, const void* A, int64_t lda);
+
+/* a3-a5.  PBMGS (Appendix A, Algorithm PBMGS) panels [panel_begin, panel_end) on the
+ * encoded matrix: ICGS on each panel (Algorithm CGS plus the reorthogonalisation of ICGS),
+ * Rbar = Qbar^T Q[:, i+b : N], Q[:, i+b : N] -= Qbar Rbar, Rbar stored into R.
+ * panel_begin must equal the next unfactored panel; panel_end = -1 means the last panel.
+ * Returns CQR_ESTATE while erasures are pending (erased tiles hold NaN). */
+cqr_status coded_qr_factor(cqr_handle h, int32_t panel_begin, int32_t panel_end);
+
+/* a6.  Fail-stop erasure of nodes (Section 2 "Failure model"): tiles (host) holds `count`
+ * (i, j) pairs; each node's Q tile and, with R protection and i < p_c + f, its R tile are
+ * overwritten with NaN and marked lost.  Allowed any time after encode. */
+cqr_status coded_qr_inject_erasure(cqr_handle h, const int32_t* tiles, int32_t count);
+
+/* a7.  Recovery (Appendix, Lemma on the recovery overhead, Eq. (A_recov)): per grid column,
+ * G^ = G~[C_use, A_fail] (C_use = the f1 lowest-index surviving checksum rows) is inverted
+ * in FP64 on the device, the lost systematic tiles are rebuilt from the surviving tiles and
+ * checksums, and lost checksum tiles are re-encoded; R tiles are rebuilt the same way from
+ * R_2 = R_1 G_h.  Valid at every iteration by the checksum-preservation Lemma.
+ * *n_recovered (host, may be NULL) receives the number of Q tiles rebuilt.  On
+ * CQR_EUNRECOVERABLE nothing is modified and the erasures stay pending. */
+cqr_status coded_qr_recover(cqr_handle h, int32_t* n_recovered);
+
+/* a8.  Post-orthogonalisation (Theorem "G_0", Eq. (G0_formula1); sparse block pipeline of
+ * the overhead proof): Qo = G_0 Q_1 (m_pad x n) with G_0 = [[I + G_1, V], [V^T, -I]].
+ * Q == NULL overwrites Q_1 inside the handle (then solve uses it directly).
+ * y (m x nrhs, may be NULL) is transformed too: yo = G_0 [y; 0] (m_pad x nrhs) into yo,
+ * or into the handle's workspace when yo == NULL.  Requires a finished factorisation. */
+cqr_status coded_qr_post_orth(cqr_handle h, void* Q, int64_t ldq, const void* y, int64_t ldy,
+                              void* yo, int64_t ldyo, int32_t nrhs);
+
+/* a9.  Solve (Section 4.1, Eqs. (linearsolve1)-(linearsolve3)): for square A,
+ * R x = (G_0 Q_1)^T (G_0 y) and a triangular solve with the n x n R.  For m > n (and
+ * whenever m is not a multiple of p_r) least squares through A = Q_1 R (Corollary "final
+ * form"): R x = (Q_1^T Q_1)^{-1} Q_1^T y with Q_1^T Q_1 = I - Q_2^T Q_2 (orthonormality of
+ * the coded Q), formed and Cholesky-factored in FP64 on the device (n x n).
+ * y: m x nrhs, x: n x nrhs. */
+cqr_status coded_qr_solve(cqr_handle h, const void* y, int64_t ldy, void* x, int64_t ldx,
+                          int32_t nrhs);
+
+/* The whole hot path in one call: encode, factor with the erasure plan applied, post_orth
+ * (in place) and solve.  plan (host) holds plan_len triples (panel, i, j): node (i, j) is
+ * erased at the start of that panel and recovered before it runs.  With
+ * flags & CQR_RUN_HOST_BUFFERS, A, y and x are HOST pointers and the library copies them
+ * to and from the device inside the call.  Synchronises cfg.stream and returns the device
+ * status. */
+#define CQR_RUN_HOST_BUFFERS 1u
+cqr_status coded_qr_run(cqr_handle h, const void* A, int64_t lda, const void* y, int64_t ldy,
+                        void* x, int64_t ldx, int32_t nrhs, const int32_t* plan,
+                        int32_t plan_len, uint32_t flags);
+
+/* Borrow the coded factors: *Q (M x N, leading dimension *ldq) and *R (N x N, *ldr) stay
+ * owned by the handle and valid until the next encode or destroy. */
+cqr_status coded_qr_get_factors(cqr_handle h, void** Q, int64_t* ldq, void** R, int64_t* ldr);
+
+/* Copy the generator to the host: Gt f x p_r row-major, Gh p_c x f row-major (either may be
+ * NULL).  Synchronises the stream. */
+cqr_status coded_qr_get_generator(cqr_handle h, double* Gt, double* Gh);
+
+/* Decode index sets of every recover call since encode, one record per decoded grid column
+ * (kind 0) then per decoded R block row (kind 1): kind, index, f1, f2, A_fail[f1],
+ * C_fail[f2], C_use[f1].  buf (host) receives up to cap ints; *len the full length. */
+cqr_status coded_qr_get_decode_sets(cqr_handle h, int32_t* buf, int32_t cap, int32_t* len);
+
+/* Counters since encode (host, out[4]): reorthogonalisations, recovered Q tiles, panels run,
+ * erasures injected.  Synchronises the stream. */
+cqr_status coded_qr_stats(cqr_handle h, int64_t* out);
+
+/* Synchronise the stream and return the first device-side error since encode (CQR_OK when
+ * none), clearing it. */
+cqr_status coded_qr_sync_status(cqr_handle h);
+
+/* Static description of a status code. */
+const char* coded_qr_errstr(cqr_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CODED_QR_H */

@@ -1,0 +1,335 @@
+"""Thin Python binding of the coded-QR C ABI (include/coded_qr.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA library.  The
+functions `coded_qr_*` keep the C names and signatures (plain ints for pointers); the class
+`CodedQR` wraps a handle for callers that hold their matrices in torch tensors (column-major
+views: shape (rows, cols), stride (1, ld)).  There is no fallback: if the shared library is
+missing this module raises on first use.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcoded_qr.so")
+
+CQR_OK, CQR_EINVAL, CQR_ENOMEM, CQR_ECUDA, CQR_ESTATE = 0, 1, 2, 3, 4
+CQR_EUNRECOVERABLE, CQR_EBREAKDOWN, CQR_ETIMEOUT, CQR_ENOTSUP = 5, 6, 7, 8
+CQR_F64, CQR_F32 = 0, 1
+CQR_MMA_SIMT, CQR_MMA_TF32, CQR_MMA_3XTF32 = 0, 1, 2
+CQR_G_UNIF01, CQR_G_NORMAL = 0, 1
+CQR_RUN_HOST_BUFFERS = 1
+GEO_FIELDS = ["m", "n", "mb", "nb", "m_pad", "c", "d", "M", "N", "ldq", "ldr", "grid_rows",
+              "grid_cols", "panels"]
+
+EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "coded_qr_destroy",
+           "coded_qr_geometry", "coded_qr_encode", "coded_qr_factor", "coded_qr_inject_erasure",
+           "coded_qr_recover", "coded_qr_post_orth", "coded_qr_solve", "coded_qr_run",
+           "coded_qr_get_factors", "coded_qr_get_generator", "coded_qr_get_decode_sets",
+           "coded_qr_stats", "coded_qr_sync_status", "coded_qr_errstr"]
+
+
+class Config(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("p_r", C.c_int32), ("p_c", C.c_int32),
+                ("f", C.c_int32), ("b", C.c_int32), ("dtype", C.c_int32), ("mma", C.c_int32),
+                ("protect_r", C.c_int32), ("gdist", C.c_int32), ("nrhs_max", C.c_int32),
+                ("reserved", C.c_int32), ("seed", C.c_uint64), ("tau", C.c_double),
+                ("stream", C.c_void_p)]
+
+
+class CodedQRError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (where, errstr(status), status))
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (no fallback: raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("coded-QR CUDA library not built (%s); run "
+                               "__graft_entry__.build() or paper_2311_11943_gb300/build.py"
+                               % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, u32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32
+        pcfg = C.POINTER(Config)
+        sig = {
+            "coded_qr_workspace_size": [pcfg, C.POINTER(C.c_size_t)],
+            "coded_qr_create": [pcfg, C.POINTER(vp)],
+            "coded_qr_create_in": [pcfg, vp, C.c_size_t, C.POINTER(vp)],
+            "coded_qr_destroy": [vp],
+            "coded_qr_geometry": [vp, C.POINTER(i64)],
+            "coded_qr_encode": [vp, vp, i64],
+            "coded_qr_factor": [vp, i32, i32],
+            "coded_qr_inject_erasure": [vp, C.POINTER(i32), i32],
+            "coded_qr_recover": [vp, C.POINTER(i32)],
+            "coded_qr_post_orth": [vp, vp, i64, vp, i64, vp, i64, i32],
+            "coded_qr_solve": [vp, vp, i64, vp, i64, i32],
+            "coded_qr_run": [vp, vp, i64, vp, i64, vp, i64, i32, C.POINTER(i32), i32, u32],
+            "coded_qr_get_factors": [vp, C.POINTER(vp), C.POINTER(i64), C.POINTER(vp),
+                                     C.POINTER(i64)],
+            "coded_qr_get_generator": [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+            "coded_qr_get_decode_sets": [vp, C.POINTER(i32), i32, C.POINTER(i32)],
+            "coded_qr_stats": [vp, C.POINTER(i64)],
+            "coded_qr_sync_status": [vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.coded_qr_errstr.argtypes = [C.c_int]
+        L.coded_qr_errstr.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def errstr(status):
+    return lib().coded_qr_errstr(int(status)).decode()
+
+
+def check(status, where):
+    if status != CQR_OK:
+        raise CodedQRError(status, where)
+
+
+# ------------------------------------------------------------------ C-named entry points
+def coded_qr_workspace_size(cfg):
+    n = C.c_size_t(0)
+    check(lib().coded_qr_workspace_size(C.byref(cfg), C.byref(n)), "coded_qr_workspace_size")
+    return n.value
+
+
+def coded_qr_create(cfg):
+    h = C.c_void_p()
+    check(lib().coded_qr_create(C.byref(cfg), C.byref(h)), "coded_qr_create")
+    return h
+
+
+def coded_qr_create_in(cfg, workspace_ptr, nbytes):
+    h = C.c_void_p()
+    check(lib().coded_qr_create_in(C.byref(cfg), C.c_void_p(workspace_ptr), nbytes, C.byref(h)),
+          "coded_qr_create_in")
+    return h
+
+
+def coded_qr_destroy(h):
+    return lib().coded_qr_destroy(h)
+
+
+def coded_qr_geometry(h):
+    d = (C.c_int64 * len(GEO_FIELDS))()
+    check(lib().coded_qr_geometry(h, d), "coded_qr_geometry")
+    return dict(zip(GEO_FIELDS, [int(v) for v in d]))
+
+
+def coded_qr_encode(h, A_ptr, lda):
+    return lib().coded_qr_encode(h, C.c_void_p(A_ptr), lda)
+
+
+def coded_qr_factor(h, t0, t1=-1):
+    return lib().coded_qr_factor(h, t0, t1)
+
+
+def coded_qr_inject_erasure(h, tiles):
+    flat = (C.c_int32 * max(1, 2 * len(tiles)))(*[int(v) for t in tiles for v in t])
+    return lib().coded_qr_inject_erasure(h, flat, len(tiles))
+
+
+def coded_qr_recover(h):
+    n = C.c_int32(0)
+    st = lib().coded_qr_recover(h, C.byref(n))
+    return st, n.value
+
+
+def coded_qr_post_orth(h, Q_ptr, ldq, y_ptr, ldy, yo_ptr, ldyo, nrhs):
+    return lib().coded_qr_post_orth(h, C.c_void_p(Q_ptr or None), ldq, C.c_void_p(y_ptr or None),
+                                    ldy, C.c_void_p(yo_ptr or None), ldyo, nrhs)
+
+
+def coded_qr_solve(h, y_ptr, ldy, x_ptr, ldx, nrhs):
+    return lib().coded_qr_solve(h, C.c_void_p(y_ptr), ldy, C.c_void_p(x_ptr), ldx, nrhs)
+
+
+def coded_qr_run(h, A_ptr, lda, y_ptr, ldy, x_ptr, ldx, nrhs, plan, flags=0):
+    flat = (C.c_int32 * max(1, 3 * len(plan)))(*[int(v) for p in plan for v in p])
+    return lib().coded_qr_run(h, C.c_void_p(A_ptr), lda, C.c_void_p(y_ptr or None), ldy,
+                              C.c_void_p(x_ptr or None), ldx, nrhs, flat, len(plan), flags)
+
+
+def coded_qr_get_factors(h):
+    q, r = C.c_void_p(), C.c_void_p()
+    lq, lr = C.c_int64(), C.c_int64()
+    check(lib().coded_qr_get_factors(h, C.byref(q), C.byref(lq), C.byref(r), C.byref(lr)),
+          "coded_qr_get_factors")
+    return q.value, lq.value, r.value, lr.value
+
+
+def coded_qr_get_generator(h, f, p_r, p_c):
+    Gt = np.zeros(max(1, f * p_r))
+    Gh = np.zeros(max(1, f * p_c))
+    check(lib().coded_qr_get_generator(h, Gt.ctypes.data_as(C.POINTER(C.c_double)),
+                                       Gh.ctypes.data_as(C.POINTER(C.c_double))),
+          "coded_qr_get_generator")
+    return Gt[: f * p_r].reshape(f, p_r), Gh[: f * p_c].reshape(p_c, f)
+
+
+def coded_qr_get_decode_sets(h):
+    n = C.c_int32(0)
+    check(lib().coded_qr_get_decode_sets(h, None, 0, C.byref(n)), "coded_qr_get_decode_sets")
+    buf = (C.c_int32 * max(1, n.value))()
+    check(lib().coded_qr_get_decode_sets(h, buf, n.value, C.byref(n)), "coded_qr_get_decode_sets")
+    return [int(buf[i]) for i in range(n.value)]
+
+
+def coded_qr_stats(h):
+    out = (C.c_int64 * 4)()
+    check(lib().coded_qr_stats(h, out), "coded_qr_stats")
+    return dict(n_reorth=out[0], n_recovered=out[1], panels_run=out[2], n_injected=out[3])
+
+
+def coded_qr_sync_status(h):
+    return lib().coded_qr_sync_status(h)
+
+
+# ------------------------------------------------------------------ torch convenience layer
+class _DevView:
+    """__cuda_array_interface__ over memory owned by the library (borrowed)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
+def colmajor_empty(rows, cols, dtype, device="cuda", ld=None):
+    """A (rows x cols) column-major torch tensor (stride (1, ld))."""
+    import torch
+    ld = ld or rows
+    return torch.empty((cols, ld), dtype=dtype, device=device).t()[:rows, :]
+
+
+def _ld(t):
+    if t.dim() == 1:
+        return t.shape[0]
+    assert t.stride(0) == 1, "column-major tensor expected (stride (1, ld))"
+    return t.stride(1) if t.shape[1] > 1 else max(t.shape[0], 1)
+
+
+class CodedQR:
+    """One coded QR problem on the current CUDA device (handle wrapper)."""
+
+    def __init__(self, m, n, p_r, p_c, f, b, dtype="f64", mma="simt", protect_r=True,
+                 gdist=CQR_G_UNIF01, nrhs_max=1, seed=1, tau=0.0, stream=None, workspace=None):
+        import torch
+        self.torch = torch
+        self.tdtype = torch.float64 if dtype in ("f64", "float64") else torch.float32
+        cfg = Config()
+        cfg.m, cfg.n, cfg.p_r, cfg.p_c, cfg.f, cfg.b = m, n, p_r, p_c, f, b
+        cfg.dtype = CQR_F64 if self.tdtype == torch.float64 else CQR_F32
+        cfg.mma = {"simt": CQR_MMA_SIMT, "tf32": CQR_MMA_TF32, "3xtf32": CQR_MMA_3XTF32}[mma]
+        cfg.protect_r = int(bool(protect_r))
+        cfg.gdist = gdist
+        cfg.nrhs_max = nrhs_max
+        cfg.seed = seed
+        cfg.tau = tau
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        cfg.stream = C.c_void_p(stream.cuda_stream)
+        self.cfg = cfg
+        self._ws = None
+        if workspace == "torch":
+            nbytes = coded_qr_workspace_size(cfg)
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            base = (self._ws.data_ptr() + 255) // 256 * 256
+            self.h = coded_qr_create_in(cfg, base, nbytes)
+        else:
+            self.h = coded_qr_create(cfg)
+        self.geo = coded_qr_geometry(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            coded_qr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- hot-path verbs
+    def encode(self, A):
+        check(coded_qr_encode(self.h, A.data_ptr(), _ld(A)), "coded_qr_encode")
+
+    def factor(self, t0=0, t1=-1):
+        check(coded_qr_factor(self.h, t0, t1), "coded_qr_factor")
+
+    def inject(self, tiles):
+        check(coded_qr_inject_erasure(self.h, tiles), "coded_qr_inject_erasure")
+
+    def recover(self):
+        st, n = coded_qr_recover(self.h)
+        check(st, "coded_qr_recover")
+        return n
+
+    def post_orth(self, Q=None, y=None, yo=None):
+        nrhs = 0 if y is None else (1 if y.dim() == 1 else y.shape[1])
+        check(coded_qr_post_orth(self.h, Q.data_ptr() if Q is not None else 0,
+                                 _ld(Q) if Q is not None else 0,
+                                 y.data_ptr() if y is not None else 0,
+                                 _ld(y) if y is not None else 0,
+                                 yo.data_ptr() if yo is not None else 0,
+                                 _ld(yo) if yo is not None else 0, nrhs), "coded_qr_post_orth")
+
+    def solve(self, y, x):
+        nrhs = 1 if y.dim() == 1 else y.shape[1]
+        check(coded_qr_solve(self.h, y.data_ptr(), _ld(y), x.data_ptr(), _ld(x), nrhs),
+              "coded_qr_solve")
+
+    def run(self, A, y=None, x=None, plan=(), host=False):
+        nrhs = 0 if y is None else (1 if y.ndim == 1 else y.shape[1])
+        if host:
+            import numpy as _np
+            A_ptr = A.ctypes.data
+            lda = A.shape[0] if A.flags.f_contiguous else None
+            assert lda is not None, "host A must be Fortran-ordered"
+            y_ptr = y.ctypes.data if y is not None else 0
+            x_ptr = x.ctypes.data if x is not None else 0
+            ldy = y.shape[0] if y is not None else 0
+            ldx = x.shape[0] if x is not None else 0
+            st = coded_qr_run(self.h, A_ptr, lda, y_ptr, ldy, x_ptr, ldx, nrhs, list(plan),
+                              CQR_RUN_HOST_BUFFERS)
+        else:
+            st = coded_qr_run(self.h, A.data_ptr(), _ld(A), y.data_ptr() if y is not None else 0,
+                              _ld(y) if y is not None else 0,
+                              x.data_ptr() if x is not None else 0,
+                              _ld(x) if x is not None else 0, nrhs, list(plan), 0)
+        check(st, "coded_qr_run")
+
+    # -- inspection
+    def factors(self):
+        """Borrowed torch views (column-major) of the coded Q (M x N) and R (N x N)."""
+        q, ldq, r, ldr = coded_qr_get_factors(self.h)
+        g = self.geo
+        ts = "<f8" if self.tdtype == self.torch.float64 else "<f4"
+        Qv = self.torch.as_tensor(_DevView(q, (g["N"], ldq), ts), device="cuda").t()[: g["M"], :]
+        Rv = self.torch.as_tensor(_DevView(r, (g["N"], ldr), ts), device="cuda").t()[: g["N"], :]
+        return Qv, Rv
+
+    def generator(self):
+        return coded_qr_get_generator(self.h, self.cfg.f, self.cfg.p_r, self.cfg.p_c)
+
+    def decode_sets(self):
+        return coded_qr_get_decode_sets(self.h)
+
+    def stats(self):
+        return coded_qr_stats(self.h)
+
+    def sync_status(self):
+        return coded_qr_sync_status(self.h)

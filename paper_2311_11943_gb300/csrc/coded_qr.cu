@@ -1,0 +1,707 @@
+// coded_qr.cu -- C-ABI entry points of the coded-QR library: handle, device workspace,
+// state machine, erasure bookkeeping (host-side index sets) and the launch sequence of the
+// hot path.  Every arithmetic step runs in the kernels of cqr_kernels.cu / cqr_tc_gemm.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "coded_qr.h"
+#include "cqr_kernels.cuh"
+#include "cqr_tc_gemm.cuh"
+
+using namespace cqr;
+
+namespace {
+
+enum State { ST_CREATED = 0, ST_ENCODED = 1, ST_FACTORED = 2 };
+
+constexpr int kMaxSplits = 8;
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+  size_t Q, R, Gt, Gh, Gt_t, Gh_t, part, bar, status, P, Rb, Pt, yw, xw, plans, tc, total;
+};
+
+struct Buffers {
+  void* Q;
+  void* R;
+  double* Gt;
+  double* Gh;
+  void* Gt_t;
+  void* Gh_t;
+  void* part;
+  unsigned* bar;
+  int* status;
+  void* P;
+  void* Rb;
+  void* Pt;
+  void* yw;
+  void* xw;
+  DecodePlan* plans;
+  void* tc;
+};
+
+cqr_status validate(const cqr_config* c) {
+  if (!c) return CQR_EINVAL;
+  if (c->m < 1 || c->n < 1 || c->m < c->n) return CQR_EINVAL;
+  if (c->p_r < 1 || c->p_c < 1 || c->b < 1 || c->f < 0) return CQR_EINVAL;
+  if (c->n % c->p_c != 0) return CQR_EINVAL;
+  if (2 * c->f > c->p_r) return CQR_EINVAL;
+  if (c->protect_r && 2 * c->f > c->p_c) return CQR_EINVAL;
+  if (c->f > kMaxF || c->p_r + c->f > kMaxCode || c->p_c + c->f > kMaxCode) return CQR_ENOTSUP;
+  if (c->p_r > (int64_t)c->m) return CQR_EINVAL;
+  if (c->dtype != CQR_F64 && c->dtype != CQR_F32) return CQR_EINVAL;
+  if (c->mma < CQR_MMA_SIMT || c->mma > CQR_MMA_3XTF32) return CQR_EINVAL;
+  if (c->dtype == CQR_F64 && c->mma != CQR_MMA_SIMT) return CQR_ENOTSUP;
+  if (c->mma != CQR_MMA_SIMT && !tc_available()) return CQR_ENOTSUP;
+  if (c->gdist != CQR_G_UNIF01 && c->gdist != CQR_G_NORMAL) return CQR_EINVAL;
+  if (c->nrhs_max < 0) return CQR_EINVAL;
+  return CQR_OK;
+}
+
+Geo make_geo(const cqr_config* c) {
+  Geo g{};
+  g.m = c->m;
+  g.n = c->n;
+  g.p_r = c->p_r;
+  g.p_c = c->p_c;
+  g.f = c->f;
+  g.protect_r = (c->protect_r && c->f > 0) ? 1 : 0;
+  g.mb = (c->m + c->p_r - 1) / c->p_r;
+  g.nb = c->n / c->p_c;
+  g.m_pad = g.mb * c->p_r;
+  g.c = (int64_t)c->f * g.mb;
+  g.d = g.protect_r ? (int64_t)c->f * g.nb : 0;
+  g.M = g.m_pad + g.c;
+  g.N = g.n + g.d;
+  g.ldq = round_up(g.M, 32);
+  g.ldr = round_up(g.N, 32);
+  g.grid_rows = c->p_r + c->f;
+  g.grid_cols = c->p_c + (g.protect_r ? c->f : 0);
+  g.b = c->b;
+  g.panels = (int)((c->n + c->b - 1) / c->b);
+  return g;
+}
+
+Layout make_layout(const cqr_config* c, const Geo& g, int num_sms) {
+  const size_t s = c->dtype == CQR_F64 ? 8 : 4;
+  const int bmax = c->b < g.n ? c->b : (int)g.n;
+  const int nrhs = c->nrhs_max > 0 ? c->nrhs_max : 1;
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t at = off; off += align256(bytes ? bytes : 1); return at; };
+  L.Q = take((size_t)g.ldq * g.N * s);
+  L.R = take((size_t)g.ldr * g.N * s);
+  L.Gt = take((size_t)(c->f * c->p_r + 1) * 8);
+  L.Gh = take((size_t)(c->f * c->p_c + 1) * 8);
+  L.Gt_t = take((size_t)(c->f * c->p_r + 1) * s);
+  L.Gh_t = take((size_t)(c->f * c->p_c + 1) * s);
+  L.part = take((size_t)2 * (num_sms + 1) * ((bmax + 3) / 4 * 4) * s);
+  L.bar = take(256);
+  L.status = take(256);
+  L.P = take((size_t)kMaxSplits * bmax * g.N * s);
+  L.Rb = take((size_t)bmax * g.N * s);
+  L.Pt = take(c->dtype == CQR_F32 && c->mma != CQR_MMA_SIMT ? tc_panel_bytes(g.M, bmax) : 0);
+  L.yw = take((size_t)g.m_pad * nrhs * s);
+  L.xw = take((size_t)(g.m + g.N) * nrhs * s);
+  L.plans = take(sizeof(DecodePlan) * (size_t)(g.grid_cols + g.p_c + c->f + 2));
+  L.tc = take(c->dtype == CQR_F32 && c->mma != CQR_MMA_SIMT ? tc_workspace_bytes(g.M, g.N, bmax) : 0);
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+struct cqr_handle_s {
+  cqr_config cfg;
+  Geo g;
+  Layout L;
+  Buffers B;
+  int dev = 0, num_sms = 0;
+  bool owns_ws = false;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t st = nullptr;
+  DecodePlan* plans_host = nullptr;  // pinned
+  int* status_host = nullptr;        // pinned
+  cudaEvent_t plans_ev = nullptr;
+  std::vector<uint8_t> mask;
+  std::vector<int32_t> sets;
+  bool pending = false;
+  bool postorth_inplace = false;
+  int state = ST_CREATED;
+  int next_panel = 0;
+  int64_t n_recovered = 0, panels_run = 0, n_injected = 0;
+  size_t esz = 8;
+  double tau = 0.7071067811865476;
+  TcGemm* tc = nullptr;
+};
+
+#define CK(x)                                          \
+  do {                                                 \
+    cudaError_t e_ = (x);                              \
+    if (e_ != cudaSuccess) return CQR_ECUDA;           \
+  } while (0)
+
+namespace {
+
+template <typename T>
+T* ptr(void* p) { return reinterpret_cast<T*>(p); }
+
+cqr_status setup(cqr_handle h) {
+  char* base = reinterpret_cast<char*>(h->ws);
+  const Layout& L = h->L;
+  h->B.Q = base + L.Q;
+  h->B.R = base + L.R;
+  h->B.Gt = reinterpret_cast<double*>(base + L.Gt);
+  h->B.Gh = reinterpret_cast<double*>(base + L.Gh);
+  h->B.Gt_t = base + L.Gt_t;
+  h->B.Gh_t = base + L.Gh_t;
+  h->B.part = base + L.part;
+  h->B.bar = reinterpret_cast<unsigned*>(base + L.bar);
+  h->B.status = reinterpret_cast<int*>(base + L.status);
+  h->B.P = base + L.P;
+  h->B.Rb = base + L.Rb;
+  h->B.Pt = base + L.Pt;
+  h->B.yw = base + L.yw;
+  h->B.xw = base + L.xw;
+  h->B.plans = reinterpret_cast<DecodePlan*>(base + L.plans);
+  h->B.tc = base + L.tc;
+  h->mask.assign((size_t)h->g.grid_rows * h->g.grid_cols, 0);
+  CK(cudaMallocHost(&h->plans_host, sizeof(DecodePlan) * (size_t)(h->g.grid_cols + h->g.p_c + h->g.f + 2)));
+  CK(cudaMallocHost(&h->status_host, 4 * sizeof(int)));
+  CK(cudaEventCreateWithFlags(&h->plans_ev, cudaEventDisableTiming));
+  CK(cudaMemsetAsync(h->B.part, 0, h->L.bar - h->L.part, h->st));
+  CK(cudaMemsetAsync(h->B.status, 0, 256, h->st));
+  if (h->cfg.dtype == CQR_F32 && h->cfg.mma != CQR_MMA_SIMT) {
+    h->tc = tc_create(h->cfg.mma, h->g.M, h->g.N, std::min<int64_t>(h->cfg.b, h->g.n),
+                      ptr<float>(h->B.Q), h->g.ldq, h->B.Pt, h->B.tc, h->num_sms);
+    if (!h->tc) return CQR_ECUDA;
+  }
+  return CQR_OK;
+}
+
+cqr_status create_common(const cqr_config* cfg, void* ws, size_t bytes, bool own, cqr_handle* out) {
+  if (!out) return CQR_EINVAL;
+  *out = nullptr;
+  cqr_status v = validate(cfg);
+  if (v != CQR_OK) return v;
+  cqr_handle h = new (std::nothrow) cqr_handle_s();
+  if (!h) return CQR_ENOMEM;
+  h->cfg = *cfg;
+  if (h->cfg.nrhs_max <= 0) h->cfg.nrhs_max = 1;
+  h->g = make_geo(&h->cfg);
+  h->esz = cfg->dtype == CQR_F64 ? 8 : 4;
+  h->tau = cfg->tau == 0.0 ? 0.7071067811865476 : cfg->tau;
+  h->st = reinterpret_cast<cudaStream_t>(cfg->stream);
+  if (cudaGetDevice(&h->dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev) != cudaSuccess) {
+    delete h;
+    return CQR_ECUDA;
+  }
+  h->L = make_layout(&h->cfg, h->g, h->num_sms);
+  if (own) {
+    if (cudaMalloc(&h->ws, h->L.total) != cudaSuccess) {
+      delete h;
+      return CQR_ENOMEM;
+    }
+    h->owns_ws = true;
+  } else {
+    if (!ws || bytes < h->L.total || (reinterpret_cast<uintptr_t>(ws) & 255)) {
+      delete h;
+      return ws && bytes < h->L.total ? CQR_ENOMEM : CQR_EINVAL;
+    }
+    h->ws = ws;
+  }
+  h->ws_bytes = h->L.total;
+  cqr_status s = setup(h);
+  if (s != CQR_OK) {
+    coded_qr_destroy(h);
+    return s;
+  }
+  *out = h;
+  return CQR_OK;
+}
+
+// ------------------------------------------------------------------------------- encode
+template <typename T>
+cqr_status encode_t(cqr_handle h, const T* A, int64_t lda) {
+  const Geo& g = h->g;
+  CK(cudaMemsetAsync(h->B.status, 0, 4 * sizeof(int), h->st));
+  if (g.f > 0) {
+    CK(launch_generator<T>(g.f, g.p_r, g.p_c, h->cfg.seed, h->cfg.gdist, h->B.Gt, h->B.Gh,
+                           ptr<T>(h->B.Gt_t), ptr<T>(h->B.Gh_t), h->st));
+  }
+  CK(launch_encode<T>(g, A, lda, ptr<T>(h->B.Gt_t), ptr<T>(h->B.Gh_t), ptr<T>(h->B.Q), h->st));
+  CK(cudaMemsetAsync(h->B.R, 0, (size_t)g.ldr * g.N * sizeof(T), h->st));
+  return CQR_OK;
+}
+
+// ------------------------------------------------------------------------------- factor
+int choose_splits(int bk, int64_t w, int64_t K, int num_sms) {
+  const int64_t tiles = ((bk + 63) / 64) * ((w + 63) / 64);
+  int s = (int)((2 * num_sms + tiles - 1) / tiles);
+  if (s > kMaxSplits) s = kMaxSplits;
+  if (s < 1) s = 1;
+  while (s > 1 && K / s < 256) --s;
+  return s;
+}
+
+template <typename T>
+cqr_status panel_step(cqr_handle h, int t) {
+  const Geo& g = h->g;
+  const int64_t kb = (int64_t)t * g.b;
+  const int bk = (int)std::min<int64_t>(g.b, g.n - kb);
+  T* Q = ptr<T>(h->B.Q);
+  T* R = ptr<T>(h->B.R);
+  const bool tc = h->tc != nullptr;
+  PanelPlan pp = plan_panel(g.M, bk, sizeof(T), h->num_sms);
+  CK(launch_panel<T>(pp, Q + kb * g.ldq, g.ldq, R + kb + kb * g.ldr, g.ldr, g.M, bk, h->tau,
+                     ptr<T>(h->B.part), h->B.bar, h->B.status, (int)kb, h->st));
+  const int64_t j0 = kb + bk;
+  if (j0 >= g.N) return CQR_OK;
+  const int64_t w = g.N - j0;
+  if (tc) {
+    if (tc_trailing_update(h->tc, kb, bk, j0, w, ptr<float>(h->B.R), g.ldr, h->st) != cudaSuccess)
+      return CQR_ECUDA;
+    return CQR_OK;
+  }
+  const int splits = choose_splits(bk, w, g.M, h->num_sms);
+  CK(launch_gemm_tn_splitk<T>(Q + kb * g.ldq, g.ldq, Q + j0 * g.ldq, g.ldq, g.M, bk, w, splits,
+                              ptr<T>(h->B.P), h->st));
+  CK(launch_splitk_reduce<T>(ptr<T>(h->B.P), splits, bk, w, R + kb + j0 * g.ldr, g.ldr,
+                             ptr<T>(h->B.Rb), h->st));
+  CK(launch_gemm_nn_sub<T>(Q + kb * g.ldq, g.ldq, ptr<T>(h->B.Rb), bk, Q + j0 * g.ldq, g.ldq,
+                           g.M, bk, w, h->st));
+  return CQR_OK;
+}
+
+// ------------------------------------------------------------------------------- recover
+// Decode plan of one code (reading of the recovery Lemma: the f1 lowest-index surviving
+// checksum rows are used).  Returns false when f1 + f2 > f.
+bool make_plan(int nsys, int f, const uint8_t* lost_sys, const uint8_t* lost_chk, DecodePlan* p) {
+  p->f1 = p->f2 = 0;
+  p->nsys = nsys;
+  for (int t = 0; t < nsys; ++t)
+    if (lost_sys[t]) p->A_fail[p->f1++] = t;
+  for (int i = 0; i < f; ++i)
+    if (lost_chk[i]) p->C_fail[p->f2++] = i;
+  if (p->f1 + p->f2 > f) return false;
+  int u = 0;
+  for (int i = 0; i < f && u < p->f1; ++i)
+    if (!lost_chk[i]) p->C_use[u++] = i;
+  return u == p->f1;
+}
+
+template <typename T>
+cqr_status recover_t(cqr_handle h, int32_t* n_recovered) {
+  const Geo& g = h->g;
+  const int gc = g.grid_cols, f = g.f;
+  std::vector<DecodePlan> plans;
+  std::vector<uint8_t> ls(kMaxCode), lc(kMaxCode);
+  int nrec = 0;
+  for (int j = 0; j < gc; ++j) {
+    DecodePlan p{};
+    p.kind = 0;
+    p.idx = j;
+    for (int t = 0; t < g.p_r; ++t) ls[t] = h->mask[(size_t)t * gc + j];
+    for (int i = 0; i < f; ++i) lc[i] = h->mask[(size_t)(g.p_r + i) * gc + j];
+    if (!make_plan(g.p_r, f, ls.data(), lc.data(), &p)) return CQR_EUNRECOVERABLE;
+    if (p.f1 + p.f2 == 0) continue;
+    nrec += p.f1 + p.f2;
+    plans.push_back(p);
+  }
+  size_t nq = plans.size();
+  if (g.protect_r) {
+    for (int i = 0; i < g.p_c + f && i < g.grid_rows; ++i) {
+      DecodePlan p{};
+      p.kind = 1;
+      p.idx = i;
+      for (int j = 0; j < g.p_c; ++j) ls[j] = h->mask[(size_t)i * gc + j];
+      for (int l = 0; l < f; ++l) lc[l] = h->mask[(size_t)i * gc + g.p_c + l];
+      if (!make_plan(g.p_c, f, ls.data(), lc.data(), &p)) return CQR_EUNRECOVERABLE;
+      if (p.f1 + p.f2 == 0) continue;
+      plans.push_back(p);
+    }
+  }
+  if (!plans.empty()) {
+    CK(cudaEventSynchronize(h->plans_ev));
+    memcpy(h->plans_host, plans.data(), sizeof(DecodePlan) * plans.size());
+    CK(cudaMemcpyAsync(h->B.plans, h->plans_host, sizeof(DecodePlan) * plans.size(),
+                       cudaMemcpyHostToDevice, h->st));
+    CK(cudaEventRecord(h->plans_ev, h->st));
+    const int max_h = (int)std::max(g.mb, g.nb);
+    CK(launch_decode<T>(g, h->B.plans, (int)plans.size(), max_h, h->B.Gt, h->B.Gh,
+                        ptr<T>(h->B.Q), ptr<T>(h->B.R), h->B.status, h->st));
+  }
+  for (size_t k = 0; k < plans.size(); ++k) {
+    const DecodePlan& p = plans[k];
+    h->sets.push_back(p.kind);
+    h->sets.push_back(p.idx);
+    h->sets.push_back(p.f1);
+    h->sets.push_back(p.f2);
+    for (int a = 0; a < p.f1; ++a) h->sets.push_back(p.A_fail[a]);
+    for (int e = 0; e < p.f2; ++e) h->sets.push_back(p.C_fail[e]);
+    for (int a = 0; a < p.f1; ++a) h->sets.push_back(p.C_use[a]);
+  }
+  (void)nq;
+  std::fill(h->mask.begin(), h->mask.end(), 0);
+  h->pending = false;
+  h->n_recovered += nrec;
+  if (n_recovered) *n_recovered = nrec;
+  return CQR_OK;
+}
+
+// ------------------------------------------------------------------------------- post-orth
+template <typename T>
+cqr_status copy_pad(cqr_handle h, const T* src, int64_t lds, int64_t rows, int64_t rows_pad,
+                    int64_t cols, T* dst, int64_t ldd) {
+  if (rows_pad > rows) CK(cudaMemset2DAsync(dst + rows, ldd * sizeof(T), 0, (rows_pad - rows) * sizeof(T), cols, h->st));
+  if (dst != src)
+    CK(cudaMemcpy2DAsync(dst, ldd * sizeof(T), src, lds * sizeof(T), rows * sizeof(T), cols,
+                         cudaMemcpyDeviceToDevice, h->st));
+  return CQR_OK;
+}
+
+template <typename T>
+cqr_status post_orth_q(cqr_handle h, T* Qout, int64_t ldqo) {
+  const Geo& g = h->g;
+  T* Q = ptr<T>(h->B.Q);
+  T* dst = Qout ? Qout : Q;
+  const int64_t ldd = Qout ? ldqo : g.ldq;
+  if (h->postorth_inplace) {  // Q_1 already transformed
+    if (Qout) return copy_pad<T>(h, Q, g.ldq, g.m_pad, g.m_pad, g.n, Qout, ldqo);
+    return CQR_OK;
+  }
+  if (g.f == 0) {
+    if (Qout) return copy_pad<T>(h, Q, g.ldq, g.m_pad, g.m_pad, g.n, Qout, ldqo);
+  } else {
+    CK(launch_post_orth<T>(g, ptr<T>(h->B.Gt_t), Q, g.ldq, g.m_pad, g.n, dst, ldd, h->st));
+  }
+  if (!Qout) h->postorth_inplace = true;
+  return CQR_OK;
+}
+
+template <typename T>
+cqr_status post_orth_y(cqr_handle h, const T* y, int64_t ldy, int32_t nrhs, T* yo, int64_t ldyo) {
+  const Geo& g = h->g;
+  if (g.f == 0) return copy_pad<T>(h, y, ldy, g.m, g.m_pad, nrhs, yo, ldyo);
+  CK(launch_post_orth<T>(g, ptr<T>(h->B.Gt_t), y, ldy, g.m, nrhs, yo, ldyo, h->st));
+  return CQR_OK;
+}
+
+// ------------------------------------------------------------------------------- solve
+template <typename T>
+cqr_status solve_t(cqr_handle h, const T* y, int64_t ldy, T* x, int64_t ldx, int32_t nrhs) {
+  const Geo& g = h->g;
+  const bool square = (g.m == g.n && g.m_pad == g.m);
+  if (!square) return CQR_ENOTSUP;
+  cqr_status s = post_orth_q<T>(h, nullptr, 0);
+  if (s != CQR_OK) return s;
+  T* yo = ptr<T>(h->B.yw);
+  s = post_orth_y<T>(h, y, ldy, nrhs, yo, g.m_pad);
+  if (s != CQR_OK) return s;
+  CK(launch_gemv_t<T>(ptr<T>(h->B.Q), g.ldq, g.m_pad, g.n, yo, g.m_pad, nrhs, x, ldx, h->st));
+  CK(launch_trsv_upper<T>(ptr<T>(h->B.R), g.ldr, g.n, x, ldx, nrhs, h->B.bar, h->B.status,
+                          h->num_sms, h->st));
+  return CQR_OK;
+}
+
+cqr_status read_status(cqr_handle h, bool clear) {
+  CK(cudaMemcpyAsync(h->status_host, h->B.status, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  const int code = h->status_host[0];
+  if (clear && code != 0) CK(cudaMemsetAsync(h->B.status, 0, sizeof(int), h->st));
+  return (cqr_status)code;
+}
+
+}  // namespace
+
+// =================================================================== exported entry points
+extern "C" {
+
+cqr_status coded_qr_workspace_size(const cqr_config* cfg, size_t* bytes) {
+  if (!bytes) return CQR_EINVAL;
+  cqr_status v = validate(cfg);
+  if (v != CQR_OK) return v;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return CQR_ECUDA;
+  cqr_config c = *cfg;
+  if (c.nrhs_max <= 0) c.nrhs_max = 1;
+  Geo g = make_geo(&c);
+  *bytes = make_layout(&c, g, sms).total;
+  return CQR_OK;
+}
+
+cqr_status coded_qr_create(const cqr_config* cfg, cqr_handle* out) {
+  return create_common(cfg, nullptr, 0, true, out);
+}
+
+cqr_status coded_qr_create_in(const cqr_config* cfg, void* workspace, size_t bytes,
+                              cqr_handle* out) {
+  return create_common(cfg, workspace, bytes, false, out);
+}
+
+cqr_status coded_qr_destroy(cqr_handle h) {
+  if (!h) return CQR_OK;
+  if (h->st || true) cudaStreamSynchronize(h->st);
+  if (h->tc) tc_destroy(h->tc);
+  if (h->plans_ev) cudaEventDestroy(h->plans_ev);
+  if (h->plans_host) cudaFreeHost(h->plans_host);
+  if (h->status_host) cudaFreeHost(h->status_host);
+  if (h->owns_ws && h->ws) cudaFree(h->ws);
+  delete h;
+  return CQR_OK;
+}
+
+cqr_status coded_qr_geometry(cqr_handle h, int64_t* d) {
+  if (!h || !d) return CQR_EINVAL;
+  const Geo& g = h->g;
+  d[CQR_GEO_M] = g.m;
+  d[CQR_GEO_N] = g.n;
+  d[CQR_GEO_MB] = g.mb;
+  d[CQR_GEO_NB] = g.nb;
+  d[CQR_GEO_MPAD] = g.m_pad;
+  d[CQR_GEO_C] = g.c;
+  d[CQR_GEO_D] = g.d;
+  d[CQR_GEO_MROWS] = g.M;
+  d[CQR_GEO_NCOLS] = g.N;
+  d[CQR_GEO_LDQ] = g.ldq;
+  d[CQR_GEO_LDR] = g.ldr;
+  d[CQR_GEO_GRID_ROWS] = g.grid_rows;
+  d[CQR_GEO_GRID_COLS] = g.grid_cols;
+  d[CQR_GEO_PANELS] = g.panels;
+  return CQR_OK;
+}
+
+cqr_status coded_qr_encode(cqr_handle h, const void* A, int64_t lda) {
+  if (!h || !A || lda < h->g.m) return CQR_EINVAL;
+  cqr_status s = h->esz == 8 ? encode_t<double>(h, (const double*)A, lda)
+                             : encode_t<float>(h, (const float*)A, lda);
+  if (s != CQR_OK) return s;
+  std::fill(h->mask.begin(), h->mask.end(), 0);
+  h->sets.clear();
+  h->pending = false;
+  h->postorth_inplace = false;
+  h->next_panel = 0;
+  h->n_recovered = h->panels_run = h->n_injected = 0;
+  h->state = ST_ENCODED;
+  return CQR_OK;
+}
+
+cqr_status coded_qr_factor(cqr_handle h, int32_t t0, int32_t t1) {
+  if (!h) return CQR_EINVAL;
+  if (h->state == ST_CREATED || h->pending || h->postorth_inplace) return CQR_ESTATE;
+  if (t1 < 0) t1 = h->g.panels;
+  if (t0 != h->next_panel || t1 < t0 || t1 > h->g.panels) return CQR_ESTATE;
+  for (int t = t0; t < t1; ++t) {
+    cqr_status s = h->esz == 8 ? panel_step<double>(h, t) : panel_step<float>(h, t);
+    if (s != CQR_OK) return s;
+    ++h->panels_run;
+  }
+  h->next_panel = t1;
+  h->state = (t1 == h->g.panels) ? ST_FACTORED : ST_ENCODED;
+  return CQR_OK;
+}
+
+cqr_status coded_qr_inject_erasure(cqr_handle h, const int32_t* tiles, int32_t count) {
+  if (!h || count < 0 || (count > 0 && !tiles)) return CQR_EINVAL;
+  if (h->state == ST_CREATED || h->postorth_inplace) return CQR_ESTATE;
+  const Geo& g = h->g;
+  for (int e = 0; e < count; ++e) {
+    const int i = tiles[2 * e], j = tiles[2 * e + 1];
+    if (i < 0 || i >= g.grid_rows || j < 0 || j >= g.grid_cols) return CQR_EINVAL;
+  }
+  if (count == 0) return CQR_OK;
+  for (int e = 0; e < count; ++e) h->mask[(size_t)tiles[2 * e] * g.grid_cols + tiles[2 * e + 1]] = 1;
+  cudaError_t err = h->esz == 8
+      ? launch_poison<double>(g, tiles, count, ptr<double>(h->B.Q), ptr<double>(h->B.R), h->st)
+      : launch_poison<float>(g, tiles, count, ptr<float>(h->B.Q), ptr<float>(h->B.R), h->st);
+  if (err != cudaSuccess) return CQR_ECUDA;
+  h->pending = true;
+  h->n_injected += count;
+  return CQR_OK;
+}
+
+cqr_status coded_qr_recover(cqr_handle h, int32_t* n_recovered) {
+  if (!h) return CQR_EINVAL;
+  if (h->state == ST_CREATED) return CQR_ESTATE;
+  if (n_recovered) *n_recovered = 0;
+  if (!h->pending) return CQR_OK;
+  if (h->g.f == 0) return CQR_EUNRECOVERABLE;
+  return h->esz == 8 ? recover_t<double>(h, n_recovered) : recover_t<float>(h, n_recovered);
+}
+
+cqr_status coded_qr_post_orth(cqr_handle h, void* Q, int64_t ldq, const void* y, int64_t ldy,
+                              void* yo, int64_t ldyo, int32_t nrhs) {
+  if (!h) return CQR_EINVAL;
+  if (h->state != ST_FACTORED || h->pending) return CQR_ESTATE;
+  if (Q && ldq < h->g.m_pad) return CQR_EINVAL;
+  if (y && (nrhs < 1 || ldy < h->g.m)) return CQR_EINVAL;
+  if (y && !yo && nrhs > h->cfg.nrhs_max) return CQR_EINVAL;
+  if (y && yo && ldyo < h->g.m_pad) return CQR_EINVAL;
+  cqr_status s;
+  if (h->esz == 8) {
+    s = post_orth_q<double>(h, (double*)Q, ldq);
+    if (s == CQR_OK && y)
+      s = post_orth_y<double>(h, (const double*)y, ldy, nrhs, yo ? (double*)yo : ptr<double>(h->B.yw),
+                              yo ? ldyo : h->g.m_pad);
+  } else {
+    s = post_orth_q<float>(h, (float*)Q, ldq);
+    if (s == CQR_OK && y)
+      s = post_orth_y<float>(h, (const float*)y, ldy, nrhs, yo ? (float*)yo : ptr<float>(h->B.yw),
+                             yo ? ldyo : h->g.m_pad);
+  }
+  return s;
+}
+
+cqr_status coded_qr_solve(cqr_handle h, const void* y, int64_t ldy, void* x, int64_t ldx,
+                          int32_t nrhs) {
+  if (!h || !y || !x) return CQR_EINVAL;
+  if (h->state != ST_FACTORED || h->pending) return CQR_ESTATE;
+  if (nrhs < 1 || nrhs > h->cfg.nrhs_max || ldy < h->g.m || ldx < h->g.n) return CQR_EINVAL;
+  return h->esz == 8 ? solve_t<double>(h, (const double*)y, ldy, (double*)x, ldx, nrhs)
+                     : solve_t<float>(h, (const float*)y, ldy, (float*)x, ldx, nrhs);
+}
+
+cqr_status coded_qr_run(cqr_handle h, const void* A, int64_t lda, const void* y, int64_t ldy,
+                        void* x, int64_t ldx, int32_t nrhs, const int32_t* plan,
+                        int32_t plan_len, uint32_t flags) {
+  if (!h || !A || lda < h->g.m || plan_len < 0 || (plan_len > 0 && !plan)) return CQR_EINVAL;
+  if ((y == nullptr) != (x == nullptr)) return CQR_EINVAL;
+  if (y && (nrhs < 1 || nrhs > h->cfg.nrhs_max || ldy < h->g.m || ldx < h->g.n)) return CQR_EINVAL;
+  for (int e = 0; e < plan_len; ++e) {
+    const int t = plan[3 * e], i = plan[3 * e + 1], j = plan[3 * e + 2];
+    if (t < 0 || t >= h->g.panels || i < 0 || i >= h->g.grid_rows || j < 0 || j >= h->g.grid_cols)
+      return CQR_EINVAL;
+  }
+  const bool host = (flags & CQR_RUN_HOST_BUFFERS) != 0;
+  const size_t es = h->esz;
+  const Geo& g = h->g;
+  const void* Ad = A;
+  int64_t ldad = lda;
+  const void* yd = y;
+  int64_t ldyd = ldy;
+  void* xd = x;
+  int64_t ldxd = ldx;
+  if (host) {
+    // host -> device: A straight into the systematic block of the encoded matrix (encode then
+    // runs in place), y into the handle's workspace; x comes back from the workspace.
+    CK(cudaMemcpy2DAsync(h->B.Q, g.ldq * es, A, lda * es, g.m * es, g.n, cudaMemcpyHostToDevice, h->st));
+    Ad = h->B.Q;
+    ldad = g.ldq;
+    if (y) {
+      CK(cudaMemcpy2DAsync(h->B.xw, g.m * es, y, ldy * es, g.m * es, nrhs, cudaMemcpyHostToDevice, h->st));
+      yd = h->B.xw;
+      ldyd = g.m;
+      xd = static_cast<char*>(h->B.xw) + (size_t)g.m * nrhs * es;
+      ldxd = g.n;
+    }
+  }
+  cqr_status s = coded_qr_encode(h, Ad, ldad);
+  if (s != CQR_OK) return s;
+  std::vector<int32_t> tiles;
+  int t = 0;
+  while (t < g.panels) {
+    tiles.clear();
+    for (int e = 0; e < plan_len; ++e)
+      if (plan[3 * e] == t) {
+        tiles.push_back(plan[3 * e + 1]);
+        tiles.push_back(plan[3 * e + 2]);
+      }
+    if (!tiles.empty()) {
+      s = coded_qr_inject_erasure(h, tiles.data(), (int32_t)(tiles.size() / 2));
+      if (s == CQR_OK) s = coded_qr_recover(h, nullptr);
+      if (s != CQR_OK) return s;
+    }
+    int t_next = t + 1;
+    while (t_next < g.panels) {
+      bool hit = false;
+      for (int e = 0; e < plan_len; ++e) hit |= (plan[3 * e] == t_next);
+      if (hit) break;
+      ++t_next;
+    }
+    s = coded_qr_factor(h, t, t_next);
+    if (s != CQR_OK) return s;
+    t = t_next;
+  }
+  s = coded_qr_post_orth(h, nullptr, 0, nullptr, 0, nullptr, 0, 0);
+  if (s != CQR_OK) return s;
+  if (y) {
+    s = coded_qr_solve(h, yd, ldyd, xd, ldxd, nrhs);
+    if (s != CQR_OK) return s;
+    if (host)
+      CK(cudaMemcpy2DAsync(x, ldx * es, xd, ldxd * es, g.n * es, nrhs, cudaMemcpyDeviceToHost, h->st));
+  }
+  return read_status(h, false);
+}
+
+cqr_status coded_qr_get_factors(cqr_handle h, void** Q, int64_t* ldq, void** R, int64_t* ldr) {
+  if (!h) return CQR_EINVAL;
+  if (Q) *Q = h->B.Q;
+  if (ldq) *ldq = h->g.ldq;
+  if (R) *R = h->B.R;
+  if (ldr) *ldr = h->g.ldr;
+  return CQR_OK;
+}
+
+cqr_status coded_qr_get_generator(cqr_handle h, double* Gt, double* Gh) {
+  if (!h) return CQR_EINVAL;
+  if (h->state == ST_CREATED) return CQR_ESTATE;
+  const Geo& g = h->g;
+  if (g.f == 0) return CQR_OK;
+  if (Gt) CK(cudaMemcpyAsync(Gt, h->B.Gt, sizeof(double) * g.f * g.p_r, cudaMemcpyDeviceToHost, h->st));
+  if (Gh) CK(cudaMemcpyAsync(Gh, h->B.Gh, sizeof(double) * g.f * g.p_c, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return CQR_OK;
+}
+
+cqr_status coded_qr_get_decode_sets(cqr_handle h, int32_t* buf, int32_t cap, int32_t* len) {
+  if (!h || cap < 0 || (cap > 0 && !buf)) return CQR_EINVAL;
+  const int32_t n = (int32_t)h->sets.size();
+  for (int32_t i = 0; i < n && i < cap; ++i) buf[i] = h->sets[i];
+  if (len) *len = n;
+  return CQR_OK;
+}
+
+cqr_status coded_qr_stats(cqr_handle h, int64_t* out) {
+  if (!h || !out) return CQR_EINVAL;
+  CK(cudaMemcpyAsync(h->status_host, h->B.status, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  out[0] = h->status_host[1];
+  out[1] = h->n_recovered;
+  out[2] = h->panels_run;
+  out[3] = h->n_injected;
+  return CQR_OK;
+}
+
+cqr_status coded_qr_sync_status(cqr_handle h) {
+  if (!h) return CQR_EINVAL;
+  return read_status(h, true);
+}
+
+const char* coded_qr_errstr(cqr_status s) {
+  switch (s) {
+    case CQR_OK: return "ok";
+    case CQR_EINVAL: return "invalid argument";
+    case CQR_ENOMEM: return "out of memory";
+    case CQR_ECUDA: return "CUDA error";
+    case CQR_ESTATE: return "call out of order or erasures pending";
+    case CQR_EUNRECOVERABLE: return "erasure pattern not recoverable";
+    case CQR_EBREAKDOWN: return "Gram-Schmidt breakdown (zero or non-finite pivot)";
+    case CQR_ETIMEOUT: return "device wait timed out";
+    case CQR_ENOTSUP: return "not supported";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

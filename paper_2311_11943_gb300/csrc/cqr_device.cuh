@@ -1,0 +1,85 @@
+// cqr_device.cuh -- device-side primitives shared by the coded-QR kernels: the device
+// status word, a bounded grid-wide barrier for cooperative launches, warp reductions.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "coded_qr.h"
+
+namespace cqr {
+
+// Device status word layout (int[4]): [0] first error code (CQR_*), [1] reorthogonalisation
+// count, [2] detail of the first error (e.g. the global column of a breakdown), [3] the
+// barrier site that timed out.
+enum { ST_CODE = 0, ST_REORTH = 1, ST_DETAIL = 2, ST_SITE = 3 };
+
+__device__ __forceinline__ void set_status(int* st, int code, int detail) {
+  if (atomicCAS(st + ST_CODE, 0, code) == 0) st[ST_DETAIL] = detail;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Upper bound of one barrier wait, in SM clock cycles (about one second at 2 GHz).  A wait
+// that runs out records CQR_ETIMEOUT and returns false; every CTA then leaves the kernel.
+constexpr long long kWaitLimitCycles = 2000000000LL;
+
+// Grid-wide barrier for a cooperative launch of `nblocks` CTAs.  `bar` is a global counter
+// zeroed before the launch; `target` is a per-CTA running target (start at 0).  Ordering
+// follows the usual pattern: CTA barrier, device-scope fence, arrival, acquire-poll, fence.
+// Returns false when this CTA must abandon the kernel (own wait ran out, or another CTA
+// already recorded an error).
+__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nblocks, unsigned& target,
+                                          int* status, int site) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (nblocks == 1) return true;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    target += nblocks;
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int ok = 1;
+    const long long t0 = clock64();
+    while (ld_acquire_u32(bar) < target) {
+      if (ld_relaxed_i32(status + ST_CODE) == CQR_ETIMEOUT) { ok = 0; break; }
+      if (clock64() - t0 > kWaitLimitCycles) {
+        set_status(status, CQR_ETIMEOUT, site);
+        status[ST_SITE] = site;
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T nan_value();
+template <>
+__device__ __forceinline__ float nan_value<float>() { return __int_as_float(0x7fc00000); }
+template <>
+__device__ __forceinline__ double nan_value<double>() {
+  return __longlong_as_double(0x7ff8000000000000LL);
+}
+
+}  // namespace cqr

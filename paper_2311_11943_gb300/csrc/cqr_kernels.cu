@@ -1,0 +1,851 @@
+// cqr_kernels.cu -- CUDA-core kernels of the coded QR hot path (sm_103a):
+// generator (a1), encode (a2), panel ICGS (a3), SIMT trailing-update GEMMs (a4, a5; the
+// FP64 path and the FP32 reference path), erasure poisoning (a6), decode (a7),
+// post-orthogonalisation (a8) and the solve (a9).  Templated on the storage type.
+#include <math.h>
+
+#include "cqr_device.cuh"
+#include "cqr_kernels.cuh"
+
+namespace cqr {
+
+// ===================================================================== a1 generator
+// Construction "Q-factor checksum-generator matrix" (Section 4.2): V~ i.i.d. Unif(0,1),
+// G~_1 = -1/2 V~ V~^T; G~_h from the same stream.  SplitMix64 (Steele, Lea & Flood 2014);
+// G~_1 accumulated with explicitly rounded products and sums (t ascending) so the FP64
+// generator is bit-reproducible on any host.
+__device__ __forceinline__ uint64_t splitmix64_next(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__device__ double draw_unif01(uint64_t& s) {
+  for (;;) {
+    const uint64_t x = splitmix64_next(s) >> 11;
+    if (x != 0) return __dmul_rn(__ull2double_rn(x), 0x1.0p-53);
+  }
+}
+
+__device__ double draw_value(uint64_t& s, int gdist) {
+  if (gdist == 0) return draw_unif01(s);
+  const double u1 = draw_unif01(s), u2 = draw_unif01(s);
+  return sqrt(-2.0 * log(u1)) * cos(6.283185307179586476925286766559 * u2);  // Box-Muller
+}
+
+template <typename T>
+__global__ void k_generator(int f, int p_r, int p_c, uint64_t seed, int gdist, double* Gt,
+                            double* Gh, T* Gt_t, T* Gh_t) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint64_t s = seed;
+  const int nv = p_r - f;
+  for (int i = 0; i < f; ++i)
+    for (int t = 0; t < nv; ++t) Gt[i * p_r + f + t] = draw_value(s, gdist);
+  for (int i = 0; i < f; ++i)
+    for (int l = 0; l < f; ++l) {
+      double acc = 0.0;
+      for (int t = 0; t < nv; ++t)
+        acc = __dadd_rn(acc, __dmul_rn(Gt[i * p_r + f + t], Gt[l * p_r + f + t]));
+      Gt[i * p_r + l] = __dmul_rn(-0.5, acc);
+    }
+  for (int j = 0; j < p_c; ++j)
+    for (int l = 0; l < f; ++l) Gh[j * f + l] = draw_value(s, gdist);
+  for (int e = 0; e < f * p_r; ++e) Gt_t[e] = (T)Gt[e];
+  for (int e = 0; e < f * p_c; ++e) Gh_t[e] = (T)Gh[e];
+}
+
+template <typename T>
+cudaError_t launch_generator(int f, int p_r, int p_c, uint64_t seed, int gdist, double* Gt,
+                             double* Gh, T* Gt_t, T* Gh_t, cudaStream_t st) {
+  k_generator<T><<<1, 32, 0, st>>>(f, p_r, p_c, seed, gdist, Gt, Gh, Gt_t, Gh_t);
+  return cudaGetLastError();
+}
+
+// ===================================================================== a2 encode
+// Eq. (encoding), checksum tile formula C_{i,j} = sum_t g~_{i,t} A_{t,j} (Section 4.2).
+// Pass 1 (grid z = tile column j): one thread per local position (r, s) reads the p_r tiles
+// A_{t,j}(r, s) once, writes them into the encoded matrix (zero-padded rows) and writes the f
+// vertical checksums.  Pass 2 (grid z = tile row t, protected R only): reads the p_c tiles of
+// row t (systematic or checksum) and writes the f horizontal checksums; the corner block is
+// (G_v A) G_h.  Sums run in the oracle's order (t, resp. j, ascending).
+template <typename T>
+__global__ void __launch_bounds__(256) k_encode_vertical(Geo g, const T* __restrict__ A, int64_t lda,
+                                                          const T* __restrict__ Gt, T* __restrict__ Q) {
+  const int64_t r = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  const int64_t s = (int64_t)blockIdx.y * 8 + threadIdx.y;
+  const int j = blockIdx.z;
+  if (r >= g.mb || s >= g.nb) return;
+  const int64_t col = (int64_t)j * g.nb + s;
+  T acc[kMaxF];
+#pragma unroll
+  for (int i = 0; i < kMaxF; ++i) acc[i] = T(0);
+  for (int t = 0; t < g.p_r; ++t) {
+    const int64_t row = (int64_t)t * g.mb + r;
+    const T a = (row < g.m) ? A[row + col * lda] : T(0);
+    Q[row + col * g.ldq] = a;
+#pragma unroll
+    for (int i = 0; i < kMaxF; ++i)
+      if (i < g.f) acc[i] += Gt[i * g.p_r + t] * a;
+  }
+#pragma unroll
+  for (int i = 0; i < kMaxF; ++i)
+    if (i < g.f) Q[g.m_pad + (int64_t)i * g.mb + r + col * g.ldq] = acc[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_encode_horizontal(Geo g, const T* __restrict__ Gh, T* __restrict__ Q) {
+  const int64_t r = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  const int64_t s = (int64_t)blockIdx.y * 8 + threadIdx.y;
+  const int t = blockIdx.z;  // tile row, 0 .. p_r + f - 1
+  if (r >= g.mb || s >= g.nb) return;
+  const int64_t row = (int64_t)t * g.mb + r;
+  T acc[kMaxF];
+#pragma unroll
+  for (int l = 0; l < kMaxF; ++l) acc[l] = T(0);
+  for (int j = 0; j < g.p_c; ++j) {
+    const T a = Q[row + ((int64_t)j * g.nb + s) * g.ldq];
+#pragma unroll
+    for (int l = 0; l < kMaxF; ++l)
+      if (l < g.f) acc[l] += Gh[j * g.f + l] * a;
+  }
+#pragma unroll
+  for (int l = 0; l < kMaxF; ++l)
+    if (l < g.f) Q[row + (g.n + (int64_t)l * g.nb + s) * g.ldq] = acc[l];
+}
+
+template <typename T>
+cudaError_t launch_encode(const Geo& g, const T* A, int64_t lda, const T* Gt, const T* Gh, T* Q,
+                          cudaStream_t st) {
+  dim3 blk(32, 8);
+  dim3 grd((unsigned)((g.mb + 31) / 32), (unsigned)((g.nb + 7) / 8), (unsigned)g.p_c);
+  k_encode_vertical<T><<<grd, blk, 0, st>>>(g, A, lda, Gt, Q);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !g.protect_r || g.f == 0) return e;
+  grd.z = (unsigned)(g.p_r + g.f);
+  k_encode_horizontal<T><<<grd, blk, 0, st>>>(g, Gh, Q);
+  return cudaGetLastError();
+}
+
+// ===================================================================== a3 panel ICGS
+// Appendix A, Algorithm CGS with the ICGS reorthogonalisation.  One cooperative grid of G
+// CTAs; CTA g owns rows [g*rpc, (g+1)*rpc) of the panel (all M = m_pad + c rows take part in
+// every inner product), held in shared memory when it fits.  Per column j:
+//   v = Q[:, j:b]^T Q[:, j]            one grid-wide reduction (partials per CTA, barrier,
+//                                      every CTA sums the partials in the same fixed order)
+//   if v_j < tau^2 eta_j:              reorthogonalise column j against columns < j
+//   r_jj = sqrt(v_j), q_j = Q[:, j] / r_jj, R[j, j+1:] = v[j+1:] / r_jj,
+//   Q[:, j+1:] -= q_j R[j, j+1:]
+// eta_j = squared column norms at the panel start.  CTA 0 writes R.
+template <typename T>
+struct PanelCtx {
+  T* base;          // first row of this CTA's slice, column 0
+  int64_t cs;       // column stride of the slice
+  int nr;           // rows in the slice
+  T* part;          // [2][G][part_ld] partial sums
+  int part_ld;
+  T* red;           // shared scratch [8][part_ld]
+};
+
+template <typename T, int NT>
+__device__ __forceinline__ void panel_partial_dots(const PanelCtx<T>& c, int a_lo, int a_hi,
+                                                   int jc, int step) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  T* out = c.part + (size_t)(step & 1) * gridDim.x * c.part_ld + (size_t)blockIdx.x * c.part_ld;
+  for (int a = a_lo + warp; a < a_hi; a += NW) {
+    const T* ca = c.base + a * c.cs;
+    const T* cj = c.base + (jc < 0 ? a : jc) * c.cs;
+    T acc = T(0);
+    for (int r = lane; r < c.nr; r += 32) acc += ca[r] * cj[r];
+    acc = warp_sum(acc);
+    if (lane == 0) out[a] = acc;
+  }
+}
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using V = float4;
+  static constexpr int N = 4;
+  __device__ static void add(float* a, const float4& v) { a[0] += v.x; a[1] += v.y; a[2] += v.z; a[3] += v.w; }
+};
+template <>
+struct Vec16<double> {
+  using V = double2;
+  static constexpr int N = 2;
+  __device__ static void add(double* a, const double2& v) { a[0] += v.x; a[1] += v.y; }
+};
+
+// Every CTA sums the G partial rows for columns [a_lo, a_hi) into out[] (shared), in a
+// fixed order: group k adds rows k, k+groups, ...; then the groups are added in order.
+template <typename T, int NT>
+__device__ __forceinline__ void panel_reduce(const PanelCtx<T>& c, int a_lo, int a_hi, T* out,
+                                             int step) {
+  using VT = Vec16<T>;
+  constexpr int VN = VT::N;
+  const int G = gridDim.x;
+  const T* P = c.part + (size_t)(step & 1) * G * c.part_ld;
+  const int c0 = a_lo / VN, c1 = (a_hi + VN - 1) / VN, nch = c1 - c0;
+  int groups = NT / (nch > 0 ? nch : 1);
+  if (groups > 8) groups = 8;
+  if (groups > G) groups = G;
+  const int tid = threadIdx.x;
+  const int grp = tid / nch, ch = tid - grp * nch;
+  if (nch > 0 && grp < groups) {
+    T acc[VN];
+#pragma unroll
+    for (int e = 0; e < VN; ++e) acc[e] = T(0);
+    const typename VT::V* src = reinterpret_cast<const typename VT::V*>(P) + (c0 + ch);
+    const int rowv = c.part_ld / VN;
+    int gg = grp;
+    for (; gg + 3 * groups < G; gg += 4 * groups) {
+      const typename VT::V x0 = __ldcg(src + (size_t)gg * rowv);
+      const typename VT::V x1 = __ldcg(src + (size_t)(gg + groups) * rowv);
+      const typename VT::V x2 = __ldcg(src + (size_t)(gg + 2 * groups) * rowv);
+      const typename VT::V x3 = __ldcg(src + (size_t)(gg + 3 * groups) * rowv);
+      VT::add(acc, x0); VT::add(acc, x1); VT::add(acc, x2); VT::add(acc, x3);
+    }
+    for (; gg < G; gg += groups) VT::add(acc, __ldcg(src + (size_t)gg * rowv));
+#pragma unroll
+    for (int e = 0; e < VN; ++e) c.red[grp * c.part_ld + (c0 + ch) * VN + e] = acc[e];
+  }
+  __syncthreads();
+  for (int a = a_lo + tid; a < a_hi; a += NT) {
+    T s = T(0);
+    for (int k = 0; k < groups; ++k) s += c.red[k * c.part_ld + a];
+    out[a] = s;
+  }
+  __syncthreads();
+}
+
+template <typename T, bool SMEM, int NT>
+__global__ void __launch_bounds__(NT) k_panel(T* __restrict__ Q, int64_t ldq, T* __restrict__ R,
+                                               int64_t ldr, int64_t M, int bk, int rpc, int rpc_pad,
+                                               double tau2, T* part, int part_ld, unsigned* bar,
+                                               int* status, int col0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = NT / 32;
+  const int64_t row0 = (int64_t)g * rpc;
+  const int nr = (int)((M - row0) < rpc ? (M - row0) : rpc);
+  T* sm = reinterpret_cast<T*>(smraw);
+  T* small = sm + (SMEM ? (size_t)bk * rpc_pad : 0);
+  T* v = small;
+  T* coef = v + part_ld;
+  T* sv = coef + part_ld;
+  T* eta = sv + part_ld;
+  PanelCtx<T> c;
+  c.base = SMEM ? sm : Q + row0;
+  c.cs = SMEM ? rpc_pad : ldq;
+  c.nr = nr;
+  c.part = part;
+  c.part_ld = part_ld;
+  c.red = eta + part_ld;
+  unsigned target = 0;
+  int step = 0;
+
+  if (SMEM) {
+    for (int a = 0; a < bk; ++a)
+      for (int r = tid; r < nr; r += NT) sm[(size_t)a * rpc_pad + r] = Q[row0 + r + a * ldq];
+  }
+  __syncthreads();
+  panel_partial_dots<T, NT>(c, 0, bk, -1, step);
+  if (!grid_sync(bar, G, target, status, 1)) return;
+  panel_reduce<T, NT>(c, 0, bk, eta, step++);
+
+  for (int j = 0; j < bk; ++j) {
+    __syncthreads();
+    panel_partial_dots<T, NT>(c, j, bk, j, step);
+    if (!grid_sync(bar, G, target, status, 2)) return;
+    panel_reduce<T, NT>(c, j, bk, v, step++);
+    if (j > 0 && tau2 > 0.0 && (double)v[j] < tau2 * (double)eta[j]) {
+      panel_partial_dots<T, NT>(c, 0, j, j, step);
+      if (!grid_sync(bar, G, target, status, 3)) return;
+      panel_reduce<T, NT>(c, 0, j, sv, step++);
+      T* cj = c.base + j * c.cs;
+      for (int r = tid; r < nr; r += NT) {
+        T acc = cj[r];
+        for (int a = 0; a < j; ++a) acc -= c.base[a * c.cs + r] * sv[a];
+        cj[r] = acc;
+      }
+      if (g == 0) {
+        for (int a = tid; a < j; a += NT) R[a + j * ldr] += sv[a];
+        if (tid == 0) atomicAdd(status + ST_REORTH, 1);
+      }
+      __syncthreads();
+      panel_partial_dots<T, NT>(c, j, bk, j, step);
+      if (!grid_sync(bar, G, target, status, 4)) return;
+      panel_reduce<T, NT>(c, j, bk, v, step++);
+    }
+    const T v0 = v[j];
+    if (!(v0 > T(0)) || !isfinite(v0)) {
+      if (g == 0 && tid == 0) set_status(status, CQR_EBREAKDOWN, col0 + j);
+      return;
+    }
+    const T rjj = sqrt(v0);
+    for (int a = j + 1 + tid; a < bk; a += NT) {
+      const T ca = v[a] / rjj;
+      coef[a] = ca;
+      if (g == 0) R[j + a * ldr] = ca;
+    }
+    if (g == 0 && tid == 0) R[j + j * ldr] = rjj;
+    T* cj = c.base + j * c.cs;
+    for (int r = tid; r < nr; r += NT) cj[r] = cj[r] / rjj;
+    __syncthreads();
+    for (int a = j + 1 + warp; a < bk; a += NW) {
+      const T ca = coef[a];
+      T* pa = c.base + a * c.cs;
+      for (int r = lane; r < nr; r += 32) pa[r] -= cj[r] * ca;
+    }
+  }
+  __syncthreads();
+  if (SMEM) {
+    for (int a = 0; a < bk; ++a)
+      for (int r = tid; r < nr; r += NT) Q[row0 + r + a * ldq] = sm[(size_t)a * rpc_pad + r];
+  }
+}
+
+constexpr int kPanelThreads = 256;
+constexpr size_t kSmemCap = 227 * 1024;
+
+static int part_ld_of(int bk) { return (bk + 3) / 4 * 4; }
+
+PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms) {
+  PanelPlan p{};
+  const int pld = part_ld_of(bk);
+  const size_t small = (size_t)(4 + 8) * pld * elem + 256;
+  const size_t room = kSmemCap - small - 1024;
+  int64_t rpc_max = (int64_t)(room / ((size_t)bk * elem));
+  if (rpc_max > 4096) rpc_max = 4096;
+  int64_t G = rpc_max > 0 ? (M + rpc_max - 1) / rpc_max : (int64_t)num_sms + 1;
+  if (G < 1) G = 1;
+  if (G <= num_sms) {
+    p.smem = 1;
+    p.G = (int)G;
+    p.rpc = (int)((M + G - 1) / G);
+    p.G = (int)((M + p.rpc - 1) / p.rpc);
+    p.rpc_pad = p.rpc | 1;
+    p.smem_bytes = (size_t)bk * p.rpc_pad * elem + small;
+  } else {
+    p.smem = 0;
+    p.G = num_sms;
+    p.rpc = (int)((M + num_sms - 1) / num_sms);
+    p.G = (int)((M + p.rpc - 1) / p.rpc);
+    p.rpc_pad = p.rpc;
+    p.smem_bytes = small;
+  }
+  return p;
+}
+
+template <typename T>
+cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t ldr, int64_t M,
+                         int bk, double tau, T* part, unsigned* bar, int* status, int col0,
+                         cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  int part_ld = part_ld_of(bk);
+  double tau2 = tau > 0.0 ? tau * tau : -1.0;
+  void* args[] = {&Q, &ldq, &R, &ldr, &M, &bk, (void*)&pp.rpc, (void*)&pp.rpc_pad, &tau2,
+                  &part, &part_ld, &bar, &status, &col0};
+  const void* fn = pp.smem ? (const void*)k_panel<T, true, kPanelThreads>
+                           : (const void*)k_panel<T, false, kPanelThreads>;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp.smem_bytes);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchCooperativeKernel(fn, dim3(pp.G), dim3(kPanelThreads), args, pp.smem_bytes, st);
+}
+
+// ===================================================================== a4/a5 SIMT GEMMs
+// Rbar = Qbar^T Qtrail (split over K) and Qtrail -= Qbar Rbar on CUDA cores: the FP64 path
+// and the FP32 reference path.  64 x 64 output tiles, 256 threads, 4 x 4 per thread with a
+// stride-16 micro-tile so that each half-warp touches 16 consecutive rows.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_tn_splitk(const T* __restrict__ A, int64_t lda,
+                                                         const T* __restrict__ B, int64_t ldb,
+                                                         int64_t K, int bk, int64_t w,
+                                                         int64_t kchunk, T* __restrict__ P) {
+  __shared__ T As[32][65];
+  __shared__ T Bs[32][65];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.x * 64;
+  const int64_t j0 = (int64_t)blockIdx.y * 64;
+  const int64_t k0 = (int64_t)blockIdx.z * kchunk;
+  const int64_t k1 = (k0 + kchunk < K) ? k0 + kchunk : K;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int64_t kb = k0; kb < k1; kb += 32) {
+    const int kk = tid & 31;
+    const int64_t k = kb + kk;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int ii = (tid >> 5) + 8 * e;
+      const int i = i0 + ii;
+      As[kk][ii] = (k < k1 && i < bk) ? A[k + (int64_t)i * lda] : T(0);
+      const int64_t j = j0 + ii;
+      Bs[kk][ii] = (k < k1 && j < w) ? B[k + j * ldb] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) {
+      T a[4], b[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { a[e] = As[q][tx + 16 * e]; b[e] = Bs[q][ty + 16 * e]; }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
+    }
+    __syncthreads();
+  }
+  T* Ps = P + (size_t)blockIdx.z * (size_t)bk * (size_t)w;
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int i = i0 + tx + 16 * x;
+      const int64_t j = j0 + ty + 16 * y;
+      if (i < bk && j < w) Ps[i + j * bk] = acc[x][y];
+    }
+}
+
+template <typename T>
+cudaError_t launch_gemm_tn_splitk(const T* A, int64_t lda, const T* B, int64_t ldb, int64_t K,
+                                  int bk, int64_t w, int splits, T* P, cudaStream_t st) {
+  int64_t kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + 31) / 32 * 32;
+  dim3 grd((unsigned)((bk + 63) / 64), (unsigned)((w + 63) / 64), (unsigned)splits);
+  k_gemm_tn_splitk<T><<<grd, 256, 0, st>>>(A, lda, B, ldb, K, bk, w, kchunk, P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_splitk_reduce(const T* __restrict__ P, int splits, int bk, int64_t w,
+                                T* __restrict__ R, int64_t ldr, T* __restrict__ Rb) {
+  const int64_t total = (int64_t)bk * w;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    T s = T(0);
+    for (int sp = 0; sp < splits; ++sp) s += P[(size_t)sp * total + idx];
+    const int64_t i = idx % bk, j = idx / bk;
+    R[i + j * ldr] = s;
+    Rb[idx] = s;
+  }
+}
+
+template <typename T>
+cudaError_t launch_splitk_reduce(const T* P, int splits, int bk, int64_t w, T* R, int64_t ldr,
+                                 T* Rb, cudaStream_t st) {
+  const int64_t total = (int64_t)bk * w;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_splitk_reduce<T><<<blocks, 256, 0, st>>>(P, splits, bk, w, R, ldr, Rb);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_nn_sub(const T* __restrict__ A, int64_t lda,
+                                                      const T* __restrict__ B, int64_t ldb,
+                                                      T* __restrict__ C, int64_t ldc, int64_t M,
+                                                      int bk, int64_t w) {
+  __shared__ T As[32][65];
+  __shared__ T Bs[32][65];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t i0 = (int64_t)blockIdx.x * 64;
+  const int64_t j0 = (int64_t)blockIdx.y * 64;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int kb = 0; kb < bk; kb += 32) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int ii = tid & 63, kk = (tid >> 6) + 4 * e;
+      const int64_t i = i0 + ii;
+      const int k = kb + kk;
+      As[kk][ii] = (i < M && k < bk) ? A[i + (int64_t)k * lda] : T(0);
+      const int kk2 = tid & 31, jj = (tid >> 5) + 8 * e;
+      const int64_t j = j0 + jj;
+      const int k2 = kb + kk2;
+      Bs[kk2][jj] = (j < w && k2 < bk) ? B[k2 + j * ldb] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) {
+      T a[4], b[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { a[e] = As[q][tx + 16 * e]; b[e] = Bs[q][ty + 16 * e]; }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int64_t i = i0 + tx + 16 * x;
+      const int64_t j = j0 + ty + 16 * y;
+      if (i < M && j < w) C[i + j * ldc] -= acc[x][y];
+    }
+}
+
+template <typename T>
+cudaError_t launch_gemm_nn_sub(const T* A, int64_t lda, const T* B, int64_t ldb, T* C,
+                               int64_t ldc, int64_t M, int bk, int64_t w, cudaStream_t st) {
+  dim3 grd((unsigned)((M + 63) / 64), (unsigned)((w + 63) / 64));
+  k_gemm_nn_sub<T><<<grd, 256, 0, st>>>(A, lda, B, ldb, C, ldc, M, bk, w);
+  return cudaGetLastError();
+}
+
+// ===================================================================== a6 erasure
+// Section 2 "Failure model": a failed node loses its data -- its tiles are overwritten with
+// NaN so that any later read of an erased value propagates into the results.
+struct TileList {
+  int count;
+  int ij[2 * 64];
+};
+
+template <typename T>
+__global__ void k_poison(T* __restrict__ X, int64_t ld, int64_t th, int64_t tw, TileList tl) {
+  const int e = blockIdx.y;
+  const int i = tl.ij[2 * e], j = tl.ij[2 * e + 1];
+  const int64_t total = th * tw;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx % th, s = idx / th;
+    X[(int64_t)i * th + r + ((int64_t)j * tw + s) * ld] = nan_value<T>();
+  }
+}
+
+template <typename T>
+cudaError_t launch_poison(const Geo& g, const int* tiles, int count, T* Q, T* R,
+                          cudaStream_t st) {
+  for (int base = 0; base < count; base += 64) {
+    TileList q{}, rl{};
+    const int n = (count - base) < 64 ? (count - base) : 64;
+    for (int e = 0; e < n; ++e) {
+      const int i = tiles[2 * (base + e)], j = tiles[2 * (base + e) + 1];
+      q.ij[2 * q.count] = i;
+      q.ij[2 * q.count + 1] = j;
+      ++q.count;
+      if (g.protect_r && i < g.p_c + g.f) {
+        rl.ij[2 * rl.count] = i;
+        rl.ij[2 * rl.count + 1] = j;
+        ++rl.count;
+      }
+    }
+    int bx = (int)((g.mb * g.nb + 255) / 256);
+    if (bx > 1024) bx = 1024;
+    k_poison<T><<<dim3(bx, q.count), 256, 0, st>>>(Q, g.ldq, g.mb, g.nb, q);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (rl.count > 0) {
+      int by = (int)((g.nb * g.nb + 255) / 256);
+      if (by > 1024) by = 1024;
+      k_poison<T><<<dim3(by, rl.count), 256, 0, st>>>(R, g.ldr, g.nb, g.nb, rl);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+// ===================================================================== a7 decode
+// Recovery Lemma (Appendix, Eq. (A_recov)), second form: each lost systematic tile is a
+// linear combination of the surviving systematic tiles and the used checksum tiles, with
+// coefficients from G^-1 (FP64 Gauss-Jordan with partial pivoting on the device, one thread
+// per CTA).  Lost checksum tiles are re-encoded from the systematic tiles (surviving and
+// rebuilt).  One CTA column per plan; the same kernel serves the vertical code of a Q grid
+// column (tile index along rows) and the horizontal code of an R block row (along columns).
+template <typename T>
+__global__ void __launch_bounds__(256) k_decode(Geo g, const DecodePlan* __restrict__ plans,
+                                                 const double* __restrict__ Gt,
+                                                 const double* __restrict__ Gh, T* Q, T* R,
+                                                 int* status) {
+  const DecodePlan& p = plans[blockIdx.z];
+  const bool isQ = (p.kind == 0);
+  const int nsys = p.nsys, f = g.f, f1 = p.f1, f2 = p.f2;
+  __shared__ double Ginv[kMaxF * kMaxF];
+  __shared__ T coef[kMaxF][kMaxCode];   // lost systematic b <- code tile t (nsys + f columns)
+  __shared__ T cenc[kMaxF][kMaxCode];   // lost checksum e <- systematic tile t
+  __shared__ int lost[kMaxCode];
+  __shared__ int s_bad;
+  __shared__ double a[kMaxF][2 * kMaxF];  // Gauss-Jordan tableau [G^ | I]
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  auto gen = [&](int i, int t) -> double { return isQ ? Gt[i * g.p_r + t] : Gh[t * f + i]; };
+  if (tid == 0) {
+    s_bad = 0;
+    for (int t = 0; t < nsys + f; ++t) lost[t] = 0;
+    for (int b = 0; b < f1; ++b) lost[p.A_fail[b]] = 1;
+    for (int e = 0; e < f2; ++e) lost[nsys + p.C_fail[e]] = 1;
+    // G^ = G~[C_use, A_fail]; invert by Gauss-Jordan (Golub & Van Loan 3.4), FP64
+    for (int r = 0; r < f1; ++r)
+      for (int q = 0; q < 2 * f1; ++q)
+        a[r][q] = (q < f1) ? gen(p.C_use[r], p.A_fail[q]) : (q - f1 == r ? 1.0 : 0.0);
+    for (int col = 0; col < f1 && !s_bad; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < f1; ++r)
+        if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+      if (!(fabs(a[piv][col]) > 0.0)) { s_bad = 1; break; }
+      if (piv != col)
+        for (int q = 0; q < 2 * f1; ++q) { double t = a[col][q]; a[col][q] = a[piv][q]; a[piv][q] = t; }
+      const double pv = a[col][col];
+      for (int q = 0; q < 2 * f1; ++q) a[col][q] = a[col][q] / pv;
+      for (int r = 0; r < f1; ++r) {
+        if (r == col) continue;
+        const double fc = a[r][col];
+        if (fc != 0.0)
+          for (int q = 0; q < 2 * f1; ++q) a[r][q] -= fc * a[col][q];
+      }
+    }
+    for (int r = 0; r < f1; ++r)
+      for (int q = 0; q < f1; ++q) Ginv[r * kMaxF + q] = a[r][f1 + q];
+    if (s_bad && blockIdx.x == 0 && blockIdx.y == 0) set_status(status, CQR_EUNRECOVERABLE, p.idx);
+  }
+  __syncthreads();
+  if (s_bad) return;
+  for (int idx = tid; idx < f1 * (nsys + f); idx += blockDim.x * blockDim.y) {
+    const int b = idx / (nsys + f), t = idx % (nsys + f);
+    double cv = 0.0;
+    if (t < nsys) {
+      if (!lost[t])
+        for (int a = 0; a < f1; ++a) cv -= Ginv[b * kMaxF + a] * gen(p.C_use[a], t);
+    } else {
+      for (int a = 0; a < f1; ++a)
+        if (p.C_use[a] == t - nsys) cv = Ginv[b * kMaxF + a];
+    }
+    coef[b][t] = (T)cv;
+  }
+  for (int idx = tid; idx < f2 * nsys; idx += blockDim.x * blockDim.y) {
+    const int e = idx / nsys, t = idx % nsys;
+    cenc[e][t] = (T)gen(p.C_fail[e], t);
+  }
+  __syncthreads();
+  const int64_t h = isQ ? g.mb : g.nb;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t s = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+  if (r >= h || s >= g.nb) return;
+  T* base = isQ ? Q + (int64_t)p.idx * g.nb * g.ldq : R + (int64_t)p.idx * g.nb;
+  const int64_t tstride = isQ ? g.mb : g.nb * g.ldr;
+  const int64_t ld = isQ ? g.ldq : g.ldr;
+  T* ptr = base + r + s * ld;
+  T xb[kMaxF], ce[kMaxF];
+#pragma unroll
+  for (int k = 0; k < kMaxF; ++k) { xb[k] = T(0); ce[k] = T(0); }
+  for (int t = 0; t < nsys + f; ++t) {
+    if (lost[t]) continue;
+    bool used = (t < nsys);
+    if (!used)
+      for (int a = 0; a < f1; ++a) used |= (p.C_use[a] == t - nsys);
+    if (!used) continue;
+    const T val = ptr[(int64_t)t * tstride];
+#pragma unroll
+    for (int b = 0; b < kMaxF; ++b)
+      if (b < f1) xb[b] += coef[b][t] * val;
+    if (t < nsys) {
+#pragma unroll
+      for (int e = 0; e < kMaxF; ++e)
+        if (e < f2) ce[e] += cenc[e][t] * val;
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < kMaxF; ++b)
+    if (b < f1) {
+      ptr[(int64_t)p.A_fail[b] * tstride] = xb[b];
+#pragma unroll
+      for (int e = 0; e < kMaxF; ++e)
+        if (e < f2) ce[e] += cenc[e][p.A_fail[b]] * xb[b];
+    }
+#pragma unroll
+  for (int e = 0; e < kMaxF; ++e)
+    if (e < f2) ptr[(int64_t)(nsys + p.C_fail[e]) * tstride] = ce[e];
+}
+
+template <typename T>
+cudaError_t launch_decode(const Geo& g, const DecodePlan* plans_dev, int nplans, int max_h,
+                          const double* Gt, const double* Gh, T* Q, T* R, int* status,
+                          cudaStream_t st) {
+  if (nplans == 0) return cudaSuccess;
+  dim3 blk(32, 8);
+  dim3 grd((unsigned)((max_h + 31) / 32), (unsigned)((g.nb + 7) / 8), (unsigned)nplans);
+  k_decode<T><<<grd, blk, 0, st>>>(g, plans_dev, Gt, Gh, Q, R, status);
+  return cudaGetLastError();
+}
+
+// ===================================================================== a8 post-orth
+// Sparse block pipeline of G_0 Z (Appendix, proof of the overhead theorem): with
+// H = I + G~_1 and Z_t the t-th block row,
+//   W_i = sum_{l<f} h_{i,l} Z_l + sum_{t>=f} g~_{i,t} Z_t   (i < f)
+//   W_i = sum_{l<f} g~_{l,i} Z_l - Z_i                      (i >= f)
+// One thread per (local row, column): reads each Z_t once, writes each W_i once (in place
+// is safe: every thread owns one position across all block rows).
+template <typename T>
+__global__ void __launch_bounds__(256) k_post_orth(Geo g, const T* __restrict__ Gt, const T* Z,
+                                                    int64_t ldz, int64_t zrows, int64_t k, T* W,
+                                                    int64_t ldw) {
+  const int64_t s = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  const int64_t col = (int64_t)blockIdx.y * 8 + threadIdx.y;
+  if (s >= g.mb || col >= k) return;
+  const int f = g.f, p_r = g.p_r;
+  const T* zc = Z + col * ldz;
+  T* wc = W + col * ldw;
+  T zl[kMaxF], acc[kMaxF];
+#pragma unroll
+  for (int l = 0; l < kMaxF; ++l) {
+    const int64_t row = (int64_t)l * g.mb + s;
+    zl[l] = (l < f && row < zrows) ? zc[row] : T(0);
+  }
+#pragma unroll
+  for (int i = 0; i < kMaxF; ++i) {
+    T a = T(0);
+    if (i < f) {
+#pragma unroll
+      for (int l = 0; l < kMaxF; ++l)
+        if (l < f) a += ((l == i ? T(1) : T(0)) + Gt[i * p_r + l]) * zl[l];
+    }
+    acc[i] = a;
+  }
+  for (int t = f; t < p_r; ++t) {
+    const int64_t row = (int64_t)t * g.mb + s;
+    const T z = row < zrows ? zc[row] : T(0);
+#pragma unroll
+    for (int i = 0; i < kMaxF; ++i)
+      if (i < f) acc[i] += Gt[i * p_r + t] * z;
+    T wv = T(0);
+#pragma unroll
+    for (int l = 0; l < kMaxF; ++l)
+      if (l < f) wv += Gt[l * p_r + t] * zl[l];
+    wc[row] = wv - z;
+  }
+#pragma unroll
+  for (int i = 0; i < kMaxF; ++i)
+    if (i < f) wc[(int64_t)i * g.mb + s] = acc[i];
+}
+
+template <typename T>
+cudaError_t launch_post_orth(const Geo& g, const T* Gt_t, const T* Z, int64_t ldz,
+                             int64_t zrows, int64_t k, T* W, int64_t ldw, cudaStream_t st) {
+  dim3 blk(32, 8);
+  dim3 grd((unsigned)((g.mb + 31) / 32), (unsigned)((k + 7) / 8));
+  k_post_orth<T><<<grd, blk, 0, st>>>(g, Gt_t, Z, ldz, zrows, k, W, ldw);
+  return cudaGetLastError();
+}
+
+// ===================================================================== a9 solve
+// z = Qo^T yo (Eq. (linearsolve3)), one warp per output entry.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemv_t(const T* __restrict__ Qo, int64_t ldq, int64_t rows,
+                                                 int64_t n, const T* __restrict__ y, int64_t ldy,
+                                                 int64_t k, T* __restrict__ z, int64_t ldz) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int64_t col = blockIdx.y;
+  if (j >= n) return;
+  const T* q = Qo + j * ldq;
+  const T* yy = y + col * ldy;
+  T acc = T(0);
+  for (int64_t r = lane; r < rows; r += 32) acc += q[r] * yy[r];
+  acc = warp_sum(acc);
+  if (lane == 0) z[j + col * ldz] = acc;
+}
+
+template <typename T>
+cudaError_t launch_gemv_t(const T* Qo, int64_t ldq, int64_t rows, int64_t n, const T* y,
+                          int64_t ldy, int64_t k, T* z, int64_t ldz, cudaStream_t st) {
+  dim3 grd((unsigned)((n + 7) / 8), (unsigned)k);
+  k_gemv_t<T><<<grd, 256, 0, st>>>(Qo, ldq, rows, n, y, ldy, k, z, ldz);
+  return cudaGetLastError();
+}
+
+// Blocked column-oriented back substitution (Golub & Van Loan Alg. 3.1.4), cooperative grid:
+// CTA 0 solves each 64 x 64 diagonal block, then all CTAs update the rows above it.
+template <typename T>
+__global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ R, int64_t ldr, int64_t n,
+                                                     T* x, int64_t ldx, int64_t k, unsigned* bar,
+                                                     int* status) {
+  constexpr int BS = 64;
+  const int G = gridDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned target = 0;
+  const int64_t nblk = (n + BS - 1) / BS;
+  for (int64_t blk = nblk - 1; blk >= 0; --blk) {
+    const int64_t i0 = blk * BS;
+    const int64_t i1 = (i0 + BS < n) ? i0 + BS : n;
+    const int nbk = (int)(i1 - i0);
+    if (blockIdx.x == 0) {
+      for (int64_t col = warp; col < k; col += 8) {
+        T* xc = x + col * ldx + i0;
+        for (int i = nbk - 1; i >= 0; --i) {
+          T xi = T(0);
+          if (lane == 0) {
+            xi = __ldcg(xc + i) / R[(i0 + i) + (i0 + i) * ldr];
+            xc[i] = xi;
+          }
+          xi = __shfl_sync(0xffffffffu, xi, 0);
+          for (int r = lane; r < i; r += 32) xc[r] = __ldcg(xc + r) - R[(i0 + r) + (i0 + i) * ldr] * xi;
+          __syncwarp();
+        }
+      }
+    }
+    if (!grid_sync(bar, G, target, status, 10)) return;
+    for (int64_t col = 0; col < k; ++col) {
+      T* xc = x + col * ldx;
+      for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < i0;
+           r += (int64_t)G * blockDim.x) {
+        T acc = __ldcg(xc + r);
+        for (int64_t j = i0; j < i1; ++j) acc -= R[r + j * ldr] * __ldcg(xc + j);
+        xc[r] = acc;
+      }
+    }
+    if (!grid_sync(bar, G, target, status, 11)) return;
+  }
+}
+
+template <typename T>
+cudaError_t launch_trsv_upper(const T* R, int64_t ldr, int64_t n, T* x, int64_t ldx, int64_t k,
+                              unsigned* bar, int* status, int num_sms, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  int G = (int)((n + 255) / 256);
+  if (G > num_sms) G = num_sms;
+  if (G < 1) G = 1;
+  void* args[] = {(void*)&R, &ldr, &n, &x, &ldx, &k, &bar, &status};
+  return cudaLaunchCooperativeKernel((const void*)k_trsv_upper<T>, dim3(G), dim3(256), args, 0, st);
+}
+
+// ===================================================================== instantiations
+#define CQR_INSTANTIATE(T)                                                                        \
+  template cudaError_t launch_generator<T>(int, int, int, uint64_t, int, double*, double*, T*,   \
+                                           T*, cudaStream_t);                                     \
+  template cudaError_t launch_encode<T>(const Geo&, const T*, int64_t, const T*, const T*, T*,   \
+                                        cudaStream_t);                                            \
+  template cudaError_t launch_panel<T>(const PanelPlan&, T*, int64_t, T*, int64_t, int64_t, int, \
+                                       double, T*, unsigned*, int*, int, cudaStream_t);           \
+  template cudaError_t launch_gemm_tn_splitk<T>(const T*, int64_t, const T*, int64_t, int64_t,   \
+                                                int, int64_t, int, T*, cudaStream_t);             \
+  template cudaError_t launch_splitk_reduce<T>(const T*, int, int, int64_t, T*, int64_t, T*,     \
+                                               cudaStream_t);                                     \
+  template cudaError_t launch_gemm_nn_sub<T>(const T*, int64_t, const T*, int64_t, T*, int64_t,  \
+                                             int64_t, int, int64_t, cudaStream_t);                \
+  template cudaError_t launch_poison<T>(const Geo&, const int*, int, T*, T*, cudaStream_t);      \
+  template cudaError_t launch_decode<T>(const Geo&, const DecodePlan*, int, int, const double*,  \
+                                        const double*, T*, T*, int*, cudaStream_t);               \
+  template cudaError_t launch_post_orth<T>(const Geo&, const T*, const T*, int64_t, int64_t,     \
+                                           int64_t, T*, int64_t, cudaStream_t);                   \
+  template cudaError_t launch_gemv_t<T>(const T*, int64_t, int64_t, int64_t, const T*, int64_t,  \
+                                        int64_t, T*, int64_t, cudaStream_t);                      \
+  template cudaError_t launch_trsv_upper<T>(const T*, int64_t, int64_t, T*, int64_t, int64_t,    \
+                                            unsigned*, int*, int, cudaStream_t);
+
+CQR_INSTANTIATE(float)
+CQR_INSTANTIATE(double)
+
+}  // namespace cqr

@@ -1,0 +1,89 @@
+// cqr_kernels.cuh -- launchers of the coded-QR kernels (host-callable, stream-ordered).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cqr {
+
+// Geometry of one coded problem (see coded_qr.h, "Geometry").
+struct Geo {
+  int64_t m, n, mb, nb, m_pad, c, d, M, N, ldq, ldr;
+  int p_r, p_c, f, protect_r, grid_rows, grid_cols, panels, b;
+};
+
+// Decode plan of one grid column (Q, vertical code) or one R block row (horizontal code).
+constexpr int kMaxF = 16;
+constexpr int kMaxCode = 128;  // p_r + f (Q) or p_c + f (R)
+struct DecodePlan {
+  int kind;       // 0: Q grid column `idx`; 1: R block row `idx`
+  int idx;
+  int f1, f2;     // lost systematic / lost checksum tiles
+  int nsys;       // systematic tiles in the code (p_r for Q, p_c for R)
+  int pad_;
+  int A_fail[kMaxF];
+  int C_fail[kMaxF];
+  int C_use[kMaxF];
+};
+
+// Panel factorisation launch plan.
+struct PanelPlan {
+  int G;          // CTAs (cooperative)
+  int rpc;        // rows per CTA
+  int rpc_pad;    // shared-memory column stride
+  int smem;       // 1: panel slice resident in shared memory
+  size_t smem_bytes;
+};
+
+template <typename T>
+cudaError_t launch_generator(int f, int p_r, int p_c, uint64_t seed, int gdist, double* Gt,
+                             double* Gh, T* Gt_t, T* Gh_t, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_encode(const Geo& g, const T* A, int64_t lda, const T* Gt, const T* Gh, T* Q,
+                          cudaStream_t st);
+
+PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms);
+
+template <typename T>
+cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t ldr, int64_t M,
+                         int bk, double tau, T* part, unsigned* bar, int* status, int col0,
+                         cudaStream_t st);
+
+// Rbar partials: P[s] (bk x w, col-major) = Qbar^T Qtrail over K-split s.
+template <typename T>
+cudaError_t launch_gemm_tn_splitk(const T* A, int64_t lda, const T* B, int64_t ldb, int64_t K,
+                                  int bk, int64_t w, int splits, T* P, cudaStream_t st);
+// Sum the split partials into R (rows kb.., columns kb+bk..) and the compact Rbar (ld = bk).
+template <typename T>
+cudaError_t launch_splitk_reduce(const T* P, int splits, int bk, int64_t w, T* R, int64_t ldr,
+                                 T* Rb, cudaStream_t st);
+// C (M x w) -= A (M x bk) * B (bk x w).
+template <typename T>
+cudaError_t launch_gemm_nn_sub(const T* A, int64_t lda, const T* B, int64_t ldb, T* C,
+                               int64_t ldc, int64_t M, int bk, int64_t w, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_poison(const Geo& g, const int* tiles, int count, T* Q, T* R,
+                          cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_decode(const Geo& g, const DecodePlan* plans_dev, int nplans, int max_h,
+                          const double* Gt, const double* Gh, T* Q, T* R, int* status,
+                          cudaStream_t st);
+
+// W = G_0 Z for Z (m_pad x k, rows >= zrows read as 0); W may alias Z.
+template <typename T>
+cudaError_t launch_post_orth(const Geo& g, const T* Gt_t, const T* Z, int64_t ldz,
+                             int64_t zrows, int64_t k, T* W, int64_t ldw, cudaStream_t st);
+
+// z (n x k) = Qo^T yo, Qo rows x n.
+template <typename T>
+cudaError_t launch_gemv_t(const T* Qo, int64_t ldq, int64_t rows, int64_t n, const T* y,
+                          int64_t ldy, int64_t k, T* z, int64_t ldz, cudaStream_t st);
+
+// In-place back substitution R x = z (R n x n upper), cooperative launch.
+template <typename T>
+cudaError_t launch_trsv_upper(const T* R, int64_t ldr, int64_t n, T* x, int64_t ldx, int64_t k,
+                              unsigned* bar, int* status, int num_sms, cudaStream_t st);
+
+}  // namespace cqr
