@@ -1,0 +1,461 @@
+#!/usr/bin/env python
+"""Benchmark: coded block Gram-Schmidt QR (arXiv 2311.11943) on GB300.
+
+One step = the whole hot path on one synthetic problem: generator + checksum encode, PBMGS
+with ICGS panels on the encoded matrix (erasures injected at the start of seeded panels and
+recovered before they run), post-orthogonalisation and the solve.  Reported: coded GS-QR
+TFLOP/s (F_coded = 2 (m+c) n (n+2d) per step), the coding overhead against the uncoded GPU
+QR of the same matrix, and the errors ||A - Q_1 R|| / ||A||, ||I - Qo^T Qo||.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config c2] [--mode 3xtf32|tf32|f32|f64]
+  python bench.py --impl reference ...     (the FP64 CPU oracle on the host cores)
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+CONFIGS = {
+    # 4096 x 4096 = U diag(sigma) V^T, kappa 1e2; grid 8 x 8, f = 2, b = 128; two nodes erased at
+    # two seeded panels
+    "c2": dict(m=4096, n=4096, p_r=8, p_c=8, f=2, b=128, kappa=1e2, seed=2, erasure_panels=2,
+               per_panel=1),
+    "c2k6": dict(m=4096, n=4096, p_r=8, p_c=8, f=2, b=128, kappa=1e6, seed=2, erasure_panels=2,
+                 per_panel=1),
+    # 16384 x 16384, kappa 1e4; grid 16 x 16, f = 4, b = 256; four simultaneous erasures
+    "c3": dict(m=16384, n=16384, p_r=16, p_c=16, f=4, b=256, kappa=1e4, seed=3, erasure_panels=1,
+               per_panel=4),
+    "c1": dict(m=256, n=256, p_r=4, p_c=4, f=1, b=32, kappa=0, seed=1, erasure_panels=1,
+               per_panel=1),
+}
+MODES = {"f64": ("f64", "simt"), "f32": ("f32", "simt"), "tf32": ("f32", "tf32"),
+         "3xtf32": ("f32", "3xtf32")}
+L2_BYTES = 126 * 1024 * 1024
+
+
+def coded_flops(m, n, p_r, p_c, f, b, protect_r=True):
+    mb = -(-m // p_r)
+    c = f * mb
+    d = f * (n // p_c) if protect_r and f > 0 else 0
+    return 2.0 * (mb * p_r + c) * n * (n + 2 * d)
+
+
+def workload_name(cfg, mode):
+    k = ("kappa=%g" % cfg["kappa"]) if cfg["kappa"] else "N(0,1)"
+    return ("coded PBMGS/ICGS %dx%d %s, grid %dx%d, f=%d, b=%d, %d erasure(s) at %d seeded "
+            "panel(s), %s" % (cfg["m"], cfg["n"], k, cfg["p_r"], cfg["p_c"], cfg["f"], cfg["b"],
+                              cfg["erasure_panels"] * cfg["per_panel"], cfg["erasure_panels"],
+                              mode))
+
+
+def make_inputs(cfg, torch=None, device=None):
+    """Seeded synthetic A (m x n, FP64) and y (m x 1)."""
+    from paper_2311_11943_gb300 import synth
+    m, n = cfg["m"], cfg["n"]
+    if not cfg["kappa"]:
+        A = synth.gaussian(m, n, cfg["seed"])
+    else:
+        A = synth.kappa_matrix(m, n, cfg["kappa"], cfg["seed"])
+    y = synth.rhs(m, 1, cfg["seed"])
+    return A, y
+
+
+def erasure_plan(cfg):
+    from paper_2311_11943_gb300 import synth
+    T = -(-cfg["n"] // cfg["b"])
+    panels = synth.random_panels(T, cfg["erasure_panels"], cfg["seed"])
+    gr = cfg["p_r"] + cfg["f"]
+    gc = cfg["p_c"] + cfg["f"]
+    plan = []
+    for t in panels:
+        for (i, j) in synth.random_erasures(gr, gc, cfg["f"], cfg["per_panel"], cfg["seed"] + t):
+            plan.append((t, i, j))
+    return plan
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons sampled while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                pw.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s, p in zip(sm, pw) if p > 200.0] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------------------ CPU oracle legs
+def oracle_sample(cfg, A, budget_s, max_panels=None):
+    """Time the FP64 oracle on a bounded sample of the workload: encode plus as many PBMGS
+    panels (full trailing updates) as fit in budget_s.  Returns (TFLOP/s, cores, sample)."""
+    from oracle import oracle as O
+    m, n, p_r, p_c, f, b = (cfg[k] for k in ("m", "n", "p_r", "p_c", "f", "b"))
+    g = O.geom(m, n, p_r, p_c, f)
+    Gt, Gh = O.generator(f, p_r, p_c, cfg["seed"])
+    t0 = time.perf_counter()
+    Q = O.encode(g, Gt, Gh, A)
+    R = np.zeros((g.N, g.N), order="F")
+    flops = 0.0
+    panels = 0
+    T = -(-n // b)
+    while panels < T and (time.perf_counter() - t0) < budget_s:
+        if max_panels is not None and panels >= max_panels:
+            break
+        kb = panels * b
+        bk = min(b, n - kb)
+        w = g.N - kb - bk
+        O.factor(Q, R, n, b, panels, panels + 1)
+        flops += 4.0 * g.M * bk * w + 4.0 * g.M * bk * bk
+        panels += 1
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = ("FP64 oracle: encode + panels 0..%d of %d (%.1f GFLOP of trailing update and panel "
+              "work) of the %dx%d coded problem, %.1f s" % (panels - 1, T, flops / 1e9, m, n, dt))
+    return flops / dt / 1e12, cores, sample, dt
+
+
+def run_reference(args, cfg):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    A, _ = make_inputs(cfg)
+    vals = []
+    sample = ""
+    cores = 1
+    for it in range(args.warmup + args.steps):
+        v, cores, sample, dt = oracle_sample(cfg, A, budget_s=1e9, max_panels=1)
+        if it >= args.warmup:
+            vals.append((v, dt))
+    value = statistics.mean(v for v, _ in vals)
+    ms = statistics.mean(dt for _, dt in vals) * 1e3
+    line = {"metric": "coded GS-QR TFLOP/s (FP64 CPU oracle, bounded sample)", "value": value,
+            "unit": "TFLOP/s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(cfg, "FP64 CPU oracle") + "; each step encode "
+                       "+ panel 0 only"},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------------ GPU leg
+def run_ours(args, cfg):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2311_11943_gb300 import binding as B
+
+    dtype, mma = MODES[args.mode]
+    td = torch.float64 if dtype == "f64" else torch.float32
+    es = 8 if dtype == "f64" else 4
+    m, n, p_r, p_c, f, b = (cfg[k] for k in ("m", "n", "p_r", "p_c", "f", "b"))
+    A_np, y_np = make_inputs(cfg)
+    plan = erasure_plan(cfg)
+    stream = torch.cuda.current_stream()
+
+    def dev_colmajor(X):
+        d = B.colmajor_empty(X.shape[0], X.shape[1], td)
+        d.copy_(torch.from_numpy(np.ascontiguousarray(X)))
+        return d
+
+    Ad, yd = dev_colmajor(A_np), dev_colmajor(y_np)
+    xd = B.colmajor_empty(n, 1, td)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(q, with_plan):
+        # the async verbs of the C ABI, in the order of coded_qr_run
+        q.encode(Ad)
+        T = q.geo["panels"]
+        pl = plan if with_plan else []
+        t = 0
+        while t < T:
+            tiles = [(i, j) for (tt, i, j) in pl if tt == t]
+            if tiles:
+                q.inject(tiles)
+                q.recover()
+            t1 = t + 1
+            while t1 < T and not any(tt == t1 for (tt, _, _) in pl):
+                t1 += 1
+            q.factor(t, t1)
+            t = t1
+        q.post_orth()
+        q.solve(yd, xd)
+
+    def timed(q, with_plan, steps, warmup, profile=False):
+        for _ in range(warmup):
+            step(q, with_plan)
+        torch.cuda.synchronize()
+        if profile:
+            q.profile(True)
+            q.profile_read(reset=True)
+        times = []
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(q, with_plan)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        prof = q.profile_read(reset=True) if profile else None
+        if profile:
+            q.profile(False)
+        st = q.sync_status()
+        if st != 0:
+            raise RuntimeError("device status %d (%s)" % (st, B.errstr(st)))
+        return times, prof
+
+    q = B.CodedQR(m, n, p_r, p_c, f, b, dtype=dtype, mma=mma, seed=cfg["seed"], stream=stream)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_coded, prof = timed(q, True, args.steps, args.warmup, profile=True)
+    clk = clocks.stop()
+    stats = q.stats()
+
+    # uncoded GPU QR of the same matrix (f = 0, no checksums, no erasures)
+    q0 = B.CodedQR(m, n, p_r, p_c, 0, b, dtype=dtype, mma=mma, seed=cfg["seed"], stream=stream)
+    t_unc, _ = timed(q0, False, args.steps, max(1, args.warmup))
+    q0.close()
+
+    # errors of one more (untimed) run: factors before post-orthogonalisation
+    q.encode(Ad)
+    T = q.geo["panels"]
+    t = 0
+    while t < T:
+        tiles = [(i, j) for (tt, i, j) in plan if tt == t]
+        if tiles:
+            q.inject(tiles)
+            q.recover()
+        q.factor(t, t + 1)
+        t += 1
+    Qc, Rc = q.factors()
+    Q1 = Qc[:m, :n].double()
+    R1 = Rc[:n, :n].double()
+    A64 = torch.from_numpy(A_np).to(dev)
+    berr = (torch.linalg.norm(A64 - Q1 @ R1) / torch.linalg.norm(A64)).item()
+    Qo = B.colmajor_empty(q.geo["m_pad"], n, td)
+    q.post_orth(Qo)
+    Qo64 = Qo.double()
+    orth = (torch.eye(n, device=dev, dtype=torch.float64) - Qo64.T @ Qo64).abs().max().item()
+    q.solve(yd, xd)
+    x64 = xd.double()
+    y64 = torch.from_numpy(y_np).to(dev)
+    resid = (torch.linalg.norm(A64 @ x64 - y64) / torch.linalg.norm(y64)).item()
+
+    # end to end through the public one-call API with host buffers (pinned)
+    A_pin = torch.empty((n, m), dtype=td, pin_memory=True)
+    A_pin.copy_(torch.from_numpy(np.ascontiguousarray(A_np.T)))
+    A_host = A_pin.numpy().T
+    y_pin = torch.empty((1, m), dtype=td, pin_memory=True)
+    y_pin.copy_(torch.from_numpy(np.ascontiguousarray(y_np.T)))
+    y_host = y_pin.numpy().T
+    x_pin = torch.empty((1, n), dtype=td, pin_memory=True)
+    x_host = x_pin.numpy().T
+    for _ in range(max(1, args.warmup)):
+        q.run(A_host, y_host, x_host, plan=plan, host=True)
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q.run(A_host, y_host, x_host, plan=plan, host=True)
+        e2e_times.append((time.perf_counter() - t0) * 1e3)
+    q.close()
+
+    F = coded_flops(m, n, p_r, p_c, f, b)
+    ms = statistics.mean(t_coded)
+    ms_unc = statistics.mean(t_unc)
+    ms_e2e = statistics.mean(e2e_times)
+    if world > 1:
+        tt = torch.tensor([ms, ms_unc, ms_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms, ms_unc, ms_e2e = tt.tolist()
+    value = world * F / (ms * 1e-3) / 1e12
+    e2e_value = world * F / (ms_e2e * 1e-3) / 1e12
+
+    # roofline of the dominant kernel (largest share of device time in the timed steps)
+    peaks, peak_src = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_launches) = dom[0], dom[1]
+    M = q.geo["M"]
+    N = q.geo["N"]
+    T = q.geo["panels"]
+    gemm_flops = sum(2.0 * M * min(b, n - t * b) * (N - t * b - min(b, n - t * b))
+                     for t in range(T) if t * b + min(b, n - t * b) < N)
+    panel_bytes = sum(2.0 * M * min(b, n - t * b) * es for t in range(T))
+    if dom_name in ("gemm_rbar_simt", "gemm_update_simt", "tc_rbar", "tc_update"):
+        per_class = {"tc_update": 2.0, "tc_rbar": 1.0, "gemm_rbar_simt": 1.0, "gemm_update_simt": 1.0}
+        algo = gemm_flops * per_class[dom_name] * args.steps / dom_launches
+        achieved = algo / (dom_ms / dom_launches * 1e-3) / 1e12
+        if dtype == "f64":
+            peak = 152 * 2 * 2 * 2.07e9 / 1e12
+            rl = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "FP64 CUDA-core: 152 SMs x 2 "
+                  "DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)"}
+        elif mma == "simt":
+            peak = 152 * 128 * 2 * 2.07e9 / 1e12
+            rl = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "FP32 CUDA-core: 152 SMs x "
+                  "128 FFMA/clk x 2 flop x 2.07 GHz"}
+        else:
+            peak = peaks["bf16_tflops_sustained"] * 1.1 / 2.25
+            rl = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": "%s bf16 sustained x "
+                  "nominal tf32/bf16 ratio 1.1/2.25" % peak_src}
+        rl.update(achieved=achieved, peak=peak, frac=achieved / peak)
+    else:
+        if dom_name == "panel_icgs":
+            algo = panel_bytes * args.steps / dom_launches
+        else:
+            algo = None
+        dur = dom_ms / dom_launches * 1e-3
+        achieved = (algo / dur / 1e9) if algo else None
+        peak = peaks["hbm_gbs"]
+        rl = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak,
+              "frac": (achieved / peak) if achieved else None,
+              "peak_source": "%s copy bandwidth" % peak_src}
+    rl.update(kernel=dom_name, launches_per_step=dom_launches / args.steps,
+              avg_launch_ms=dom_ms / dom_launches, traffic=None)
+    launches = int(sum(v[1] for v in prof.values()) / args.steps)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+        v, cores, sample, _ = oracle_sample(cfg, A_np, budget_s=args.cpu_budget)
+        cpu = {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": "coded GS-QR TFLOP/s (F_coded = 2(m+c)n(n+2d) per step) + coding overhead "
+                      "vs uncoded, at the stated QR/orthogonality error",
+            "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f64": "f64", "f32": "f32", "tf32": "f32 storage, tf32 tensor-core GEMMs",
+                      "3xtf32": "f32 storage, 3xtf32 tensor-core GEMMs"}[args.mode],
+            "data": "synthetic (seeded U diag(sigma) V^T / N(0,1), generated on the host)",
+            "config": {"workload": workload_name(cfg, args.mode), "m": m, "n": n, "p_r": p_r,
+                       "p_c": p_c, "f": f, "b": b, "kappa": cfg["kappa"],
+                       "erasures": [list(p) for p in plan],
+                       "l2": "L2 flushed between timed steps (256 MB write outside the events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "coded_flops_per_step": F,
+            "uncoded": {"ms_per_step": ms_unc, "tflops_uncoded_equiv": 2.0 * m * n * n /
+                        (ms_unc * 1e-3) / 1e12},
+            "coding_overhead": ms / ms_unc - 1.0,
+            "flop_model_overhead_floor": F / (2.0 * m * n * n) - 1.0,
+            "errors": {"backward_rel_fro": berr, "orth_max_post_orth": orth,
+                       "solve_rel_residual": resid},
+            "reorth_per_step": stats["n_reorth"] / max(1, (args.steps + args.warmup)),
+            "recovered_tiles_per_step": len(plan),
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "roofline": rl,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "TFLOP/s", "ms_per_step": ms_e2e,
+                    "h2d_bytes_per_step": m * n * es + m * es, "d2h_bytes_per_step": n * es},
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--mode", default=os.environ.get("CQR_BENCH_MODE", "f32"),
+                    choices=sorted(MODES))
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    cfg = CONFIGS[args.config]
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+    return run_ours(args, cfg)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

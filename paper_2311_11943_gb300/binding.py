@@ -27,7 +27,9 @@ EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "
            "coded_qr_geometry", "coded_qr_encode", "coded_qr_factor", "coded_qr_inject_erasure",
            "coded_qr_recover", "coded_qr_post_orth", "coded_qr_solve", "coded_qr_run",
            "coded_qr_get_factors", "coded_qr_get_generator", "coded_qr_get_decode_sets",
-           "coded_qr_stats", "coded_qr_sync_status", "coded_qr_errstr"]
+           "coded_qr_stats", "coded_qr_sync_status", "coded_qr_errstr", "coded_qr_profile",
+           "coded_qr_profile_read", "coded_qr_profile_name"]
+PROF_CLASSES = 13
 
 
 class Config(C.Structure):
@@ -77,6 +79,8 @@ def lib():
             "coded_qr_get_decode_sets": [vp, C.POINTER(i32), i32, C.POINTER(i32)],
             "coded_qr_stats": [vp, C.POINTER(i64)],
             "coded_qr_sync_status": [vp],
+            "coded_qr_profile": [vp, i32],
+            "coded_qr_profile_read": [vp, C.POINTER(C.c_double), C.POINTER(i64), i32, i32],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -84,6 +88,8 @@ def lib():
             fn.restype = C.c_int
         L.coded_qr_errstr.argtypes = [C.c_int]
         L.coded_qr_errstr.restype = C.c_char_p
+        L.coded_qr_profile_name.argtypes = [C.c_int32]
+        L.coded_qr_profile_name.restype = C.c_char_p
         _lib = L
     return _lib
 
@@ -194,6 +200,23 @@ def coded_qr_stats(h):
 
 def coded_qr_sync_status(h):
     return lib().coded_qr_sync_status(h)
+
+
+def coded_qr_profile(h, enable):
+    return lib().coded_qr_profile(h, int(bool(enable)))
+
+
+def coded_qr_profile_read(h, reset=True):
+    ms = (C.c_double * PROF_CLASSES)()
+    ln = (C.c_int64 * PROF_CLASSES)()
+    check(lib().coded_qr_profile_read(h, ms, ln, PROF_CLASSES, int(bool(reset))),
+          "coded_qr_profile_read")
+    return {coded_qr_profile_name(k): (ms[k], ln[k]) for k in range(PROF_CLASSES)}
+
+
+def coded_qr_profile_name(k):
+    v = lib().coded_qr_profile_name(k)
+    return v.decode() if v else None
 
 
 # ------------------------------------------------------------------ torch convenience layer
@@ -333,3 +356,9 @@ class CodedQR:
 
     def sync_status(self):
         return coded_qr_sync_status(self.h)
+
+    def profile(self, enable=True):
+        check(coded_qr_profile(self.h, enable), "coded_qr_profile")
+
+    def profile_read(self, reset=True):
+        return coded_qr_profile_read(self.h, reset)

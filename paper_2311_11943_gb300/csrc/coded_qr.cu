@@ -119,6 +119,20 @@ Layout make_layout(const cqr_config* c, const Geo& g, int num_sms) {
 
 }  // namespace
 
+// Kernel classes of the per-launch-site profile (coded_qr_profile_read).
+enum KClass {
+  K_GENERATOR = 0, K_ENCODE, K_PANEL, K_GEMM_RBAR, K_SPLITK_REDUCE, K_GEMM_UPDATE, K_POISON,
+  K_DECODE, K_POST_ORTH, K_SOLVE_GEMV, K_TRSV, K_TC_RBAR, K_TC_UPDATE, K_COUNT
+};
+static const char* kClassNames[K_COUNT] = {
+    "generator", "encode", "panel_icgs", "gemm_rbar_simt", "splitk_reduce", "gemm_update_simt",
+    "erasure_poison", "decode", "post_orth", "solve_gemv", "trsv", "tc_rbar", "tc_update"};
+
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+};
+
 struct cqr_handle_s {
   cqr_config cfg;
   Geo g;
@@ -142,7 +156,49 @@ struct cqr_handle_s {
   size_t esz = 8;
   double tau = 0.7071067811865476;
   TcGemm* tc = nullptr;
+  // profile: launch counts always, event-pair device times when enabled
+  bool prof_on = false;
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+  double prof_ms[K_COUNT] = {0};
+  int64_t prof_launches[K_COUNT] = {0};
 };
+
+namespace {
+
+cudaEvent_t prof_event(cqr_handle h) {
+  if (!h->prof_pool.empty()) {
+    cudaEvent_t e = h->prof_pool.back();
+    h->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets the launches of one kernel class at one call site.
+struct ProfScope {
+  cqr_handle h;
+  int cls;
+  cudaEvent_t a = nullptr;
+  ProfScope(cqr_handle h_, int cls_, int nlaunch) : h(h_), cls(cls_) {
+    h->prof_launches[cls] += nlaunch;
+    if (h->prof_on) {
+      a = prof_event(h);
+      cudaEventRecord(a, h->st);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = prof_event(h);
+      cudaEventRecord(b, h->st);
+      h->prof_recs.push_back(ProfRec{cls, a, b});
+    }
+  }
+};
+
+}  // namespace
 
 #define CK(x)                                          \
   do {                                                 \
@@ -236,10 +292,14 @@ cqr_status encode_t(cqr_handle h, const T* A, int64_t lda) {
   const Geo& g = h->g;
   CK(cudaMemsetAsync(h->B.status, 0, 4 * sizeof(int), h->st));
   if (g.f > 0) {
+    ProfScope ps(h, K_GENERATOR, 1);
     CK(launch_generator<T>(g.f, g.p_r, g.p_c, h->cfg.seed, h->cfg.gdist, h->B.Gt, h->B.Gh,
                            ptr<T>(h->B.Gt_t), ptr<T>(h->B.Gh_t), h->st));
   }
-  CK(launch_encode<T>(g, A, lda, ptr<T>(h->B.Gt_t), ptr<T>(h->B.Gh_t), ptr<T>(h->B.Q), h->st));
+  {
+    ProfScope ps(h, K_ENCODE, (g.protect_r && g.f > 0) ? 2 : 1);
+    CK(launch_encode<T>(g, A, lda, ptr<T>(h->B.Gt_t), ptr<T>(h->B.Gh_t), ptr<T>(h->B.Q), h->st));
+  }
   CK(cudaMemsetAsync(h->B.R, 0, (size_t)g.ldr * g.N * sizeof(T), h->st));
   return CQR_OK;
 }
@@ -263,23 +323,36 @@ cqr_status panel_step(cqr_handle h, int t) {
   T* R = ptr<T>(h->B.R);
   const bool tc = h->tc != nullptr;
   PanelPlan pp = plan_panel(g.M, bk, sizeof(T), h->num_sms);
-  CK(launch_panel<T>(pp, Q + kb * g.ldq, g.ldq, R + kb + kb * g.ldr, g.ldr, g.M, bk, h->tau,
-                     ptr<T>(h->B.part), h->B.bar, h->B.status, (int)kb, h->st));
+  {
+    ProfScope ps(h, K_PANEL, 1);
+    CK(launch_panel<T>(pp, Q + kb * g.ldq, g.ldq, R + kb + kb * g.ldr, g.ldr, g.M, bk, h->tau,
+                       ptr<T>(h->B.part), h->B.bar, h->B.status, (int)kb, h->st));
+  }
   const int64_t j0 = kb + bk;
   if (j0 >= g.N) return CQR_OK;
   const int64_t w = g.N - j0;
   if (tc) {
+    ProfScope ps(h, K_TC_UPDATE, tc_launches_per_update(h->tc));
     if (tc_trailing_update(h->tc, kb, bk, j0, w, ptr<float>(h->B.R), g.ldr, h->st) != cudaSuccess)
       return CQR_ECUDA;
     return CQR_OK;
   }
   const int splits = choose_splits(bk, w, g.M, h->num_sms);
-  CK(launch_gemm_tn_splitk<T>(Q + kb * g.ldq, g.ldq, Q + j0 * g.ldq, g.ldq, g.M, bk, w, splits,
-                              ptr<T>(h->B.P), h->st));
-  CK(launch_splitk_reduce<T>(ptr<T>(h->B.P), splits, bk, w, R + kb + j0 * g.ldr, g.ldr,
-                             ptr<T>(h->B.Rb), h->st));
-  CK(launch_gemm_nn_sub<T>(Q + kb * g.ldq, g.ldq, ptr<T>(h->B.Rb), bk, Q + j0 * g.ldq, g.ldq,
-                           g.M, bk, w, h->st));
+  {
+    ProfScope ps(h, K_GEMM_RBAR, 1);
+    CK(launch_gemm_tn_splitk<T>(Q + kb * g.ldq, g.ldq, Q + j0 * g.ldq, g.ldq, g.M, bk, w, splits,
+                                ptr<T>(h->B.P), h->st));
+  }
+  {
+    ProfScope ps(h, K_SPLITK_REDUCE, 1);
+    CK(launch_splitk_reduce<T>(ptr<T>(h->B.P), splits, bk, w, R + kb + j0 * g.ldr, g.ldr,
+                               ptr<T>(h->B.Rb), h->st));
+  }
+  {
+    ProfScope ps(h, K_GEMM_UPDATE, 1);
+    CK(launch_gemm_nn_sub<T>(Q + kb * g.ldq, g.ldq, ptr<T>(h->B.Rb), bk, Q + j0 * g.ldq, g.ldq,
+                             g.M, bk, w, h->st));
+  }
   return CQR_OK;
 }
 
@@ -338,6 +411,7 @@ cqr_status recover_t(cqr_handle h, int32_t* n_recovered) {
                        cudaMemcpyHostToDevice, h->st));
     CK(cudaEventRecord(h->plans_ev, h->st));
     const int max_h = (int)std::max(g.mb, g.nb);
+    ProfScope ps(h, K_DECODE, 1);
     CK(launch_decode<T>(g, h->B.plans, (int)plans.size(), max_h, h->B.Gt, h->B.Gh,
                         ptr<T>(h->B.Q), ptr<T>(h->B.R), h->B.status, h->st));
   }
@@ -383,6 +457,7 @@ cqr_status post_orth_q(cqr_handle h, T* Qout, int64_t ldqo) {
   if (g.f == 0) {
     if (Qout) return copy_pad<T>(h, Q, g.ldq, g.m_pad, g.m_pad, g.n, Qout, ldqo);
   } else {
+    ProfScope ps(h, K_POST_ORTH, 1);
     CK(launch_post_orth<T>(g, ptr<T>(h->B.Gt_t), Q, g.ldq, g.m_pad, g.n, dst, ldd, h->st));
   }
   if (!Qout) h->postorth_inplace = true;
@@ -393,6 +468,7 @@ template <typename T>
 cqr_status post_orth_y(cqr_handle h, const T* y, int64_t ldy, int32_t nrhs, T* yo, int64_t ldyo) {
   const Geo& g = h->g;
   if (g.f == 0) return copy_pad<T>(h, y, ldy, g.m, g.m_pad, nrhs, yo, ldyo);
+  ProfScope ps(h, K_POST_ORTH, 1);
   CK(launch_post_orth<T>(g, ptr<T>(h->B.Gt_t), y, ldy, g.m, nrhs, yo, ldyo, h->st));
   return CQR_OK;
 }
@@ -408,9 +484,15 @@ cqr_status solve_t(cqr_handle h, const T* y, int64_t ldy, T* x, int64_t ldx, int
   T* yo = ptr<T>(h->B.yw);
   s = post_orth_y<T>(h, y, ldy, nrhs, yo, g.m_pad);
   if (s != CQR_OK) return s;
-  CK(launch_gemv_t<T>(ptr<T>(h->B.Q), g.ldq, g.m_pad, g.n, yo, g.m_pad, nrhs, x, ldx, h->st));
-  CK(launch_trsv_upper<T>(ptr<T>(h->B.R), g.ldr, g.n, x, ldx, nrhs, h->B.bar, h->B.status,
-                          h->num_sms, h->st));
+  {
+    ProfScope ps(h, K_SOLVE_GEMV, 1);
+    CK(launch_gemv_t<T>(ptr<T>(h->B.Q), g.ldq, g.m_pad, g.n, yo, g.m_pad, nrhs, x, ldx, h->st));
+  }
+  {
+    ProfScope ps(h, K_TRSV, 1);
+    CK(launch_trsv_upper<T>(ptr<T>(h->B.R), g.ldr, g.n, x, ldx, nrhs, h->B.bar, h->B.status,
+                            h->num_sms, h->st));
+  }
   return CQR_OK;
 }
 
@@ -455,6 +537,8 @@ cqr_status coded_qr_destroy(cqr_handle h) {
   if (!h) return CQR_OK;
   if (h->st || true) cudaStreamSynchronize(h->st);
   if (h->tc) tc_destroy(h->tc);
+  for (auto& r : h->prof_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : h->prof_pool) cudaEventDestroy(e);
   if (h->plans_ev) cudaEventDestroy(h->plans_ev);
   if (h->plans_host) cudaFreeHost(h->plans_host);
   if (h->status_host) cudaFreeHost(h->status_host);
@@ -523,6 +607,9 @@ cqr_status coded_qr_inject_erasure(cqr_handle h, const int32_t* tiles, int32_t c
   }
   if (count == 0) return CQR_OK;
   for (int e = 0; e < count; ++e) h->mask[(size_t)tiles[2 * e] * g.grid_cols + tiles[2 * e + 1]] = 1;
+  int nr_tiles = 0;
+  for (int e = 0; e < count; ++e) nr_tiles += (g.protect_r && tiles[2 * e] < g.p_c + g.f) ? 1 : 0;
+  ProfScope ps(h, K_POISON, (count + 63) / 64 + (nr_tiles + 63) / 64);
   cudaError_t err = h->esz == 8
       ? launch_poison<double>(g, tiles, count, ptr<double>(h->B.Q), ptr<double>(h->B.R), h->st)
       : launch_poison<float>(g, tiles, count, ptr<float>(h->B.Q), ptr<float>(h->B.R), h->st);
@@ -687,6 +774,36 @@ cqr_status coded_qr_stats(cqr_handle h, int64_t* out) {
 cqr_status coded_qr_sync_status(cqr_handle h) {
   if (!h) return CQR_EINVAL;
   return read_status(h, true);
+}
+
+cqr_status coded_qr_profile(cqr_handle h, int32_t enable) {
+  if (!h) return CQR_EINVAL;
+  h->prof_on = enable != 0;
+  return CQR_OK;
+}
+
+cqr_status coded_qr_profile_read(cqr_handle h, double* ms, int64_t* launches, int32_t cap,
+                                 int32_t reset) {
+  if (!h || cap < 0) return CQR_EINVAL;
+  CK(cudaStreamSynchronize(h->st));
+  for (auto& r : h->prof_recs) {
+    float dt = 0.f;
+    if (cudaEventElapsedTime(&dt, r.a, r.b) == cudaSuccess) h->prof_ms[r.cls] += dt;
+    h->prof_pool.push_back(r.a);
+    h->prof_pool.push_back(r.b);
+  }
+  h->prof_recs.clear();
+  for (int k = 0; k < K_COUNT && k < cap; ++k) {
+    if (ms) ms[k] = h->prof_ms[k];
+    if (launches) launches[k] = h->prof_launches[k];
+  }
+  if (reset)
+    for (int k = 0; k < K_COUNT; ++k) { h->prof_ms[k] = 0.0; h->prof_launches[k] = 0; }
+  return CQR_OK;
+}
+
+const char* coded_qr_profile_name(int32_t cls) {
+  return (cls >= 0 && cls < K_COUNT) ? kClassNames[cls] : nullptr;
 }
 
 const char* coded_qr_errstr(cqr_status s) {
