@@ -103,7 +103,7 @@ Layout make_layout(const cqr_config* c, const Geo& g, int num_sms) {
   L.Gh = take((size_t)(c->f * c->p_c + 1) * 8);
   L.Gt_t = take((size_t)(c->f * c->p_r + 1) * s);
   L.Gh_t = take((size_t)(c->f * c->p_c + 1) * s);
-  L.part = take((size_t)2 * (num_sms + 1) * ((bmax + 3) / 4 * 4) * s);
+  L.part = take(panel_partial_bytes(bmax, s, num_sms));
   L.bar = take(256);
   L.status = take(256);
   L.P = take((size_t)kMaxSplits * bmax * g.N * s);
@@ -156,6 +156,8 @@ struct cqr_handle_s {
   size_t esz = 8;
   double tau = 0.7071067811865476;
   TcGemm* tc = nullptr;
+  PanelPlan plan{};
+  int plan_bk = -1;
   // profile: launch counts always, event-pair device times when enabled
   bool prof_on = false;
   std::vector<ProfRec> prof_recs;
@@ -322,7 +324,13 @@ cqr_status panel_step(cqr_handle h, int t) {
   T* Q = ptr<T>(h->B.Q);
   T* R = ptr<T>(h->B.R);
   const bool tc = h->tc != nullptr;
-  PanelPlan pp = plan_panel(g.M, bk, sizeof(T), h->num_sms);
+  if (bk != h->plan_bk) {
+    h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, true);
+    if (h->plan.cluster && !panel_cluster_fits<T>(h->plan))
+      h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, false);
+    h->plan_bk = bk;
+  }
+  const PanelPlan& pp = h->plan;
   {
     ProfScope ps(h, K_PANEL, 1);
     CK(launch_panel<T>(pp, Q + kb * g.ldq, g.ldq, R + kb + kb * g.ldr, g.ldr, g.M, bk, h->tau,

@@ -34,8 +34,10 @@ __device__ __forceinline__ int ld_relaxed_i32(const int* p) {
 constexpr long long kWaitLimitCycles = 2000000000LL;
 
 // Grid-wide barrier for a cooperative launch of `nblocks` CTAs.  `bar` is a global counter
-// zeroed before the launch; `target` is a per-CTA running target (start at 0).  Ordering
-// follows the usual pattern: CTA barrier, device-scope fence, arrival, acquire-poll, fence.
+// zeroed before the launch; `target` is a per-CTA running target (start at 0).  Ordering:
+// CTA barrier, then thread 0 arrives with a release add (cumulative over the CTA's writes
+// ordered before it by the CTA barrier) and polls with acquire loads; a CTA barrier then
+// extends the acquire to every thread.
 // Returns false when this CTA must abandon the kernel (own wait ran out, or another CTA
 // already recorded an error).
 __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nblocks, unsigned& target,
@@ -45,8 +47,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nblocks, unsig
   if (nblocks == 1) return true;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     target += nblocks;
-    __threadfence();
-    atomicAdd(bar, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
     int ok = 1;
     const long long t0 = clock64();
     while (ld_acquire_u32(bar) < target) {
@@ -57,9 +58,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nblocks, unsig
         ok = 0;
         break;
       }
-      __nanosleep(32);
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();

@@ -127,236 +127,6 @@ cudaError_t launch_encode(const Geo& g, const T* A, int64_t lda, const T* Gt, co
   return cudaGetLastError();
 }
 
-// ===================================================================== a3 panel ICGS
-// Appendix A, Algorithm CGS with the ICGS reorthogonalisation.  One cooperative grid of G
-// CTAs; CTA g owns rows [g*rpc, (g+1)*rpc) of the panel (all M = m_pad + c rows take part in
-// every inner product), held in shared memory when it fits.  Per column j:
-//   v = Q[:, j:b]^T Q[:, j]            one grid-wide reduction (partials per CTA, barrier,
-//                                      every CTA sums the partials in the same fixed order)
-//   if v_j < tau^2 eta_j:              reorthogonalise column j against columns < j
-//   r_jj = sqrt(v_j), q_j = Q[:, j] / r_jj, R[j, j+1:] = v[j+1:] / r_jj,
-//   Q[:, j+1:] -= q_j R[j, j+1:]
-// eta_j = squared column norms at the panel start.  CTA 0 writes R.
-template <typename T>
-struct PanelCtx {
-  T* base;          // first row of this CTA's slice, column 0
-  int64_t cs;       // column stride of the slice
-  int nr;           // rows in the slice
-  T* part;          // [2][G][part_ld] partial sums
-  int part_ld;
-  T* red;           // shared scratch [8][part_ld]
-};
-
-template <typename T, int NT>
-__device__ __forceinline__ void panel_partial_dots(const PanelCtx<T>& c, int a_lo, int a_hi,
-                                                   int jc, int step) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int NW = NT / 32;
-  T* out = c.part + (size_t)(step & 1) * gridDim.x * c.part_ld + (size_t)blockIdx.x * c.part_ld;
-  for (int a = a_lo + warp; a < a_hi; a += NW) {
-    const T* ca = c.base + a * c.cs;
-    const T* cj = c.base + (jc < 0 ? a : jc) * c.cs;
-    T acc = T(0);
-    for (int r = lane; r < c.nr; r += 32) acc += ca[r] * cj[r];
-    acc = warp_sum(acc);
-    if (lane == 0) out[a] = acc;
-  }
-}
-
-template <typename T>
-struct Vec16;
-template <>
-struct Vec16<float> {
-  using V = float4;
-  static constexpr int N = 4;
-  __device__ static void add(float* a, const float4& v) { a[0] += v.x; a[1] += v.y; a[2] += v.z; a[3] += v.w; }
-};
-template <>
-struct Vec16<double> {
-  using V = double2;
-  static constexpr int N = 2;
-  __device__ static void add(double* a, const double2& v) { a[0] += v.x; a[1] += v.y; }
-};
-
-// Every CTA sums the G partial rows for columns [a_lo, a_hi) into out[] (shared), in a
-// fixed order: group k adds rows k, k+groups, ...; then the groups are added in order.
-template <typename T, int NT>
-__device__ __forceinline__ void panel_reduce(const PanelCtx<T>& c, int a_lo, int a_hi, T* out,
-                                             int step) {
-  using VT = Vec16<T>;
-  constexpr int VN = VT::N;
-  const int G = gridDim.x;
-  const T* P = c.part + (size_t)(step & 1) * G * c.part_ld;
-  const int c0 = a_lo / VN, c1 = (a_hi + VN - 1) / VN, nch = c1 - c0;
-  int groups = NT / (nch > 0 ? nch : 1);
-  if (groups > 8) groups = 8;
-  if (groups > G) groups = G;
-  const int tid = threadIdx.x;
-  const int grp = tid / nch, ch = tid - grp * nch;
-  if (nch > 0 && grp < groups) {
-    T acc[VN];
-#pragma unroll
-    for (int e = 0; e < VN; ++e) acc[e] = T(0);
-    const typename VT::V* src = reinterpret_cast<const typename VT::V*>(P) + (c0 + ch);
-    const int rowv = c.part_ld / VN;
-    int gg = grp;
-    for (; gg + 3 * groups < G; gg += 4 * groups) {
-      const typename VT::V x0 = __ldcg(src + (size_t)gg * rowv);
-      const typename VT::V x1 = __ldcg(src + (size_t)(gg + groups) * rowv);
-      const typename VT::V x2 = __ldcg(src + (size_t)(gg + 2 * groups) * rowv);
-      const typename VT::V x3 = __ldcg(src + (size_t)(gg + 3 * groups) * rowv);
-      VT::add(acc, x0); VT::add(acc, x1); VT::add(acc, x2); VT::add(acc, x3);
-    }
-    for (; gg < G; gg += groups) VT::add(acc, __ldcg(src + (size_t)gg * rowv));
-#pragma unroll
-    for (int e = 0; e < VN; ++e) c.red[grp * c.part_ld + (c0 + ch) * VN + e] = acc[e];
-  }
-  __syncthreads();
-  for (int a = a_lo + tid; a < a_hi; a += NT) {
-    T s = T(0);
-    for (int k = 0; k < groups; ++k) s += c.red[k * c.part_ld + a];
-    out[a] = s;
-  }
-  __syncthreads();
-}
-
-template <typename T, bool SMEM, int NT>
-__global__ void __launch_bounds__(NT) k_panel(T* __restrict__ Q, int64_t ldq, T* __restrict__ R,
-                                               int64_t ldr, int64_t M, int bk, int rpc, int rpc_pad,
-                                               double tau2, T* part, int part_ld, unsigned* bar,
-                                               int* status, int col0) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = NT / 32;
-  const int64_t row0 = (int64_t)g * rpc;
-  const int nr = (int)((M - row0) < rpc ? (M - row0) : rpc);
-  T* sm = reinterpret_cast<T*>(smraw);
-  T* small = sm + (SMEM ? (size_t)bk * rpc_pad : 0);
-  T* v = small;
-  T* coef = v + part_ld;
-  T* sv = coef + part_ld;
-  T* eta = sv + part_ld;
-  PanelCtx<T> c;
-  c.base = SMEM ? sm : Q + row0;
-  c.cs = SMEM ? rpc_pad : ldq;
-  c.nr = nr;
-  c.part = part;
-  c.part_ld = part_ld;
-  c.red = eta + part_ld;
-  unsigned target = 0;
-  int step = 0;
-
-  if (SMEM) {
-    for (int a = 0; a < bk; ++a)
-      for (int r = tid; r < nr; r += NT) sm[(size_t)a * rpc_pad + r] = Q[row0 + r + a * ldq];
-  }
-  __syncthreads();
-  panel_partial_dots<T, NT>(c, 0, bk, -1, step);
-  if (!grid_sync(bar, G, target, status, 1)) return;
-  panel_reduce<T, NT>(c, 0, bk, eta, step++);
-
-  for (int j = 0; j < bk; ++j) {
-    __syncthreads();
-    panel_partial_dots<T, NT>(c, j, bk, j, step);
-    if (!grid_sync(bar, G, target, status, 2)) return;
-    panel_reduce<T, NT>(c, j, bk, v, step++);
-    if (j > 0 && tau2 > 0.0 && (double)v[j] < tau2 * (double)eta[j]) {
-      panel_partial_dots<T, NT>(c, 0, j, j, step);
-      if (!grid_sync(bar, G, target, status, 3)) return;
-      panel_reduce<T, NT>(c, 0, j, sv, step++);
-      T* cj = c.base + j * c.cs;
-      for (int r = tid; r < nr; r += NT) {
-        T acc = cj[r];
-        for (int a = 0; a < j; ++a) acc -= c.base[a * c.cs + r] * sv[a];
-        cj[r] = acc;
-      }
-      if (g == 0) {
-        for (int a = tid; a < j; a += NT) R[a + j * ldr] += sv[a];
-        if (tid == 0) atomicAdd(status + ST_REORTH, 1);
-      }
-      __syncthreads();
-      panel_partial_dots<T, NT>(c, j, bk, j, step);
-      if (!grid_sync(bar, G, target, status, 4)) return;
-      panel_reduce<T, NT>(c, j, bk, v, step++);
-    }
-    const T v0 = v[j];
-    if (!(v0 > T(0)) || !isfinite(v0)) {
-      if (g == 0 && tid == 0) set_status(status, CQR_EBREAKDOWN, col0 + j);
-      return;
-    }
-    const T rjj = sqrt(v0);
-    for (int a = j + 1 + tid; a < bk; a += NT) {
-      const T ca = v[a] / rjj;
-      coef[a] = ca;
-      if (g == 0) R[j + a * ldr] = ca;
-    }
-    if (g == 0 && tid == 0) R[j + j * ldr] = rjj;
-    T* cj = c.base + j * c.cs;
-    for (int r = tid; r < nr; r += NT) cj[r] = cj[r] / rjj;
-    __syncthreads();
-    for (int a = j + 1 + warp; a < bk; a += NW) {
-      const T ca = coef[a];
-      T* pa = c.base + a * c.cs;
-      for (int r = lane; r < nr; r += 32) pa[r] -= cj[r] * ca;
-    }
-  }
-  __syncthreads();
-  if (SMEM) {
-    for (int a = 0; a < bk; ++a)
-      for (int r = tid; r < nr; r += NT) Q[row0 + r + a * ldq] = sm[(size_t)a * rpc_pad + r];
-  }
-}
-
-constexpr int kPanelThreads = 256;
-constexpr size_t kSmemCap = 227 * 1024;
-
-static int part_ld_of(int bk) { return (bk + 3) / 4 * 4; }
-
-PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms) {
-  PanelPlan p{};
-  const int pld = part_ld_of(bk);
-  const size_t small = (size_t)(4 + 8) * pld * elem + 256;
-  const size_t room = kSmemCap - small - 1024;
-  int64_t rpc_max = (int64_t)(room / ((size_t)bk * elem));
-  if (rpc_max > 4096) rpc_max = 4096;
-  int64_t G = rpc_max > 0 ? (M + rpc_max - 1) / rpc_max : (int64_t)num_sms + 1;
-  if (G < 1) G = 1;
-  if (G <= num_sms) {
-    p.smem = 1;
-    p.G = (int)G;
-    p.rpc = (int)((M + G - 1) / G);
-    p.G = (int)((M + p.rpc - 1) / p.rpc);
-    p.rpc_pad = p.rpc | 1;
-    p.smem_bytes = (size_t)bk * p.rpc_pad * elem + small;
-  } else {
-    p.smem = 0;
-    p.G = num_sms;
-    p.rpc = (int)((M + num_sms - 1) / num_sms);
-    p.G = (int)((M + p.rpc - 1) / p.rpc);
-    p.rpc_pad = p.rpc;
-    p.smem_bytes = small;
-  }
-  return p;
-}
-
-template <typename T>
-cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t ldr, int64_t M,
-                         int bk, double tau, T* part, unsigned* bar, int* status, int col0,
-                         cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
-  if (e != cudaSuccess) return e;
-  int part_ld = part_ld_of(bk);
-  double tau2 = tau > 0.0 ? tau * tau : -1.0;
-  void* args[] = {&Q, &ldq, &R, &ldr, &M, &bk, (void*)&pp.rpc, (void*)&pp.rpc_pad, &tau2,
-                  &part, &part_ld, &bar, &status, &col0};
-  const void* fn = pp.smem ? (const void*)k_panel<T, true, kPanelThreads>
-                           : (const void*)k_panel<T, false, kPanelThreads>;
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp.smem_bytes);
-  if (e != cudaSuccess) return e;
-  return cudaLaunchCooperativeKernel(fn, dim3(pp.G), dim3(kPanelThreads), args, pp.smem_bytes, st);
-}
-
 // ===================================================================== a4/a5 SIMT GEMMs
 // Rbar = Qbar^T Qtrail (split over K) and Qtrail -= Qbar Rbar on CUDA cores: the FP64 path
 // and the FP32 reference path.  64 x 64 output tiles, 256 threads, 4 x 4 per thread with a
@@ -765,45 +535,66 @@ cudaError_t launch_gemv_t(const T* Qo, int64_t ldq, int64_t rows, int64_t n, con
   return cudaGetLastError();
 }
 
-// Blocked column-oriented back substitution (Golub & Van Loan Alg. 3.1.4), cooperative grid:
-// CTA 0 solves each 64 x 64 diagonal block, then all CTAs update the rows above it.
+// Blocked back substitution (Golub & Van Loan, Alg. 3.1.4, column version), cooperative grid,
+// one grid barrier per 64-row block: in phase k, CTA 0 first applies the just-solved block
+// k+1 to the rows of block k and solves block k in shared memory, while the other CTAs apply
+// block k+1 to the rows above block k.
 template <typename T>
 __global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ R, int64_t ldr, int64_t n,
                                                      T* x, int64_t ldx, int64_t k, unsigned* bar,
                                                      int* status) {
   constexpr int BS = 64;
-  const int G = gridDim.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ T Rd[BS][BS + 1];
+  __shared__ T xs[BS];
+  const int G = gridDim.x, tid = threadIdx.x;
   unsigned target = 0;
   const int64_t nblk = (n + BS - 1) / BS;
-  for (int64_t blk = nblk - 1; blk >= 0; --blk) {
-    const int64_t i0 = blk * BS;
-    const int64_t i1 = (i0 + BS < n) ? i0 + BS : n;
-    const int nbk = (int)(i1 - i0);
-    if (blockIdx.x == 0) {
-      for (int64_t col = warp; col < k; col += 8) {
-        T* xc = x + col * ldx + i0;
-        for (int i = nbk - 1; i >= 0; --i) {
-          T xi = T(0);
-          if (lane == 0) {
-            xi = __ldcg(xc + i) / R[(i0 + i) + (i0 + i) * ldr];
-            xc[i] = xi;
+  for (int64_t col = 0; col < k; ++col) {
+    T* xc = x + col * ldx;
+    target = 0;
+    for (int64_t blk = nblk - 1; blk >= 0; --blk) {
+      const int64_t i0 = blk * BS;
+      const int64_t i1 = (i0 + BS < n) ? i0 + BS : n;
+      const int nbk = (int)(i1 - i0);
+      const int64_t p0 = i1, p1 = (i1 + BS < n) ? i1 + BS : n;  // previously solved block
+      if (blockIdx.x == 0) {
+        // rows of this block: subtract the previous block's contribution, load into smem
+        for (int r = tid; r < nbk; r += blockDim.x) {
+          T acc = __ldcg(xc + i0 + r);
+          for (int64_t j = p0; j < p1; ++j) acc -= R[(i0 + r) + j * ldr] * __ldcg(xc + j);
+          xs[r] = acc;
+        }
+        for (int e = tid; e < nbk * nbk; e += blockDim.x) {
+          const int r = e % nbk, cidx = e / nbk;
+          Rd[r][cidx] = R[(i0 + r) + (i0 + cidx) * ldr];
+        }
+        __syncthreads();
+        if (tid < 32) {
+          for (int i = nbk - 1; i >= 0; --i) {
+            T xi = T(0);
+            if (tid == 0) {
+              xi = xs[i] / Rd[i][i];
+              xs[i] = xi;
+            }
+            xi = __shfl_sync(0xffffffffu, xi, 0);
+            for (int r = tid; r < i; r += 32) xs[r] -= Rd[r][i] * xi;
+            __syncwarp();
           }
-          xi = __shfl_sync(0xffffffffu, xi, 0);
-          for (int r = lane; r < i; r += 32) xc[r] = __ldcg(xc + r) - R[(i0 + r) + (i0 + i) * ldr] * xi;
-          __syncwarp();
+        }
+        __syncthreads();
+        for (int r = tid; r < nbk; r += blockDim.x) xc[i0 + r] = xs[r];
+      } else if (p0 < p1 && (int64_t)(blockIdx.x - 1) * blockDim.x < i0) {
+        // rows above this block: subtract the previous block's contribution
+        for (int e = tid; e < (int)(p1 - p0); e += blockDim.x) xs[e] = __ldcg(xc + p0 + e);
+        __syncthreads();
+        for (int64_t r = (int64_t)(blockIdx.x - 1) * blockDim.x + tid; r < i0;
+             r += (int64_t)(G - 1) * blockDim.x) {
+          T acc = __ldcg(xc + r);
+          for (int64_t j = p0; j < p1; ++j) acc -= R[r + j * ldr] * xs[j - p0];
+          xc[r] = acc;
         }
       }
-    }
-    if (!grid_sync(bar, G, target, status, 10)) return;
-    for (int64_t col = 0; col < k; ++col) {
-      T* xc = x + col * ldx;
-      for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < i0;
-           r += (int64_t)G * blockDim.x) {
-        T acc = __ldcg(xc + r);
-        for (int64_t j = i0; j < i1; ++j) acc -= R[r + j * ldr] * __ldcg(xc + j);
-        xc[r] = acc;
-      }
+      if (!grid_sync(bar, G, target, status, 10)) return;
     }
     if (!grid_sync(bar, G, target, status, 11)) return;
   }
@@ -812,13 +603,19 @@ __global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ R, int
 template <typename T>
 cudaError_t launch_trsv_upper(const T* R, int64_t ldr, int64_t n, T* x, int64_t ldx, int64_t k,
                               unsigned* bar, int* status, int num_sms, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
-  if (e != cudaSuccess) return e;
-  int G = (int)((n + 255) / 256);
+  int G = (int)((n + 255) / 256) + 1;
   if (G > num_sms) G = num_sms;
-  if (G < 1) G = 1;
-  void* args[] = {(void*)&R, &ldr, &n, &x, &ldx, &k, &bar, &status};
-  return cudaLaunchCooperativeKernel((const void*)k_trsv_upper<T>, dim3(G), dim3(256), args, 0, st);
+  if (G < 2) G = 2;
+  for (int64_t col = 0; col < k; ++col) {
+    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    T* xc = x + col * ldx;
+    int64_t one = 1;
+    void* args[] = {(void*)&R, &ldr, &n, &xc, &ldx, &one, &bar, &status};
+    e = cudaLaunchCooperativeKernel((const void*)k_trsv_upper<T>, dim3(G), dim3(256), args, 0, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // ===================================================================== instantiations
@@ -827,8 +624,6 @@ cudaError_t launch_trsv_upper(const T* R, int64_t ldr, int64_t n, T* x, int64_t 
                                            T*, cudaStream_t);                                     \
   template cudaError_t launch_encode<T>(const Geo&, const T*, int64_t, const T*, const T*, T*,   \
                                         cudaStream_t);                                            \
-  template cudaError_t launch_panel<T>(const PanelPlan&, T*, int64_t, T*, int64_t, int64_t, int, \
-                                       double, T*, unsigned*, int*, int, cudaStream_t);           \
   template cudaError_t launch_gemm_tn_splitk<T>(const T*, int64_t, const T*, int64_t, int64_t,   \
                                                 int, int64_t, int, T*, cudaStream_t);             \
   template cudaError_t launch_splitk_reduce<T>(const T*, int, int, int64_t, T*, int64_t, T*,     \

@@ -31,6 +31,7 @@ struct PanelPlan {
   int rpc;        // rows per CTA
   int rpc_pad;    // shared-memory column stride
   int smem;       // 1: panel slice resident in shared memory
+  int cluster;    // 1: one thread-block cluster (distributed shared memory reductions)
   size_t smem_bytes;
 };
 
@@ -42,7 +43,10 @@ template <typename T>
 cudaError_t launch_encode(const Geo& g, const T* A, int64_t lda, const T* Gt, const T* Gh, T* Q,
                           cudaStream_t st);
 
-PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms);
+PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_cluster);
+template <typename T>
+bool panel_cluster_fits(const PanelPlan& pp);
+size_t panel_partial_bytes(int bk, size_t elem, int num_sms);
 
 template <typename T>
 cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t ldr, int64_t M,

@@ -1,0 +1,489 @@
+// cqr_panel.cu -- panel factorisation of PBMGS (a3): ICGS on one block column of the
+// encoded matrix, all M = m_pad + c rows, on G CTAs that each own a contiguous slice of rows.
+//
+// Appendix A, Algorithm CGS (one reduction per column, right-looking) with the ICGS
+// reorthogonalisation.  Per column j, with v_a = p_a^T p_j (a >= j) already reduced:
+//   if j > 0 and v_j < tau^2 eta_j:   reorthogonalise p_j against columns < j (two more
+//                                      reductions), add the coefficients to R, recompute v
+//   r_jj = sqrt(v_j), q_j = p_j / r_jj, R[j, a] = v_a / r_jj,
+//   p_a -= q_j R[j, a] for a > j                  -- fused with the next column's products
+//   v'_a = p_a^T p_{j+1} for a > j                  (p_{j+1} updated first, in registers)
+// eta_j are the squared column norms at the panel start (reduced together with v for j = 0).
+//
+// Reductions are deterministic: every CTA sums the G per-CTA partials in the same order.
+// Two synchronisation variants:
+//   cluster: G <= 16 CTAs form one thread-block cluster; partials live in shared memory and
+//            are read through distributed shared memory after a hardware cluster barrier;
+//   grid:    G <= #SMs CTAs in a cooperative launch; partials go through global memory
+//            (L2) and a release/acquire counter barrier with a bounded wait.
+#include <math.h>
+#include <stdlib.h>
+
+#include "cqr_device.cuh"
+#include "cqr_kernels.cuh"
+
+namespace cqr {
+
+namespace {
+
+constexpr int kNT = 256;
+constexpr int kNW = kNT / 32;
+constexpr size_t kSmemCap = 227 * 1024;
+constexpr int kMaxCluster = 16;
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint32_t map_peer(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ float ld_peer(uint32_t addr, float) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ double ld_peer(uint32_t addr, double) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// Release/acquire grid barrier for a cooperative launch.  bar is zeroed before the launch.
+// Thread 0 arrives with a release add (ordered after the CTA barrier, hence after every
+// thread's prior writes) and polls with acquire loads; the wait is bounded.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& target,
+                                             int* status, int site) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    target += nblocks;
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
+    int ok = 1;
+    const long long t0 = clock64();
+    while (ld_acquire_u32(bar) < target) {
+      if (ld_relaxed_i32(status + ST_CODE) == CQR_ETIMEOUT) { ok = 0; break; }
+      if (clock64() - t0 > kWaitLimitCycles) {
+        set_status(status, CQR_ETIMEOUT, site);
+        status[ST_SITE] = site;
+        ok = 0;
+        break;
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename T>
+struct Ctx {
+  T* base;       // slice, column 0, first row of this CTA
+  int64_t cs;    // column stride of the slice
+  int nr;        // rows owned
+  int pld;       // padded panel width
+  T* gpart;      // grid variant: [2][G][2*pld]
+  T* lpart;      // cluster variant: this CTA's [2][2*pld] in shared memory
+  T* red;        // grid variant: shared [8][2*pld] scratch
+  unsigned* bar;
+  int* status;
+  unsigned target;
+};
+
+template <typename T, bool CL>
+__device__ __forceinline__ void put_partial(const Ctx<T>& c, int idx, T val, int step) {
+  if (CL)
+    c.lpart[(step & 1) * 2 * c.pld + idx] = val;
+  else
+    c.gpart[((size_t)(step & 1) * gridDim.x + blockIdx.x) * 2 * c.pld + idx] = val;
+}
+
+// Synchronise and reduce entries [lo, hi) of the partial vectors into out[].
+template <typename T, bool CL>
+__device__ __forceinline__ bool sync_reduce(Ctx<T>& c, int lo, int hi, T* out, int step, int site) {
+  const int G = gridDim.x, tid = threadIdx.x;
+  if (CL) {
+    __syncthreads();
+    cluster_sync_all();
+    const uint32_t base = smem_addr(c.lpart + (step & 1) * 2 * c.pld);
+    for (int a = lo + tid; a < hi; a += kNT) {
+      T x[kMaxCluster];
+#pragma unroll
+      for (int g = 0; g < kMaxCluster; ++g)
+        x[g] = (g < G) ? ld_peer(map_peer(base + a * (uint32_t)sizeof(T), g), T(0)) : T(0);
+      T s = T(0);
+#pragma unroll
+      for (int g = 0; g < kMaxCluster; ++g) s += x[g];
+      out[a] = s;
+    }
+    __syncthreads();
+    return true;
+  }
+  if (!grid_barrier(c.bar, G, c.target, c.status, site)) return false;
+  const T* P = c.gpart + (size_t)(step & 1) * G * 2 * c.pld;
+  const int n = hi - lo;
+  if (n <= 0) {
+    __syncthreads();
+    return true;
+  }
+  // `groups` threads share one entry; group k sums partial rows k, k+groups, ...
+  int groups = kNT / n;
+  if (groups > 8) groups = 8;
+  if (groups > G) groups = G;
+  if (groups < 1) groups = 1;
+  for (int idx = tid; idx < n * groups; idx += kNT) {
+    const int grp = idx / n, a = lo + idx - grp * n;
+    T acc = T(0);
+    int g = grp;
+    for (; g + 3 * groups < G; g += 4 * groups) {
+      const T x0 = __ldcg(P + (size_t)g * 2 * c.pld + a);
+      const T x1 = __ldcg(P + (size_t)(g + groups) * 2 * c.pld + a);
+      const T x2 = __ldcg(P + (size_t)(g + 2 * groups) * 2 * c.pld + a);
+      const T x3 = __ldcg(P + (size_t)(g + 3 * groups) * 2 * c.pld + a);
+      acc += x0; acc += x1; acc += x2; acc += x3;
+    }
+    for (; g < G; g += groups) acc += __ldcg(P + (size_t)g * 2 * c.pld + a);
+    c.red[grp * 2 * c.pld + a] = acc;
+  }
+  __syncthreads();
+  for (int k = lo + tid; k < hi; k += kNT) {
+    T s = T(0);
+    for (int q = 0; q < groups; ++q) s += c.red[q * 2 * c.pld + k];
+    out[k] = s;
+  }
+  __syncthreads();
+  return true;
+}
+
+template <typename T, int RPL, bool CL, bool SMEM>
+__global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq, T* __restrict__ R,
+                                                   int64_t ldr, int64_t M, int bk, int rpc,
+                                                   int rpc_pad, double tau2, T* gpart,
+                                                   unsigned* bar, int* status, int col0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int g = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int pld = (bk + 3) / 4 * 4;
+  const int64_t row0 = (int64_t)g * rpc;
+  const int nr = (int)((M - row0) < rpc ? (M - row0) : rpc);
+  T* sm = reinterpret_cast<T*>(smraw);
+  T* small = sm + (SMEM ? (size_t)bk * rpc_pad : 0);
+  T* v = small;          // [2 pld]: v, and eta in the second half (first reduction)
+  T* eta = v + pld;
+  T* coef = v + 2 * pld;
+  T* sv = coef + pld;
+  Ctx<T> c;
+  c.base = SMEM ? sm : Q + row0;
+  c.cs = SMEM ? rpc_pad : ldq;
+  c.nr = nr;
+  c.pld = pld;
+  c.gpart = gpart;
+  c.red = sv + pld;
+  c.lpart = c.red + (CL ? 0 : 8 * 2 * pld);
+  c.bar = bar;
+  c.status = status;
+  c.target = 0;
+  int step = 0;
+
+  if (SMEM)
+    for (int a = 0; a < bk; ++a)
+      for (int r = tid; r < nr; r += kNT) sm[(size_t)a * rpc_pad + r] = Q[row0 + r + a * ldq];
+  __syncthreads();
+
+  T q[RPL], pn[RPL];
+  // step 0: v_a = p_a^T p_0 and eta_a = p_a^T p_a
+  {
+    const T* p0 = c.base;
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) {
+      const int r = lane + 32 * i;
+      pn[i] = (r < nr) ? p0[r] : T(0);
+    }
+    for (int a = warp; a < bk; a += kNW) {
+      const T* pa = c.base + a * c.cs;
+      T d0 = T(0), d1 = T(0);
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        const int r = lane + 32 * i;
+        if (r < nr) {
+          const T x = pa[r];
+          d0 += x * pn[i];
+          d1 += x * x;
+        }
+      }
+      d0 = warp_sum(d0);
+      d1 = warp_sum(d1);
+      if (lane == 0) {
+        put_partial<T, CL>(c, a, d0, step);
+        put_partial<T, CL>(c, pld + a, d1, step);
+      }
+    }
+    if (!sync_reduce<T, CL>(c, 0, 2 * pld, v, step++, 1)) return;
+  }
+
+  for (int j = 0; j < bk; ++j) {
+    if (j > 0 && tau2 > 0.0 && (double)v[j] < tau2 * (double)eta[j]) {
+      // ICGS: one more projection of p_j on the computed columns 0 .. j-1
+      const T* pj = c.base + j * c.cs;
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        const int r = lane + 32 * i;
+        pn[i] = (r < nr) ? pj[r] : T(0);
+      }
+      for (int a = warp; a < j; a += kNW) {
+        const T* pa = c.base + a * c.cs;
+        T d = T(0);
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+          const int r = lane + 32 * i;
+          if (r < nr) d += pa[r] * pn[i];
+        }
+        d = warp_sum(d);
+        if (lane == 0) put_partial<T, CL>(c, a, d, step);
+      }
+      if (!sync_reduce<T, CL>(c, 0, j, sv, step++, 3)) return;
+      T* pjw = c.base + j * c.cs;
+      for (int r = tid; r < nr; r += kNT) {
+        T acc = pjw[r];
+        for (int a = 0; a < j; ++a) acc -= c.base[a * c.cs + r] * sv[a];
+        pjw[r] = acc;
+      }
+      if (g == 0) {
+        for (int a = tid; a < j; a += kNT) R[a + j * ldr] += sv[a];
+        if (tid == 0) atomicAdd(status + ST_REORTH, 1);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        const int r = lane + 32 * i;
+        pn[i] = (r < nr) ? pjw[r] : T(0);
+      }
+      for (int a = j + warp; a < bk; a += kNW) {
+        const T* pa = c.base + a * c.cs;
+        T d = T(0);
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+          const int r = lane + 32 * i;
+          if (r < nr) d += pa[r] * pn[i];
+        }
+        d = warp_sum(d);
+        if (lane == 0) put_partial<T, CL>(c, a, d, step);
+      }
+      if (!sync_reduce<T, CL>(c, j, bk, v, step++, 4)) return;
+    }
+    const T v0 = v[j];
+    if (!(v0 > T(0)) || !isfinite(v0)) {
+      if (g == 0 && tid == 0) set_status(status, CQR_EBREAKDOWN, col0 + j);
+      if (CL) cluster_sync_all();
+      return;
+    }
+    const T rjj = sqrt(v0);
+    for (int a = j + 1 + tid; a < bk; a += kNT) {
+      const T ca = v[a] / rjj;
+      coef[a] = ca;
+      if (g == 0) R[j + a * ldr] = ca;
+    }
+    if (g == 0 && tid == 0) R[j + j * ldr] = rjj;
+    __syncthreads();
+    // q_j (registers), updated p_{j+1} (registers), then update + next products
+    const T* pj = c.base + j * c.cs;
+    const bool nxt = (j + 1 < bk);
+    const T cn = nxt ? coef[j + 1] : T(0);
+    const T* pj1 = c.base + (j + 1) * c.cs;
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) {
+      const int r = lane + 32 * i;
+      q[i] = (r < nr) ? pj[r] / rjj : T(0);
+      pn[i] = (nxt && r < nr) ? pj1[r] - q[i] * cn : T(0);
+    }
+    __syncthreads();
+    for (int a = j + 1 + warp; a < bk; a += kNW) {
+      T* pa = c.base + a * c.cs;
+      const T ca = coef[a];
+      T d = T(0);
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        const int r = lane + 32 * i;
+        if (r < nr) {
+          const T x = pa[r] - q[i] * ca;
+          pa[r] = x;
+          d += x * pn[i];
+        }
+      }
+      d = warp_sum(d);
+      if (lane == 0) put_partial<T, CL>(c, a, d, step);
+    }
+    if (warp == 0) {
+      T* pjw = c.base + j * c.cs;
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        const int r = lane + 32 * i;
+        if (r < nr) pjw[r] = q[i];
+      }
+    }
+    if (!nxt) break;
+    if (!sync_reduce<T, CL>(c, j + 1, bk, v, step++, 2)) return;
+  }
+  __syncthreads();
+  if (SMEM)
+    for (int a = 0; a < bk; ++a)
+      for (int r = tid; r < nr; r += kNT) Q[row0 + r + a * ldq] = sm[(size_t)a * rpc_pad + r];
+  if (CL) cluster_sync_all();  // peers may still read this CTA's partials
+}
+
+size_t small_bytes(int bk, size_t elem, bool cl) {
+  const int pld = (bk + 3) / 4 * 4;
+  // v (2 pld, includes eta), coef, sv, then either red [8][2 pld] or lpart [2][2 pld]
+  return (size_t)(2 * pld + 2 * pld + (cl ? 4 * pld : 16 * pld)) * elem + 256;
+}
+
+int env_int(const char* name, int dflt) {
+  const char* s = getenv(name);
+  return s ? atoi(s) : dflt;
+}
+
+template <typename T, int RPL>
+const void* kernel_of(bool cl, bool smem) {
+  if (cl) return (const void*)k_panel<T, RPL, true, true>;
+  if (smem) return (const void*)k_panel<T, RPL, false, true>;
+  return (const void*)k_panel<T, RPL, false, false>;
+}
+
+template <typename T>
+const void* pick_kernel(int rpl, bool cl, bool smem) {
+  switch (rpl) {
+    case 4: return kernel_of<T, 4>(cl, smem);
+    case 8: return kernel_of<T, 8>(cl, smem);
+    case 16: return kernel_of<T, 16>(cl, smem);
+    default: return kernel_of<T, 32>(cl, smem);
+  }
+}
+
+}  // namespace
+
+// Launch plan: smallest G whose row slices fit in shared memory; a cluster when that G can
+// be at most 16 (then the cluster is widened to 16 CTAs, or fewer rows per CTA than 64 would
+// leave idle lanes), else the grid variant.  CQR_PANEL_G / CQR_PANEL_CLUSTER override.
+PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_cluster) {
+  PanelPlan p{};
+  const size_t room = kSmemCap - small_bytes(bk, elem, false) - 1024;
+  int64_t rpc_max = (int64_t)(room / ((size_t)bk * elem));
+  if (rpc_max > 1024) rpc_max = 1024;
+  int64_t G = rpc_max > 0 ? (M + rpc_max - 1) / rpc_max : num_sms + 1;
+  if (G < 1) G = 1;
+  bool smem = G <= num_sms;
+  bool cl = allow_cluster && smem && G <= kMaxCluster;
+  if (cl) {
+    int64_t Gc = (M + 63) / 64;
+    G = Gc < kMaxCluster ? (Gc > G ? Gc : G) : kMaxCluster;
+  }
+  if (!smem) G = (M + 1023) / 1024;
+  const int ge = env_int("CQR_PANEL_G", 0);
+  if (ge > 0) G = ge;
+  const int ce = env_int("CQR_PANEL_CLUSTER", -1);
+  if (ce == 0) cl = false;
+  if (cl && G > kMaxCluster) cl = false;
+  p.rpc = (int)((M + G - 1) / G);
+  if (p.rpc > 1024) p.rpc = 1024;
+  p.G = (int)((M + p.rpc - 1) / p.rpc);
+  smem = (size_t)bk * (p.rpc | 1) * elem + small_bytes(bk, elem, cl) + 1024 <= kSmemCap;
+  if (!smem) cl = false;
+  p.smem = smem ? 1 : 0;
+  p.cluster = cl ? 1 : 0;
+  p.rpc_pad = smem ? (p.rpc | 1) : p.rpc;
+  p.smem_bytes = (smem ? (size_t)bk * p.rpc_pad * elem : 0) + small_bytes(bk, elem, cl);
+  return p;
+}
+
+template <typename T>
+cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t ldr, int64_t M,
+                         int bk, double tau, T* part, unsigned* bar, int* status, int col0,
+                         cudaStream_t st) {
+  if (pp.G > 1 && !pp.cluster) {
+    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+  }
+  int rpl = (pp.rpc + 31) / 32;
+  rpl = rpl <= 4 ? 4 : rpl <= 8 ? 8 : rpl <= 16 ? 16 : 32;
+  double tau2 = tau > 0.0 ? tau * tau : -1.0;
+  int rpc = pp.rpc, rpc_pad = pp.rpc_pad;
+  void* args[] = {&Q, &ldq, &R, &ldr, &M, &bk, &rpc, &rpc_pad, &tau2, &part, &bar, &status, &col0};
+  const void* fn = pick_kernel<T>(rpl, pp.cluster != 0, pp.smem != 0);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)pp.smem_bytes);
+  if (e != cudaSuccess) return e;
+  if (pp.cluster) {
+    if (pp.G > 8) {
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(pp.G);
+    cfg.blockDim = dim3(kNT);
+    cfg.dynamicSmemBytes = pp.smem_bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = pp.G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+  }
+  return cudaLaunchCooperativeKernel(fn, dim3(pp.G), dim3(kNT), args, pp.smem_bytes, st);
+}
+
+// Whether a cluster of pp.G CTAs with this shared-memory footprint can be scheduled.
+template <typename T>
+bool panel_cluster_fits(const PanelPlan& pp) {
+  int rpl = (pp.rpc + 31) / 32;
+  rpl = rpl <= 4 ? 4 : rpl <= 8 ? 8 : rpl <= 16 ? 16 : 32;
+  const void* fn = pick_kernel<T>(rpl, true, true);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp.smem_bytes) !=
+      cudaSuccess)
+    return false;
+  if (pp.G > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                      cudaSuccess)
+    return false;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(pp.G);
+  cfg.blockDim = dim3(kNT);
+  cfg.dynamicSmemBytes = pp.smem_bytes;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = pp.G;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n >= 1;
+}
+
+size_t panel_partial_bytes(int bk, size_t elem, int num_sms) {
+  const int pld = (bk + 3) / 4 * 4;
+  return (size_t)2 * (num_sms + 1) * 2 * pld * elem;
+}
+
+template cudaError_t launch_panel<float>(const PanelPlan&, float*, int64_t, float*, int64_t, int64_t,
+                                         int, double, float*, unsigned*, int*, int, cudaStream_t);
+template cudaError_t launch_panel<double>(const PanelPlan&, double*, int64_t, double*, int64_t,
+                                          int64_t, int, double, double*, unsigned*, int*, int,
+                                          cudaStream_t);
+template bool panel_cluster_fits<float>(const PanelPlan&);
+template bool panel_cluster_fits<double>(const PanelPlan&);
+
+}  // namespace cqr
