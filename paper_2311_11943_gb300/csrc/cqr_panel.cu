@@ -26,7 +26,7 @@ namespace cqr {
 
 namespace {
 
-constexpr int kNT = 256;
+constexpr int kNT = 512;
 constexpr int kNW = kNT / 32;
 constexpr size_t kSmemCap = 227 * 1024;
 constexpr int kMaxCluster = 16;
@@ -163,6 +163,13 @@ __device__ __forceinline__ bool sync_reduce(Ctx<T>& c, int lo, int hi, T* out, i
   return true;
 }
 
+// Rows of the slice visited by one lane: r = lane + 32 i, i < RPL.  With the slice in shared
+// memory the CTA's rows are padded with zeros to exactly 32 RPL, so no row guard is needed.
+template <typename T, int RPL, bool SMEM>
+__device__ __forceinline__ bool row_ok(int r, int nr) {
+  return SMEM ? true : (r < nr);
+}
+
 template <typename T, int RPL, bool CL, bool SMEM>
 __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq, T* __restrict__ R,
                                                    int64_t ldr, int64_t M, int bk, int rpc,
@@ -195,7 +202,8 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
 
   if (SMEM)
     for (int a = 0; a < bk; ++a)
-      for (int r = tid; r < nr; r += kNT) sm[(size_t)a * rpc_pad + r] = Q[row0 + r + a * ldq];
+      for (int r = tid; r < rpc; r += kNT)
+        sm[(size_t)a * rpc_pad + r] = (r < nr) ? Q[row0 + r + a * ldq] : T(0);
   __syncthreads();
 
   T q[RPL], pn[RPL];
@@ -205,7 +213,7 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
 #pragma unroll
     for (int i = 0; i < RPL; ++i) {
       const int r = lane + 32 * i;
-      pn[i] = (r < nr) ? p0[r] : T(0);
+      pn[i] = row_ok<T, RPL, SMEM>(r, nr) ? p0[r] : T(0);
     }
     for (int a = warp; a < bk; a += kNW) {
       const T* pa = c.base + a * c.cs;
@@ -213,7 +221,7 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
 #pragma unroll
       for (int i = 0; i < RPL; ++i) {
         const int r = lane + 32 * i;
-        if (r < nr) {
+        if (row_ok<T, RPL, SMEM>(r, nr)) {
           const T x = pa[r];
           d0 += x * pn[i];
           d1 += x * x;
@@ -236,7 +244,7 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
 #pragma unroll
       for (int i = 0; i < RPL; ++i) {
         const int r = lane + 32 * i;
-        pn[i] = (r < nr) ? pj[r] : T(0);
+        pn[i] = row_ok<T, RPL, SMEM>(r, nr) ? pj[r] : T(0);
       }
       for (int a = warp; a < j; a += kNW) {
         const T* pa = c.base + a * c.cs;
@@ -244,14 +252,14 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
 #pragma unroll
         for (int i = 0; i < RPL; ++i) {
           const int r = lane + 32 * i;
-          if (r < nr) d += pa[r] * pn[i];
+          if (row_ok<T, RPL, SMEM>(r, nr)) d += pa[r] * pn[i];
         }
         d = warp_sum(d);
         if (lane == 0) put_partial<T, CL>(c, a, d, step);
       }
       if (!sync_reduce<T, CL>(c, 0, j, sv, step++, 3)) return;
       T* pjw = c.base + j * c.cs;
-      for (int r = tid; r < nr; r += kNT) {
+      for (int r = tid; r < (SMEM ? rpc : nr); r += kNT) {
         T acc = pjw[r];
         for (int a = 0; a < j; ++a) acc -= c.base[a * c.cs + r] * sv[a];
         pjw[r] = acc;
@@ -264,7 +272,7 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
 #pragma unroll
       for (int i = 0; i < RPL; ++i) {
         const int r = lane + 32 * i;
-        pn[i] = (r < nr) ? pjw[r] : T(0);
+        pn[i] = row_ok<T, RPL, SMEM>(r, nr) ? pjw[r] : T(0);
       }
       for (int a = j + warp; a < bk; a += kNW) {
         const T* pa = c.base + a * c.cs;
@@ -272,7 +280,7 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
 #pragma unroll
         for (int i = 0; i < RPL; ++i) {
           const int r = lane + 32 * i;
-          if (r < nr) d += pa[r] * pn[i];
+          if (row_ok<T, RPL, SMEM>(r, nr)) d += pa[r] * pn[i];
         }
         d = warp_sum(d);
         if (lane == 0) put_partial<T, CL>(c, a, d, step);
@@ -286,8 +294,9 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
       return;
     }
     const T rjj = sqrt(v0);
+    const T inv = T(1) / rjj;
     for (int a = j + 1 + tid; a < bk; a += kNT) {
-      const T ca = v[a] / rjj;
+      const T ca = v[a] * inv;
       coef[a] = ca;
       if (g == 0) R[j + a * ldr] = ca;
     }
@@ -301,32 +310,62 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
 #pragma unroll
     for (int i = 0; i < RPL; ++i) {
       const int r = lane + 32 * i;
-      q[i] = (r < nr) ? pj[r] / rjj : T(0);
-      pn[i] = (nxt && r < nr) ? pj1[r] - q[i] * cn : T(0);
+      const bool ok = row_ok<T, RPL, SMEM>(r, nr);
+      q[i] = ok ? pj[r] * inv : T(0);
+      pn[i] = (nxt && ok) ? pj1[r] - q[i] * cn : T(0);
     }
     __syncthreads();
-    for (int a = j + 1 + warp; a < bk; a += kNW) {
+    // two columns per iteration so that their loads and shuffle reductions overlap
+    int a = j + 1 + warp;
+    for (; a + kNW < bk; a += 2 * kNW) {
       T* pa = c.base + a * c.cs;
-      const T ca = coef[a];
-      T d = T(0);
+      T* pb = c.base + (a + kNW) * c.cs;
+      const T ca = coef[a], cb = coef[a + kNW];
+      T da = T(0), db = T(0);
 #pragma unroll
       for (int i = 0; i < RPL; ++i) {
         const int r = lane + 32 * i;
-        if (r < nr) {
-          const T x = pa[r] - q[i] * ca;
-          pa[r] = x;
-          d += x * pn[i];
+        if (row_ok<T, RPL, SMEM>(r, nr)) {
+          const T xa = pa[r] - q[i] * ca;
+          const T xb = pb[r] - q[i] * cb;
+          pa[r] = xa;
+          pb[r] = xb;
+          da += xa * pn[i];
+          db += xb * pn[i];
         }
       }
-      d = warp_sum(d);
-      if (lane == 0) put_partial<T, CL>(c, a, d, step);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        da += __shfl_xor_sync(0xffffffffu, da, o);
+        db += __shfl_xor_sync(0xffffffffu, db, o);
+      }
+      if (lane == 0) {
+        put_partial<T, CL>(c, a, da, step);
+        put_partial<T, CL>(c, a + kNW, db, step);
+      }
+    }
+    if (a < bk) {
+      T* pa = c.base + a * c.cs;
+      const T ca = coef[a];
+      T da = T(0);
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        const int r = lane + 32 * i;
+        if (row_ok<T, RPL, SMEM>(r, nr)) {
+          const T xa = pa[r] - q[i] * ca;
+          pa[r] = xa;
+          da += xa * pn[i];
+        }
+      }
+      da = warp_sum(da);
+      if (lane == 0) put_partial<T, CL>(c, a, da, step);
     }
     if (warp == 0) {
       T* pjw = c.base + j * c.cs;
 #pragma unroll
       for (int i = 0; i < RPL; ++i) {
         const int r = lane + 32 * i;
-        if (r < nr) pjw[r] = q[i];
+        if (row_ok<T, RPL, SMEM>(r, nr)) pjw[r] = q[i];
       }
     }
     if (!nxt) break;
@@ -361,45 +400,71 @@ template <typename T>
 const void* pick_kernel(int rpl, bool cl, bool smem) {
   switch (rpl) {
     case 4: return kernel_of<T, 4>(cl, smem);
+    case 6: return kernel_of<T, 6>(cl, smem);
     case 8: return kernel_of<T, 8>(cl, smem);
+    case 12: return kernel_of<T, 12>(cl, smem);
     case 16: return kernel_of<T, 16>(cl, smem);
+    case 24: return kernel_of<T, 24>(cl, smem);
     default: return kernel_of<T, 32>(cl, smem);
   }
 }
 
+constexpr int kRpl[] = {4, 6, 8, 12, 16, 24, 32};
+
+int rpl_for_rows(int rpc) {
+  for (int r : kRpl)
+    if (32 * r >= rpc) return r;
+  return 32;
+}
+
 }  // namespace
 
-// Launch plan: smallest G whose row slices fit in shared memory; a cluster when that G can
-// be at most 16 (then the cluster is widened to 16 CTAs, or fewer rows per CTA than 64 would
-// leave idle lanes), else the grid variant.  CQR_PANEL_G / CQR_PANEL_CLUSTER override.
+// Launch plan.  A CTA's slice has rpc = 32 RPL rows (RPL rows per lane).  Preferred: the
+// smallest RPL whose slices fit shared memory and give G <= 16 CTAs (one cluster); otherwise
+// the smallest RPL that fits shared memory with G <= #SMs (grid barrier); otherwise slices in
+// global memory.  CQR_PANEL_RPL / CQR_PANEL_CLUSTER override the choice (tuning).
 PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_cluster) {
   PanelPlan p{};
-  const size_t room = kSmemCap - small_bytes(bk, elem, false) - 1024;
-  int64_t rpc_max = (int64_t)(room / ((size_t)bk * elem));
-  if (rpc_max > 1024) rpc_max = 1024;
-  int64_t G = rpc_max > 0 ? (M + rpc_max - 1) / rpc_max : num_sms + 1;
-  if (G < 1) G = 1;
-  bool smem = G <= num_sms;
-  bool cl = allow_cluster && smem && G <= kMaxCluster;
-  if (cl) {
-    int64_t Gc = (M + 63) / 64;
-    G = Gc < kMaxCluster ? (Gc > G ? Gc : G) : kMaxCluster;
+  const int rpl_env = env_int("CQR_PANEL_RPL", 0);
+  const int cl_env = env_int("CQR_PANEL_CLUSTER", -1);
+  auto fits = [&](int rpl, bool cl) {
+    const int rpc = 32 * rpl;
+    return (size_t)bk * (rpc + 1) * elem + small_bytes(bk, elem, cl) + 1024 <= kSmemCap;
+  };
+  int best = -1;
+  bool best_cl = false;
+  if (allow_cluster && cl_env != 0)
+    for (int r : kRpl)
+      if ((rpl_env == 0 || r == rpl_env) && fits(r, true) && (M + 32 * r - 1) / (32 * r) <= kMaxCluster) {
+        best = r;
+        best_cl = true;
+        break;
+      }
+  if (best < 0)
+    for (int r : kRpl)
+      if ((rpl_env == 0 || r == rpl_env) && fits(r, false) && (M + 32 * r - 1) / (32 * r) <= num_sms) {
+        best = r;
+        break;
+      }
+  if (best > 0) {
+    p.smem = 1;
+    p.cluster = best_cl ? 1 : 0;
+    p.rpc = 32 * best;
+    p.G = (int)((M + p.rpc - 1) / p.rpc);
+    p.rpc_pad = p.rpc + 1;
+    p.smem_bytes = (size_t)bk * p.rpc_pad * elem + small_bytes(bk, elem, best_cl);
+    return p;
   }
-  if (!smem) G = (M + 1023) / 1024;
-  const int ge = env_int("CQR_PANEL_G", 0);
-  if (ge > 0) G = ge;
-  const int ce = env_int("CQR_PANEL_CLUSTER", -1);
-  if (ce == 0) cl = false;
-  if (cl && G > kMaxCluster) cl = false;
-  p.rpc = (int)((M + G - 1) / G);
-  if (p.rpc > 1024) p.rpc = 1024;
+  // slices stay in global memory (L2): at most 32 rows per lane
+  int rpl = (int)((M + 32LL * num_sms - 1) / (32LL * num_sms));
+  rpl = rpl_for_rows(32 * rpl);
+  if (rpl_env > 0) rpl = rpl_env;
+  p.smem = 0;
+  p.cluster = 0;
+  p.rpc = 32 * rpl;
   p.G = (int)((M + p.rpc - 1) / p.rpc);
-  smem = (size_t)bk * (p.rpc | 1) * elem + small_bytes(bk, elem, cl) + 1024 <= kSmemCap;
-  if (!smem) cl = false;
-  p.smem = smem ? 1 : 0;
-  p.cluster = cl ? 1 : 0;
-  p.rpc_pad = smem ? (p.rpc | 1) : p.rpc;
-  p.smem_bytes = (smem ? (size_t)bk * p.rpc_pad * elem : 0) + small_bytes(bk, elem, cl);
+  p.rpc_pad = p.rpc;
+  p.smem_bytes = small_bytes(bk, elem, false);
   return p;
 }
 
@@ -411,8 +476,7 @@ cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t l
     cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
   }
-  int rpl = (pp.rpc + 31) / 32;
-  rpl = rpl <= 4 ? 4 : rpl <= 8 ? 8 : rpl <= 16 ? 16 : 32;
+  const int rpl = rpl_for_rows(pp.rpc);
   double tau2 = tau > 0.0 ? tau * tau : -1.0;
   int rpc = pp.rpc, rpc_pad = pp.rpc_pad;
   void* args[] = {&Q, &ldq, &R, &ldr, &M, &bk, &rpc, &rpc_pad, &tau2, &part, &bar, &status, &col0};
@@ -445,9 +509,7 @@ cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t l
 // Whether a cluster of pp.G CTAs with this shared-memory footprint can be scheduled.
 template <typename T>
 bool panel_cluster_fits(const PanelPlan& pp) {
-  int rpl = (pp.rpc + 31) / 32;
-  rpl = rpl <= 4 ? 4 : rpl <= 8 ? 8 : rpl <= 16 ? 16 : 32;
-  const void* fn = pick_kernel<T>(rpl, true, true);
+  const void* fn = pick_kernel<T>(rpl_for_rows(pp.rpc), true, true);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp.smem_bytes) !=
       cudaSuccess)
     return false;
