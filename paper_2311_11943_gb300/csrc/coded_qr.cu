@@ -202,10 +202,15 @@ struct ProfScope {
 
 }  // namespace
 
+// A failed runtime call returns CQR_ECUDA; the runtime's last-error slot is cleared so that a
+// later, unrelated launch check does not report it again (sticky errors stay sticky).
 #define CK(x)                                          \
   do {                                                 \
     cudaError_t e_ = (x);                              \
-    if (e_ != cudaSuccess) return CQR_ECUDA;           \
+    if (e_ != cudaSuccess) {                           \
+      cudaGetLastError();                              \
+      return CQR_ECUDA;                                \
+    }                                                  \
   } while (0)
 
 namespace {
@@ -242,6 +247,7 @@ cqr_status setup(cqr_handle h) {
     h->tc = tc_create(h->cfg.mma, h->g.M, h->g.N, std::min<int64_t>(h->cfg.b, h->g.n),
                       ptr<float>(h->B.Q), h->g.ldq, h->B.Pt, h->B.tc, h->num_sms);
     if (!h->tc) return CQR_ECUDA;
+    tc_set_status(h->tc, h->B.status);
   }
   return CQR_OK;
 }
@@ -621,7 +627,10 @@ cqr_status coded_qr_inject_erasure(cqr_handle h, const int32_t* tiles, int32_t c
   cudaError_t err = h->esz == 8
       ? launch_poison<double>(g, tiles, count, ptr<double>(h->B.Q), ptr<double>(h->B.R), h->st)
       : launch_poison<float>(g, tiles, count, ptr<float>(h->B.Q), ptr<float>(h->B.R), h->st);
-  if (err != cudaSuccess) return CQR_ECUDA;
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return CQR_ECUDA;
+  }
   h->pending = true;
   h->n_injected += count;
   return CQR_OK;

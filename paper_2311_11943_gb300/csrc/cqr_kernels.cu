@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ R, int
                                                      int* status) {
   constexpr int BS = 64;
   __shared__ T Rd[BS][BS + 1];
-  __shared__ T xs[BS];
+  __shared__ T xs[2 * BS];
   const int G = gridDim.x, tid = threadIdx.x;
   unsigned target = 0;
   const int64_t nblk = (n + BS - 1) / BS;
@@ -559,9 +559,12 @@ __global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ R, int
       const int64_t p0 = i1, p1 = (i1 + BS < n) ? i1 + BS : n;  // previously solved block
       if (blockIdx.x == 0) {
         // rows of this block: subtract the previous block's contribution, load into smem
+        for (int e = tid; e < (int)(p1 - p0); e += blockDim.x) xs[BS + e] = __ldcg(xc + p0 + e);
+        __syncthreads();
         for (int r = tid; r < nbk; r += blockDim.x) {
           T acc = __ldcg(xc + i0 + r);
-          for (int64_t j = p0; j < p1; ++j) acc -= R[(i0 + r) + j * ldr] * __ldcg(xc + j);
+#pragma unroll 16
+          for (int jj = 0; jj < (int)(p1 - p0); ++jj) acc -= R[(i0 + r) + (p0 + jj) * ldr] * xs[BS + jj];
           xs[r] = acc;
         }
         for (int e = tid; e < nbk * nbk; e += blockDim.x) {
@@ -590,7 +593,8 @@ __global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ R, int
         for (int64_t r = (int64_t)(blockIdx.x - 1) * blockDim.x + tid; r < i0;
              r += (int64_t)(G - 1) * blockDim.x) {
           T acc = __ldcg(xc + r);
-          for (int64_t j = p0; j < p1; ++j) acc -= R[r + j * ldr] * xs[j - p0];
+#pragma unroll 16
+          for (int jj = 0; jj < (int)(p1 - p0); ++jj) acc -= R[r + (p0 + jj) * ldr] * xs[jj];
           xc[r] = acc;
         }
       }

@@ -458,7 +458,7 @@ PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_clu
   // slices stay in global memory (L2): at most 32 rows per lane
   int rpl = (int)((M + 32LL * num_sms - 1) / (32LL * num_sms));
   rpl = rpl_for_rows(32 * rpl);
-  if (rpl_env > 0) rpl = rpl_env;
+  if (rpl_env > rpl) rpl = rpl_for_rows(32 * rpl_env);  // never more CTAs than SMs
   p.smem = 0;
   p.cluster = 0;
   p.rpc = 32 * rpl;

@@ -15,6 +15,7 @@ TcGemm* tc_create(int mode, int64_t M, int64_t N, int64_t b, float* Q, int64_t l
                   void* ws, int num_sms);
 void tc_destroy(TcGemm* t);
 int tc_launches_per_update(const TcGemm* t);
+void tc_set_status(TcGemm* t, int* status);
 // Rbar = Qbar^T Q[:, j0:j0+w] into R[kb:kb+bk, j0:j0+w], then Q[:, j0:j0+w] -= Qbar Rbar.
 cudaError_t tc_trailing_update(TcGemm* t, int64_t kb, int bk, int64_t j0, int64_t w, float* R,
                                int64_t ldr, cudaStream_t st);

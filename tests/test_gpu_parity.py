@@ -265,3 +265,54 @@ def test_c2_fp64_full_size_sampled():
     assert np.abs(got["Q"][n: g.M, :n] - Gv @ Q1).max() < 1e-12
     Ghk = np.kron(got["Gh"], np.eye(g.nb))
     assert np.abs(got["R"][:n, n:] - R1 @ Ghk).max() < 1e-12 * np.abs(R1).max()
+
+
+# ----------------------------------------------------------------- tensor-core trailing update
+# 3xTF32 splits each FP32 operand into a TF32 head and tail (three tcgen05 products); its
+# products carry a relative error of about 2^-21 (8 u32).  Plain TF32 has unit roundoff 2^-11.
+U3X = 8 * U32
+UTF32 = 2.0 ** -11
+
+
+@pytest.mark.parametrize("shape", [(256, 256, 4, 4, 1, 32), (203, 96, 8, 4, 2, 20),
+                                   (640, 640, 8, 8, 2, 128), (1024, 512, 8, 4, 2, 256)])
+def test_3xtf32_path_parity(shape):
+    m, n, p_r, p_c, f, b = shape
+    A = synth.kappa_matrix(m, n, 1e2, seed=3)
+    y = synth.rhs(m, 1, 3)
+    T = -(-n // b)
+    er = {T // 2: synth.random_erasures(p_r + f, p_c + f, f, 2, seed=5)}
+    ref = O.run(A, p_r, p_c, f, b, seed=4, erasures=er, y=y)
+    got = gpu_run(A, p_r, p_c, f, b, seed=4, erasures=er, y=y, dtype="f32", mma="3xtf32")
+    assert got["status"] == 0
+    assert got["sets"] == ref["sets"]
+    g = ref["geom"]
+    tol = n * U3X * 1e2
+    assert rel(got["Q"][: g.M, :n], ref["Q"][:, :n]) < tol
+    assert rel(got["R"], ref["R"]) < tol
+    assert rel(got["Qo"], ref["Qo"]) < tol
+    if "x" in got:
+        assert rel(got["x"], ref["x"]) < tol * 1e2
+    Q1, R1 = got["Q"][:m, :n], got["R"][:n, :n]
+    assert np.linalg.norm(A - Q1 @ R1) / np.linalg.norm(A) < 1e-5
+
+
+def test_tf32_path_well_conditioned():
+    m = n = 512
+    A = synth.kappa_matrix(m, n, 4.0, seed=8)
+    ref = O.run(A, 8, 8, 2, 128, seed=1)
+    got = gpu_run(A, 8, 8, 2, 128, seed=1, dtype="f32", mma="tf32")
+    assert got["status"] == 0
+    Q1, R1 = got["Q"][:m, :n], got["R"][:n, :n]
+    assert np.linalg.norm(A - Q1 @ R1) / np.linalg.norm(A) < 8 * UTF32
+    assert rel(got["R"], ref["R"]) < n * UTF32 * 4.0
+    Qo = got["Qo"]
+    assert np.abs(Qo.T @ Qo - np.eye(n)).max() < n * UTF32
+
+
+def test_tc_matches_simt_fp32_closely():
+    # same FP32 storage, trailing updates on tensor cores (3xTF32) vs CUDA cores (FP32 FMA)
+    A = synth.kappa_matrix(384, 384, 10.0, seed=9)
+    a = gpu_run(A, 4, 4, 1, 64, seed=2, dtype="f32", mma="simt")
+    b = gpu_run(A, 4, 4, 1, 64, seed=2, dtype="f32", mma="3xtf32")
+    assert rel(b["R"], a["R"]) < 384 * U3X * 10.0
