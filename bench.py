@@ -363,7 +363,7 @@ def run_ours(args, cfg):
                      for t in range(T) if t * b + min(b, n - t * b) < N)
     panel_bytes = sum(2.0 * M * min(b, n - t * b) * es for t in range(T))
     if dom_name in ("gemm_rbar_simt", "gemm_update_simt", "tc_rbar", "tc_update"):
-        per_class = {"tc_update": 2.0, "tc_rbar": 1.0, "gemm_rbar_simt": 1.0, "gemm_update_simt": 1.0}
+        per_class = {"tc_update": 1.0, "tc_rbar": 1.0, "gemm_rbar_simt": 1.0, "gemm_update_simt": 1.0}
         algo = gemm_flops * per_class[dom_name] * args.steps / dom_launches
         achieved = algo / (dom_ms / dom_launches * 1e-3) / 1e12
         if dtype == "f64":
@@ -446,7 +446,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
-    ap.add_argument("--mode", default=os.environ.get("CQR_BENCH_MODE", "f32"),
+    ap.add_argument("--mode", default=os.environ.get("CQR_BENCH_MODE", "3xtf32"),
                     choices=sorted(MODES))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -195,7 +195,7 @@ cqr_status coded_qr_sync_status(cqr_handle h);
  * synchronises the stream and fills (host) ms[k] (device milliseconds) and launches[k]
  * for the first cap classes (CQR_PROF_CLASSES in total) since the last reset; reset != 0
  * clears the accumulators.  coded_qr_profile_name gives the class name (NULL past the end). */
-#define CQR_PROF_CLASSES 13
+#define CQR_PROF_CLASSES 14
 cqr_status coded_qr_profile(cqr_handle h, int32_t enable);
 cqr_status coded_qr_profile_read(cqr_handle h, double* ms, int64_t* launches, int32_t cap,
                                  int32_t reset);

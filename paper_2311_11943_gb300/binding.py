@@ -29,7 +29,7 @@ EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "
            "coded_qr_get_factors", "coded_qr_get_generator", "coded_qr_get_decode_sets",
            "coded_qr_stats", "coded_qr_sync_status", "coded_qr_errstr", "coded_qr_profile",
            "coded_qr_profile_read", "coded_qr_profile_name"]
-PROF_CLASSES = 13
+PROF_CLASSES = 14
 
 
 class Config(C.Structure):

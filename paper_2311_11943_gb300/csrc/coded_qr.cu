@@ -122,11 +122,12 @@ Layout make_layout(const cqr_config* c, const Geo& g, int num_sms) {
 // Kernel classes of the per-launch-site profile (coded_qr_profile_read).
 enum KClass {
   K_GENERATOR = 0, K_ENCODE, K_PANEL, K_GEMM_RBAR, K_SPLITK_REDUCE, K_GEMM_UPDATE, K_POISON,
-  K_DECODE, K_POST_ORTH, K_SOLVE_GEMV, K_TRSV, K_TC_RBAR, K_TC_UPDATE, K_COUNT
+  K_DECODE, K_POST_ORTH, K_SOLVE_GEMV, K_TRSV, K_TC_RBAR, K_TC_UPDATE, K_TC_SPLIT, K_COUNT
 };
 static const char* kClassNames[K_COUNT] = {
     "generator", "encode", "panel_icgs", "gemm_rbar_simt", "splitk_reduce", "gemm_update_simt",
-    "erasure_poison", "decode", "post_orth", "solve_gemv", "trsv", "tc_rbar", "tc_update"};
+    "erasure_poison", "decode", "post_orth", "solve_gemv", "trsv", "tc_rbar", "tc_update",
+    "tc_split_panel"};
 
 struct ProfRec {
   int cls;
@@ -346,9 +347,22 @@ cqr_status panel_step(cqr_handle h, int t) {
   if (j0 >= g.N) return CQR_OK;
   const int64_t w = g.N - j0;
   if (tc) {
-    ProfScope ps(h, K_TC_UPDATE, tc_launches_per_update(h->tc));
-    if (tc_trailing_update(h->tc, kb, bk, j0, w, ptr<float>(h->B.R), g.ldr, h->st) != cudaSuccess)
-      return CQR_ECUDA;
+    {
+      ProfScope ps(h, K_TC_SPLIT, 1);
+      CK(tc_split_panel(h->tc, kb, bk, h->st));
+    }
+    {
+      ProfScope ps(h, K_TC_RBAR, 1);
+      CK(tc_gemm_rbar(h->tc, bk, j0, w, h->st));
+    }
+    {
+      ProfScope ps(h, K_SPLITK_REDUCE, 1);
+      CK(tc_reduce(h->tc, kb, bk, j0, w, ptr<float>(h->B.R), g.ldr, h->st));
+    }
+    {
+      ProfScope ps(h, K_TC_UPDATE, 1);
+      CK(tc_gemm_update(h->tc, bk, j0, w, h->st));
+    }
     return CQR_OK;
   }
   const int splits = choose_splits(bk, w, g.M, h->num_sms);

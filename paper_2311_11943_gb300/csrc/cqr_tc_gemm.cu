@@ -19,6 +19,7 @@
 // Every mbarrier wait is bounded: on expiry the kernel records CQR_ETIMEOUT, stops issuing,
 // waits (bounded) for its own copies, frees TMEM and returns.
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -459,13 +460,30 @@ struct TcGemm {
 
 namespace {
 
+// The driver's tensor-map encoder, resolved through the runtime (the library does not link
+// the driver library, so it loads on machines without a GPU driver).
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
 bool encode_2d(CUtensorMap* tm, void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
                uint32_t box_inner, uint32_t box_outer) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+  if (!enc) return false;
   cuuint64_t dims[2] = {inner, outer};
   cuuint64_t strides[1] = {row_bytes};
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = cuTensorMapEncodeTiled(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
                                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -545,97 +563,107 @@ TcGemm* tc_create(int mode, int64_t M, int64_t N, int64_t b, float* Q, int64_t l
 
 void tc_destroy(TcGemm* t) { delete t; }
 
-int tc_launches_per_update(const TcGemm*) { return 4; }
-
 void tc_set_status(TcGemm* t, int* status) { t->status = status; }
 
-cudaError_t tc_trailing_update(TcGemm* t, int64_t kb, int bk, int64_t j0, int64_t w, float* R,
-                               int64_t ldr, cudaStream_t st) {
-  const int three = t->nplanes == 2;
-  const int bkp = (int)((bk + BK - 1) / BK * BK);
-  const int m1 = (bk + BM - 1) / BM;            // GEMM1 M tiles (panel columns)
-  const int n1 = (int)((w + BN - 1) / BN);       // GEMM1 N tiles (trailing columns)
-  // 1. split the panel into the operand planes of both GEMMs
-  {
-    dim3 grd((unsigned)((t->M + 255) / 256), (unsigned)std::max(bkp, m1 * BM));
-    k_split_panel<<<grd, 256, 0, st>>>(t->Q + kb * t->ldq, t->ldq, t->M, bk, bkp, m1 * BM,
-                                       t->nplanes, t->Ak_hi, t->Ak_lo, t->ldk, t->At_hi, t->At_lo);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  // 2. GEMM1 (split-K over the M rows): partials P[s] = Ak^T Q[:, j0 : j0+w]
+namespace {
+int tc_splits(const TcGemm* t, int m1, int n1, int64_t* kchunk) {
   int splits = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplits, (t->num_sms + m1 * n1 - 1) / (m1 * n1)));
   const int64_t kblocks = (t->M + BK - 1) / BK;
   if (splits > kblocks) splits = (int)kblocks;
-  int64_t kchunk = (kblocks + splits - 1) / splits * BK;
-  splits = (int)((t->M + kchunk - 1) / kchunk);
-  {
-    TcMaps maps;
-    maps.a[0] = t->tm_ak[0];
-    maps.a[1] = t->tm_ak[1];
-    maps.b[0] = t->tm_q_b;
-    maps.b[1] = t->tm_q_b;
-    TcJob job{};
-    job.nprod = three ? 3 : 1;
-    job.split_b_smem = three;
-    job.epi = 0;
-    job.m_tiles = m1;
-    job.n_tiles = n1;
-    job.splits = splits;
-    job.a_row0 = 0;
-    job.b_row0 = j0;
-    job.k0 = 0;
-    job.kchunk = kchunk;
-    job.K = t->M;
-    job.mrows = bk;
-    job.ncols = w;
-    job.out = t->P;
-    job.ldo = bkp;
-    job.split_stride = (int64_t)bkp * w;
-    job.status = t->status;
-    cudaError_t e = three ? launch_gemm<3, 2, 2>(maps, job, t->num_sms, st)
-                          : launch_gemm<6, 1, 1>(maps, job, t->num_sms, st);
-    if (e != cudaSuccess) return e;
-  }
-  // 3. reduce the partials into R and GEMM2's B planes
-  {
-    const int64_t total = (int64_t)bkp * w;
-    int blocks = (int)std::min<int64_t>(4096, (total + 255) / 256);
-    k_tc_reduce<<<blocks, 256, 0, st>>>(t->P, splits, (int64_t)bkp * w, bkp, bk, bkp, w,
-                                        R + kb + j0 * ldr, ldr, t->nplanes, t->Bh, t->Bl);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  // 4. GEMM2: Q[:, j0 : j0+w] -= At Rbar  (M tiles over rows, N tiles over trailing columns)
-  {
-    TcMaps maps;
-    maps.a[0] = t->tm_at[0];
-    maps.a[1] = t->tm_at[1];
-    maps.b[0] = t->tm_bh[0];
-    maps.b[1] = t->tm_bh[1];
-    TcJob job{};
-    job.nprod = three ? 3 : 1;
-    job.split_b_smem = 0;
-    job.epi = 1;
-    job.m_tiles = (int)((t->M + BM - 1) / BM);
-    job.n_tiles = n1;
-    job.splits = 1;
-    job.a_row0 = 0;
-    job.b_row0 = 0;
-    job.k0 = 0;
-    job.kchunk = bkp;
-    job.K = bkp;
-    job.mrows = t->M;
-    job.ncols = w;
-    job.out = t->Q + j0 * t->ldq;
-    job.ldo = t->ldq;
-    job.split_stride = 0;
-    job.status = t->status;
-    cudaError_t e = three ? launch_gemm<3, 2, 2>(maps, job, t->num_sms, st)
-                          : launch_gemm<6, 1, 1>(maps, job, t->num_sms, st);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  *kchunk = (kblocks + splits - 1) / splits * BK;
+  return (int)((t->M + *kchunk - 1) / *kchunk);
+}
+}  // namespace
+
+// 1. split the panel Q[:, kb : kb+bk] into the operand planes of both GEMMs
+cudaError_t tc_split_panel(TcGemm* t, int64_t kb, int bk, cudaStream_t st) {
+  const int bkp = (int)((bk + BK - 1) / BK * BK);
+  const int m1 = (bk + BM - 1) / BM;
+  dim3 grd((unsigned)((t->M + 255) / 256), (unsigned)std::max(bkp, m1 * BM));
+  k_split_panel<<<grd, 256, 0, st>>>(t->Q + kb * t->ldq, t->ldq, t->M, bk, bkp, m1 * BM, t->nplanes,
+                                     t->Ak_hi, t->Ak_lo, t->ldk, t->At_hi, t->At_lo);
+  return cudaGetLastError();
+}
+
+// 2. GEMM1, split-K over the M rows: partials P[s] = Qbar^T Q[:, j0 : j0+w]
+cudaError_t tc_gemm_rbar(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t st) {
+  const int three = t->nplanes == 2;
+  const int bkp = (int)((bk + BK - 1) / BK * BK);
+  const int m1 = (bk + BM - 1) / BM;
+  const int n1 = (int)((w + BN - 1) / BN);
+  int64_t kchunk = 0;
+  const int splits = tc_splits(t, m1, n1, &kchunk);
+  TcMaps maps;
+  maps.a[0] = t->tm_ak[0];
+  maps.a[1] = t->tm_ak[1];
+  maps.b[0] = t->tm_q_b;
+  maps.b[1] = t->tm_q_b;
+  TcJob job{};
+  job.nprod = three ? 3 : 1;
+  job.split_b_smem = three;
+  job.epi = 0;
+  job.m_tiles = m1;
+  job.n_tiles = n1;
+  job.splits = splits;
+  job.a_row0 = 0;
+  job.b_row0 = j0;
+  job.k0 = 0;
+  job.kchunk = kchunk;
+  job.K = t->M;
+  job.mrows = bk;
+  job.ncols = w;
+  job.out = t->P;
+  job.ldo = bkp;
+  job.split_stride = (int64_t)bkp * w;
+  job.status = t->status;
+  return three ? launch_gemm<3, 2, 2>(maps, job, t->num_sms, st)
+               : launch_gemm<6, 1, 1>(maps, job, t->num_sms, st);
+}
+
+// 3. reduce the partials into R[kb.., j0..] and GEMM2's B planes
+cudaError_t tc_reduce(TcGemm* t, int64_t kb, int bk, int64_t j0, int64_t w, float* R, int64_t ldr,
+                      cudaStream_t st) {
+  const int bkp = (int)((bk + BK - 1) / BK * BK);
+  const int m1 = (bk + BM - 1) / BM;
+  const int n1 = (int)((w + BN - 1) / BN);
+  int64_t kchunk = 0;
+  const int splits = tc_splits(t, m1, n1, &kchunk);
+  const int64_t total = (int64_t)bkp * w;
+  const int blocks = (int)std::min<int64_t>(4096, (total + 255) / 256);
+  k_tc_reduce<<<blocks, 256, 0, st>>>(t->P, splits, (int64_t)bkp * w, bkp, bk, bkp, w,
+                                      R + kb + j0 * ldr, ldr, t->nplanes, t->Bh, t->Bl);
+  return cudaGetLastError();
+}
+
+// 4. GEMM2: Q[:, j0 : j0+w] -= Qbar Rbar (M tiles over rows, N tiles over trailing columns)
+cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t st) {
+  const int three = t->nplanes == 2;
+  const int bkp = (int)((bk + BK - 1) / BK * BK);
+  TcMaps maps;
+  maps.a[0] = t->tm_at[0];
+  maps.a[1] = t->tm_at[1];
+  maps.b[0] = t->tm_bh[0];
+  maps.b[1] = t->tm_bh[1];
+  TcJob job{};
+  job.nprod = three ? 3 : 1;
+  job.split_b_smem = 0;
+  job.epi = 1;
+  job.m_tiles = (int)((t->M + BM - 1) / BM);
+  job.n_tiles = (int)((w + BN - 1) / BN);
+  job.splits = 1;
+  job.a_row0 = 0;
+  job.b_row0 = 0;
+  job.k0 = 0;
+  job.kchunk = bkp;
+  job.K = bkp;
+  job.mrows = t->M;
+  job.ncols = w;
+  job.out = t->Q + j0 * t->ldq;
+  job.ldo = t->ldq;
+  job.split_stride = 0;
+  job.status = t->status;
+  return three ? launch_gemm<3, 2, 2>(maps, job, t->num_sms, st)
+               : launch_gemm<6, 1, 1>(maps, job, t->num_sms, st);
 }
 
 }  // namespace cqr

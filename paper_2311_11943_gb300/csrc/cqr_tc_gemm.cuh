@@ -14,10 +14,14 @@ size_t tc_workspace_bytes(int64_t M, int64_t N, int b);
 TcGemm* tc_create(int mode, int64_t M, int64_t N, int64_t b, float* Q, int64_t ldq, void* panel_buf,
                   void* ws, int num_sms);
 void tc_destroy(TcGemm* t);
-int tc_launches_per_update(const TcGemm* t);
 void tc_set_status(TcGemm* t, int* status);
-// Rbar = Qbar^T Q[:, j0:j0+w] into R[kb:kb+bk, j0:j0+w], then Q[:, j0:j0+w] -= Qbar Rbar.
-cudaError_t tc_trailing_update(TcGemm* t, int64_t kb, int bk, int64_t j0, int64_t w, float* R,
-                               int64_t ldr, cudaStream_t st);
+// The trailing update of one panel, in four stream-ordered launches:
+//   split the panel into operand planes; Rbar partials = Qbar^T Q[:, j0:j0+w] (split-K);
+//   reduce into R[kb:kb+bk, j0:j0+w] and GEMM2's operand; Q[:, j0:j0+w] -= Qbar Rbar.
+cudaError_t tc_split_panel(TcGemm* t, int64_t kb, int bk, cudaStream_t st);
+cudaError_t tc_gemm_rbar(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t st);
+cudaError_t tc_reduce(TcGemm* t, int64_t kb, int bk, int64_t j0, int64_t w, float* R, int64_t ldr,
+                      cudaStream_t st);
+cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t st);
 
 }  // namespace cqr
