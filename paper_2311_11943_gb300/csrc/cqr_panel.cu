@@ -106,13 +106,19 @@ __device__ __forceinline__ void put_partial(const Ctx<T>& c, int idx, T val, int
     c.gpart[((size_t)(step & 1) * gridDim.x + blockIdx.x) * 2 * c.pld + idx] = val;
 }
 
-// Synchronise and reduce entries [lo, hi) of the partial vectors into out[].
-template <typename T, bool CL>
-__device__ __forceinline__ bool sync_reduce(Ctx<T>& c, int lo, int hi, T* out, int step, int site) {
+struct NoHook {
+  __device__ void operator()() const {}
+};
+
+// Synchronise and reduce entries [lo, hi) of the partial vectors into out[].  `hook` runs
+// right after the barrier, when every thread of this CTA has finished the step's reads.
+template <typename T, bool CL, typename Hook = NoHook>
+__device__ __forceinline__ bool sync_reduce(Ctx<T>& c, int lo, int hi, T* out, int step, int site,
+                                            Hook hook = Hook()) {
   const int G = gridDim.x, tid = threadIdx.x;
   if (CL) {
-    __syncthreads();
     cluster_sync_all();
+    hook();
     const uint32_t base = smem_addr(c.lpart + (step & 1) * 2 * c.pld);
     for (int a = lo + tid; a < hi; a += kNT) {
       T x[kMaxCluster];
@@ -128,6 +134,7 @@ __device__ __forceinline__ bool sync_reduce(Ctx<T>& c, int lo, int hi, T* out, i
     return true;
   }
   if (!grid_barrier(c.bar, G, c.target, c.status, site)) return false;
+  hook();
   const T* P = c.gpart + (size_t)(step & 1) * G * 2 * c.pld;
   const int n = hi - lo;
   if (n <= 0) {
@@ -163,18 +170,59 @@ __device__ __forceinline__ bool sync_reduce(Ctx<T>& c, int lo, int hi, T* out, i
   return true;
 }
 
-// Rows of the slice visited by one lane: r = lane + 32 i, i < RPL.  With the slice in shared
-// memory the CTA's rows are padded with zeros to exactly 32 RPL, so no row guard is needed.
-template <typename T, int RPL, bool SMEM>
-__device__ __forceinline__ bool row_ok(int r, int nr) {
-  return SMEM ? true : (r < nr);
+// Lane-local access to the slice.  VW = 2 (FP32 in shared memory): a lane owns row pairs
+// r = 64 i + 2 lane + {0, 1} and works on them with 64-bit loads and packed f32x2 FMAs;
+// VW = 1: rows r = 32 i + lane.  With the slice in shared memory the CTA's rows are padded
+// with zeros to exactly 32 RPL, so no row guard is needed.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  uint64_t ra, rb, rc, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rc) : "f"(c.x), "f"(c.y));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
 }
+
+template <typename T, int VW>
+struct LaneOps;
+
+template <>
+struct LaneOps<float, 2> {
+  using V = float2;
+  __device__ static int row(int i, int lane) { return 64 * i + 2 * lane; }
+  __device__ static V ld(const float* p) { return *reinterpret_cast<const float2*>(p); }
+  __device__ static void st(float* p, V v) { *reinterpret_cast<float2*>(p) = v; }
+  __device__ static V fma(V a, V b, V c) { return ffma2(a, b, c); }
+  __device__ static V splat(float s) { return make_float2(s, s); }
+  __device__ static V zero() { return make_float2(0.f, 0.f); }
+  __device__ static V scale(V a, float s) { return make_float2(a.x * s, a.y * s); }
+  __device__ static float sum(V v) { return v.x + v.y; }
+};
+
+template <typename T>
+struct LaneOps<T, 1> {
+  using V = T;
+  __device__ static int row(int i, int lane) { return 32 * i + lane; }
+  __device__ static V ld(const T* p) { return *p; }
+  __device__ static void st(T* p, V v) { *p = v; }
+  __device__ static V fma(V a, V b, V c) { return a * b + c; }
+  __device__ static V splat(T s) { return s; }
+  __device__ static V zero() { return T(0); }
+  __device__ static V scale(V a, T s) { return a * s; }
+  __device__ static T sum(V v) { return v; }
+};
 
 template <typename T, int RPL, bool CL, bool SMEM>
 __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq, T* __restrict__ R,
                                                    int64_t ldr, int64_t M, int bk, int rpc,
                                                    int rpc_pad, double tau2, T* gpart,
                                                    unsigned* bar, int* status, int col0) {
+  constexpr int VW = (SMEM && sizeof(T) == 4 && RPL % 2 == 0) ? 2 : 1;
+  constexpr int NV = RPL / VW;  // vectors per lane
+  using L = LaneOps<T, VW>;
+  using V = typename L::V;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int g = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -185,20 +233,20 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
   T* small = sm + (SMEM ? (size_t)bk * rpc_pad : 0);
   T* v = small;          // [2 pld]: v, and eta in the second half (first reduction)
   T* eta = v + pld;
-  T* coef = v + 2 * pld;
-  T* sv = coef + pld;
+  T* sv = v + 2 * pld;
   Ctx<T> c;
   c.base = SMEM ? sm : Q + row0;
   c.cs = SMEM ? rpc_pad : ldq;
   c.nr = nr;
   c.pld = pld;
   c.gpart = gpart;
-  c.red = sv + pld;
+  c.red = sv + 2 * pld;
   c.lpart = c.red + (CL ? 0 : 8 * 2 * pld);
   c.bar = bar;
   c.status = status;
   c.target = 0;
   int step = 0;
+  auto ok_row = [&](int r) { return SMEM ? true : (r < nr); };
 
   if (SMEM)
     for (int a = 0; a < bk; ++a)
@@ -206,32 +254,31 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
         sm[(size_t)a * rpc_pad + r] = (r < nr) ? Q[row0 + r + a * ldq] : T(0);
   __syncthreads();
 
-  T q[RPL], pn[RPL];
+  V q[NV], pn[NV];
   // step 0: v_a = p_a^T p_0 and eta_a = p_a^T p_a
   {
     const T* p0 = c.base;
 #pragma unroll
-    for (int i = 0; i < RPL; ++i) {
-      const int r = lane + 32 * i;
-      pn[i] = row_ok<T, RPL, SMEM>(r, nr) ? p0[r] : T(0);
+    for (int i = 0; i < NV; ++i) {
+      const int r = L::row(i, lane);
+      pn[i] = ok_row(r) ? L::ld(p0 + r) : L::zero();
     }
     for (int a = warp; a < bk; a += kNW) {
       const T* pa = c.base + a * c.cs;
-      T d0 = T(0), d1 = T(0);
+      V d0 = L::zero(), d1 = L::zero();
 #pragma unroll
-      for (int i = 0; i < RPL; ++i) {
-        const int r = lane + 32 * i;
-        if (row_ok<T, RPL, SMEM>(r, nr)) {
-          const T x = pa[r];
-          d0 += x * pn[i];
-          d1 += x * x;
+      for (int i = 0; i < NV; ++i) {
+        const int r = L::row(i, lane);
+        if (ok_row(r)) {
+          const V x = L::ld(pa + r);
+          d0 = L::fma(x, pn[i], d0);
+          d1 = L::fma(x, x, d1);
         }
       }
-      d0 = warp_sum(d0);
-      d1 = warp_sum(d1);
+      T s0 = warp_sum(L::sum(d0)), s1 = warp_sum(L::sum(d1));
       if (lane == 0) {
-        put_partial<T, CL>(c, a, d0, step);
-        put_partial<T, CL>(c, pld + a, d1, step);
+        put_partial<T, CL>(c, a, s0, step);
+        put_partial<T, CL>(c, pld + a, s1, step);
       }
     }
     if (!sync_reduce<T, CL>(c, 0, 2 * pld, v, step++, 1)) return;
@@ -242,20 +289,20 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
       // ICGS: one more projection of p_j on the computed columns 0 .. j-1
       const T* pj = c.base + j * c.cs;
 #pragma unroll
-      for (int i = 0; i < RPL; ++i) {
-        const int r = lane + 32 * i;
-        pn[i] = row_ok<T, RPL, SMEM>(r, nr) ? pj[r] : T(0);
+      for (int i = 0; i < NV; ++i) {
+        const int r = L::row(i, lane);
+        pn[i] = ok_row(r) ? L::ld(pj + r) : L::zero();
       }
       for (int a = warp; a < j; a += kNW) {
         const T* pa = c.base + a * c.cs;
-        T d = T(0);
+        V d = L::zero();
 #pragma unroll
-        for (int i = 0; i < RPL; ++i) {
-          const int r = lane + 32 * i;
-          if (row_ok<T, RPL, SMEM>(r, nr)) d += pa[r] * pn[i];
+        for (int i = 0; i < NV; ++i) {
+          const int r = L::row(i, lane);
+          if (ok_row(r)) d = L::fma(L::ld(pa + r), pn[i], d);
         }
-        d = warp_sum(d);
-        if (lane == 0) put_partial<T, CL>(c, a, d, step);
+        const T s0 = warp_sum(L::sum(d));
+        if (lane == 0) put_partial<T, CL>(c, a, s0, step);
       }
       if (!sync_reduce<T, CL>(c, 0, j, sv, step++, 3)) return;
       T* pjw = c.base + j * c.cs;
@@ -270,20 +317,20 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
       }
       __syncthreads();
 #pragma unroll
-      for (int i = 0; i < RPL; ++i) {
-        const int r = lane + 32 * i;
-        pn[i] = row_ok<T, RPL, SMEM>(r, nr) ? pjw[r] : T(0);
+      for (int i = 0; i < NV; ++i) {
+        const int r = L::row(i, lane);
+        pn[i] = ok_row(r) ? L::ld(pjw + r) : L::zero();
       }
       for (int a = j + warp; a < bk; a += kNW) {
         const T* pa = c.base + a * c.cs;
-        T d = T(0);
+        V d = L::zero();
 #pragma unroll
-        for (int i = 0; i < RPL; ++i) {
-          const int r = lane + 32 * i;
-          if (row_ok<T, RPL, SMEM>(r, nr)) d += pa[r] * pn[i];
+        for (int i = 0; i < NV; ++i) {
+          const int r = L::row(i, lane);
+          if (ok_row(r)) d = L::fma(L::ld(pa + r), pn[i], d);
         }
-        d = warp_sum(d);
-        if (lane == 0) put_partial<T, CL>(c, a, d, step);
+        const T s0 = warp_sum(L::sum(d));
+        if (lane == 0) put_partial<T, CL>(c, a, s0, step);
       }
       if (!sync_reduce<T, CL>(c, j, bk, v, step++, 4)) return;
     }
@@ -295,81 +342,109 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
     }
     const T rjj = sqrt(v0);
     const T inv = T(1) / rjj;
-    for (int a = j + 1 + tid; a < bk; a += kNT) {
-      const T ca = v[a] * inv;
-      coef[a] = ca;
-      if (g == 0) R[j + a * ldr] = ca;
-    }
-    if (g == 0 && tid == 0) R[j + j * ldr] = rjj;
-    __syncthreads();
-    // q_j (registers), updated p_{j+1} (registers), then update + next products
-    const T* pj = c.base + j * c.cs;
     const bool nxt = (j + 1 < bk);
-    const T cn = nxt ? coef[j + 1] : T(0);
+    const T cn = nxt ? v[j + 1] * inv : T(0);
+    if (g == 0 && tid == 0) R[j + j * ldr] = rjj;
+    // q_j and the updated p_{j+1} live in registers; warp 0 stores both to shared memory
+    // right after the next barrier, when no warp of this CTA still reads columns j, j+1
+    const T* pj = c.base + j * c.cs;
     const T* pj1 = c.base + (j + 1) * c.cs;
+    const V ncn = L::splat(-cn);
 #pragma unroll
-    for (int i = 0; i < RPL; ++i) {
-      const int r = lane + 32 * i;
-      const bool ok = row_ok<T, RPL, SMEM>(r, nr);
-      q[i] = ok ? pj[r] * inv : T(0);
-      pn[i] = (nxt && ok) ? pj1[r] - q[i] * cn : T(0);
+    for (int i = 0; i < NV; ++i) {
+      const int r = L::row(i, lane);
+      const bool ok = ok_row(r);
+      q[i] = ok ? L::scale(L::ld(pj + r), inv) : L::zero();
+      pn[i] = (nxt && ok) ? L::fma(q[i], ncn, L::ld(pj1 + r)) : L::zero();
     }
-    __syncthreads();
-    // two columns per iteration so that their loads and shuffle reductions overlap
+    // update columns a >= j+2 and form p_a^T p_{j+1}; column j+1 contributes its norm
     int a = j + 1 + warp;
     for (; a + kNW < bk; a += 2 * kNW) {
+      const int b2 = a + kNW;
+      const T ca = v[a] * inv, cb = v[b2] * inv;
+      if (g == 0 && lane == 0) {
+        R[j + a * ldr] = ca;
+        R[j + b2 * ldr] = cb;
+      }
       T* pa = c.base + a * c.cs;
-      T* pb = c.base + (a + kNW) * c.cs;
-      const T ca = coef[a], cb = coef[a + kNW];
-      T da = T(0), db = T(0);
+      T* pb = c.base + b2 * c.cs;
+      const V nca = L::splat(-ca), ncb = L::splat(-cb);
+      V da = L::zero(), db = L::zero();
+      const bool first = (a == j + 1);
 #pragma unroll
-      for (int i = 0; i < RPL; ++i) {
-        const int r = lane + 32 * i;
-        if (row_ok<T, RPL, SMEM>(r, nr)) {
-          const T xa = pa[r] - q[i] * ca;
-          const T xb = pb[r] - q[i] * cb;
-          pa[r] = xa;
-          pb[r] = xb;
-          da += xa * pn[i];
-          db += xb * pn[i];
+      for (int i = 0; i < NV; ++i) {
+        const int r = L::row(i, lane);
+        if (ok_row(r)) {
+          if (first) {
+            da = L::fma(pn[i], pn[i], da);
+          } else {
+            const V xa = L::fma(q[i], nca, L::ld(pa + r));
+            L::st(pa + r, xa);
+            da = L::fma(xa, pn[i], da);
+          }
+          const V xb = L::fma(q[i], ncb, L::ld(pb + r));
+          L::st(pb + r, xb);
+          db = L::fma(xb, pn[i], db);
         }
       }
+      T sa = L::sum(da), sb = L::sum(db);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        da += __shfl_xor_sync(0xffffffffu, da, o);
-        db += __shfl_xor_sync(0xffffffffu, db, o);
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
       }
       if (lane == 0) {
-        put_partial<T, CL>(c, a, da, step);
-        put_partial<T, CL>(c, a + kNW, db, step);
+        put_partial<T, CL>(c, a, sa, step);
+        put_partial<T, CL>(c, b2, sb, step);
       }
     }
     if (a < bk) {
+      const T ca = v[a] * inv;
+      if (g == 0 && lane == 0) R[j + a * ldr] = ca;
       T* pa = c.base + a * c.cs;
-      const T ca = coef[a];
-      T da = T(0);
+      const V nca = L::splat(-ca);
+      V da = L::zero();
+      const bool first = (a == j + 1);
 #pragma unroll
-      for (int i = 0; i < RPL; ++i) {
-        const int r = lane + 32 * i;
-        if (row_ok<T, RPL, SMEM>(r, nr)) {
-          const T xa = pa[r] - q[i] * ca;
-          pa[r] = xa;
-          da += xa * pn[i];
+      for (int i = 0; i < NV; ++i) {
+        const int r = L::row(i, lane);
+        if (ok_row(r)) {
+          if (first) {
+            da = L::fma(pn[i], pn[i], da);
+          } else {
+            const V xa = L::fma(q[i], nca, L::ld(pa + r));
+            L::st(pa + r, xa);
+            da = L::fma(xa, pn[i], da);
+          }
         }
       }
-      da = warp_sum(da);
-      if (lane == 0) put_partial<T, CL>(c, a, da, step);
+      const T sa = warp_sum(L::sum(da));
+      if (lane == 0) put_partial<T, CL>(c, a, sa, step);
     }
-    if (warp == 0) {
-      T* pjw = c.base + j * c.cs;
+    T* pjw = c.base + j * c.cs;
+    T* pj1w = c.base + (j + 1) * c.cs;
+    if (!nxt) {
+      __syncthreads();
+      if (warp == 0)
 #pragma unroll
-      for (int i = 0; i < RPL; ++i) {
-        const int r = lane + 32 * i;
-        if (row_ok<T, RPL, SMEM>(r, nr)) pjw[r] = q[i];
-      }
+        for (int i = 0; i < NV; ++i) {
+          const int r = L::row(i, lane);
+          if (ok_row(r)) L::st(pjw + r, q[i]);
+        }
+      break;
     }
-    if (!nxt) break;
-    if (!sync_reduce<T, CL>(c, j + 1, bk, v, step++, 2)) return;
+    auto publish = [&]() {
+      if (warp == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+          const int r = L::row(i, lane);
+          if (ok_row(r)) {
+            L::st(pjw + r, q[i]);
+            L::st(pj1w + r, pn[i]);
+          }
+        }
+    };
+    if (!sync_reduce<T, CL>(c, j + 1, bk, v, step++, 2, publish)) return;
   }
   __syncthreads();
   if (SMEM)
@@ -380,7 +455,7 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
 
 size_t small_bytes(int bk, size_t elem, bool cl) {
   const int pld = (bk + 3) / 4 * 4;
-  // v (2 pld, includes eta), coef, sv, then either red [8][2 pld] or lpart [2][2 pld]
+  // v (2 pld, includes eta), sv (2 pld), then either red [8][2 pld] or lpart [2][2 pld]
   return (size_t)(2 * pld + 2 * pld + (cl ? 4 * pld : 16 * pld)) * elem + 256;
 }
 
@@ -429,7 +504,7 @@ PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_clu
   const int cl_env = env_int("CQR_PANEL_CLUSTER", -1);
   auto fits = [&](int rpl, bool cl) {
     const int rpc = 32 * rpl;
-    return (size_t)bk * (rpc + 1) * elem + small_bytes(bk, elem, cl) + 1024 <= kSmemCap;
+    return (size_t)bk * rpc * elem + small_bytes(bk, elem, cl) + 1024 <= kSmemCap;
   };
   int best = -1;
   bool best_cl = false;
@@ -451,7 +526,7 @@ PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_clu
     p.cluster = best_cl ? 1 : 0;
     p.rpc = 32 * best;
     p.G = (int)((M + p.rpc - 1) / p.rpc);
-    p.rpc_pad = p.rpc + 1;
+    p.rpc_pad = p.rpc;
     p.smem_bytes = (size_t)bk * p.rpc_pad * elem + small_bytes(bk, elem, best_cl);
     return p;
   }
