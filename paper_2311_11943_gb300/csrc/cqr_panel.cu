@@ -174,14 +174,10 @@ __device__ __forceinline__ bool sync_reduce(Ctx<T>& c, int lo, int hi, T* out, i
 // r = 64 i + 2 lane + {0, 1} and works on them with 64-bit loads and packed f32x2 FMAs;
 // VW = 1: rows r = 32 i + lane.  With the slice in shared memory the CTA's rows are padded
 // with zeros to exactly 32 RPL, so no row guard is needed.
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-  uint64_t ra, rb, rc, rd;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
-  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
-  asm("mov.b64 %0, {%1, %2};" : "=l"(rc) : "f"(c.x), "f"(c.y));
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
-  float2 d;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+// Packed FP32 pair held in one 64-bit register (low half = even row).
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
 }
 
@@ -190,15 +186,23 @@ struct LaneOps;
 
 template <>
 struct LaneOps<float, 2> {
-  using V = float2;
+  using V = uint64_t;
   __device__ static int row(int i, int lane) { return 64 * i + 2 * lane; }
-  __device__ static V ld(const float* p) { return *reinterpret_cast<const float2*>(p); }
-  __device__ static void st(float* p, V v) { *reinterpret_cast<float2*>(p) = v; }
+  __device__ static V ld(const float* p) { return *reinterpret_cast<const unsigned long long*>(p); }
+  __device__ static void st(float* p, V v) { *reinterpret_cast<unsigned long long*>(p) = v; }
   __device__ static V fma(V a, V b, V c) { return ffma2(a, b, c); }
-  __device__ static V splat(float s) { return make_float2(s, s); }
-  __device__ static V zero() { return make_float2(0.f, 0.f); }
-  __device__ static V scale(V a, float s) { return make_float2(a.x * s, a.y * s); }
-  __device__ static float sum(V v) { return v.x + v.y; }
+  __device__ static V splat(float s) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(s));
+    return r;
+  }
+  __device__ static V zero() { return 0ull; }
+  __device__ static V scale(V a, float s) { return ffma2(a, splat(s), 0ull); }
+  __device__ static float sum(V v) {
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+    return x + y;
+  }
 };
 
 template <typename T>
