@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -159,6 +160,8 @@ struct cqr_handle_s {
   TcGemm* tc = nullptr;
   PanelPlan plan{};
   int plan_bk = -1;
+  bool reg_ok = false;
+  int reg_rpl = 0, reg_cpw = 0, reg_G = 0;
   // profile: launch counts always, event-pair device times when enabled
   bool prof_on = false;
   std::vector<ProfRec> prof_recs;
@@ -335,13 +338,24 @@ cqr_status panel_step(cqr_handle h, int t) {
     h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, true);
     if (h->plan.cluster && !panel_cluster_fits<T>(h->plan))
       h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, false);
+    h->reg_ok = false;
+    const char* env = getenv("CQR_PANEL_REG");
+    if (sizeof(T) == 4 && !(env && env[0] == '0') &&
+        plan_panel_reg(g.M, bk, &h->reg_rpl, &h->reg_cpw, &h->reg_G))
+      h->reg_ok = panel_reg_cluster_fits(h->reg_rpl, h->reg_cpw, h->reg_G);
     h->plan_bk = bk;
   }
   const PanelPlan& pp = h->plan;
   {
     ProfScope ps(h, K_PANEL, 1);
-    CK(launch_panel<T>(pp, Q + kb * g.ldq, g.ldq, R + kb + kb * g.ldr, g.ldr, g.M, bk, h->tau,
-                       ptr<T>(h->B.part), h->B.bar, h->B.status, (int)kb, h->st));
+    if (sizeof(T) == 4 && h->reg_ok) {
+      CK(launch_panel_reg(h->reg_rpl, h->reg_cpw, h->reg_G, reinterpret_cast<float*>(Q + kb * g.ldq),
+                          g.ldq, reinterpret_cast<float*>(R + kb + kb * g.ldr), g.ldr, g.M, bk, h->tau,
+                          h->B.status, (int)kb, h->st));
+    } else {
+      CK(launch_panel<T>(pp, Q + kb * g.ldq, g.ldq, R + kb + kb * g.ldr, g.ldr, g.M, bk, h->tau,
+                         ptr<T>(h->B.part), h->B.bar, h->B.status, (int)kb, h->st));
+    }
   }
   const int64_t j0 = kb + bk;
   if (j0 >= g.N) return CQR_OK;

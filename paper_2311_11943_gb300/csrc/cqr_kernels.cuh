@@ -48,6 +48,12 @@ template <typename T>
 bool panel_cluster_fits(const PanelPlan& pp);
 size_t panel_partial_bytes(int bk, size_t elem, int num_sms);
 
+// Register-resident FP32 panel in one cluster (cqr_panel_reg.cu).
+bool plan_panel_reg(int64_t M, int bk, int* rpl, int* cpw, int* G);
+bool panel_reg_cluster_fits(int rpl, int cpw, int G);
+cudaError_t launch_panel_reg(int rpl, int cpw, int G, float* Q, int64_t ldq, float* R, int64_t ldr,
+                             int64_t M, int bk, double tau, int* status, int col0, cudaStream_t st);
+
 template <typename T>
 cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t ldr, int64_t M,
                          int bk, double tau, T* part, unsigned* bar, int* status, int col0,

@@ -1,0 +1,475 @@
+// cqr_panel_reg.cu -- register-resident panel ICGS (a3) for FP32 panels that fit one
+// thread-block cluster: same algorithm and arithmetic order as cqr_panel.cu (Appendix A,
+// Algorithm CGS with the ICGS reorthogonalisation, one reduction per column), but the slice
+// of the panel owned by a CTA lives in registers instead of shared memory.
+//
+// Layout: G <= 16 CTAs (one cluster), CTA g owns rows [g rpc, (g+1) rpc), rpc = 32 RPL.
+// Warp w owns panel columns a = w + 8 k (k < CPW); lane l owns row pairs
+// 64 i + 2 l + {0, 1} (i < RPL / 2), packed in 64-bit registers for f32x2 FMAs.
+// Per column j (v_a = p_a^T p_j already reduced, identical in every CTA):
+//   q_j = p_j / r_jj and the updated p_{j+1} are formed by every warp from a shared staging
+//   copy of columns j, j+1 (double-buffered by column parity); each warp updates its own
+//   columns a > j in registers and forms p_a^T p_{j+1}; the per-lane partials of a warp's
+//   columns are combined by a butterfly over the lanes, and every CTA pushes its per-column
+//   partials into every peer's shared memory (st.shared::cluster); after the hardware
+//   cluster barrier each CTA sums the G partials locally in a fixed order.  The owners of
+//   columns j+1 and j+2 write them to the other staging buffer before the barrier.
+#include <math.h>
+
+#include "cqr_device.cuh"
+#include "cqr_kernels.cuh"
+
+namespace cqr {
+
+namespace {
+
+constexpr int kNT = 256;
+constexpr int kNW = kNT / 32;   // 8 warps
+constexpr int kMaxG = 16;
+
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void st_peer(uint32_t local_addr, uint32_t rank, float v) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(r), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2splat(float s) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(s));
+  return r;
+}
+__device__ __forceinline__ float f2sum(uint64_t v) {
+  float x, y;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+  return x + y;
+}
+
+// Butterfly over the 32 lanes of CPW per-lane values (one per owned column slot).  After it,
+// lane l holds the full 32-lane sum of slot slot_of(l).
+template <int CPW>
+__device__ __forceinline__ float butterfly(float (&x)[CPW], int lane) {
+  float y[CPW];
+#pragma unroll
+  for (int k = 0; k < CPW; ++k) y[k] = x[k];
+  int n = CPW;
+  int off = 16;
+#pragma unroll
+  for (int round = 0; round < 4; ++round) {
+    if ((CPW >> round) > 1) {
+      const int h = (CPW >> round) / 2;
+      const bool upper = (lane & off) != 0;
+#pragma unroll
+      for (int k = 0; k < CPW / 2; ++k) {
+        if (k < h) {
+          const float mine = upper ? y[k + h] : y[k];
+          const float other = upper ? y[k] : y[k + h];
+          y[k] = mine + __shfl_xor_sync(0xffffffffu, other, off);
+        }
+      }
+      n = h;
+      off >>= 1;
+    }
+  }
+  (void)n;
+  float s = y[0];
+  for (; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
+template <int CPW>
+__device__ __forceinline__ int slot_of(int lane) {
+  // bit 4 of the lane picks the upper half of the slots in the first round, bit 3 in the
+  // second, and so on (as many rounds as log2 CPW)
+  int s = 0, h = CPW, off = 16;
+#pragma unroll
+  for (int round = 0; round < 4; ++round) {
+    if ((CPW >> round) > 1) {
+      h >>= 1;
+      if (lane & off) s += h;
+      off >>= 1;
+    }
+  }
+  return s;
+}
+
+template <int CPW>
+__device__ __forceinline__ int lanes_per_slot() {
+  return 32 / CPW;
+}
+
+template <int RPL, int CPW>
+__global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int64_t ldq,
+                                                       float* __restrict__ R, int64_t ldr,
+                                                       int64_t M, int bk, double tau2, int* status,
+                                                       int col0) {
+  constexpr int NP = RPL / 2;            // row pairs per lane
+  constexpr int RPC = 32 * RPL;          // rows per CTA
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* stage = reinterpret_cast<float*>(smraw);       // [2 parity][2 columns][RPC]
+  float* pin = stage + 4 * RPC;                          // [2 parity][kMaxG][2 * 256]
+  float* v = pin + 2 * kMaxG * 512;                      // [512]: v, eta in [256..)
+  float* sv = v + 512;                                   // [256]
+  float* racc = sv + 256;                                // [kNW][RPC] reorth contributions
+  const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int64_t row0 = (int64_t)g * RPC;
+  const int nr = (int)((M - row0) < RPC ? (M - row0) : RPC);
+  float* eta = v + 256;
+  constexpr int GS = CPW < 8 ? CPW : 8;  // slots reduced per butterfly
+  constexpr int NG = CPW / GS;
+  const int slot = slot_of<GS>(lane);
+  const int lps = lanes_per_slot<GS>();
+  const int sub = lane % lps;            // which subset of peers this lane pushes to
+
+  uint64_t P[CPW][NP];
+  // load the slice (zero rows past M)
+#pragma unroll
+  for (int k = 0; k < CPW; ++k) {
+    const int a = warp + kNW * k;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      const int r = 64 * i + 2 * lane;
+      float x0 = 0.f, x1 = 0.f;
+      if (a < bk) {
+        if (r < nr) x0 = Q[row0 + r + a * ldq];
+        if (r + 1 < nr) x1 = Q[row0 + r + 1 + a * ldq];
+      }
+      asm("mov.b64 %0, {%1, %2};" : "=l"(P[k][i]) : "f"(x0), "f"(x1));
+    }
+  }
+  auto owner_write = [&](int col, float* dst) {  // owner warp of `col` stores it to dst[RPC]
+    if (col < bk && warp == (col % kNW)) {
+      const int k = col / kNW;
+#pragma unroll
+      for (int kk = 0; kk < CPW; ++kk)
+        if (kk == k)
+#pragma unroll
+          for (int i = 0; i < NP; ++i)
+            *reinterpret_cast<uint64_t*>(dst + 64 * i + 2 * lane) = P[kk][i];
+    }
+  };
+  // push the warp's per-slot sums (after the butterfly) into every CTA's pin[par][g][base + a]
+  auto push = [&](float s, int par, int base, bool active_slot, int a) {
+    if (active_slot) {
+      const uint32_t local = saddr(pin + ((size_t)par * kMaxG + g) * 512 + base + a);
+      for (int peer = sub; peer < G; peer += lps) st_peer(local, peer, s);
+    }
+  };
+  auto reduce_local = [&](int par, int lo, int hi, float* out) {
+    for (int a = lo + tid; a < hi; a += kNT) {
+      float s = 0.f;
+      for (int q = 0; q < G; ++q) s += pin[((size_t)par * kMaxG + q) * 512 + a];
+      out[a] = s;
+    }
+  };
+
+  int par = 0;
+  // ---- step 0: v_a = p_a^T p_0, eta_a = p_a^T p_a
+  owner_write(0, stage);
+  __syncthreads();
+  {
+    uint64_t p0[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) p0[i] = *reinterpret_cast<const uint64_t*>(stage + 64 * i + 2 * lane);
+#pragma unroll
+    for (int gr = 0; gr < NG; ++gr) {
+      float d0[GS], d1[GS];
+#pragma unroll
+      for (int kk = 0; kk < GS; ++kk) {
+        const int k = gr * GS + kk;
+        uint64_t s0 = 0ull, s1 = 0ull;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          s0 = f2fma(P[k][i], p0[i], s0);
+          s1 = f2fma(P[k][i], P[k][i], s1);
+        }
+        d0[kk] = f2sum(s0);
+        d1[kk] = f2sum(s1);
+      }
+      const float e0 = butterfly<GS>(d0, lane), e1 = butterfly<GS>(d1, lane);
+      const int a = warp + kNW * (gr * GS + slot);
+      push(e0, par, 0, a < bk, a);
+      push(e1, par, 256, a < bk, a);
+    }
+  }
+  // columns 0 and 1 go to staging buffer 0 (column 0 is still there)
+  owner_write(1, stage + RPC);
+  cl_sync();
+  reduce_local(par, 0, bk, v);
+  reduce_local(par, 256, 256 + bk, v);
+  __syncthreads();
+  par ^= 1;
+
+  for (int j = 0; j < bk; ++j) {
+    float* st_cur = stage + (size_t)(j & 1) * 2 * RPC;   // p_j, p_{j+1}
+    float* st_nxt = stage + (size_t)((j + 1) & 1) * 2 * RPC;
+    if (j > 0 && tau2 > 0.0 && (double)v[j] < tau2 * (double)eta[j]) {
+      // ICGS reorthogonalisation of p_j against columns 0 .. j-1 (held by their owners)
+      uint64_t pj[NP];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) pj[i] = *reinterpret_cast<const uint64_t*>(st_cur + 64 * i + 2 * lane);
+#pragma unroll
+      for (int gr = 0; gr < NG; ++gr) {
+        float d[GS];
+#pragma unroll
+        for (int kk = 0; kk < GS; ++kk) {
+          uint64_t s = 0ull;
+#pragma unroll
+          for (int i = 0; i < NP; ++i) s = f2fma(P[gr * GS + kk][i], pj[i], s);
+          d[kk] = f2sum(s);
+        }
+        const float e = butterfly<GS>(d, lane);
+        const int a = warp + kNW * (gr * GS + slot);
+        push(e, par, 0, a < j, a);
+      }
+      cl_sync();
+      reduce_local(par, 0, j, sv);
+      __syncthreads();
+      par ^= 1;
+      // each warp's contribution sum_{a < j, owned} q_a s_a for its rows, then the owner sums
+      uint64_t cacc[NP];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) cacc[i] = 0ull;
+#pragma unroll
+      for (int k = 0; k < CPW; ++k) {
+        const int a = warp + kNW * k;
+        if (a < j) {
+          const uint64_t sa = f2splat(sv[a]);
+#pragma unroll
+          for (int i = 0; i < NP; ++i) cacc[i] = f2fma(P[k][i], sa, cacc[i]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NP; ++i)
+        *reinterpret_cast<uint64_t*>(racc + (size_t)warp * RPC + 64 * i + 2 * lane) = cacc[i];
+      __syncthreads();
+      if (warp == (j % kNW)) {
+        const int kj = j / kNW;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          float t0 = 0.f, t1 = 0.f;
+          for (int w = 0; w < kNW; ++w) {
+            const float2 c2 = *reinterpret_cast<const float2*>(racc + (size_t)w * RPC + 64 * i + 2 * lane);
+            t0 += c2.x;
+            t1 += c2.y;
+          }
+          uint64_t tt;
+          asm("mov.b64 %0, {%1, %2};" : "=l"(tt) : "f"(-t0), "f"(-t1));
+#pragma unroll
+          for (int kk = 0; kk < CPW; ++kk)
+            if (kk == kj) {
+              P[kk][i] = f2fma(tt, f2splat(1.f), P[kk][i]);
+              *reinterpret_cast<uint64_t*>(st_cur + 64 * i + 2 * lane) = P[kk][i];
+            }
+        }
+      }
+      if (g == 0) {
+        for (int a = tid; a < j; a += kNT) R[a + j * ldr] += sv[a];
+        if (tid == 0) atomicAdd(status + ST_REORTH, 1);
+      }
+      __syncthreads();
+      // v_a = p_a^T p_j for a >= j with the new p_j
+#pragma unroll
+      for (int i = 0; i < NP; ++i) pj[i] = *reinterpret_cast<const uint64_t*>(st_cur + 64 * i + 2 * lane);
+#pragma unroll
+      for (int gr = 0; gr < NG; ++gr) {
+        float d[GS];
+#pragma unroll
+        for (int kk = 0; kk < GS; ++kk) {
+          uint64_t s = 0ull;
+#pragma unroll
+          for (int i = 0; i < NP; ++i) s = f2fma(P[gr * GS + kk][i], pj[i], s);
+          d[kk] = f2sum(s);
+        }
+        const float e = butterfly<GS>(d, lane);
+        const int a = warp + kNW * (gr * GS + slot);
+        push(e, par, 0, a >= j && a < bk, a);
+      }
+      cl_sync();
+      reduce_local(par, j, bk, v);
+      __syncthreads();
+      par ^= 1;
+    }
+    const float v0 = v[j];
+    if (!(v0 > 0.f) || !isfinite(v0)) {
+      if (g == 0 && tid == 0) set_status(status, CQR_EBREAKDOWN, col0 + j);
+      return;  // uniform: every CTA sees the same v0; no peer accesses follow
+    }
+    const float rjj = sqrtf(v0);
+    const float inv = 1.f / rjj;
+    const bool nxt = j + 1 < bk;
+    const float cn = nxt ? v[j + 1] * inv : 0.f;
+    if (g == 0 && tid == 0) R[j + j * ldr] = rjj;
+    uint64_t q[NP], pn[NP];
+    const uint64_t sinv = f2splat(inv), ncn = f2splat(-cn);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      q[i] = f2fma(*reinterpret_cast<const uint64_t*>(st_cur + 64 * i + 2 * lane), sinv, 0ull);
+      pn[i] = nxt ? f2fma(q[i], ncn, *reinterpret_cast<const uint64_t*>(st_cur + RPC + 64 * i + 2 * lane))
+                  : 0ull;
+    }
+#pragma unroll
+    for (int gr = 0; gr < NG; ++gr) {
+      float d[GS];
+#pragma unroll
+      for (int kk = 0; kk < GS; ++kk) {
+        const int k = gr * GS + kk;
+        const int a = warp + kNW * k;
+        d[kk] = 0.f;
+        if (a == j) {
+#pragma unroll
+          for (int i = 0; i < NP; ++i) P[k][i] = q[i];
+        } else if (a > j && a < bk) {
+          const float ca = v[a] * inv;
+          if (g == 0 && lane == 0) R[j + a * ldr] = ca;
+          const uint64_t nca = f2splat(-ca);
+          uint64_t s = 0ull;
+#pragma unroll
+          for (int i = 0; i < NP; ++i) {
+            const uint64_t x = f2fma(q[i], nca, P[k][i]);
+            P[k][i] = x;
+            s = f2fma(x, pn[i], s);
+          }
+          d[kk] = f2sum(s);
+        }
+      }
+      if (nxt) {
+        const float e = butterfly<GS>(d, lane);
+        const int a = warp + kNW * (gr * GS + slot);
+        push(e, par, 0, a > j && a < bk, a);
+      }
+    }
+    if (!nxt) break;
+    owner_write(j + 1, st_nxt);
+    owner_write(j + 2, st_nxt + RPC);
+    cl_sync();
+    reduce_local(par, j + 1, bk, v);
+    __syncthreads();
+    par ^= 1;
+  }
+  // write the finished slice back
+#pragma unroll
+  for (int k = 0; k < CPW; ++k) {
+    const int a = warp + kNW * k;
+    if (a < bk)
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        const int r = 64 * i + 2 * lane;
+        float x0, x1;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(x0), "=f"(x1) : "l"(P[k][i]));
+        if (r < nr) Q[row0 + r + a * ldq] = x0;
+        if (r + 1 < nr) Q[row0 + r + 1 + a * ldq] = x1;
+      }
+  }
+}
+
+size_t reg_smem_bytes(int rpl) {
+  const size_t rpc = 32 * (size_t)rpl;
+  return (4 * rpc + 2 * kMaxG * 512 + 512 + 256 + (size_t)kNW * rpc) * sizeof(float) + 256;
+}
+
+template <int RPL, int CPW>
+const void* reg_fn() { return (const void*)k_panel_reg<RPL, CPW>; }
+
+const void* pick_reg(int rpl, int cpw) {
+#define CQR_REG_CASE(R_, C_) \
+  if (rpl == R_ && cpw == C_) return reg_fn<R_, C_>();
+  CQR_REG_CASE(4, 4) CQR_REG_CASE(4, 8) CQR_REG_CASE(4, 16)
+  CQR_REG_CASE(6, 4) CQR_REG_CASE(6, 8) CQR_REG_CASE(6, 16)
+  CQR_REG_CASE(8, 4) CQR_REG_CASE(8, 8) CQR_REG_CASE(8, 16)
+  CQR_REG_CASE(10, 4) CQR_REG_CASE(10, 8) CQR_REG_CASE(10, 16)
+  CQR_REG_CASE(12, 4) CQR_REG_CASE(12, 8)
+#undef CQR_REG_CASE
+  return nullptr;
+}
+
+}  // namespace
+
+// Register plan for an FP32 panel of M rows and bk columns: rows per lane (even) and columns
+// per warp; false when the slice does not fit one cluster's registers.
+bool plan_panel_reg(int64_t M, int bk, int* rpl_out, int* cpw_out, int* G_out) {
+  if (bk > 128) return false;
+  const int cpw = bk <= 32 ? 4 : bk <= 64 ? 8 : 16;
+  for (int rpl : {4, 6, 8, 10, 12}) {
+    if (cpw == 16 && rpl > 10) break;
+    const int64_t G = (M + 32LL * rpl - 1) / (32LL * rpl);
+    if (G <= kMaxG) {
+      *rpl_out = rpl;
+      *cpw_out = cpw;
+      *G_out = (int)G;
+      return pick_reg(rpl, cpw) != nullptr;
+    }
+  }
+  return false;
+}
+
+cudaError_t launch_panel_reg(int rpl, int cpw, int G, float* Q, int64_t ldq, float* R, int64_t ldr,
+                             int64_t M, int bk, double tau, int* status, int col0, cudaStream_t st) {
+  const void* fn = pick_reg(rpl, cpw);
+  if (!fn) return cudaErrorInvalidValue;
+  const size_t smem = reg_smem_bytes(rpl);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (G > 8) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  double tau2 = tau > 0.0 ? tau * tau : -1.0;
+  void* args[] = {&Q, &ldq, &R, &ldr, &M, &bk, &tau2, &status, &col0};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(kNT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = G;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+bool panel_reg_cluster_fits(int rpl, int cpw, int G) {
+  const void* fn = pick_reg(rpl, cpw);
+  if (!fn) return false;
+  const size_t smem = reg_smem_bytes(rpl);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return false;
+  if (G > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return false;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(kNT);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = G;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n >= 1;
+}
+
+}  // namespace cqr

@@ -316,3 +316,22 @@ def test_tc_matches_simt_fp32_closely():
     a = gpu_run(A, 4, 4, 1, 64, seed=2, dtype="f32", mma="simt")
     b = gpu_run(A, 4, 4, 1, 64, seed=2, dtype="f32", mma="3xtf32")
     assert rel(b["R"], a["R"]) < 384 * U3X * 10.0
+
+
+@pytest.mark.parametrize("shape", [(256, 256, 4, 1, 32), (640, 640, 8, 2, 128), (4096, 512, 8, 2, 64)])
+def test_register_and_shared_memory_panels_agree(shape, monkeypatch):
+    # the FP32 panel runs register-resident in one cluster when it fits, else from shared
+    # memory; both follow the same column recurrence (reorthogonalisation included)
+    m, n, p, f, b = shape
+    A = synth.gaussian(m, n, 12)
+    A[:, 1::7] = A[:, 0::7][:, : A[:, 1::7].shape[1]] + 1e-4 * A[:, 1::7]  # force reorth
+    a = gpu_run(A, p, p if n % p == 0 else 4, f, b, seed=3, dtype="f32", mma="3xtf32")
+    monkeypatch.setenv("CQR_PANEL_REG", "0")
+    bb = gpu_run(A, p, p if n % p == 0 else 4, f, b, seed=3, dtype="f32", mma="3xtf32")
+    assert a["status"] == 0 and bb["status"] == 0
+    assert a["stats"]["n_reorth"] > 0
+    assert abs(a["stats"]["n_reorth"] - bb["stats"]["n_reorth"]) <= 2
+    kap = np.linalg.cond(A)
+    assert rel(a["R"], bb["R"]) < n * U3X * kap
+    ref = O.run(A, p, p if n % p == 0 else 4, f, b, seed=3)
+    assert rel(a["R"], ref["R"]) < n * U3X * kap
