@@ -10,10 +10,10 @@
 //   q_j = p_j / r_jj and the updated p_{j+1} are formed by every warp from a shared staging
 //   copy of columns j, j+1 (double-buffered by column parity); each warp updates its own
 //   columns a > j in registers and forms p_a^T p_{j+1}; the per-lane partials of a warp's
-//   columns are combined by a butterfly over the lanes, and every CTA pushes its per-column
-//   partials into every peer's shared memory (st.shared::cluster); after the hardware
-//   cluster barrier each CTA sums the G partials locally in a fixed order.  The owners of
-//   columns j+1 and j+2 write them to the other staging buffer before the barrier.
+//   columns are combined by a butterfly over the lanes into this CTA's partial vector in
+//   shared memory; after the hardware cluster barrier every CTA reads all G partial vectors
+//   (16-byte distributed-shared-memory loads) and sums them in the same fixed order.  The
+//   owners of columns j+1 and j+2 write them to the other staging buffer before the barrier.
 #include <math.h>
 
 #include "cqr_device.cuh"
@@ -36,10 +36,15 @@ __device__ __forceinline__ uint32_t saddr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ void st_peer(uint32_t local_addr, uint32_t rank, float v) {
+__device__ __forceinline__ float4 ld_peer4(uint32_t local_addr, uint32_t rank) {
   uint32_t r;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
-  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(r), "f"(v) : "memory");
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(r)
+               : "memory");
+  return v;
 }
 
 __device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
@@ -120,8 +125,9 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
   constexpr int RPC = 32 * RPL;          // rows per CTA
   extern __shared__ __align__(16) unsigned char smraw[];
   float* stage = reinterpret_cast<float*>(smraw);       // [2 parity][2 columns][RPC]
-  float* pin = stage + 4 * RPC;                          // [2 parity][kMaxG][2 * 256]
-  float* v = pin + 2 * kMaxG * 512;                      // [512]: v, eta in [256..)
+  float* lpart = stage + 4 * RPC;                        // [2 parity][512] own partials
+  float* red = lpart + 2 * 512;                          // [8][512] peer-group sums
+  float* v = red + 8 * 512;                              // [512]: v, eta in [256..)
   float* sv = v + 512;                                   // [256]
   float* racc = sv + 256;                                // [kNW][RPC] reorth contributions
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
@@ -162,17 +168,28 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
             *reinterpret_cast<uint64_t*>(dst + 64 * i + 2 * lane) = P[kk][i];
     }
   };
-  // push the warp's per-slot sums (after the butterfly) into every CTA's pin[par][g][base + a]
+  // the warp's per-slot sums (after the butterfly) into this CTA's partial vector
   auto push = [&](float s, int par, int base, bool active_slot, int a) {
-    if (active_slot) {
-      const uint32_t local = saddr(pin + ((size_t)par * kMaxG + g) * 512 + base + a);
-      for (int peer = sub; peer < G; peer += lps) st_peer(local, peer, s);
-    }
+    if (active_slot && sub == 0) lpart[par * 512 + base + a] = s;
   };
+  // out[a] (lo <= a < hi) = sum over the G CTAs of their partial vectors: thread t reads the
+  // 4-column chunk t % 32 of peers t / 32 and t / 32 + 8, then the 8 peer-group sums are added
   auto reduce_local = [&](int par, int lo, int hi, float* out) {
+    const int c0 = lo / 4, c1 = (hi + 3) / 4;
+    const int ch = c0 + (tid & 31), pg = tid >> 5;
+    if (ch < c1) {
+      const uint32_t local = saddr(lpart + par * 512 + 4 * ch);
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f), y = x;
+      if (pg < G) x = ld_peer4(local, pg);
+      if (pg + 8 < G) y = ld_peer4(local, pg + 8);
+      *reinterpret_cast<float4*>(red + pg * 512 + 4 * ch) =
+          make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+    }
+    __syncthreads();
     for (int a = lo + tid; a < hi; a += kNT) {
       float s = 0.f;
-      for (int q = 0; q < G; ++q) s += pin[((size_t)par * kMaxG + q) * 512 + a];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s += red[q * 512 + a];
       out[a] = s;
     }
   };
@@ -210,6 +227,7 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
   owner_write(1, stage + RPC);
   cl_sync();
   reduce_local(par, 0, bk, v);
+  __syncthreads();
   reduce_local(par, 256, 256 + bk, v);
   __syncthreads();
   par ^= 1;
@@ -307,7 +325,8 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
     const float v0 = v[j];
     if (!(v0 > 0.f) || !isfinite(v0)) {
       if (g == 0 && tid == 0) set_status(status, CQR_EBREAKDOWN, col0 + j);
-      return;  // uniform: every CTA sees the same v0; no peer accesses follow
+      cl_sync();  // uniform exit: no peer may still be reading this CTA's partials
+      return;
     }
     const float rjj = sqrtf(v0);
     const float inv = 1.f / rjj;
@@ -361,6 +380,7 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
     __syncthreads();
     par ^= 1;
   }
+  cl_sync();  // the last reduction's remote reads of this CTA's partials are done
   // write the finished slice back
 #pragma unroll
   for (int k = 0; k < CPW; ++k) {
@@ -379,7 +399,7 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
 
 size_t reg_smem_bytes(int rpl) {
   const size_t rpc = 32 * (size_t)rpl;
-  return (4 * rpc + 2 * kMaxG * 512 + 512 + 256 + (size_t)kNW * rpc) * sizeof(float) + 256;
+  return (4 * rpc + 2 * 512 + 8 * 512 + 512 + 256 + (size_t)kNW * rpc) * sizeof(float) + 256;
 }
 
 template <int RPL, int CPW>
