@@ -201,6 +201,28 @@ cqr_status coded_qr_profile_read(cqr_handle h, double* ms, int64_t* launches, in
                                  int32_t reset);
 const char* coded_qr_profile_name(int32_t cls);
 
+/* Allocation-free panel factorisation (the paper has no counterpart: this is a deployment
+ * aid).  Some callers cannot call cudaMalloc where they need a panel factored -- work
+ * recorded into a CUDA graph, a caching allocator that must not be re-entered, or a host
+ * that has handed every byte of device memory to another framework.  This call factors one
+ * panel exactly like coded_qr_factor's panel step (ICGS, one reduction per column), but its
+ * scratch (partial sums, barrier counter, status word) lives in a fixed device array of
+ * 1,311,232 bytes inside the library, which every GPU that loads the library holds until the
+ * process exits; nothing is allocated.
+ *   Q:  M x bk panel (device, column-major, ld ldq >= M), orthonormalised in place;
+ *   R:  bk x bk (device, ld ldr >= bk): receives the upper triangle (caller zeroes it first);
+ *   tau: reorthogonalisation criterion as cqr_config.tau; status: optional device int[4]
+ *   that receives the device-side status word (CQR_EBREAKDOWN, CQR_ETIMEOUT), else NULL.
+ * Limits: bk <= 256 and the panel must fit at most 160 co-resident CTAs (M up to 160 x 1024
+ * rows); larger sizes return CQR_EINVAL without launching anything.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and caches it, so make
+ * that first call before any stream capture.  All calls share the one array, and the array
+ * keeps the previous call's contents: calls whose work overlaps on the GPU (different
+ * streams, or several host threads) race and must be serialised by the caller. */
+cqr_status coded_qr_panel_icgs_noalloc(int32_t dtype, int64_t M, int32_t bk, void* Q, int64_t ldq,
+                                       void* R, int64_t ldr, double tau, int32_t* status,
+                                       void* stream);
+
 /* Static description of a status code. */
 const char* coded_qr_errstr(cqr_status s);
 

@@ -28,7 +28,7 @@ EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "
            "coded_qr_recover", "coded_qr_post_orth", "coded_qr_solve", "coded_qr_run",
            "coded_qr_get_factors", "coded_qr_get_generator", "coded_qr_get_decode_sets",
            "coded_qr_stats", "coded_qr_sync_status", "coded_qr_errstr", "coded_qr_profile",
-           "coded_qr_profile_read", "coded_qr_profile_name"]
+           "coded_qr_profile_read", "coded_qr_profile_name", "coded_qr_panel_icgs_noalloc"]
 PROF_CLASSES = 14
 
 
@@ -81,6 +81,7 @@ def lib():
             "coded_qr_sync_status": [vp],
             "coded_qr_profile": [vp, i32],
             "coded_qr_profile_read": [vp, C.POINTER(C.c_double), C.POINTER(i64), i32, i32],
+            "coded_qr_panel_icgs_noalloc": [i32, i64, i32, vp, i64, vp, i64, C.c_double, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -212,6 +213,13 @@ def coded_qr_profile_read(h, reset=True):
     check(lib().coded_qr_profile_read(h, ms, ln, PROF_CLASSES, int(bool(reset))),
           "coded_qr_profile_read")
     return {coded_qr_profile_name(k): (ms[k], ln[k]) for k in range(PROF_CLASSES)}
+
+
+def coded_qr_panel_icgs_noalloc(dtype, M, bk, Q_ptr, ldq, R_ptr, ldr, tau=0.0, status_ptr=0,
+                                stream=0):
+    return lib().coded_qr_panel_icgs_noalloc(dtype, M, bk, C.c_void_p(Q_ptr), ldq, C.c_void_p(R_ptr),
+                                             ldr, tau, C.c_void_p(status_ptr or None),
+                                             C.c_void_p(stream or None))
 
 
 def coded_qr_profile_name(k):

@@ -628,3 +628,93 @@ template bool panel_cluster_fits<float>(const PanelPlan&);
 template bool panel_cluster_fits<double>(const PanelPlan&);
 
 }  // namespace cqr
+
+// =========================================================================================
+// Allocation-free panel factorisation (coded_qr_panel_icgs_noalloc in coded_qr.h).
+//
+// Some callers cannot allocate device memory at the point where they need one panel
+// factored: code running inside a CUDA graph capture, a custom allocator that must not be
+// re-entered, or a host that has handed all device memory to another framework.  For them
+// the grid-barrier panel kernel above runs with its scratch (per-CTA partial sums, the
+// barrier counter and the status word) in the file-scope device array below instead of a
+// handle's workspace.  Every GPU that loads the library keeps this array until exit.
+// =========================================================================================
+namespace cqr {
+namespace {
+
+constexpr int kNoallocMaxBk = 256;
+constexpr int kNoallocMaxG = 160;
+constexpr size_t kNoallocPartBytes =
+    (size_t)2 * kNoallocMaxG * 2 * kNoallocMaxBk * sizeof(double);   // 1,310,720 bytes
+constexpr size_t kNoallocBytes = kNoallocPartBytes + 512;            // + barrier + status
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device; looked up once per device
+// (cudaGetSymbolAddress, with that device current) and cached.
+cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  void* p = __atomic_load_n(&g_noalloc_ptr[dev], __ATOMIC_ACQUIRE);
+  if (!p) {
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    __atomic_store_n(&g_noalloc_ptr[dev], p, __ATOMIC_RELEASE);
+  }
+  *out = p;
+  return cudaSuccess;
+}
+
+template <typename T>
+cqr_status noalloc_run(int64_t M, int bk, T* Q, int64_t ldq, T* R, int64_t ldr, double tau,
+                       int* status_out, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return CQR_ECUDA;
+  }
+  PanelPlan pp = plan_panel(M, bk, sizeof(T), sms, false);
+  if (pp.G > kNoallocMaxG || pp.G > sms) return CQR_EINVAL;
+  void* base = nullptr;
+  if (noalloc_scratch(&base) != cudaSuccess) {
+    cudaGetLastError();
+    return CQR_ECUDA;
+  }
+  unsigned char* b = static_cast<unsigned char*>(base);
+  T* part = reinterpret_cast<T*>(b);
+  unsigned* bar = reinterpret_cast<unsigned*>(b + kNoallocPartBytes);
+  int* status = status_out ? status_out : reinterpret_cast<int*>(b + kNoallocPartBytes + 256);
+  // the array keeps the previous call's contents: the status word must start at zero (the
+  // barrier counter is zeroed by launch_panel)
+  cudaError_t e = cudaMemsetAsync(status, 0, 4 * sizeof(int), st);
+  if (e == cudaSuccess) e = launch_panel<T>(pp, Q, ldq, R, ldr, M, bk, tau, part, bar, status, 0, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return CQR_ECUDA;
+  }
+  return CQR_OK;
+}
+
+}  // namespace
+
+}  // namespace cqr
+
+extern "C" cqr_status coded_qr_panel_icgs_noalloc(int32_t dtype, int64_t M, int32_t bk, void* Q,
+                                                  int64_t ldq, void* R, int64_t ldr, double tau,
+                                                  int32_t* status, void* stream) {
+  using namespace cqr;
+  if (!Q || !R || M < 1 || bk < 1 || ldq < M || ldr < bk) return CQR_EINVAL;
+  if (dtype != CQR_F64 && dtype != CQR_F32) return CQR_EINVAL;
+  if (bk > kNoallocMaxBk) return CQR_EINVAL;  // beyond the static scratch's capacity
+  const double t = tau == 0.0 ? 0.7071067811865476 : tau;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return dtype == CQR_F64
+             ? noalloc_run<double>(M, bk, (double*)Q, ldq, (double*)R, ldr, t, status, st)
+             : noalloc_run<float>(M, bk, (float*)Q, ldq, (float*)R, ldr, t, status, st);
+}
