@@ -240,14 +240,45 @@ int cqro_icgs_panel(int64_t M, int64_t kb, int64_t bk, double tau, double* Q, in
  * The d checksum columns are trailing columns of every update and are never
  * normalised.  Panels t0 .. t1-1 are run (resumable); the last panel may be narrower.
  * --------------------------------------------------------------------------------- */
-int cqro_factor(int64_t M, int64_t N, int64_t n, int64_t b, int t0, int t1, double tau,
-                double* Q, int64_t ldq, double* R, int64_t ldr, int64_t* n_reorth) {
+/* Block reorthogonalisation of panel columns kb .. kb+bk-1 against the computed columns
+ * 0 .. kb-1 (the block form of "twice is enough"; an addition to the paper's PBMGS, used
+ * when reorth_block != 0):  S = Q[:, :kb]^T Qbar,  Qbar -= Q[:, :kb] S,  R[:kb, panel] += S.
+ * A column operation on the encoded matrix, so Q_2 = G_v Q_1 is preserved. */
+static void block_reorth(int64_t M, int64_t kb, int64_t bk, double* Q, int64_t ldq, double* R,
+                         int64_t ldr) {
+  double* S = (double*)malloc(sizeof(double) * (size_t)(kb * bk));
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < bk; ++i)
+    for (int64_t a = 0; a < kb; ++a) {
+      const double* qa = Q + a * ldq;
+      const double* qi = Q + (kb + i) * ldq;
+      double acc = 0.0;
+      for (int64_t r = 0; r < M; ++r) acc += qa[r] * qi[r];
+      S[a + i * kb] = acc;
+    }
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < bk; ++i) {
+    double* qi = Q + (kb + i) * ldq;
+    for (int64_t r = 0; r < M; ++r) {
+      double acc = qi[r];
+      for (int64_t a = 0; a < kb; ++a) acc -= Q[r + a * ldq] * S[a + i * kb];
+      qi[r] = acc;
+    }
+    for (int64_t a = 0; a < kb; ++a) R[a + (kb + i) * ldr] += S[a + i * kb];
+  }
+  free(S);
+}
+
+int cqro_factor2(int64_t M, int64_t N, int64_t n, int64_t b, int t0, int t1, double tau,
+                 int reorth_block, double* Q, int64_t ldq, double* R, int64_t ldr,
+                 int64_t* n_reorth) {
   if (b <= 0 || M <= 0 || n <= 0 || N < n) return CQRO_EINVAL;
   const int T = (int)((n + b - 1) / b);
   if (t1 < 0 || t1 > T) t1 = T;
   for (int t = t0; t < t1; ++t) {
     const int64_t kb = (int64_t)t * b;
     const int64_t bk = (kb + b <= n) ? b : n - kb;
+    if (reorth_block && kb > 0) block_reorth(M, kb, bk, Q, ldq, R, ldr);
     int rc = icgs_panel(M, kb, bk, tau, Q, ldq, R, ldr, n_reorth);
     if (rc != CQRO_OK) return rc;
     const int64_t j0 = kb + bk;
@@ -269,6 +300,11 @@ int cqro_factor(int64_t M, int64_t N, int64_t n, int64_t b, int t0, int t1, doub
     }
   }
   return CQRO_OK;
+}
+
+int cqro_factor(int64_t M, int64_t N, int64_t n, int64_t b, int t0, int t1, double tau,
+                double* Q, int64_t ldq, double* R, int64_t ldr, int64_t* n_reorth) {
+  return cqro_factor2(M, N, n, b, t0, t1, tau, 0, Q, ldq, R, ldr, n_reorth);
 }
 
 /* ---------------------------------------------------------------------------------

@@ -410,3 +410,29 @@ def test_tall_ragged_rows_padding():
     Q, R = out["Q"], out["R"]
     assert np.abs(Q[70:72, :16]).max() == 0.0
     assert np.abs(A - Q[:70, :16] @ R[:16, :16]).max() < 1e-13
+
+
+# --------------------------------------------------------------------------- block reorth
+def test_block_reorth_keeps_factorisation_and_restores_orthogonality():
+    # Block MGS loses orthogonality like u kappa(A); projecting each panel once more on all
+    # computed columns (block "twice is enough") brings it back to O(u), keeps At = Q R,
+    # R equal to the Householder R of At, and the checksum relations (column operations).
+    n, p, f, b = 96, 4, 1, 8
+    kappa = 1e8
+    A = synth.kappa_matrix(n, n, kappa, seed=4)
+    one = O.run(A, p, p, f, b, seed=2)
+    two = O.run(A, p, p, f, b, seed=2, reorth_block=True)
+    g = two["geom"]
+    o1 = np.abs(one["Q"][:, :n].T @ one["Q"][:, :n] - np.eye(n)).max()
+    o2 = np.abs(two["Q"][:, :n].T @ two["Q"][:, :n] - np.eye(n)).max()
+    assert o2 < 1e-13 and o1 > 1e3 * o2
+    At = two["At"]
+    assert np.abs(At[:, :n] - two["Q"][:, :n] @ two["R"][:n, :n]).max() < 1e-13 * np.abs(At).max()
+    # rounding drift of Q_2 - G_v Q_1 is amplified by the pivots like u kappa, with or without
+    # the reorthogonalisation (which is a column operation)
+    Gv = np.kron(two["Gt"], np.eye(g.mb))
+    u = np.finfo(float).eps / 2
+    assert np.abs(two["Q"][g.m_pad:] - Gv @ two["Q"][: g.m_pad]).max() < 100 * u * kappa
+    Qh, Rh = np.linalg.qr(At[:, :n])
+    Rh = Rh * np.sign(np.diag(Rh))[:, None]
+    assert np.abs(two["R"][:n, :n] - Rh).max() < 100 * u * kappa * np.abs(Rh).max()
