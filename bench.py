@@ -49,12 +49,12 @@ def coded_flops(m, n, p_r, p_c, f, b, protect_r=True):
     return 2.0 * (mb * p_r + c) * n * (n + 2 * d)
 
 
-def workload_name(cfg, mode):
+def workload_name(cfg, mode, reorth_block=True):
     k = ("kappa=%g" % cfg["kappa"]) if cfg["kappa"] else "N(0,1)"
     return ("coded PBMGS/ICGS %dx%d %s, grid %dx%d, f=%d, b=%d, %d erasure(s) at %d seeded "
-            "panel(s), %s" % (cfg["m"], cfg["n"], k, cfg["p_r"], cfg["p_c"], cfg["f"], cfg["b"],
-                              cfg["erasure_panels"] * cfg["per_panel"], cfg["erasure_panels"],
-                              mode))
+            "panel(s), %s%s" % (cfg["m"], cfg["n"], k, cfg["p_r"], cfg["p_c"], cfg["f"], cfg["b"],
+                                cfg["erasure_panels"] * cfg["per_panel"], cfg["erasure_panels"],
+                                mode, ", block reorthogonalisation" if reorth_block else ""))
 
 
 def make_inputs(cfg, torch=None, device=None):
@@ -284,7 +284,9 @@ def run_ours(args, cfg):
             raise RuntimeError("device status %d (%s)" % (st, B.errstr(st)))
         return times, prof
 
-    q = B.CodedQR(m, n, p_r, p_c, f, b, dtype=dtype, mma=mma, seed=cfg["seed"], stream=stream)
+    rb = not args.no_reorth_block
+    q = B.CodedQR(m, n, p_r, p_c, f, b, dtype=dtype, mma=mma, seed=cfg["seed"], stream=stream,
+                  reorth_block=rb)
     clocks = ClockSampler(local)
     clocks.start()
     t_coded, prof = timed(q, True, args.steps, args.warmup, profile=True)
@@ -292,7 +294,8 @@ def run_ours(args, cfg):
     stats = q.stats()
 
     # uncoded GPU QR of the same matrix (f = 0, no checksums, no erasures)
-    q0 = B.CodedQR(m, n, p_r, p_c, 0, b, dtype=dtype, mma=mma, seed=cfg["seed"], stream=stream)
+    q0 = B.CodedQR(m, n, p_r, p_c, 0, b, dtype=dtype, mma=mma, seed=cfg["seed"], stream=stream,
+                   reorth_block=rb)
     t_unc, _ = timed(q0, False, args.steps, max(1, args.warmup))
     q0.close()
 
@@ -410,9 +413,9 @@ def run_ours(args, cfg):
             "dtype": {"f64": "f64", "f32": "f32", "tf32": "f32 storage, tf32 tensor-core GEMMs",
                       "3xtf32": "f32 storage, 3xtf32 tensor-core GEMMs"}[args.mode],
             "data": "synthetic (seeded U diag(sigma) V^T / N(0,1), generated on the host)",
-            "config": {"workload": workload_name(cfg, args.mode), "m": m, "n": n, "p_r": p_r,
+            "config": {"workload": workload_name(cfg, args.mode, rb), "m": m, "n": n, "p_r": p_r,
                        "p_c": p_c, "f": f, "b": b, "kappa": cfg["kappa"],
-                       "erasures": [list(p) for p in plan],
+                       "erasures": [list(p) for p in plan], "reorth_block": rb,
                        "l2": "L2 flushed between timed steps (256 MB write outside the events)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "coded_flops_per_step": F,
@@ -450,6 +453,8 @@ def main():
                     choices=sorted(MODES))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-reorth-block", action="store_true",
+                    help="skip the block reorthogonalisation pass (faster, orthogonality ~ u kappa)")
     args = ap.parse_args()
     cfg = CONFIGS[args.config]
     if args.impl == "reference":

@@ -78,7 +78,9 @@ typedef struct {
   int32_t protect_r;   /* 1: horizontal checksums protect R (Eq. (encoding)); 0: Q only */
   int32_t gdist;       /* distribution of V~ and G~_h: CQR_G_UNIF01 (paper) | CQR_G_NORMAL */
   int32_t nrhs_max;    /* largest right-hand-side count for post_orth / solve (>= 1) */
-  int32_t reserved;
+  int32_t reorth_block; /* 1: before each panel's ICGS, project the panel once more on all
+                           computed columns (block "twice is enough"; an addition to the
+                           paper's PBMGS that keeps Q_2 = G_v Q_1); 0: off */
   uint64_t seed;       /* seed of the generator's SplitMix64 stream */
   double tau;          /* ICGS criterion: reorthogonalise column j when its norm fell below
                           tau times its norm at the panel start.  0 selects 1/sqrt(2);
@@ -195,7 +197,7 @@ cqr_status coded_qr_sync_status(cqr_handle h);
  * synchronises the stream and fills (host) ms[k] (device milliseconds) and launches[k]
  * for the first cap classes (CQR_PROF_CLASSES in total) since the last reset; reset != 0
  * clears the accumulators.  coded_qr_profile_name gives the class name (NULL past the end). */
-#define CQR_PROF_CLASSES 14
+#define CQR_PROF_CLASSES 15
 cqr_status coded_qr_profile(cqr_handle h, int32_t enable);
 cqr_status coded_qr_profile_read(cqr_handle h, double* ms, int64_t* launches, int32_t cap,
                                  int32_t reset);

@@ -29,14 +29,14 @@ EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "
            "coded_qr_get_factors", "coded_qr_get_generator", "coded_qr_get_decode_sets",
            "coded_qr_stats", "coded_qr_sync_status", "coded_qr_errstr", "coded_qr_profile",
            "coded_qr_profile_read", "coded_qr_profile_name", "coded_qr_panel_icgs_noalloc"]
-PROF_CLASSES = 14
+PROF_CLASSES = 15
 
 
 class Config(C.Structure):
     _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("p_r", C.c_int32), ("p_c", C.c_int32),
                 ("f", C.c_int32), ("b", C.c_int32), ("dtype", C.c_int32), ("mma", C.c_int32),
                 ("protect_r", C.c_int32), ("gdist", C.c_int32), ("nrhs_max", C.c_int32),
-                ("reserved", C.c_int32), ("seed", C.c_uint64), ("tau", C.c_double),
+                ("reorth_block", C.c_int32), ("seed", C.c_uint64), ("tau", C.c_double),
                 ("stream", C.c_void_p)]
 
 
@@ -255,7 +255,8 @@ class CodedQR:
     """One coded QR problem on the current CUDA device (handle wrapper)."""
 
     def __init__(self, m, n, p_r, p_c, f, b, dtype="f64", mma="simt", protect_r=True,
-                 gdist=CQR_G_UNIF01, nrhs_max=1, seed=1, tau=0.0, stream=None, workspace=None):
+                 gdist=CQR_G_UNIF01, nrhs_max=1, seed=1, tau=0.0, stream=None, workspace=None,
+                 reorth_block=False):
         import torch
         self.torch = torch
         self.tdtype = torch.float64 if dtype in ("f64", "float64") else torch.float32
@@ -266,6 +267,7 @@ class CodedQR:
         cfg.protect_r = int(bool(protect_r))
         cfg.gdist = gdist
         cfg.nrhs_max = nrhs_max
+        cfg.reorth_block = int(bool(reorth_block))
         cfg.seed = seed
         cfg.tau = tau
         if stream is None:

@@ -113,7 +113,9 @@ Layout make_layout(const cqr_config* c, const Geo& g, int num_sms) {
   L.yw = take((size_t)g.m_pad * nrhs * s);
   L.xw = take((size_t)(g.m + g.N) * nrhs * s);
   L.plans = take(sizeof(DecodePlan) * (size_t)(g.grid_cols + g.p_c + c->f + 2));
-  L.tc = take(c->dtype == CQR_F32 && c->mma != CQR_MMA_SIMT ? tc_workspace_bytes(g.M, g.N, bmax) : 0);
+  L.tc = take(c->dtype == CQR_F32 && c->mma != CQR_MMA_SIMT
+                  ? tc_workspace_bytes(g.M, g.N, g.n, bmax, c->reorth_block != 0)
+                  : 0);
   L.total = off;
   return L;
 }
@@ -123,12 +125,13 @@ Layout make_layout(const cqr_config* c, const Geo& g, int num_sms) {
 // Kernel classes of the per-launch-site profile (coded_qr_profile_read).
 enum KClass {
   K_GENERATOR = 0, K_ENCODE, K_PANEL, K_GEMM_RBAR, K_SPLITK_REDUCE, K_GEMM_UPDATE, K_POISON,
-  K_DECODE, K_POST_ORTH, K_SOLVE_GEMV, K_TRSV, K_TC_RBAR, K_TC_UPDATE, K_TC_SPLIT, K_COUNT
+  K_DECODE, K_POST_ORTH, K_SOLVE_GEMV, K_TRSV, K_TC_RBAR, K_TC_UPDATE, K_TC_SPLIT,
+  K_BLOCK_REORTH, K_COUNT
 };
 static const char* kClassNames[K_COUNT] = {
     "generator", "encode", "panel_icgs", "gemm_rbar_simt", "splitk_reduce", "gemm_update_simt",
     "erasure_poison", "decode", "post_orth", "solve_gemv", "trsv", "tc_rbar", "tc_update",
-    "tc_split_panel"};
+    "tc_split_panel", "block_reorth"};
 
 struct ProfRec {
   int cls;
@@ -248,8 +251,9 @@ cqr_status setup(cqr_handle h) {
   CK(cudaMemsetAsync(h->B.part, 0, h->L.bar - h->L.part, h->st));
   CK(cudaMemsetAsync(h->B.status, 0, 256, h->st));
   if (h->cfg.dtype == CQR_F32 && h->cfg.mma != CQR_MMA_SIMT) {
-    h->tc = tc_create(h->cfg.mma, h->g.M, h->g.N, std::min<int64_t>(h->cfg.b, h->g.n),
-                      ptr<float>(h->B.Q), h->g.ldq, h->B.Pt, h->B.tc, h->num_sms);
+    h->tc = tc_create(h->cfg.mma, h->g.M, h->g.N, h->g.n, std::min<int64_t>(h->cfg.b, h->g.n),
+                      ptr<float>(h->B.Q), h->g.ldq, h->B.tc, h->num_sms, h->cfg.reorth_block != 0,
+                      h->st);
     if (!h->tc) return CQR_ECUDA;
     tc_set_status(h->tc, h->B.status);
   }
@@ -334,6 +338,22 @@ cqr_status panel_step(cqr_handle h, int t) {
   T* Q = ptr<T>(h->B.Q);
   T* R = ptr<T>(h->B.R);
   const bool tc = h->tc != nullptr;
+  if (h->cfg.reorth_block && kb > 0) {
+    // block reorthogonalisation: S = Q[:, :kb]^T Qbar, Qbar -= Q[:, :kb] S, R[:kb, panel] += S
+    if (tc) {
+      ProfScope ps(h, K_BLOCK_REORTH, 4);
+      CK(tc_block_reorth(h->tc, kb, bk, ptr<float>(h->B.R), g.ldr, h->st));
+    } else {
+      ProfScope ps(h, K_BLOCK_REORTH, 3);
+      const int sp = choose_splits((int)kb, bk, g.M, h->num_sms);
+      CK(launch_gemm_tn_splitk<T>(Q, g.ldq, Q + kb * g.ldq, g.ldq, g.M, (int)kb, bk, sp,
+                                  ptr<T>(h->B.P), h->st));
+      CK(launch_splitk_reduce<T>(ptr<T>(h->B.P), sp, (int)kb, bk, R + kb * g.ldr, g.ldr,
+                                 ptr<T>(h->B.Rb), h->st, 1));
+      CK(launch_gemm_nn_sub<T>(Q, g.ldq, ptr<T>(h->B.Rb), kb, Q + kb * g.ldq, g.ldq, g.M, (int)kb,
+                               bk, h->st));
+    }
+  }
   if (bk != h->plan_bk) {
     h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, true);
     if (h->plan.cluster && !panel_cluster_fits<T>(h->plan))
@@ -363,7 +383,7 @@ cqr_status panel_step(cqr_handle h, int t) {
   if (tc) {
     {
       ProfScope ps(h, K_TC_SPLIT, 1);
-      CK(tc_split_panel(h->tc, kb, bk, h->st));
+      CK(tc_split_panel(h->tc, kb, bk, true, h->st));
     }
     {
       ProfScope ps(h, K_TC_RBAR, 1);
@@ -468,6 +488,10 @@ cqr_status recover_t(cqr_handle h, int32_t* n_recovered) {
     for (int a = 0; a < p.f1; ++a) h->sets.push_back(p.C_use[a]);
   }
   (void)nq;
+  if (h->tc && tc_has_block_reorth(h->tc) && !plans.empty()) {
+    // the row-major copy of the computed columns is part of the nodes' state: rebuild it
+    CK(tc_refresh_rows(h->tc, std::min<int64_t>((int64_t)h->next_panel * g.b, g.n), h->st));
+  }
   std::fill(h->mask.begin(), h->mask.end(), 0);
   h->pending = false;
   h->n_recovered += nrec;

@@ -193,27 +193,32 @@ cudaError_t launch_gemm_tn_splitk(const T* A, int64_t lda, const T* B, int64_t l
   return cudaGetLastError();
 }
 
+// Sum the split partials in a fixed order; store (accumulate = 0) or add (accumulate = 1)
+// into R, and store into the compact operand Rb.
 template <typename T>
 __global__ void k_splitk_reduce(const T* __restrict__ P, int splits, int bk, int64_t w,
-                                T* __restrict__ R, int64_t ldr, T* __restrict__ Rb) {
+                                T* __restrict__ R, int64_t ldr, T* __restrict__ Rb, int accumulate) {
   const int64_t total = (int64_t)bk * w;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     T s = T(0);
     for (int sp = 0; sp < splits; ++sp) s += P[(size_t)sp * total + idx];
     const int64_t i = idx % bk, j = idx / bk;
-    R[i + j * ldr] = s;
+    if (accumulate)
+      R[i + j * ldr] += s;
+    else
+      R[i + j * ldr] = s;
     Rb[idx] = s;
   }
 }
 
 template <typename T>
 cudaError_t launch_splitk_reduce(const T* P, int splits, int bk, int64_t w, T* R, int64_t ldr,
-                                 T* Rb, cudaStream_t st) {
+                                 T* Rb, cudaStream_t st, int accumulate) {
   const int64_t total = (int64_t)bk * w;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 4096) blocks = 4096;
-  k_splitk_reduce<T><<<blocks, 256, 0, st>>>(P, splits, bk, w, R, ldr, Rb);
+  k_splitk_reduce<T><<<blocks, 256, 0, st>>>(P, splits, bk, w, R, ldr, Rb, accumulate);
   return cudaGetLastError();
 }
 
@@ -631,7 +636,7 @@ cudaError_t launch_trsv_upper(const T* R, int64_t ldr, int64_t n, T* x, int64_t 
   template cudaError_t launch_gemm_tn_splitk<T>(const T*, int64_t, const T*, int64_t, int64_t,   \
                                                 int, int64_t, int, T*, cudaStream_t);             \
   template cudaError_t launch_splitk_reduce<T>(const T*, int, int, int64_t, T*, int64_t, T*,     \
-                                               cudaStream_t);                                     \
+                                               cudaStream_t, int);                                \
   template cudaError_t launch_gemm_nn_sub<T>(const T*, int64_t, const T*, int64_t, T*, int64_t,  \
                                              int64_t, int, int64_t, cudaStream_t);                \
   template cudaError_t launch_poison<T>(const Geo&, const int*, int, T*, T*, cudaStream_t);      \

@@ -63,10 +63,10 @@ cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t l
 template <typename T>
 cudaError_t launch_gemm_tn_splitk(const T* A, int64_t lda, const T* B, int64_t ldb, int64_t K,
                                   int bk, int64_t w, int splits, T* P, cudaStream_t st);
-// Sum the split partials into R (rows kb.., columns kb+bk..) and the compact Rbar (ld = bk).
+// Sum the split partials into R (store, or add when accumulate) and the compact Rbar (ld = bk).
 template <typename T>
 cudaError_t launch_splitk_reduce(const T* P, int splits, int bk, int64_t w, T* R, int64_t ldr,
-                                 T* Rb, cudaStream_t st);
+                                 T* Rb, cudaStream_t st, int accumulate = 0);
 // C (M x w) -= A (M x bk) * B (bk x w).
 template <typename T>
 cudaError_t launch_gemm_nn_sub(const T* A, int64_t lda, const T* B, int64_t ldb, T* C,

@@ -400,11 +400,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
 // ------------------------------------------------------------------ helper kernels
 // Panel split: Qbar = Q[:, kb : kb+bk] (M x bk) -> for GEMM1's A (column-major, ld ldk):
 // Ak_hi / Ak_lo; for GEMM2's A (row-major, row stride bkp): At_hi / At_lo; columns k >= bk
-// zero-filled up to bkp (and up to 128 columns for GEMM1's M tile).
+// zero-filled up to bkp (and up to 128 columns for GEMM1's M tile).  With Qr != nullptr the
+// finished panel is also copied into the row-major planes of all computed columns
+// (Qr[r * ldrow + kb + k]), the K-major operand of the block reorthogonalisation.
 __global__ void k_split_panel(const float* __restrict__ Q, int64_t ldq, int64_t M, int bk, int bkp,
                               int ak_cols, int nplanes, float* __restrict__ Ak_hi,
                               float* __restrict__ Ak_lo, int64_t ldk, float* __restrict__ At_hi,
-                              float* __restrict__ At_lo) {
+                              float* __restrict__ At_lo, float* __restrict__ Qr_hi,
+                              float* __restrict__ Qr_lo, int64_t ldrow, int64_t kb) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
   if (r >= M) return;
@@ -418,6 +421,47 @@ __global__ void k_split_panel(const float* __restrict__ Q, int64_t ldq, int64_t 
   if (k < bkp) {
     At_hi[r * bkp + k] = h;
     if (nplanes == 2) At_lo[r * bkp + k] = l;
+  }
+  if (Qr_hi && k < bk) {
+    Qr_hi[r * ldrow + kb + k] = h;
+    if (nplanes == 2) Qr_lo[r * ldrow + kb + k] = l;
+  }
+}
+
+// Row-major planes of the computed columns 0 .. ncols-1 from Q (after a recovery).
+__global__ void k_refresh_rows(const float* __restrict__ Q, int64_t ldq, int64_t M, int64_t ncols,
+                               int nplanes, float* __restrict__ Qr_hi, float* __restrict__ Qr_lo,
+                               int64_t ldrow) {
+  const int64_t total = M * ncols;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx % M, c = idx / M;
+    const float x = Q[r + c * ldq];
+    const float h = nplanes == 2 ? tf32_hi(x) : x;
+    Qr_hi[r * ldrow + c] = h;
+    if (nplanes == 2) Qr_lo[r * ldrow + c] = x - h;
+  }
+}
+
+// Block reorthogonalisation, reduce: the GEMM1 partials hold S^T = Qbar^T Q[:, 0:kb]
+// (P[s][i + j bkp]); R[j, kb+i] += S[j][i] and S (column-major, ld ldrow, rows >= kb zero)
+// goes into the B planes of the second product.
+__global__ void k_tc_reduce_t(const float* __restrict__ P, int splits, int64_t split_stride,
+                              int64_t ldp, int bk, int64_t kb, int64_t kbp, float* __restrict__ R,
+                              int64_t ldr, int nplanes, float* __restrict__ Sh,
+                              float* __restrict__ Sl, int64_t ldrow) {
+  const int64_t total = kbp * bk;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = idx % kbp, i = idx / kbp;
+    float s = 0.f;
+    if (j < kb) {
+      for (int sp = 0; sp < splits; ++sp) s += P[sp * split_stride + i + j * ldp];
+      R[j + (kb + i) * ldr] += s;
+    }
+    const float h = nplanes == 2 ? tf32_hi(s) : s;
+    Sh[j + i * ldrow] = h;
+    if (nplanes == 2) Sl[j + i * ldrow] = s - h;
   }
 }
 
@@ -450,12 +494,16 @@ struct TcGemm {
   int64_t M, N, b, bkp, ldq, ldk;
   float* Q;
   float *Ak_hi, *Ak_lo, *At_hi, *At_lo, *Bh, *Bl, *P;
+  float *Qr_hi, *Qr_lo, *Sh, *Sl;   // block reorthogonalisation operands
+  int64_t n, ldrow;
   int num_sms;
   int* status;
   CUtensorMap tm_q_b;     // Q as GEMM1's B (box 32 x BN)
   CUtensorMap tm_ak[2];   // panel, column-major (box 32 x BM)
   CUtensorMap tm_at[2];   // panel, row-major (box 32 x BM)
   CUtensorMap tm_bh[2];   // Rbar planes (box 32 x BN)
+  CUtensorMap tm_qr[2];   // computed columns, row-major (box 32 x BM)
+  CUtensorMap tm_s[2];    // S planes, column-major ld ldrow (box 32 x BN)
 };
 
 namespace {
@@ -510,20 +558,25 @@ bool tc_available() { return true; }
 
 size_t tc_panel_bytes(int64_t, int) { return 0; }
 
-size_t tc_workspace_bytes(int64_t M, int64_t N, int b) {
+size_t tc_workspace_bytes(int64_t M, int64_t N, int64_t n, int b, int reorth_block) {
   const int64_t bkp = (b + BK - 1) / BK * BK;
   const int64_t ldk = (M + 31) / 32 * 32;
   const int64_t akc = std::max<int64_t>(bkp, (b + BM - 1) / BM * BM);
+  const int64_t ldrow = (n + 31) / 32 * 32;
   size_t s = 0;
   s += 2 * al256((size_t)ldk * akc * 4);        // Ak hi/lo
   s += 2 * al256((size_t)M * bkp * 4);          // At hi/lo
   s += 2 * al256((size_t)bkp * N * 4);          // Rbar planes
   s += al256((size_t)kMaxSplits * bkp * N * 4);  // split-K partials
+  if (reorth_block) {
+    s += 2 * al256((size_t)M * ldrow * 4);      // row-major computed columns hi/lo
+    s += 2 * al256((size_t)ldrow * akc * 4);    // S planes
+  }
   return s;
 }
 
-TcGemm* tc_create(int mode, int64_t M, int64_t N, int64_t b, float* Q, int64_t ldq, void*,
-                  void* ws, int num_sms) {
+TcGemm* tc_create(int mode, int64_t M, int64_t N, int64_t n, int64_t b, float* Q, int64_t ldq,
+                  void* ws, int num_sms, int reorth_block, cudaStream_t st) {
   TcGemm* t = new (std::nothrow) TcGemm();
   if (!t) return nullptr;
   t->mode = mode;
@@ -546,6 +599,22 @@ TcGemm* tc_create(int mode, int64_t M, int64_t N, int64_t b, float* Q, int64_t l
   t->Bh = take((size_t)t->bkp * N * 4);
   t->Bl = take((size_t)t->bkp * N * 4);
   t->P = take((size_t)kMaxSplits * t->bkp * N * 4);
+  t->n = n;
+  t->ldrow = (n + 31) / 32 * 32;
+  t->Qr_hi = t->Qr_lo = t->Sh = t->Sl = nullptr;
+  if (reorth_block) {
+    t->Qr_hi = take((size_t)M * t->ldrow * 4);
+    t->Qr_lo = take((size_t)M * t->ldrow * 4);
+    t->Sh = take((size_t)t->ldrow * akc * 4);
+    t->Sl = take((size_t)t->ldrow * akc * 4);
+    // columns not yet computed are read (times zero rows of S) when kb is not a multiple of
+    // 32: keep them finite
+    if (cudaMemsetAsync(t->Qr_hi, 0, (size_t)M * t->ldrow * 4, st) != cudaSuccess ||
+        cudaMemsetAsync(t->Qr_lo, 0, (size_t)M * t->ldrow * 4, st) != cudaSuccess) {
+      delete t;
+      return nullptr;
+    }
+  }
   bool ok = true;
   ok &= encode_2d(&t->tm_q_b, Q, (uint64_t)M, (uint64_t)N, (uint64_t)ldq * 4, BK, BN);
   ok &= encode_2d(&t->tm_ak[0], t->Ak_hi, (uint64_t)M, (uint64_t)akc, (uint64_t)t->ldk * 4, BK, BM);
@@ -554,6 +623,12 @@ TcGemm* tc_create(int mode, int64_t M, int64_t N, int64_t b, float* Q, int64_t l
   ok &= encode_2d(&t->tm_at[1], t->At_lo, (uint64_t)t->bkp, (uint64_t)M, (uint64_t)t->bkp * 4, BK, BM);
   ok &= encode_2d(&t->tm_bh[0], t->Bh, (uint64_t)t->bkp, (uint64_t)N, (uint64_t)t->bkp * 4, BK, BN);
   ok &= encode_2d(&t->tm_bh[1], t->Bl, (uint64_t)t->bkp, (uint64_t)N, (uint64_t)t->bkp * 4, BK, BN);
+  if (reorth_block) {
+    ok &= encode_2d(&t->tm_qr[0], t->Qr_hi, (uint64_t)t->ldrow, (uint64_t)M, (uint64_t)t->ldrow * 4, BK, BM);
+    ok &= encode_2d(&t->tm_qr[1], t->Qr_lo, (uint64_t)t->ldrow, (uint64_t)M, (uint64_t)t->ldrow * 4, BK, BM);
+    ok &= encode_2d(&t->tm_s[0], t->Sh, (uint64_t)t->ldrow, (uint64_t)akc, (uint64_t)t->ldrow * 4, BK, BN);
+    ok &= encode_2d(&t->tm_s[1], t->Sl, (uint64_t)t->ldrow, (uint64_t)akc, (uint64_t)t->ldrow * 4, BK, BN);
+  }
   if (!ok) {
     delete t;
     return nullptr;
@@ -575,13 +650,28 @@ int tc_splits(const TcGemm* t, int m1, int n1, int64_t* kchunk) {
 }
 }  // namespace
 
-// 1. split the panel Q[:, kb : kb+bk] into the operand planes of both GEMMs
-cudaError_t tc_split_panel(TcGemm* t, int64_t kb, int bk, cudaStream_t st) {
+// 1. split the panel Q[:, kb : kb+bk] into the operand planes of both GEMMs (and, for a
+//    finished panel with block reorthogonalisation on, into the row-major computed columns)
+cudaError_t tc_split_panel(TcGemm* t, int64_t kb, int bk, bool finished, cudaStream_t st) {
   const int bkp = (int)((bk + BK - 1) / BK * BK);
   const int m1 = (bk + BM - 1) / BM;
   dim3 grd((unsigned)((t->M + 255) / 256), (unsigned)std::max(bkp, m1 * BM));
+  float* qh = finished ? t->Qr_hi : nullptr;
   k_split_panel<<<grd, 256, 0, st>>>(t->Q + kb * t->ldq, t->ldq, t->M, bk, bkp, m1 * BM, t->nplanes,
-                                     t->Ak_hi, t->Ak_lo, t->ldk, t->At_hi, t->At_lo);
+                                     t->Ak_hi, t->Ak_lo, t->ldk, t->At_hi, t->At_lo, qh, t->Qr_lo,
+                                     t->ldrow, kb);
+  return cudaGetLastError();
+}
+
+bool tc_has_block_reorth(const TcGemm* t) { return t->Qr_hi != nullptr; }
+
+// Row-major planes of columns 0 .. ncols-1 rebuilt from Q (after a recovery changed tiles).
+cudaError_t tc_refresh_rows(TcGemm* t, int64_t ncols, cudaStream_t st) {
+  if (!t->Qr_hi || ncols <= 0) return cudaSuccess;
+  const int64_t total = t->M * ncols;
+  const int blocks = (int)std::min<int64_t>(8192, (total + 255) / 256);
+  k_refresh_rows<<<blocks, 256, 0, st>>>(t->Q, t->ldq, t->M, ncols, t->nplanes, t->Qr_hi, t->Qr_lo,
+                                         t->ldrow);
   return cudaGetLastError();
 }
 
@@ -659,6 +749,57 @@ cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_
   job.mrows = t->M;
   job.ncols = w;
   job.out = t->Q + j0 * t->ldq;
+  job.ldo = t->ldq;
+  job.split_stride = 0;
+  job.status = t->status;
+  return three ? launch_gemm<3, 2, 2>(maps, job, t->num_sms, st)
+               : launch_gemm<6, 1, 1>(maps, job, t->num_sms, st);
+}
+
+// Block reorthogonalisation of panel kb .. kb+bk-1 against columns 0 .. kb-1 (four
+// launches: split the panel, S^T = Qbar^T Q[:, 0:kb] split-K on the tensor cores, reduce
+// into R and S, Qbar -= Qrows S on the tensor cores).
+cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr, cudaStream_t st) {
+  if (!t->Qr_hi || kb <= 0) return cudaSuccess;
+  cudaError_t e = tc_split_panel(t, kb, bk, false, st);
+  if (e != cudaSuccess) return e;
+  e = tc_gemm_rbar(t, bk, 0, kb, st);  // partials of S^T (bk x kb)
+  if (e != cudaSuccess) return e;
+  const int three = t->nplanes == 2;
+  const int bkp = (int)((bk + BK - 1) / BK * BK);
+  const int m1 = (bk + BM - 1) / BM;
+  const int n1 = (int)((kb + BN - 1) / BN);
+  int64_t kchunk = 0;
+  const int splits = tc_splits(t, m1, n1, &kchunk);
+  const int64_t kbp = (kb + BK - 1) / BK * BK;
+  {
+    const int64_t total = kbp * bk;
+    const int blocks = (int)std::min<int64_t>(4096, (total + 255) / 256);
+    k_tc_reduce_t<<<blocks, 256, 0, st>>>(t->P, splits, (int64_t)bkp * kb, bkp, bk, kb, kbp, R, ldr,
+                                          t->nplanes, t->Sh, t->Sl, t->ldrow);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  TcMaps maps;
+  maps.a[0] = t->tm_qr[0];
+  maps.a[1] = t->tm_qr[1];
+  maps.b[0] = t->tm_s[0];
+  maps.b[1] = t->tm_s[1];
+  TcJob job{};
+  job.nprod = three ? 3 : 1;
+  job.split_b_smem = 0;
+  job.epi = 1;
+  job.m_tiles = (int)((t->M + BM - 1) / BM);
+  job.n_tiles = (bk + BN - 1) / BN;
+  job.splits = 1;
+  job.a_row0 = 0;
+  job.b_row0 = 0;
+  job.k0 = 0;
+  job.kchunk = kbp;
+  job.K = kbp;
+  job.mrows = t->M;
+  job.ncols = bk;
+  job.out = t->Q + kb * t->ldq;
   job.ldo = t->ldq;
   job.split_stride = 0;
   job.status = t->status;

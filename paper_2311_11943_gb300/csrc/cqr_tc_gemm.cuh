@@ -10,18 +10,24 @@ struct TcGemm;
 
 bool tc_available();
 size_t tc_panel_bytes(int64_t M, int b);
-size_t tc_workspace_bytes(int64_t M, int64_t N, int b);
-TcGemm* tc_create(int mode, int64_t M, int64_t N, int64_t b, float* Q, int64_t ldq, void* panel_buf,
-                  void* ws, int num_sms);
+size_t tc_workspace_bytes(int64_t M, int64_t N, int64_t n, int b, int reorth_block);
+TcGemm* tc_create(int mode, int64_t M, int64_t N, int64_t n, int64_t b, float* Q, int64_t ldq,
+                  void* ws, int num_sms, int reorth_block, cudaStream_t st);
 void tc_destroy(TcGemm* t);
 void tc_set_status(TcGemm* t, int* status);
 // The trailing update of one panel, in four stream-ordered launches:
 //   split the panel into operand planes; Rbar partials = Qbar^T Q[:, j0:j0+w] (split-K);
 //   reduce into R[kb:kb+bk, j0:j0+w] and GEMM2's operand; Q[:, j0:j0+w] -= Qbar Rbar.
-cudaError_t tc_split_panel(TcGemm* t, int64_t kb, int bk, cudaStream_t st);
+cudaError_t tc_split_panel(TcGemm* t, int64_t kb, int bk, bool finished, cudaStream_t st);
 cudaError_t tc_gemm_rbar(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t st);
 cudaError_t tc_reduce(TcGemm* t, int64_t kb, int bk, int64_t j0, int64_t w, float* R, int64_t ldr,
                       cudaStream_t st);
 cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t st);
+
+// Block reorthogonalisation of panel columns kb .. kb+bk-1 against columns 0 .. kb-1:
+// S = Q[:, 0:kb]^T Qbar, Qbar -= Q[:, 0:kb] S, R[0:kb, kb:kb+bk] += S (four launches).
+bool tc_has_block_reorth(const TcGemm* t);
+cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr, cudaStream_t st);
+cudaError_t tc_refresh_rows(TcGemm* t, int64_t ncols, cudaStream_t st);
 
 }  // namespace cqr

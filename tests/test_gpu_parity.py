@@ -335,3 +335,41 @@ def test_register_and_shared_memory_panels_agree(shape, monkeypatch):
     assert rel(a["R"], bb["R"]) < n * U3X * kap
     ref = O.run(A, p, p if n % p == 0 else 4, f, b, seed=3)
     assert rel(a["R"], ref["R"]) < n * U3X * kap
+
+
+# ----------------------------------------------------------------- block reorthogonalisation
+@pytest.mark.parametrize("dtype,mma,kappa", [("f64", "simt", 1e8), ("f32", "3xtf32", 1e4),
+                                             ("f32", "simt", 1e4)])
+def test_block_reorth_parity_and_orthogonality(dtype, mma, kappa):
+    m = n = 512
+    p, f, b = 8, 2, 64
+    A = synth.kappa_matrix(m, n, kappa, seed=13)
+    er = {3: synth.random_erasures(p + f, p + f, f, 2, seed=3), 6: [(1, 1)]}
+    ref = O.run(A, p, p, f, b, seed=6, erasures=er, reorth_block=True)
+    q = B.CodedQR(m, n, p, p, f, b, dtype=dtype, mma=mma, seed=6, reorth_block=True)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    q.encode(to_dev(A, td))
+    for t in range(q.geo["panels"]):
+        if er.get(t):
+            q.inject(er[t])
+            q.recover()
+        q.factor(t, t + 1)
+    Qc, Rc = q.factors()
+    Q, R = to_np(Qc), to_np(Rc)
+    Qo = B.colmajor_empty(q.geo["m_pad"], n, td)
+    q.post_orth(Qo)
+    torch.cuda.synchronize()
+    assert q.sync_status() == 0
+    assert q.decode_sets() == ref["sets"]
+    q.close()
+    u = U64 if dtype == "f64" else (U3X if mma == "3xtf32" else U32)
+    g = ref["geom"]
+    tol = n * u * kappa
+    assert rel(R, ref["R"]) < tol
+    Qo = to_np(Qo)
+    orth = np.abs(Qo.T @ Qo - np.eye(n)).max()
+    back = np.linalg.norm(A - Q[:m, :n] @ R[:n, :n]) / np.linalg.norm(A)
+    if dtype == "f32":
+        assert orth < 1e-5 and back < 1e-5, (orth, back)   # the FP32 accuracy target
+    else:
+        assert orth < 1e-12 and back < 1e-12, (orth, back)
