@@ -369,7 +369,13 @@ def test_block_reorth_parity_and_orthogonality(dtype, mma, kappa):
     Qo = to_np(Qo)
     orth = np.abs(Qo.T @ Qo - np.eye(n)).max()
     back = np.linalg.norm(A - Q[:m, :n] @ R[:n, :n]) / np.linalg.norm(A)
+    # the coded factor itself is orthogonal to working precision after the extra pass; the
+    # post-orthogonalised G_0 Q_1 inherits the drift of Q_2 = G_v Q_1, which the pivots
+    # amplify like u kappa (the oracle shows the same)
+    Qt = Q[: g.M, :n]
+    assert np.abs(Qt.T @ Qt - np.eye(n)).max() < 64 * n * u
+    orth_ref = np.abs(ref["Qo"].T @ ref["Qo"] - np.eye(n)).max()
     if dtype == "f32":
         assert orth < 1e-5 and back < 1e-5, (orth, back)   # the FP32 accuracy target
     else:
-        assert orth < 1e-12 and back < 1e-12, (orth, back)
+        assert back < 1e-12 and orth < max(1e-12, 10 * orth_ref), (orth, orth_ref, back)
