@@ -27,7 +27,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-  size_t Q, R, Gt, Gh, Gt_t, Gh_t, part, bar, status, P, Rb, Pt, yw, xw, plans, tc, total;
+  size_t Q, R, Gt, Gh, Gt_t, Gh_t, part, bar, status, P, Rb, Pt, yw, xw, plans, cg, tc, total;
 };
 
 struct Buffers {
@@ -46,6 +46,7 @@ struct Buffers {
   void* yw;
   void* xw;
   DecodePlan* plans;
+  double* cg;
   void* tc;
 };
 
@@ -113,6 +114,7 @@ Layout make_layout(const cqr_config* c, const Geo& g, int num_sms) {
   L.yw = take((size_t)g.m_pad * nrhs * s);
   L.xw = take((size_t)(g.m + g.N) * nrhs * s);
   L.plans = take(sizeof(DecodePlan) * (size_t)(g.grid_cols + g.p_c + c->f + 2));
+  L.cg = take(sizeof(double) * (size_t)(7 * g.n + g.c + 2 * (num_sms + 1)));
   L.tc = take(c->dtype == CQR_F32 && c->mma != CQR_MMA_SIMT
                   ? tc_workspace_bytes(g.M, g.N, g.n, bmax, c->reorth_block != 0)
                   : 0);
@@ -243,6 +245,7 @@ cqr_status setup(cqr_handle h) {
   h->B.yw = base + L.yw;
   h->B.xw = base + L.xw;
   h->B.plans = reinterpret_cast<DecodePlan*>(base + L.plans);
+  h->B.cg = reinterpret_cast<double*>(base + L.cg);
   h->B.tc = base + L.tc;
   h->mask.assign((size_t)h->g.grid_rows * h->g.grid_cols, 0);
   CK(cudaMallocHost(&h->plans_host, sizeof(DecodePlan) * (size_t)(h->g.grid_cols + h->g.p_c + h->g.f + 2)));
@@ -544,7 +547,21 @@ template <typename T>
 cqr_status solve_t(cqr_handle h, const T* y, int64_t ldy, T* x, int64_t ldx, int32_t nrhs) {
   const Geo& g = h->g;
   const bool square = (g.m == g.n && g.m_pad == g.m);
-  if (!square) return CQR_ENOTSUP;
+  if (!square) {
+    // least squares through A = Q_1 R: CG in FP64 on (I - Q_2^T Q_2) w = Q_1^T y, then R x = w
+    if (h->postorth_inplace) return CQR_ESTATE;  // Q_1 was overwritten by G_0 Q_1
+    for (int32_t k = 0; k < nrhs; ++k) {
+      {
+        ProfScope ps(h, K_SOLVE_GEMV, 1);
+        CK(launch_ls_cg<T>(ptr<T>(h->B.Q), g.ldq, g.m, g.m_pad, g.c, g.n, y + (int64_t)k * ldy,
+                           x + (int64_t)k * ldx, h->B.cg, h->B.bar, h->B.status, h->num_sms, h->st));
+      }
+    }
+    ProfScope ps(h, K_TRSV, nrhs);
+    CK(launch_trsv_upper<T>(ptr<T>(h->B.R), g.ldr, g.n, x, ldx, nrhs, h->B.bar, h->B.status,
+                            h->num_sms, h->st));
+    return CQR_OK;
+  }
   cqr_status s = post_orth_q<T>(h, nullptr, 0);
   if (s != CQR_OK) return s;
   T* yo = ptr<T>(h->B.yw);
@@ -790,8 +807,10 @@ cqr_status coded_qr_run(cqr_handle h, const void* A, int64_t lda, const void* y,
     if (s != CQR_OK) return s;
     t = t_next;
   }
-  s = coded_qr_post_orth(h, nullptr, 0, nullptr, 0, nullptr, 0, 0);
-  if (s != CQR_OK) return s;
+  if (g.m == g.n && g.m_pad == g.m) {
+    s = coded_qr_post_orth(h, nullptr, 0, nullptr, 0, nullptr, 0, 0);
+    if (s != CQR_OK) return s;
+  }
   if (y) {
     s = coded_qr_solve(h, yd, ldyd, xd, ldxd, nrhs);
     if (s != CQR_OK) return s;

@@ -627,6 +627,126 @@ cudaError_t launch_trsv_upper(const T* R, int64_t ldr, int64_t n, T* x, int64_t 
   return cudaSuccess;
 }
 
+// Least squares for tall A (reading: A = Q_1 R, so R x = (Q_1^T Q_1)^{-1} Q_1^T y with
+// Q_1^T Q_1 = I - Q_2^T Q_2 by the orthonormality of the coded Q).  One cooperative kernel,
+// FP64 vectors: z = Q_1^T y, then conjugate gradients on (I - Q_2^T Q_2) w = z.  The matrix
+// is SPD with condition number <= 1 + ||G~||^2 (Q_1^T (I + G_v^T G_v) Q_1 = I), a property
+// of the code, so a few dozen iterations reach FP64 accuracy.  w goes to x (n entries), the
+// back substitution with R follows.  Work vectors: ws[6 n + c + 2 G] doubles.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ls_cg(const T* __restrict__ Q, int64_t ldq, int64_t m,
+                                                int64_t m_pad, int64_t c, int64_t n,
+                                                const T* __restrict__ y, T* __restrict__ x,
+                                                double* ws, int maxit, unsigned* bar, int* status) {
+  const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int64_t gw = (int64_t)g * 8 + warp, nw = (int64_t)G * 8;  // global warp index
+  double* z = ws;
+  double* w = z + n;
+  double* r = w + n;
+  double* p = r + n;
+  double* sp = p + n;
+  double* tv = sp + n + n;  // c entries
+  double* part = tv + c;    // [2][G]
+  unsigned target = 0;
+  __shared__ double red[8];
+  const T* Q2 = Q + m_pad;
+  auto block_sum = [&](double v) -> double {  // sum over the CTA, result in every thread
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += red[k];
+    return t;
+  };
+  auto grid_sum = [&](double v, int slot, int site, double* out) -> bool {
+    const double s = block_sum(v);
+    if (tid == 0) part[slot * G + g] = s;
+    if (!grid_sync(bar, G, target, status, site)) return false;
+    double t = 0.0;
+    for (int k = 0; k < G; ++k) t += __ldcg(part + slot * G + k);
+    *out = t;
+    return true;
+  };
+  // z = Q_1^T y (warp per column), w = 0, r = p = z
+  double zz_loc = 0.0;
+  for (int64_t j = gw; j < n; j += nw) {
+    const T* qj = Q + j * ldq;
+    double acc = 0.0;
+    for (int64_t i = lane; i < m; i += 32) acc += (double)qj[i] * (double)y[i];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      z[j] = acc; w[j] = 0.0; r[j] = acc; p[j] = acc;
+      zz_loc += acc * acc;
+    }
+  }
+  double rr;
+  if (!grid_sum(lane == 0 ? zz_loc : 0.0, 0, 30, &rr)) return;
+  const double stop = rr * 1e-30;  // |r| <= 1e-15 |z|
+  int slot = 1;
+  for (int it = 0; it < maxit && c > 0 && rr > stop; ++it) {
+    // t = Q_2 p (thread per row of Q_2)
+    for (int64_t i = (int64_t)g * blockDim.x + tid; i < c; i += (int64_t)G * blockDim.x) {
+      double acc = 0.0;
+      for (int64_t j = 0; j < n; ++j) acc += (double)Q2[i + j * ldq] * __ldcg(p + j);
+      tv[i] = acc;
+    }
+    if (!grid_sync(bar, G, target, status, 31)) return;
+    // sp = p - Q_2^T t (warp per column), partial p . sp
+    double psp_loc = 0.0;
+    for (int64_t j = gw; j < n; j += nw) {
+      const T* qj = Q2 + j * ldq;
+      double acc = 0.0;
+      for (int64_t i = lane; i < c; i += 32) acc += (double)qj[i] * __ldcg(tv + i);
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        const double pj = __ldcg(p + j);
+        const double v = pj - acc;
+        sp[j] = v;
+        psp_loc += pj * v;
+      }
+    }
+    double psp;
+    if (!grid_sum(lane == 0 ? psp_loc : 0.0, slot, 32, &psp)) return;
+    slot ^= 1;
+    const double alpha = rr / psp;
+    double rr_loc = 0.0;
+    for (int64_t j = (int64_t)g * blockDim.x + tid; j < n; j += (int64_t)G * blockDim.x) {
+      w[j] += alpha * __ldcg(p + j);
+      const double rj = __ldcg(r + j) - alpha * __ldcg(sp + j);
+      r[j] = rj;
+      rr_loc += rj * rj;
+    }
+    double rr_new;
+    if (!grid_sum(rr_loc, slot, 33, &rr_new)) return;
+    slot ^= 1;
+    const double beta = rr_new / rr;
+    rr = rr_new;
+    for (int64_t j = (int64_t)g * blockDim.x + tid; j < n; j += (int64_t)G * blockDim.x)
+      p[j] = __ldcg(r + j) + beta * __ldcg(p + j);
+    if (!grid_sync(bar, G, target, status, 34)) return;
+  }
+  for (int64_t j = (int64_t)g * blockDim.x + tid; j < n; j += (int64_t)G * blockDim.x)
+    x[j] = (T)(c > 0 ? __ldcg(w + j) : __ldcg(z + j));
+}
+
+template <typename T>
+cudaError_t launch_ls_cg(const T* Q, int64_t ldq, int64_t m, int64_t m_pad, int64_t c, int64_t n,
+                         const T* y, T* x, double* ws, unsigned* bar, int* status, int num_sms,
+                         cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  int G = (int)((n + 255) / 256);
+  const int Gc = (int)((c + 255) / 256);
+  if (Gc > G) G = Gc;
+  if (G > num_sms) G = num_sms;
+  if (G < 1) G = 1;
+  int maxit = 200;
+  void* args[] = {(void*)&Q, &ldq, &m, &m_pad, &c, &n, (void*)&y, &x, &ws, &maxit, &bar, &status};
+  return cudaLaunchCooperativeKernel((const void*)k_ls_cg<T>, dim3(G), dim3(256), args, 0, st);
+}
+
 // ===================================================================== instantiations
 #define CQR_INSTANTIATE(T)                                                                        \
   template cudaError_t launch_generator<T>(int, int, int, uint64_t, int, double*, double*, T*,   \
@@ -647,7 +767,9 @@ cudaError_t launch_trsv_upper(const T* R, int64_t ldr, int64_t n, T* x, int64_t 
   template cudaError_t launch_gemv_t<T>(const T*, int64_t, int64_t, int64_t, const T*, int64_t,  \
                                         int64_t, T*, int64_t, cudaStream_t);                      \
   template cudaError_t launch_trsv_upper<T>(const T*, int64_t, int64_t, T*, int64_t, int64_t,    \
-                                            unsigned*, int*, int, cudaStream_t);
+                                            unsigned*, int*, int, cudaStream_t);                   \
+  template cudaError_t launch_ls_cg<T>(const T*, int64_t, int64_t, int64_t, int64_t, int64_t,     \
+                                       const T*, T*, double*, unsigned*, int*, int, cudaStream_t);
 
 CQR_INSTANTIATE(float)
 CQR_INSTANTIATE(double)

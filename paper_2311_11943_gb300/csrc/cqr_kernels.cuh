@@ -96,4 +96,11 @@ template <typename T>
 cudaError_t launch_trsv_upper(const T* R, int64_t ldr, int64_t n, T* x, int64_t ldx, int64_t k,
                               unsigned* bar, int* status, int num_sms, cudaStream_t st);
 
+// Tall least squares through the coded factors: x (n, one column) = (I - Q_2^T Q_2)^{-1} Q_1^T y
+// by conjugate gradients in FP64 (cooperative launch); ws holds 7 n + c + 2 #SMs doubles.
+template <typename T>
+cudaError_t launch_ls_cg(const T* Q, int64_t ldq, int64_t m, int64_t m_pad, int64_t c, int64_t n,
+                         const T* y, T* x, double* ws, unsigned* bar, int* status, int num_sms,
+                         cudaStream_t st);
+
 }  // namespace cqr

@@ -379,3 +379,34 @@ def test_block_reorth_parity_and_orthogonality(dtype, mma, kappa):
         assert orth < 1e-5 and back < 1e-5, (orth, back)   # the FP32 accuracy target
     else:
         assert back < 1e-12 and orth < max(1e-12, 10 * orth_ref), (orth, orth_ref, back)
+
+
+# ----------------------------------------------------------------- tall least squares (a9)
+@pytest.mark.parametrize("dtype,mma,shape", [("f64", "simt", (1024, 256, 8, 4, 2, 64)),
+                                             ("f64", "simt", (1003, 192, 8, 4, 1, 48)),
+                                             ("f32", "3xtf32", (2048, 256, 8, 4, 2, 128))])
+def test_tall_least_squares(dtype, mma, shape):
+    m, n, p_r, p_c, f, b = shape
+    A = synth.kappa_matrix(m, n, 1e3, seed=17)
+    y = synth.rhs(m, 2, 17)
+    er = {1: [(2, 1)]}
+    ref = O.run(A, p_r, p_c, f, b, seed=7, y=y, erasures=er)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    q = B.CodedQR(m, n, p_r, p_c, f, b, dtype=dtype, mma=mma, seed=7, nrhs_max=2)
+    q.encode(to_dev(A, td))
+    for t in range(q.geo["panels"]):
+        if er.get(t):
+            q.inject(er[t])
+            q.recover()
+        q.factor(t, t + 1)
+    x = B.colmajor_empty(n, 2, td)
+    q.solve(to_dev(y, td), x)
+    torch.cuda.synchronize()
+    assert q.sync_status() == 0
+    q.close()
+    x = to_np(x)
+    xl, *_ = np.linalg.lstsq(A, y, rcond=None)
+    u = U64 if dtype == "f64" else U3X
+    tol = n * u * 1e3 * 10
+    assert rel(x, ref["x"]) < tol * max(1.0, np.abs(ref["x"]).max())
+    assert rel(x, xl) < tol * max(1.0, np.abs(xl).max())
