@@ -313,6 +313,9 @@ def run_ours(args, cfg):
     Qc, Rc = q.factors()
     Q1 = Qc[:m, :n].double()
     R1 = Rc[:n, :n].double()
+    Qt64 = Qc[: q.geo["M"], :n].double()
+    orth_coded = (torch.eye(n, device=dev, dtype=torch.float64) - Qt64.T @ Qt64).abs().max().item()
+    del Qt64
     A64 = torch.from_numpy(A_np).to(dev)
     berr = (torch.linalg.norm(A64 - Q1 @ R1) / torch.linalg.norm(A64)).item()
     Qo = B.colmajor_empty(q.geo["m_pad"], n, td)
@@ -423,8 +426,8 @@ def run_ours(args, cfg):
                         (ms_unc * 1e-3) / 1e12},
             "coding_overhead": ms / ms_unc - 1.0,
             "flop_model_overhead_floor": F / (2.0 * m * n * n) - 1.0,
-            "errors": {"backward_rel_fro": berr, "orth_max_post_orth": orth,
-                       "solve_rel_residual": resid},
+            "errors": {"backward_rel_fro": berr, "orth_max_coded_Q": orth_coded,
+                       "orth_max_post_orth": orth, "solve_rel_residual": resid},
             "reorth_per_step": stats["n_reorth"] / max(1, (args.steps + args.warmup)),
             "recovered_tiles_per_step": len(plan),
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
