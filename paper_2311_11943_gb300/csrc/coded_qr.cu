@@ -344,8 +344,11 @@ cqr_status panel_step(cqr_handle h, int t) {
   if (h->cfg.reorth_block && kb > 0) {
     // block reorthogonalisation: S = Q[:, :kb]^T Qbar, Qbar -= Q[:, :kb] S, R[:kb, panel] += S
     if (tc) {
-      ProfScope ps(h, K_BLOCK_REORTH, 4);
-      CK(tc_block_reorth(h->tc, kb, bk, ptr<float>(h->B.R), g.ldr, h->st));
+      ProfScope ps(h, K_BLOCK_REORTH, 0);
+      int nl = 0;
+      const cudaError_t e = tc_block_reorth(h->tc, kb, bk, ptr<float>(h->B.R), g.ldr, h->st, &nl);
+      h->prof_launches[K_BLOCK_REORTH] += nl;
+      CK(e);
     } else {
       ProfScope ps(h, K_BLOCK_REORTH, 3);
       const int sp = choose_splits((int)kb, bk, g.M, h->num_sms);

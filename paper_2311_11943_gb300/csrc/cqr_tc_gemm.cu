@@ -37,6 +37,7 @@ namespace {
 
 constexpr int BM = 128;       // UMMA M (TMEM lanes)
 constexpr int BN = 128;       // UMMA N (TMEM columns)
+constexpr int kTmemCols = 2 * BN;  // two accumulator buffers (power of two, <= 512)
 constexpr int BK = 32;        // K per stage: 32 FP32 = 128 bytes = one swizzle row
 constexpr int UMMA_K = 8;     // K per tcgen05.mma kind::tf32
 constexpr int kThreads = 256;
@@ -191,6 +192,8 @@ struct Smem {
   static constexpr uint32_t kStageBytes = NA * kTileBytesA + NB * kTileBytesB;
   static constexpr uint32_t kTiles = STAGES * kStageBytes;
   static constexpr uint32_t kTotal = kTiles + 1024 /*alignment*/ + 256 /*barriers*/;
+  // full/ready/empty per stage, acc_full[2], acc_empty[2], TMEM slot, abort flag
+  static_assert(STAGES * 3 * 8 + 4 * 8 + 8 <= 256, "barrier region too small");
 };
 
 template <int STAGES, int NA, int NB>
@@ -204,9 +207,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
   uint64_t* full = reinterpret_cast<uint64_t*>(tiles + S::kTiles);
   uint64_t* ready = full + STAGES;     // B split done (3xTF32 in-smem split)
   uint64_t* empty = ready + STAGES;
-  uint64_t* acc_full = empty + STAGES;
-  uint64_t* acc_empty = acc_full + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  uint64_t* acc_full = empty + STAGES;  // [2]: one per TMEM accumulator buffer
+  uint64_t* acc_empty = acc_full + 2;   // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -219,8 +222,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
       mbar_init(&ready[s], 64);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 4);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     prefetch_tmap(&maps.a[0]);
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      su32(tmem_slot)),
-                 "r"((uint32_t)BN)
+                 "r"((uint32_t)kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -283,7 +288,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
       for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x, ++tl) {
         const int split = t % job.splits;
         const int nk = kblocks(split);
-        if (!mbar_wait(acc_empty, (tl & 1) ^ 1, abort_flag)) break;
+        // two accumulators: the epilogue drains tile tl-1 while tile tl accumulates
+        const int buf = tl & 1;
+        const uint32_t acc = tmem + (uint32_t)(buf * BN);
+        if (!mbar_wait(&acc_empty[buf], ((tl >> 1) & 1) ^ 1, abort_flag)) break;
         tc_fence_after();
         bool ok = true;
         for (int kb = 0; kb < nk; ++kb, ++it) {
@@ -298,16 +306,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
           for (int ks = 0; ks < BK / UMMA_K; ++ks) {
             const uint32_t off = ks * UMMA_K * 4;
             const uint32_t acc0 = (kb > 0 || ks > 0) ? 1u : 0u;
-            mma_tf32(tmem, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
+            mma_tf32(acc, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
             if (job.nprod == 3) {
-              mma_tf32(tmem, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
-              mma_tf32(tmem, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
+              mma_tf32(acc, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
+              mma_tf32(acc, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
             }
           }
           mma_commit(&empty[s]);
         }
         if (!ok) break;
-        mma_commit(acc_full);
+        mma_commit(&acc_full[buf]);
       }
     }
   } else if (warp == 2 || warp == 3) {
@@ -347,7 +355,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
       const int split = t % job.splits;
       const int mn = t / job.splits;
       const int mt = mn % job.m_tiles, nt = mn / job.m_tiles;
-      if (!mbar_wait(acc_full, tl & 1, abort_flag)) break;
+      const int buf = tl & 1;
+      if (!mbar_wait(&acc_full[buf], (tl >> 1) & 1, abort_flag)) break;
       tc_fence_after();
       const int64_t row = (int64_t)mt * BM + ew * 32 + lane;
       const bool row_ok = row < job.mrows;
@@ -355,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
 #pragma unroll 1
       for (int c = 0; c < BN / 32; ++c) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(c * 32), v);
+        tmem_ld32(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
         if (!has_k)
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = 0.f;
@@ -383,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
     }
   }
 
@@ -392,7 +401,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)kTmemCols)
                  : "memory");
   }
 }
@@ -425,6 +435,21 @@ __global__ void k_split_panel(const float* __restrict__ Q, int64_t ldq, int64_t 
   if (Qr_hi && k < bk) {
     Qr_hi[r * ldrow + kb + k] = h;
     if (nplanes == 2) Qr_lo[r * ldrow + kb + k] = l;
+  }
+}
+
+// C -= sum_s P[s] in a fixed order of s (split-K partials of a C -= A B update; P[s] is
+// mrows x ncols column-major with leading dimension mrows).
+__global__ void k_tc_sub_partials(const float* __restrict__ P, int splits, int64_t mrows,
+                                  int64_t ncols, float* __restrict__ C, int64_t ldc) {
+  const int64_t total = mrows * ncols;
+  const int64_t stride = total;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx % mrows, c = idx / mrows;
+    float s = 0.f;
+    for (int sp = 0; sp < splits; ++sp) s += __ldcs(P + sp * stride + idx);
+    C[r + c * ldc] -= s;
   }
 }
 
@@ -759,8 +784,11 @@ cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_
 // Block reorthogonalisation of panel kb .. kb+bk-1 against columns 0 .. kb-1 (four
 // launches: split the panel, S^T = Qbar^T Q[:, 0:kb] split-K on the tensor cores, reduce
 // into R and S, Qbar -= Qrows S on the tensor cores).
-cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr, cudaStream_t st) {
+cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr, cudaStream_t st,
+                            int* launches) {
+  *launches = 0;
   if (!t->Qr_hi || kb <= 0) return cudaSuccess;
+  *launches = 4;
   cudaError_t e = tc_split_panel(t, kb, bk, false, st);
   if (e != cudaSuccess) return e;
   e = tc_gemm_rbar(t, bk, 0, kb, st);  // partials of S^T (bk x kb)
@@ -791,20 +819,45 @@ cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr
   job.epi = 1;
   job.m_tiles = (int)((t->M + BM - 1) / BM);
   job.n_tiles = (bk + BN - 1) / BN;
-  job.splits = 1;
+  // Split K (the kb computed columns) when the M x bk output has too few tiles to fill the
+  // SMs; the partials go to P (capacity kMaxSplits * bkp * N floats) and are subtracted in
+  // a fixed order, so the result does not depend on the schedule.
+  const int64_t kblk = kbp / BK;
+  const int tiles2 = job.m_tiles * job.n_tiles;
+  int64_t want = std::min<int64_t>(std::min<int64_t>(kMaxSplits, kblk), t->num_sms / std::max(1, tiles2));
+  const int64_t cap = (int64_t)kMaxSplits * t->bkp * t->N / (t->M * (int64_t)bk);
+  want = std::min<int64_t>(want, cap);
+  int64_t kchunk2 = kbp;
+  if (want > 1) kchunk2 = (kblk + want - 1) / want * BK;
+  const int splits2 = (int)((kbp + kchunk2 - 1) / kchunk2);
+  job.splits = splits2;
   job.a_row0 = 0;
   job.b_row0 = 0;
   job.k0 = 0;
-  job.kchunk = kbp;
+  job.kchunk = kchunk2;
   job.K = kbp;
   job.mrows = t->M;
   job.ncols = bk;
-  job.out = t->Q + kb * t->ldq;
-  job.ldo = t->ldq;
-  job.split_stride = 0;
   job.status = t->status;
-  return three ? launch_gemm<3, 2, 2>(maps, job, t->num_sms, st)
-               : launch_gemm<6, 1, 1>(maps, job, t->num_sms, st);
+  if (splits2 == 1) {
+    job.epi = 1;
+    job.out = t->Q + kb * t->ldq;
+    job.ldo = t->ldq;
+    job.split_stride = 0;
+  } else {
+    job.epi = 0;
+    job.out = t->P;
+    job.ldo = t->M;
+    job.split_stride = t->M * (int64_t)bk;
+  }
+  e = three ? launch_gemm<3, 2, 2>(maps, job, t->num_sms, st)
+            : launch_gemm<6, 1, 1>(maps, job, t->num_sms, st);
+  if (e != cudaSuccess || splits2 == 1) return e;
+  *launches = 5;
+  const int64_t total = t->M * (int64_t)bk;
+  const int blocks = (int)std::min<int64_t>((int64_t)t->num_sms * 8, (total + 255) / 256);
+  k_tc_sub_partials<<<blocks, 256, 0, st>>>(t->P, splits2, t->M, bk, t->Q + kb * t->ldq, t->ldq);
+  return cudaGetLastError();
 }
 
 }  // namespace cqr

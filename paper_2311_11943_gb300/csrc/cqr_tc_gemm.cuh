@@ -25,9 +25,11 @@ cudaError_t tc_reduce(TcGemm* t, int64_t kb, int bk, int64_t j0, int64_t w, floa
 cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t st);
 
 // Block reorthogonalisation of panel columns kb .. kb+bk-1 against columns 0 .. kb-1:
-// S = Q[:, 0:kb]^T Qbar, Qbar -= Q[:, 0:kb] S, R[0:kb, kb:kb+bk] += S (four launches).
+// S = Q[:, 0:kb]^T Qbar, Qbar -= Q[:, 0:kb] S, R[0:kb, kb:kb+bk] += S (four launches, five
+// when the second product is split over K); *launches receives the count.
 bool tc_has_block_reorth(const TcGemm* t);
-cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr, cudaStream_t st);
+cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr, cudaStream_t st,
+                            int* launches);
 cudaError_t tc_refresh_rows(TcGemm* t, int64_t ncols, cudaStream_t st);
 
 }  // namespace cqr
