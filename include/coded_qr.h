@@ -225,6 +225,74 @@ cqr_status coded_qr_panel_icgs_noalloc(int32_t dtype, int64_t M, int32_t bk, voi
                                        void* R, int64_t ldr, double tau, int32_t* status,
                                        void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Batches.  `count` independent instances of the coded method (Section 4 applied to each
+ * m_i x n_i matrix; tall-skinny shapes), FP32 on the CUDA cores, sharing p_r, p_c, f, protect_r,
+ * gdist, tau, seed (one generator for every instance) and the stream of the configuration.
+ * cfg->m and cfg->n are ignored; cfg->dtype must be CQR_F32 and cfg->mma CQR_MMA_SIMT
+ * (CQR_ENOTSUP otherwise), cfg->reorth_block must be 0.  cfg->b in 1..64 fixes every panel
+ * width; cfg->b == 0 picks each width from the instance's shape (the widest of 64/32/16 whose
+ * per-CTA panel slice fits shared memory), which coded_qr_batched_autotune can then refine.
+ * Every instance is factorised by one thread-block cluster of the persistent factor launch;
+ * the results are those of the single-instance verbs up to rounding order.  Each instance
+ * owns its encoded matrix Q (M_i x N_i) and R (N_i x N_i) inside the batch's device memory.
+ * Per-instance arrays (m, n, A, lda, panel_end) are host arrays of length count. */
+typedef struct cqr_batched_s* cqr_batched;
+
+enum { CQR_BATCH_GRAPH = 1, CQR_BATCH_POST_ORTH = 2 };
+
+/* Allocate the batch (cudaMalloc on the current device) and compute the shared generator.
+ * Every instance must satisfy the single-instance rules (m_i >= n_i, p_c | n_i, ...). */
+cqr_status coded_qr_batched_create(const cqr_config* cfg, const int64_t* m, const int64_t* n,
+                                   int32_t count, cqr_batched* out);
+cqr_status coded_qr_batched_destroy(cqr_batched bh);
+/* Geometry of instance i, as coded_qr_geometry. */
+cqr_status coded_qr_batched_geometry(cqr_batched bh, int32_t i, int64_t* dims);
+/* a2 for every instance: A[i] (device pointer, m_i x n_i column-major, lda[i] >= m_i). */
+cqr_status coded_qr_batched_encode(cqr_batched bh, const void* const* A, const int64_t* lda);
+/* a3-a5: instance i runs its panels from where it stopped up to panel_end[i] (NULL: to the
+ * last panel), all instances in one persistent launch. */
+cqr_status coded_qr_batched_factor(cqr_batched bh, const int32_t* panel_end);
+/* a6: tiles holds count triples (instance, grid row, grid column), as
+ * coded_qr_inject_erasure per instance. */
+cqr_status coded_qr_batched_inject_erasure(cqr_batched bh, const int32_t* tiles, int32_t count);
+/* a7 for every instance with pending erasures, one launch; CQR_EUNRECOVERABLE (nothing
+ * launched) when an instance lost more than f tiles of one code. */
+cqr_status coded_qr_batched_recover(cqr_batched bh, int32_t* n_recovered);
+/* a8: Q_1 <- G_0 Q_1 in place for every instance (after the last panel). */
+cqr_status coded_qr_batched_post_orth(cqr_batched bh);
+/* The whole sequence: encode, factor up to each instance's erasure panel, erase, recover,
+ * factor to the end, and with CQR_BATCH_POST_ORTH the post-orthogonalisation.  erasures
+ * holds count quadruples (instance, panel t, grid row, grid column): the tiles are lost at
+ * the start of panel t (every tile of one instance at the same t, CQR_ENOTSUP otherwise).
+ * With CQR_BATCH_GRAPH the launches are recorded into a CUDA graph on the first call and the
+ * graph is replayed while the erasure list, the inputs and the tuning stay the same. */
+cqr_status coded_qr_batched_run(cqr_batched bh, const void* const* A, const int64_t* lda,
+                                const int32_t* erasures, int32_t count, int32_t flags);
+/* Autotuner: times the batch factorisation of A (CUDA events, best of reps) over the
+ * cluster sizes 1/2/4/8 and the width rules 16/32/64/shape-fit, then refines the width per
+ * class of encoded height (< 1024, < 4096, >= 4096 rows); keeps the fastest and leaves the
+ * batch encoded and factorised with it.  *cluster (host, optional) receives the cluster size. */
+cqr_status coded_qr_batched_autotune(cqr_batched bh, const void* const* A, const int64_t* lda,
+                                     int32_t reps, int32_t* cluster);
+/* Set / read the tuning: cluster size (1, 2, 4, 8) and the panel widths b[count] (host; NULL
+ * on set: the shape rule).  Setting it requires a new encode. */
+cqr_status coded_qr_batched_set_tuning(cqr_batched bh, int32_t cluster, const int32_t* b);
+cqr_status coded_qr_batched_get_tuning(cqr_batched bh, int32_t* cluster, int32_t* b);
+/* Borrow instance i's coded factors (device, owned by the batch). */
+cqr_status coded_qr_batched_get_factors(cqr_batched bh, int32_t i, void** Q, int64_t* ldq,
+                                        void** R, int64_t* ldr);
+/* Decode index sets of instance i since the last encode/run (format of
+ * coded_qr_get_decode_sets). */
+cqr_status coded_qr_batched_get_decode_sets(cqr_batched bh, int32_t i, int32_t* buf, int32_t cap,
+                                            int32_t* len);
+/* Synchronise; the status of the first instance whose device status word is set (CQR_OK if
+ * none), *first_bad its index or -1, *reorth the reorthogonalisations of all instances. */
+cqr_status coded_qr_batched_sync_status(cqr_batched bh, int32_t* first_bad, int64_t* reorth);
+
+/* Name of the last CUDA error behind a CQR_ECUDA of a batch entry point on this host thread. */
+const char* coded_qr_batched_last_error(void);
+
 /* Static description of a status code. */
 const char* coded_qr_errstr(cqr_status s);
 

@@ -28,7 +28,15 @@ EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "
            "coded_qr_recover", "coded_qr_post_orth", "coded_qr_solve", "coded_qr_run",
            "coded_qr_get_factors", "coded_qr_get_generator", "coded_qr_get_decode_sets",
            "coded_qr_stats", "coded_qr_sync_status", "coded_qr_errstr", "coded_qr_profile",
-           "coded_qr_profile_read", "coded_qr_profile_name", "coded_qr_panel_icgs_noalloc"]
+           "coded_qr_profile_read", "coded_qr_profile_name", "coded_qr_panel_icgs_noalloc",
+           "coded_qr_batched_create", "coded_qr_batched_destroy", "coded_qr_batched_geometry",
+           "coded_qr_batched_encode", "coded_qr_batched_factor",
+           "coded_qr_batched_inject_erasure", "coded_qr_batched_recover",
+           "coded_qr_batched_post_orth", "coded_qr_batched_run", "coded_qr_batched_autotune",
+           "coded_qr_batched_set_tuning", "coded_qr_batched_get_tuning",
+           "coded_qr_batched_get_factors", "coded_qr_batched_get_decode_sets",
+           "coded_qr_batched_sync_status", "coded_qr_batched_last_error"]
+CQR_BATCH_GRAPH, CQR_BATCH_POST_ORTH = 1, 2
 PROF_CLASSES = 15
 
 
@@ -82,6 +90,22 @@ def lib():
             "coded_qr_profile": [vp, i32],
             "coded_qr_profile_read": [vp, C.POINTER(C.c_double), C.POINTER(i64), i32, i32],
             "coded_qr_panel_icgs_noalloc": [i32, i64, i32, vp, i64, vp, i64, C.c_double, vp, vp],
+            "coded_qr_batched_create": [pcfg, C.POINTER(i64), C.POINTER(i64), i32, C.POINTER(vp)],
+            "coded_qr_batched_destroy": [vp],
+            "coded_qr_batched_geometry": [vp, i32, C.POINTER(i64)],
+            "coded_qr_batched_encode": [vp, C.POINTER(vp), C.POINTER(i64)],
+            "coded_qr_batched_factor": [vp, C.POINTER(i32)],
+            "coded_qr_batched_inject_erasure": [vp, C.POINTER(i32), i32],
+            "coded_qr_batched_recover": [vp, C.POINTER(i32)],
+            "coded_qr_batched_post_orth": [vp],
+            "coded_qr_batched_run": [vp, C.POINTER(vp), C.POINTER(i64), C.POINTER(i32), i32, i32],
+            "coded_qr_batched_autotune": [vp, C.POINTER(vp), C.POINTER(i64), i32, C.POINTER(i32)],
+            "coded_qr_batched_set_tuning": [vp, i32, C.POINTER(i32)],
+            "coded_qr_batched_get_tuning": [vp, C.POINTER(i32), C.POINTER(i32)],
+            "coded_qr_batched_get_factors": [vp, i32, C.POINTER(vp), C.POINTER(i64),
+                                             C.POINTER(vp), C.POINTER(i64)],
+            "coded_qr_batched_get_decode_sets": [vp, i32, C.POINTER(i32), i32, C.POINTER(i32)],
+            "coded_qr_batched_sync_status": [vp, C.POINTER(i32), C.POINTER(i64)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -89,6 +113,8 @@ def lib():
             fn.restype = C.c_int
         L.coded_qr_errstr.argtypes = [C.c_int]
         L.coded_qr_errstr.restype = C.c_char_p
+        L.coded_qr_batched_last_error.argtypes = []
+        L.coded_qr_batched_last_error.restype = C.c_char_p
         L.coded_qr_profile_name.argtypes = [C.c_int32]
         L.coded_qr_profile_name.restype = C.c_char_p
         _lib = L
@@ -228,6 +254,117 @@ def coded_qr_profile_name(k):
 
 
 # ------------------------------------------------------------------ torch convenience layer
+def _i64s(vals):
+    return (C.c_int64 * len(vals))(*[int(v) for v in vals])
+
+
+def _i32s(vals):
+    vals = list(vals)
+    return (C.c_int32 * max(1, len(vals)))(*[int(v) for v in vals])
+
+
+def _ptrs(vals):
+    return (C.c_void_p * len(vals))(*[int(v) for v in vals])
+
+
+def coded_qr_batched_last_error():
+    return lib().coded_qr_batched_last_error().decode()
+
+
+def _bcheck(status, where):
+    if status == CQR_ECUDA:
+        where = "%s [%s]" % (where, coded_qr_batched_last_error())
+    check(status, where)
+
+
+def coded_qr_batched_create(cfg, m, n):
+    bh = C.c_void_p()
+    _bcheck(lib().coded_qr_batched_create(C.byref(cfg), _i64s(m), _i64s(n), len(m), C.byref(bh)),
+          "coded_qr_batched_create")
+    return bh
+
+
+def coded_qr_batched_destroy(bh):
+    return lib().coded_qr_batched_destroy(bh)
+
+
+def coded_qr_batched_geometry(bh, i):
+    d = (C.c_int64 * len(GEO_FIELDS))()
+    _bcheck(lib().coded_qr_batched_geometry(bh, i, d), "coded_qr_batched_geometry")
+    return dict(zip(GEO_FIELDS, [int(v) for v in d]))
+
+
+def coded_qr_batched_encode(bh, A_ptrs, ldas):
+    return lib().coded_qr_batched_encode(bh, _ptrs(A_ptrs), _i64s(ldas))
+
+
+def coded_qr_batched_factor(bh, panel_end=None):
+    return lib().coded_qr_batched_factor(bh, _i32s(panel_end) if panel_end is not None else None)
+
+
+def coded_qr_batched_inject_erasure(bh, triples):
+    flat = [v for t in triples for v in t]
+    return lib().coded_qr_batched_inject_erasure(bh, _i32s(flat), len(triples))
+
+
+def coded_qr_batched_recover(bh):
+    n = C.c_int32(0)
+    st = lib().coded_qr_batched_recover(bh, C.byref(n))
+    return st, n.value
+
+
+def coded_qr_batched_post_orth(bh):
+    return lib().coded_qr_batched_post_orth(bh)
+
+
+def coded_qr_batched_run(bh, A_ptrs, ldas, erasures, flags):
+    flat = [v for e in erasures for v in e]
+    return lib().coded_qr_batched_run(bh, _ptrs(A_ptrs), _i64s(ldas), _i32s(flat), len(erasures),
+                                      flags)
+
+
+def coded_qr_batched_autotune(bh, A_ptrs, ldas, reps):
+    g = C.c_int32(0)
+    st = lib().coded_qr_batched_autotune(bh, _ptrs(A_ptrs), _i64s(ldas), reps, C.byref(g))
+    return st, g.value
+
+
+def coded_qr_batched_set_tuning(bh, cluster, b=None):
+    return lib().coded_qr_batched_set_tuning(bh, cluster, _i32s(b) if b is not None else None)
+
+
+def coded_qr_batched_get_tuning(bh, count):
+    g = C.c_int32(0)
+    b = (C.c_int32 * count)()
+    _bcheck(lib().coded_qr_batched_get_tuning(bh, C.byref(g), b), "coded_qr_batched_get_tuning")
+    return g.value, [int(v) for v in b]
+
+
+def coded_qr_batched_get_factors(bh, i):
+    q, r = C.c_void_p(), C.c_void_p()
+    ldq, ldr = C.c_int64(0), C.c_int64(0)
+    _bcheck(lib().coded_qr_batched_get_factors(bh, i, C.byref(q), C.byref(ldq), C.byref(r),
+                                             C.byref(ldr)), "coded_qr_batched_get_factors")
+    return q.value, ldq.value, r.value, ldr.value
+
+
+def coded_qr_batched_get_decode_sets(bh, i):
+    n = C.c_int32(0)
+    _bcheck(lib().coded_qr_batched_get_decode_sets(bh, i, None, 0, C.byref(n)),
+          "coded_qr_batched_get_decode_sets")
+    buf = (C.c_int32 * max(1, n.value))()
+    _bcheck(lib().coded_qr_batched_get_decode_sets(bh, i, buf, n.value, C.byref(n)),
+          "coded_qr_batched_get_decode_sets")
+    return [int(v) for v in buf[: n.value]]
+
+
+def coded_qr_batched_sync_status(bh):
+    bad = C.c_int32(-1)
+    nre = C.c_int64(0)
+    st = lib().coded_qr_batched_sync_status(bh, C.byref(bad), C.byref(nre))
+    return st, bad.value, nre.value
+
+
 class _DevView:
     """__cuda_array_interface__ over memory owned by the library (borrowed)."""
 
@@ -372,3 +509,96 @@ class CodedQR:
 
     def profile_read(self, reset=True):
         return coded_qr_profile_read(self.h, reset)
+
+
+class CodedQRBatch:
+    """A batch of independent FP32 coded QRs of shapes (m_i, n_i) (batch handle wrapper).
+    Inputs are lists of column-major torch tensors on the current CUDA device."""
+
+    def __init__(self, shapes, p_r, p_c, f, b=0, protect_r=True, gdist=CQR_G_UNIF01, seed=1,
+                 tau=0.0, stream=None):
+        import torch
+        self.torch = torch
+        cfg = Config()
+        cfg.m, cfg.n = 0, 0
+        cfg.p_r, cfg.p_c, cfg.f, cfg.b = p_r, p_c, f, b
+        cfg.dtype, cfg.mma = CQR_F32, CQR_MMA_SIMT
+        cfg.protect_r = int(bool(protect_r))
+        cfg.gdist = gdist
+        cfg.nrhs_max = 1
+        cfg.seed = seed
+        cfg.tau = tau
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        cfg.stream = C.c_void_p(stream.cuda_stream)
+        self.cfg = cfg
+        self.shapes = [(int(m), int(n)) for m, n in shapes]
+        self.count = len(self.shapes)
+        self.h = coded_qr_batched_create(cfg, [m for m, _ in self.shapes],
+                                         [n for _, n in self.shapes])
+        self.geo = [coded_qr_batched_geometry(self.h, i) for i in range(self.count)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            coded_qr_batched_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _args(As):
+        return [a.data_ptr() for a in As], [_ld(a) for a in As]
+
+    def encode(self, As):
+        _bcheck(coded_qr_batched_encode(self.h, *self._args(As)), "coded_qr_batched_encode")
+
+    def factor(self, panel_end=None):
+        _bcheck(coded_qr_batched_factor(self.h, panel_end), "coded_qr_batched_factor")
+
+    def inject(self, triples):
+        _bcheck(coded_qr_batched_inject_erasure(self.h, triples), "coded_qr_batched_inject_erasure")
+
+    def recover(self):
+        st, n = coded_qr_batched_recover(self.h)
+        _bcheck(st, "coded_qr_batched_recover")
+        return n
+
+    def post_orth(self):
+        _bcheck(coded_qr_batched_post_orth(self.h), "coded_qr_batched_post_orth")
+
+    def run(self, As, erasures=(), graph=True, post_orth=False):
+        flags = (CQR_BATCH_GRAPH if graph else 0) | (CQR_BATCH_POST_ORTH if post_orth else 0)
+        _bcheck(coded_qr_batched_run(self.h, *self._args(As), list(erasures), flags),
+              "coded_qr_batched_run")
+
+    def autotune(self, As, reps=2):
+        st, g = coded_qr_batched_autotune(self.h, *self._args(As), reps)
+        _bcheck(st, "coded_qr_batched_autotune")
+        self.geo = [coded_qr_batched_geometry(self.h, i) for i in range(self.count)]
+        return g
+
+    def set_tuning(self, cluster, b=None):
+        _bcheck(coded_qr_batched_set_tuning(self.h, cluster, b), "coded_qr_batched_set_tuning")
+        self.geo = [coded_qr_batched_geometry(self.h, i) for i in range(self.count)]
+
+    def tuning(self):
+        return coded_qr_batched_get_tuning(self.h, self.count)
+
+    def factors(self, i):
+        """Borrowed column-major views of instance i's coded Q (M x N) and R (N x N)."""
+        q, ldq, r, ldr = coded_qr_batched_get_factors(self.h, i)
+        g = self.geo[i]
+        Qv = self.torch.as_tensor(_DevView(q, (g["N"], ldq), "<f4"), device="cuda").t()[: g["M"], :]
+        Rv = self.torch.as_tensor(_DevView(r, (g["N"], ldr), "<f4"), device="cuda").t()[: g["N"], :]
+        return Qv, Rv
+
+    def decode_sets(self, i):
+        return coded_qr_batched_get_decode_sets(self.h, i)
+
+    def sync_status(self):
+        return coded_qr_batched_sync_status(self.h)

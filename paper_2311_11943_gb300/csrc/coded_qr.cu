@@ -913,3 +913,13 @@ const char* coded_qr_errstr(cqr_status s) {
 }
 
 }  // extern "C"
+
+// Host helpers shared with the batched entry points (coded_qr_batched.cu).
+namespace cqr {
+cqr_status host_validate(const cqr_config* c) { return validate(c); }
+Geo host_geo(const cqr_config* c) { return make_geo(c); }
+bool host_make_plan(int nsys, int f, const uint8_t* lost_sys, const uint8_t* lost_chk,
+                    DecodePlan* p) {
+  return make_plan(nsys, f, lost_sys, lost_chk, p);
+}
+}  // namespace cqr

@@ -4,6 +4,8 @@
 // post-orthogonalisation (a8) and the solve (a9).  Templated on the storage type.
 #include <math.h>
 
+#include <algorithm>
+
 #include "cqr_device.cuh"
 #include "cqr_kernels.cuh"
 
@@ -69,12 +71,14 @@ cudaError_t launch_generator(int f, int p_r, int p_c, uint64_t seed, int gdist, 
 // vertical checksums.  Pass 2 (grid z = tile row t, protected R only): reads the p_c tiles of
 // row t (systematic or checksum) and writes the f horizontal checksums; the corner block is
 // (G_v A) G_h.  Sums run in the oracle's order (t, resp. j, ascending).
+// The bodies take their block coordinates as arguments so that the batched kernels can map
+// a flat list of blocks over many instances onto them.
 template <typename T>
-__global__ void __launch_bounds__(256) k_encode_vertical(Geo g, const T* __restrict__ A, int64_t lda,
-                                                          const T* __restrict__ Gt, T* __restrict__ Q) {
-  const int64_t r = (int64_t)blockIdx.x * 32 + threadIdx.x;
-  const int64_t s = (int64_t)blockIdx.y * 8 + threadIdx.y;
-  const int j = blockIdx.z;
+__device__ __forceinline__ void encode_vertical_body(const Geo& g, const T* __restrict__ A,
+                                                     int64_t lda, const T* __restrict__ Gt,
+                                                     T* __restrict__ Q, int bx, int by, int j) {
+  const int64_t r = (int64_t)bx * 32 + threadIdx.x;
+  const int64_t s = (int64_t)by * 8 + threadIdx.y;
   if (r >= g.mb || s >= g.nb) return;
   const int64_t col = (int64_t)j * g.nb + s;
   T acc[kMaxF];
@@ -94,10 +98,16 @@ __global__ void __launch_bounds__(256) k_encode_vertical(Geo g, const T* __restr
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_encode_horizontal(Geo g, const T* __restrict__ Gh, T* __restrict__ Q) {
-  const int64_t r = (int64_t)blockIdx.x * 32 + threadIdx.x;
-  const int64_t s = (int64_t)blockIdx.y * 8 + threadIdx.y;
-  const int t = blockIdx.z;  // tile row, 0 .. p_r + f - 1
+__global__ void __launch_bounds__(256) k_encode_vertical(Geo g, const T* __restrict__ A, int64_t lda,
+                                                          const T* __restrict__ Gt, T* __restrict__ Q) {
+  encode_vertical_body<T>(g, A, lda, Gt, Q, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <typename T>
+__device__ __forceinline__ void encode_horizontal_body(const Geo& g, const T* __restrict__ Gh,
+                                                       T* __restrict__ Q, int bx, int by, int t) {
+  const int64_t r = (int64_t)bx * 32 + threadIdx.x;
+  const int64_t s = (int64_t)by * 8 + threadIdx.y;
   if (r >= g.mb || s >= g.nb) return;
   const int64_t row = (int64_t)t * g.mb + r;
   T acc[kMaxF];
@@ -112,6 +122,11 @@ __global__ void __launch_bounds__(256) k_encode_horizontal(Geo g, const T* __res
 #pragma unroll
   for (int l = 0; l < kMaxF; ++l)
     if (l < g.f) Q[row + (g.n + (int64_t)l * g.nb + s) * g.ldq] = acc[l];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_encode_horizontal(Geo g, const T* __restrict__ Gh, T* __restrict__ Q) {
+  encode_horizontal_body<T>(g, Gh, Q, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <typename T>
@@ -341,11 +356,10 @@ cudaError_t launch_poison(const Geo& g, const int* tiles, int count, T* Q, T* R,
 // rebuilt).  One CTA column per plan; the same kernel serves the vertical code of a Q grid
 // column (tile index along rows) and the horizontal code of an R block row (along columns).
 template <typename T>
-__global__ void __launch_bounds__(256) k_decode(Geo g, const DecodePlan* __restrict__ plans,
-                                                 const double* __restrict__ Gt,
-                                                 const double* __restrict__ Gh, T* Q, T* R,
-                                                 int* status) {
-  const DecodePlan& p = plans[blockIdx.z];
+__device__ __forceinline__ void decode_body(const Geo& g, const DecodePlan& p,
+                                            const double* __restrict__ Gt,
+                                            const double* __restrict__ Gh, T* Q, T* R,
+                                            int* status, int bx, int by) {
   const bool isQ = (p.kind == 0);
   const int nsys = p.nsys, f = g.f, f1 = p.f1, f2 = p.f2;
   __shared__ double Ginv[kMaxF * kMaxF];
@@ -383,7 +397,7 @@ __global__ void __launch_bounds__(256) k_decode(Geo g, const DecodePlan* __restr
     }
     for (int r = 0; r < f1; ++r)
       for (int q = 0; q < f1; ++q) Ginv[r * kMaxF + q] = a[r][f1 + q];
-    if (s_bad && blockIdx.x == 0 && blockIdx.y == 0) set_status(status, CQR_EUNRECOVERABLE, p.idx);
+    if (s_bad && bx == 0 && by == 0) set_status(status, CQR_EUNRECOVERABLE, p.idx);
   }
   __syncthreads();
   if (s_bad) return;
@@ -405,8 +419,8 @@ __global__ void __launch_bounds__(256) k_decode(Geo g, const DecodePlan* __restr
   }
   __syncthreads();
   const int64_t h = isQ ? g.mb : g.nb;
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t s = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+  const int64_t r = (int64_t)bx * blockDim.x + threadIdx.x;
+  const int64_t s = (int64_t)by * blockDim.y + threadIdx.y;
   if (r >= h || s >= g.nb) return;
   T* base = isQ ? Q + (int64_t)p.idx * g.nb * g.ldq : R + (int64_t)p.idx * g.nb;
   const int64_t tstride = isQ ? g.mb : g.nb * g.ldr;
@@ -445,6 +459,14 @@ __global__ void __launch_bounds__(256) k_decode(Geo g, const DecodePlan* __restr
 }
 
 template <typename T>
+__global__ void __launch_bounds__(256) k_decode(Geo g, const DecodePlan* __restrict__ plans,
+                                                 const double* __restrict__ Gt,
+                                                 const double* __restrict__ Gh, T* Q, T* R,
+                                                 int* status) {
+  decode_body<T>(g, plans[blockIdx.z], Gt, Gh, Q, R, status, blockIdx.x, blockIdx.y);
+}
+
+template <typename T>
 cudaError_t launch_decode(const Geo& g, const DecodePlan* plans_dev, int nplans, int max_h,
                           const double* Gt, const double* Gh, T* Q, T* R, int* status,
                           cudaStream_t st) {
@@ -463,11 +485,11 @@ cudaError_t launch_decode(const Geo& g, const DecodePlan* plans_dev, int nplans,
 // One thread per (local row, column): reads each Z_t once, writes each W_i once (in place
 // is safe: every thread owns one position across all block rows).
 template <typename T>
-__global__ void __launch_bounds__(256) k_post_orth(Geo g, const T* __restrict__ Gt, const T* Z,
-                                                    int64_t ldz, int64_t zrows, int64_t k, T* W,
-                                                    int64_t ldw) {
-  const int64_t s = (int64_t)blockIdx.x * 32 + threadIdx.x;
-  const int64_t col = (int64_t)blockIdx.y * 8 + threadIdx.y;
+__device__ __forceinline__ void post_orth_body(const Geo& g, const T* __restrict__ Gt, const T* Z,
+                                               int64_t ldz, int64_t zrows, int64_t k, T* W,
+                                               int64_t ldw, int bx, int by) {
+  const int64_t s = (int64_t)bx * 32 + threadIdx.x;
+  const int64_t col = (int64_t)by * 8 + threadIdx.y;
   if (s >= g.mb || col >= k) return;
   const int f = g.f, p_r = g.p_r;
   const T* zc = Z + col * ldz;
@@ -503,6 +525,13 @@ __global__ void __launch_bounds__(256) k_post_orth(Geo g, const T* __restrict__ 
 #pragma unroll
   for (int i = 0; i < kMaxF; ++i)
     if (i < f) wc[(int64_t)i * g.mb + s] = acc[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_post_orth(Geo g, const T* __restrict__ Gt, const T* Z,
+                                                    int64_t ldz, int64_t zrows, int64_t k, T* W,
+                                                    int64_t ldw) {
+  post_orth_body<T>(g, Gt, Z, ldz, zrows, k, W, ldw, blockIdx.x, blockIdx.y);
 }
 
 template <typename T>
@@ -748,6 +777,165 @@ cudaError_t launch_ls_cg(const T* Q, int64_t ldq, int64_t m, int64_t m_pad, int6
 }
 
 // ===================================================================== instantiations
+// ===================================================================== batches
+// Each batched kernel walks a flat list of virtual blocks; block v belongs to the instance i
+// with off[i] <= v < off[i+1] and plays block `v - off[i]` of that instance's own grid.
+__device__ __forceinline__ int find_instance(const int64_t* __restrict__ off, int count, int64_t v) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= v) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+int64_t batch_encode_blocks(const Geo& g, bool horizontal) {
+  if (horizontal && (!g.protect_r || g.f == 0)) return 0;
+  return ((g.mb + 31) / 32) * ((g.nb + 7) / 8) * (horizontal ? (g.p_r + g.f) : g.p_c);
+}
+int64_t batch_post_orth_blocks(const Geo& g) {
+  if (g.f == 0) return 0;
+  return ((g.mb + 31) / 32) * ((g.n + 7) / 8);
+}
+int64_t batch_decode_blocks(const Geo& g, const DecodePlan& p) {
+  const int64_t h = p.kind == 0 ? g.mb : g.nb;
+  return ((h + 31) / 32) * ((g.nb + 7) / 8);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_encode_vertical(const BatchInst<T>* __restrict__ inst,
+                                                            int count, const int64_t* __restrict__ off,
+                                                            const T* __restrict__ Gt) {
+  const int64_t total = off[count];
+  for (int64_t v = blockIdx.x; v < total; v += gridDim.x) {
+    const int i = find_instance(off, count, v);
+    const BatchInst<T>& I = inst[i];
+    int64_t loc = v - off[i];
+    const int64_t nbx = (I.g.mb + 31) / 32, nby = (I.g.nb + 7) / 8;
+    const int bx = (int)(loc % nbx);
+    loc /= nbx;
+    encode_vertical_body<T>(I.g, I.A, I.lda, Gt, I.Q, bx, (int)(loc % nby), (int)(loc / nby));
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_encode_horizontal(const BatchInst<T>* __restrict__ inst,
+                                                              int count, const int64_t* __restrict__ off,
+                                                              const T* __restrict__ Gh) {
+  const int64_t total = off[count];
+  for (int64_t v = blockIdx.x; v < total; v += gridDim.x) {
+    const int i = find_instance(off, count, v);
+    const BatchInst<T>& I = inst[i];
+    int64_t loc = v - off[i];
+    const int64_t nbx = (I.g.mb + 31) / 32, nby = (I.g.nb + 7) / 8;
+    const int bx = (int)(loc % nbx);
+    loc /= nbx;
+    encode_horizontal_body<T>(I.g, Gh, I.Q, bx, (int)(loc % nby), (int)(loc / nby));
+  }
+}
+
+template <typename T>
+cudaError_t launch_b_encode(const BatchInst<T>* inst, int count, const int64_t* off_v,
+                            int64_t total_v, const int64_t* off_h, int64_t total_h,
+                            const T* Gt_t, const T* Gh_t, int num_sms, cudaStream_t st) {
+  const dim3 blk(32, 8);
+  const int64_t cap = (int64_t)num_sms * 16;
+  if (total_v > 0) {
+    k_b_encode_vertical<T><<<(unsigned)std::min(total_v, cap), blk, 0, st>>>(inst, count, off_v, Gt_t);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (total_h > 0) {
+    k_b_encode_horizontal<T><<<(unsigned)std::min(total_h, cap), blk, 0, st>>>(inst, count, off_h, Gh_t);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_poison(const BatchInst<T>* __restrict__ inst,
+                                                   const BatchTile* __restrict__ tiles) {
+  const BatchTile t = tiles[blockIdx.y];
+  const Geo& g = inst[t.inst].g;
+  T* X = t.isR ? inst[t.inst].R : inst[t.inst].Q;
+  const int64_t ld = t.isR ? g.ldr : g.ldq;
+  const int64_t th = t.isR ? g.nb : g.mb, tw = g.nb;
+  const int64_t total = th * tw;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx % th, s = idx / th;
+    X[(int64_t)t.i * th + r + ((int64_t)t.j * tw + s) * ld] = nan_value<T>();
+  }
+}
+
+template <typename T>
+cudaError_t launch_b_poison(const BatchInst<T>* inst, const BatchTile* tiles, int count,
+                            int64_t max_elems, int num_sms, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  for (int base = 0; base < count; base += 65535) {
+    const int n = std::min(count - base, 65535);
+    const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (max_elems + 255) / 256));
+    k_b_poison<T><<<dim3(bx, (unsigned)n), 256, 0, st>>>(inst, tiles + base);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  (void)num_sms;
+  return cudaSuccess;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_decode(const BatchInst<T>* __restrict__ inst,
+                                                   const BatchPlan* __restrict__ plans, int nplans,
+                                                   const int64_t* __restrict__ off,
+                                                   const double* __restrict__ Gt,
+                                                   const double* __restrict__ Gh) {
+  const int64_t total = off[nplans];
+  for (int64_t v = blockIdx.x; v < total; v += gridDim.x) {
+    __syncthreads();  // the previous block's readers of the shared tableau are done
+    const int k = find_instance(off, nplans, v);
+    const BatchPlan& bp = plans[k];
+    const BatchInst<T>& I = inst[bp.inst];
+    const int64_t h = bp.p.kind == 0 ? I.g.mb : I.g.nb;
+    const int64_t nbx = (h + 31) / 32;
+    const int64_t loc = v - off[k];
+    decode_body<T>(I.g, bp.p, Gt, Gh, I.Q, I.R, I.status, (int)(loc % nbx), (int)(loc / nbx));
+  }
+}
+
+template <typename T>
+cudaError_t launch_b_decode(const BatchInst<T>* inst, const BatchPlan* plans, int nplans,
+                            const int64_t* off, int64_t total, const double* Gt, const double* Gh,
+                            int num_sms, cudaStream_t st) {
+  if (nplans == 0 || total == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>(total, (int64_t)num_sms * 8);
+  k_b_decode<T><<<grid, dim3(32, 8), 0, st>>>(inst, plans, nplans, off, Gt, Gh);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_post_orth(const BatchInst<T>* __restrict__ inst,
+                                                      int count, const int64_t* __restrict__ off,
+                                                      const T* __restrict__ Gt) {
+  const int64_t total = off[count];
+  for (int64_t v = blockIdx.x; v < total; v += gridDim.x) {
+    const int i = find_instance(off, count, v);
+    const BatchInst<T>& I = inst[i];
+    const int64_t nbx = (I.g.mb + 31) / 32;
+    const int64_t loc = v - off[i];
+    post_orth_body<T>(I.g, Gt, I.Q, I.g.ldq, I.g.m_pad, I.g.n, I.Q, I.g.ldq, (int)(loc % nbx),
+                      (int)(loc / nbx));
+  }
+}
+
+template <typename T>
+cudaError_t launch_b_post_orth(const BatchInst<T>* inst, int count, const int64_t* off,
+                               int64_t total, const T* Gt_t, int num_sms, cudaStream_t st) {
+  if (total == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>(total, (int64_t)num_sms * 16);
+  k_b_post_orth<T><<<grid, dim3(32, 8), 0, st>>>(inst, count, off, Gt_t);
+  return cudaGetLastError();
+}
+
 #define CQR_INSTANTIATE(T)                                                                        \
   template cudaError_t launch_generator<T>(int, int, int, uint64_t, int, double*, double*, T*,   \
                                            T*, cudaStream_t);                                     \
@@ -772,6 +960,16 @@ cudaError_t launch_ls_cg(const T* Q, int64_t ldq, int64_t m, int64_t m_pad, int6
                                        const T*, T*, double*, unsigned*, int*, int, cudaStream_t);
 
 CQR_INSTANTIATE(float)
+template cudaError_t launch_b_encode<float>(const BatchInst<float>*, int, const int64_t*, int64_t,
+                                            const int64_t*, int64_t, const float*, const float*,
+                                            int, cudaStream_t);
+template cudaError_t launch_b_poison<float>(const BatchInst<float>*, const BatchTile*, int, int64_t,
+                                            int, cudaStream_t);
+template cudaError_t launch_b_decode<float>(const BatchInst<float>*, const BatchPlan*, int,
+                                            const int64_t*, int64_t, const double*, const double*,
+                                            int, cudaStream_t);
+template cudaError_t launch_b_post_orth<float>(const BatchInst<float>*, int, const int64_t*,
+                                               int64_t, const float*, int, cudaStream_t);
 CQR_INSTANTIATE(double)
 
 }  // namespace cqr

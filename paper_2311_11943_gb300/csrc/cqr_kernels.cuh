@@ -103,4 +103,51 @@ cudaError_t launch_ls_cg(const T* Q, int64_t ldq, int64_t m, int64_t m_pad, int6
                          const T* y, T* x, double* ws, unsigned* bar, int* status, int num_sms,
                          cudaStream_t st);
 
+// ---------------------------------------------------------------- batches of instances
+// One instance of a batch of independent coded QRs (device copy).  Every batched launch maps
+// a flat list of "virtual blocks" onto the instances: off[i] .. off[i+1]-1 belong to
+// instance i (prefix sums over the per-instance block counts of the single-instance grid).
+template <typename T>
+struct BatchInst {
+  Geo g;
+  T* Q;             // encoded matrix, M x N, ld g.ldq
+  T* R;             // N x N, ld g.ldr
+  const T* A;       // input (encode), m x n, ld lda
+  int64_t lda;
+  int* status;      // this instance's status words
+  int b;            // panel width
+  int pad_;
+};
+
+struct BatchPlan {
+  int inst;
+  int pad_;
+  DecodePlan p;
+};
+
+struct BatchTile {  // one poisoned tile
+  int inst, i, j, isR;
+};
+
+// Virtual blocks of the single-instance encode / post-orth grids (32 x 8 threads per block).
+int64_t batch_encode_blocks(const Geo& g, bool horizontal);
+int64_t batch_post_orth_blocks(const Geo& g);
+int64_t batch_decode_blocks(const Geo& g, const DecodePlan& p);
+
+template <typename T>
+cudaError_t launch_b_encode(const BatchInst<T>* inst, int count, const int64_t* off_v,
+                            int64_t total_v, const int64_t* off_h, int64_t total_h,
+                            const T* Gt_t, const T* Gh_t, int num_sms, cudaStream_t st);
+template <typename T>
+cudaError_t launch_b_poison(const BatchInst<T>* inst, const BatchTile* tiles, int count,
+                            int64_t max_elems, int num_sms, cudaStream_t st);
+template <typename T>
+cudaError_t launch_b_decode(const BatchInst<T>* inst, const BatchPlan* plans, int nplans,
+                            const int64_t* off, int64_t total, const double* Gt, const double* Gh,
+                            int num_sms, cudaStream_t st);
+// Q_1 <- G_0 Q_1 in place for every instance.
+template <typename T>
+cudaError_t launch_b_post_orth(const BatchInst<T>* inst, int count, const int64_t* off,
+                               int64_t total, const T* Gt_t, int num_sms, cudaStream_t st);
+
 }  // namespace cqr
