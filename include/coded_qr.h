@@ -231,8 +231,8 @@ cqr_status coded_qr_panel_icgs_noalloc(int32_t dtype, int64_t M, int32_t bk, voi
  * gdist, tau, seed (one generator for every instance) and the stream of the configuration.
  * cfg->m and cfg->n are ignored; cfg->dtype must be CQR_F32 and cfg->mma CQR_MMA_SIMT
  * (CQR_ENOTSUP otherwise), cfg->reorth_block must be 0.  cfg->b in 1..64 fixes every panel
- * width; cfg->b == 0 picks each width from the instance's shape (the widest of 64/32/16 whose
- * per-CTA panel slice fits shared memory), which coded_qr_batched_autotune can then refine.
+ * width; cfg->b == 0 picks each width from the instance's shape (32 for n_i >= 96, else 16),
+ * which coded_qr_batched_autotune can then refine.
  * Every instance is factorised by one thread-block cluster of the persistent factor launch;
  * the results are those of the single-instance verbs up to rounding order.  Each instance
  * owns its encoded matrix Q (M_i x N_i) and R (N_i x N_i) inside the batch's device memory.
@@ -269,12 +269,15 @@ cqr_status coded_qr_batched_post_orth(cqr_batched bh);
  * graph is replayed while the erasure list, the inputs and the tuning stay the same. */
 cqr_status coded_qr_batched_run(cqr_batched bh, const void* const* A, const int64_t* lda,
                                 const int32_t* erasures, int32_t count, int32_t flags);
-/* Autotuner: times the batch factorisation of A (CUDA events, best of reps) over the
- * cluster sizes 1/2/4/8 and the width rules 16/32/64/shape-fit, then refines the width per
- * class of encoded height (< 1024, < 4096, >= 4096 rows); keeps the fastest and leaves the
- * batch encoded and factorised with it.  *cluster (host, optional) receives the cluster size. */
+/* Autotuner: times coded_qr_batched_run on A with the given erasure list (CUDA events, best
+ * of reps after one untimed run) over the cluster sizes 1/2/4/8 and the width rules
+ * 16/32/64/shape, then refines the width per class of encoded height (< 1024, < 4096,
+ * >= 4096 rows); keeps the fastest and leaves the batch encoded and factorised (without
+ * erasures) with it.  The erasure panels refer to the current widths; for other widths each
+ * event keeps its column position.  *cluster (host, optional) receives the cluster size. */
 cqr_status coded_qr_batched_autotune(cqr_batched bh, const void* const* A, const int64_t* lda,
-                                     int32_t reps, int32_t* cluster);
+                                     const int32_t* erasures, int32_t count, int32_t reps,
+                                     int32_t* cluster);
 /* Set / read the tuning: cluster size (1, 2, 4, 8) and the panel widths b[count] (host; NULL
  * on set: the shape rule).  Setting it requires a new encode. */
 cqr_status coded_qr_batched_set_tuning(cqr_batched bh, int32_t cluster, const int32_t* b);

@@ -99,7 +99,8 @@ def lib():
             "coded_qr_batched_recover": [vp, C.POINTER(i32)],
             "coded_qr_batched_post_orth": [vp],
             "coded_qr_batched_run": [vp, C.POINTER(vp), C.POINTER(i64), C.POINTER(i32), i32, i32],
-            "coded_qr_batched_autotune": [vp, C.POINTER(vp), C.POINTER(i64), i32, C.POINTER(i32)],
+            "coded_qr_batched_autotune": [vp, C.POINTER(vp), C.POINTER(i64), C.POINTER(i32), i32,
+                                          i32, C.POINTER(i32)],
             "coded_qr_batched_set_tuning": [vp, i32, C.POINTER(i32)],
             "coded_qr_batched_get_tuning": [vp, C.POINTER(i32), C.POINTER(i32)],
             "coded_qr_batched_get_factors": [vp, i32, C.POINTER(vp), C.POINTER(i64),
@@ -323,9 +324,11 @@ def coded_qr_batched_run(bh, A_ptrs, ldas, erasures, flags):
                                       flags)
 
 
-def coded_qr_batched_autotune(bh, A_ptrs, ldas, reps):
+def coded_qr_batched_autotune(bh, A_ptrs, ldas, erasures, reps):
     g = C.c_int32(0)
-    st = lib().coded_qr_batched_autotune(bh, _ptrs(A_ptrs), _i64s(ldas), reps, C.byref(g))
+    flat = [v for e in erasures for v in e]
+    st = lib().coded_qr_batched_autotune(bh, _ptrs(A_ptrs), _i64s(ldas), _i32s(flat),
+                                         len(erasures), reps, C.byref(g))
     return st, g.value
 
 
@@ -576,8 +579,8 @@ class CodedQRBatch:
         _bcheck(coded_qr_batched_run(self.h, *self._args(As), list(erasures), flags),
               "coded_qr_batched_run")
 
-    def autotune(self, As, reps=2):
-        st, g = coded_qr_batched_autotune(self.h, *self._args(As), reps)
+    def autotune(self, As, erasures=(), reps=2):
+        st, g = coded_qr_batched_autotune(self.h, *self._args(As), list(erasures), reps)
         _bcheck(st, "coded_qr_batched_autotune")
         self.geo = [coded_qr_batched_geometry(self.h, i) for i in range(self.count)]
         return g

@@ -96,13 +96,12 @@ cqr_status upload(cqr_batched bh, void* dst, const void* src, size_t bytes) {
   return CQR_OK;
 }
 
-// Panel width from the shape: the widest of 64, 32, 16 whose slice of one CTA fits the
-// shared-memory panel region; 16 (panel worked on in L2) when none does.
+// Panel width from the shape: 32 (fewer passes over the trailing columns) unless the
+// instance is narrow, where the ICGS column steps of a wide panel dominate.
 int fit_width(const Geo& g, int G, int cap) {
-  const int64_t rpc = ((g.M + G - 1) / G + 3) / 4 * 4;
-  for (int w : {64, 32, 16})
-    if (rpc * w <= cap) return w;
-  return 16;
+  (void)G;
+  (void)cap;
+  return g.n >= 96 ? 32 : 16;
 }
 
 cqr_status set_cluster(cqr_batched bh, int G) {
@@ -233,15 +232,6 @@ void reset_state(cqr_batched bh) {
   bh->post_orthed = false;
   bh->n_injected = bh->n_recovered = 0;
   bh->encoded = true;
-}
-
-cqr_status full_ranges(cqr_batched bh, int* d_range) {
-  std::vector<int> r(2 * bh->count);
-  for (int i = 0; i < bh->count; ++i) {
-    r[2 * i] = 0;
-    r[2 * i + 1] = bh->geo[i].panels;
-  }
-  return upload(bh, d_range, r.data(), sizeof(int) * r.size());
 }
 
 }  // namespace
@@ -680,35 +670,46 @@ cqr_status coded_qr_batched_get_tuning(cqr_batched bh, int32_t* cluster, int32_t
 }
 
 cqr_status coded_qr_batched_autotune(cqr_batched bh, const void* const* A, const int64_t* lda,
-                                     int32_t reps, int32_t* cluster_out) {
-  if (!bh || reps < 1) return CQR_EINVAL;
+                                     const int32_t* erasures, int32_t count, int32_t reps,
+                                     int32_t* cluster_out) {
+  if (!bh || reps < 1 || count < 0 || (count > 0 && !erasures)) return CQR_EINVAL;
   cqr_status s = check_inputs(bh, A, lda);
   if (s != CQR_OK) return s;
+  // the erasure panels are given for the shape rule's widths; a candidate with other widths
+  // keeps each event at the same column position (panel index rescaled, clamped)
+  std::vector<int> t_col(count);
+  for (int e = 0; e < count; ++e) {
+    const int k = erasures[4 * e];
+    if (k < 0 || k >= bh->count) return CQR_EINVAL;
+    t_col[e] = erasures[4 * e + 1] * bh->b[k];
+  }
   cudaEvent_t e0, e1;
   BK(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
     cudaEventDestroy(e0);
     return CQR_ECUDA;
   }
-  // time of the whole-batch factorisation under (G, widths): encode, then the best of `reps`
-  // factor launches (each preceded by a fresh encode)
+  // time of the whole sequence of coded_qr_batched_run (encode, factor, erase, recover,
+  // factor) under (G, widths): the best of `reps` runs, after one untimed run
+  std::vector<int32_t> er(erasures ? erasures : (const int32_t*)nullptr,
+                          erasures ? erasures + 4 * count : (const int32_t*)nullptr);
   auto measure = [&](int G, const std::vector<int>& w, float* ms) -> cqr_status {
     cqr_status r = coded_qr_batched_set_tuning(bh, G, w.data());
     if (r != CQR_OK) return r;
-    r = full_ranges(bh, bh->d_range_a);
-    if (r != CQR_OK) return r;
+    for (int e = 0; e < count; ++e) {
+      const int k = er[4 * e];
+      er[4 * e + 1] = std::min(t_col[e] / bh->b[k], bh->geo[k].panels - 1);
+    }
     float best = 1e30f;
-    for (int k = 0; k < reps; ++k) {
-      r = enqueue_encode(bh);
-      if (r != CQR_OK) return r;
+    for (int k = -1; k < reps; ++k) {
       BK(cudaEventRecord(e0, bh->st));
-      r = enqueue_factor(bh, bh->d_range_a, 0);
+      r = coded_qr_batched_run(bh, A, lda, er.data(), count, 0);
       if (r != CQR_OK) return r;
       BK(cudaEventRecord(e1, bh->st));
       BK(cudaEventSynchronize(e1));
       float t = 0.f;
       BK(cudaEventElapsedTime(&t, e0, e1));
-      best = std::min(best, t);
+      if (k >= 0) best = std::min(best, t);
     }
     *ms = best;
     return CQR_OK;
@@ -763,7 +764,7 @@ cqr_status coded_qr_batched_autotune(cqr_batched bh, const void* const* A, const
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != CQR_OK) return s;
-  // leave the batch encoded and factorised under the chosen tuning
+  // leave the batch encoded and factorised (no erasures) under the chosen tuning
   s = coded_qr_batched_set_tuning(bh, bestG, bestw.data());
   if (s == CQR_OK) s = coded_qr_batched_encode(bh, A, lda);
   if (s == CQR_OK) s = coded_qr_batched_factor(bh, nullptr);

@@ -32,7 +32,6 @@ namespace {
 
 constexpr int kBT = 512;        // threads per CTA
 constexpr int kBW = kBT / 32;   // warps per CTA
-constexpr int kKT = 32;         // rows per staged tile of the Rbar product
 
 __device__ __forceinline__ void cl_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
@@ -62,27 +61,35 @@ __device__ __forceinline__ int ld_cl_i32(uint32_t local_addr, uint32_t rank) {
 }
 
 // Shared-memory layout (in floats), the same for every CTA of a launch.
+//   small : v, eta, sv [kBMax each], warp partials [256]
+//   cpart : cluster partials, two buffers of kBMax * kWC (G > 1)
+//   rbar  : the summed Rbar chunk [kBMax][kWC]
+//   pool  : the stages of the trailing-update pipeline (B rows and Qbar rows, see b_update);
+//           after a K loop it holds the K-split partial sums (<= 8192 floats); during the
+//           panel it is scratch for per-CTA sums
+constexpr int kKT = 64;        // rows per pipeline stage
+constexpr int kLDS = kKT + 4;  // row stride of a staged column (16-byte aligned)
+constexpr int kMaxStages = 8;
+constexpr int kPanelScratch = 8192 + kBW * 2 * kBMax;  // per-CTA sums and warp partials
+
 struct BLayout {
-  int small;   // v [kBMax], eta [kBMax], sv [kBMax]
-  int wpart;   // panel: warp partials [kBW][2 kBMax]; GEMM: K-split partials [8192]
-  int stage;   // GEMM staging: As [kKT][kBMax + 4], Bs [kKT][kWC + 4]
-  int cpart;   // cluster partials [2][kBMax kWC] (G > 1)
-  int rbar;    // Rbar chunk [kBMax][kWC]
-  int panel;   // panel slice
-  int total;   // floats before the panel slice
+  int small, wpart, cpart, rbar, pool, total;
 };
 
 __host__ __device__ inline BLayout b_layout(int G) {
   BLayout L;
   L.small = 0;
   L.wpart = 3 * kBMax;
-  L.stage = L.wpart + 8192;
-  L.cpart = L.stage + kKT * (kBMax + 4) + kKT * (kWC + 4);
+  L.cpart = L.wpart + 256;
   L.rbar = L.cpart + (G > 1 ? 2 * kBMax * kWC : 0);
-  L.panel = L.rbar + kBMax * kWC;
-  L.total = L.panel;
+  L.pool = L.rbar + kBMax * kWC;
+  L.total = L.pool;
   return L;
 }
+
+// Floats of one pipeline stage for a panel of width bk: kWC columns of B and bk (rounded up
+// to 4) columns of Qbar, kKT rows each.
+__host__ __device__ inline int stage_floats(int bk) { return (kWC + (bk + 3) / 4 * 4) * kLDS; }
 
 template <int G>
 struct BCtx {
@@ -92,6 +99,28 @@ struct BCtx {
   uint32_t rank;
   unsigned step;  // reduction counter (same sequence on every CTA of the cluster)
 };
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Wait until at most n committed groups are pending (n is rounded down to 0 .. 6).
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_wait_dyn(int n) {
+  switch (n) {
+    case 6: cp_wait<6>(); break;
+    case 5: cp_wait<5>(); break;
+    case 4: cp_wait<4>(); break;
+    case 3: cp_wait<3>(); break;
+    case 2: cp_wait<2>(); break;
+    case 1: cp_wait<1>(); break;
+    default: cp_wait<0>(); break;
+  }
+}
 
 // Sum over the cluster of this CTA's values loc[0 .. n) (already summed over the CTA) into
 // out[0 .. n).  The partials go to the cpart buffer of parity `step`; a buffer is rewritten
@@ -119,54 +148,191 @@ __device__ __forceinline__ void cluster_sum(BCtx<G>& c, const float* loc, int n,
   __syncthreads();
 }
 
-// Column sums over the rows of this CTA's slice.  Values a in [0, nv): val(a, r) is the
-// summand of row r.  Warps form a (column group) x (row group) grid that depends on nv only.
-// The per-CTA result (warp partials summed in a fixed order) lands in loc[0 .. nv).
+// Warps form a (column group) x (row group) grid that depends on nv only: cg column groups
+// (a power of two <= min(nv, 16)), 16 / cg row groups; row group q covers rows
+// q*32 + lane + k*32*(16/cg).
+struct ColGrid {
+  int cg, rg, cgi, rgi;
+  __device__ ColGrid(int nv, int warp) {
+    cg = 1;
+    while (cg * 2 <= nv && cg * 2 <= kBW) cg *= 2;
+    rg = kBW / cg;
+    cgi = warp % cg;
+    rgi = warp / cg;
+  }
+};
+
+// Per-CTA column sums of a load-only summand val(a, r) for a in [0, nv), over rows [0, nr).
+// Four independent partial sums per lane keep several loads in flight; the combination order
+// is fixed.  Result in loc[0 .. nv) (after the CTA barrier inside).
 template <int G, typename F>
 __device__ __forceinline__ void cta_colsums(BCtx<G>& c, int nv, int nr, float* loc, F val) {
-  int cg = 1;
-  while (cg * 2 <= nv && cg * 2 <= kBW) cg *= 2;
-  const int rg = kBW / cg;
-  const int cgi = c.warp % cg, rgi = c.warp / cg;
-  float* wp = c.sm + c.L.wpart;  // [rg][nv]
-  for (int a = cgi; a < nv; a += cg) {
-    float s = 0.f;
-    for (int r = rgi * 32 + c.lane; r < nr; r += 32 * rg) s += val(a, r);
-    s = warp_sum(s);
-    if (c.lane == 0) wp[rgi * nv + a] = s;
+  const ColGrid cg(nv, c.warp);
+  float* wp = c.sm + c.L.wpart;  // [rg][nv], rg * nv <= 256
+  const int step = 32 * cg.rg;
+  for (int a = cg.cgi; a < nv; a += cg.cg) {
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int r = cg.rgi * 32 + c.lane;
+    for (; r + 3 * step < nr; r += 4 * step) {
+      s0 += val(a, r);
+      s1 += val(a, r + step);
+      s2 += val(a, r + 2 * step);
+      s3 += val(a, r + 3 * step);
+    }
+    for (; r < nr; r += step) s0 += val(a, r);
+    const float s = warp_sum((s0 + s1) + (s2 + s3));
+    if (c.lane == 0) wp[cg.rgi * nv + a] = s;
   }
   __syncthreads();
   for (int a = c.tid; a < nv; a += kBT) {
     float s = 0.f;
-    for (int q = 0; q < rg; ++q) s += wp[q * nv + a];
+    for (int q = 0; q < cg.rg; ++q) s += wp[q * nv + a];
     loc[a] = s;
+  }
+}
+
+// Rows of the slice per thread and block: thread t owns rows blk*RPT*kBT + t + k*kBT, k < RPT
+// (RPT = 4, 8 or 20 by the slice height, so that short slices run short loops).
+
+// Sum of one value per thread over the CTA for each of nv columns: warp shuffles, then a
+// fixed-order sum over the warps (wp: [kBW][nv] scratch) into loc (accumulate when add).
+__device__ __forceinline__ void warp_part(float s, int a, int nv, float* wp, int warp, int lane) {
+  s = warp_sum(s);
+  if (lane == 0) wp[warp * nv + a] = s;
+}
+
+// The fused column step of the panel, row-split: with q = p_j / r_jj and p' = p_{j+1} - q c1
+// (kept in registers for the thread's own rows and written back at once, since no other
+// thread reads these rows during the step),
+//   p_a -= q (v_a / r_jj) for a >= j+2, and per-CTA sums v'_a = p_a^T p' for a >= j+1
+//   (a = j+1 giving |p'|^2), into loc[0 .. bk-j-1).
+template <int G, int kRPT>
+__device__ __forceinline__ void cta_update_sums(BCtx<G>& c, float* P, int64_t cs, int nr, int bk,
+                                                int j, float inv, float c1, const float* v,
+                                                float* loc) {
+  constexpr int kRB = kRPT * kBT;
+  const int nv = bk - j - 1;
+  float* wp = c.sm + c.L.pool + 8192;  // [kBW][nv] (the pool is idle during the panel)
+  float* pj = P + j * cs;
+  float* pj1 = P + (j + 1) * cs;
+  for (int a = c.tid; a < nv; a += kBT) loc[a] = 0.f;
+  for (int blk = 0; blk * kRB < nr; ++blk) {
+    const int rb = blk * kRB + c.tid;
+    float q[kRPT], p1[kRPT];
+#pragma unroll
+    for (int k = 0; k < kRPT; ++k) {
+      const int r = rb + k * kBT;
+      q[k] = 0.f;
+      p1[k] = 0.f;
+      if (r < nr) {
+        q[k] = pj[r] * inv;
+        p1[k] = fmaf(-q[k], c1, pj1[r]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kRPT; ++k) {
+      const int r = rb + k * kBT;
+      if (r < nr) {
+        pj[r] = q[k];
+        pj1[r] = p1[k];
+      }
+    }
+    {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < kRPT; ++k) s = fmaf(p1[k], p1[k], s);
+      warp_part(s, 0, nv, wp, c.warp, c.lane);
+    }
+    for (int a1 = 1; a1 < nv; ++a1) {
+      float* pa = P + (j + 1 + a1) * cs;
+      const float ca = v[j + 1 + a1] * inv;
+      float x[kRPT];
+#pragma unroll
+      for (int k = 0; k < kRPT; ++k) {
+        const int r = rb + k * kBT;
+        x[k] = (r < nr) ? pa[r] : 0.f;
+      }
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < kRPT; ++k) {
+        const int r = rb + k * kBT;
+        x[k] = fmaf(-q[k], ca, x[k]);
+        if (r < nr) pa[r] = x[k];
+        s = fmaf(x[k], p1[k], s);
+      }
+      warp_part(s, a1, nv, wp, c.warp, c.lane);
+    }
+    __syncthreads();
+    for (int a = c.tid; a < nv; a += kBT) {
+      float t = 0.f;
+      for (int w = 0; w < kBW; ++w) t += wp[w * nv + a];
+      loc[a] += t;
+    }
+    __syncthreads();
+  }
+}
+
+// Step 0 of the panel, row-split: per-CTA v_a = p_a^T p_0 (loc[a]) and eta_a = p_a^T p_a
+// (loc[bk + a]).
+template <int G, int kRPT>
+__device__ __forceinline__ void cta_start_sums(BCtx<G>& c, const float* P, int64_t cs, int nr,
+                                               int bk, float* loc) {
+  constexpr int kRB = kRPT * kBT;
+  float* wp = c.sm + c.L.pool + 8192;  // [kBW][2 bk]
+  for (int a = c.tid; a < 2 * bk; a += kBT) loc[a] = 0.f;
+  for (int blk = 0; blk * kRB < nr; ++blk) {
+    const int rb = blk * kRB + c.tid;
+    float p0[kRPT];
+#pragma unroll
+    for (int k = 0; k < kRPT; ++k) {
+      const int r = rb + k * kBT;
+      p0[k] = (r < nr) ? P[r] : 0.f;
+    }
+    for (int a = 0; a < bk; ++a) {
+      const float* pa = P + a * cs;
+      float x[kRPT];
+#pragma unroll
+      for (int k = 0; k < kRPT; ++k) {
+        const int r = rb + k * kBT;
+        x[k] = (r < nr) ? pa[r] : 0.f;
+      }
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < kRPT; ++k) {
+        s0 = fmaf(x[k], p0[k], s0);
+        s1 = fmaf(x[k], x[k], s1);
+      }
+      warp_part(s0, a, 2 * bk, wp, c.warp, c.lane);
+      warp_part(s1, bk + a, 2 * bk, wp, c.warp, c.lane);
+    }
+    __syncthreads();
+    for (int a = c.tid; a < 2 * bk; a += kBT) {
+      float t = 0.f;
+      for (int w = 0; w < kBW; ++w) t += wp[w * 2 * bk + a];
+      loc[a] += t;
+    }
+    __syncthreads();
   }
 }
 
 // One panel: columns kb .. kb+bk-1 of the instance, this CTA's rows [0, nr) of the slice at
 // P (column stride cs).  Writes R's diagonal block (rank 0).  Returns false on breakdown.
-template <int G>
+template <int G, int RPT>
 __device__ bool b_panel(BCtx<G>& c, float* P, int64_t cs, int nr, int bk, float* R, int64_t ldr,
                         int kb, double tau2, int* status) {
   float* v = c.sm + c.L.small;
   float* eta = v + kBMax;
   float* sv = eta + kBMax;
-  float* loc = c.sm + c.L.stage;  // scratch for per-CTA sums (the GEMM staging is idle here)
+  float* loc = c.sm + c.L.pool;  // per-CTA sums (the pipeline stages are idle during the panel)
+  float* tmp = c.sm + c.L.rbar;  // cluster sums
   // step 0: v_a = p_a^T p_0 and eta_a = p_a^T p_a
-  cta_colsums<G>(c, 2 * bk, nr, loc, [&](int a, int r) {
-    if (a < bk) return P[r + a * cs] * P[r];
-    const float x = P[r + (a - bk) * cs];
-    return x * x;
-  });
-  {
-    float* tmp = c.sm + c.L.rbar;
-    cluster_sum<G>(c, loc, 2 * bk, tmp);
-    for (int a = c.tid; a < bk; a += kBT) {
-      v[a] = tmp[a];
-      eta[a] = tmp[bk + a];
-    }
-    __syncthreads();
+  cta_start_sums<G, RPT>(c, P, cs, nr, bk, loc);
+  cluster_sum<G>(c, loc, 2 * bk, tmp);
+  for (int a = c.tid; a < bk; a += kBT) {
+    v[a] = tmp[a];
+    eta[a] = tmp[bk + a];
   }
+  __syncthreads();
   for (int j = 0; j < bk; ++j) {
     if (j > 0 && tau2 > 0.0 && (double)v[j] < tau2 * (double)eta[j]) {
       // ICGS: project p_j once more on q_0 .. q_{j-1}
@@ -184,7 +350,6 @@ __device__ bool b_panel(BCtx<G>& c, float* P, int64_t cs, int nr, int bk, float*
       __syncthreads();
       cta_colsums<G>(c, bk - j, nr, loc,
                      [&](int a, int r) { return P[r + (j + a) * cs] * P[r + j * cs]; });
-      float* tmp = c.sm + c.L.rbar;
       cluster_sum<G>(c, loc, bk - j, tmp);
       for (int a = c.tid; a < bk - j; a += kBT) v[j + a] = tmp[a];
       __syncthreads();
@@ -206,139 +371,193 @@ __device__ bool b_panel(BCtx<G>& c, float* P, int64_t cs, int nr, int bk, float*
       break;
     }
     const float c1 = v[j + 1] * inv;
-    // p_a -= q_j R[j, a] for a >= j+2 (stored) and v'_a = p_a^T p'_{j+1} for a >= j+1, with
-    // q_j = p_j / r_jj and p'_{j+1} = p_{j+1} - q_j R[j, j+1] formed on the fly
-    cta_colsums<G>(c, bk - j - 1, nr, loc, [&](int a1, int r) {
-      const float q = P[r + j * cs] * inv;
-      const float p1 = fmaf(-q, c1, P[r + (j + 1) * cs]);
-      if (a1 == 0) return p1 * p1;
-      const int a = j + 1 + a1;
-      const float x = fmaf(-q, v[a] * inv, P[r + a * cs]);
-      P[r + a * cs] = x;
-      return x * p1;
-    });
-    // every read of columns j, j+1 is done: publish q_j and p'_{j+1}
-    for (int r = c.tid; r < nr; r += kBT) {
-      const float q = P[r + j * cs] * inv;
-      P[r + j * cs] = q;
-      P[r + (j + 1) * cs] = fmaf(-q, c1, P[r + (j + 1) * cs]);
-    }
-    {
-      float* tmp = c.sm + c.L.rbar;
-      cluster_sum<G>(c, loc, bk - j - 1, tmp);
-      for (int a = c.tid; a < bk - j - 1; a += kBT) v[j + 1 + a] = tmp[a];
-      __syncthreads();
-    }
+    cta_update_sums<G, RPT>(c, P, cs, nr, bk, j, inv, c1, v, loc);
+    cluster_sum<G>(c, loc, bk - j - 1, tmp);
+    for (int a = c.tid; a < bk - j - 1; a += kBT) v[j + 1 + a] = tmp[a];
+    __syncthreads();
   }
   return true;
 }
 
 // Trailing update of one panel on this CTA's rows, in chunks of kWC columns:
-//   S = Qbar^T B (per CTA, K-split over 4x4 register tiles), Rbar = cluster sum of S,
-//   R[kb.., col] = Rbar (rank 0), B -= Qbar Rbar.
-// Qbar: P (rows [0, nr), stride cs); B: Qs + col * ldq (rows [0, nr) of the slice).
+//   S = Qbar^T B over this CTA's rows: stages of kKT rows of B and of Qbar stream in through
+//       a cp.async pipeline as deep as the shared-memory pool allows (up to kMaxStages); each
+//       thread accumulates a 4 x 4 tile of S over a K-split share of four-row groups;
+//   Rbar = cluster sum of S (fixed order);  R[kb.., col] = Rbar (rank 0);
+//   B -= Qbar Rbar: the same stages stream in again, each thread updates four rows x two
+//       columns and stores them straight to global memory.
+// Qbar: P (global, rows [0, nr) of the slice, stride cs); B: Qs + col * ldq.
 template <int G>
 __device__ void b_update(BCtx<G>& c, const float* P, int64_t cs, int nr, int bk, float* Qs,
                          int64_t ldq, int64_t col_begin, int64_t col_end, float* R, int64_t ldr,
-                         int kb) {
-  float* spart = c.sm + c.L.wpart;
-  float* As = c.sm + c.L.stage;              // [kKT][kBMax + 4]
-  float* Bs = As + kKT * (kBMax + 4);        // [kKT][kWC + 4]
-  float* rbar = c.sm + c.L.rbar;             // [bk][kWC]
-  float* loc = spart;                        // per-CTA S after the K-split sum (first bk*kWC)
-  const int bkq = (bk + 3) / 4;              // row quads of S
+                         int kb, int pool_floats) {
+  float* pool = c.sm + c.L.pool;
+  float* spart = pool;             // K-split partials after the K loop
+  float* rbar = c.sm + c.L.rbar;   // [bk][kWC]
+  const int sf = stage_floats(bk);
+  int nst = pool_floats / sf;
+  if (nst > kMaxStages) nst = kMaxStages;
+  const int depth = nst - 1;       // stages in flight ahead of the one being consumed
+  const int bkq = (bk + 3) / 4;
   const int tiles = bkq * (kWC / 4);
-  const int ks_n = kBT / tiles >= 1 ? (kBT / tiles > 8 ? 8 : kBT / tiles) : 1;
+  int ks_n = kBT / tiles;
+  if (ks_n > 8) ks_n = 8;
+  if (ks_n < 1) ks_n = 1;
+  const int t_id = c.tid % tiles, ks = c.tid / tiles;
+  const bool active = c.tid < tiles * ks_n;
+  // a thread's S tile: columns ai + x bkq of Qbar and ji + 16 y of B (x, y < 4); neighbouring
+  // lanes read neighbouring staged columns, so the 16-byte shared loads do not conflict
+  const int ai = t_id % bkq, ji = t_id / bkq;
+  const int nkt = (nr + kKT - 1) / kKT;
+  const uint32_t pool_u = s_addr(pool);
+  // GEMM2 thread layout: rows 4*rq4 .. +3 of a stage, columns 2*cp, 2*cp+1
+  const int rq4 = c.tid % (kKT / 4), cp = c.tid / (kKT / 4);
   for (int64_t c0 = col_begin; c0 < col_end; c0 += kWC) {
-    const int wc = (int)std::min<int64_t>(kWC, col_end - c0);
-    // --- S = Qbar^T B over this CTA's rows
-    const int t = c.tid % tiles, ks = c.tid / tiles;
-    const bool active = ks < ks_n && c.tid < tiles * ks_n;
-    const int a0 = (t % bkq) * 4, j0 = (t / bkq) * 4;
+    const int wc = (int)((col_end - c0) < kWC ? (col_end - c0) : kWC);
+    // stage t: B rows [r0, r0 + kKT) x columns [c0, c0 + kWC), then Qbar rows [r0, r0 + kKT) x
+    // columns [0, bk), as 16-byte pieces (four rows of one column); rows >= nr and columns
+    // beyond the block are zero-filled.  One commit group per stage (empty past the end).
+    auto issue = [&](int t) {
+      if (t < nkt) {
+        const uint32_t base = pool_u + 4u * (uint32_t)((t % nst) * sf);
+        const int r0 = t * kKT;
+        for (int e = c.tid; e < (kWC + bkq * 4) * (kKT / 4); e += kBT) {
+          const int q4 = e % (kKT / 4), j = e / (kKT / 4);
+          const int r = r0 + 4 * q4;
+          const bool isB = j < kWC;
+          const int col = isB ? j : j - kWC;
+          const bool ok = (isB ? col < wc : col < bk) && r < nr;
+          const int nb = ok ? ((nr - r) >= 4 ? 16 : 4 * (nr - r)) : 0;
+          const float* src = isB ? Qs + (ok ? r : 0) + (c0 + (ok ? col : 0)) * ldq
+                                 : P + (ok ? r : 0) + (ok ? col : 0) * cs;
+          cp_async16(base + 4u * (uint32_t)(j * kLDS + 4 * q4), src, nb);
+        }
+      }
+      cp_commit();
+    };
+    auto stage = [&](int t) { return pool + (t % nst) * sf; };
+    // ---------------------------------------------------------------- S = Qbar^T B
     float acc[4][4];
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
       for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
-    for (int r0 = 0; r0 < nr; r0 += kKT) {
+    __syncthreads();  // the previous readers of the pool are done
+    for (int t = 0; t < depth; ++t) issue(t);
+    for (int t = 0; t < nkt; ++t) {
+      cp_wait_dyn(depth - 1);
+      __syncthreads();
+      issue(t + depth);
+      const int r0 = t * kKT;
       const int kr = (nr - r0) < kKT ? (nr - r0) : kKT;
-      __syncthreads();
-      for (int e = c.tid; e < kKT * kBMax; e += kBT) {
-        const int rr = e % kKT, a = e / kKT;
-        As[rr * (kBMax + 4) + a] = (rr < kr && a < bk) ? P[(r0 + rr) + a * cs] : 0.f;
-      }
-      for (int e = c.tid; e < kKT * kWC; e += kBT) {
-        const int rr = e % kKT, j = e / kKT;
-        Bs[rr * (kWC + 4) + j] = (rr < kr && j < wc) ? Qs[(r0 + rr) + (c0 + j) * ldq] : 0.f;
-      }
-      __syncthreads();
+      const int ng = (kr + 3) / 4;
       if (active) {
-        for (int rr = ks; rr < kr; rr += ks_n) {
-          const float4 av = *reinterpret_cast<const float4*>(As + rr * (kBMax + 4) + a0);
-          const float4 bv = *reinterpret_cast<const float4*>(Bs + rr * (kWC + 4) + j0);
-          const float ax[4] = {av.x, av.y, av.z, av.w};
-          const float bx[4] = {bv.x, bv.y, bv.z, bv.w};
+        const float* Bt = stage(t);
+        const float* At = Bt + kWC * kLDS;
+        for (int g4 = ks; g4 < ng; g4 += ks_n) {
+          const int rr = 4 * g4;
+          float4 qv[4], bv[4];
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+            qv[x] = (ai + x * bkq < bk) ? *reinterpret_cast<const float4*>(At + (ai + x * bkq) * kLDS + rr)
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int y = 0; y < 4; ++y)
+            bv[y] = *reinterpret_cast<const float4*>(Bt + (ji + 16 * y) * kLDS + rr);
 #pragma unroll
           for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(ax[x], bx[y], acc[x][y]);
+            for (int y = 0; y < 4; ++y) {
+              float a = acc[x][y];
+              a = fmaf(qv[x].x, bv[y].x, a);
+              a = fmaf(qv[x].y, bv[y].y, a);
+              a = fmaf(qv[x].z, bv[y].z, a);
+              a = fmaf(qv[x].w, bv[y].w, a);
+              acc[x][y] = a;
+            }
         }
       }
     }
+    cp_wait<0>();
     __syncthreads();
-    // K-split partials -> spart[ks][a][j] (ld kWC), then a fixed-order sum into loc
+    // K-split partials -> spart[ks][a][j] (ld kWC), then a fixed-order sum
     if (active)
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) spart[ks * (bkq * 4 * kWC) + (a0 + x) * kWC + j0 + y] = acc[x][y];
+        for (int y = 0; y < 4; ++y)
+          if (ai + x * bkq < bk) spart[ks * (bkq * 4 * kWC) + (ai + x * bkq) * kWC + ji + 16 * y] = acc[x][y];
     __syncthreads();
-    float sum_local[8];
-    int nloc = 0;
-    for (int e = c.tid; e < bk * kWC; e += kBT) {
-      float s = 0.f;
-      for (int q = 0; q < ks_n; ++q) s += spart[q * (bkq * 4 * kWC) + e];
-      sum_local[nloc++] = s;
+    if (G == 1) {
+      for (int e = c.tid; e < bk * kWC; e += kBT) {
+        float sum = 0.f;
+        for (int q = 0; q < ks_n; ++q) sum += spart[q * (bkq * 4 * kWC) + e];
+        rbar[e] = sum;
+      }
+      __syncthreads();
+    } else {
+      float* mine = c.sm + c.L.cpart + (c.step & 1) * (kBMax * kWC);
+      for (int e = c.tid; e < bk * kWC; e += kBT) {
+        float sum = 0.f;
+        for (int q = 0; q < ks_n; ++q) sum += spart[q * (bkq * 4 * kWC) + e];
+        mine[e] = sum;
+      }
+      cl_sync();
+      const uint32_t base = s_addr(mine);
+      for (int e = c.tid; e < bk * kWC; e += kBT) {
+        float sum = 0.f;
+#pragma unroll
+        for (int g = 0; g < G; ++g) sum += ld_cl(base + 4u * (uint32_t)e, (uint32_t)g);
+        rbar[e] = sum;
+      }
+      ++c.step;
+      __syncthreads();
     }
-    __syncthreads();
-    nloc = 0;
-    for (int e = c.tid; e < bk * kWC; e += kBT) loc[e] = sum_local[nloc++];
-    cluster_sum<G>(c, loc, bk * kWC, rbar);
     if (c.rank == 0)
       for (int e = c.tid; e < bk * wc; e += kBT) {
         const int a = e / wc, j = e % wc;
         R[(kb + a) + (c0 + j) * ldr] = rbar[a * kWC + j];
       }
-    // --- B -= Qbar Rbar on this CTA's rows (4 rows x 4 columns per thread and step)
-    const int rq = (nr + 3) / 4;
-    for (int e = c.tid; e < rq * (kWC / 4); e += kBT) {
-      const int r = (e % rq) * 4, j = (e / rq) * 4;
-      if (j >= wc) continue;
-      float o[4][4];
+    // ---------------------------------------------------------------- B -= Qbar Rbar
+    for (int t = 0; t < depth; ++t) issue(t);
+    for (int t = 0; t < nkt; ++t) {
+      cp_wait_dyn(depth - 1);
+      __syncthreads();
+      issue(t + depth);
+      const int r = t * kKT + 4 * rq4;
+      const int j = 2 * cp;
+      if (r < nr && j < wc) {
+        const float* Bt = stage(t);
+        const float* At = Bt + kWC * kLDS;
+        float o[4][2];
 #pragma unroll
-      for (int x = 0; x < 4; ++x)
+        for (int x = 0; x < 4; ++x) o[x][0] = o[x][1] = 0.f;
+        for (int a = 0; a < bk; ++a) {
+          const float4 q = *reinterpret_cast<const float4*>(At + a * kLDS + 4 * rq4);
+          const float2 rv = *reinterpret_cast<const float2*>(rbar + a * kWC + j);
+          o[0][0] = fmaf(q.x, rv.x, o[0][0]); o[0][1] = fmaf(q.x, rv.y, o[0][1]);
+          o[1][0] = fmaf(q.y, rv.x, o[1][0]); o[1][1] = fmaf(q.y, rv.y, o[1][1]);
+          o[2][0] = fmaf(q.z, rv.x, o[2][0]); o[2][1] = fmaf(q.z, rv.y, o[2][1]);
+          o[3][0] = fmaf(q.w, rv.x, o[3][0]); o[3][1] = fmaf(q.w, rv.y, o[3][1]);
+        }
 #pragma unroll
-        for (int y = 0; y < 4; ++y) o[x][y] = 0.f;
-      for (int a = 0; a < bk; ++a) {
-        float q[4];
+        for (int y = 0; y < 2; ++y) {
+          if (j + y >= wc) break;
+          const float4 b4 = *reinterpret_cast<const float4*>(Bt + (j + y) * kLDS + 4 * rq4);
+          float* dst = Qs + r + (c0 + j + y) * ldq;
+          if (r + 4 <= nr) {
+            *reinterpret_cast<float4*>(dst) =
+                make_float4(b4.x - o[0][y], b4.y - o[1][y], b4.z - o[2][y], b4.w - o[3][y]);
+          } else {
+            const float bb[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
-        for (int x = 0; x < 4; ++x) q[x] = (r + x < nr) ? P[(r + x) + a * cs] : 0.f;
-        const float4 rv = *reinterpret_cast<const float4*>(rbar + a * kWC + j);
-        const float rr4[4] = {rv.x, rv.y, rv.z, rv.w};
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 4; ++y) o[x][y] = fmaf(q[x], rr4[y], o[x][y]);
-      }
-#pragma unroll
-      for (int y = 0; y < 4; ++y) {
-        if (j + y >= wc) break;
-        float* bc = Qs + (c0 + j + y) * ldq;
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-          if (r + x < nr) bc[r + x] -= o[x][y];
+            for (int x = 0; x < 4; ++x)
+              if (r + x < nr) dst[x] = bb[x] - o[x][y];
+          }
+        }
       }
     }
+    cp_wait<0>();
   }
   __syncthreads();
 }
@@ -379,37 +598,39 @@ __global__ void __launch_bounds__(kBT, 1) k_b_factor(BatchInst<float>* __restric
     const int64_t rpc = ((g.M + G - 1) / G + 3) / 4 * 4;
     const int64_t row0 = (int64_t)c.rank * rpc;
     const int nr = (int)std::max<int64_t>(0, std::min<int64_t>(rpc, g.M - row0));
-    const int rpad = (nr + 3) / 4 * 4;
     float* Qs = I.Q + row0;
     bool ok = true;
     for (int k = pb; k < pe && ok; ++k) {
       const int kb = k * I.b;
       const int bk = (int)std::min<int64_t>(I.b, g.n - kb);
-      const bool in_smem = (int64_t)rpad * bk <= panel_cap;
-      float* P;
-      int64_t cs;
+      // ICGS on the panel slice: in the shared-memory pool (after the panel's scratch) when it
+      // fits, else in place in global memory (L2); the update then streams it from global
+      float* Pg = Qs + (int64_t)kb * g.ldq;
+      const int rpad = (nr + 3) / 4 * 4;
+      const bool in_smem = rpad * bk <= panel_cap - kPanelScratch;
+      float* P = in_smem ? smem + c.L.pool + kPanelScratch : Pg;
+      const int64_t cs = in_smem ? rpad : g.ldq;
       if (in_smem) {
-        P = smem + c.L.panel;
-        cs = rpad;
         for (int e = c.tid; e < rpad * bk; e += kBT) {
           const int r = e % rpad, a = e / rpad;
-          P[e] = (r < nr) ? Qs[r + (int64_t)(kb + a) * g.ldq] : 0.f;
+          P[e] = (r < nr) ? Pg[r + (int64_t)a * g.ldq] : 0.f;
         }
         __syncthreads();
-      } else {
-        P = Qs + (int64_t)kb * g.ldq;
-        cs = g.ldq;
       }
-      ok = b_panel<G>(c, P, cs, nr, bk, I.R, g.ldr, kb, tau2, I.status);
+      if (nr <= 4 * kBT)
+        ok = b_panel<G, 4>(c, P, cs, nr, bk, I.R, g.ldr, kb, tau2, I.status);
+      else if (nr <= 8 * kBT)
+        ok = b_panel<G, 8>(c, P, cs, nr, bk, I.R, g.ldr, kb, tau2, I.status);
+      else
+        ok = b_panel<G, 20>(c, P, cs, nr, bk, I.R, g.ldr, kb, tau2, I.status);
       if (!ok) break;
-      if (in_smem) {
+      if (in_smem)
         for (int e = c.tid; e < rpad * bk; e += kBT) {
           const int r = e % rpad, a = e / rpad;
-          if (r < nr) Qs[r + (int64_t)(kb + a) * g.ldq] = P[e];
+          if (r < nr) Pg[r + (int64_t)a * g.ldq] = P[e];
         }
-      }
       __syncthreads();
-      b_update<G>(c, P, cs, nr, bk, Qs, g.ldq, kb + bk, g.N, I.R, g.ldr, kb);
+      b_update<G>(c, Pg, g.ldq, nr, bk, Qs, g.ldq, kb + bk, g.N, I.R, g.ldr, kb, panel_cap);
     }
   }
   if (G > 1) cl_sync();  // peers may still read this CTA's shared memory
