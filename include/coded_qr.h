@@ -296,6 +296,30 @@ cqr_status coded_qr_batched_sync_status(cqr_batched bh, int32_t* first_bad, int6
 /* Name of the last CUDA error behind a CQR_ECUDA of a batch entry point on this host thread. */
 const char* coded_qr_batched_last_error(void);
 
+/* Reverse mode (no counterpart in the paper, which has no differentiation): gradients of a
+ * loss through the outputs of the coded method.  Both verbs need the handle after the last
+ * panel with no pending erasure; they ACCUMULATE into Abar (m x n, ld ldab) and ybar, use
+ * the handle's stream, and allocate scratch device memory on first use (kept until destroy).
+ *
+ * coded_qr_adjoint_qr: outputs Q = G_0 Q_1 (m_pad x n, as written by coded_qr_post_orth into
+ * a caller buffer) and the coded R (n x n) satisfy G_0 A = Q R with Q^T Q = I (Theorem on
+ * post-orthogonalisation, Section 4.3), so the thin-QR reverse rule applies to G_0 A:
+ *   M = R Rbar^T - Qbar^T Q,  Bbar = (Qbar + Q copyltu(M)) R^{-T},  Abar += G_0^T Bbar
+ * (copyltu(M) = tril(M) + tril(M,-1)^T; G_0 is symmetric).  Qbar (m_pad x n) or Rbar (n x n,
+ * only its upper triangle is meaningful) may be NULL, not both. */
+cqr_status coded_qr_adjoint_qr(cqr_handle h, const void* Q, int64_t ldq, const void* Qbar,
+                               int64_t ldqb, const void* Rbar, int64_t ldrb, void* Abar,
+                               int64_t ldab);
+/* coded_qr_adjoint_lstsq: x = argmin |A x - y| (x n x nrhs from coded_qr_solve on this handle,
+ * A m x n with full column rank, y m x nrhs).  With z = (A^T A)^{-1} xbar evaluated through the
+ * coded factors as R^{-1} (I - Q_2^T Q_2)^{-1} R^{-T} xbar (FP64 conjugate gradients for the
+ * middle factor) and r = y - A x:  Abar += r z^T - (A z) x^T,  ybar += A z.  Abar or ybar may
+ * be NULL.  Needs Q_1 in the handle (CQR_ESTATE after an in-place post-orthogonalisation). */
+cqr_status coded_qr_adjoint_lstsq(cqr_handle h, const void* A, int64_t lda, const void* y,
+                                  int64_t ldy, const void* x, int64_t ldx, const void* xbar,
+                                  int64_t ldxb, int32_t nrhs, void* Abar, int64_t ldab,
+                                  void* ybar, int64_t ldyb);
+
 /* Static description of a status code. */
 const char* coded_qr_errstr(cqr_status s);
 

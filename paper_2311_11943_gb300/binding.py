@@ -35,7 +35,8 @@ EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "
            "coded_qr_batched_post_orth", "coded_qr_batched_run", "coded_qr_batched_autotune",
            "coded_qr_batched_set_tuning", "coded_qr_batched_get_tuning",
            "coded_qr_batched_get_factors", "coded_qr_batched_get_decode_sets",
-           "coded_qr_batched_sync_status", "coded_qr_batched_last_error"]
+           "coded_qr_batched_sync_status", "coded_qr_batched_last_error",
+           "coded_qr_adjoint_qr", "coded_qr_adjoint_lstsq"]
 CQR_BATCH_GRAPH, CQR_BATCH_POST_ORTH = 1, 2
 PROF_CLASSES = 15
 
@@ -90,6 +91,9 @@ def lib():
             "coded_qr_profile": [vp, i32],
             "coded_qr_profile_read": [vp, C.POINTER(C.c_double), C.POINTER(i64), i32, i32],
             "coded_qr_panel_icgs_noalloc": [i32, i64, i32, vp, i64, vp, i64, C.c_double, vp, vp],
+            "coded_qr_adjoint_qr": [vp, vp, i64, vp, i64, vp, i64, vp, i64],
+            "coded_qr_adjoint_lstsq": [vp, vp, i64, vp, i64, vp, i64, vp, i64, i32, vp, i64, vp,
+                                       i64],
             "coded_qr_batched_create": [pcfg, C.POINTER(i64), C.POINTER(i64), i32, C.POINTER(vp)],
             "coded_qr_batched_destroy": [vp],
             "coded_qr_batched_geometry": [vp, i32, C.POINTER(i64)],
@@ -247,6 +251,17 @@ def coded_qr_panel_icgs_noalloc(dtype, M, bk, Q_ptr, ldq, R_ptr, ldr, tau=0.0, s
     return lib().coded_qr_panel_icgs_noalloc(dtype, M, bk, C.c_void_p(Q_ptr), ldq, C.c_void_p(R_ptr),
                                              ldr, tau, C.c_void_p(status_ptr or None),
                                              C.c_void_p(stream or None))
+
+
+def coded_qr_adjoint_qr(h, Q_ptr, ldq, Qbar_ptr, ldqb, Rbar_ptr, ldrb, Abar_ptr, ldab):
+    return lib().coded_qr_adjoint_qr(h, Q_ptr, ldq, Qbar_ptr or None, ldqb, Rbar_ptr or None, ldrb,
+                                     Abar_ptr, ldab)
+
+
+def coded_qr_adjoint_lstsq(h, A_ptr, lda, y_ptr, ldy, x_ptr, ldx, xbar_ptr, ldxb, nrhs, Abar_ptr,
+                           ldab, ybar_ptr, ldyb):
+    return lib().coded_qr_adjoint_lstsq(h, A_ptr, lda, y_ptr, ldy, x_ptr, ldx, xbar_ptr, ldxb, nrhs,
+                                        Abar_ptr or None, ldab, ybar_ptr or None, ldyb)
 
 
 def coded_qr_profile_name(k):
@@ -512,6 +527,25 @@ class CodedQR:
 
     def profile_read(self, reset=True):
         return coded_qr_profile_read(self.h, reset)
+
+    # -- reverse mode (accumulating into Abar / ybar)
+    def adjoint_qr(self, Q, Qbar, Rbar, Abar):
+        check(coded_qr_adjoint_qr(self.h, Q.data_ptr(), _ld(Q),
+                                  Qbar.data_ptr() if Qbar is not None else 0,
+                                  _ld(Qbar) if Qbar is not None else 0,
+                                  Rbar.data_ptr() if Rbar is not None else 0,
+                                  _ld(Rbar) if Rbar is not None else 0,
+                                  Abar.data_ptr(), _ld(Abar)), "coded_qr_adjoint_qr")
+
+    def adjoint_lstsq(self, A, y, x, xbar, Abar, ybar):
+        nrhs = 1 if x.dim() == 1 else x.shape[1]
+        check(coded_qr_adjoint_lstsq(self.h, A.data_ptr(), _ld(A), y.data_ptr(), _ld(y),
+                                     x.data_ptr(), _ld(x), xbar.data_ptr(), _ld(xbar), nrhs,
+                                     Abar.data_ptr() if Abar is not None else 0,
+                                     _ld(Abar) if Abar is not None else 0,
+                                     ybar.data_ptr() if ybar is not None else 0,
+                                     _ld(ybar) if ybar is not None else 0),
+              "coded_qr_adjoint_lstsq")
 
 
 class CodedQRBatch:

@@ -173,6 +173,9 @@ struct cqr_handle_s {
   std::vector<cudaEvent_t> prof_pool;
   double prof_ms[K_COUNT] = {0};
   int64_t prof_launches[K_COUNT] = {0};
+  // adjoint scratch (allocated by the first adjoint call)
+  void* adj = nullptr;
+  size_t adj_bytes = 0;
 };
 
 namespace {
@@ -629,6 +632,7 @@ cqr_status coded_qr_destroy(cqr_handle h) {
   if (h->plans_host) cudaFreeHost(h->plans_host);
   if (h->status_host) cudaFreeHost(h->status_host);
   if (h->owns_ws && h->ws) cudaFree(h->ws);
+  if (h->adj) cudaFree(h->adj);
   delete h;
   return CQR_OK;
 }
@@ -913,6 +917,126 @@ const char* coded_qr_errstr(cqr_status s) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------- adjoints
+namespace {
+
+cqr_status adj_scratch(cqr_handle h, size_t bytes) {
+  if (h->adj_bytes >= bytes) return CQR_OK;
+  CK(cudaStreamSynchronize(h->st));
+  if (h->adj) cudaFree(h->adj);
+  h->adj = nullptr;
+  h->adj_bytes = 0;
+  if (cudaMalloc(&h->adj, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return CQR_ENOMEM;
+  }
+  h->adj_bytes = bytes;
+  return CQR_OK;
+}
+
+template <typename T>
+cqr_status adjoint_qr_t(cqr_handle h, const T* Q, int64_t ldq, const T* Qbar, int64_t ldqb,
+                        const T* Rbar, int64_t ldrb, T* Abar, int64_t ldab) {
+  const Geo& g = h->g;
+  const int64_t n = g.n, mp = g.m_pad;
+  const size_t nn = (size_t)n * n;
+  cqr_status s = adj_scratch(h, sizeof(T) * (2 * nn + (size_t)mp * n));
+  if (s != CQR_OK) return s;
+  T* Mm = static_cast<T*>(h->adj);
+  T* S = Mm + nn;
+  T* Bb = S + nn;
+  const T* R = ptr<T>(h->B.R);
+  // M = R Rbar^T - Qbar^T Q
+  if (Rbar)
+    CK(launch_gemm_general<T>(0, 1, n, n, n, T(1), R, g.ldr, Rbar, ldrb, T(0), Mm, n, h->st));
+  else
+    CK(cudaMemsetAsync(Mm, 0, sizeof(T) * nn, h->st));
+  if (Qbar)
+    CK(launch_gemm_general<T>(1, 0, n, n, mp, T(-1), Qbar, ldqb, Q, ldq, T(1), Mm, n, h->st));
+  CK(launch_copyltu<T>(Mm, n, S, h->st));
+  // Bbar = Qbar + Q copyltu(M), then Bbar R^{-T}
+  if (Qbar)
+    CK(launch_axpy2d<T>(mp, n, T(1), Qbar, 1, ldqb, Bb, 1, mp, true, h->st));
+  CK(launch_gemm_general<T>(0, 0, mp, n, n, T(1), Q, ldq, S, n, Qbar ? T(1) : T(0), Bb, mp, h->st));
+  CK(launch_trsm_right<T>(1, R, g.ldr, n, Bb, 1, mp, mp, h->st));
+  // Abar += G_0^T Bbar (G_0 is symmetric: its leading block I - V V^T / 2 is), rows < m
+  if (g.f > 0) CK(launch_post_orth<T>(g, ptr<T>(h->B.Gt_t), Bb, mp, mp, n, Bb, mp, h->st));
+  CK(launch_axpy2d<T>(g.m, n, T(1), Bb, 1, mp, Abar, 1, ldab, false, h->st));
+  return CQR_OK;
+}
+
+template <typename T>
+cqr_status adjoint_lstsq_t(cqr_handle h, const T* A, int64_t lda, const T* y, int64_t ldy,
+                           const T* x, int64_t ldx, const T* xbar, int64_t ldxb, int32_t k,
+                           T* Abar, int64_t ldab, T* ybar, int64_t ldyb) {
+  const Geo& g = h->g;
+  const int64_t m = g.m, n = g.n;
+  cqr_status s = adj_scratch(h, sizeof(T) * ((size_t)2 * n * k + (size_t)2 * m * k));
+  if (s != CQR_OK) return s;
+  T* u = static_cast<T*>(h->adj);  // n x k: R^{-T} xbar, then z
+  T* w = u + (size_t)n * k;        // n x k
+  T* Az = w + (size_t)n * k;       // m x k
+  T* r = Az + (size_t)m * k;       // m x k
+  const T* R = ptr<T>(h->B.R);
+  // u = R^{-T} xbar: rows of the (k x n) view solve u^T R = xbar^T
+  CK(launch_axpy2d<T>(n, k, T(1), xbar, 1, ldxb, u, 1, n, true, h->st));
+  CK(launch_trsm_right<T>(0, R, g.ldr, n, u, n, 1, k, h->st));
+  // w = (I - Q_2^T Q_2)^{-1} u (FP64 conjugate gradients), z = R^{-1} w
+  for (int32_t j = 0; j < k; ++j)
+    CK(launch_ls_cg<T>(ptr<T>(h->B.Q), g.ldq, g.m, g.m_pad, g.c, n, nullptr, w + (size_t)j * n,
+                       h->B.cg, h->B.bar, h->B.status, h->num_sms, h->st, u + (size_t)j * n));
+  CK(launch_trsm_right<T>(1, R, g.ldr, n, w, n, 1, k, h->st));
+  const T* z = w;
+  // Az, r = y - A x
+  CK(launch_gemm_general<T>(0, 0, m, k, n, T(1), A, lda, z, n, T(0), Az, m, h->st));
+  CK(launch_axpy2d<T>(m, k, T(1), y, 1, ldy, r, 1, m, true, h->st));
+  CK(launch_gemm_general<T>(0, 0, m, k, n, T(-1), A, lda, x, ldx, T(1), r, m, h->st));
+  // Abar += r z^T - (A z) x^T;  ybar += A z
+  if (Abar) {
+    CK(launch_gemm_general<T>(0, 1, m, n, k, T(1), r, m, z, n, T(1), Abar, ldab, h->st));
+    CK(launch_gemm_general<T>(0, 1, m, n, k, T(-1), Az, m, x, ldx, T(1), Abar, ldab, h->st));
+  }
+  if (ybar) CK(launch_axpy2d<T>(m, k, T(1), Az, 1, m, ybar, 1, ldyb, false, h->st));
+  return CQR_OK;
+}
+
+}  // namespace
+
+cqr_status coded_qr_adjoint_qr(cqr_handle h, const void* Q, int64_t ldq, const void* Qbar,
+                               int64_t ldqb, const void* Rbar, int64_t ldrb, void* Abar,
+                               int64_t ldab) {
+  if (!h || !Q || !Abar || (!Qbar && !Rbar)) return CQR_EINVAL;
+  if (h->state != ST_FACTORED || h->pending || h->next_panel < h->g.panels) return CQR_ESTATE;
+  if (ldq < h->g.m_pad || (Qbar && ldqb < h->g.m_pad) || (Rbar && ldrb < h->g.n) ||
+      ldab < h->g.m)
+    return CQR_EINVAL;
+  return h->esz == 8
+             ? adjoint_qr_t<double>(h, (const double*)Q, ldq, (const double*)Qbar, ldqb,
+                                    (const double*)Rbar, ldrb, (double*)Abar, ldab)
+             : adjoint_qr_t<float>(h, (const float*)Q, ldq, (const float*)Qbar, ldqb,
+                                   (const float*)Rbar, ldrb, (float*)Abar, ldab);
+}
+
+cqr_status coded_qr_adjoint_lstsq(cqr_handle h, const void* A, int64_t lda, const void* y,
+                                  int64_t ldy, const void* x, int64_t ldx, const void* xbar,
+                                  int64_t ldxb, int32_t nrhs, void* Abar, int64_t ldab,
+                                  void* ybar, int64_t ldyb) {
+  if (!h || !A || !y || !x || !xbar || nrhs < 1 || (!Abar && !ybar)) return CQR_EINVAL;
+  if (h->state != ST_FACTORED || h->pending || h->next_panel < h->g.panels) return CQR_ESTATE;
+  if (h->postorth_inplace) return CQR_ESTATE;  // Q_1 was overwritten by G_0 Q_1
+  const Geo& g = h->g;
+  if (lda < g.m || ldy < g.m || ldx < g.n || ldxb < g.n || (Abar && ldab < g.m) ||
+      (ybar && ldyb < g.m))
+    return CQR_EINVAL;
+  return h->esz == 8
+             ? adjoint_lstsq_t<double>(h, (const double*)A, lda, (const double*)y, ldy,
+                                       (const double*)x, ldx, (const double*)xbar, ldxb, nrhs,
+                                       (double*)Abar, ldab, (double*)ybar, ldyb)
+             : adjoint_lstsq_t<float>(h, (const float*)A, lda, (const float*)y, ldy,
+                                      (const float*)x, ldx, (const float*)xbar, ldxb, nrhs,
+                                      (float*)Abar, ldab, (float*)ybar, ldyb);
+}
 
 // Host helpers shared with the batched entry points (coded_qr_batched.cu).
 namespace cqr {

@@ -665,8 +665,9 @@ cudaError_t launch_trsv_upper(const T* R, int64_t ldr, int64_t n, T* x, int64_t 
 template <typename T>
 __global__ void __launch_bounds__(256) k_ls_cg(const T* __restrict__ Q, int64_t ldq, int64_t m,
                                                 int64_t m_pad, int64_t c, int64_t n,
-                                                const T* __restrict__ y, T* __restrict__ x,
-                                                double* ws, int maxit, unsigned* bar, int* status) {
+                                                const T* __restrict__ y, const T* __restrict__ u,
+                                                T* __restrict__ x, double* ws, int maxit,
+                                                unsigned* bar, int* status) {
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int64_t gw = (int64_t)g * 8 + warp, nw = (int64_t)G * 8;  // global warp index
@@ -698,13 +699,17 @@ __global__ void __launch_bounds__(256) k_ls_cg(const T* __restrict__ Q, int64_t 
     *out = t;
     return true;
   };
-  // z = Q_1^T y (warp per column), w = 0, r = p = z
+  // z = Q_1^T y (warp per column), or z = u when the right-hand side is given; w = 0, r = p = z
   double zz_loc = 0.0;
   for (int64_t j = gw; j < n; j += nw) {
-    const T* qj = Q + j * ldq;
     double acc = 0.0;
-    for (int64_t i = lane; i < m; i += 32) acc += (double)qj[i] * (double)y[i];
-    acc = warp_sum(acc);
+    if (u) {
+      acc = (double)u[j];
+    } else {
+      const T* qj = Q + j * ldq;
+      for (int64_t i = lane; i < m; i += 32) acc += (double)qj[i] * (double)y[i];
+      acc = warp_sum(acc);
+    }
     if (lane == 0) {
       z[j] = acc; w[j] = 0.0; r[j] = acc; p[j] = acc;
       zz_loc += acc * acc;
@@ -763,7 +768,7 @@ __global__ void __launch_bounds__(256) k_ls_cg(const T* __restrict__ Q, int64_t 
 template <typename T>
 cudaError_t launch_ls_cg(const T* Q, int64_t ldq, int64_t m, int64_t m_pad, int64_t c, int64_t n,
                          const T* y, T* x, double* ws, unsigned* bar, int* status, int num_sms,
-                         cudaStream_t st) {
+                         cudaStream_t st, const T* u) {
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   int G = (int)((n + 255) / 256);
@@ -772,7 +777,8 @@ cudaError_t launch_ls_cg(const T* Q, int64_t ldq, int64_t m, int64_t m_pad, int6
   if (G > num_sms) G = num_sms;
   if (G < 1) G = 1;
   int maxit = 200;
-  void* args[] = {(void*)&Q, &ldq, &m, &m_pad, &c, &n, (void*)&y, &x, &ws, &maxit, &bar, &status};
+  void* args[] = {(void*)&Q, &ldq, &m, &m_pad, &c, &n, (void*)&y, (void*)&u, &x, &ws, &maxit,
+                  &bar, &status};
   return cudaLaunchCooperativeKernel((const void*)k_ls_cg<T>, dim3(G), dim3(256), args, 0, st);
 }
 
@@ -957,7 +963,8 @@ cudaError_t launch_b_post_orth(const BatchInst<T>* inst, int count, const int64_
   template cudaError_t launch_trsv_upper<T>(const T*, int64_t, int64_t, T*, int64_t, int64_t,    \
                                             unsigned*, int*, int, cudaStream_t);                   \
   template cudaError_t launch_ls_cg<T>(const T*, int64_t, int64_t, int64_t, int64_t, int64_t,     \
-                                       const T*, T*, double*, unsigned*, int*, int, cudaStream_t);
+                                       const T*, T*, double*, unsigned*, int*, int, cudaStream_t,  \
+                                       const T*);
 
 CQR_INSTANTIATE(float)
 template cudaError_t launch_b_encode<float>(const BatchInst<float>*, int, const int64_t*, int64_t,

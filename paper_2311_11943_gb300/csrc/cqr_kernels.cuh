@@ -98,10 +98,29 @@ cudaError_t launch_trsv_upper(const T* R, int64_t ldr, int64_t n, T* x, int64_t 
 
 // Tall least squares through the coded factors: x (n, one column) = (I - Q_2^T Q_2)^{-1} Q_1^T y
 // by conjugate gradients in FP64 (cooperative launch); ws holds 7 n + c + 2 #SMs doubles.
+// With u non-null the right-hand side is u (n entries) instead of Q_1^T y.
 template <typename T>
 cudaError_t launch_ls_cg(const T* Q, int64_t ldq, int64_t m, int64_t m_pad, int64_t c, int64_t n,
                          const T* y, T* x, double* ws, unsigned* bar, int* status, int num_sms,
-                         cudaStream_t st);
+                         cudaStream_t st, const T* u = nullptr);
+
+// ---------------------------------------------------------------- adjoint building blocks
+// C (M x N) = alpha op(A) op(B) + beta C (op = transpose when ta / tb); beta == 0 ignores C.
+template <typename T>
+cudaError_t launch_gemm_general(int ta, int tb, int64_t M, int64_t N, int64_t K, T alpha,
+                                const T* A, int64_t lda, const T* B, int64_t ldb, T beta, T* C,
+                                int64_t ldc, cudaStream_t st);
+// S = tril(M) + tril(M, -1)^T (n x n, ld n).
+template <typename T>
+cudaError_t launch_copyltu(const T* Mm, int64_t n, T* S, cudaStream_t st);
+// Y += alpha X (or Y = alpha X when overwrite); element (i, j) at i rs + j cs.
+template <typename T>
+cudaError_t launch_axpy2d(int64_t rows, int64_t cols, T alpha, const T* X, int64_t xrs, int64_t xcs,
+                          T* Y, int64_t yrs, int64_t ycs, bool overwrite, cudaStream_t st);
+// X op(R) = B in place, R n x n upper; trans = 1: X R^T = B; trans = 0: X R = B.
+template <typename T>
+cudaError_t launch_trsm_right(int trans, const T* R, int64_t ldr, int64_t n, T* B, int64_t rs,
+                              int64_t cs, int64_t m, cudaStream_t st);
 
 // ---------------------------------------------------------------- batches of instances
 // One instance of a batch of independent coded QRs (device copy).  Every batched launch maps

@@ -436,3 +436,13 @@ def test_block_reorth_keeps_factorisation_and_restores_orthogonality():
     Qh, Rh = np.linalg.qr(At[:, :n])
     Rh = Rh * np.sign(np.diag(Rh))[:, None]
     assert np.abs(two["R"][:n, :n] - Rh).max() < 100 * u * kappa * np.abs(Rh).max()
+
+
+def test_G0_is_symmetric():
+    # G_0 = [[I + G~_1, V~], [V~^T, -I]] (x) I_mb with G~_1 = -V~ V~^T / 2 symmetric, so
+    # G_0^T = G_0: the reverse pass applies G_0^T with the post-orthogonalisation pipeline
+    for (p_r, f, gdist) in [(4, 1, 0), (8, 2, 0), (6, 3, 1)]:
+        g = O.geom(5 * p_r, 8, p_r, 8, f, True)
+        Gt, _ = O.generator(f, p_r, 8, 17, gdist)
+        G0 = O.build_G0(g, Gt)
+        assert np.array_equal(G0, G0.T)
