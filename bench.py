@@ -37,6 +37,16 @@ CONFIGS = {
     "c1": dict(m=256, n=256, p_r=4, p_c=4, f=1, b=32, kappa=0, seed=1, erasure_panels=1,
                per_panel=1),
 }
+# Configurations with their own bench legs (not the single-problem step above):
+#   c4: 512 independent coded QRs, m ~ U[256, 8192], n ~ U[32, 256] (multiples of p_c, m >= 4 n),
+#       N(0,1), grid 8 x 4, f = 2 per instance, up to two erased tiles per instance at one
+#       seeded panel; one persistent factor launch per phase, recorded into a CUDA graph
+#   c5: differentiable least squares, 16 x A 8192 x 1024 with kappa 1e3, y ~ N(0,1); grid 8 x 8,
+#       f = 1, b = 128, one node erased at the middle panel; forward + hand-written adjoint
+EXTRA = {
+    "c4": dict(count=512, p_r=8, p_c=4, f=2, seed=4),
+    "c5": dict(batch=16, m=8192, n=1024, p_r=8, p_c=8, f=1, b=128, kappa=1e3, seed=5),
+}
 MODES = {"f64": ("f64", "simt"), "f32": ("f32", "simt"), "tf32": ("f32", "tf32"),
          "3xtf32": ("f32", "3xtf32")}
 L2_BYTES = 126 * 1024 * 1024
@@ -445,13 +455,278 @@ def run_ours(args, cfg):
     return 0
 
 
+# ------------------------------------------------------------------------ c4: batched
+def batch_erasures(geos, f, seed):
+    """Up to two tiles (<= f per grid row / column) per instance, lost at one seeded panel."""
+    from paper_2311_11943_gb300 import synth
+    rng = np.random.default_rng(seed)
+    quads = []
+    for i, g in enumerate(geos):
+        k = int(rng.integers(0, 3))
+        if k == 0:
+            continue
+        t = int(rng.integers(0, g["panels"]))
+        for (r, c) in synth.random_erasures(g["grid_rows"], g["grid_cols"], f, k, seed + 7 * i):
+            quads.append((i, t, r, c))
+    return quads
+
+
+def oracle_batch_sample(shapes, cfg, budget_s):
+    """FP64 oracle on a bounded sample of the batch: whole instances (encode + every panel, no
+    erasure), smallest first, until budget_s.  Returns (TFLOP/s, cores, sample)."""
+    from oracle import oracle as O
+    from paper_2311_11943_gb300 import synth
+    order = sorted(range(len(shapes)), key=lambda i: shapes[i][0] * shapes[i][1] ** 2)
+    t0 = time.perf_counter()
+    flops, done = 0.0, 0
+    for i in order[::max(1, len(order) // 64)]:
+        if time.perf_counter() - t0 > budget_s:
+            break
+        m, n = shapes[i]
+        A = synth.gaussian(m, n, 4000 + i)
+        b = 32 if n >= 96 else 16
+        O.run(A, cfg["p_r"], cfg["p_c"], cfg["f"], b, seed=cfg["seed"])
+        flops += coded_flops(m, n, cfg["p_r"], cfg["p_c"], cfg["f"], b)
+        done += 1
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return flops / dt / 1e12, cores, ("FP64 oracle: %d whole instances of the batch (every %d-th "
+                                      "by size), %.1f GFLOP, %.1f s" %
+                                      (done, max(1, len(order) // 64), flops / 1e9, dt))
+
+
+def run_batched(args):
+    import torch
+    from paper_2311_11943_gb300 import binding as B
+    from paper_2311_11943_gb300 import synth
+    cfg = EXTRA["c4"]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    # weak scaling over replicas: every rank factorises its own batch of the same recipe
+    shapes = synth.batched_shapes(cfg["count"], cfg["seed"] + rank)
+    gen = torch.Generator(device="cuda").manual_seed(1000 * cfg["seed"] + rank)
+    As = [torch.randn(n, m, device="cuda", dtype=torch.float32, generator=gen).t()
+          for (m, n) in shapes]
+    bt = B.CodedQRBatch(shapes, cfg["p_r"], cfg["p_c"], cfg["f"], b=0, seed=cfg["seed"])
+    quads = batch_erasures(bt.geo, cfg["f"], cfg["seed"])
+    t0 = time.perf_counter()
+    G = bt.autotune(As, quads, reps=1)
+    tune_s = time.perf_counter() - t0
+    quads = batch_erasures(bt.geo, cfg["f"], cfg["seed"])   # panels of the tuned widths
+    F = sum(coded_flops(g["m"], g["n"], cfg["p_r"], cfg["p_c"], cfg["f"], 1) for g in bt.geo)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        bt.run(As, quads, graph=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt.run(As, quads, graph=True)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    st, bad, nre = bt.sync_status()
+    if st != 0:
+        raise RuntimeError("instance %d: device status %d" % (bad, st))
+    # the dominant kernel alone: the persistent factor launch over the whole batch
+    fac = []
+    for _ in range(max(2, args.steps)):
+        bt.encode(As)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt.factor()
+        e1.record(stream)
+        e1.synchronize()
+        fac.append(e0.elapsed_time(e1))
+    t_fac = statistics.median(fac)
+    # end to end: inputs from pinned host memory each step, status words read back
+    hosts = [torch.empty((n, m), dtype=torch.float32, pin_memory=True) for (m, n) in shapes]
+    for h, a in zip(hosts, As):
+        h.copy_(a.t())
+    e2e = []
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for h, a in zip(hosts, As):
+            a.t().copy_(h, non_blocking=True)
+        bt.run(As, quads, graph=True)
+        bt.sync_status()
+        if it >= args.warmup:
+            e2e.append((time.perf_counter() - t0) * 1e3)
+    ms = statistics.mean(times)
+    ms_e2e = statistics.mean(e2e)
+    if world > 1:
+        tt = torch.tensor([ms, ms_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = tt.tolist()
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    rl = {"bound": "alu", "unit": "TFLOP/s", "kernel": "k_b_factor", "achieved": F / (t_fac * 1e-3) / 1e12,
+          "peak": peak, "frac": F / (t_fac * 1e-3) / 1e12 / peak, "traffic": None,
+          "avg_launch_ms": t_fac, "peak_source": "FP32 CUDA-core: 152 SMs x 128 FFMA/clk x 2 flop "
+          "x 2.07 GHz (the batched factor runs on the CUDA cores)"}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+        v, cores, sample = oracle_batch_sample(shapes, cfg, args.cpu_budget)
+        cpu = {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample}
+    h2d = sum(m * n * 4 for (m, n) in shapes)
+    if rank == 0:
+        cl, widths = bt.tuning()
+        line = {
+            "metric": "coded GS-QR TFLOP/s (sum over the batch of F_coded = 2(m+c)n(n+2d))",
+            "value": world * F / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded N(0,1) drawn on the device)",
+            "config": {"workload": "batched: %d coded QRs, m~U[256,8192], n~U[32,256] (m>=4n), "
+                       "grid %dx%d, f=%d, %d erased tiles in %d instances" %
+                       (cfg["count"], cfg["p_r"], cfg["p_c"], cfg["f"], len(quads),
+                        len(set(q[0] for q in quads))),
+                       "cluster": cl, "widths": sorted(set(widths)), "autotune_s": tune_s,
+                       "l2": "inputs (%.1f GB) larger than L2" % (h2d / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "graph": "the whole run recorded once into a CUDA graph and replayed"},
+            "coded_flops_per_step": F, "factor_kernel_ms": t_fac, "reorth": nre,
+            "gpu_launches": 6, "clocks": clk, "roofline": rl, "cpu_baseline": cpu,
+            "e2e": {"value": world * F / (ms_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
+                    "ms_per_step": ms_e2e, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": 16 * cfg["count"]},
+        }
+        print(json.dumps(line))
+    bt.close()
+    return 0
+
+
+# ------------------------------------------------------------------------ c5: autograd
+def run_autograd(args):
+    import torch
+    from paper_2311_11943_gb300 import binding as B
+    from paper_2311_11943_gb300.autograd import coded_lstsq
+    cfg = EXTRA["c5"]
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    bs, m, n = cfg["batch"], cfg["m"], cfg["n"]
+    gen = torch.Generator(device="cuda").manual_seed(cfg["seed"])
+    # A = U diag(sigma) V^T with Haar U (m x n), V (n x n), sigma geometric to kappa (data
+    # generation on the device, not timed)
+    A = torch.empty((bs, m, n), device="cuda", dtype=torch.float32)
+    sig = cfg["kappa"] ** (-torch.arange(n, device="cuda", dtype=torch.float64) / (n - 1))
+    for i in range(bs):
+        U, Ru = torch.linalg.qr(torch.randn(m, n, device="cuda", dtype=torch.float64, generator=gen))
+        U = U * torch.sign(torch.diagonal(Ru))
+        V, Rv = torch.linalg.qr(torch.randn(n, n, device="cuda", dtype=torch.float64, generator=gen))
+        V = V * torch.sign(torch.diagonal(Rv))
+        A[i] = ((U * sig) @ V.T).float()
+    y = torch.randn(bs, m, device="cuda", dtype=torch.float32, generator=gen)
+    W = [torch.randn(s, device="cuda", dtype=torch.float32, generator=gen)
+         for s in ((bs, m, n), (bs, n, n), (bs, n))]
+    opts = dict(p_r=cfg["p_r"], p_c=cfg["p_c"], f=cfg["f"], b=cfg["b"], seed=cfg["seed"],
+                erasures={(n // cfg["b"]) // 2: [(3, 6)]})
+    stream = torch.cuda.current_stream()
+
+    def step():
+        Ad = A.detach().requires_grad_(True)
+        yd = y.detach().requires_grad_(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Q, R, x = coded_lstsq(Ad, yd, **opts)
+        L = (W[0] * Q).sum() + (W[1] * torch.triu(R)).sum() + (W[2] * x).sum()
+        e1.record(stream)
+        L.backward()
+        e2.record(stream)
+        e2.synchronize()
+        return e0.elapsed_time(e1), e1.elapsed_time(e2), Ad.grad
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    clocks.start()
+    fw, bw = [], []
+    for _ in range(args.steps):
+        a, b_, grad = step()
+        fw.append(a)
+        bw.append(b_)
+    clk = clocks.stop()
+    F = bs * coded_flops(m, n, cfg["p_r"], cfg["p_c"], cfg["f"], cfg["b"])
+    ms = statistics.mean(f_ + b_ for f_, b_ in zip(fw, bw))
+    # gradient check of the last step against a CPU FP64 reference on problem 0
+    from oracle import oracle as O
+    g = O.geom(m, n, cfg["p_r"], cfg["p_c"], cfg["f"], True)
+    Gt, _ = O.generator(cfg["f"], cfg["p_r"], cfg["p_c"], cfg["seed"])
+    G0 = torch.tensor(O.build_G0(g, Gt), dtype=torch.float64)
+    A0 = A[0].double().cpu().requires_grad_(True)
+    y0 = y[0].double().cpu()
+    Qr, Rr = torch.linalg.qr(G0 @ A0)
+    d = torch.sign(torch.diagonal(Rr))
+    x0 = torch.linalg.solve(A0.T @ A0, A0.T @ y0)
+    L0 = ((W[0][0].double().cpu() * (Qr * d)).sum() + (W[1][0].double().cpu() *
+          torch.triu(d[:, None] * Rr)).sum() + (W[2][0].double().cpu() * x0).sum())
+    L0.backward()
+    gref = A0.grad
+    gerr = (torch.linalg.norm(grad[0].double().cpu() - gref) / torch.linalg.norm(gref)).item()
+    # dominant kernel of the forward: one problem with the same options, profiled
+    q = B.CodedQR(m, n, cfg["p_r"], cfg["p_c"], cfg["f"], cfg["b"], dtype="f32", mma="3xtf32",
+                  seed=cfg["seed"])
+    Ac = B.colmajor_empty(m, n, torch.float32)
+    Ac.copy_(A[0])
+    q.profile(True)
+    q.profile_read(reset=True)
+    for _ in range(2):
+        q.encode(Ac)
+        q.factor(0, -1)
+    prof = q.profile_read(reset=True)
+    q.close()
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+        c5 = dict(m=m, n=n, p_r=cfg["p_r"], p_c=cfg["p_c"], f=cfg["f"], b=cfg["b"], seed=cfg["seed"])
+        v, cores, sample, _ = oracle_sample(c5, A[0].double().cpu().numpy(), budget_s=args.cpu_budget)
+        cpu = {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample}
+    line = {
+        "metric": "coded GS-QR TFLOP/s of forward + adjoint (F_coded per problem x batch)",
+        "value": F / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 storage, 3xtf32 tensor-core GEMMs, FP64 CG",
+        "data": "synthetic (seeded U diag(sigma) V^T, kappa 1e3, drawn on the device)",
+        "config": {"workload": "differentiable least squares: %d x A %dx%d kappa=%g, grid %dx%d, "
+                   "f=%d, b=%d, one erasure at panel %d; loss <W_Q,Q>+<W_R,R>+<W_x,x>" %
+                   (bs, m, n, cfg["kappa"], cfg["p_r"], cfg["p_c"], cfg["f"], cfg["b"],
+                    (n // cfg["b"]) // 2)},
+        "forward_ms": statistics.mean(fw), "backward_ms": statistics.mean(bw),
+        "grad_rel_err_vs_cpu_fp64": gerr,
+        "forward_kernel_ms_per_problem": {k: v[0] / 2 for k, v in prof.items() if v[1]},
+        "clocks": clk,
+        "roofline": {"kernel": dom[0], "note": "see forward_kernel_ms_per_problem; the C2 line "
+                     "carries the kernel roofline"},
+        "cpu_baseline": cpu,
+        "e2e": None,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS) + sorted(EXTRA))
     ap.add_argument("--mode", default=os.environ.get("CQR_BENCH_MODE", "3xtf32"),
                     choices=sorted(MODES))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -459,6 +734,12 @@ def main():
     ap.add_argument("--no-reorth-block", action="store_true",
                     help="skip the block reorthogonalisation pass (faster, orthogonality ~ u kappa)")
     args = ap.parse_args()
+    if args.config in EXTRA:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the "
+                              "oracle on the c2 workload only"}))
+            return 0
+        return run_batched(args) if args.config == "c4" else run_autograd(args)
     cfg = CONFIGS[args.config]
     if args.impl == "reference":
         return run_reference(args, cfg)

@@ -9,6 +9,10 @@ the zero-padded A beyond m give the last m_pad - m rows of Q).
 Backward: the hand-written adjoint kernels of the library (coded_qr_adjoint_qr for the (Q, R)
 outputs, coded_qr_adjoint_lstsq for x).  Only tall problems (m > n) are accepted: for square
 ones the solve post-orthogonalises in place and the least-squares adjoint needs Q_1.
+
+The problems of a batch run concurrently, each on its own CUDA stream (joined to the caller's
+stream at the end): one problem's panel factorisation occupies at most one thread-block
+cluster, so several of them share the GPU.
 """
 import torch
 
@@ -38,57 +42,89 @@ class CodedLstsqFunction(torch.autograd.Function):
         dt = "f64" if A.dtype == torch.float64 else "f32"
         mma = opts.get("mma", "simt" if dt == "f64" else "3xtf32")
         erasures = opts.get("erasures") or {}
+        cur = torch.cuda.current_stream()
+        streams = [torch.cuda.Stream() for _ in range(min(batch, opts.get("streams", 16)))]
+        Q = torch.empty((batch, m, n), dtype=A.dtype, device=A.device)
+        R = torch.empty((batch, n, n), dtype=A.dtype, device=A.device)
+        X = torch.empty((batch, n, k), dtype=A.dtype, device=A.device)
+        for s in streams:
+            s.wait_stream(cur)
         saved = []
-        Qs, Rs, Xs = [], [], []
         for i in range(batch):
-            q = B.CodedQR(m, n, opts["p_r"], opts["p_c"], opts["f"], opts["b"], dtype=dt, mma=mma,
-                          nrhs_max=k, seed=opts.get("seed", 1), tau=opts.get("tau", 0.0))
-            Ac = _cm(A[i])
-            yc = _cm(y[i])
-            q.encode(Ac)
-            T = q.geo["panels"]
-            t = 0
-            while t < T:
-                if erasures.get(t):
-                    q.inject(erasures[t])
-                    q.recover()
-                nxt = t + 1
-                while nxt < T and not erasures.get(nxt):
-                    nxt += 1
-                q.factor(t, nxt)
-                t = nxt
-            Qo = B.colmajor_empty(q.geo["m_pad"], n, A.dtype)
-            q.post_orth(Qo)
-            xc = B.colmajor_empty(n, k, A.dtype)
-            q.solve(yc, xc)
-            _, Rc = q.factors()
-            Qs.append(Qo[:m].clone())
-            Rs.append(torch.triu(Rc[:n, :n]).clone())
-            Xs.append(xc.clone())
-            saved.append((q, Ac, yc, Qo, xc))
+            s = streams[i % len(streams)]
+            with torch.cuda.stream(s):
+                q = B.CodedQR(m, n, opts["p_r"], opts["p_c"], opts["f"], opts["b"], dtype=dt,
+                              mma=mma, nrhs_max=k, seed=opts.get("seed", 1),
+                              tau=opts.get("tau", 0.0), stream=s)
+                Ac = _cm(A[i])
+                yc = _cm(y[i])
+                q.encode(Ac)
+                T = q.geo["panels"]
+                t = 0
+                while t < T:
+                    if erasures.get(t):
+                        q.inject(erasures[t])
+                        q.recover()
+                    nxt = t + 1
+                    while nxt < T and not erasures.get(nxt):
+                        nxt += 1
+                    q.factor(t, nxt)
+                    t = nxt
+                Qo = B.colmajor_empty(q.geo["m_pad"], n, A.dtype)
+                q.post_orth(Qo)
+                xc = B.colmajor_empty(n, k, A.dtype)
+                q.solve(yc, xc)
+                _, Rc = q.factors()
+                Q[i].copy_(Qo[:m])
+                R[i].copy_(torch.triu(Rc[:n, :n]))
+                X[i].copy_(xc)
+            saved.append((q, Ac, yc, Qo, xc, s))
+        for s in streams:
+            cur.wait_stream(s)
+        for (_, Ac, yc, Qo, xc, s) in saved:
+            for t_ in (Ac, yc, Qo, xc):
+                t_.record_stream(cur)
         ctx.saved = saved
         ctx.shape = (batch, m, n, k)
-        return torch.stack(Qs), torch.stack(Rs), torch.stack(Xs)
+        return Q, R, X
 
     @staticmethod
     def backward(ctx, Qbar, Rbar, xbar):
         batch, m, n, k = ctx.shape
+        cur = torch.cuda.current_stream()
         Abar = torch.zeros((batch, m, n), dtype=ctx.saved[0][1].dtype, device="cuda")
         ybar = torch.zeros((batch, m, k), dtype=Abar.dtype, device="cuda")
-        for i, (q, Ac, yc, Qo, xc) in enumerate(ctx.saved):
-            Ab = B.colmajor_empty(m, n, Abar.dtype)
-            Ab.zero_()
-            if Qbar is not None or Rbar is not None:
-                Qb = _cm(Qbar[i], rows=q.geo["m_pad"]) if Qbar is not None else None
-                Rb = _cm(torch.triu(Rbar[i])) if Rbar is not None else None
-                q.adjoint_qr(Qo, Qb, Rb, Ab)
-            if xbar is not None:
-                yb = B.colmajor_empty(m, k, Abar.dtype)
-                yb.zero_()
-                q.adjoint_lstsq(Ac, yc, xc, _cm(xbar[i]), Ab, yb)
-                ybar[i] = yb
-            Abar[i] = Ab
-            q.close()
+        streams = []
+        for (_, _, _, _, _, s) in ctx.saved:
+            if s not in streams:
+                streams.append(s)
+        for s in streams:
+            s.wait_stream(cur)
+        keep = []
+        for i, (q, Ac, yc, Qo, xc, s) in enumerate(ctx.saved):
+            with torch.cuda.stream(s):
+                Ab = B.colmajor_empty(m, n, Abar.dtype)
+                Ab.zero_()
+                if Qbar is not None or Rbar is not None:
+                    Qb = _cm(Qbar[i], rows=q.geo["m_pad"]) if Qbar is not None else None
+                    Rb = _cm(torch.triu(Rbar[i])) if Rbar is not None else None
+                    q.adjoint_qr(Qo, Qb, Rb, Ab)
+                    keep += [t_ for t_ in (Qb, Rb) if t_ is not None]
+                if xbar is not None:
+                    yb = B.colmajor_empty(m, k, Abar.dtype)
+                    yb.zero_()
+                    xb = _cm(xbar[i])
+                    q.adjoint_lstsq(Ac, yc, xc, xb, Ab, yb)
+                    ybar[i].copy_(yb)
+                    keep += [yb, xb]
+                Abar[i].copy_(Ab)
+                keep.append(Ab)
+        for s in streams:
+            cur.wait_stream(s)
+        for t_ in keep:
+            t_.record_stream(cur)
+        for (q, *_rest) in ctx.saved:
+            q.close()  # synchronises the handle's stream before freeing its memory
         ctx.saved = None
         return Abar, ybar, None
 

@@ -981,12 +981,14 @@ cqr_status adjoint_lstsq_t(cqr_handle h, const T* A, int64_t lda, const T* y, in
   const T* R = ptr<T>(h->B.R);
   // u = R^{-T} xbar: rows of the (k x n) view solve u^T R = xbar^T
   CK(launch_axpy2d<T>(n, k, T(1), xbar, 1, ldxb, u, 1, n, true, h->st));
-  CK(launch_trsm_right<T>(0, R, g.ldr, n, u, n, 1, k, h->st));
+  for (int32_t j = 0; j < k; ++j)  // each right-hand side is one contiguous row
+    CK(launch_trsm_right<T>(0, R, g.ldr, n, u + (size_t)j * n, 1, 1, 1, h->st));
   // w = (I - Q_2^T Q_2)^{-1} u (FP64 conjugate gradients), z = R^{-1} w
   for (int32_t j = 0; j < k; ++j)
     CK(launch_ls_cg<T>(ptr<T>(h->B.Q), g.ldq, g.m, g.m_pad, g.c, n, nullptr, w + (size_t)j * n,
                        h->B.cg, h->B.bar, h->B.status, h->num_sms, h->st, u + (size_t)j * n));
-  CK(launch_trsm_right<T>(1, R, g.ldr, n, w, n, 1, k, h->st));
+  for (int32_t j = 0; j < k; ++j)
+    CK(launch_trsm_right<T>(1, R, g.ldr, n, w + (size_t)j * n, 1, 1, 1, h->st));
   const T* z = w;
   // Az, r = y - A x
   CK(launch_gemm_general<T>(0, 0, m, k, n, T(1), A, lda, z, n, T(0), Az, m, h->st));

@@ -114,39 +114,58 @@ __global__ void k_axpy2d(int64_t rows, int64_t cols, T alpha, const T* __restric
 // element (i, j) at B[i rs + j cs].  trans = 1: X R^T = B, columns solved from the last
 // (X[:, j] = (B[:, j] - sum_{k>j} X[:, k] R[j, k]) / R[j, j]); trans = 0: X R = B, columns
 // solved from the first (X[:, j] = (B[:, j] - sum_{k<j} X[:, k] R[k, j]) / R[j, j]).
-// One CTA per block of rb rows, held in shared memory [rb][n]; right-looking: once column j
-// is final, its contribution is removed from every column still to be solved.
+// One CTA per block of rb <= 32 rows, held in shared memory [rb][n + 1]; right-looking: once
+// column j is final, its contribution leaves every column still to be solved.  Thread t works
+// on row t % 32 and the columns congruent to t / 32 modulo 8 (all lanes of a warp read the
+// same coefficient of R).  Used for diagonal blocks and for a few right-hand sides.
 template <typename T>
 __global__ void __launch_bounds__(256) k_trsm_right(int trans, const T* __restrict__ R, int64_t ldr,
-                                                    int64_t n, T* __restrict__ B, int64_t rs,
+                                                    int n, T* __restrict__ B, int64_t rs,
                                                     int64_t cs, int64_t m, int rb) {
   extern __shared__ __align__(16) unsigned char trsm_raw[];
-  T* X = reinterpret_cast<T*>(trsm_raw);  // [rb][n]
-  const int tid = threadIdx.x;
+  T* X = reinterpret_cast<T*>(trsm_raw);  // [rb][n + 1]
+  const int tid = threadIdx.x, ld = n + 1;
   const int64_t r0 = (int64_t)blockIdx.x * rb;
-  const int nrow = (int)std::min<int64_t>(rb, m - r0);
-  for (int64_t e = tid; e < (int64_t)nrow * n; e += 256) {
-    const int64_t j = e / nrow, r = e % nrow;
-    X[r * n + j] = B[(r0 + r) * rs + j * cs];
+  const int nrow = (int)((m - r0) < rb ? (m - r0) : rb);
+  for (int e = tid; e < nrow * n; e += 256) {
+    const int j = e / nrow, r = e % nrow;
+    X[r * ld + j] = B[(r0 + r) * rs + (int64_t)j * cs];
   }
   __syncthreads();
-  for (int64_t s = 0; s < n; ++s) {
-    const int64_t j = trans ? n - 1 - s : s;
-    if (tid < nrow) X[tid * n + j] /= R[j + j * ldr];
+  const int r = tid & 31, grp = tid >> 5;
+  for (int s = 0; s < n; ++s) {
+    const int j = trans ? n - 1 - s : s;
+    if (tid < nrow) X[tid * ld + j] /= R[j + (int64_t)j * ldr];
     __syncthreads();
-    const int64_t len = trans ? j : n - 1 - j;
-    for (int64_t e = tid; e < (int64_t)nrow * len; e += 256) {
-      const int64_t r = e / len, k = e % len;
-      const int64_t col = trans ? k : j + 1 + k;
-      const T coef = trans ? R[k + j * ldr] : R[j + col * ldr];
-      X[r * n + col] -= X[r * n + j] * coef;
+    if (r < nrow) {
+      const T xj = X[r * ld + j];
+      if (trans) {
+        for (int k = grp; k < j; k += 8) X[r * ld + k] -= xj * R[k + (int64_t)j * ldr];
+      } else {
+        for (int k = j + 1 + grp; k < n; k += 8) X[r * ld + k] -= xj * R[j + (int64_t)k * ldr];
+      }
     }
     __syncthreads();
   }
-  for (int64_t e = tid; e < (int64_t)nrow * n; e += 256) {
-    const int64_t j = e / nrow, r = e % nrow;
-    B[(r0 + r) * rs + j * cs] = X[r * n + j];
+  for (int e = tid; e < nrow * n; e += 256) {
+    const int j = e / nrow, r2 = e % nrow;
+    B[(r0 + r2) * rs + (int64_t)j * cs] = X[r2 * ld + j];
   }
+}
+
+template <typename T>
+cudaError_t trsm_unblocked(int trans, const T* R, int64_t ldr, int n, T* B, int64_t rs, int64_t cs,
+                           int64_t m, cudaStream_t st) {
+  const size_t cap = 200 * 1024;
+  int rb = (int)std::min<int64_t>(32, (int64_t)(cap / ((size_t)(n + 1) * sizeof(T))));
+  if (rb < 1) return cudaErrorInvalidValue;  // n too large for one row in shared memory
+  const size_t smem = (size_t)rb * (n + 1) * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(k_trsm_right<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((m + rb - 1) / rb);
+  k_trsm_right<T><<<grid, 256, smem, st>>>(trans, R, ldr, n, B, rs, cs, m, rb);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -177,20 +196,34 @@ cudaError_t launch_axpy2d(int64_t rows, int64_t cols, T alpha, const T* X, int64
   return cudaGetLastError();
 }
 
+// Blocked for a column-major B (rs == 1) with many rows: diagonal blocks of kTB columns are
+// solved by the row-block kernel, the rest of each step is one GEMM update
+//   trans = 1 (blocks from the last):  B[:, K] -= X[:, J] R[K, J]^T  for the blocks K < J
+//   trans = 0 (blocks from the first): B[:, K] -= X[:, J] R[J, K]    for the blocks K > J.
 template <typename T>
 cudaError_t launch_trsm_right(int trans, const T* R, int64_t ldr, int64_t n, T* B, int64_t rs,
                               int64_t cs, int64_t m, cudaStream_t st) {
   if (m <= 0 || n <= 0) return cudaSuccess;
-  const size_t cap = 200 * 1024;
-  int rb = (int)std::min<int64_t>(32, (int64_t)(cap / ((size_t)n * sizeof(T))));
-  if (rb < 1) return cudaErrorInvalidValue;  // n too large for one row in shared memory
-  const size_t smem = (size_t)rb * n * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(k_trsm_right<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)std::max<size_t>(smem, 1));
-  if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)((m + rb - 1) / rb);
-  k_trsm_right<T><<<grid, 256, smem, st>>>(trans, R, ldr, n, B, rs, cs, m, rb);
-  return cudaGetLastError();
+  constexpr int kTB = 64;
+  // blocked when B is column-major (or a single contiguous row, cs == 1)
+  const bool colmajor = (rs == 1) || (m == 1);
+  if (!colmajor || n <= kTB) return trsm_unblocked<T>(trans, R, ldr, (int)n, B, rs, cs, m, st);
+  const int64_t nblk = (n + kTB - 1) / kTB;
+  for (int64_t s = 0; s < nblk; ++s) {
+    const int64_t J = trans ? nblk - 1 - s : s;
+    const int64_t j0 = J * kTB, jb = std::min<int64_t>(kTB, n - j0);
+    cudaError_t e = trsm_unblocked<T>(trans, R + j0 + j0 * ldr, ldr, (int)jb, B + j0 * cs, 1, cs, m, st);
+    if (e != cudaSuccess) return e;
+    if (trans && j0 > 0) {
+      e = launch_gemm_general<T>(0, 1, m, j0, jb, T(-1), B + j0 * cs, cs, R + j0 * ldr, ldr, T(1),
+                                 B, cs, st);
+    } else if (!trans && j0 + jb < n) {
+      e = launch_gemm_general<T>(0, 0, m, n - j0 - jb, jb, T(-1), B + j0 * cs, cs,
+                                 R + j0 + (j0 + jb) * ldr, ldr, T(1), B + (j0 + jb) * cs, cs, st);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 #define CQR_ADJ_INSTANTIATE(T)                                                                   \

@@ -680,6 +680,7 @@ __global__ void __launch_bounds__(256) k_ls_cg(const T* __restrict__ Q, int64_t 
   double* part = tv + c;    // [2][G]
   unsigned target = 0;
   __shared__ double red[8];
+  __shared__ double tpart[8][33];
   const T* Q2 = Q + m_pad;
   auto block_sum = [&](double v) -> double {  // sum over the CTA, result in every thread
     v = warp_sum(v);
@@ -720,11 +721,21 @@ __global__ void __launch_bounds__(256) k_ls_cg(const T* __restrict__ Q, int64_t 
   const double stop = rr * 1e-30;  // |r| <= 1e-15 |z|
   int slot = 1;
   for (int it = 0; it < maxit && c > 0 && rr > stop; ++it) {
-    // t = Q_2 p (thread per row of Q_2)
-    for (int64_t i = (int64_t)g * blockDim.x + tid; i < c; i += (int64_t)G * blockDim.x) {
+    // t = Q_2 p: tiles of 32 rows per CTA, lanes on rows (coalesced), the 8 warps on
+    // interleaved columns, partial sums combined in a fixed order
+    for (int64_t i0 = (int64_t)g * 32; i0 < c; i0 += (int64_t)G * 32) {
+      const int64_t i = i0 + lane;
       double acc = 0.0;
-      for (int64_t j = 0; j < n; ++j) acc += (double)Q2[i + j * ldq] * __ldcg(p + j);
-      tv[i] = acc;
+      if (i < c)
+        for (int64_t j = warp; j < n; j += 8) acc += (double)Q2[i + j * ldq] * __ldcg(p + j);
+      tpart[warp][lane] = acc;
+      __syncthreads();
+      if (warp == 0 && i < c) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += tpart[k][lane];
+        tv[i] = t;
+      }
+      __syncthreads();
     }
     if (!grid_sync(bar, G, target, status, 31)) return;
     // sp = p - Q_2^T t (warp per column), partial p . sp
@@ -771,9 +782,10 @@ cudaError_t launch_ls_cg(const T* Q, int64_t ldq, int64_t m, int64_t m_pad, int6
                          cudaStream_t st, const T* u) {
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  int G = (int)((n + 255) / 256);
-  const int Gc = (int)((c + 255) / 256);
-  if (Gc > G) G = Gc;
+  // enough CTAs to spread the two products with Q_2 (c x n) per iteration, few enough that a
+  // grid barrier stays near a microsecond
+  int64_t want = std::max<int64_t>((c + 31) / 32, (n + 7) / 8);
+  int G = (int)std::min<int64_t>(want, 32);
   if (G > num_sms) G = num_sms;
   if (G < 1) G = 1;
   int maxit = 200;
