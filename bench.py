@@ -361,12 +361,11 @@ def run_ours(args, cfg):
     ms = statistics.mean(t_coded)
     ms_unc = statistics.mean(t_unc)
     ms_e2e = statistics.mean(e2e_times)
-    if world > 1:
-        tt = torch.tensor([ms, ms_unc, ms_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms, ms_unc, ms_e2e = tt.tolist()
-    value = world * F / (ms * 1e-3) / 1e12
-    e2e_value = world * F / (ms_e2e * 1e-3) / 1e12
+    from paper_2311_11943_gb300 import replicas
+    ms, ms_unc, ms_e2e = replicas.max_over_ranks([ms, ms_unc, ms_e2e], dist if world > 1 else None,
+                                                 device=dev)
+    value = replicas.job_throughput(F, world, ms)
+    e2e_value = replicas.job_throughput(F, world, ms_e2e)
 
     # roofline of the dominant kernel (largest share of device time in the timed steps)
     peaks, peak_src = measured_peaks()
@@ -508,8 +507,9 @@ def run_batched(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     # weak scaling over replicas: every rank factorises its own batch of the same recipe
-    shapes = synth.batched_shapes(cfg["count"], cfg["seed"] + rank)
-    gen = torch.Generator(device="cuda").manual_seed(1000 * cfg["seed"] + rank)
+    from paper_2311_11943_gb300 import replicas
+    shapes = synth.batched_shapes(cfg["count"], replicas.rank_seed(cfg["seed"], rank))
+    gen = torch.Generator(device="cuda").manual_seed(replicas.rank_seed(1000 * cfg["seed"], rank))
     As = [torch.randn(n, m, device="cuda", dtype=torch.float32, generator=gen).t()
           for (m, n) in shapes]
     bt = B.CodedQRBatch(shapes, cfg["p_r"], cfg["p_c"], cfg["f"], b=0, seed=cfg["seed"])
@@ -566,10 +566,7 @@ def run_batched(args):
             e2e.append((time.perf_counter() - t0) * 1e3)
     ms = statistics.mean(times)
     ms_e2e = statistics.mean(e2e)
-    if world > 1:
-        tt = torch.tensor([ms, ms_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = tt.tolist()
+    ms, ms_e2e = replicas.max_over_ranks([ms, ms_e2e], dist if world > 1 else None, device="cuda")
     peak = 152 * 128 * 2 * 2.07e9 / 1e12
     rl = {"bound": "alu", "unit": "TFLOP/s", "kernel": "k_b_factor", "achieved": F / (t_fac * 1e-3) / 1e12,
           "peak": peak, "frac": F / (t_fac * 1e-3) / 1e12 / peak, "traffic": None,
@@ -585,7 +582,7 @@ def run_batched(args):
         cl, widths = bt.tuning()
         line = {
             "metric": "coded GS-QR TFLOP/s (sum over the batch of F_coded = 2(m+c)n(n+2d))",
-            "value": world * F / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": world,
+            "value": replicas.job_throughput(F, world, ms), "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded N(0,1) drawn on the device)",
@@ -599,12 +596,15 @@ def run_batched(args):
                        "graph": "the whole run recorded once into a CUDA graph and replayed"},
             "coded_flops_per_step": F, "factor_kernel_ms": t_fac, "reorth": nre,
             "gpu_launches": 6, "clocks": clk, "roofline": rl, "cpu_baseline": cpu,
-            "e2e": {"value": world * F / (ms_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
+            "e2e": {"value": replicas.job_throughput(F, world, ms_e2e), "unit": "TFLOP/s",
                     "ms_per_step": ms_e2e, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 16 * cfg["count"]},
         }
         print(json.dumps(line))
     bt.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
     return 0
 
 
