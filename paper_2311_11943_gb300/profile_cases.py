@@ -1,0 +1,89 @@
+"""Small fixed workloads for capturing single kernels under a profiler (ncu), through the
+library's public API.  Each case runs twice (the first run warms up the handle).
+
+  python -m paper_2311_11943_gb300.profile_cases tc_c2      # C2 shape, FP32 3xTF32: 2 panels
+  python -m paper_2311_11943_gb300.profile_cases panel_c2   # same handle (register panel)
+  python -m paper_2311_11943_gb300.profile_cases bfactor64  # 64 batched instances, no erasure
+  python -m paper_2311_11943_gb300.profile_cases adjoint    # 8192 x 1024: forward + both adjoints
+
+Launch order per run (for ncu's --launch-skip):
+  tc_c2 / panel_c2: generator, encode (2), then per panel: panel, split, GEMM1, reduce, GEMM2
+  bfactor64:        encode (2), one k_b_factor
+"""
+import sys
+
+import numpy as np
+
+
+def _cm(torch, B, X):
+    d = B.colmajor_empty(X.shape[0], X.shape[1], torch.float32)
+    d.copy_(torch.as_tensor(np.ascontiguousarray(X), dtype=torch.float32))
+    return d
+
+
+def case_c2(panels=2):
+    import torch
+    from . import binding as B
+    from . import synth
+    A = _cm(torch, B, synth.gaussian(4096, 4096, 2))
+    q = B.CodedQR(4096, 4096, 8, 8, 2, 128, dtype="f32", mma="3xtf32", seed=2)
+    for _ in range(2):
+        q.encode(A)
+        q.factor(0, panels)
+    torch.cuda.synchronize()
+    assert q.sync_status() == 0
+    q.close()
+
+
+def case_bfactor(count=64):
+    import torch
+    from . import binding as B
+    from . import synth
+    shapes = synth.batched_shapes(count, 4)
+    As = [_cm(torch, B, synth.gaussian(m, n, 4000 + i, dtype=np.float32))
+          for i, (m, n) in enumerate(shapes)]
+    bt = B.CodedQRBatch(shapes, 8, 4, 2, b=0, seed=4)
+    bt.set_tuning(2)
+    for _ in range(2):
+        bt.run(As, [], graph=False)
+    torch.cuda.synchronize()
+    assert bt.sync_status()[0] == 0
+    bt.close()
+
+
+def case_adjoint():
+    import torch
+    from . import binding as B
+    from . import synth
+    m, n = 8192, 1024
+    A = synth.kappa_matrix(m, n, 1e3, 31)
+    y = synth.rhs(m, 1, 81)
+    q = B.CodedQR(m, n, 8, 8, 1, 128, dtype="f32", mma="3xtf32", seed=5)
+    Ac, yc = _cm(torch, B, A), _cm(torch, B, y)
+    rng = np.random.default_rng(3)
+    Qb = _cm(torch, B, rng.standard_normal((q.geo["m_pad"], n)))
+    Rb = _cm(torch, B, np.triu(rng.standard_normal((n, n))))
+    xb = _cm(torch, B, rng.standard_normal((n, 1)))
+    for _ in range(2):
+        q.encode(Ac)
+        q.factor(0, -1)
+        Qo = B.colmajor_empty(q.geo["m_pad"], n, torch.float32)
+        q.post_orth(Qo)
+        x = B.colmajor_empty(n, 1, torch.float32)
+        q.solve(yc, x)
+        Ab = B.colmajor_empty(m, n, torch.float32)
+        Ab.zero_()
+        yb = B.colmajor_empty(m, 1, torch.float32)
+        yb.zero_()
+        q.adjoint_qr(Qo, Qb, Rb, Ab)
+        q.adjoint_lstsq(Ac, yc, x, xb, Ab, yb)
+    torch.cuda.synchronize()
+    assert q.sync_status() == 0
+    q.close()
+
+
+CASES = {"tc_c2": case_c2, "panel_c2": case_c2, "bfactor64": case_bfactor, "adjoint": case_adjoint}
+
+if __name__ == "__main__":
+    CASES[sys.argv[1]]()
+    print("ok", sys.argv[1])
