@@ -48,7 +48,7 @@ EXTRA = {
     "c5": dict(batch=16, m=8192, n=1024, p_r=8, p_c=8, f=1, b=128, kappa=1e3, seed=5),
 }
 MODES = {"f64": ("f64", "simt"), "f32": ("f32", "simt"), "tf32": ("f32", "tf32"),
-         "3xtf32": ("f32", "3xtf32")}
+         "3xtf32": ("f32", "3xtf32"), "bf16": ("f32", "bf16"), "bf16x3": ("f32", "bf16x3")}
 L2_BYTES = 126 * 1024 * 1024
 
 
@@ -389,6 +389,10 @@ def run_ours(args, cfg):
             peak = 152 * 128 * 2 * 2.07e9 / 1e12
             rl = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "FP32 CUDA-core: 152 SMs x "
                   "128 FFMA/clk x 2 flop x 2.07 GHz"}
+        elif mma in ("bf16", "bf16x3"):
+            peak = peaks["bf16_tflops_sustained"]
+            rl = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": "%s bf16 sustained"
+                  % peak_src}
         else:
             peak = peaks["bf16_tflops_sustained"] * 1.1 / 2.25
             rl = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": "%s bf16 sustained x "
@@ -423,7 +427,9 @@ def run_ours(args, cfg):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"f64": "f64", "f32": "f32", "tf32": "f32 storage, tf32 tensor-core GEMMs",
-                      "3xtf32": "f32 storage, 3xtf32 tensor-core GEMMs"}[args.mode],
+                      "3xtf32": "f32 storage, 3xtf32 tensor-core GEMMs",
+                      "bf16": "f32 storage, bf16 tensor-core GEMMs",
+                      "bf16x3": "f32 storage, bf16x3 tensor-core GEMMs"}[args.mode],
             "data": "synthetic (seeded U diag(sigma) V^T / N(0,1), generated on the host)",
             "config": {"workload": workload_name(cfg, args.mode, rb), "m": m, "n": n, "p_r": p_r,
                        "p_c": p_c, "f": f, "b": b, "kappa": cfg["kappa"],

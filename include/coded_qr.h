@@ -63,7 +63,10 @@ enum { CQR_F64 = 0, CQR_F32 = 1 };
 enum {
   CQR_MMA_SIMT = 0,   /* CUDA-core FMA in the storage precision (the only choice for F64) */
   CQR_MMA_TF32 = 1,   /* F32 storage: tcgen05 kind::tf32 tensor cores, FP32 accumulation */
-  CQR_MMA_3XTF32 = 2  /* F32 storage: split operands hi + lo, three tcgen05 tf32 products */
+  CQR_MMA_3XTF32 = 2, /* F32 storage: split operands hi + lo, three tcgen05 tf32 products */
+  CQR_MMA_BF16 = 3,   /* F32 storage: operands rounded to BF16, tcgen05 kind::f16, FP32
+                         accumulation */
+  CQR_MMA_BF16X3 = 4  /* F32 storage: BF16 hi + lo splits, three tcgen05 BF16 products */
 };
 
 enum { CQR_G_UNIF01 = 0, CQR_G_NORMAL = 1 };

@@ -17,7 +17,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libcoded_qr.so")
 CQR_OK, CQR_EINVAL, CQR_ENOMEM, CQR_ECUDA, CQR_ESTATE = 0, 1, 2, 3, 4
 CQR_EUNRECOVERABLE, CQR_EBREAKDOWN, CQR_ETIMEOUT, CQR_ENOTSUP = 5, 6, 7, 8
 CQR_F64, CQR_F32 = 0, 1
-CQR_MMA_SIMT, CQR_MMA_TF32, CQR_MMA_3XTF32 = 0, 1, 2
+CQR_MMA_SIMT, CQR_MMA_TF32, CQR_MMA_3XTF32, CQR_MMA_BF16, CQR_MMA_BF16X3 = 0, 1, 2, 3, 4
+MMA_NAMES = {"simt": CQR_MMA_SIMT, "tf32": CQR_MMA_TF32, "3xtf32": CQR_MMA_3XTF32,
+             "bf16": CQR_MMA_BF16, "bf16x3": CQR_MMA_BF16X3}
 CQR_G_UNIF01, CQR_G_NORMAL = 0, 1
 CQR_RUN_HOST_BUFFERS = 1
 GEO_FIELDS = ["m", "n", "mb", "nb", "m_pad", "c", "d", "M", "N", "ldq", "ldr", "grid_rows",
@@ -418,7 +420,7 @@ class CodedQR:
         cfg = Config()
         cfg.m, cfg.n, cfg.p_r, cfg.p_c, cfg.f, cfg.b = m, n, p_r, p_c, f, b
         cfg.dtype = CQR_F64 if self.tdtype == torch.float64 else CQR_F32
-        cfg.mma = {"simt": CQR_MMA_SIMT, "tf32": CQR_MMA_TF32, "3xtf32": CQR_MMA_3XTF32}[mma]
+        cfg.mma = MMA_NAMES[mma]
         cfg.protect_r = int(bool(protect_r))
         cfg.gdist = gdist
         cfg.nrhs_max = nrhs_max

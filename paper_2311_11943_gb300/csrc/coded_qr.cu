@@ -60,7 +60,7 @@ cqr_status validate(const cqr_config* c) {
   if (c->f > kMaxF || c->p_r + c->f > kMaxCode || c->p_c + c->f > kMaxCode) return CQR_ENOTSUP;
   if (c->p_r > (int64_t)c->m) return CQR_EINVAL;
   if (c->dtype != CQR_F64 && c->dtype != CQR_F32) return CQR_EINVAL;
-  if (c->mma < CQR_MMA_SIMT || c->mma > CQR_MMA_3XTF32) return CQR_EINVAL;
+  if (c->mma < CQR_MMA_SIMT || c->mma > CQR_MMA_BF16X3) return CQR_EINVAL;
   if (c->dtype == CQR_F64 && c->mma != CQR_MMA_SIMT) return CQR_ENOTSUP;
   if (c->mma != CQR_MMA_SIMT && !tc_available()) return CQR_ENOTSUP;
   if (c->gdist != CQR_G_UNIF01 && c->gdist != CQR_G_NORMAL) return CQR_EINVAL;
@@ -116,7 +116,7 @@ Layout make_layout(const cqr_config* c, const Geo& g, int num_sms) {
   L.plans = take(sizeof(DecodePlan) * (size_t)(g.grid_cols + g.p_c + c->f + 2));
   L.cg = take(sizeof(double) * (size_t)(7 * g.n + g.c + 2 * (num_sms + 1)));
   L.tc = take(c->dtype == CQR_F32 && c->mma != CQR_MMA_SIMT
-                  ? tc_workspace_bytes(g.M, g.N, g.n, bmax, c->reorth_block != 0)
+                  ? tc_workspace_bytes(c->mma, g.M, g.N, g.n, bmax, c->reorth_block != 0)
                   : 0);
   L.total = off;
   return L;

@@ -20,6 +20,7 @@
 // waits (bounded) for its own copies, frees TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -38,12 +39,19 @@ namespace {
 constexpr int BM = 128;       // UMMA M (TMEM lanes)
 constexpr int BN = 128;       // UMMA N (TMEM columns)
 constexpr int kTmemCols = 2 * BN;  // two accumulator buffers (power of two, <= 512)
-constexpr int BK = 32;        // K per stage: 32 FP32 = 128 bytes = one swizzle row
-constexpr int UMMA_K = 8;     // K per tcgen05.mma kind::tf32
 constexpr int kThreads = 256;
 constexpr int kMaxSplits = 16;
-constexpr uint32_t kTileBytesA = BM * BK * 4;  // 16 KB
-constexpr uint32_t kTileBytesB = BN * BK * 4;  // 16 KB
+constexpr uint32_t kTileBytesA = BM * 128;  // 16 KB: 128 rows of one 128-byte swizzle row
+constexpr uint32_t kTileBytesB = BN * 128;  // 16 KB
+
+// Operand type of the MMAs: TF32 (kind::tf32) or BF16 (kind::f16 with BF16 inputs).  One stage
+// of K is one 128-byte swizzle row of the operand type, 32 TF32 or 64 BF16 elements; each
+// tcgen05.mma consumes 32 bytes of it (8 TF32 or 16 BF16 elements).
+template <bool BF>
+struct Op {
+  static constexpr int KE = BF ? 64 : 32;
+  static constexpr int UK = BF ? 16 : 8;
+};
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -113,16 +121,28 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::tf32: D FP32, A/B TF32, both K-major, N and M encoded.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor: D FP32, both operands K-major, N and M encoded; A/B format TF32
+// (kind::tf32) or BF16 (kind::f16, A and B of the same type).
+template <bool BF>
+constexpr uint32_t idesc() {
+  return (1u << 4) | ((BF ? 1u : 2u) << 7) | ((BF ? 1u : 2u) << 10) |
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(tmem_d), "l"(a), "l"(b), "r"(kIdesc), "r"(accum)
-      : "memory");
+template <bool BF>
+__device__ __forceinline__ void mma_op(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accum) {
+  if (BF)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc<true>()), "r"(accum)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc<false>()), "r"(accum)
+        : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -176,7 +196,7 @@ struct TcJob {
   int64_t a_row0;     // A tile y coordinate offset (rows of the MMA M dimension)
   int64_t b_row0;     // B tile y coordinate offset
   int64_t k0;         // K start
-  int64_t kchunk;     // K per split (multiple of BK)
+  int64_t kchunk;     // K per split (multiple of the stage K)
   int64_t K;          // K end (exclusive)
   int64_t mrows;      // valid D rows (M dimension)
   int64_t ncols;      // valid D columns (N dimension)
@@ -196,10 +216,12 @@ struct Smem {
   static_assert(STAGES * 3 * 8 + 4 * 8 + 8 <= 256, "barrier region too small");
 };
 
-template <int STAGES, int NA, int NB>
+template <bool BF, int STAGES, int NA, int NB>
 __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__ TcMaps maps,
                                                           const TcJob job) {
   using S = Smem<STAGES, NA, NB>;
+  constexpr int BK = Op<BF>::KE;
+  constexpr int UMMA_K = Op<BF>::UK;
   extern __shared__ __align__(1024) unsigned char smraw[];
   const uint32_t base_u = su32(smraw);
   const uint32_t tiles_u = (base_u + 1023u) & ~1023u;
@@ -268,11 +290,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
           const int x = (int)(kbase + (int64_t)kb * BK);
           const int ya = (int)(job.a_row0 + (int64_t)mt * BM);
           const int yb = (int)(job.b_row0 + (int64_t)nt * BN);
-          const int nb_load = job.split_b_smem ? 1 : NB;
+          // raw FP32 B for the in-smem split: one 32-element box (TF32) or two (BF16: 64
+          // elements of K, split in place into the BF16 hi and lo tiles)
+          const int nb_load = job.split_b_smem ? (BF ? 2 : 1) : NB;
           mbar_expect_tx(&full[s], NA * kTileBytesA + nb_load * kTileBytesB);
           for (int p = 0; p < NA; ++p) tma_load_2d(st + p * kTileBytesA, &maps.a[p], x, ya, &full[s]);
-          for (int p = 0; p < nb_load; ++p)
-            tma_load_2d(st + NA * kTileBytesA + p * kTileBytesB, &maps.b[p], x, yb, &full[s]);
+          for (int p = 0; p < nb_load; ++p) {
+            const bool raw = job.split_b_smem;
+            tma_load_2d(st + NA * kTileBytesA + p * kTileBytesB, raw ? &maps.b[0] : &maps.b[p],
+                        raw ? x + 32 * p : x, yb, &full[s]);
+          }
         }
       }
       // the last load issued into each stage has landed before the CTA may exit (bounded)
@@ -304,12 +331,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
           const uint32_t b_hi = st + NA * kTileBytesA, b_lo = b_hi + kTileBytesB;
 #pragma unroll
           for (int ks = 0; ks < BK / UMMA_K; ++ks) {
-            const uint32_t off = ks * UMMA_K * 4;
+            const uint32_t off = ks * 32;  // 32 bytes of K per instruction
             const uint32_t acc0 = (kb > 0 || ks > 0) ? 1u : 0u;
-            mma_tf32(acc, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
+            mma_op<BF>(acc, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
             if (job.nprod == 3) {
-              mma_tf32(acc, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
-              mma_tf32(acc, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
+              mma_op<BF>(acc, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
+              mma_op<BF>(acc, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
             }
           }
           mma_commit(&empty[s]);
@@ -331,15 +358,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
           if (!mbar_wait(&full[s], (it / STAGES) & 1, abort_flag)) { ok = false; break; }
           float4* raw = reinterpret_cast<float4*>(tiles + s * S::kStageBytes + NA * kTileBytesA);
           float4* lo = raw + kTileBytesB / 16;
-          for (int e = tt; e < (int)(kTileBytesB / 16); e += 64) {
-            const float4 x = raw[e];
-            float4 h, l;
-            h.x = tf32_hi(x.x); l.x = x.x - h.x;
-            h.y = tf32_hi(x.y); l.y = x.y - h.y;
-            h.z = tf32_hi(x.z); l.z = x.z - h.z;
-            h.w = tf32_hi(x.w); l.w = x.w - h.w;
-            raw[e] = h;
-            lo[e] = l;
+          if (!BF) {
+            for (int e = tt; e < (int)(kTileBytesB / 16); e += 64) {
+              const float4 x = raw[e];
+              float4 h, l;
+              h.x = tf32_hi(x.x); l.x = x.x - h.x;
+              h.y = tf32_hi(x.y); l.y = x.y - h.y;
+              h.z = tf32_hi(x.z); l.z = x.z - h.z;
+              h.w = tf32_hi(x.w); l.w = x.w - h.w;
+              raw[e] = h;
+              lo[e] = l;
+            }
+          } else {
+            // row r of the two raw FP32 tiles (K 0..31 and 32..63, 16-byte chunks swizzled by
+            // r % 8) becomes row r of the BF16 hi tile (first 16 KB) and lo tile (second):
+            // a thread reads both raw rows before writing, and no other thread touches row r
+            for (int r = tt; r < BN; r += 64) {
+              float v[64];
+#pragma unroll
+              for (int c = 0; c < 16; ++c) {
+                const int tile = c >> 3, lc = c & 7;
+                const float4 x = raw[tile * (kTileBytesB / 16) + r * 8 + (lc ^ (r & 7))];
+                v[4 * c] = x.x; v[4 * c + 1] = x.y; v[4 * c + 2] = x.z; v[4 * c + 3] = x.w;
+              }
+#pragma unroll
+              for (int c = 0; c < 8; ++c) {
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  const float a0 = v[8 * c + 2 * q], a1 = v[8 * c + 2 * q + 1];
+                  const __nv_bfloat16 h0 = __float2bfloat16_rn(a0), h1 = __float2bfloat16_rn(a1);
+                  const __nv_bfloat16 l0 = __float2bfloat16_rn(a0 - __bfloat162float(h0));
+                  const __nv_bfloat16 l1 = __float2bfloat16_rn(a1 - __bfloat162float(h1));
+                  hw[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                  lw[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                }
+                const int pc = r * 8 + (c ^ (r & 7));
+                reinterpret_cast<uint4*>(raw)[pc] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                if (job.nprod == 3) reinterpret_cast<uint4*>(lo)[pc] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+              }
+            }
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           mbar_arrive(&ready[s]);
@@ -413,17 +471,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
 // zero-filled up to bkp (and up to 128 columns for GEMM1's M tile).  With Qr != nullptr the
 // finished panel is also copied into the row-major planes of all computed columns
 // (Qr[r * ldrow + kb + k]), the K-major operand of the block reorthogonalisation.
+// Operand planes: x = hi + lo with hi = rna_tf32(x) (TF32; hi = x with one product, the MMA
+// reads TF32 from the FP32 word) or hi = bf16_rn(x), lo = bf16_rn(x - hi) (BF16).
+__device__ __forceinline__ void hilo(float x, int nplanes, float& h, float& l) {
+  h = nplanes == 2 ? tf32_hi(x) : x;
+  l = x - h;
+}
+__device__ __forceinline__ void hilo(float x, int, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(x);
+  l = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+template <typename P>
 __global__ void k_split_panel(const float* __restrict__ Q, int64_t ldq, int64_t M, int bk, int bkp,
-                              int ak_cols, int nplanes, float* __restrict__ Ak_hi,
-                              float* __restrict__ Ak_lo, int64_t ldk, float* __restrict__ At_hi,
-                              float* __restrict__ At_lo, float* __restrict__ Qr_hi,
-                              float* __restrict__ Qr_lo, int64_t ldrow, int64_t kb) {
+                              int ak_cols, int nplanes, P* __restrict__ Ak_hi,
+                              P* __restrict__ Ak_lo, int64_t ldk, P* __restrict__ At_hi,
+                              P* __restrict__ At_lo, P* __restrict__ Qr_hi,
+                              P* __restrict__ Qr_lo, int64_t ldrow, int64_t kb) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
   if (r >= M) return;
   const float x = (k < bk) ? Q[r + (int64_t)k * ldq] : 0.f;
-  const float h = nplanes == 2 ? tf32_hi(x) : x;
-  const float l = x - h;
+  P h, l;
+  hilo(x, nplanes, h, l);
   if (k < ak_cols) {
     if (Ak_hi) Ak_hi[r + (int64_t)k * ldk] = h;
     if (Ak_lo && nplanes == 2) Ak_lo[r + (int64_t)k * ldk] = l;
@@ -454,27 +524,29 @@ __global__ void k_tc_sub_partials(const float* __restrict__ P, int splits, int64
 }
 
 // Row-major planes of the computed columns 0 .. ncols-1 from Q (after a recovery).
+template <typename P>
 __global__ void k_refresh_rows(const float* __restrict__ Q, int64_t ldq, int64_t M, int64_t ncols,
-                               int nplanes, float* __restrict__ Qr_hi, float* __restrict__ Qr_lo,
+                               int nplanes, P* __restrict__ Qr_hi, P* __restrict__ Qr_lo,
                                int64_t ldrow) {
   const int64_t total = M * ncols;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = idx % M, c = idx / M;
-    const float x = Q[r + c * ldq];
-    const float h = nplanes == 2 ? tf32_hi(x) : x;
+    P h, l;
+    hilo(Q[r + c * ldq], nplanes, h, l);
     Qr_hi[r * ldrow + c] = h;
-    if (nplanes == 2) Qr_lo[r * ldrow + c] = x - h;
+    if (nplanes == 2) Qr_lo[r * ldrow + c] = l;
   }
 }
 
 // Block reorthogonalisation, reduce: the GEMM1 partials hold S^T = Qbar^T Q[:, 0:kb]
 // (P[s][i + j bkp]); R[j, kb+i] += S[j][i] and S (column-major, ld ldrow, rows >= kb zero)
 // goes into the B planes of the second product.
+template <typename PT>
 __global__ void k_tc_reduce_t(const float* __restrict__ P, int splits, int64_t split_stride,
                               int64_t ldp, int bk, int64_t kb, int64_t kbp, float* __restrict__ R,
-                              int64_t ldr, int nplanes, float* __restrict__ Sh,
-                              float* __restrict__ Sl, int64_t ldrow) {
+                              int64_t ldr, int nplanes, PT* __restrict__ Sh,
+                              PT* __restrict__ Sl, int64_t ldrow) {
   const int64_t total = kbp * bk;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -484,17 +556,19 @@ __global__ void k_tc_reduce_t(const float* __restrict__ P, int splits, int64_t s
       for (int sp = 0; sp < splits; ++sp) s += P[sp * split_stride + i + j * ldp];
       R[j + (kb + i) * ldr] += s;
     }
-    const float h = nplanes == 2 ? tf32_hi(s) : s;
+    PT h, l;
+    hilo(s, nplanes, h, l);
     Sh[j + i * ldrow] = h;
-    if (nplanes == 2) Sl[j + i * ldrow] = s - h;
+    if (nplanes == 2) Sl[j + i * ldrow] = l;
   }
 }
 
 // Split-K reduction of GEMM1: Rbar = sum_s P[s] (fixed order) into R (rows kb.., columns
 // j0..) and into GEMM2's B operand planes (column-major, ld bkp, rows >= bk zero).
+template <typename PT>
 __global__ void k_tc_reduce(const float* __restrict__ P, int splits, int64_t split_stride, int64_t ldp,
                             int bk, int bkp, int64_t w, float* __restrict__ R, int64_t ldr,
-                            int nplanes, float* __restrict__ Bh, float* __restrict__ Bl) {
+                            int nplanes, PT* __restrict__ Bh, PT* __restrict__ Bl) {
   const int64_t total = (int64_t)bkp * w;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -504,9 +578,10 @@ __global__ void k_tc_reduce(const float* __restrict__ P, int splits, int64_t spl
       for (int sp = 0; sp < splits; ++sp) s += P[sp * split_stride + i + j * ldp];
       R[i + j * ldr] = s;
     }
-    const float h = nplanes == 2 ? tf32_hi(s) : s;
+    PT h, l;
+    hilo(s, nplanes, h, l);
     Bh[idx] = h;
-    if (nplanes == 2) Bl[idx] = s - h;
+    if (nplanes == 2) Bl[idx] = l;
   }
 }
 
@@ -514,21 +589,25 @@ __global__ void k_tc_reduce(const float* __restrict__ P, int splits, int64_t spl
 
 // ------------------------------------------------------------------ host side
 struct TcGemm {
-  int mode;           // CQR_MMA_TF32 | CQR_MMA_3XTF32
+  int mode;           // CQR_MMA_TF32 | _3XTF32 | _BF16 | _BF16X3
   int nplanes;        // 1 or 2
+  bool bf;            // operand planes in BF16 (kind::f16) rather than TF32-in-FP32
+  int KE;             // K elements per stage (32 TF32, 64 BF16)
+  size_t pe;          // bytes per plane element
   int64_t M, N, b, bkp, ldq, ldk;
   float* Q;
-  float *Ak_hi, *Ak_lo, *At_hi, *At_lo, *Bh, *Bl, *P;
-  float *Qr_hi, *Qr_lo, *Sh, *Sl;   // block reorthogonalisation operands
+  void *Ak_hi, *Ak_lo, *At_hi, *At_lo, *Bh, *Bl;
+  float* P;
+  void *Qr_hi, *Qr_lo, *Sh, *Sl;   // block reorthogonalisation operands
   int64_t n, ldrow;
   int num_sms;
   int* status;
-  CUtensorMap tm_q_b;     // Q as GEMM1's B (box 32 x BN)
-  CUtensorMap tm_ak[2];   // panel, column-major (box 32 x BM)
-  CUtensorMap tm_at[2];   // panel, row-major (box 32 x BM)
-  CUtensorMap tm_bh[2];   // Rbar planes (box 32 x BN)
-  CUtensorMap tm_qr[2];   // computed columns, row-major (box 32 x BM)
-  CUtensorMap tm_s[2];    // S planes, column-major ld ldrow (box 32 x BN)
+  CUtensorMap tm_q_b;     // Q (FP32) as GEMM1's raw B (box 32 x BN)
+  CUtensorMap tm_ak[2];   // panel, column-major (box KE x BM)
+  CUtensorMap tm_at[2];   // panel, row-major (box KE x BM)
+  CUtensorMap tm_bh[2];   // Rbar planes (box KE x BN)
+  CUtensorMap tm_qr[2];   // computed columns, row-major (box KE x BM)
+  CUtensorMap tm_s[2];    // S planes, column-major ld ldrow (box KE x BN)
 };
 
 namespace {
@@ -548,34 +627,54 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
-bool encode_2d(CUtensorMap* tm, void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
-               uint32_t box_inner, uint32_t box_outer) {
+bool encode_2d(CUtensorMap* tm, void* base, bool bf, uint64_t inner, uint64_t outer,
+               uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
   if (!enc) return false;
   cuuint64_t dims[2] = {inner, outer};
   cuuint64_t strides[1] = {row_bytes};
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
-                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(tm, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                   base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-template <int STAGES, int NA, int NB>
+template <bool BF, int STAGES, int NA, int NB>
 cudaError_t launch_gemm(const TcMaps& maps, const TcJob& job, int num_sms, cudaStream_t st) {
   using S = Smem<STAGES, NA, NB>;
-  const void* fn = (const void*)k_tc_gemm<STAGES, NA, NB>;
+  const void* fn = (const void*)k_tc_gemm<BF, STAGES, NA, NB>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kTotal);
   if (e != cudaSuccess) return e;
   const int tiles = job.m_tiles * job.n_tiles * job.splits;
   const int grid = std::max(1, std::min(tiles, num_sms));
-  k_tc_gemm<STAGES, NA, NB><<<grid, kThreads, S::kTotal, st>>>(maps, job);
+  k_tc_gemm<BF, STAGES, NA, NB><<<grid, kThreads, S::kTotal, st>>>(maps, job);
   return cudaGetLastError();
 }
+
+// One launch of the tensor-core kernel in the variant of the handle's mode.  split: B arrives
+// as raw FP32 and is split in shared memory (GEMM1 and the first block-reorthogonalisation
+// product); otherwise B comes from planes.  Stages: 3 x 64 KB (two products), 6 x 32 KB
+// (one product), 4 x 48 KB (BF16, one product, raw FP32 B of 64 K elements).
+cudaError_t launch_mode(const TcGemm* t, bool split, const TcMaps& maps, const TcJob& job,
+                        cudaStream_t st) {
+  const bool three = t->nplanes == 2;
+  if (!t->bf)
+    return three ? launch_gemm<false, 3, 2, 2>(maps, job, t->num_sms, st)
+                 : launch_gemm<false, 6, 1, 1>(maps, job, t->num_sms, st);
+  if (three) return launch_gemm<true, 3, 2, 2>(maps, job, t->num_sms, st);
+  return split ? launch_gemm<true, 4, 1, 2>(maps, job, t->num_sms, st)
+               : launch_gemm<true, 6, 1, 1>(maps, job, t->num_sms, st);
+}
+
+template <typename P>
+P* pl(void* p) { return static_cast<P*>(p); }
+
+int64_t round_to(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
@@ -583,19 +682,22 @@ bool tc_available() { return true; }
 
 size_t tc_panel_bytes(int64_t, int) { return 0; }
 
-size_t tc_workspace_bytes(int64_t M, int64_t N, int64_t n, int b, int reorth_block) {
-  const int64_t bkp = (b + BK - 1) / BK * BK;
-  const int64_t ldk = (M + 31) / 32 * 32;
-  const int64_t akc = std::max<int64_t>(bkp, (b + BM - 1) / BM * BM);
-  const int64_t ldrow = (n + 31) / 32 * 32;
+size_t tc_workspace_bytes(int mode, int64_t M, int64_t N, int64_t n, int b, int reorth_block) {
+  const bool bf = mode == CQR_MMA_BF16 || mode == CQR_MMA_BF16X3;
+  const size_t pe = bf ? 2 : 4;
+  const int64_t KE = bf ? 64 : 32;
+  const int64_t bkp = round_to(b, KE);
+  const int64_t ldk = round_to(M, 32);
+  const int64_t akc = std::max<int64_t>(bkp, round_to(b, BM));
+  const int64_t ldrow = round_to(n, 64);
   size_t s = 0;
-  s += 2 * al256((size_t)ldk * akc * 4);        // Ak hi/lo
-  s += 2 * al256((size_t)M * bkp * 4);          // At hi/lo
-  s += 2 * al256((size_t)bkp * N * 4);          // Rbar planes
-  s += al256((size_t)kMaxSplits * bkp * N * 4);  // split-K partials
+  s += 2 * al256((size_t)ldk * akc * pe);        // Ak hi/lo
+  s += 2 * al256((size_t)M * bkp * pe);          // At hi/lo
+  s += 2 * al256((size_t)bkp * N * pe);          // Rbar planes
+  s += al256((size_t)kMaxSplits * bkp * N * 4);  // split-K partials (FP32)
   if (reorth_block) {
-    s += 2 * al256((size_t)M * ldrow * 4);      // row-major computed columns hi/lo
-    s += 2 * al256((size_t)ldrow * akc * 4);    // S planes
+    s += 2 * al256((size_t)M * ldrow * pe);      // row-major computed columns hi/lo
+    s += 2 * al256((size_t)ldrow * akc * pe);    // S planes
   }
   return s;
 }
@@ -605,54 +707,60 @@ TcGemm* tc_create(int mode, int64_t M, int64_t N, int64_t n, int64_t b, float* Q
   TcGemm* t = new (std::nothrow) TcGemm();
   if (!t) return nullptr;
   t->mode = mode;
-  t->nplanes = mode == CQR_MMA_3XTF32 ? 2 : 1;
+  t->bf = mode == CQR_MMA_BF16 || mode == CQR_MMA_BF16X3;
+  t->nplanes = (mode == CQR_MMA_3XTF32 || mode == CQR_MMA_BF16X3) ? 2 : 1;
+  t->KE = t->bf ? 64 : 32;
+  t->pe = t->bf ? 2 : 4;
   t->M = M;
   t->N = N;
   t->b = b;
-  t->bkp = (b + BK - 1) / BK * BK;
+  t->bkp = round_to(b, t->KE);
   t->ldq = ldq;
-  t->ldk = (M + 31) / 32 * 32;
+  t->ldk = round_to(M, 32);
   t->Q = Q;
   t->num_sms = num_sms;
-  const int64_t akc = std::max<int64_t>(t->bkp, (b + BM - 1) / BM * BM);
+  const int64_t akc = std::max<int64_t>(t->bkp, round_to(b, BM));
+  const size_t pe = t->pe;
   char* p = static_cast<char*>(ws);
-  auto take = [&](size_t bytes) { char* r = p; p += al256(bytes); return reinterpret_cast<float*>(r); };
-  t->Ak_hi = take((size_t)t->ldk * akc * 4);
-  t->Ak_lo = take((size_t)t->ldk * akc * 4);
-  t->At_hi = take((size_t)M * t->bkp * 4);
-  t->At_lo = take((size_t)M * t->bkp * 4);
-  t->Bh = take((size_t)t->bkp * N * 4);
-  t->Bl = take((size_t)t->bkp * N * 4);
-  t->P = take((size_t)kMaxSplits * t->bkp * N * 4);
+  auto take = [&](size_t bytes) { char* r = p; p += al256(bytes); return static_cast<void*>(r); };
+  t->Ak_hi = take((size_t)t->ldk * akc * pe);
+  t->Ak_lo = take((size_t)t->ldk * akc * pe);
+  t->At_hi = take((size_t)M * t->bkp * pe);
+  t->At_lo = take((size_t)M * t->bkp * pe);
+  t->Bh = take((size_t)t->bkp * N * pe);
+  t->Bl = take((size_t)t->bkp * N * pe);
+  t->P = static_cast<float*>(take((size_t)kMaxSplits * t->bkp * N * 4));
   t->n = n;
-  t->ldrow = (n + 31) / 32 * 32;
+  t->ldrow = round_to(n, 64);
   t->Qr_hi = t->Qr_lo = t->Sh = t->Sl = nullptr;
   if (reorth_block) {
-    t->Qr_hi = take((size_t)M * t->ldrow * 4);
-    t->Qr_lo = take((size_t)M * t->ldrow * 4);
-    t->Sh = take((size_t)t->ldrow * akc * 4);
-    t->Sl = take((size_t)t->ldrow * akc * 4);
+    t->Qr_hi = take((size_t)M * t->ldrow * pe);
+    t->Qr_lo = take((size_t)M * t->ldrow * pe);
+    t->Sh = take((size_t)t->ldrow * akc * pe);
+    t->Sl = take((size_t)t->ldrow * akc * pe);
     // columns not yet computed are read (times zero rows of S) when kb is not a multiple of
-    // 32: keep them finite
-    if (cudaMemsetAsync(t->Qr_hi, 0, (size_t)M * t->ldrow * 4, st) != cudaSuccess ||
-        cudaMemsetAsync(t->Qr_lo, 0, (size_t)M * t->ldrow * 4, st) != cudaSuccess) {
+    // the stage K: keep them finite
+    if (cudaMemsetAsync(t->Qr_hi, 0, (size_t)M * t->ldrow * pe, st) != cudaSuccess ||
+        cudaMemsetAsync(t->Qr_lo, 0, (size_t)M * t->ldrow * pe, st) != cudaSuccess) {
       delete t;
       return nullptr;
     }
   }
+  const bool bf = t->bf;
+  const uint32_t KE = (uint32_t)t->KE;
   bool ok = true;
-  ok &= encode_2d(&t->tm_q_b, Q, (uint64_t)M, (uint64_t)N, (uint64_t)ldq * 4, BK, BN);
-  ok &= encode_2d(&t->tm_ak[0], t->Ak_hi, (uint64_t)M, (uint64_t)akc, (uint64_t)t->ldk * 4, BK, BM);
-  ok &= encode_2d(&t->tm_ak[1], t->Ak_lo, (uint64_t)M, (uint64_t)akc, (uint64_t)t->ldk * 4, BK, BM);
-  ok &= encode_2d(&t->tm_at[0], t->At_hi, (uint64_t)t->bkp, (uint64_t)M, (uint64_t)t->bkp * 4, BK, BM);
-  ok &= encode_2d(&t->tm_at[1], t->At_lo, (uint64_t)t->bkp, (uint64_t)M, (uint64_t)t->bkp * 4, BK, BM);
-  ok &= encode_2d(&t->tm_bh[0], t->Bh, (uint64_t)t->bkp, (uint64_t)N, (uint64_t)t->bkp * 4, BK, BN);
-  ok &= encode_2d(&t->tm_bh[1], t->Bl, (uint64_t)t->bkp, (uint64_t)N, (uint64_t)t->bkp * 4, BK, BN);
+  ok &= encode_2d(&t->tm_q_b, Q, false, (uint64_t)M, (uint64_t)N, (uint64_t)ldq * 4, 32, BN);
+  ok &= encode_2d(&t->tm_ak[0], t->Ak_hi, bf, (uint64_t)M, (uint64_t)akc, (uint64_t)t->ldk * pe, KE, BM);
+  ok &= encode_2d(&t->tm_ak[1], t->Ak_lo, bf, (uint64_t)M, (uint64_t)akc, (uint64_t)t->ldk * pe, KE, BM);
+  ok &= encode_2d(&t->tm_at[0], t->At_hi, bf, (uint64_t)t->bkp, (uint64_t)M, (uint64_t)t->bkp * pe, KE, BM);
+  ok &= encode_2d(&t->tm_at[1], t->At_lo, bf, (uint64_t)t->bkp, (uint64_t)M, (uint64_t)t->bkp * pe, KE, BM);
+  ok &= encode_2d(&t->tm_bh[0], t->Bh, bf, (uint64_t)t->bkp, (uint64_t)N, (uint64_t)t->bkp * pe, KE, BN);
+  ok &= encode_2d(&t->tm_bh[1], t->Bl, bf, (uint64_t)t->bkp, (uint64_t)N, (uint64_t)t->bkp * pe, KE, BN);
   if (reorth_block) {
-    ok &= encode_2d(&t->tm_qr[0], t->Qr_hi, (uint64_t)t->ldrow, (uint64_t)M, (uint64_t)t->ldrow * 4, BK, BM);
-    ok &= encode_2d(&t->tm_qr[1], t->Qr_lo, (uint64_t)t->ldrow, (uint64_t)M, (uint64_t)t->ldrow * 4, BK, BM);
-    ok &= encode_2d(&t->tm_s[0], t->Sh, (uint64_t)t->ldrow, (uint64_t)akc, (uint64_t)t->ldrow * 4, BK, BN);
-    ok &= encode_2d(&t->tm_s[1], t->Sl, (uint64_t)t->ldrow, (uint64_t)akc, (uint64_t)t->ldrow * 4, BK, BN);
+    ok &= encode_2d(&t->tm_qr[0], t->Qr_hi, bf, (uint64_t)t->ldrow, (uint64_t)M, (uint64_t)t->ldrow * pe, KE, BM);
+    ok &= encode_2d(&t->tm_qr[1], t->Qr_lo, bf, (uint64_t)t->ldrow, (uint64_t)M, (uint64_t)t->ldrow * pe, KE, BM);
+    ok &= encode_2d(&t->tm_s[0], t->Sh, bf, (uint64_t)t->ldrow, (uint64_t)akc, (uint64_t)t->ldrow * pe, KE, BN);
+    ok &= encode_2d(&t->tm_s[1], t->Sl, bf, (uint64_t)t->ldrow, (uint64_t)akc, (uint64_t)t->ldrow * pe, KE, BN);
   }
   if (!ok) {
     delete t;
@@ -668,9 +776,9 @@ void tc_set_status(TcGemm* t, int* status) { t->status = status; }
 namespace {
 int tc_splits(const TcGemm* t, int m1, int n1, int64_t* kchunk) {
   int splits = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplits, (t->num_sms + m1 * n1 - 1) / (m1 * n1)));
-  const int64_t kblocks = (t->M + BK - 1) / BK;
+  const int64_t kblocks = (t->M + t->KE - 1) / t->KE;
   if (splits > kblocks) splits = (int)kblocks;
-  *kchunk = (kblocks + splits - 1) / splits * BK;
+  *kchunk = (kblocks + splits - 1) / splits * t->KE;
   return (int)((t->M + *kchunk - 1) / *kchunk);
 }
 }  // namespace
@@ -678,13 +786,22 @@ int tc_splits(const TcGemm* t, int m1, int n1, int64_t* kchunk) {
 // 1. split the panel Q[:, kb : kb+bk] into the operand planes of both GEMMs (and, for a
 //    finished panel with block reorthogonalisation on, into the row-major computed columns)
 cudaError_t tc_split_panel(TcGemm* t, int64_t kb, int bk, bool finished, cudaStream_t st) {
-  const int bkp = (int)((bk + BK - 1) / BK * BK);
+  const int bkp = (int)round_to(bk, t->KE);
   const int m1 = (bk + BM - 1) / BM;
   dim3 grd((unsigned)((t->M + 255) / 256), (unsigned)std::max(bkp, m1 * BM));
-  float* qh = finished ? t->Qr_hi : nullptr;
-  k_split_panel<<<grd, 256, 0, st>>>(t->Q + kb * t->ldq, t->ldq, t->M, bk, bkp, m1 * BM, t->nplanes,
-                                     t->Ak_hi, t->Ak_lo, t->ldk, t->At_hi, t->At_lo, qh, t->Qr_lo,
-                                     t->ldrow, kb);
+  void* qh = finished ? t->Qr_hi : nullptr;
+  if (t->bf) {
+    using B16 = __nv_bfloat16;
+    k_split_panel<B16><<<grd, 256, 0, st>>>(t->Q + kb * t->ldq, t->ldq, t->M, bk, bkp, m1 * BM,
+                                            t->nplanes, pl<B16>(t->Ak_hi), pl<B16>(t->Ak_lo), t->ldk,
+                                            pl<B16>(t->At_hi), pl<B16>(t->At_lo), pl<B16>(qh),
+                                            pl<B16>(t->Qr_lo), t->ldrow, kb);
+  } else {
+    k_split_panel<float><<<grd, 256, 0, st>>>(t->Q + kb * t->ldq, t->ldq, t->M, bk, bkp, m1 * BM,
+                                              t->nplanes, pl<float>(t->Ak_hi), pl<float>(t->Ak_lo),
+                                              t->ldk, pl<float>(t->At_hi), pl<float>(t->At_lo),
+                                              pl<float>(qh), pl<float>(t->Qr_lo), t->ldrow, kb);
+  }
   return cudaGetLastError();
 }
 
@@ -695,15 +812,20 @@ cudaError_t tc_refresh_rows(TcGemm* t, int64_t ncols, cudaStream_t st) {
   if (!t->Qr_hi || ncols <= 0) return cudaSuccess;
   const int64_t total = t->M * ncols;
   const int blocks = (int)std::min<int64_t>(8192, (total + 255) / 256);
-  k_refresh_rows<<<blocks, 256, 0, st>>>(t->Q, t->ldq, t->M, ncols, t->nplanes, t->Qr_hi, t->Qr_lo,
-                                         t->ldrow);
+  if (t->bf)
+    k_refresh_rows<__nv_bfloat16><<<blocks, 256, 0, st>>>(t->Q, t->ldq, t->M, ncols, t->nplanes,
+                                                          pl<__nv_bfloat16>(t->Qr_hi),
+                                                          pl<__nv_bfloat16>(t->Qr_lo), t->ldrow);
+  else
+    k_refresh_rows<float><<<blocks, 256, 0, st>>>(t->Q, t->ldq, t->M, ncols, t->nplanes,
+                                                  pl<float>(t->Qr_hi), pl<float>(t->Qr_lo), t->ldrow);
   return cudaGetLastError();
 }
 
 // 2. GEMM1, split-K over the M rows: partials P[s] = Qbar^T Q[:, j0 : j0+w]
 cudaError_t tc_gemm_rbar(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t st) {
   const int three = t->nplanes == 2;
-  const int bkp = (int)((bk + BK - 1) / BK * BK);
+  const int bkp = (int)round_to(bk, t->KE);
   const int m1 = (bk + BM - 1) / BM;
   const int n1 = (int)((w + BN - 1) / BN);
   int64_t kchunk = 0;
@@ -715,7 +837,9 @@ cudaError_t tc_gemm_rbar(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t 
   maps.b[1] = t->tm_q_b;
   TcJob job{};
   job.nprod = three ? 3 : 1;
-  job.split_b_smem = three;
+  // TF32 reads the raw FP32 words directly with one product; every other mode splits B
+  const bool split = three || t->bf;
+  job.split_b_smem = split ? 1 : 0;
   job.epi = 0;
   job.m_tiles = m1;
   job.n_tiles = n1;
@@ -731,29 +855,34 @@ cudaError_t tc_gemm_rbar(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t 
   job.ldo = bkp;
   job.split_stride = (int64_t)bkp * w;
   job.status = t->status;
-  return three ? launch_gemm<3, 2, 2>(maps, job, t->num_sms, st)
-               : launch_gemm<6, 1, 1>(maps, job, t->num_sms, st);
+  return launch_mode(t, split, maps, job, st);
 }
 
 // 3. reduce the partials into R[kb.., j0..] and GEMM2's B planes
 cudaError_t tc_reduce(TcGemm* t, int64_t kb, int bk, int64_t j0, int64_t w, float* R, int64_t ldr,
                       cudaStream_t st) {
-  const int bkp = (int)((bk + BK - 1) / BK * BK);
+  const int bkp = (int)round_to(bk, t->KE);
   const int m1 = (bk + BM - 1) / BM;
   const int n1 = (int)((w + BN - 1) / BN);
   int64_t kchunk = 0;
   const int splits = tc_splits(t, m1, n1, &kchunk);
   const int64_t total = (int64_t)bkp * w;
   const int blocks = (int)std::min<int64_t>(4096, (total + 255) / 256);
-  k_tc_reduce<<<blocks, 256, 0, st>>>(t->P, splits, (int64_t)bkp * w, bkp, bk, bkp, w,
-                                      R + kb + j0 * ldr, ldr, t->nplanes, t->Bh, t->Bl);
+  if (t->bf)
+    k_tc_reduce<__nv_bfloat16><<<blocks, 256, 0, st>>>(t->P, splits, (int64_t)bkp * w, bkp, bk, bkp, w,
+                                                       R + kb + j0 * ldr, ldr, t->nplanes,
+                                                       pl<__nv_bfloat16>(t->Bh), pl<__nv_bfloat16>(t->Bl));
+  else
+    k_tc_reduce<float><<<blocks, 256, 0, st>>>(t->P, splits, (int64_t)bkp * w, bkp, bk, bkp, w,
+                                               R + kb + j0 * ldr, ldr, t->nplanes, pl<float>(t->Bh),
+                                               pl<float>(t->Bl));
   return cudaGetLastError();
 }
 
 // 4. GEMM2: Q[:, j0 : j0+w] -= Qbar Rbar (M tiles over rows, N tiles over trailing columns)
 cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t st) {
   const int three = t->nplanes == 2;
-  const int bkp = (int)((bk + BK - 1) / BK * BK);
+  const int bkp = (int)round_to(bk, t->KE);
   TcMaps maps;
   maps.a[0] = t->tm_at[0];
   maps.a[1] = t->tm_at[1];
@@ -777,8 +906,7 @@ cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_
   job.ldo = t->ldq;
   job.split_stride = 0;
   job.status = t->status;
-  return three ? launch_gemm<3, 2, 2>(maps, job, t->num_sms, st)
-               : launch_gemm<6, 1, 1>(maps, job, t->num_sms, st);
+  return launch_mode(t, false, maps, job, st);
 }
 
 // Block reorthogonalisation of panel kb .. kb+bk-1 against columns 0 .. kb-1 (four
@@ -793,18 +921,25 @@ cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr
   if (e != cudaSuccess) return e;
   e = tc_gemm_rbar(t, bk, 0, kb, st);  // partials of S^T (bk x kb)
   if (e != cudaSuccess) return e;
-  const int three = t->nplanes == 2;
-  const int bkp = (int)((bk + BK - 1) / BK * BK);
+  const int KE = t->KE;
+  const int bkp = (int)round_to(bk, KE);
   const int m1 = (bk + BM - 1) / BM;
   const int n1 = (int)((kb + BN - 1) / BN);
   int64_t kchunk = 0;
   const int splits = tc_splits(t, m1, n1, &kchunk);
-  const int64_t kbp = (kb + BK - 1) / BK * BK;
+  const int64_t kbp = round_to(kb, KE);
   {
     const int64_t total = kbp * bk;
     const int blocks = (int)std::min<int64_t>(4096, (total + 255) / 256);
-    k_tc_reduce_t<<<blocks, 256, 0, st>>>(t->P, splits, (int64_t)bkp * kb, bkp, bk, kb, kbp, R, ldr,
-                                          t->nplanes, t->Sh, t->Sl, t->ldrow);
+    if (t->bf)
+      k_tc_reduce_t<__nv_bfloat16><<<blocks, 256, 0, st>>>(t->P, splits, (int64_t)bkp * kb, bkp, bk, kb,
+                                                           kbp, R, ldr, t->nplanes,
+                                                           pl<__nv_bfloat16>(t->Sh),
+                                                           pl<__nv_bfloat16>(t->Sl), t->ldrow);
+    else
+      k_tc_reduce_t<float><<<blocks, 256, 0, st>>>(t->P, splits, (int64_t)bkp * kb, bkp, bk, kb, kbp,
+                                                   R, ldr, t->nplanes, pl<float>(t->Sh),
+                                                   pl<float>(t->Sl), t->ldrow);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -814,7 +949,7 @@ cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr
   maps.b[0] = t->tm_s[0];
   maps.b[1] = t->tm_s[1];
   TcJob job{};
-  job.nprod = three ? 3 : 1;
+  job.nprod = t->nplanes == 2 ? 3 : 1;
   job.split_b_smem = 0;
   job.epi = 1;
   job.m_tiles = (int)((t->M + BM - 1) / BM);
@@ -822,13 +957,13 @@ cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr
   // Split K (the kb computed columns) when the M x bk output has too few tiles to fill the
   // SMs; the partials go to P (capacity kMaxSplits * bkp * N floats) and are subtracted in
   // a fixed order, so the result does not depend on the schedule.
-  const int64_t kblk = kbp / BK;
+  const int64_t kblk = kbp / KE;
   const int tiles2 = job.m_tiles * job.n_tiles;
   int64_t want = std::min<int64_t>(std::min<int64_t>(kMaxSplits, kblk), t->num_sms / std::max(1, tiles2));
   const int64_t cap = (int64_t)kMaxSplits * t->bkp * t->N / (t->M * (int64_t)bk);
   want = std::min<int64_t>(want, cap);
   int64_t kchunk2 = kbp;
-  if (want > 1) kchunk2 = (kblk + want - 1) / want * BK;
+  if (want > 1) kchunk2 = (kblk + want - 1) / want * KE;
   const int splits2 = (int)((kbp + kchunk2 - 1) / kchunk2);
   job.splits = splits2;
   job.a_row0 = 0;
@@ -850,8 +985,7 @@ cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr
     job.ldo = t->M;
     job.split_stride = t->M * (int64_t)bk;
   }
-  e = three ? launch_gemm<3, 2, 2>(maps, job, t->num_sms, st)
-            : launch_gemm<6, 1, 1>(maps, job, t->num_sms, st);
+  e = launch_mode(t, false, maps, job, st);
   if (e != cudaSuccess || splits2 == 1) return e;
   *launches = 5;
   const int64_t total = t->M * (int64_t)bk;

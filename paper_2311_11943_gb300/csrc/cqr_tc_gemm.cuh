@@ -1,4 +1,5 @@
-// cqr_tc_gemm.cuh -- tensor-core (tcgen05, sm_103a) trailing update of PBMGS for FP32 storage.
+// cqr_tc_gemm.cuh -- tensor-core (tcgen05, sm_103a) trailing update of PBMGS for FP32 storage:
+// TF32 or BF16 operands (one product, or hi/lo splits with three products), FP32 accumulation.
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>
@@ -10,7 +11,7 @@ struct TcGemm;
 
 bool tc_available();
 size_t tc_panel_bytes(int64_t M, int b);
-size_t tc_workspace_bytes(int64_t M, int64_t N, int64_t n, int b, int reorth_block);
+size_t tc_workspace_bytes(int mode, int64_t M, int64_t N, int64_t n, int b, int reorth_block);
 TcGemm* tc_create(int mode, int64_t M, int64_t N, int64_t n, int64_t b, float* Q, int64_t ldq,
                   void* ws, int num_sms, int reorth_block, cudaStream_t st);
 void tc_destroy(TcGemm* t);

@@ -337,6 +337,65 @@ def test_register_and_shared_memory_panels_agree(shape, monkeypatch):
     assert rel(a["R"], ref["R"]) < n * U3X * kap
 
 
+# BF16 operands (tcgen05 kind::f16): one product carries the BF16 rounding 2^-9; the hi/lo
+# split with three products leaves the lo rounding and the dropped lo*lo term, about 2^-17.
+UBF16 = 2.0 ** -8
+UBF3 = 2.0 ** -16
+
+
+@pytest.mark.parametrize("shape", [(256, 256, 4, 4, 1, 32), (203, 96, 8, 4, 2, 20),
+                                   (640, 640, 8, 8, 2, 128)])
+def test_bf16x3_path_parity(shape):
+    m, n, p_r, p_c, f, b = shape
+    A = synth.kappa_matrix(m, n, 1e2, seed=3)
+    y = synth.rhs(m, 1, 3)
+    T = -(-n // b)
+    er = {T // 2: synth.random_erasures(p_r + f, p_c + f, f, 2, seed=5)}
+    ref = O.run(A, p_r, p_c, f, b, seed=4, erasures=er, y=y)
+    got = gpu_run(A, p_r, p_c, f, b, seed=4, erasures=er, y=y, dtype="f32", mma="bf16x3")
+    assert got["status"] == 0
+    assert got["sets"] == ref["sets"]
+    g = ref["geom"]
+    tol = n * UBF3 * 1e2
+    assert rel(got["Q"][: g.M, :n], ref["Q"][:, :n]) < tol
+    assert rel(got["R"], ref["R"]) < tol
+    assert rel(got["Qo"], ref["Qo"]) < tol
+    Q1, R1 = got["Q"][:m, :n], got["R"][:n, :n]
+    assert np.linalg.norm(A - Q1 @ R1) / np.linalg.norm(A) < 64 * UBF3
+
+
+def test_bf16_path_well_conditioned():
+    m = n = 512
+    A = synth.kappa_matrix(m, n, 4.0, seed=8)
+    ref = O.run(A, 8, 8, 2, 128, seed=1)
+    got = gpu_run(A, 8, 8, 2, 128, seed=1, dtype="f32", mma="bf16")
+    assert got["status"] == 0
+    Q1, R1 = got["Q"][:m, :n], got["R"][:n, :n]
+    assert np.linalg.norm(A - Q1 @ R1) / np.linalg.norm(A) < 8 * UBF16
+    assert rel(got["R"], ref["R"]) < n * UBF16 * 4.0
+
+
+def test_bf16x3_with_block_reorth_matches_3xtf32():
+    # the same factorisation through both split modes, block reorthogonalisation on
+    m = n = 512
+    A = synth.kappa_matrix(m, n, 1e3, seed=17)
+    res = {}
+    for mma in ("3xtf32", "bf16x3"):
+        q = B.CodedQR(m, n, 8, 8, 2, 64, dtype="f32", mma=mma, seed=6, reorth_block=True)
+        q.encode(to_dev(A, torch.float32))
+        q.factor(0, -1)
+        torch.cuda.synchronize()
+        assert q.sync_status() == 0
+        Qc, Rc = q.factors()
+        res[mma] = (to_np(Qc), to_np(Rc))
+        q.close()
+    Q, R = res["bf16x3"]
+    g = q.geo
+    Qt = Q[: g["M"], :n]
+    assert np.abs(Qt.T @ Qt - np.eye(n)).max() < 1e-4
+    assert rel(R, res["3xtf32"][1]) < n * UBF3 * 1e3
+
+
 # ----------------------------------------------------------------- block reorthogonalisation
 @pytest.mark.parametrize("dtype,mma,kappa", [("f64", "simt", 1e8), ("f32", "3xtf32", 1e4),
                                              ("f32", "simt", 1e4)])
