@@ -46,6 +46,7 @@ CONFIGS = {
 EXTRA = {
     "c4": dict(count=512, p_r=8, p_c=4, f=2, seed=4),
     "c5": dict(batch=16, m=8192, n=1024, p_r=8, p_c=8, f=1, b=128, kappa=1e3, seed=5),
+    "e1": dict(),
 }
 MODES = {"f64": ("f64", "simt"), "f32": ("f32", "simt"), "tf32": ("f32", "tf32"),
          "3xtf32": ("f32", "3xtf32"), "bf16": ("f32", "bf16"), "bf16x3": ("f32", "bf16x3")}
@@ -614,6 +615,66 @@ def run_batched(args):
     return 0
 
 
+# ------------------------------------------------------------------------ e1: MDS statistics
+def run_mds(args):
+    """E1: least |det| and largest condition number over all square submatrices of the
+    structured generator G~ = [-V V^T / 2, V] and of the completely random G~' = [G1', V]
+    (G1' i.i.d. Unif(0,1)), f = 2..6, p_r = 16, 32, 64, mean of log10 over seeded trials."""
+    import torch
+    from paper_2311_11943_gb300 import binding as B
+    from paper_2311_11943_gb300 import synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    trials = max(1, args.steps)
+    table = []
+    total_sub, total_ms = 0, 0.0
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    for p_r in (16, 32, 64):
+        for f in range(2, 7):
+            acc = {"det": [], "cond": [], "det_rand": [], "cond_rand": []}
+            for t in range(trials):
+                q = B.CodedQR(p_r, 1, p_r, 1, f, 1, dtype="f64", protect_r=False, seed=100 + t)
+                q.encode(torch.zeros((1, p_r), dtype=torch.float64, device="cuda").t())
+                Gt, _ = q.generator()      # computed on the device by encode
+                q.close()
+                Gr = Gt.copy()
+                Gr[:, :f] = synth.unif01(f, f, 100 + t)
+                for G, kd, kc in ((Gt, "det", "cond"), (Gr, "det_rand", "cond_rand")):
+                    t0 = time.perf_counter()
+                    md, mc, cnt = B.coded_qr_mds_stats(G)
+                    total_ms += (time.perf_counter() - t0) * 1e3
+                    total_sub += cnt
+                    acc[kd].append(np.log10(md[0]))
+                    acc[kc].append(np.log10(mc[0]))
+            table.append({"p_r": p_r, "f": f, **{k: float(np.mean(v)) for k, v in acc.items()}})
+    clk = clocks.stop()
+    # CPU oracle on a bounded sample: the smallest case, structured generator
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        q = B.CodedQR(16, 1, 16, 1, 3, 1, dtype="f64", protect_r=False, seed=100)
+        q.encode(torch.zeros((1, 16), dtype=torch.float64, device="cuda").t())
+        Gt, _ = q.generator()
+        q.close()
+        t0 = time.perf_counter()
+        O.mds_stats(Gt)
+        dt = time.perf_counter() - t0
+        n3 = 3 * 16 + 3 * 120 + 560
+        cpu = {"value": n3 / dt, "unit": "submatrices/s", "cores": 1, "kind": "oracle",
+               "sample": "numpy brute force, f = 3, p_r = 16 (%d submatrices), %.2f s" % (n3, dt)}
+    line = {"metric": "E1 MDS statistics: square submatrices (|det| and 2-norm condition) per second",
+            "value": total_sub / (total_ms * 1e-3), "unit": "submatrices/s", "n_gpus": 1,
+            "steps": trials, "warmup": 0, "ms_per_step": total_ms / trials,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (the library's seeded generator; G1' from a seeded Unif(0,1))",
+            "config": {"workload": "E1: f = 2..6, p_r = 16/32/64, structured vs completely "
+                       "random generator, %d trial(s) each" % trials},
+            "log10_table": table, "submatrices": total_sub, "clocks": clk, "cpu_baseline": cpu,
+            "e2e": None}
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------------------ c5: autograd
 def run_autograd(args):
     import torch
@@ -745,6 +806,8 @@ def main():
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the "
                               "oracle on the c2 workload only"}))
             return 0
+        if args.config == "e1":
+            return run_mds(args)
         return run_batched(args) if args.config == "c4" else run_autograd(args)
     cfg = CONFIGS[args.config]
     if args.impl == "reference":

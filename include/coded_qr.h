@@ -323,6 +323,18 @@ cqr_status coded_qr_adjoint_lstsq(cqr_handle h, const void* A, int64_t lda, cons
                                   int64_t ldxb, int32_t nrhs, void* Abar, int64_t ldab,
                                   void* ybar, int64_t ldyb);
 
+/* E1 MDS statistics (Theorem prob_det, Section 4.2, and the comparison of the structured
+ * generator with a completely random one that follows it): over every square submatrix S of
+ * the f x p_r matrix G (host, row-major, FP64), the least |det S| and the largest 2-norm
+ * condition number (+inf when sigma_min <= 2^-52 sigma_max).  min_det[k], max_cond[k] (host, f + 1 entries) hold
+ * the values over the k x k submatrices, k = 1..f, and entry 0 those over all of them;
+ * *count (optional) receives the number of submatrices.  One GPU thread per submatrix:
+ * |det| by LU with partial pivoting, singular values by one-sided Jacobi, FP64.
+ * 1 <= f <= 6, f <= p_r <= 64.  Allocates and frees a small device buffer; synchronises
+ * `stream` (cudaStream_t). */
+cqr_status coded_qr_mds_stats(const double* G, int32_t f, int32_t p_r, double* min_det,
+                              double* max_cond, int64_t* count, void* stream);
+
 /* Static description of a status code. */
 const char* coded_qr_errstr(cqr_status s);
 

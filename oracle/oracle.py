@@ -258,3 +258,30 @@ def run(A, p_r, p_c, f, b, seed=1, erasures=None, protect_r=True, gdist=0, tau=0
         else:
             out["x"] = solve_ls(Q[: g.m_pad, :n], R[:n, :n], yp)
     return out
+
+
+def mds_stats(G):
+    """E1 (Theorem prob_det and the comparison after it, Section 4.2): the least |det S| and
+    the largest 2-norm condition number over every square submatrix S of G, per size k
+    (index k) and overall (index 0).  Brute force over all row and column k-subsets with
+    numpy's LU determinant and SVD singular values; a condition number of 1/eps or more
+    (eps = 2^-52) is reported as +inf.  Small sizes only."""
+    import itertools
+    G = np.asarray(G, dtype=np.float64)
+    f, p = G.shape
+    mind = [np.inf] * (f + 1)
+    maxc = [0.0] * (f + 1)
+    for k in range(1, f + 1):
+        for rows in itertools.combinations(range(f), k):
+            sub = G[list(rows), :]
+            for cols in itertools.combinations(range(p), k):
+                S = sub[:, list(cols)]
+                d = abs(np.linalg.det(S))
+                sv = np.linalg.svd(S, compute_uv=False)
+                # numerically singular (sigma_min <= eps sigma_max, eps = 2^-52): +inf
+                c = np.inf if sv[-1] <= np.finfo(np.float64).eps * sv[0] else sv[0] / sv[-1]
+                mind[k] = min(mind[k], d)
+                maxc[k] = max(maxc[k], c)
+    mind[0] = min(mind[1:])
+    maxc[0] = max(maxc[1:])
+    return mind, maxc

@@ -38,7 +38,7 @@ EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "
            "coded_qr_batched_set_tuning", "coded_qr_batched_get_tuning",
            "coded_qr_batched_get_factors", "coded_qr_batched_get_decode_sets",
            "coded_qr_batched_sync_status", "coded_qr_batched_last_error",
-           "coded_qr_adjoint_qr", "coded_qr_adjoint_lstsq"]
+           "coded_qr_adjoint_qr", "coded_qr_adjoint_lstsq", "coded_qr_mds_stats"]
 CQR_BATCH_GRAPH, CQR_BATCH_POST_ORTH = 1, 2
 PROF_CLASSES = 15
 
@@ -94,6 +94,8 @@ def lib():
             "coded_qr_profile_read": [vp, C.POINTER(C.c_double), C.POINTER(i64), i32, i32],
             "coded_qr_panel_icgs_noalloc": [i32, i64, i32, vp, i64, vp, i64, C.c_double, vp, vp],
             "coded_qr_adjoint_qr": [vp, vp, i64, vp, i64, vp, i64, vp, i64],
+            "coded_qr_mds_stats": [C.POINTER(C.c_double), i32, i32, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double), C.POINTER(i64), vp],
             "coded_qr_adjoint_lstsq": [vp, vp, i64, vp, i64, vp, i64, vp, i64, i32, vp, i64, vp,
                                        i64],
             "coded_qr_batched_create": [pcfg, C.POINTER(i64), C.POINTER(i64), i32, C.POINTER(vp)],
@@ -264,6 +266,19 @@ def coded_qr_adjoint_lstsq(h, A_ptr, lda, y_ptr, ldy, x_ptr, ldx, xbar_ptr, ldxb
                            ldab, ybar_ptr, ldyb):
     return lib().coded_qr_adjoint_lstsq(h, A_ptr, lda, y_ptr, ldy, x_ptr, ldx, xbar_ptr, ldxb, nrhs,
                                         Abar_ptr or None, ldab, ybar_ptr or None, ldyb)
+
+
+def coded_qr_mds_stats(G, stream=0):
+    """(min |det| per size, max condition number per size, count) over every square
+    submatrix of G (f x p_r); index 0 of each list is the value over all sizes."""
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    f, p = G.shape
+    md = (C.c_double * (f + 1))()
+    mc = (C.c_double * (f + 1))()
+    cnt = C.c_int64(0)
+    check(lib().coded_qr_mds_stats(G.ctypes.data_as(C.POINTER(C.c_double)), f, p, md, mc,
+                                   C.byref(cnt), C.c_void_p(stream)), "coded_qr_mds_stats")
+    return list(md), list(mc), cnt.value
 
 
 def coded_qr_profile_name(k):

@@ -78,3 +78,9 @@ def batched_shapes(count, seed, p_r=8, p_c=4, m_lo=256, m_hi=8192, n_lo=32, n_hi
         if m >= 4 * n:
             shapes.append((m, n))
     return shapes
+
+
+def unif01(m, n, seed):
+    """i.i.d. Unif(0,1) entries (the completely random generator block of the MDS comparison)."""
+    rng = np.random.default_rng(seed + 15485863)
+    return rng.random((m, n))

@@ -446,3 +446,36 @@ def test_G0_is_symmetric():
         Gt, _ = O.generator(f, p_r, 8, 17, gdist)
         G0 = O.build_G0(g, Gt)
         assert np.array_equal(G0, G0.T)
+
+
+# ----------------------------------------------------------------- E1 MDS statistics
+def test_mds_stats_closed_forms():
+    G = np.array([[1.0, 2.0, 3.0], [4.0, -5.0, 6.0]])
+    mind, maxc = O.mds_stats(G)
+    # 1 x 1 submatrices: |det| = |entry|, condition number 1
+    assert mind[1] == 1.0 and maxc[1] == 1.0
+    # 2 x 2 minors, by hand: |1*-5 - 2*4| = 13, |1*6 - 3*4| = 6, |2*6 - 3*-5| = 27
+    assert mind[2] == pytest.approx(6.0, rel=1e-14)
+
+    def cond2x2(S):  # sigma^2 = (T +- sqrt(T^2 - 4 D^2)) / 2, T = |S|_F^2, D = det S
+        T = (S ** 2).sum()
+        D = S[0, 0] * S[1, 1] - S[0, 1] * S[1, 0]
+        disc = np.sqrt(T * T - 4 * D * D)
+        return np.sqrt((T + disc) / (T - disc))
+
+    worst = max(cond2x2(G[:, [a, b]]) for a, b in [(0, 1), (0, 2), (1, 2)])
+    assert maxc[2] == pytest.approx(worst, rel=1e-12)
+    assert mind[0] == 1.0 and maxc[0] == pytest.approx(worst, rel=1e-12)
+
+
+def test_mds_stats_detects_a_singular_minor():
+    G = np.array([[1.0, 2.0, 2.0, 5.0], [3.0, 1.0, 1.0, 7.0]])   # columns 1 and 2 equal
+    mind, maxc = O.mds_stats(G)
+    assert mind[2] == 0.0 and maxc[2] == np.inf
+
+
+def test_structured_generator_has_no_singular_minor():
+    for (f, p_r, seed) in [(2, 8, 1), (3, 10, 2), (4, 12, 3)]:
+        Gt, _ = O.generator(f, p_r, 4, seed)
+        mind, maxc = O.mds_stats(Gt)
+        assert mind[0] > 0.0 and np.isfinite(maxc[0])
