@@ -47,6 +47,7 @@ EXTRA = {
     "c4": dict(count=512, p_r=8, p_c=4, f=2, seed=4),
     "c5": dict(batch=16, m=8192, n=1024, p_r=8, p_c=8, f=1, b=128, kappa=1e3, seed=5),
     "e1": dict(),
+    "f3": dict(),
 }
 MODES = {"f64": ("f64", "simt"), "f32": ("f32", "simt"), "tf32": ("f32", "tf32"),
          "3xtf32": ("f32", "3xtf32"), "bf16": ("f32", "bf16"), "bf16x3": ("f32", "bf16x3")}
@@ -615,6 +616,62 @@ def run_batched(args):
     return 0
 
 
+# ------------------------------------------------------------------------ f3: panel variants
+def run_panels(args):
+    """NEXT f3: panel latency vs orthogonality on the C2 shape for the paper's ICGS and the
+    MGS / CGS1 / CGS2 variants (FP32, 3xTF32 trailing updates, block reorthogonalisation on,
+    so that the loss between panels is removed and the panel sets the orthogonality),
+    kappa 1e2 and 1e4."""
+    import torch
+    from paper_2311_11943_gb300 import binding as B
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    rows = []
+    for kappa in (1e2, 1e4):
+        cfg = dict(CONFIGS["c2"], kappa=kappa)
+        A_np, _ = make_inputs(cfg)
+        Ad = B.colmajor_empty(cfg["m"], cfg["n"], torch.float32)
+        Ad.copy_(torch.from_numpy(np.ascontiguousarray(A_np)))
+        A64 = torch.from_numpy(A_np).cuda()
+        for panel, reg in (("icgs", "1"), ("icgs", "0"), ("mgs", "0"), ("cgs1", "0"), ("cgs2", "0")):
+            os.environ["CQR_PANEL_REG"] = reg
+            q = B.CodedQR(cfg["m"], cfg["n"], cfg["p_r"], cfg["p_c"], cfg["f"], cfg["b"],
+                          dtype="f32", mma="3xtf32", seed=cfg["seed"], panel=panel,
+                          reorth_block=True)
+            q.profile(True)
+            for it in range(args.warmup + args.steps):
+                if it == args.warmup:
+                    q.profile_read(reset=True)
+                q.encode(Ad)
+                q.factor(0, -1)
+            prof = q.profile_read(reset=True)
+            st = q.sync_status()
+            Qc, Rc = q.factors()
+            M, n = q.geo["M"], cfg["n"]
+            Qt = Qc[:M, :n].double()
+            orth = (torch.eye(n, device="cuda", dtype=torch.float64) - Qt.T @ Qt).abs().max().item()
+            back = (torch.linalg.norm(A64 - Qc[:cfg["m"], :n].double() @ Rc[:n, :n].double()) /
+                    torch.linalg.norm(A64)).item()
+            q.close()
+            pm = prof["panel_icgs"][0] / args.steps
+            rows.append({"kappa": kappa, "panel": panel,
+                         "kernel": "register" if (panel == "icgs" and reg == "1") else "shared-memory",
+                         "panel_ms_per_factorisation": pm, "us_per_column": pm * 1e3 / n,
+                         "orth_coded_Q": orth, "backward_rel_fro": back, "status": st})
+    os.environ.pop("CQR_PANEL_REG", None)
+    best = min(r["panel_ms_per_factorisation"] for r in rows)
+    line = {"metric": "panel factorisation time per C2 factorisation (NEXT f3 comparison)",
+            "value": best, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": best, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 storage, 3xtf32 trailing updates",
+            "data": "synthetic (seeded U diag(sigma) V^T)",
+            "config": {"workload": "C2 shape 4096x4096, grid 8x8, f=2, b=128; ICGS / MGS / CGS1 / "
+                       "CGS2 panels, block reorthogonalisation, kappa 1e2 and 1e4, no erasure"},
+            "variants": rows, "cpu_baseline": None, "e2e": None}
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------------------ e1: MDS statistics
 def run_mds(args):
     """E1: least |det| and largest condition number over all square submatrices of the
@@ -808,6 +865,8 @@ def main():
             return 0
         if args.config == "e1":
             return run_mds(args)
+        if args.config == "f3":
+            return run_panels(args)
         return run_batched(args) if args.config == "c4" else run_autograd(args)
     cfg = CONFIGS[args.config]
     if args.impl == "reference":

@@ -84,12 +84,27 @@ typedef struct {
   int32_t reorth_block; /* 1: before each panel's ICGS, project the panel once more on all
                            computed columns (block "twice is enough"; an addition to the
                            paper's PBMGS that keeps Q_2 = G_v Q_1); 0: off */
+  int32_t panel;       /* CQR_PANEL_*: the panel factorisation (the paper's ICGS by default) */
   uint64_t seed;       /* seed of the generator's SplitMix64 stream */
   double tau;          /* ICGS criterion: reorthogonalise column j when its norm fell below
                           tau times its norm at the panel start.  0 selects 1/sqrt(2);
                           a negative value disables reorthogonalisation. */
   void* stream;        /* cudaStream_t */
 } cqr_config;
+
+/* Panel factorisation variants (a3).  ICGS is the paper's (Algorithm CGS with the
+ * reorthogonalisation of ICGS, right-looking, one reduction per column).  The others serve
+ * the latency / orthogonality comparison: MGS is the same column loop without the
+ * reorthogonalisation test; CGS1 is left-looking classical Gram-Schmidt with one reduction per
+ * column (projections and norm together, Pythagorean norm); CGS2 repeats its projection
+ * once ("twice is enough").  The variants other than ICGS run on the shared-memory panel
+ * kernels (not the register-resident FP32 one). */
+enum {
+  CQR_PANEL_ICGS = 0,
+  CQR_PANEL_MGS = 1,
+  CQR_PANEL_CGS1 = 2,
+  CQR_PANEL_CGS2 = 3
+};
 
 /* Geometry record filled by coded_qr_geometry (all int64). */
 enum {

@@ -227,6 +227,58 @@ static int icgs_panel(int64_t M, int64_t kb, int64_t bk, double tau, double* Q, 
 }
 
 /* Stand-alone panel routine (same arithmetic as inside cqro_factor). */
+/* Panel variants for the comparison of NEXT f3 (left-looking classical Gram-Schmidt,
+ * Bjorck, "Numerics of Gram-Schmidt orthogonalization", 1994):
+ *   passes = 1 ("CGS1", one reduction per column): s = Q_{:,0:j}^T p_j and |p_j|^2 from the
+ *     original p_j; p_j -= Q_{:,0:j} s; r_jj^2 = |p_j|^2 - |s|^2 (Pythagorean identity, Smoktunowicz,
+ *     Barlow & Langou 2006); loses orthogonality like u kappa^2.
+ *   passes = 2 ("CGS2", twice is enough): the projection repeated once on the result, R gets
+ *     s + s', r_jj^2 = |p'|^2 - |s'|^2; orthogonal to O(u).
+ * Columns kb .. kb+bk-1 of Q (M rows); R rows / columns kb.. receive the panel's block. */
+static int cgs_panel(int64_t M, int64_t kb, int64_t bk, int passes, double* Q, int64_t ldq,
+                     double* R, int64_t ldr) {
+  double* s = (double*)malloc(sizeof(double) * (size_t)(bk + 1));
+  int rc = CQRO_OK;
+  for (int64_t j = 0; j < bk && rc == CQRO_OK; ++j) {
+    const int64_t c = kb + j;
+    double* qc = Q + c * ldq;
+    double r2 = 0.0;
+    for (int pass = 0; pass < passes; ++pass) {
+#pragma omp parallel for schedule(static)
+      for (int64_t a = 0; a <= j; ++a) {  /* s_a = q_a^T p (a < j), s_j = p^T p */
+        const double* qa = Q + (kb + a) * ldq;
+        double acc = 0.0;
+        for (int64_t r = 0; r < M; ++r) acc += qa[r] * qc[r];
+        s[a] = acc;
+      }
+#pragma omp parallel for schedule(static)
+      for (int64_t r = 0; r < M; ++r) {
+        double acc = qc[r];
+        for (int64_t a = 0; a < j; ++a) acc -= Q[r + (kb + a) * ldq] * s[a];
+        qc[r] = acc;
+      }
+      double ss = 0.0;
+      for (int64_t a = 0; a < j; ++a) {
+        R[(kb + a) + c * ldr] += s[a];
+        ss += s[a] * s[a];
+      }
+      r2 = s[j] - ss;
+    }
+    if (!(r2 > 0.0) || !isfinite(r2)) { rc = CQRO_EBREAKDOWN; break; }
+    const double rcc = sqrt(r2);
+    R[c + c * ldr] = rcc;
+    for (int64_t r = 0; r < M; ++r) qc[r] = qc[r] / rcc;
+  }
+  free(s);
+  return rc;
+}
+
+int cqro_cgs_panel(int64_t M, int64_t kb, int64_t bk, int passes, double* Q, int64_t ldq,
+                   double* R, int64_t ldr) {
+  if (passes != 1 && passes != 2) return CQRO_EINVAL;
+  return cgs_panel(M, kb, bk, passes, Q, ldq, R, ldr);
+}
+
 int cqro_icgs_panel(int64_t M, int64_t kb, int64_t bk, double tau, double* Q, int64_t ldq,
                     double* R, int64_t ldr, int64_t* n_reorth) {
   return icgs_panel(M, kb, bk, tau, Q, ldq, R, ldr, n_reorth);
@@ -269,8 +321,10 @@ static void block_reorth(int64_t M, int64_t kb, int64_t bk, double* Q, int64_t l
   free(S);
 }
 
-int cqro_factor2(int64_t M, int64_t N, int64_t n, int64_t b, int t0, int t1, double tau,
-                 int reorth_block, double* Q, int64_t ldq, double* R, int64_t ldr,
+/* panel: 0 ICGS (the paper's listing with the reorthogonalisation test), 1 MGS (the same
+ * right-looking column loop without it), 2 CGS1, 3 CGS2 (see cgs_panel). */
+int cqro_factor3(int64_t M, int64_t N, int64_t n, int64_t b, int t0, int t1, double tau,
+                 int reorth_block, int panel, double* Q, int64_t ldq, double* R, int64_t ldr,
                  int64_t* n_reorth) {
   if (b <= 0 || M <= 0 || n <= 0 || N < n) return CQRO_EINVAL;
   const int T = (int)((n + b - 1) / b);
@@ -279,7 +333,11 @@ int cqro_factor2(int64_t M, int64_t N, int64_t n, int64_t b, int t0, int t1, dou
     const int64_t kb = (int64_t)t * b;
     const int64_t bk = (kb + b <= n) ? b : n - kb;
     if (reorth_block && kb > 0) block_reorth(M, kb, bk, Q, ldq, R, ldr);
-    int rc = icgs_panel(M, kb, bk, tau, Q, ldq, R, ldr, n_reorth);
+    int rc;
+    if (panel == 2 || panel == 3)
+      rc = cgs_panel(M, kb, bk, panel - 1, Q, ldq, R, ldr);
+    else
+      rc = icgs_panel(M, kb, bk, panel == 1 ? -1.0 : tau, Q, ldq, R, ldr, n_reorth);
     if (rc != CQRO_OK) return rc;
     const int64_t j0 = kb + bk;
     if (j0 >= N) continue;
@@ -300,6 +358,12 @@ int cqro_factor2(int64_t M, int64_t N, int64_t n, int64_t b, int t0, int t1, dou
     }
   }
   return CQRO_OK;
+}
+
+int cqro_factor2(int64_t M, int64_t N, int64_t n, int64_t b, int t0, int t1, double tau,
+                 int reorth_block, double* Q, int64_t ldq, double* R, int64_t ldr,
+                 int64_t* n_reorth) {
+  return cqro_factor3(M, N, n, b, t0, t1, tau, reorth_block, 0, Q, ldq, R, ldr, n_reorth);
 }
 
 int cqro_factor(int64_t M, int64_t N, int64_t n, int64_t b, int t0, int t1, double tau,

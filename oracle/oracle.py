@@ -42,6 +42,9 @@ def lib():
                                   i64, C.POINTER(i64)]
         L.cqro_factor2.argtypes = [i64, i64, i64, i64, C.c_int, C.c_int, C.c_double, C.c_int, d,
                                    i64, d, i64, C.POINTER(i64)]
+        L.cqro_factor3.argtypes = [i64, i64, i64, i64, C.c_int, C.c_int, C.c_double, C.c_int,
+                                   C.c_int, d, i64, d, i64, C.POINTER(i64)]
+        L.cqro_cgs_panel.argtypes = [i64, i64, i64, C.c_int, d, i64, d, i64]
         L.cqro_inject.argtypes = [C.POINTER(Geom), C.POINTER(C.c_int), C.c_int,
                                   C.POINTER(C.c_uint8), d, i64, d, i64]
         L.cqro_invert_small.argtypes = [C.c_int, d, d]
@@ -118,12 +121,23 @@ def icgs_panel(Q, R, kb, bk, tau=0.7071067811865476):
     return nre.value
 
 
-def factor(Q, R, n, b, t0=0, t1=-1, tau=0.7071067811865476, reorth_block=False):
+PANELS = {"icgs": 0, "mgs": 1, "cgs1": 2, "cgs2": 3}
+
+
+def cgs_panel(Q, R, kb, bk, passes):
+    """Left-looking classical Gram-Schmidt on columns kb..kb+bk-1 (passes 1 or 2)."""
+    _chk(lib().cqro_cgs_panel(Q.shape[0], kb, bk, passes, _p(Q), _ld(Q), _p(R), _ld(R)),
+         "cgs_panel")
+
+
+def factor(Q, R, n, b, t0=0, t1=-1, tau=0.7071067811865476, reorth_block=False, panel="icgs"):
     """a3-a5: PBMGS panels t0..t1-1 in place on Q (M x N) and R (N x N). Returns #reorth.
-    reorth_block: project each panel once more on all computed columns before its ICGS."""
+    reorth_block: project each panel once more on all computed columns before its ICGS.
+    panel: "icgs" (the paper's), "mgs" (no reorthogonalisation test), "cgs1" / "cgs2"
+    (left-looking classical Gram-Schmidt, one / two passes)."""
     nre = C.c_int64(0)
-    rc = lib().cqro_factor2(Q.shape[0], Q.shape[1], n, b, t0, t1, tau, int(bool(reorth_block)),
-                            _p(Q), _ld(Q), _p(R), _ld(R), C.byref(nre))
+    rc = lib().cqro_factor3(Q.shape[0], Q.shape[1], n, b, t0, t1, tau, int(bool(reorth_block)),
+                            PANELS[panel], _p(Q), _ld(Q), _p(R), _ld(R), C.byref(nre))
     _chk(rc, "factor")
     return nre.value
 
@@ -208,7 +222,7 @@ def solve_ls(Q1, R, y):
 
 
 def run(A, p_r, p_c, f, b, seed=1, erasures=None, protect_r=True, gdist=0, tau=0.7071067811865476,
-        y=None, Gt=None, Gh=None, keep_states=False, reorth_block=False):
+        y=None, Gt=None, Gh=None, keep_states=False, reorth_block=False, panel="icgs"):
     """The whole hot path on the CPU: generator, encode, PBMGS with erasures injected at the
     start of the listed panels (dict panel -> list of (i, j)) and recovered, post-orth, solve.
 
@@ -236,7 +250,7 @@ def run(A, p_r, p_c, f, b, seed=1, erasures=None, protect_r=True, gdist=0, tau=0
             s, k = recover(g, Gt, Gh, mask, Q, R)
             sets += s
             nrec += k
-        nre += factor(Q, R, n, b, t, t + 1, tau, reorth_block)
+        nre += factor(Q, R, n, b, t, t + 1, tau, reorth_block, panel)
         if keep_states:
             states.append((Q.copy(order="F"), R.copy(order="F")))
     out = dict(geom=g, Gt=Gt, Gh=Gh, At=At, Q=Q, R=R, sets=sets, n_recovered=nrec,

@@ -21,6 +21,7 @@ CQR_MMA_SIMT, CQR_MMA_TF32, CQR_MMA_3XTF32, CQR_MMA_BF16, CQR_MMA_BF16X3 = 0, 1,
 MMA_NAMES = {"simt": CQR_MMA_SIMT, "tf32": CQR_MMA_TF32, "3xtf32": CQR_MMA_3XTF32,
              "bf16": CQR_MMA_BF16, "bf16x3": CQR_MMA_BF16X3}
 CQR_G_UNIF01, CQR_G_NORMAL = 0, 1
+PANEL_NAMES = {"icgs": 0, "mgs": 1, "cgs1": 2, "cgs2": 3}
 CQR_RUN_HOST_BUFFERS = 1
 GEO_FIELDS = ["m", "n", "mb", "nb", "m_pad", "c", "d", "M", "N", "ldq", "ldr", "grid_rows",
               "grid_cols", "panels"]
@@ -47,7 +48,8 @@ class Config(C.Structure):
     _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("p_r", C.c_int32), ("p_c", C.c_int32),
                 ("f", C.c_int32), ("b", C.c_int32), ("dtype", C.c_int32), ("mma", C.c_int32),
                 ("protect_r", C.c_int32), ("gdist", C.c_int32), ("nrhs_max", C.c_int32),
-                ("reorth_block", C.c_int32), ("seed", C.c_uint64), ("tau", C.c_double),
+                ("reorth_block", C.c_int32), ("panel", C.c_int32), ("seed", C.c_uint64),
+                ("tau", C.c_double),
                 ("stream", C.c_void_p)]
 
 
@@ -428,7 +430,7 @@ class CodedQR:
 
     def __init__(self, m, n, p_r, p_c, f, b, dtype="f64", mma="simt", protect_r=True,
                  gdist=CQR_G_UNIF01, nrhs_max=1, seed=1, tau=0.0, stream=None, workspace=None,
-                 reorth_block=False):
+                 reorth_block=False, panel="icgs"):
         import torch
         self.torch = torch
         self.tdtype = torch.float64 if dtype in ("f64", "float64") else torch.float32
@@ -440,6 +442,7 @@ class CodedQR:
         cfg.gdist = gdist
         cfg.nrhs_max = nrhs_max
         cfg.reorth_block = int(bool(reorth_block))
+        cfg.panel = PANEL_NAMES[panel]
         cfg.seed = seed
         cfg.tau = tau
         if stream is None:

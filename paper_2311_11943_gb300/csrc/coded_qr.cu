@@ -65,6 +65,7 @@ cqr_status validate(const cqr_config* c) {
   if (c->mma != CQR_MMA_SIMT && !tc_available()) return CQR_ENOTSUP;
   if (c->gdist != CQR_G_UNIF01 && c->gdist != CQR_G_NORMAL) return CQR_EINVAL;
   if (c->nrhs_max < 0) return CQR_EINVAL;
+  if (c->panel < CQR_PANEL_ICGS || c->panel > CQR_PANEL_CGS2) return CQR_EINVAL;
   return CQR_OK;
 }
 
@@ -278,6 +279,7 @@ cqr_status create_common(const cqr_config* cfg, void* ws, size_t bytes, bool own
   h->g = make_geo(&h->cfg);
   h->esz = cfg->dtype == CQR_F64 ? 8 : 4;
   h->tau = cfg->tau == 0.0 ? 0.7071067811865476 : cfg->tau;
+  if (cfg->panel == CQR_PANEL_MGS) h->tau = -1.0;  // the same column loop, no reorthogonalisation
   h->st = reinterpret_cast<cudaStream_t>(cfg->stream);
   if (cudaGetDevice(&h->dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev) != cudaSuccess) {
@@ -369,7 +371,8 @@ cqr_status panel_step(cqr_handle h, int t) {
       h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, false);
     h->reg_ok = false;
     const char* env = getenv("CQR_PANEL_REG");
-    if (sizeof(T) == 4 && !(env && env[0] == '0') &&
+    const bool left_looking = h->cfg.panel == CQR_PANEL_CGS1 || h->cfg.panel == CQR_PANEL_CGS2;
+    if (sizeof(T) == 4 && !(env && env[0] == '0') && !left_looking &&
         plan_panel_reg(g.M, bk, &h->reg_rpl, &h->reg_cpw, &h->reg_G))
       h->reg_ok = panel_reg_cluster_fits(h->reg_rpl, h->reg_cpw, h->reg_G);
     h->plan_bk = bk;
@@ -382,8 +385,9 @@ cqr_status panel_step(cqr_handle h, int t) {
                           g.ldq, reinterpret_cast<float*>(R + kb + kb * g.ldr), g.ldr, g.M, bk, h->tau,
                           h->B.status, (int)kb, h->st));
     } else {
+      const int variant = h->cfg.panel == CQR_PANEL_CGS1 ? 1 : (h->cfg.panel == CQR_PANEL_CGS2 ? 2 : 0);
       CK(launch_panel<T>(pp, Q + kb * g.ldq, g.ldq, R + kb + kb * g.ldr, g.ldr, g.M, bk, h->tau,
-                         ptr<T>(h->B.part), h->B.bar, h->B.status, (int)kb, h->st));
+                         ptr<T>(h->B.part), h->B.bar, h->B.status, (int)kb, h->st, variant));
     }
   }
   const int64_t j0 = kb + bk;

@@ -54,10 +54,12 @@ bool panel_reg_cluster_fits(int rpl, int cpw, int G);
 cudaError_t launch_panel_reg(int rpl, int cpw, int G, float* Q, int64_t ldq, float* R, int64_t ldr,
                              int64_t M, int bk, double tau, int* status, int col0, cudaStream_t st);
 
+// variant: 0 the paper's ICGS panel (MGS order; no reorthogonalisation when tau <= 0),
+// 1 left-looking CGS with one reduction per column, 2 CGS2.
 template <typename T>
 cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t ldr, int64_t M,
                          int bk, double tau, T* part, unsigned* bar, int* status, int col0,
-                         cudaStream_t st);
+                         cudaStream_t st, int variant = 0);
 
 // Rbar partials: P[s] (bk x w, col-major) = Qbar^T Qtrail over K-split s.
 template <typename T>

@@ -457,6 +457,100 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
   if (CL) cluster_sync_all();  // peers may still read this CTA's partials
 }
 
+// Left-looking classical Gram-Schmidt on the panel (the variants compared in NEXT f3):
+// per column j and pass, one reduction gives s_a = q_a^T p_j (a < j) and |p_j|^2 from the
+// current p_j; then p_j -= Q_{:,0:j} s, R[0:j, j] += s, r_jj^2 = |p_j|^2 - |s|^2 (Pythagorean).
+// PASSES = 1: one reduction per column (orthogonality ~ u kappa^2); PASSES = 2: CGS2.
+// Same slices, reductions and synchronisation variants as k_panel.
+template <typename T, int RPL, bool CL, bool SMEM, int PASSES>
+__global__ void __launch_bounds__(kNT, 1) k_panel_cgs(T* __restrict__ Q, int64_t ldq, T* __restrict__ R,
+                                                       int64_t ldr, int64_t M, int bk, int rpc,
+                                                       int rpc_pad, double tau2, T* gpart,
+                                                       unsigned* bar, int* status, int col0) {
+  constexpr int VW = (SMEM && sizeof(T) == 4 && RPL % 2 == 0) ? 2 : 1;
+  constexpr int NV = RPL / VW;
+  using L = LaneOps<T, VW>;
+  using V = typename L::V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int g = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int pld = (bk + 3) / 4 * 4;
+  const int64_t row0 = (int64_t)g * rpc;
+  const int nr = (int)((M - row0) < rpc ? (M - row0) : rpc);
+  T* sm = reinterpret_cast<T*>(smraw);
+  T* small = sm + (SMEM ? (size_t)bk * rpc_pad : 0);
+  T* sv = small + 2 * pld;
+  Ctx<T> c;
+  c.base = SMEM ? sm : Q + row0;
+  c.cs = SMEM ? rpc_pad : ldq;
+  c.nr = nr;
+  c.pld = pld;
+  c.gpart = gpart;
+  c.red = sv + 2 * pld;
+  c.lpart = c.red + (CL ? 0 : 8 * 2 * pld);
+  c.bar = bar;
+  c.status = status;
+  c.target = 0;
+  (void)tau2;
+  int step = 0;
+  auto ok_row = [&](int r) { return SMEM ? true : (r < nr); };
+  const int nrows = SMEM ? rpc : nr;
+  if (SMEM)
+    for (int a = 0; a < bk; ++a)
+      for (int r = tid; r < rpc; r += kNT)
+        sm[(size_t)a * rpc_pad + r] = (r < nr) ? Q[row0 + r + a * ldq] : T(0);
+  __syncthreads();
+  for (int j = 0; j < bk; ++j) {
+    T* pj = c.base + j * c.cs;
+    T r2 = T(0);
+    for (int pass = 0; pass < PASSES; ++pass) {
+      V pv[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        const int r = L::row(i, lane);
+        pv[i] = ok_row(r) ? L::ld(pj + r) : L::zero();
+      }
+      for (int a = warp; a <= j; a += kNW) {
+        const T* pa = c.base + a * c.cs;
+        V d = L::zero();
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+          const int r = L::row(i, lane);
+          if (ok_row(r)) d = L::fma(L::ld(pa + r), pv[i], d);
+        }
+        const T s0 = warp_sum(L::sum(d));
+        if (lane == 0) put_partial<T, CL>(c, a, s0, step);
+      }
+      if (!sync_reduce<T, CL>(c, 0, j + 1, sv, step++, 5)) return;
+      for (int r = tid; r < nrows; r += kNT) {
+        T acc = pj[r];
+        for (int a = 0; a < j; ++a) acc -= c.base[a * c.cs + r] * sv[a];
+        pj[r] = acc;
+      }
+      T ss = T(0);
+      for (int a = 0; a < j; ++a) ss += sv[a] * sv[a];
+      r2 = sv[j] - ss;
+      if (g == 0)
+        for (int a = tid; a < j; a += kNT) R[a + j * ldr] += sv[a];
+      __syncthreads();
+    }
+    if (!(r2 > T(0)) || !isfinite(r2)) {
+      if (g == 0 && tid == 0) set_status(status, CQR_EBREAKDOWN, col0 + j);
+      if (CL) cluster_sync_all();
+      return;
+    }
+    const T rjj = sqrt(r2);
+    const T inv = T(1) / rjj;
+    if (g == 0 && tid == 0) R[j + j * ldr] = rjj;
+    for (int r = tid; r < nrows; r += kNT) pj[r] *= inv;
+    __syncthreads();
+  }
+  if (SMEM)
+    for (int a = 0; a < bk; ++a)
+      for (int r = tid; r < nr; r += kNT) Q[row0 + r + a * ldq] = sm[(size_t)a * rpc_pad + r];
+  if (CL) cluster_sync_all();  // peers may still read this CTA's partials
+}
+
 size_t small_bytes(int bk, size_t elem, bool cl) {
   const int pld = (bk + 3) / 4 * 4;
   // v (2 pld, includes eta), sv (2 pld), then either red [8][2 pld] or lpart [2][2 pld]
@@ -468,23 +562,33 @@ int env_int(const char* name, int dflt) {
   return s ? atoi(s) : dflt;
 }
 
+template <typename T, int RPL, int PASSES>
+const void* cgs_of(bool cl, bool smem) {
+  if (cl) return (const void*)k_panel_cgs<T, RPL, true, true, PASSES>;
+  if (smem) return (const void*)k_panel_cgs<T, RPL, false, true, PASSES>;
+  return (const void*)k_panel_cgs<T, RPL, false, false, PASSES>;
+}
+
+// variant: 0 the paper's ICGS (MGS when tau2 <= 0), 1 CGS1, 2 CGS2
 template <typename T, int RPL>
-const void* kernel_of(bool cl, bool smem) {
+const void* kernel_of(bool cl, bool smem, int variant) {
+  if (variant == 1) return cgs_of<T, RPL, 1>(cl, smem);
+  if (variant == 2) return cgs_of<T, RPL, 2>(cl, smem);
   if (cl) return (const void*)k_panel<T, RPL, true, true>;
   if (smem) return (const void*)k_panel<T, RPL, false, true>;
   return (const void*)k_panel<T, RPL, false, false>;
 }
 
 template <typename T>
-const void* pick_kernel(int rpl, bool cl, bool smem) {
+const void* pick_kernel(int rpl, bool cl, bool smem, int variant = 0) {
   switch (rpl) {
-    case 4: return kernel_of<T, 4>(cl, smem);
-    case 6: return kernel_of<T, 6>(cl, smem);
-    case 8: return kernel_of<T, 8>(cl, smem);
-    case 12: return kernel_of<T, 12>(cl, smem);
-    case 16: return kernel_of<T, 16>(cl, smem);
-    case 24: return kernel_of<T, 24>(cl, smem);
-    default: return kernel_of<T, 32>(cl, smem);
+    case 4: return kernel_of<T, 4>(cl, smem, variant);
+    case 6: return kernel_of<T, 6>(cl, smem, variant);
+    case 8: return kernel_of<T, 8>(cl, smem, variant);
+    case 12: return kernel_of<T, 12>(cl, smem, variant);
+    case 16: return kernel_of<T, 16>(cl, smem, variant);
+    case 24: return kernel_of<T, 24>(cl, smem, variant);
+    default: return kernel_of<T, 32>(cl, smem, variant);
   }
 }
 
@@ -550,7 +654,7 @@ PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_clu
 template <typename T>
 cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t ldr, int64_t M,
                          int bk, double tau, T* part, unsigned* bar, int* status, int col0,
-                         cudaStream_t st) {
+                         cudaStream_t st, int variant) {
   if (pp.G > 1 && !pp.cluster) {
     cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
@@ -559,7 +663,7 @@ cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t l
   double tau2 = tau > 0.0 ? tau * tau : -1.0;
   int rpc = pp.rpc, rpc_pad = pp.rpc_pad;
   void* args[] = {&Q, &ldq, &R, &ldr, &M, &bk, &rpc, &rpc_pad, &tau2, &part, &bar, &status, &col0};
-  const void* fn = pick_kernel<T>(rpl, pp.cluster != 0, pp.smem != 0);
+  const void* fn = pick_kernel<T>(rpl, pp.cluster != 0, pp.smem != 0, variant);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)pp.smem_bytes);
   if (e != cudaSuccess) return e;
@@ -620,10 +724,11 @@ size_t panel_partial_bytes(int bk, size_t elem, int num_sms) {
 }
 
 template cudaError_t launch_panel<float>(const PanelPlan&, float*, int64_t, float*, int64_t, int64_t,
-                                         int, double, float*, unsigned*, int*, int, cudaStream_t);
+                                         int, double, float*, unsigned*, int*, int, cudaStream_t,
+                                         int);
 template cudaError_t launch_panel<double>(const PanelPlan&, double*, int64_t, double*, int64_t,
                                           int64_t, int, double, double*, unsigned*, int*, int,
-                                          cudaStream_t);
+                                          cudaStream_t, int);
 template bool panel_cluster_fits<float>(const PanelPlan&);
 template bool panel_cluster_fits<double>(const PanelPlan&);
 

@@ -479,3 +479,40 @@ def test_structured_generator_has_no_singular_minor():
         Gt, _ = O.generator(f, p_r, 4, seed)
         mind, maxc = O.mds_stats(Gt)
         assert mind[0] > 0.0 and np.isfinite(maxc[0])
+
+
+# ----------------------------------------------------------------- panel variants (NEXT f3)
+def _orth(Q):
+    return np.abs(Q.T @ Q - np.eye(Q.shape[1])).max()
+
+
+def test_panel_variants_follow_their_known_orthogonality_scaling():
+    # one panel over a whole 600 x 80 matrix with kappa 1e5: CGS2 and ICGS orthogonal to O(u),
+    # MGS loses like u kappa, CGS1 (Pythagorean norm) like u kappa^2 (Bjorck 1994; Giraud,
+    # Langou & Rozloznik 2005; Smoktunowicz, Barlow & Langou 2006)
+    m, n, kappa = 600, 80, 1e5
+    u = np.finfo(np.float64).eps / 2
+    A = synth.kappa_matrix(m, n, kappa, 7)
+    orth = {}
+    for panel in ("icgs", "mgs", "cgs1", "cgs2"):
+        Q = np.asfortranarray(A.copy())
+        R = np.zeros((n, n), order="F")
+        O.factor(Q, R, n, n, panel=panel)
+        assert np.linalg.norm(A - Q @ R) / np.linalg.norm(A) < 50 * n * u, panel
+        assert np.allclose(np.tril(R, -1), 0.0), panel
+        orth[panel] = _orth(Q)
+    assert orth["cgs2"] < 100 * n * u and orth["icgs"] < 100 * n * u
+    assert 10 * u * kappa * 1e-3 < orth["mgs"] < 10 * n * u * kappa
+    assert orth["mgs"] < orth["cgs1"] < 10 * n * u * kappa ** 2
+
+
+def test_panel_variants_agree_with_householder_r():
+    m, n = 300, 40
+    A = synth.kappa_matrix(m, n, 1e2, 3)
+    Rh = np.linalg.qr(A, mode="r")
+    Rh = np.diag(np.sign(np.diag(Rh))) @ Rh
+    for panel in ("mgs", "cgs1", "cgs2"):
+        Q = np.asfortranarray(A.copy())
+        R = np.zeros((n, n), order="F")
+        O.factor(Q, R, n, 16, panel=panel)
+        assert np.abs(R - Rh).max() / np.abs(Rh).max() < 1e-12, panel
