@@ -85,6 +85,13 @@ typedef struct {
                            computed columns (block "twice is enough"; an addition to the
                            paper's PBMGS that keeps Q_2 = G_v Q_1); 0: off */
   int32_t panel;       /* CQR_PANEL_*: the panel factorisation (the paper's ICGS by default) */
+  int32_t in_node;     /* 0: out-of-node checksum storage (f checksum node rows / columns, the
+                          paper's main setting); 1: in-node storage (Section 5): K = f + f
+                          ceil(f / (p_r - f)) checksum blocks per code hosted by the data nodes
+                          with the load-balanced distribution (Definition innode_distr); the
+                          vertical generator is the K x p_r structured matrix of Construction
+                          in_node_qr, encoded conventionally (Remark alt_in_node); needs
+                          2 K <= p_r and, with protect_r, p_c = p_r */
   uint64_t seed;       /* seed of the generator's SplitMix64 stream */
   double tau;          /* ICGS criterion: reorthogonalise column j when its norm fell below
                           tau times its norm at the panel start.  0 selects 1/sqrt(2);
@@ -110,7 +117,7 @@ enum {
 enum {
   CQR_GEO_M = 0, CQR_GEO_N, CQR_GEO_MB, CQR_GEO_NB, CQR_GEO_MPAD, CQR_GEO_C, CQR_GEO_D,
   CQR_GEO_MROWS, CQR_GEO_NCOLS, CQR_GEO_LDQ, CQR_GEO_LDR, CQR_GEO_GRID_ROWS,
-  CQR_GEO_GRID_COLS, CQR_GEO_PANELS, CQR_GEO_COUNT
+  CQR_GEO_GRID_COLS, CQR_GEO_PANELS, CQR_GEO_CODE_BLOCKS, CQR_GEO_COUNT
 };
 
 /* Bytes of device workspace a handle with this configuration needs (for coded_qr_create_in). */
@@ -159,6 +166,13 @@ cqr_status coded_qr_inject_erasure(cqr_handle h, const int32_t* tiles, int32_t c
  * *n_recovered (host, may be NULL) receives the number of Q tiles rebuilt.  On
  * CQR_EUNRECOVERABLE nothing is modified and the erasures stay pending. */
 cqr_status coded_qr_recover(cqr_handle h, int32_t* n_recovered);
+
+/* a6 by node: nodes holds count pairs (node row, node column).  Out-of-node storage: nodes of
+ * the extended (p_r + f) x (p_c + f) grid, each holding one tile (same as
+ * coded_qr_inject_erasure).  In-node storage: nodes of the p_r x p_c grid; a failed node loses
+ * its data tile and every checksum tile it hosts.  coded_qr_run's plan uses the same node
+ * coordinates. */
+cqr_status coded_qr_inject_node_failure(cqr_handle h, const int32_t* nodes, int32_t count);
 
 /* a8.  Post-orthogonalisation (Theorem "G_0", Eq. (G0_formula1); sparse block pipeline of
  * the overhead proof): Qo = G_0 Q_1 (m_pad x n) with G_0 = [[I + G_1, V], [V^T, -I]].

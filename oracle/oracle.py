@@ -299,3 +299,47 @@ def mds_stats(G):
     mind[0] = min(mind[1:])
     maxc[0] = max(maxc[1:])
     return mind, maxc
+
+
+# ------------------------------------------------------------------ in-node checksum storage
+def in_node_checks(P, L, f):
+    """Theorem in_node_opt with equality: K = f L / P + f ceil(f L / ((P - f) P)) checksum blocks
+    (P nodes, L data blocks, P | L)."""
+    return f * L // P + f * (-(-(f * L) // ((P - f) * P)))
+
+
+def in_node_hosts(K, P):
+    """Load-balanced in-node checksum distribution (Definition innode_distr): checksum block k
+    goes to node (k P) // K when K <= P (spread over the nodes), else to node k mod P; either
+    way K - P floor(K/P) nodes host ceil(K/P) blocks and the others floor(K/P)."""
+    return [(k * P) // K if K <= P else k % P for k in range(K)]
+
+
+def node_tiles(p_r, p_c, K, protect_r, i, j):
+    """Every tile (I, J) of the encoded grid hosted by node (i, j) of the p_r x p_c node grid:
+    data tile (i, j), the vertical checksum tiles of column j hosted by row node i, the
+    horizontal checksum tiles of row i hosted by column node j, and the checksum-of-checksum
+    tiles hosted by (i, j)."""
+    hv = in_node_hosts(K, p_r)
+    hh = in_node_hosts(K, p_c) if protect_r else []
+    rows = [i] + [p_r + k for k in range(K) if hv[k] == i]
+    cols = [j] + [p_c + l for l in range(len(hh)) if hh[l] == j]
+    return [(I, J) for I in rows for J in cols]
+
+
+def run_in_node(A, p, f, b, seed=1, node_failures=None, protect_r=True, tau=0.7071067811865476,
+                y=None):
+    """The coded QR with in-node checksum storage (Section 5, Construction in_node and
+    Remark alt_in_node; the Q generator of Construction in_node_qr): K checksum blocks per code
+    on a p x p node grid, the structured K x p generator, node failures {panel t: [(i, j)]}
+    erasing every tile their node hosts.  Returns oracle.run's dict plus K."""
+    K = in_node_checks(p, p, f)
+    er = {}
+    for t, nodes in (node_failures or {}).items():
+        tiles = []
+        for (i, j) in nodes:
+            tiles += node_tiles(p, p, K, protect_r, i, j)
+        er[t] = tiles
+    out = run(A, p, p, K, b, seed=seed, erasures=er, protect_r=protect_r, tau=tau, y=y)
+    out["K"] = K
+    return out

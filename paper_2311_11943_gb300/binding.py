@@ -24,7 +24,7 @@ CQR_G_UNIF01, CQR_G_NORMAL = 0, 1
 PANEL_NAMES = {"icgs": 0, "mgs": 1, "cgs1": 2, "cgs2": 3}
 CQR_RUN_HOST_BUFFERS = 1
 GEO_FIELDS = ["m", "n", "mb", "nb", "m_pad", "c", "d", "M", "N", "ldq", "ldr", "grid_rows",
-              "grid_cols", "panels"]
+              "grid_cols", "panels", "code_blocks"]
 
 EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "coded_qr_destroy",
            "coded_qr_geometry", "coded_qr_encode", "coded_qr_factor", "coded_qr_inject_erasure",
@@ -39,7 +39,8 @@ EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "
            "coded_qr_batched_set_tuning", "coded_qr_batched_get_tuning",
            "coded_qr_batched_get_factors", "coded_qr_batched_get_decode_sets",
            "coded_qr_batched_sync_status", "coded_qr_batched_last_error",
-           "coded_qr_adjoint_qr", "coded_qr_adjoint_lstsq", "coded_qr_mds_stats"]
+           "coded_qr_adjoint_qr", "coded_qr_adjoint_lstsq", "coded_qr_mds_stats",
+           "coded_qr_inject_node_failure"]
 CQR_BATCH_GRAPH, CQR_BATCH_POST_ORTH = 1, 2
 PROF_CLASSES = 15
 
@@ -48,8 +49,8 @@ class Config(C.Structure):
     _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("p_r", C.c_int32), ("p_c", C.c_int32),
                 ("f", C.c_int32), ("b", C.c_int32), ("dtype", C.c_int32), ("mma", C.c_int32),
                 ("protect_r", C.c_int32), ("gdist", C.c_int32), ("nrhs_max", C.c_int32),
-                ("reorth_block", C.c_int32), ("panel", C.c_int32), ("seed", C.c_uint64),
-                ("tau", C.c_double),
+                ("reorth_block", C.c_int32), ("panel", C.c_int32), ("in_node", C.c_int32),
+                ("seed", C.c_uint64), ("tau", C.c_double),
                 ("stream", C.c_void_p)]
 
 
@@ -82,6 +83,7 @@ def lib():
             "coded_qr_encode": [vp, vp, i64],
             "coded_qr_factor": [vp, i32, i32],
             "coded_qr_inject_erasure": [vp, C.POINTER(i32), i32],
+            "coded_qr_inject_node_failure": [vp, C.POINTER(i32), i32],
             "coded_qr_recover": [vp, C.POINTER(i32)],
             "coded_qr_post_orth": [vp, vp, i64, vp, i64, vp, i64, i32],
             "coded_qr_solve": [vp, vp, i64, vp, i64, i32],
@@ -182,6 +184,11 @@ def coded_qr_factor(h, t0, t1=-1):
 def coded_qr_inject_erasure(h, tiles):
     flat = (C.c_int32 * max(1, 2 * len(tiles)))(*[int(v) for t in tiles for v in t])
     return lib().coded_qr_inject_erasure(h, flat, len(tiles))
+
+
+def coded_qr_inject_node_failure(h, nodes):
+    flat = (C.c_int32 * max(1, 2 * len(nodes)))(*[v for t in nodes for v in t])
+    return lib().coded_qr_inject_node_failure(h, flat, len(nodes))
 
 
 def coded_qr_recover(h):
@@ -430,7 +437,7 @@ class CodedQR:
 
     def __init__(self, m, n, p_r, p_c, f, b, dtype="f64", mma="simt", protect_r=True,
                  gdist=CQR_G_UNIF01, nrhs_max=1, seed=1, tau=0.0, stream=None, workspace=None,
-                 reorth_block=False, panel="icgs"):
+                 reorth_block=False, panel="icgs", in_node=False):
         import torch
         self.torch = torch
         self.tdtype = torch.float64 if dtype in ("f64", "float64") else torch.float32
@@ -443,6 +450,7 @@ class CodedQR:
         cfg.nrhs_max = nrhs_max
         cfg.reorth_block = int(bool(reorth_block))
         cfg.panel = PANEL_NAMES[panel]
+        cfg.in_node = int(bool(in_node))
         cfg.seed = seed
         cfg.tau = tau
         if stream is None:
@@ -480,6 +488,9 @@ class CodedQR:
 
     def inject(self, tiles):
         check(coded_qr_inject_erasure(self.h, tiles), "coded_qr_inject_erasure")
+
+    def fail_nodes(self, nodes):
+        check(coded_qr_inject_node_failure(self.h, nodes), "coded_qr_inject_node_failure")
 
     def recover(self):
         st, n = coded_qr_recover(self.h)

@@ -50,14 +50,26 @@ struct Buffers {
   void* tc;
 };
 
+// Checksum blocks per code.  Out-of-node storage: f (one per tolerated failure, on f extra
+// nodes).  In-node storage (Section 5): K = f + f ceil(f / (P - f)) with P = p_r nodes per code
+// and L = P data blocks, the equality case of Theorem in_node_opt.
+int code_blocks(const cqr_config* c) {
+  if (!c->in_node || c->f == 0) return c->f;
+  return c->f + c->f * ((c->f + (c->p_r - c->f) - 1) / (c->p_r - c->f));
+}
+
 cqr_status validate(const cqr_config* c) {
   if (!c) return CQR_EINVAL;
   if (c->m < 1 || c->n < 1 || c->m < c->n) return CQR_EINVAL;
   if (c->p_r < 1 || c->p_c < 1 || c->b < 1 || c->f < 0) return CQR_EINVAL;
   if (c->n % c->p_c != 0) return CQR_EINVAL;
-  if (2 * c->f > c->p_r) return CQR_EINVAL;
-  if (c->protect_r && 2 * c->f > c->p_c) return CQR_EINVAL;
-  if (c->f > kMaxF || c->p_r + c->f > kMaxCode || c->p_c + c->f > kMaxCode) return CQR_ENOTSUP;
+  if (c->in_node != 0 && c->in_node != 1) return CQR_EINVAL;
+  if (c->in_node && c->f >= c->p_r) return CQR_EINVAL;
+  if (c->in_node && c->protect_r && c->p_c != c->p_r) return CQR_ENOTSUP;  // one K for both codes
+  const int K = code_blocks(c);
+  if (2 * K > c->p_r) return CQR_EINVAL;
+  if (c->protect_r && 2 * K > c->p_c) return CQR_EINVAL;
+  if (K > kMaxF || c->p_r + K > kMaxCode || c->p_c + K > kMaxCode) return CQR_ENOTSUP;
   if (c->p_r > (int64_t)c->m) return CQR_EINVAL;
   if (c->dtype != CQR_F64 && c->dtype != CQR_F32) return CQR_EINVAL;
   if (c->mma < CQR_MMA_SIMT || c->mma > CQR_MMA_BF16X3) return CQR_EINVAL;
@@ -75,19 +87,20 @@ Geo make_geo(const cqr_config* c) {
   g.n = c->n;
   g.p_r = c->p_r;
   g.p_c = c->p_c;
-  g.f = c->f;
-  g.protect_r = (c->protect_r && c->f > 0) ? 1 : 0;
+  const int K = code_blocks(c);
+  g.f = K;  // checksum blocks of each code (= f out of node)
+  g.protect_r = (c->protect_r && K > 0) ? 1 : 0;
   g.mb = (c->m + c->p_r - 1) / c->p_r;
   g.nb = c->n / c->p_c;
   g.m_pad = g.mb * c->p_r;
-  g.c = (int64_t)c->f * g.mb;
-  g.d = g.protect_r ? (int64_t)c->f * g.nb : 0;
+  g.c = (int64_t)K * g.mb;
+  g.d = g.protect_r ? (int64_t)K * g.nb : 0;
   g.M = g.m_pad + g.c;
   g.N = g.n + g.d;
   g.ldq = round_up(g.M, 32);
   g.ldr = round_up(g.N, 32);
-  g.grid_rows = c->p_r + c->f;
-  g.grid_cols = c->p_c + (g.protect_r ? c->f : 0);
+  g.grid_rows = c->p_r + K;
+  g.grid_cols = c->p_c + (g.protect_r ? K : 0);
   g.b = c->b;
   g.panels = (int)((c->n + c->b - 1) / c->b);
   return g;
@@ -102,10 +115,10 @@ Layout make_layout(const cqr_config* c, const Geo& g, int num_sms) {
   auto take = [&](size_t bytes) { size_t at = off; off += align256(bytes ? bytes : 1); return at; };
   L.Q = take((size_t)g.ldq * g.N * s);
   L.R = take((size_t)g.ldr * g.N * s);
-  L.Gt = take((size_t)(c->f * c->p_r + 1) * 8);
-  L.Gh = take((size_t)(c->f * c->p_c + 1) * 8);
-  L.Gt_t = take((size_t)(c->f * c->p_r + 1) * s);
-  L.Gh_t = take((size_t)(c->f * c->p_c + 1) * s);
+  L.Gt = take((size_t)(g.f * c->p_r + 1) * 8);
+  L.Gh = take((size_t)(g.f * c->p_c + 1) * 8);
+  L.Gt_t = take((size_t)(g.f * c->p_r + 1) * s);
+  L.Gh_t = take((size_t)(g.f * c->p_c + 1) * s);
   L.part = take(panel_partial_bytes(bmax, s, num_sms));
   L.bar = take(256);
   L.status = take(256);
@@ -114,7 +127,7 @@ Layout make_layout(const cqr_config* c, const Geo& g, int num_sms) {
   L.Pt = take(c->dtype == CQR_F32 && c->mma != CQR_MMA_SIMT ? tc_panel_bytes(g.M, bmax) : 0);
   L.yw = take((size_t)g.m_pad * nrhs * s);
   L.xw = take((size_t)(g.m + g.N) * nrhs * s);
-  L.plans = take(sizeof(DecodePlan) * (size_t)(g.grid_cols + g.p_c + c->f + 2));
+  L.plans = take(sizeof(DecodePlan) * (size_t)(g.grid_cols + g.p_c + g.f + 2));
   L.cg = take(sizeof(double) * (size_t)(7 * g.n + g.c + 2 * (num_sms + 1)));
   L.tc = take(c->dtype == CQR_F32 && c->mma != CQR_MMA_SIMT
                   ? tc_workspace_bytes(c->mma, g.M, g.N, g.n, bmax, c->reorth_block != 0)
@@ -658,6 +671,7 @@ cqr_status coded_qr_geometry(cqr_handle h, int64_t* d) {
   d[CQR_GEO_GRID_ROWS] = g.grid_rows;
   d[CQR_GEO_GRID_COLS] = g.grid_cols;
   d[CQR_GEO_PANELS] = g.panels;
+  d[CQR_GEO_CODE_BLOCKS] = g.f;
   return CQR_OK;
 }
 
@@ -716,6 +730,53 @@ cqr_status coded_qr_inject_erasure(cqr_handle h, const int32_t* tiles, int32_t c
   return CQR_OK;
 }
 
+namespace {
+
+// Checksum block k of a code of K blocks over P nodes goes to node (k P) / K when K <= P,
+// else to node k mod P: the load-balanced in-node distribution (Definition innode_distr).
+int in_node_host(int k, int K, int P) { return K <= P ? (int)((int64_t)k * P / K) : k % P; }
+
+// Tiles of the encoded grid lost when node (i, j) fails (as (row, col) pairs).  In-node:
+// the node's data tile and every checksum tile it hosts (vertical checksums of column j hosted
+// by row node i, horizontal checksums of row i hosted by column node j, and their corner
+// tiles).  Out of node: node (i, j) of the extended grid holds tile (i, j).
+void node_tiles(const cqr_handle h, int i, int j, std::vector<int32_t>* out) {
+  const Geo& g = h->g;
+  if (!h->cfg.in_node) {
+    out->push_back(i);
+    out->push_back(j);
+    return;
+  }
+  std::vector<int> rows{i}, cols{j};
+  for (int k = 0; k < g.f; ++k)
+    if (in_node_host(k, g.f, g.p_r) == i) rows.push_back(g.p_r + k);
+  if (g.protect_r)
+    for (int l = 0; l < g.f; ++l)
+      if (in_node_host(l, g.f, g.p_c) == j) cols.push_back(g.p_c + l);
+  for (int I : rows)
+    for (int J : cols) {
+      out->push_back(I);
+      out->push_back(J);
+    }
+}
+
+bool node_in_range(const cqr_handle h, int i, int j) {
+  const Geo& g = h->g;
+  if (h->cfg.in_node) return i >= 0 && i < g.p_r && j >= 0 && j < g.p_c;
+  return i >= 0 && i < g.grid_rows && j >= 0 && j < g.grid_cols;
+}
+
+}  // namespace
+
+cqr_status coded_qr_inject_node_failure(cqr_handle h, const int32_t* nodes, int32_t count) {
+  if (!h || count < 0 || (count > 0 && !nodes)) return CQR_EINVAL;
+  for (int e = 0; e < count; ++e)
+    if (!node_in_range(h, nodes[2 * e], nodes[2 * e + 1])) return CQR_EINVAL;
+  std::vector<int32_t> tiles;
+  for (int e = 0; e < count; ++e) node_tiles(h, nodes[2 * e], nodes[2 * e + 1], &tiles);
+  return coded_qr_inject_erasure(h, tiles.data(), (int32_t)(tiles.size() / 2));
+}
+
 cqr_status coded_qr_recover(cqr_handle h, int32_t* n_recovered) {
   if (!h) return CQR_EINVAL;
   if (h->state == ST_CREATED) return CQR_ESTATE;
@@ -765,8 +826,7 @@ cqr_status coded_qr_run(cqr_handle h, const void* A, int64_t lda, const void* y,
   if (y && (nrhs < 1 || nrhs > h->cfg.nrhs_max || ldy < h->g.m || ldx < h->g.n)) return CQR_EINVAL;
   for (int e = 0; e < plan_len; ++e) {
     const int t = plan[3 * e], i = plan[3 * e + 1], j = plan[3 * e + 2];
-    if (t < 0 || t >= h->g.panels || i < 0 || i >= h->g.grid_rows || j < 0 || j >= h->g.grid_cols)
-      return CQR_EINVAL;
+    if (t < 0 || t >= h->g.panels || !node_in_range(h, i, j)) return CQR_EINVAL;
   }
   const bool host = (flags & CQR_RUN_HOST_BUFFERS) != 0;
   const size_t es = h->esz;
@@ -798,10 +858,7 @@ cqr_status coded_qr_run(cqr_handle h, const void* A, int64_t lda, const void* y,
   while (t < g.panels) {
     tiles.clear();
     for (int e = 0; e < plan_len; ++e)
-      if (plan[3 * e] == t) {
-        tiles.push_back(plan[3 * e + 1]);
-        tiles.push_back(plan[3 * e + 2]);
-      }
+      if (plan[3 * e] == t) node_tiles(h, plan[3 * e + 1], plan[3 * e + 2], &tiles);
     if (!tiles.empty()) {
       s = coded_qr_inject_erasure(h, tiles.data(), (int32_t)(tiles.size() / 2));
       if (s == CQR_OK) s = coded_qr_recover(h, nullptr);

@@ -245,7 +245,7 @@ cqr_status coded_qr_batched_create(const cqr_config* cfg, const int64_t* m, cons
   if (cfg->dtype != CQR_F32) return CQR_ENOTSUP;
   if (cfg->mma != CQR_MMA_SIMT) return CQR_ENOTSUP;
   if (cfg->b < 0 || cfg->b > kBMax) return cfg->b < 0 ? CQR_EINVAL : CQR_ENOTSUP;
-  if (cfg->reorth_block) return CQR_ENOTSUP;
+  if (cfg->reorth_block || cfg->in_node || cfg->panel != CQR_PANEL_ICGS) return CQR_ENOTSUP;
   std::vector<Geo> geo(count);
   for (int i = 0; i < count; ++i) {
     cqr_config c = *cfg;
@@ -432,6 +432,7 @@ cqr_status coded_qr_batched_geometry(cqr_batched bh, int32_t i, int64_t* d) {
   d[CQR_GEO_GRID_ROWS] = g.grid_rows;
   d[CQR_GEO_GRID_COLS] = g.grid_cols;
   d[CQR_GEO_PANELS] = g.panels;
+  d[CQR_GEO_CODE_BLOCKS] = g.f;
   return CQR_OK;
 }
 

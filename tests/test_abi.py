@@ -44,7 +44,7 @@ def test_binding_names_match_header(libpath):
 def test_config_struct_layout(libpath):
     from paper_2311_11943_gb300 import binding
     assert C.sizeof(binding.Config) == 88
-    assert binding.Config.panel.offset == 56
+    assert binding.Config.panel.offset == 56 and binding.Config.in_node.offset == 60
     assert binding.Config.seed.offset == 64 and binding.Config.stream.offset == 80
 
 

@@ -516,3 +516,51 @@ def test_panel_variants_agree_with_householder_r():
         R = np.zeros((n, n), order="F")
         O.factor(Q, R, n, 16, panel=panel)
         assert np.abs(R - Rh).max() / np.abs(Rh).max() < 1e-12, panel
+
+
+# ----------------------------------------------------------------- in-node storage (NEXT f2)
+def _min_k_brute(P, f):
+    """Smallest K for which the load-balanced distribution leaves at least f surviving checksum
+    blocks (the f lost data blocks, L = P) for every set of f failed nodes."""
+    for K in range(1, 4 * P):
+        hosts = O.in_node_hosts(K, P)
+        load = [hosts.count(q) for q in range(P)]
+        worst = max(sum(load[q] for q in S) for S in itertools.combinations(range(P), f))
+        if K - worst >= f:
+            return K
+    return None
+
+
+def test_in_node_k_bound_is_tight_by_brute_force():
+    for P in range(3, 11):
+        for f in range(1, P // 2 + 1):
+            assert _min_k_brute(P, f) == O.in_node_checks(P, P, f), (P, f)
+
+
+def test_in_node_distribution_is_load_balanced():
+    for (K, P) in [(4, 8), (3, 8), (8, 16), (10, 4), (7, 3)]:
+        hosts = O.in_node_hosts(K, P)
+        load = sorted(hosts.count(q) for q in range(P))
+        a_bar = K - P * (K // P)
+        assert load == [K // P] * (P - a_bar) + [-(-K // P)] * a_bar
+
+
+@pytest.mark.parametrize("p,f", [(4, 1), (8, 2)])
+def test_in_node_every_node_failure_pattern_recovers(p, f):
+    # every set of at most f failed nodes with at most f per node row and column, at the
+    # start of a middle panel, recovers the fault-free factorisation
+    m = n = 8 * p
+    A = synth.gaussian(m, n, 31)
+    clean = O.run_in_node(A, p, f, b=8, seed=5)
+    K = clean["K"]
+    assert 2 * K <= p
+    nodes = [(i, j) for i in range(p) for j in range(p)]
+    pats = [c for r in range(1, f + 1) for c in itertools.combinations(nodes, r)
+            if max(sum(1 for (i, _) in c if i == q) for q in range(p)) <= f
+            and max(sum(1 for (_, j) in c if j == q) for q in range(p)) <= f]
+    if len(pats) > 400:
+        pats = [pats[k] for k in np.random.default_rng(3).choice(len(pats), 400, replace=False)]
+    for pat in pats:
+        hit = O.run_in_node(A, p, f, b=8, seed=5, node_failures={3: list(pat)})
+        assert np.abs(hit["Q"] - clean["Q"]).max() < 1e-9, pat
+        assert np.abs(hit["R"] - clean["R"]).max() < 1e-9, pat
