@@ -569,91 +569,301 @@ cudaError_t launch_gemv_t(const T* Qo, int64_t ldq, int64_t rows, int64_t n, con
   return cudaGetLastError();
 }
 
-// Blocked back substitution (Golub & Van Loan, Alg. 3.1.4, column version), cooperative grid,
-// one grid barrier per 64-row block: in phase k, CTA 0 first applies the just-solved block
-// k+1 to the rows of block k and solves block k in shared memory, while the other CTAs apply
-// block k+1 to the rows above block k.
+// Blocked back substitution (Golub & Van Loan, Alg. 3.1.4, column version) on one thread-block
+// cluster of C CTAs.  The 64-row blocks of x are owned cyclically (block p by CTA p % C) and
+// live in the owner's shared memory from start to end.  Phase p (p = nblk-1 .. 0):
+//   * the owner of block p applies the just-solved x_{p+1} to it (the R[p, p+1] tile is
+//     already in shared memory), solves the 64 x 64 diagonal system in one warp and stores
+//     x_p into every CTA's shared memory (distributed shared memory, buffer p mod 3);
+//   * every CTA arrives at the cluster barrier (release), then, off the critical path, applies
+//     x_{p+1} to its other blocks below p from tiles R[i, p+1] that cp.async brought into
+//     shared memory during the previous phase, starts the copies of the tiles R[i, p] that
+//     the next phase needs (and of its next diagonal block), then waits (acquire).
+// The diagonal solve goes by 8-row sub-blocks: the warp gathers the sub-block's 8 right-hand
+// sides by shuffle, every lane solves the 8 x 8 triangle (reciprocals of the diagonal
+// precomputed), and the lanes owning rows above the sub-block apply it.  Every update of b_i
+// by x_j (i < j) happens once: by i's owner, in phase j-1.  Three x buffers suffice: when
+// the owner of p writes buffer p mod 3, every CTA has arrived at phase p+1's barrier, so none
+// still reads x_{p+3}.  Tiles are column-major with a padded column stride (16-byte aligned).
 template <typename T>
-__global__ void __launch_bounds__(256) k_trsv_upper(const T* __restrict__ R, int64_t ldr, int64_t n,
-                                                     T* x, int64_t ldx, int64_t k, unsigned* bar,
-                                                     int* status) {
-  constexpr int BS = 64;
-  __shared__ T Rd[BS][BS + 1];
-  __shared__ T xs[2 * BS];
-  const int G = gridDim.x, tid = threadIdx.x;
-  unsigned target = 0;
+__device__ __forceinline__ void st_dsmem(T* local, uint32_t rank, T v);
+template <>
+__device__ __forceinline__ void st_dsmem<float>(float* local, uint32_t rank, float v) {
+  uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(local)), r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(r), "f"(v) : "memory");
+}
+template <>
+__device__ __forceinline__ void st_dsmem<double>(double* local, uint32_t rank, double v) {
+  uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(local)), r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(r), "d"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// asynchronous global -> shared copy of `bytes` (16, 8 or 4) with the tail past `valid` zeroed
+__device__ __forceinline__ void cp_async_n(void* dst, const void* src, int bytes, int valid) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid) : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+constexpr int kTrsvBS = 64;
+template <typename T>
+constexpr int trsv_ldc() { return sizeof(T) == 4 ? 68 : 66; }  // 16-byte aligned columns
+
+template <typename T>
+size_t trsv_smem_bytes(int64_t n, int C, int npf) {
+  const int64_t nblk = (n + kTrsvBS - 1) / kTrsvBS;
+  const int64_t nloc = (nblk + C - 1) / C;
+  return sizeof(T) * (size_t)((2 + npf) * kTrsvBS * trsv_ldc<T>() + 8 * kTrsvBS + nloc * kTrsvBS);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 1) k_trsv_upper(const T* __restrict__ R, int64_t ldr,
+                                                        int64_t n, T* x, int64_t ldx, int64_t k,
+                                                        int npf, int vec) {
+  constexpr int BS = kTrsvBS, LDC = trsv_ldc<T>();
+  constexpr int VE = 16 / (int)sizeof(T);  // elements per 16-byte copy
+  extern __shared__ __align__(16) unsigned char trsv_raw[];
+  T* Rd = reinterpret_cast<T*>(trsv_raw);  // [BS columns][LDC] diagonal tile of the next own block
+  T* Ro = Rd + BS * LDC;                    // its tile right of the diagonal
+  T* tiles = Ro + BS * LDC;                 // [npf][BS][LDC] tiles of the bulk updates
+  T* rinv = tiles + (size_t)npf * BS * LDC; // [BS]
+  T* xs = rinv + BS;                        // [3][BS] x_p in buffer p mod 3
+  T* red = xs + 3 * BS;                     // [4][BS]
+  T* xb = red + 4 * BS;                     // [nloc][BS] own blocks: b, then x
+  const int C = gridDim.x, c = blockIdx.x, tid = threadIdx.x;
   const int64_t nblk = (n + BS - 1) / BS;
+  const int r64 = tid & (BS - 1), q4 = tid >> 6;  // row of a tile, quarter of its columns
+
+  // column-major tile of R at (i0, k0) into t; zero outside R
+  auto tile_async = [&](T* t, int64_t i0, int64_t k0) {
+    if (vec) {
+      for (int e = tid; e < BS * BS / VE; e += blockDim.x) {
+        const int rv = (e % (BS / VE)) * VE, cc = e / (BS / VE);
+        const int64_t gi = i0 + rv, gc = k0 + cc, rows = n - gi;
+        const int valid = (gc < n && rows > 0) ? (int)(sizeof(T) * (rows < VE ? rows : VE)) : 0;
+        cp_async_n(t + cc * LDC + rv, valid ? (const void*)(R + gi + gc * ldr) : (const void*)R, 16, valid);
+      }
+    } else {
+      for (int e = tid; e < BS * BS; e += blockDim.x) {
+        const int r = e & (BS - 1), cc = e >> 6;
+        const int64_t gi = i0 + r, gc = k0 + cc;
+        const int valid = (gc < n && gi < n) ? (int)sizeof(T) : 0;
+        cp_async_n(t + cc * LDC + r, valid ? (const void*)(R + gi + gc * ldr) : (const void*)R,
+                   (int)sizeof(T), valid);
+      }
+    }
+  };
+  auto issue_diag = [&](int64_t p) {
+    tile_async(Rd, p * BS, p * BS);
+    tile_async(Ro, p * BS, p * BS + BS);
+  };
+  auto fix_diag = [&](int64_t p) {  // identity on the padded diagonal, reciprocals
+    if (tid < BS) {
+      if (p * BS + tid >= n) Rd[tid * LDC + tid] = T(1);
+      rinv[tid] = T(1) / Rd[tid * LDC + tid];
+    }
+  };
+  auto issue_bulk = [&](int64_t q) {  // R[i, q] for the first npf own blocks i < q - 1
+    int u = 0;
+    for (int64_t i = c; i < q - 1 && u < npf; i += C, ++u) tile_async(tiles + (size_t)u * BS * LDC, i * BS, q * BS);
+  };
+
   for (int64_t col = 0; col < k; ++col) {
     T* xc = x + col * ldx;
-    target = 0;
-    for (int64_t blk = nblk - 1; blk >= 0; --blk) {
-      const int64_t i0 = blk * BS;
-      const int64_t i1 = (i0 + BS < n) ? i0 + BS : n;
-      const int nbk = (int)(i1 - i0);
-      const int64_t p0 = i1, p1 = (i1 + BS < n) ? i1 + BS : n;  // previously solved block
-      if (blockIdx.x == 0) {
-        // rows of this block: subtract the previous block's contribution, load into smem
-        for (int e = tid; e < (int)(p1 - p0); e += blockDim.x) xs[BS + e] = __ldcg(xc + p0 + e);
-        __syncthreads();
-        for (int r = tid; r < nbk; r += blockDim.x) {
-          T acc = __ldcg(xc + i0 + r);
-#pragma unroll 16
-          for (int jj = 0; jj < (int)(p1 - p0); ++jj) acc -= R[(i0 + r) + (p0 + jj) * ldr] * xs[BS + jj];
-          xs[r] = acc;
+    for (int64_t l = 0, p = c; p < nblk; ++l, p += C)
+      if (tid < BS) xb[l * BS + tid] = (p * BS + tid < n) ? xc[p * BS + tid] : T(0);
+    int64_t mine = -1;  // highest own block
+    for (int64_t p = c; p < nblk; p += C) mine = p;
+    if (mine >= 0) issue_diag(mine);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    if (mine >= 0) fix_diag(mine);
+    int64_t pend = -1;  // own diagonal block whose tiles are in flight
+    __syncthreads();
+
+    for (int64_t p = nblk - 1; p >= 0; --p) {
+      const bool own = (p % C) == c;
+      const T* xnext = xs + ((p + 1) % 3) * BS;  // x_{p+1}
+      if (own) {
+        T* bp = xb + (p / C) * BS;
+        if (p + 1 < nblk) {
+          T s = T(0);
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) s += Ro[(q4 * 16 + cc) * LDC + r64] * xnext[q4 * 16 + cc];
+          red[q4 * BS + r64] = s;
+          __syncthreads();
+          if (tid < BS) bp[tid] -= ((red[tid] + red[BS + tid]) + (red[2 * BS + tid] + red[3 * BS + tid]));
+          __syncthreads();
         }
-        for (int e = tid; e < nbk * nbk; e += blockDim.x) {
-          const int r = e % nbk, cidx = e / nbk;
-          Rd[r][cidx] = R[(i0 + r) + (i0 + cidx) * ldr];
-        }
-        __syncthreads();
         if (tid < 32) {
-          for (int i = nbk - 1; i >= 0; --i) {
-            T xi = T(0);
-            if (tid == 0) {
-              xi = xs[i] / Rd[i][i];
-              xs[i] = xi;
+          const int lane = tid;
+          T b0 = bp[lane], b1 = bp[lane + 32];  // rows lane and lane + 32
+#pragma unroll
+          for (int sb = 7; sb >= 0; --sb) {
+            const int base = sb * 8;
+            T v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = __shfl_sync(0xffffffffu, sb >= 4 ? b1 : b0, (base + q) & 31);
+#pragma unroll
+            for (int q = 7; q >= 0; --q) {
+              v[q] *= rinv[base + q];
+#pragma unroll
+              for (int qq = 0; qq < q; ++qq) v[qq] -= Rd[(base + q) * LDC + base + qq] * v[q];
             }
-            xi = __shfl_sync(0xffffffffu, xi, 0);
-            for (int r = tid; r < i; r += 32) xs[r] -= Rd[r][i] * xi;
-            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              if (sb >= 4) {
+                if (lane == ((base + q) & 31)) b1 = v[q];
+              } else if (lane == base + q) {
+                b0 = v[q];
+              }
+            }
+            T a0 = T(0), a1 = T(0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              a0 += Rd[(base + q) * LDC + lane] * v[q];
+              a1 += Rd[(base + q) * LDC + lane + 32] * v[q];
+            }
+            if (lane < base) b0 -= a0;
+            if (lane + 32 < base) b1 -= a1;
           }
+          bp[lane] = b0;
+          bp[lane + 32] = b1;
         }
         __syncthreads();
-        for (int r = tid; r < nbk; r += blockDim.x) xc[i0 + r] = xs[r];
-      } else if (p0 < p1 && (int64_t)(blockIdx.x - 1) * blockDim.x < i0) {
-        // rows above this block: subtract the previous block's contribution
-        for (int e = tid; e < (int)(p1 - p0); e += blockDim.x) xs[e] = __ldcg(xc + p0 + e);
-        __syncthreads();
-        for (int64_t r = (int64_t)(blockIdx.x - 1) * blockDim.x + tid; r < i0;
-             r += (int64_t)(G - 1) * blockDim.x) {
-          T acc = __ldcg(xc + r);
+        // x_p into buffer p mod 3 of every CTA of the cluster (this one included)
+        T* dst = xs + (p % 3) * BS;
+        for (int e = tid; e < BS * C; e += blockDim.x)
+          st_dsmem<T>(dst + (e & (BS - 1)), (uint32_t)(e >> 6), bp[e & (BS - 1)]);
+      }
+      cluster_arrive_release();
+      // this phase's bulk tiles (started one phase ago) and any diagonal prefetch have landed
+      cp_async_wait_all();
+      __syncthreads();
+      if (pend >= 0) {
+        fix_diag(pend);
+        pend = -1;
+      }
+      if (p + 1 < nblk) {
+        const int64_t k0 = (p + 1) * BS;
+        int u = 0;
+        for (int64_t l = 0, i = c; i < p; ++l, i += C, ++u) {
+          T s = T(0);
+          if (u < npf) {
+            const T* t = tiles + (size_t)u * BS * LDC;
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc) s += t[(q4 * 16 + cc) * LDC + r64] * xnext[q4 * 16 + cc];
+          } else {
 #pragma unroll 16
-          for (int jj = 0; jj < (int)(p1 - p0); ++jj) acc -= R[r + (p0 + jj) * ldr] * xs[jj];
-          xc[r] = acc;
+            for (int cc = 0; cc < 16; ++cc) {
+              const int64_t gc = k0 + q4 * 16 + cc;
+              if (gc < n) s += R[i * BS + r64 + gc * ldr] * xnext[q4 * 16 + cc];
+            }
+          }
+          red[q4 * BS + r64] = s;
+          __syncthreads();
+          if (tid < BS) xb[l * BS + tid] -= ((red[tid] + red[BS + tid]) + (red[2 * BS + tid] + red[3 * BS + tid]));
+          __syncthreads();
         }
       }
-      if (!grid_sync(bar, G, target, status, 10)) return;
+      // refill: the next phase's bulk tiles, the next own diagonal block
+      if (p >= 1) issue_bulk(p);
+      if (own && p - C >= 0) {
+        issue_diag(p - C);
+        pend = p - C;
+      }
+      cp_async_commit();
+      cluster_wait_acquire();
     }
-    if (!grid_sync(bar, G, target, status, 11)) return;
+    cp_async_wait_all();
+    for (int64_t l = 0, p = c; p < nblk; ++l, p += C)
+      if (tid < BS && p * BS + tid < n) xc[p * BS + tid] = xb[l * BS + tid];
+    // no CTA may overwrite its blocks or buffers for the next column while a peer could
+    // still write into them or read them
+    cluster_arrive_release();
+    cluster_wait_acquire();
   }
 }
 
 template <typename T>
-cudaError_t launch_trsv_upper(const T* R, int64_t ldr, int64_t n, T* x, int64_t ldx, int64_t k,
-                              unsigned* bar, int* status, int num_sms, cudaStream_t st) {
-  int G = (int)((n + 255) / 256) + 1;
-  if (G > num_sms) G = num_sms;
-  if (G < 2) G = 2;
-  for (int64_t col = 0; col < k; ++col) {
-    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
-    if (e != cudaSuccess) return e;
-    T* xc = x + col * ldx;
-    int64_t one = 1;
-    void* args[] = {(void*)&R, &ldr, &n, &xc, &ldx, &one, &bar, &status};
-    e = cudaLaunchCooperativeKernel((const void*)k_trsv_upper<T>, dim3(G), dim3(256), args, 0, st);
-    if (e != cudaSuccess) return e;
+bool trsv_cluster_fits(int C, size_t smem) {
+  const void* fn = (const void*)k_trsv_upper<T>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      (C > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+    cudaGetLastError();
+    return false;
   }
-  return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return nc >= 1;
+}
+
+template <typename T>
+cudaError_t launch_trsv_upper(const T* R, int64_t ldr, int64_t n, T* x, int64_t ldx, int64_t k,
+                              unsigned* /*bar*/, int* /*status*/, int /*num_sms*/, cudaStream_t st) {
+  if (n <= 0 || k <= 0) return cudaSuccess;
+  constexpr size_t kSmemMax = 227 * 1024;
+  const int64_t nblk = (n + kTrsvBS - 1) / kTrsvBS;
+  const size_t tile = sizeof(T) * kTrsvBS * trsv_ldc<T>();
+  int C = 0, npf = 0;
+  size_t smem = 0;
+  for (int Ct : {16, 8}) {
+    const int Cc = (int)std::min<int64_t>(Ct, nblk);
+    const size_t base = trsv_smem_bytes<T>(n, Cc, 0);
+    if (base > kSmemMax) continue;
+    const int64_t below = (nblk + Cc - 1) / Cc;  // own blocks of a CTA, the upper bound of a phase's bulk
+    const int np = (int)std::min<int64_t>(std::min<int64_t>(8, below), (int64_t)((kSmemMax - base) / tile));
+    const size_t sm = trsv_smem_bytes<T>(n, Cc, np);
+    if (trsv_cluster_fits<T>(Cc, sm)) {
+      C = Cc;
+      npf = np;
+      smem = sm;
+      break;
+    }
+  }
+  if (C == 0) return cudaErrorInvalidValue;
+  const int vec = ((reinterpret_cast<uintptr_t>(R) & 15) == 0 && (ldr * (int64_t)sizeof(T)) % 16 == 0) ? 1 : 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_trsv_upper<T>, R, ldr, n, x, ldx, k, npf, vec);
 }
 
 // Least squares for tall A (reading: A = Q_1 R, so R x = (Q_1^T Q_1)^{-1} Q_1^T y with

@@ -482,29 +482,50 @@ __device__ __forceinline__ void hilo(float x, int, __nv_bfloat16& h, __nv_bfloat
   l = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
+// One 32-row x 32-column tile per CTA: Q is read and Ak written along the rows (coalesced);
+// the row-major planes (At, Qr) are written from a shared-memory transpose of the tile, so
+// that consecutive threads write consecutive columns of a row.
 template <typename P>
-__global__ void k_split_panel(const float* __restrict__ Q, int64_t ldq, int64_t M, int bk, int bkp,
-                              int ak_cols, int nplanes, P* __restrict__ Ak_hi,
-                              P* __restrict__ Ak_lo, int64_t ldk, P* __restrict__ At_hi,
-                              P* __restrict__ At_lo, P* __restrict__ Qr_hi,
-                              P* __restrict__ Qr_lo, int64_t ldrow, int64_t kb) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int k = blockIdx.y;
-  if (r >= M) return;
-  const float x = (k < bk) ? Q[r + (int64_t)k * ldq] : 0.f;
-  P h, l;
-  hilo(x, nplanes, h, l);
-  if (k < ak_cols) {
-    if (Ak_hi) Ak_hi[r + (int64_t)k * ldk] = h;
-    if (Ak_lo && nplanes == 2) Ak_lo[r + (int64_t)k * ldk] = l;
+__global__ void __launch_bounds__(256) k_split_panel(const float* __restrict__ Q, int64_t ldq,
+                                                     int64_t M, int bk, int bkp, int ak_cols,
+                                                     int nplanes, P* __restrict__ Ak_hi,
+                                                     P* __restrict__ Ak_lo, int64_t ldk,
+                                                     P* __restrict__ At_hi, P* __restrict__ At_lo,
+                                                     P* __restrict__ Qr_hi, P* __restrict__ Qr_lo,
+                                                     int64_t ldrow, int64_t kb) {
+  __shared__ P sh[32][33], sl[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int k0 = blockIdx.y * 32;
+  const int64_t r = r0 + tx;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int k = k0 + ty + 8 * i;
+    const float x = (r < M && k < bk) ? Q[r + (int64_t)k * ldq] : 0.f;
+    P h, l;
+    hilo(x, nplanes, h, l);
+    if (r < M && k < ak_cols) {
+      if (Ak_hi) Ak_hi[r + (int64_t)k * ldk] = h;
+      if (Ak_lo && nplanes == 2) Ak_lo[r + (int64_t)k * ldk] = l;
+    }
+    sh[ty + 8 * i][tx] = h;
+    sl[ty + 8 * i][tx] = l;
   }
-  if (k < bkp) {
-    At_hi[r * bkp + k] = h;
-    if (nplanes == 2) At_lo[r * bkp + k] = l;
-  }
-  if (Qr_hi && k < bk) {
-    Qr_hi[r * ldrow + kb + k] = h;
-    if (nplanes == 2) Qr_lo[r * ldrow + kb + k] = l;
+  __syncthreads();
+  const int k = k0 + tx;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t rr = r0 + ty + 8 * i;
+    if (rr >= M) continue;
+    const P h = sh[tx][ty + 8 * i], l = sl[tx][ty + 8 * i];
+    if (k < bkp) {
+      At_hi[rr * bkp + k] = h;
+      if (nplanes == 2) At_lo[rr * bkp + k] = l;
+    }
+    if (Qr_hi && k < bk) {
+      Qr_hi[rr * ldrow + kb + k] = h;
+      if (nplanes == 2) Qr_lo[rr * ldrow + kb + k] = l;
+    }
   }
 }
 
@@ -788,7 +809,7 @@ int tc_splits(const TcGemm* t, int m1, int n1, int64_t* kchunk) {
 cudaError_t tc_split_panel(TcGemm* t, int64_t kb, int bk, bool finished, cudaStream_t st) {
   const int bkp = (int)round_to(bk, t->KE);
   const int m1 = (bk + BM - 1) / BM;
-  dim3 grd((unsigned)((t->M + 255) / 256), (unsigned)std::max(bkp, m1 * BM));
+  dim3 grd((unsigned)((t->M + 31) / 32), (unsigned)((std::max(bkp, m1 * BM) + 31) / 32));
   void* qh = finished ? t->Qr_hi : nullptr;
   if (t->bf) {
     using B16 = __nv_bfloat16;

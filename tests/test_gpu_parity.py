@@ -445,6 +445,26 @@ def test_block_reorth_parity_and_orthogonality(dtype, mma, kappa):
         assert back < 1e-12 and orth < max(1e-12, 10 * orth_ref), (orth, orth_ref, back)
 
 
+# ----------------------------------------------------------------- square solve (a9)
+@pytest.mark.parametrize("dtype,mma", [("f64", "simt"), ("f32", "3xtf32")])
+def test_square_solve_ragged_block_count(dtype, mma):
+    # n = 1096: 18 row blocks of the back substitution (the last one 8 rows), more than the
+    # 16 CTAs of its cluster, so some CTAs own two blocks; three right-hand sides
+    n = 1096
+    A = synth.kappa_matrix(n, n, 1e2, seed=23)
+    y = synth.rhs(n, 3, 23)
+    er = {2: [(5, 3)]}
+    ref = O.run(A, 8, 8, 1, 64, seed=4, erasures=er, y=y)
+    got = gpu_run(A, 8, 8, 1, 64, seed=4, erasures=er, y=y, dtype=dtype, mma=mma)
+    assert got["status"] == 0
+    u = U64 if dtype == "f64" else U3X
+    tol = n * u * 1e2 * 10
+    assert rel(got["x"], ref["x"]) < tol * max(1.0, np.abs(ref["x"]).max())
+    # the residual of the computed x against A itself
+    res = np.linalg.norm(A @ got["x"] - y) / (np.linalg.norm(A) * np.linalg.norm(got["x"]))
+    assert res < 10 * n * u
+
+
 # ----------------------------------------------------------------- tall least squares (a9)
 @pytest.mark.parametrize("dtype,mma,shape", [("f64", "simt", (1024, 256, 8, 4, 2, 64)),
                                              ("f64", "simt", (1003, 192, 8, 4, 1, 48)),
