@@ -190,6 +190,10 @@ struct cqr_handle_s {
   // adjoint scratch (allocated by the first adjoint call)
   void* adj = nullptr;
   size_t adj_bytes = 0;
+  // look-ahead of the tensor-core path: the critical stream (highest priority) and the stream
+  // of the wide trailing updates (lowest priority), created on first use; events fork, a, w
+  cudaStream_t la_st[2] = {nullptr, nullptr};
+  cudaEvent_t la_ev[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -205,22 +209,24 @@ cudaEvent_t prof_event(cqr_handle h) {
   return e;
 }
 
-// Brackets the launches of one kernel class at one call site.
+// Brackets the launches of one kernel class at one call site, on the stream they go to.
 struct ProfScope {
   cqr_handle h;
   int cls;
+  cudaStream_t st;
   cudaEvent_t a = nullptr;
-  ProfScope(cqr_handle h_, int cls_, int nlaunch) : h(h_), cls(cls_) {
+  ProfScope(cqr_handle h_, int cls_, int nlaunch, cudaStream_t s = nullptr)
+      : h(h_), cls(cls_), st(s ? s : h_->st) {
     h->prof_launches[cls] += nlaunch;
     if (h->prof_on) {
       a = prof_event(h);
-      cudaEventRecord(a, h->st);
+      cudaEventRecord(a, st);
     }
   }
   ~ProfScope() {
     if (a) {
       cudaEvent_t b = prof_event(h);
-      cudaEventRecord(b, h->st);
+      cudaEventRecord(b, st);
       h->prof_recs.push_back(ProfRec{cls, a, b});
     }
   }
@@ -352,78 +358,111 @@ int choose_splits(int bk, int64_t w, int64_t K, int num_sms) {
 }
 
 template <typename T>
+void ensure_panel_plan(cqr_handle h, int bk) {
+  if (bk == h->plan_bk) return;
+  const Geo& g = h->g;
+  h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, true);
+  if (h->plan.cluster && !panel_cluster_fits<T>(h->plan))
+    h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, false);
+  h->reg_ok = false;
+  const char* env = getenv("CQR_PANEL_REG");
+  const bool left_looking = h->cfg.panel == CQR_PANEL_CGS1 || h->cfg.panel == CQR_PANEL_CGS2;
+  if (sizeof(T) == 4 && !(env && env[0] == '0') && !left_looking &&
+      plan_panel_reg(g.M, bk, &h->reg_rpl, &h->reg_cpw, &h->reg_G))
+    h->reg_ok = panel_reg_cluster_fits(h->reg_rpl, h->reg_cpw, h->reg_G);
+  h->plan_bk = bk;
+}
+
+// Block reorthogonalisation of panel columns kb .. kb+bk-1 against columns 0 .. kb-1:
+// S = Q[:, :kb]^T Qbar, Qbar -= Q[:, :kb] S, R[:kb, panel] += S.
+template <typename T>
+cqr_status reorth_block_step(cqr_handle h, int64_t kb, int bk, int buf, cudaStream_t st) {
+  if (!h->cfg.reorth_block || kb <= 0) return CQR_OK;
+  const Geo& g = h->g;
+  T* Q = ptr<T>(h->B.Q);
+  T* R = ptr<T>(h->B.R);
+  if (h->tc) {
+    ProfScope ps(h, K_BLOCK_REORTH, 0, st);
+    int nl = 0;
+    const cudaError_t e = tc_block_reorth(h->tc, kb, bk, ptr<float>(h->B.R), g.ldr, buf, st, &nl);
+    h->prof_launches[K_BLOCK_REORTH] += nl;
+    CK(e);
+    return CQR_OK;
+  }
+  ProfScope ps(h, K_BLOCK_REORTH, 3, st);
+  const int sp = choose_splits((int)kb, bk, g.M, h->num_sms);
+  CK(launch_gemm_tn_splitk<T>(Q, g.ldq, Q + kb * g.ldq, g.ldq, g.M, (int)kb, bk, sp,
+                              ptr<T>(h->B.P), st));
+  CK(launch_splitk_reduce<T>(ptr<T>(h->B.P), sp, (int)kb, bk, R + kb * g.ldr, g.ldr,
+                             ptr<T>(h->B.Rb), st, 1));
+  CK(launch_gemm_nn_sub<T>(Q, g.ldq, ptr<T>(h->B.Rb), kb, Q + kb * g.ldq, g.ldq, g.M, (int)kb,
+                           bk, st));
+  return CQR_OK;
+}
+
+// The panel factorisation (ICGS, or the chosen variant) of columns kb .. kb+bk-1.
+template <typename T>
+cqr_status panel_kernel_step(cqr_handle h, int64_t kb, int bk, cudaStream_t st) {
+  const Geo& g = h->g;
+  T* Q = ptr<T>(h->B.Q);
+  T* R = ptr<T>(h->B.R);
+  ensure_panel_plan<T>(h, bk);
+  ProfScope ps(h, K_PANEL, 1, st);
+  if (sizeof(T) == 4 && h->reg_ok) {
+    CK(launch_panel_reg(h->reg_rpl, h->reg_cpw, h->reg_G, reinterpret_cast<float*>(Q + kb * g.ldq),
+                        g.ldq, reinterpret_cast<float*>(R + kb + kb * g.ldr), g.ldr, g.M, bk, h->tau,
+                        h->B.status, (int)kb, st));
+  } else {
+    const int variant = h->cfg.panel == CQR_PANEL_CGS1 ? 1 : (h->cfg.panel == CQR_PANEL_CGS2 ? 2 : 0);
+    CK(launch_panel<T>(h->plan, Q + kb * g.ldq, g.ldq, R + kb + kb * g.ldr, g.ldr, g.M, bk, h->tau,
+                       ptr<T>(h->B.part), h->B.bar, h->B.status, (int)kb, st, variant));
+  }
+  return CQR_OK;
+}
+
+// Tensor-core trailing update of columns j0 .. j0+w-1 by the panel kb .. kb+bk-1 (its operand
+// planes in buffer buf), partials and Rbar planes of context ctx, at most max_ctas CTAs.
+cqr_status tc_update_cols(cqr_handle h, int64_t kb, int bk, int64_t j0, int64_t w, int buf, int ctx,
+                          int max_ctas, cudaStream_t st) {
+  if (w <= 0) return CQR_OK;
+  {
+    ProfScope ps(h, K_TC_RBAR, 1, st);
+    CK(tc_gemm_rbar(h->tc, bk, j0, w, buf, ctx, max_ctas, st));
+  }
+  {
+    ProfScope ps(h, K_SPLITK_REDUCE, 1, st);
+    CK(tc_reduce(h->tc, kb, bk, j0, w, ptr<float>(h->B.R), h->g.ldr, ctx, max_ctas, st));
+  }
+  {
+    ProfScope ps(h, K_TC_UPDATE, 1, st);
+    CK(tc_gemm_update(h->tc, bk, j0, w, buf, ctx, max_ctas, st));
+  }
+  return CQR_OK;
+}
+
+// One panel in stream order: block reorthogonalisation, panel, trailing update of every
+// column to the right.
+template <typename T>
 cqr_status panel_step(cqr_handle h, int t) {
   const Geo& g = h->g;
   const int64_t kb = (int64_t)t * g.b;
   const int bk = (int)std::min<int64_t>(g.b, g.n - kb);
   T* Q = ptr<T>(h->B.Q);
   T* R = ptr<T>(h->B.R);
-  const bool tc = h->tc != nullptr;
-  if (h->cfg.reorth_block && kb > 0) {
-    // block reorthogonalisation: S = Q[:, :kb]^T Qbar, Qbar -= Q[:, :kb] S, R[:kb, panel] += S
-    if (tc) {
-      ProfScope ps(h, K_BLOCK_REORTH, 0);
-      int nl = 0;
-      const cudaError_t e = tc_block_reorth(h->tc, kb, bk, ptr<float>(h->B.R), g.ldr, h->st, &nl);
-      h->prof_launches[K_BLOCK_REORTH] += nl;
-      CK(e);
-    } else {
-      ProfScope ps(h, K_BLOCK_REORTH, 3);
-      const int sp = choose_splits((int)kb, bk, g.M, h->num_sms);
-      CK(launch_gemm_tn_splitk<T>(Q, g.ldq, Q + kb * g.ldq, g.ldq, g.M, (int)kb, bk, sp,
-                                  ptr<T>(h->B.P), h->st));
-      CK(launch_splitk_reduce<T>(ptr<T>(h->B.P), sp, (int)kb, bk, R + kb * g.ldr, g.ldr,
-                                 ptr<T>(h->B.Rb), h->st, 1));
-      CK(launch_gemm_nn_sub<T>(Q, g.ldq, ptr<T>(h->B.Rb), kb, Q + kb * g.ldq, g.ldq, g.M, (int)kb,
-                               bk, h->st));
-    }
-  }
-  if (bk != h->plan_bk) {
-    h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, true);
-    if (h->plan.cluster && !panel_cluster_fits<T>(h->plan))
-      h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, false);
-    h->reg_ok = false;
-    const char* env = getenv("CQR_PANEL_REG");
-    const bool left_looking = h->cfg.panel == CQR_PANEL_CGS1 || h->cfg.panel == CQR_PANEL_CGS2;
-    if (sizeof(T) == 4 && !(env && env[0] == '0') && !left_looking &&
-        plan_panel_reg(g.M, bk, &h->reg_rpl, &h->reg_cpw, &h->reg_G))
-      h->reg_ok = panel_reg_cluster_fits(h->reg_rpl, h->reg_cpw, h->reg_G);
-    h->plan_bk = bk;
-  }
-  const PanelPlan& pp = h->plan;
-  {
-    ProfScope ps(h, K_PANEL, 1);
-    if (sizeof(T) == 4 && h->reg_ok) {
-      CK(launch_panel_reg(h->reg_rpl, h->reg_cpw, h->reg_G, reinterpret_cast<float*>(Q + kb * g.ldq),
-                          g.ldq, reinterpret_cast<float*>(R + kb + kb * g.ldr), g.ldr, g.M, bk, h->tau,
-                          h->B.status, (int)kb, h->st));
-    } else {
-      const int variant = h->cfg.panel == CQR_PANEL_CGS1 ? 1 : (h->cfg.panel == CQR_PANEL_CGS2 ? 2 : 0);
-      CK(launch_panel<T>(pp, Q + kb * g.ldq, g.ldq, R + kb + kb * g.ldr, g.ldr, g.M, bk, h->tau,
-                         ptr<T>(h->B.part), h->B.bar, h->B.status, (int)kb, h->st, variant));
-    }
-  }
+  const int buf = t & 1;
+  cqr_status s = reorth_block_step<T>(h, kb, bk, buf, h->st);
+  if (s != CQR_OK) return s;
+  s = panel_kernel_step<T>(h, kb, bk, h->st);
+  if (s != CQR_OK) return s;
   const int64_t j0 = kb + bk;
   if (j0 >= g.N) return CQR_OK;
   const int64_t w = g.N - j0;
-  if (tc) {
+  if (h->tc) {
     {
       ProfScope ps(h, K_TC_SPLIT, 1);
-      CK(tc_split_panel(h->tc, kb, bk, true, h->st));
+      CK(tc_split_panel(h->tc, kb, bk, true, buf, h->st));
     }
-    {
-      ProfScope ps(h, K_TC_RBAR, 1);
-      CK(tc_gemm_rbar(h->tc, bk, j0, w, h->st));
-    }
-    {
-      ProfScope ps(h, K_SPLITK_REDUCE, 1);
-      CK(tc_reduce(h->tc, kb, bk, j0, w, ptr<float>(h->B.R), g.ldr, h->st));
-    }
-    {
-      ProfScope ps(h, K_TC_UPDATE, 1);
-      CK(tc_gemm_update(h->tc, bk, j0, w, h->st));
-    }
-    return CQR_OK;
+    return tc_update_cols(h, kb, bk, j0, w, buf, 0, 0, h->st);
   }
   const int splits = choose_splits(bk, w, g.M, h->num_sms);
   {
@@ -441,6 +480,92 @@ cqr_status panel_step(cqr_handle h, int t) {
     CK(launch_gemm_nn_sub<T>(Q + kb * g.ldq, g.ldq, ptr<T>(h->B.Rb), bk, Q + j0 * g.ldq, g.ldq,
                              g.M, bk, w, h->st));
   }
+  return CQR_OK;
+}
+
+// Look-ahead (tensor-core path, panel on one thread-block cluster): the trailing update of
+// panel t is split into the next panel's columns (narrow, on the critical stream A) and the
+// rest (wide, on stream B, at most num_sms - panel CTAs CTAs), so that the wide update runs
+// while panel t+1 is factorised.  Per panel t on A: block reorthogonalisation of panel t;
+// event a (B waits on it, then issues the wide update of panel t-1 and records event w); the
+// panel; the operand split (buffer t mod 2); A waits on w (the wide update of panel t-1 wrote
+// panel t+1's columns); the narrow update.  Both streams fork from and join into the
+// handle's stream, so the result of the call is stream-ordered like the sequential form.
+// The arithmetic of every panel (the column ranges of its two updates, their split-K
+// factors) does not depend on where factor calls start and end.
+bool lookahead_eligible(cqr_handle h) {
+  if (!h->tc) return false;
+  const char* env = getenv("CQR_LOOKAHEAD");
+  if (env && env[0] == '0') return false;
+  ensure_panel_plan<float>(h, (int)std::min<int64_t>(h->g.b, h->g.n));
+  // a cooperative (grid-barrier) panel must not wait for CTAs of a concurrent GEMM
+  return h->reg_ok || h->plan.cluster;
+}
+
+cqr_status lookahead_setup(cqr_handle h) {
+  if (h->la_st[0]) return CQR_OK;
+  int least = 0, greatest = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  CK(cudaStreamCreateWithPriority(&h->la_st[0], cudaStreamNonBlocking, greatest));
+  CK(cudaStreamCreateWithPriority(&h->la_st[1], cudaStreamNonBlocking, least));
+  for (auto& e : h->la_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return CQR_OK;
+}
+
+cqr_status factor_lookahead(cqr_handle h, int t0, int t1) {
+  cqr_status s = lookahead_setup(h);
+  if (s != CQR_OK) return s;
+  const Geo& g = h->g;
+  cudaStream_t A = h->la_st[0], Bst = h->la_st[1];
+  cudaEvent_t ev_fork = h->la_ev[0], ev_a = h->la_ev[1], ev_w = h->la_ev[2];
+  CK(cudaEventRecord(ev_fork, h->st));
+  CK(cudaStreamWaitEvent(A, ev_fork, 0));  // B joins through A's events (only if it gets work)
+  // the wide update waiting to be issued: panel (kb, bk), columns j0 .. j0+w-1, buffer
+  struct Wide { int64_t kb, j0, w; int bk, buf; } wide{0, 0, 0, 0, 0};
+  bool wide_due = false, w_pending = false;
+  auto issue_wide = [&]() -> cqr_status {
+    CK(cudaEventRecord(ev_a, A));
+    CK(cudaStreamWaitEvent(Bst, ev_a, 0));
+    const int pc = h->reg_ok ? h->reg_G : h->plan.G;
+    cqr_status r = tc_update_cols(h, wide.kb, wide.bk, wide.j0, wide.w, wide.buf, 1,
+                                  std::max(1, h->num_sms - pc), Bst);
+    if (r != CQR_OK) return r;
+    CK(cudaEventRecord(ev_w, Bst));
+    wide_due = false;
+    w_pending = true;
+    return CQR_OK;
+  };
+  for (int t = t0; t < t1; ++t) {
+    const int64_t kb = (int64_t)t * g.b;
+    const int bk = (int)std::min<int64_t>(g.b, g.n - kb);
+    const int buf = t & 1;
+    s = reorth_block_step<float>(h, kb, bk, buf, A);
+    if (s != CQR_OK) return s;
+    if (wide_due && (s = issue_wide()) != CQR_OK) return s;
+    s = panel_kernel_step<float>(h, kb, bk, A);
+    if (s != CQR_OK) return s;
+    const int64_t j0 = kb + bk;
+    if (j0 >= g.N) continue;
+    {
+      ProfScope ps(h, K_TC_SPLIT, 1, A);
+      CK(tc_split_panel(h->tc, kb, bk, true, buf, A));
+    }
+    const int64_t wn = j0 < g.n ? std::min<int64_t>(g.b, g.n - j0) : g.N - j0;
+    if (w_pending) {
+      CK(cudaStreamWaitEvent(A, ev_w, 0));
+      w_pending = false;
+    }
+    s = tc_update_cols(h, kb, bk, j0, wn, buf, 0, 0, A);
+    if (s != CQR_OK) return s;
+    if (j0 + wn < g.N) {
+      wide = Wide{kb, j0 + wn, g.N - j0 - wn, bk, buf};
+      wide_due = true;
+    }
+  }
+  if (wide_due && (s = issue_wide()) != CQR_OK) return s;
+  if (w_pending) CK(cudaStreamWaitEvent(A, ev_w, 0));
+  CK(cudaEventRecord(ev_a, A));
+  CK(cudaStreamWaitEvent(h->st, ev_a, 0));
   return CQR_OK;
 }
 
@@ -643,6 +768,10 @@ cqr_status coded_qr_destroy(cqr_handle h) {
   if (!h) return CQR_OK;
   if (h->st || true) cudaStreamSynchronize(h->st);
   if (h->tc) tc_destroy(h->tc);
+  for (auto e : h->la_ev)
+    if (e) cudaEventDestroy(e);
+  for (auto q : h->la_st)
+    if (q) cudaStreamDestroy(q);
   for (auto& r : h->prof_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : h->prof_pool) cudaEventDestroy(e);
   if (h->plans_ev) cudaEventDestroy(h->plans_ev);
@@ -695,10 +824,16 @@ cqr_status coded_qr_factor(cqr_handle h, int32_t t0, int32_t t1) {
   if (h->state == ST_CREATED || h->pending || h->postorth_inplace) return CQR_ESTATE;
   if (t1 < 0) t1 = h->g.panels;
   if (t0 != h->next_panel || t1 < t0 || t1 > h->g.panels) return CQR_ESTATE;
-  for (int t = t0; t < t1; ++t) {
-    cqr_status s = h->esz == 8 ? panel_step<double>(h, t) : panel_step<float>(h, t);
+  if (t1 > t0 && h->esz == 4 && lookahead_eligible(h)) {
+    cqr_status s = factor_lookahead(h, t0, t1);
     if (s != CQR_OK) return s;
-    ++h->panels_run;
+    h->panels_run += t1 - t0;
+  } else {
+    for (int t = t0; t < t1; ++t) {
+      cqr_status s = h->esz == 8 ? panel_step<double>(h, t) : panel_step<float>(h, t);
+      if (s != CQR_OK) return s;
+      ++h->panels_run;
+    }
   }
   h->next_panel = t1;
   h->state = (t1 == h->g.panels) ? ST_FACTORED : ST_ENCODED;

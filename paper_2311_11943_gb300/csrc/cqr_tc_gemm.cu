@@ -617,18 +617,20 @@ struct TcGemm {
   size_t pe;          // bytes per plane element
   int64_t M, N, b, bkp, ldq, ldk;
   float* Q;
-  void *Ak_hi, *Ak_lo, *At_hi, *At_lo, *Bh, *Bl;
-  float* P;
+  // panel operand planes, two buffers (panels of alternating parity), and the Rbar planes and
+  // split-K partials of two update contexts (the look-ahead runs two updates concurrently)
+  void *Ak_hi[2], *Ak_lo[2], *At_hi[2], *At_lo[2], *Bh[2], *Bl[2];
+  float* P[2];
   void *Qr_hi, *Qr_lo, *Sh, *Sl;   // block reorthogonalisation operands
   int64_t n, ldrow;
   int num_sms;
   int* status;
-  CUtensorMap tm_q_b;     // Q (FP32) as GEMM1's raw B (box 32 x BN)
-  CUtensorMap tm_ak[2];   // panel, column-major (box KE x BM)
-  CUtensorMap tm_at[2];   // panel, row-major (box KE x BM)
-  CUtensorMap tm_bh[2];   // Rbar planes (box KE x BN)
-  CUtensorMap tm_qr[2];   // computed columns, row-major (box KE x BM)
-  CUtensorMap tm_s[2];    // S planes, column-major ld ldrow (box KE x BN)
+  CUtensorMap tm_q_b;        // Q (FP32) as GEMM1's raw B (box 32 x BN)
+  CUtensorMap tm_ak[2][2];   // [buffer][plane] panel, column-major (box KE x BM)
+  CUtensorMap tm_at[2][2];   // [buffer][plane] panel, row-major (box KE x BM)
+  CUtensorMap tm_bh[2][2];   // [context][plane] Rbar planes (box KE x BN)
+  CUtensorMap tm_qr[2];      // computed columns, row-major (box KE x BM)
+  CUtensorMap tm_s[2];       // S planes, column-major ld ldrow (box KE x BN)
 };
 
 namespace {
@@ -666,13 +668,13 @@ bool encode_2d(CUtensorMap* tm, void* base, bool bf, uint64_t inner, uint64_t ou
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 template <bool BF, int STAGES, int NA, int NB>
-cudaError_t launch_gemm(const TcMaps& maps, const TcJob& job, int num_sms, cudaStream_t st) {
+cudaError_t launch_gemm(const TcMaps& maps, const TcJob& job, int max_ctas, cudaStream_t st) {
   using S = Smem<STAGES, NA, NB>;
   const void* fn = (const void*)k_tc_gemm<BF, STAGES, NA, NB>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kTotal);
   if (e != cudaSuccess) return e;
   const int tiles = job.m_tiles * job.n_tiles * job.splits;
-  const int grid = std::max(1, std::min(tiles, num_sms));
+  const int grid = std::max(1, std::min(tiles, max_ctas));
   k_tc_gemm<BF, STAGES, NA, NB><<<grid, kThreads, S::kTotal, st>>>(maps, job);
   return cudaGetLastError();
 }
@@ -682,14 +684,15 @@ cudaError_t launch_gemm(const TcMaps& maps, const TcJob& job, int num_sms, cudaS
 // product); otherwise B comes from planes.  Stages: 3 x 64 KB (two products), 6 x 32 KB
 // (one product), 4 x 48 KB (BF16, one product, raw FP32 B of 64 K elements).
 cudaError_t launch_mode(const TcGemm* t, bool split, const TcMaps& maps, const TcJob& job,
-                        cudaStream_t st) {
+                        cudaStream_t st, int max_ctas = 0) {
   const bool three = t->nplanes == 2;
+  const int mc = max_ctas > 0 ? std::min(max_ctas, t->num_sms) : t->num_sms;
   if (!t->bf)
-    return three ? launch_gemm<false, 3, 2, 2>(maps, job, t->num_sms, st)
-                 : launch_gemm<false, 6, 1, 1>(maps, job, t->num_sms, st);
-  if (three) return launch_gemm<true, 3, 2, 2>(maps, job, t->num_sms, st);
-  return split ? launch_gemm<true, 4, 1, 2>(maps, job, t->num_sms, st)
-               : launch_gemm<true, 6, 1, 1>(maps, job, t->num_sms, st);
+    return three ? launch_gemm<false, 3, 2, 2>(maps, job, mc, st)
+                 : launch_gemm<false, 6, 1, 1>(maps, job, mc, st);
+  if (three) return launch_gemm<true, 3, 2, 2>(maps, job, mc, st);
+  return split ? launch_gemm<true, 4, 1, 2>(maps, job, mc, st)
+               : launch_gemm<true, 6, 1, 1>(maps, job, mc, st);
 }
 
 template <typename P>
@@ -712,10 +715,10 @@ size_t tc_workspace_bytes(int mode, int64_t M, int64_t N, int64_t n, int b, int 
   const int64_t akc = std::max<int64_t>(bkp, round_to(b, BM));
   const int64_t ldrow = round_to(n, 64);
   size_t s = 0;
-  s += 2 * al256((size_t)ldk * akc * pe);        // Ak hi/lo
-  s += 2 * al256((size_t)M * bkp * pe);          // At hi/lo
-  s += 2 * al256((size_t)bkp * N * pe);          // Rbar planes
-  s += al256((size_t)kMaxSplits * bkp * N * 4);  // split-K partials (FP32)
+  s += 4 * al256((size_t)ldk * akc * pe);            // Ak hi/lo, two buffers
+  s += 4 * al256((size_t)M * bkp * pe);              // At hi/lo, two buffers
+  s += 4 * al256((size_t)bkp * N * pe);              // Rbar planes, two contexts
+  s += 2 * al256((size_t)kMaxSplits * bkp * N * 4);  // split-K partials (FP32), two contexts
   if (reorth_block) {
     s += 2 * al256((size_t)M * ldrow * pe);      // row-major computed columns hi/lo
     s += 2 * al256((size_t)ldrow * akc * pe);    // S planes
@@ -744,13 +747,15 @@ TcGemm* tc_create(int mode, int64_t M, int64_t N, int64_t n, int64_t b, float* Q
   const size_t pe = t->pe;
   char* p = static_cast<char*>(ws);
   auto take = [&](size_t bytes) { char* r = p; p += al256(bytes); return static_cast<void*>(r); };
-  t->Ak_hi = take((size_t)t->ldk * akc * pe);
-  t->Ak_lo = take((size_t)t->ldk * akc * pe);
-  t->At_hi = take((size_t)M * t->bkp * pe);
-  t->At_lo = take((size_t)M * t->bkp * pe);
-  t->Bh = take((size_t)t->bkp * N * pe);
-  t->Bl = take((size_t)t->bkp * N * pe);
-  t->P = static_cast<float*>(take((size_t)kMaxSplits * t->bkp * N * 4));
+  for (int u = 0; u < 2; ++u) {
+    t->Ak_hi[u] = take((size_t)t->ldk * akc * pe);
+    t->Ak_lo[u] = take((size_t)t->ldk * akc * pe);
+    t->At_hi[u] = take((size_t)M * t->bkp * pe);
+    t->At_lo[u] = take((size_t)M * t->bkp * pe);
+    t->Bh[u] = take((size_t)t->bkp * N * pe);
+    t->Bl[u] = take((size_t)t->bkp * N * pe);
+    t->P[u] = static_cast<float*>(take((size_t)kMaxSplits * t->bkp * N * 4));
+  }
   t->n = n;
   t->ldrow = round_to(n, 64);
   t->Qr_hi = t->Qr_lo = t->Sh = t->Sl = nullptr;
@@ -771,12 +776,14 @@ TcGemm* tc_create(int mode, int64_t M, int64_t N, int64_t n, int64_t b, float* Q
   const uint32_t KE = (uint32_t)t->KE;
   bool ok = true;
   ok &= encode_2d(&t->tm_q_b, Q, false, (uint64_t)M, (uint64_t)N, (uint64_t)ldq * 4, 32, BN);
-  ok &= encode_2d(&t->tm_ak[0], t->Ak_hi, bf, (uint64_t)M, (uint64_t)akc, (uint64_t)t->ldk * pe, KE, BM);
-  ok &= encode_2d(&t->tm_ak[1], t->Ak_lo, bf, (uint64_t)M, (uint64_t)akc, (uint64_t)t->ldk * pe, KE, BM);
-  ok &= encode_2d(&t->tm_at[0], t->At_hi, bf, (uint64_t)t->bkp, (uint64_t)M, (uint64_t)t->bkp * pe, KE, BM);
-  ok &= encode_2d(&t->tm_at[1], t->At_lo, bf, (uint64_t)t->bkp, (uint64_t)M, (uint64_t)t->bkp * pe, KE, BM);
-  ok &= encode_2d(&t->tm_bh[0], t->Bh, bf, (uint64_t)t->bkp, (uint64_t)N, (uint64_t)t->bkp * pe, KE, BN);
-  ok &= encode_2d(&t->tm_bh[1], t->Bl, bf, (uint64_t)t->bkp, (uint64_t)N, (uint64_t)t->bkp * pe, KE, BN);
+  for (int u = 0; u < 2; ++u) {
+    ok &= encode_2d(&t->tm_ak[u][0], t->Ak_hi[u], bf, (uint64_t)M, (uint64_t)akc, (uint64_t)t->ldk * pe, KE, BM);
+    ok &= encode_2d(&t->tm_ak[u][1], t->Ak_lo[u], bf, (uint64_t)M, (uint64_t)akc, (uint64_t)t->ldk * pe, KE, BM);
+    ok &= encode_2d(&t->tm_at[u][0], t->At_hi[u], bf, (uint64_t)t->bkp, (uint64_t)M, (uint64_t)t->bkp * pe, KE, BM);
+    ok &= encode_2d(&t->tm_at[u][1], t->At_lo[u], bf, (uint64_t)t->bkp, (uint64_t)M, (uint64_t)t->bkp * pe, KE, BM);
+    ok &= encode_2d(&t->tm_bh[u][0], t->Bh[u], bf, (uint64_t)t->bkp, (uint64_t)N, (uint64_t)t->bkp * pe, KE, BN);
+    ok &= encode_2d(&t->tm_bh[u][1], t->Bl[u], bf, (uint64_t)t->bkp, (uint64_t)N, (uint64_t)t->bkp * pe, KE, BN);
+  }
   if (reorth_block) {
     ok &= encode_2d(&t->tm_qr[0], t->Qr_hi, bf, (uint64_t)t->ldrow, (uint64_t)M, (uint64_t)t->ldrow * pe, KE, BM);
     ok &= encode_2d(&t->tm_qr[1], t->Qr_lo, bf, (uint64_t)t->ldrow, (uint64_t)M, (uint64_t)t->ldrow * pe, KE, BM);
@@ -795,8 +802,9 @@ void tc_destroy(TcGemm* t) { delete t; }
 void tc_set_status(TcGemm* t, int* status) { t->status = status; }
 
 namespace {
-int tc_splits(const TcGemm* t, int m1, int n1, int64_t* kchunk) {
-  int splits = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplits, (t->num_sms + m1 * n1 - 1) / (m1 * n1)));
+int tc_splits(const TcGemm* t, int m1, int n1, int64_t* kchunk, int max_ctas = 0) {
+  const int ctas = max_ctas > 0 ? std::min(max_ctas, t->num_sms) : t->num_sms;
+  int splits = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplits, (ctas + m1 * n1 - 1) / (m1 * n1)));
   const int64_t kblocks = (t->M + t->KE - 1) / t->KE;
   if (splits > kblocks) splits = (int)kblocks;
   *kchunk = (kblocks + splits - 1) / splits * t->KE;
@@ -806,7 +814,7 @@ int tc_splits(const TcGemm* t, int m1, int n1, int64_t* kchunk) {
 
 // 1. split the panel Q[:, kb : kb+bk] into the operand planes of both GEMMs (and, for a
 //    finished panel with block reorthogonalisation on, into the row-major computed columns)
-cudaError_t tc_split_panel(TcGemm* t, int64_t kb, int bk, bool finished, cudaStream_t st) {
+cudaError_t tc_split_panel(TcGemm* t, int64_t kb, int bk, bool finished, int buf, cudaStream_t st) {
   const int bkp = (int)round_to(bk, t->KE);
   const int m1 = (bk + BM - 1) / BM;
   dim3 grd((unsigned)((t->M + 31) / 32), (unsigned)((std::max(bkp, m1 * BM) + 31) / 32));
@@ -814,13 +822,13 @@ cudaError_t tc_split_panel(TcGemm* t, int64_t kb, int bk, bool finished, cudaStr
   if (t->bf) {
     using B16 = __nv_bfloat16;
     k_split_panel<B16><<<grd, 256, 0, st>>>(t->Q + kb * t->ldq, t->ldq, t->M, bk, bkp, m1 * BM,
-                                            t->nplanes, pl<B16>(t->Ak_hi), pl<B16>(t->Ak_lo), t->ldk,
-                                            pl<B16>(t->At_hi), pl<B16>(t->At_lo), pl<B16>(qh),
+                                            t->nplanes, pl<B16>(t->Ak_hi[buf]), pl<B16>(t->Ak_lo[buf]), t->ldk,
+                                            pl<B16>(t->At_hi[buf]), pl<B16>(t->At_lo[buf]), pl<B16>(qh),
                                             pl<B16>(t->Qr_lo), t->ldrow, kb);
   } else {
     k_split_panel<float><<<grd, 256, 0, st>>>(t->Q + kb * t->ldq, t->ldq, t->M, bk, bkp, m1 * BM,
-                                              t->nplanes, pl<float>(t->Ak_hi), pl<float>(t->Ak_lo),
-                                              t->ldk, pl<float>(t->At_hi), pl<float>(t->At_lo),
+                                              t->nplanes, pl<float>(t->Ak_hi[buf]), pl<float>(t->Ak_lo[buf]),
+                                              t->ldk, pl<float>(t->At_hi[buf]), pl<float>(t->At_lo[buf]),
                                               pl<float>(qh), pl<float>(t->Qr_lo), t->ldrow, kb);
   }
   return cudaGetLastError();
@@ -844,16 +852,17 @@ cudaError_t tc_refresh_rows(TcGemm* t, int64_t ncols, cudaStream_t st) {
 }
 
 // 2. GEMM1, split-K over the M rows: partials P[s] = Qbar^T Q[:, j0 : j0+w]
-cudaError_t tc_gemm_rbar(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t st) {
+cudaError_t tc_gemm_rbar(TcGemm* t, int bk, int64_t j0, int64_t w, int buf, int ctx, int max_ctas,
+                         cudaStream_t st) {
   const int three = t->nplanes == 2;
   const int bkp = (int)round_to(bk, t->KE);
   const int m1 = (bk + BM - 1) / BM;
   const int n1 = (int)((w + BN - 1) / BN);
   int64_t kchunk = 0;
-  const int splits = tc_splits(t, m1, n1, &kchunk);
+  const int splits = tc_splits(t, m1, n1, &kchunk, max_ctas);
   TcMaps maps;
-  maps.a[0] = t->tm_ak[0];
-  maps.a[1] = t->tm_ak[1];
+  maps.a[0] = t->tm_ak[buf][0];
+  maps.a[1] = t->tm_ak[buf][1];
   maps.b[0] = t->tm_q_b;
   maps.b[1] = t->tm_q_b;
   TcJob job{};
@@ -872,43 +881,44 @@ cudaError_t tc_gemm_rbar(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t 
   job.K = t->M;
   job.mrows = bk;
   job.ncols = w;
-  job.out = t->P;
+  job.out = t->P[ctx];
   job.ldo = bkp;
   job.split_stride = (int64_t)bkp * w;
   job.status = t->status;
-  return launch_mode(t, split, maps, job, st);
+  return launch_mode(t, split, maps, job, st, max_ctas);
 }
 
 // 3. reduce the partials into R[kb.., j0..] and GEMM2's B planes
 cudaError_t tc_reduce(TcGemm* t, int64_t kb, int bk, int64_t j0, int64_t w, float* R, int64_t ldr,
-                      cudaStream_t st) {
+                      int ctx, int max_ctas, cudaStream_t st) {
   const int bkp = (int)round_to(bk, t->KE);
   const int m1 = (bk + BM - 1) / BM;
   const int n1 = (int)((w + BN - 1) / BN);
   int64_t kchunk = 0;
-  const int splits = tc_splits(t, m1, n1, &kchunk);
+  const int splits = tc_splits(t, m1, n1, &kchunk, max_ctas);
   const int64_t total = (int64_t)bkp * w;
   const int blocks = (int)std::min<int64_t>(4096, (total + 255) / 256);
   if (t->bf)
-    k_tc_reduce<__nv_bfloat16><<<blocks, 256, 0, st>>>(t->P, splits, (int64_t)bkp * w, bkp, bk, bkp, w,
+    k_tc_reduce<__nv_bfloat16><<<blocks, 256, 0, st>>>(t->P[ctx], splits, (int64_t)bkp * w, bkp, bk, bkp, w,
                                                        R + kb + j0 * ldr, ldr, t->nplanes,
-                                                       pl<__nv_bfloat16>(t->Bh), pl<__nv_bfloat16>(t->Bl));
+                                                       pl<__nv_bfloat16>(t->Bh[ctx]), pl<__nv_bfloat16>(t->Bl[ctx]));
   else
-    k_tc_reduce<float><<<blocks, 256, 0, st>>>(t->P, splits, (int64_t)bkp * w, bkp, bk, bkp, w,
-                                               R + kb + j0 * ldr, ldr, t->nplanes, pl<float>(t->Bh),
-                                               pl<float>(t->Bl));
+    k_tc_reduce<float><<<blocks, 256, 0, st>>>(t->P[ctx], splits, (int64_t)bkp * w, bkp, bk, bkp, w,
+                                               R + kb + j0 * ldr, ldr, t->nplanes, pl<float>(t->Bh[ctx]),
+                                               pl<float>(t->Bl[ctx]));
   return cudaGetLastError();
 }
 
 // 4. GEMM2: Q[:, j0 : j0+w] -= Qbar Rbar (M tiles over rows, N tiles over trailing columns)
-cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t st) {
+cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, int buf, int ctx, int max_ctas,
+                           cudaStream_t st) {
   const int three = t->nplanes == 2;
   const int bkp = (int)round_to(bk, t->KE);
   TcMaps maps;
-  maps.a[0] = t->tm_at[0];
-  maps.a[1] = t->tm_at[1];
-  maps.b[0] = t->tm_bh[0];
-  maps.b[1] = t->tm_bh[1];
+  maps.a[0] = t->tm_at[buf][0];
+  maps.a[1] = t->tm_at[buf][1];
+  maps.b[0] = t->tm_bh[ctx][0];
+  maps.b[1] = t->tm_bh[ctx][1];
   TcJob job{};
   job.nprod = three ? 3 : 1;
   job.split_b_smem = 0;
@@ -927,20 +937,20 @@ cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_
   job.ldo = t->ldq;
   job.split_stride = 0;
   job.status = t->status;
-  return launch_mode(t, false, maps, job, st);
+  return launch_mode(t, false, maps, job, st, max_ctas);
 }
 
 // Block reorthogonalisation of panel kb .. kb+bk-1 against columns 0 .. kb-1 (four
 // launches: split the panel, S^T = Qbar^T Q[:, 0:kb] split-K on the tensor cores, reduce
 // into R and S, Qbar -= Qrows S on the tensor cores).
-cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr, cudaStream_t st,
-                            int* launches) {
+cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr, int buf,
+                            cudaStream_t st, int* launches) {
   *launches = 0;
   if (!t->Qr_hi || kb <= 0) return cudaSuccess;
   *launches = 4;
-  cudaError_t e = tc_split_panel(t, kb, bk, false, st);
+  cudaError_t e = tc_split_panel(t, kb, bk, false, buf, st);
   if (e != cudaSuccess) return e;
-  e = tc_gemm_rbar(t, bk, 0, kb, st);  // partials of S^T (bk x kb)
+  e = tc_gemm_rbar(t, bk, 0, kb, buf, 0, 0, st);  // partials of S^T (bk x kb), context 0
   if (e != cudaSuccess) return e;
   const int KE = t->KE;
   const int bkp = (int)round_to(bk, KE);
@@ -953,12 +963,12 @@ cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr
     const int64_t total = kbp * bk;
     const int blocks = (int)std::min<int64_t>(4096, (total + 255) / 256);
     if (t->bf)
-      k_tc_reduce_t<__nv_bfloat16><<<blocks, 256, 0, st>>>(t->P, splits, (int64_t)bkp * kb, bkp, bk, kb,
+      k_tc_reduce_t<__nv_bfloat16><<<blocks, 256, 0, st>>>(t->P[0], splits, (int64_t)bkp * kb, bkp, bk, kb,
                                                            kbp, R, ldr, t->nplanes,
                                                            pl<__nv_bfloat16>(t->Sh),
                                                            pl<__nv_bfloat16>(t->Sl), t->ldrow);
     else
-      k_tc_reduce_t<float><<<blocks, 256, 0, st>>>(t->P, splits, (int64_t)bkp * kb, bkp, bk, kb, kbp,
+      k_tc_reduce_t<float><<<blocks, 256, 0, st>>>(t->P[0], splits, (int64_t)bkp * kb, bkp, bk, kb, kbp,
                                                    R, ldr, t->nplanes, pl<float>(t->Sh),
                                                    pl<float>(t->Sl), t->ldrow);
     e = cudaGetLastError();
@@ -1002,7 +1012,7 @@ cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr
     job.split_stride = 0;
   } else {
     job.epi = 0;
-    job.out = t->P;
+    job.out = t->P[0];
     job.ldo = t->M;
     job.split_stride = t->M * (int64_t)bk;
   }
@@ -1011,7 +1021,7 @@ cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr
   *launches = 5;
   const int64_t total = t->M * (int64_t)bk;
   const int blocks = (int)std::min<int64_t>((int64_t)t->num_sms * 8, (total + 255) / 256);
-  k_tc_sub_partials<<<blocks, 256, 0, st>>>(t->P, splits2, t->M, bk, t->Q + kb * t->ldq, t->ldq);
+  k_tc_sub_partials<<<blocks, 256, 0, st>>>(t->P[0], splits2, t->M, bk, t->Q + kb * t->ldq, t->ldq);
   return cudaGetLastError();
 }
 

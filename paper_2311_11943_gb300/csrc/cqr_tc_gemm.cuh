@@ -19,18 +19,24 @@ void tc_set_status(TcGemm* t, int* status);
 // The trailing update of one panel, in four stream-ordered launches:
 //   split the panel into operand planes; Rbar partials = Qbar^T Q[:, j0:j0+w] (split-K);
 //   reduce into R[kb:kb+bk, j0:j0+w] and GEMM2's operand; Q[:, j0:j0+w] -= Qbar Rbar.
-cudaError_t tc_split_panel(TcGemm* t, int64_t kb, int bk, bool finished, cudaStream_t st);
-cudaError_t tc_gemm_rbar(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t st);
+// buf (0/1) selects the panel's operand planes (panels of alternating parity use different
+// buffers), ctx (0/1) the partials and Rbar planes of an update, so that two updates of
+// disjoint column ranges can run concurrently on two streams; max_ctas (0: all SMs) caps the
+// CTAs of a GEMM launch and its split-K factor (the same cap for rbar and reduce).
+cudaError_t tc_split_panel(TcGemm* t, int64_t kb, int bk, bool finished, int buf, cudaStream_t st);
+cudaError_t tc_gemm_rbar(TcGemm* t, int bk, int64_t j0, int64_t w, int buf, int ctx, int max_ctas,
+                         cudaStream_t st);
 cudaError_t tc_reduce(TcGemm* t, int64_t kb, int bk, int64_t j0, int64_t w, float* R, int64_t ldr,
-                      cudaStream_t st);
-cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, cudaStream_t st);
+                      int ctx, int max_ctas, cudaStream_t st);
+cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, int buf, int ctx, int max_ctas,
+                           cudaStream_t st);
 
 // Block reorthogonalisation of panel columns kb .. kb+bk-1 against columns 0 .. kb-1:
 // S = Q[:, 0:kb]^T Qbar, Qbar -= Q[:, 0:kb] S, R[0:kb, kb:kb+bk] += S (four launches, five
 // when the second product is split over K); *launches receives the count.
 bool tc_has_block_reorth(const TcGemm* t);
-cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr, cudaStream_t st,
-                            int* launches);
+cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr, int buf,
+                            cudaStream_t st, int* launches);
 cudaError_t tc_refresh_rows(TcGemm* t, int64_t ncols, cudaStream_t st);
 
 }  // namespace cqr
