@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
   const int64_t row0 = (int64_t)g * RPC;
   const int nr = (int)((M - row0) < RPC ? (M - row0) : RPC);
   float* eta = v + 256;
-  constexpr int GS = CPW < 8 ? CPW : 8;  // slots reduced per butterfly
+  constexpr int GS = CPW < 4 ? CPW : 4;  // slots reduced per butterfly
   constexpr int NG = CPW / GS;
   const int slot = slot_of<GS>(lane);
   const int lps = lanes_per_slot<GS>();
@@ -332,7 +332,10 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
     const float inv = 1.f / rjj;
     const bool nxt = j + 1 < bk;
     const float cn = nxt ? v[j + 1] * inv : 0.f;
-    if (g == 0 && tid == 0) R[j + j * ldr] = rjj;
+    if (g == 0) {  // row j of R: r_jj and r_ja = v_a / r_jj (a > j)
+      if (tid == 0) R[j + j * ldr] = rjj;
+      for (int a = j + 1 + tid; a < bk; a += kNT) R[j + a * ldr] = v[a] * inv;
+    }
     uint64_t q[NP], pn[NP];
     const uint64_t sinv = f2splat(inv), ncn = f2splat(-cn);
 #pragma unroll
@@ -341,36 +344,43 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
       pn[i] = nxt ? f2fma(q[i], ncn, *reinterpret_cast<const uint64_t*>(st_cur + RPC + 64 * i + 2 * lane))
                   : 0ull;
     }
+    // Straight-line update of the owned columns of a group of GS (no branch between columns,
+    // so the compiler interleaves their independent chains): a column that is not active
+    // (a <= j or past the panel) is updated with the coefficient 0, which leaves it exactly
+    // unchanged, and its product is not pushed; column j then takes q_j.
 #pragma unroll
     for (int gr = 0; gr < NG; ++gr) {
+      // a group whose columns are all finished (a <= j) has nothing to update or push
+      if (warp + kNW * (gr * GS + GS - 1) <= j) continue;
       float d[GS];
 #pragma unroll
       for (int kk = 0; kk < GS; ++kk) {
         const int k = gr * GS + kk;
         const int a = warp + kNW * k;
-        d[kk] = 0.f;
-        if (a == j) {
+        const bool act = a > j && a < bk;
+        const uint64_t nca = f2splat(act ? -(v[a] * inv) : 0.f);
+        uint64_t s = 0ull;
 #pragma unroll
-          for (int i = 0; i < NP; ++i) P[k][i] = q[i];
-        } else if (a > j && a < bk) {
-          const float ca = v[a] * inv;
-          if (g == 0 && lane == 0) R[j + a * ldr] = ca;
-          const uint64_t nca = f2splat(-ca);
-          uint64_t s = 0ull;
-#pragma unroll
-          for (int i = 0; i < NP; ++i) {
-            const uint64_t x = f2fma(q[i], nca, P[k][i]);
-            P[k][i] = x;
-            s = f2fma(x, pn[i], s);
-          }
-          d[kk] = f2sum(s);
+        for (int i = 0; i < NP; ++i) {
+          const uint64_t x = f2fma(q[i], nca, P[k][i]);
+          P[k][i] = x;
+          s = f2fma(x, pn[i], s);
         }
+        d[kk] = f2sum(s);
       }
       if (nxt) {
         const float e = butterfly<GS>(d, lane);
         const int a = warp + kNW * (gr * GS + slot);
         push(e, par, 0, a > j && a < bk, a);
       }
+    }
+    if (warp == (j % kNW)) {
+      const int kj = j / kNW;
+#pragma unroll
+      for (int k = 0; k < CPW; ++k)
+        if (k == kj)
+#pragma unroll
+          for (int i = 0; i < NP; ++i) P[k][i] = q[i];
     }
     if (!nxt) break;
     owner_write(j + 1, st_nxt);
