@@ -11,9 +11,13 @@
 //   copy of columns j, j+1 (double-buffered by column parity); each warp updates its own
 //   columns a > j in registers and forms p_a^T p_{j+1}; the per-lane partials of a warp's
 //   columns are combined by a butterfly over the lanes into this CTA's partial vector in
-//   shared memory; after the hardware cluster barrier every CTA reads all G partial vectors
-//   (16-byte distributed-shared-memory loads) and sums them in the same fixed order.  The
-//   owners of columns j+1 and j+2 write them to the other staging buffer before the barrier.
+//   shared memory; every CTA then stores its partial vector into every CTA's receive buffer
+//   (16-byte asynchronous distributed-shared-memory stores that count their bytes on the
+//   receiver's mbarrier), waits on its own mbarrier for the G vectors and sums them in the
+//   same fixed order.  The owners of columns j+1 and j+2 write them to the other staging
+//   buffer before the exchange.  Receive buffers and mbarriers alternate by reduction parity:
+//   a CTA sends reduction k+2 only after it has received reduction k+1 from every CTA, each
+//   of which sent it after finishing with its own buffer of reduction k.
 #include <math.h>
 
 #include "cqr_device.cuh"
@@ -36,15 +40,30 @@ __device__ __forceinline__ uint32_t saddr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ float4 ld_peer4(uint32_t local_addr, uint32_t rank) {
+__device__ __forceinline__ uint32_t peer_addr(uint32_t local_addr, uint32_t rank) {
   uint32_t r;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
-  float4 v;
-  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "r"(r)
-               : "memory");
-  return v;
+  return r;
+}
+// 16 bytes into a peer's shared memory, completing 16 transaction bytes on its mbarrier
+__device__ __forceinline__ void st_async4(uint32_t dst, float4 v, uint32_t mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+               ::"r"(dst), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
+               ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\t"
+               "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(ok) : "r"(saddr(bar)), "r"(parity) : "memory");
+  return ok != 0;
 }
 
 __device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
@@ -126,10 +145,11 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
   extern __shared__ __align__(16) unsigned char smraw[];
   float* stage = reinterpret_cast<float*>(smraw);       // [2 parity][2 columns][RPC]
   float* lpart = stage + 4 * RPC;                        // [2 parity][512] own partials
-  float* red = lpart + 2 * 512;                          // [8][512] peer-group sums
-  float* v = red + 8 * 512;                              // [512]: v, eta in [256..)
+  float* rbuf = lpart + 2 * 512;                         // [2 parity][kMaxG senders][512]
+  float* v = rbuf + 2 * kMaxG * 512;                     // [512]: v, eta in [256..)
   float* sv = v + 512;                                   // [256]
   float* racc = sv + 256;                                // [kNW][RPC] reorth contributions
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(racc + kNW * RPC);  // [2 parity]
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int64_t row0 = (int64_t)g * RPC;
@@ -140,6 +160,13 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
   const int slot = slot_of<GS>(lane);
   const int lps = lanes_per_slot<GS>();
   const int sub = lane % lps;            // which subset of peers this lane pushes to
+
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    mbar_init(mbar + 1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  cl_sync();  // every CTA's mbarriers are initialised before any peer stores into it
 
   uint64_t P[CPW][NP];
   // load the slice (zero rows past M)
@@ -172,25 +199,52 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
   auto push = [&](float s, int par, int base, bool active_slot, int a) {
     if (active_slot && sub == 0) lpart[par * 512 + base + a] = s;
   };
-  // out[a] (lo <= a < hi) = sum over the G CTAs of their partial vectors: thread t reads the
-  // 4-column chunk t % 32 of peers t / 32 and t / 32 + 8, then the 8 peer-group sums are added
-  auto reduce_local = [&](int par, int lo, int hi, float* out) {
-    const int c0 = lo / 4, c1 = (hi + 3) / 4;
-    const int ch = c0 + (tid & 31), pg = tid >> 5;
-    if (ch < c1) {
-      const uint32_t local = saddr(lpart + par * 512 + 4 * ch);
-      float4 x = make_float4(0.f, 0.f, 0.f, 0.f), y = x;
-      if (pg < G) x = ld_peer4(local, pg);
-      if (pg + 8 < G) y = ld_peer4(local, pg + 8);
-      *reinterpret_cast<float4*>(red + pg * 512 + 4 * ch) =
-          make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+  // exchange of the partial vectors, entries lo .. hi-1 (whole 4-entry chunks): this CTA's
+  // chunks go into receive buffer [par][g] of every CTA; then the wait for all G vectors
+  unsigned phases = 0u;  // bit p: the phase parity of mbarrier p
+  auto exchange = [&](int par, int lo, int hi) {
+    const int c0 = lo / 4, nch = (hi + 3) / 4 - c0;
+    __syncthreads();  // this CTA's partials are complete
+    if (tid == 0) mbar_expect(mbar + par, (unsigned)(G * nch * 16));
+    const uint32_t dst0 = saddr(rbuf + ((size_t)par * kMaxG + g) * 512);
+    const uint32_t bar0 = saddr(mbar + par);
+    if (nch <= 32) {
+      // lane l sends chunk c0 + l to the peers warp, warp + 8 (one float4 read, G <= 16)
+      const int l = tid & 31;
+      if (l < nch) {
+        const float4 x = *reinterpret_cast<const float4*>(lpart + par * 512 + 4 * (c0 + l));
+        for (int peer = warp; peer < G; peer += kNW)
+          st_async4(peer_addr(dst0, peer) + 16u * (c0 + l), x, peer_addr(bar0, peer));
+      }
+    } else {
+      for (int it = tid; it < G * nch; it += kNT) {
+        const int peer = it / nch, ch = c0 + it % nch;
+        const float4 x = *reinterpret_cast<const float4*>(lpart + par * 512 + 4 * ch);
+        st_async4(peer_addr(dst0, peer) + 16u * ch, x, peer_addr(bar0, peer));
+      }
     }
-    __syncthreads();
+    const long long t0 = clock64();
+    while (!mbar_try_wait(mbar + par, (phases >> par) & 1u)) {
+      if (clock64() - t0 > kWaitLimitCycles) {  // never expected: report and go on
+        set_status(status, CQR_ETIMEOUT, 40);
+        break;
+      }
+    }
+    phases ^= 1u << par;
+  };
+  // out[a] (lo <= a < hi) = sum over the G CTAs of their partial vectors, in a fixed order
+  auto gather = [&](int par, int lo, int hi, float* out) {
+    const float* rb = rbuf + (size_t)par * kMaxG * 512;
     for (int a = lo + tid; a < hi; a += kNT) {
-      float s = 0.f;
+      // fixed-shape tree over kMaxG senders (absent ones add zero)
+      float x[kMaxG];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) s += red[q * 512 + a];
-      out[a] = s;
+      for (int q = 0; q < kMaxG; ++q) x[q] = q < G ? rb[q * 512 + a] : 0.f;
+#pragma unroll
+      for (int w = kMaxG / 2; w > 0; w /= 2)
+#pragma unroll
+        for (int q = 0; q < w; ++q) x[q] += x[q + w];
+      out[a] = x[0];
     }
   };
 
@@ -225,10 +279,9 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
   }
   // columns 0 and 1 go to staging buffer 0 (column 0 is still there)
   owner_write(1, stage + RPC);
-  cl_sync();
-  reduce_local(par, 0, bk, v);
-  __syncthreads();
-  reduce_local(par, 256, 256 + bk, v);
+  exchange(par, 0, 256 + bk);
+  gather(par, 0, bk, v);
+  gather(par, 256, 256 + bk, v);
   __syncthreads();
   par ^= 1;
 
@@ -254,8 +307,8 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
         const int a = warp + kNW * (gr * GS + slot);
         push(e, par, 0, a < j, a);
       }
-      cl_sync();
-      reduce_local(par, 0, j, sv);
+      exchange(par, 0, j);
+      gather(par, 0, j, sv);
       __syncthreads();
       par ^= 1;
       // each warp's contribution sum_{a < j, owned} q_a s_a for its rows, then the owner sums
@@ -317,15 +370,15 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
         const int a = warp + kNW * (gr * GS + slot);
         push(e, par, 0, a >= j && a < bk, a);
       }
-      cl_sync();
-      reduce_local(par, j, bk, v);
+      exchange(par, j, bk);
+      gather(par, j, bk, v);
       __syncthreads();
       par ^= 1;
     }
     const float v0 = v[j];
     if (!(v0 > 0.f) || !isfinite(v0)) {
       if (g == 0 && tid == 0) set_status(status, CQR_EBREAKDOWN, col0 + j);
-      cl_sync();  // uniform exit: no peer may still be reading this CTA's partials
+      cl_sync();  // uniform exit (every CTA sees the same v)
       return;
     }
     const float rjj = sqrtf(v0);
@@ -385,12 +438,12 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
     if (!nxt) break;
     owner_write(j + 1, st_nxt);
     owner_write(j + 2, st_nxt + RPC);
-    cl_sync();
-    reduce_local(par, j + 1, bk, v);
+    exchange(par, j + 1, bk);
+    gather(par, j + 1, bk, v);
     __syncthreads();
     par ^= 1;
   }
-  cl_sync();  // the last reduction's remote reads of this CTA's partials are done
+  cl_sync();  // uniform end
   // write the finished slice back
 #pragma unroll
   for (int k = 0; k < CPW; ++k) {
@@ -409,7 +462,8 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
 
 size_t reg_smem_bytes(int rpl) {
   const size_t rpc = 32 * (size_t)rpl;
-  return (4 * rpc + 2 * 512 + 8 * 512 + 512 + 256 + (size_t)kNW * rpc) * sizeof(float) + 256;
+  return (4 * rpc + 2 * 512 + 2 * (size_t)kMaxG * 512 + 512 + 256 + (size_t)kNW * rpc) * sizeof(float) +
+         2 * sizeof(uint64_t) + 256;
 }
 
 template <int RPL, int CPW>
