@@ -194,6 +194,7 @@ struct cqr_handle_s {
   // of the wide trailing updates (lowest priority), created on first use; events fork, a, w
   cudaStream_t la_st[2] = {nullptr, nullptr};
   cudaEvent_t la_ev[3] = {nullptr, nullptr, nullptr};
+  bool la_pdl = false;  // programmatic dependent launch on the critical stream
 };
 
 namespace {
@@ -411,7 +412,7 @@ cqr_status panel_kernel_step(cqr_handle h, int64_t kb, int bk, cudaStream_t st) 
   if (sizeof(T) == 4 && h->reg_ok) {
     CK(launch_panel_reg(h->reg_rpl, h->reg_cpw, h->reg_G, reinterpret_cast<float*>(Q + kb * g.ldq),
                         g.ldq, reinterpret_cast<float*>(R + kb + kb * g.ldr), g.ldr, g.M, bk, h->tau,
-                        h->B.status, (int)kb, st));
+                        h->B.status, (int)kb, st, h->la_pdl && st == h->la_st[0]));
   } else {
     const int variant = h->cfg.panel == CQR_PANEL_CGS1 ? 1 : (h->cfg.panel == CQR_PANEL_CGS2 ? 2 : 0);
     CK(launch_panel<T>(h->plan, Q + kb * g.ldq, g.ldq, R + kb + kb * g.ldr, g.ldr, g.M, bk, h->tau,
@@ -517,6 +518,10 @@ cqr_status factor_lookahead(cqr_handle h, int t0, int t1) {
   if (s != CQR_OK) return s;
   const Geo& g = h->g;
   cudaStream_t A = h->la_st[0], Bst = h->la_st[1];
+  // programmatic dependent launch along the critical stream (CQR_PDL=0 turns it off)
+  const char* pe = getenv("CQR_PDL");
+  h->la_pdl = !(pe && pe[0] == '0');
+  tc_set_pdl_stream(h->tc, h->la_pdl ? A : nullptr);
   cudaEvent_t ev_fork = h->la_ev[0], ev_a = h->la_ev[1], ev_w = h->la_ev[2];
   CK(cudaEventRecord(ev_fork, h->st));
   CK(cudaStreamWaitEvent(A, ev_fork, 0));  // B joins through A's events (only if it gets work)

@@ -51,8 +51,10 @@ size_t panel_partial_bytes(int bk, size_t elem, int num_sms);
 // Register-resident FP32 panel in one cluster (cqr_panel_reg.cu).
 bool plan_panel_reg(int64_t M, int bk, int* rpl, int* cpw, int* G);
 bool panel_reg_cluster_fits(int rpl, int cpw, int G);
+// pdl: launch with programmatic stream serialization (the kernel waits for its predecessor).
 cudaError_t launch_panel_reg(int rpl, int cpw, int G, float* Q, int64_t ldq, float* R, int64_t ldr,
-                             int64_t M, int bk, double tau, int* status, int col0, cudaStream_t st);
+                             int64_t M, int bk, double tau, int* status, int col0, cudaStream_t st,
+                             bool pdl = false);
 
 // variant: 0 the paper's ICGS panel (MGS order; no reorthogonalisation when tau <= 0),
 // 1 left-looking CGS with one reduction per column, 2 CGS2.

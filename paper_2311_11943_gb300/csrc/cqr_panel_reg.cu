@@ -167,6 +167,10 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   cl_sync();  // every CTA's mbarriers are initialised before any peer stores into it
+  // launched with programmatic stream serialization, the kernel may start while its
+  // predecessor finishes: wait for it before reading the panel (no early trigger of the
+  // successor, whose waiting CTAs would take SMs from concurrent work)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   uint64_t P[CPW][NP];
   // load the slice (zero rows past M)
@@ -502,7 +506,8 @@ bool plan_panel_reg(int64_t M, int bk, int* rpl_out, int* cpw_out, int* G_out) {
 }
 
 cudaError_t launch_panel_reg(int rpl, int cpw, int G, float* Q, int64_t ldq, float* R, int64_t ldr,
-                             int64_t M, int bk, double tau, int* status, int col0, cudaStream_t st) {
+                             int64_t M, int bk, double tau, int* status, int col0, cudaStream_t st,
+                             bool pdl) {
   const void* fn = pick_reg(rpl, cpw);
   if (!fn) return cudaErrorInvalidValue;
   const size_t smem = reg_smem_bytes(rpl);
@@ -519,13 +524,15 @@ cudaError_t launch_panel_reg(int rpl, int cpw, int G, float* Q, int64_t ldq, flo
   cfg.blockDim = dim3(kNT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = G;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl ? 2 : 1;
   return cudaLaunchKernelExC(&cfg, fn, args);
 }
 

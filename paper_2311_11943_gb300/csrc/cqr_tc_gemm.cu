@@ -216,6 +216,13 @@ struct Smem {
   static_assert(STAGES * 3 * 8 + 4 * 8 + 8 <= 256, "barrier region too small");
 };
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start while its predecessor in the stream finishes.  Every kernel here waits for the
+// predecessor's completion (and memory) before touching any data, and only then lets its own
+// successor launch, so at most one kernel ahead is resident and waiting.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <bool BF, int STAGES, int NA, int NB>
 __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__ TcMaps maps,
                                                           const TcJob job) {
@@ -264,6 +271,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  pdl_wait();
+  pdl_trigger();
 
   // K blocks of tile t
   auto kblocks = [&](int split) -> int {
@@ -494,6 +503,8 @@ __global__ void __launch_bounds__(256) k_split_panel(const float* __restrict__ Q
                                                      P* __restrict__ Qr_hi, P* __restrict__ Qr_lo,
                                                      int64_t ldrow, int64_t kb) {
   __shared__ P sh[32][33], sl[32][33];
+  pdl_wait();
+  pdl_trigger();
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t r0 = (int64_t)blockIdx.x * 32;
   const int k0 = blockIdx.y * 32;
@@ -533,6 +544,8 @@ __global__ void __launch_bounds__(256) k_split_panel(const float* __restrict__ Q
 // mrows x ncols column-major with leading dimension mrows).
 __global__ void k_tc_sub_partials(const float* __restrict__ P, int splits, int64_t mrows,
                                   int64_t ncols, float* __restrict__ C, int64_t ldc) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t total = mrows * ncols;
   const int64_t stride = total;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -568,6 +581,8 @@ __global__ void k_tc_reduce_t(const float* __restrict__ P, int splits, int64_t s
                               int64_t ldp, int bk, int64_t kb, int64_t kbp, float* __restrict__ R,
                               int64_t ldr, int nplanes, PT* __restrict__ Sh,
                               PT* __restrict__ Sl, int64_t ldrow) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t total = kbp * bk;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -590,6 +605,8 @@ template <typename PT>
 __global__ void k_tc_reduce(const float* __restrict__ P, int splits, int64_t split_stride, int64_t ldp,
                             int bk, int bkp, int64_t w, float* __restrict__ R, int64_t ldr,
                             int nplanes, PT* __restrict__ Bh, PT* __restrict__ Bl) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t total = (int64_t)bkp * w;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -625,6 +642,7 @@ struct TcGemm {
   int64_t n, ldrow;
   int num_sms;
   int* status;
+  cudaStream_t pdl_st = nullptr;  // launches on this stream use programmatic dependent launch
   CUtensorMap tm_q_b;        // Q (FP32) as GEMM1's raw B (box 32 x BN)
   CUtensorMap tm_ak[2][2];   // [buffer][plane] panel, column-major (box KE x BM)
   CUtensorMap tm_at[2][2];   // [buffer][plane] panel, row-major (box KE x BM)
@@ -667,16 +685,32 @@ bool encode_2d(CUtensorMap* tm, void* base, bool bf, uint64_t inner, uint64_t ou
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Kernel launch, with programmatic stream serialization when pdl is set.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? at : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <bool BF, int STAGES, int NA, int NB>
-cudaError_t launch_gemm(const TcMaps& maps, const TcJob& job, int max_ctas, cudaStream_t st) {
+cudaError_t launch_gemm(const TcMaps& maps, const TcJob& job, int max_ctas, cudaStream_t st, bool pdl) {
   using S = Smem<STAGES, NA, NB>;
   const void* fn = (const void*)k_tc_gemm<BF, STAGES, NA, NB>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kTotal);
   if (e != cudaSuccess) return e;
   const int tiles = job.m_tiles * job.n_tiles * job.splits;
   const int grid = std::max(1, std::min(tiles, max_ctas));
-  k_tc_gemm<BF, STAGES, NA, NB><<<grid, kThreads, S::kTotal, st>>>(maps, job);
-  return cudaGetLastError();
+  return launch_k(k_tc_gemm<BF, STAGES, NA, NB>, dim3(grid), dim3(kThreads), S::kTotal, st, pdl, maps, job);
 }
 
 // One launch of the tensor-core kernel in the variant of the handle's mode.  split: B arrives
@@ -687,12 +721,13 @@ cudaError_t launch_mode(const TcGemm* t, bool split, const TcMaps& maps, const T
                         cudaStream_t st, int max_ctas = 0) {
   const bool three = t->nplanes == 2;
   const int mc = max_ctas > 0 ? std::min(max_ctas, t->num_sms) : t->num_sms;
+  const bool pdl = st == t->pdl_st && st != nullptr;
   if (!t->bf)
-    return three ? launch_gemm<false, 3, 2, 2>(maps, job, mc, st)
-                 : launch_gemm<false, 6, 1, 1>(maps, job, mc, st);
-  if (three) return launch_gemm<true, 3, 2, 2>(maps, job, mc, st);
-  return split ? launch_gemm<true, 4, 1, 2>(maps, job, mc, st)
-               : launch_gemm<true, 6, 1, 1>(maps, job, mc, st);
+    return three ? launch_gemm<false, 3, 2, 2>(maps, job, mc, st, pdl)
+                 : launch_gemm<false, 6, 1, 1>(maps, job, mc, st, pdl);
+  if (three) return launch_gemm<true, 3, 2, 2>(maps, job, mc, st, pdl);
+  return split ? launch_gemm<true, 4, 1, 2>(maps, job, mc, st, pdl)
+               : launch_gemm<true, 6, 1, 1>(maps, job, mc, st, pdl);
 }
 
 template <typename P>
@@ -801,6 +836,8 @@ void tc_destroy(TcGemm* t) { delete t; }
 
 void tc_set_status(TcGemm* t, int* status) { t->status = status; }
 
+void tc_set_pdl_stream(TcGemm* t, cudaStream_t st) { t->pdl_st = st; }
+
 namespace {
 int tc_splits(const TcGemm* t, int m1, int n1, int64_t* kchunk, int max_ctas = 0) {
   const int ctas = max_ctas > 0 ? std::min(max_ctas, t->num_sms) : t->num_sms;
@@ -819,19 +856,19 @@ cudaError_t tc_split_panel(TcGemm* t, int64_t kb, int bk, bool finished, int buf
   const int m1 = (bk + BM - 1) / BM;
   dim3 grd((unsigned)((t->M + 31) / 32), (unsigned)((std::max(bkp, m1 * BM) + 31) / 32));
   void* qh = finished ? t->Qr_hi : nullptr;
+  const bool pdl = st == t->pdl_st && st != nullptr;
+  const float* q0 = t->Q + kb * t->ldq;
   if (t->bf) {
     using B16 = __nv_bfloat16;
-    k_split_panel<B16><<<grd, 256, 0, st>>>(t->Q + kb * t->ldq, t->ldq, t->M, bk, bkp, m1 * BM,
-                                            t->nplanes, pl<B16>(t->Ak_hi[buf]), pl<B16>(t->Ak_lo[buf]), t->ldk,
-                                            pl<B16>(t->At_hi[buf]), pl<B16>(t->At_lo[buf]), pl<B16>(qh),
-                                            pl<B16>(t->Qr_lo), t->ldrow, kb);
-  } else {
-    k_split_panel<float><<<grd, 256, 0, st>>>(t->Q + kb * t->ldq, t->ldq, t->M, bk, bkp, m1 * BM,
-                                              t->nplanes, pl<float>(t->Ak_hi[buf]), pl<float>(t->Ak_lo[buf]),
-                                              t->ldk, pl<float>(t->At_hi[buf]), pl<float>(t->At_lo[buf]),
-                                              pl<float>(qh), pl<float>(t->Qr_lo), t->ldrow, kb);
+    return launch_k(k_split_panel<B16>, grd, dim3(256), 0, st, pdl, q0, t->ldq, t->M, bk, bkp,
+                    (int)(m1 * BM), t->nplanes, pl<B16>(t->Ak_hi[buf]), pl<B16>(t->Ak_lo[buf]), t->ldk,
+                    pl<B16>(t->At_hi[buf]), pl<B16>(t->At_lo[buf]), pl<B16>(qh), pl<B16>(t->Qr_lo),
+                    t->ldrow, kb);
   }
-  return cudaGetLastError();
+  return launch_k(k_split_panel<float>, grd, dim3(256), 0, st, pdl, q0, t->ldq, t->M, bk, bkp,
+                  (int)(m1 * BM), t->nplanes, pl<float>(t->Ak_hi[buf]), pl<float>(t->Ak_lo[buf]), t->ldk,
+                  pl<float>(t->At_hi[buf]), pl<float>(t->At_lo[buf]), pl<float>(qh), pl<float>(t->Qr_lo),
+                  t->ldrow, kb);
 }
 
 bool tc_has_block_reorth(const TcGemm* t) { return t->Qr_hi != nullptr; }
@@ -898,15 +935,16 @@ cudaError_t tc_reduce(TcGemm* t, int64_t kb, int bk, int64_t j0, int64_t w, floa
   const int splits = tc_splits(t, m1, n1, &kchunk, max_ctas);
   const int64_t total = (int64_t)bkp * w;
   const int blocks = (int)std::min<int64_t>(4096, (total + 255) / 256);
+  const bool pdl = st == t->pdl_st && st != nullptr;
+  const float* P = t->P[ctx];
+  float* Rd = R + kb + j0 * ldr;
   if (t->bf)
-    k_tc_reduce<__nv_bfloat16><<<blocks, 256, 0, st>>>(t->P[ctx], splits, (int64_t)bkp * w, bkp, bk, bkp, w,
-                                                       R + kb + j0 * ldr, ldr, t->nplanes,
-                                                       pl<__nv_bfloat16>(t->Bh[ctx]), pl<__nv_bfloat16>(t->Bl[ctx]));
-  else
-    k_tc_reduce<float><<<blocks, 256, 0, st>>>(t->P[ctx], splits, (int64_t)bkp * w, bkp, bk, bkp, w,
-                                               R + kb + j0 * ldr, ldr, t->nplanes, pl<float>(t->Bh[ctx]),
-                                               pl<float>(t->Bl[ctx]));
-  return cudaGetLastError();
+    return launch_k(k_tc_reduce<__nv_bfloat16>, dim3(blocks), dim3(256), 0, st, pdl, P, splits,
+                    (int64_t)bkp * w, (int64_t)bkp, bk, bkp, w, Rd, ldr, t->nplanes,
+                    pl<__nv_bfloat16>(t->Bh[ctx]), pl<__nv_bfloat16>(t->Bl[ctx]));
+  return launch_k(k_tc_reduce<float>, dim3(blocks), dim3(256), 0, st, pdl, P, splits, (int64_t)bkp * w,
+                  (int64_t)bkp, bk, bkp, w, Rd, ldr, t->nplanes, pl<float>(t->Bh[ctx]),
+                  pl<float>(t->Bl[ctx]));
 }
 
 // 4. GEMM2: Q[:, j0 : j0+w] -= Qbar Rbar (M tiles over rows, N tiles over trailing columns)
@@ -962,16 +1000,16 @@ cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr
   {
     const int64_t total = kbp * bk;
     const int blocks = (int)std::min<int64_t>(4096, (total + 255) / 256);
+    const bool pdl = st == t->pdl_st && st != nullptr;
+    const float* P0 = t->P[0];
     if (t->bf)
-      k_tc_reduce_t<__nv_bfloat16><<<blocks, 256, 0, st>>>(t->P[0], splits, (int64_t)bkp * kb, bkp, bk, kb,
-                                                           kbp, R, ldr, t->nplanes,
-                                                           pl<__nv_bfloat16>(t->Sh),
-                                                           pl<__nv_bfloat16>(t->Sl), t->ldrow);
+      e = launch_k(k_tc_reduce_t<__nv_bfloat16>, dim3(blocks), dim3(256), 0, st, pdl, P0, splits,
+                   (int64_t)bkp * kb, (int64_t)bkp, bk, kb, kbp, R, ldr, t->nplanes,
+                   pl<__nv_bfloat16>(t->Sh), pl<__nv_bfloat16>(t->Sl), t->ldrow);
     else
-      k_tc_reduce_t<float><<<blocks, 256, 0, st>>>(t->P[0], splits, (int64_t)bkp * kb, bkp, bk, kb, kbp,
-                                                   R, ldr, t->nplanes, pl<float>(t->Sh),
-                                                   pl<float>(t->Sl), t->ldrow);
-    e = cudaGetLastError();
+      e = launch_k(k_tc_reduce_t<float>, dim3(blocks), dim3(256), 0, st, pdl, P0, splits,
+                   (int64_t)bkp * kb, (int64_t)bkp, bk, kb, kbp, R, ldr, t->nplanes,
+                   pl<float>(t->Sh), pl<float>(t->Sl), t->ldrow);
     if (e != cudaSuccess) return e;
   }
   TcMaps maps;
@@ -1021,8 +1059,9 @@ cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr
   *launches = 5;
   const int64_t total = t->M * (int64_t)bk;
   const int blocks = (int)std::min<int64_t>((int64_t)t->num_sms * 8, (total + 255) / 256);
-  k_tc_sub_partials<<<blocks, 256, 0, st>>>(t->P[0], splits2, t->M, bk, t->Q + kb * t->ldq, t->ldq);
-  return cudaGetLastError();
+  const bool pdl = st == t->pdl_st && st != nullptr;
+  return launch_k(k_tc_sub_partials, dim3(blocks), dim3(256), 0, st, pdl, (const float*)t->P[0], splits2,
+                  t->M, (int64_t)bk, t->Q + kb * t->ldq, t->ldq);
 }
 
 }  // namespace cqr

@@ -16,6 +16,9 @@ TcGemm* tc_create(int mode, int64_t M, int64_t N, int64_t n, int64_t b, float* Q
                   void* ws, int num_sms, int reorth_block, cudaStream_t st);
 void tc_destroy(TcGemm* t);
 void tc_set_status(TcGemm* t, int* status);
+// Launches on stream st (and only there) use programmatic dependent launch: each kernel waits
+// for its predecessor's completion before touching data, then lets its successor launch.
+void tc_set_pdl_stream(TcGemm* t, cudaStream_t st);
 // The trailing update of one panel, in four stream-ordered launches:
 //   split the panel into operand planes; Rbar partials = Qbar^T Q[:, j0:j0+w] (split-K);
 //   reduce into R[kb:kb+bk, j0:j0+w] and GEMM2's operand; Q[:, j0:j0+w] -= Qbar Rbar.
