@@ -225,11 +225,12 @@ cqr_status coded_qr_sync_status(cqr_handle h);
 
 /* Profile of the library's own kernels (instrumentation, no counterpart in the paper).
  * Launch counts per kernel class are always kept; with enable != 0 every launch site is
- * also bracketed by a pair of CUDA events on cfg.stream.  coded_qr_profile_read
+ * also bracketed by a pair of CUDA events on the stream its launches go to (cfg.stream, or
+ * one of the two internal streams of the look-ahead; classes on different streams overlap).  coded_qr_profile_read
  * synchronises the stream and fills (host) ms[k] (device milliseconds) and launches[k]
  * for the first cap classes (CQR_PROF_CLASSES in total) since the last reset; reset != 0
  * clears the accumulators.  coded_qr_profile_name gives the class name (NULL past the end). */
-#define CQR_PROF_CLASSES 15
+#define CQR_PROF_CLASSES 16
 cqr_status coded_qr_profile(cqr_handle h, int32_t enable);
 cqr_status coded_qr_profile_read(cqr_handle h, double* ms, int64_t* launches, int32_t cap,
                                  int32_t reset);

@@ -142,12 +142,12 @@ Layout make_layout(const cqr_config* c, const Geo& g, int num_sms) {
 enum KClass {
   K_GENERATOR = 0, K_ENCODE, K_PANEL, K_GEMM_RBAR, K_SPLITK_REDUCE, K_GEMM_UPDATE, K_POISON,
   K_DECODE, K_POST_ORTH, K_SOLVE_GEMV, K_TRSV, K_TC_RBAR, K_TC_UPDATE, K_TC_SPLIT,
-  K_BLOCK_REORTH, K_COUNT
+  K_BLOCK_REORTH, K_TC_NARROW, K_COUNT
 };
 static const char* kClassNames[K_COUNT] = {
     "generator", "encode", "panel_icgs", "gemm_rbar_simt", "splitk_reduce", "gemm_update_simt",
     "erasure_poison", "decode", "post_orth", "solve_gemv", "trsv", "tc_rbar", "tc_update",
-    "tc_split_panel", "block_reorth"};
+    "tc_split_panel", "block_reorth", "tc_narrow_update"};
 
 struct ProfRec {
   int cls;
@@ -560,7 +560,12 @@ cqr_status factor_lookahead(cqr_handle h, int t0, int t1) {
       CK(cudaStreamWaitEvent(A, ev_w, 0));
       w_pending = false;
     }
-    s = tc_update_cols(h, kb, bk, j0, wn, buf, 0, 0, A);
+    {
+      // the look-ahead's narrow update as a whole (its three launches are also counted in
+      // their own classes)
+      ProfScope ps(h, K_TC_NARROW, 0, A);
+      s = tc_update_cols(h, kb, bk, j0, wn, buf, 0, 0, A);
+    }
     if (s != CQR_OK) return s;
     if (j0 + wn < g.N) {
       wide = Wide{kb, j0 + wn, g.N - j0 - wn, bk, buf};

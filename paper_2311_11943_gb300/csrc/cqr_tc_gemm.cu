@@ -575,23 +575,38 @@ __global__ void k_refresh_rows(const float* __restrict__ Q, int64_t ldq, int64_t
 
 // Block reorthogonalisation, reduce: the GEMM1 partials hold S^T = Qbar^T Q[:, 0:kb]
 // (P[s][i + j bkp]); R[j, kb+i] += S[j][i] and S (column-major, ld ldrow, rows >= kb zero)
-// goes into the B planes of the second product.
+// goes into the B planes of the second product.  One 32 x 32 tile (i, j) per CTA: the
+// partials are read along i and the sums go through shared memory, so R and S are written
+// along j (both coalesced).
 template <typename PT>
-__global__ void k_tc_reduce_t(const float* __restrict__ P, int splits, int64_t split_stride,
-                              int64_t ldp, int bk, int64_t kb, int64_t kbp, float* __restrict__ R,
-                              int64_t ldr, int nplanes, PT* __restrict__ Sh,
-                              PT* __restrict__ Sl, int64_t ldrow) {
+__global__ void __launch_bounds__(256) k_tc_reduce_t(const float* __restrict__ P, int splits,
+                                                     int64_t split_stride, int64_t ldp, int bk,
+                                                     int64_t kb, int64_t kbp, float* __restrict__ R,
+                                                     int64_t ldr, int nplanes, PT* __restrict__ Sh,
+                                                     PT* __restrict__ Sl, int64_t ldrow) {
+  __shared__ float tile[32][33];
   pdl_wait();
   pdl_trigger();
-  const int64_t total = kbp * bk;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = idx % kbp, i = idx / kbp;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * 32;
+  const int64_t j0 = (int64_t)blockIdx.y * 32;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + tx;
+    const int64_t j = j0 + ty + 8 * u;
     float s = 0.f;
-    if (j < kb) {
+    if (i < bk && j < kb)
       for (int sp = 0; sp < splits; ++sp) s += P[sp * split_stride + i + j * ldp];
-      R[j + (kb + i) * ldr] += s;
-    }
+    tile[ty + 8 * u][tx] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + ty + 8 * u;
+    const int64_t j = j0 + tx;
+    if (i >= bk || j >= kbp) continue;
+    const float s = tile[tx][ty + 8 * u];
+    if (j < kb) R[j + (kb + i) * ldr] += s;
     PT h, l;
     hilo(s, nplanes, h, l);
     Sh[j + i * ldrow] = h;
@@ -998,16 +1013,15 @@ cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr
   const int splits = tc_splits(t, m1, n1, &kchunk);
   const int64_t kbp = round_to(kb, KE);
   {
-    const int64_t total = kbp * bk;
-    const int blocks = (int)std::min<int64_t>(4096, (total + 255) / 256);
+    const dim3 blocks((unsigned)((bk + 31) / 32), (unsigned)((kbp + 31) / 32));
     const bool pdl = st == t->pdl_st && st != nullptr;
     const float* P0 = t->P[0];
     if (t->bf)
-      e = launch_k(k_tc_reduce_t<__nv_bfloat16>, dim3(blocks), dim3(256), 0, st, pdl, P0, splits,
+      e = launch_k(k_tc_reduce_t<__nv_bfloat16>, blocks, dim3(256), 0, st, pdl, P0, splits,
                    (int64_t)bkp * kb, (int64_t)bkp, bk, kb, kbp, R, ldr, t->nplanes,
                    pl<__nv_bfloat16>(t->Sh), pl<__nv_bfloat16>(t->Sl), t->ldrow);
     else
-      e = launch_k(k_tc_reduce_t<float>, dim3(blocks), dim3(256), 0, st, pdl, P0, splits,
+      e = launch_k(k_tc_reduce_t<float>, blocks, dim3(256), 0, st, pdl, P0, splits,
                    (int64_t)bkp * kb, (int64_t)bkp, bk, kb, kbp, R, ldr, t->nplanes,
                    pl<float>(t->Sh), pl<float>(t->Sl), t->ldrow);
     if (e != cudaSuccess) return e;
