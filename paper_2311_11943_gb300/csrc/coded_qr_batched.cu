@@ -66,6 +66,7 @@ struct cqr_batched_s {
   int64_t* d_off_p = nullptr;
   int64_t tot_v = 0, tot_h = 0, tot_p = 0;
   int* d_order = nullptr;
+  int* d_order_ab = nullptr;   // [2][count]: the two factor phases of a run, each by its own work
   int* d_queue = nullptr;      // two counters
   int* d_range_a = nullptr;
   int* d_range_b = nullptr;
@@ -129,18 +130,19 @@ cqr_status enqueue_encode(cqr_batched bh) {
   BK(cudaMemsetAsync(bh->d_R0, 0, bh->r_bytes, bh->st));
   BK(cudaMemsetAsync(bh->d_status, 0, sizeof(int) * 4 * bh->count, bh->st));
   BK(launch_b_encode<float>(bh->d_inst, bh->count, bh->d_off_v, bh->tot_v, bh->d_off_h, bh->tot_h,
-                            bh->d_Gt_t, bh->d_Gh_t, bh->num_sms, bh->st));
+                            bh->d_Gt_t, bh->d_Gh_t, bh->cfg.f, bh->st));
   return CQR_OK;
 }
 
-cqr_status enqueue_factor(cqr_batched bh, const int* d_range, int queue_slot) {
+cqr_status enqueue_factor(cqr_batched bh, const int* d_range, int queue_slot,
+                          const int* d_order = nullptr) {
   BK(cudaMemsetAsync(bh->d_queue + queue_slot, 0, sizeof(int), bh->st));
   BFactorLaunch L;
   L.G = bh->G;
   L.grid = bh->grid;
   L.inst = bh->d_inst;
   L.count = bh->count;
-  L.order = bh->d_order;
+  L.order = d_order ? d_order : bh->d_order;
   L.range = d_range;
   L.queue = bh->d_queue + queue_slot;
   L.tau2 = bh->tau2;
@@ -319,6 +321,7 @@ cqr_status coded_qr_batched_create(const cqr_config* cfg, const int64_t* m, cons
   const size_t o_offh = take(sizeof(int64_t) * (count + 1));
   const size_t o_offp = take(sizeof(int64_t) * (count + 1));
   const size_t o_order = take(sizeof(int) * count);
+  const size_t o_order_ab = take(sizeof(int) * 2 * count);
   const size_t o_queue = take(sizeof(int) * 2);
   const size_t o_ra = take(sizeof(int) * 2 * count);
   const size_t o_rb = take(sizeof(int) * 2 * count);
@@ -344,6 +347,7 @@ cqr_status coded_qr_batched_create(const cqr_config* cfg, const int64_t* m, cons
   bh->d_off_h = reinterpret_cast<int64_t*>(base + o_offh);
   bh->d_off_p = reinterpret_cast<int64_t*>(base + o_offp);
   bh->d_order = reinterpret_cast<int*>(base + o_order);
+  bh->d_order_ab = reinterpret_cast<int*>(base + o_order_ab);
   bh->d_queue = reinterpret_cast<int*>(base + o_queue);
   bh->d_range_a = reinterpret_cast<int*>(base + o_ra);
   bh->d_range_b = reinterpret_cast<int*>(base + o_rb);
@@ -574,6 +578,24 @@ cqr_status coded_qr_batched_run(cqr_batched bh, const void* const* A, const int6
       return s;
     }
   }
+  // work order of each factor phase: decreasing work of that phase (longest first), the work
+  // of panel t being M bk (N - t b) (its panel and its trailing update)
+  std::vector<int> ord(2 * bh->count);
+  for (int ph = 0; ph < 2; ++ph) {
+    const std::vector<int>& rg = ph == 0 ? ra : rb;
+    std::vector<double> w(bh->count, 0.0);
+    for (int k = 0; k < bh->count; ++k) {
+      const Geo& g = bh->geo[k];
+      const int b = bh->h_inst[k].b;
+      for (int t = rg[2 * k]; t < rg[2 * k + 1]; ++t) {
+        const int64_t kb = (int64_t)t * b;
+        w[k] += (double)g.M * (double)std::min<int64_t>(b, g.n - kb) * (double)(g.N - kb);
+      }
+    }
+    int* o = ord.data() + ph * bh->count;
+    std::iota(o, o + bh->count, 0);
+    std::stable_sort(o, o + bh->count, [&](int x, int y) { return w[x] > w[y]; });
+  }
   std::vector<int64_t> key;
   key.push_back(flags);
   for (int e = 0; e < 4 * count; ++e) key.push_back(erasures[e]);
@@ -586,20 +608,21 @@ cqr_status coded_qr_batched_run(cqr_batched bh, const void* const* A, const int6
   if (!replay) {
     s = upload(bh, bh->d_range_a, ra.data(), sizeof(int) * ra.size());
     if (s == CQR_OK) s = upload(bh, bh->d_range_b, rb.data(), sizeof(int) * rb.size());
+    if (s == CQR_OK) s = upload(bh, bh->d_order_ab, ord.data(), sizeof(int) * ord.size());
     if (s == CQR_OK) s = upload(bh, bh->d_tiles, list.data(), sizeof(BatchTile) * list.size());
     if (s == CQR_OK) s = upload_plans(bh, plans, &dec_total);
     if (s != CQR_OK) return s;
   }
   auto sequence = [&]() -> cqr_status {
     cqr_status r = enqueue_encode(bh);
-    if (r == CQR_OK) r = enqueue_factor(bh, bh->d_range_a, 0);
+    if (r == CQR_OK) r = enqueue_factor(bh, bh->d_range_a, 0, bh->d_order_ab);
     if (r == CQR_OK && !list.empty()) {
       BK(launch_b_poison<float>(bh->d_inst, bh->d_tiles, (int)list.size(), bh->max_tile_elems,
                                 bh->num_sms, bh->st));
       BK(launch_b_decode<float>(bh->d_inst, bh->d_plans, (int)plans.size(), bh->d_plan_off,
                                 dec_total, bh->d_Gt, bh->d_Gh, bh->num_sms, bh->st));
     }
-    if (r == CQR_OK && !list.empty()) r = enqueue_factor(bh, bh->d_range_b, 1);
+    if (r == CQR_OK && !list.empty()) r = enqueue_factor(bh, bh->d_range_b, 1, bh->d_order_ab + bh->count);
     if (r == CQR_OK && (flags & CQR_BATCH_POST_ORTH))
       BK(launch_b_post_orth<float>(bh->d_inst, bh->count, bh->d_off_p, bh->tot_p, bh->d_Gt_t,
                                    bh->num_sms, bh->st));

@@ -73,73 +73,119 @@ cudaError_t launch_generator(int f, int p_r, int p_c, uint64_t seed, int gdist, 
 // (G_v A) G_h.  Sums run in the oracle's order (t, resp. j, ascending).
 // The bodies take their block coordinates as arguments so that the batched kernels can map
 // a flat list of blocks over many instances onto them.
-template <typename T>
-__device__ __forceinline__ void encode_vertical_body(const Geo& g, const T* __restrict__ A,
-                                                     int64_t lda, const T* __restrict__ Gt,
-                                                     T* __restrict__ Q, int bx, int by, int j) {
-  const int64_t r = (int64_t)bx * 32 + threadIdx.x;
-  const int64_t s = (int64_t)by * 8 + threadIdx.y;
-  if (r >= g.mb || s >= g.nb) return;
-  const int64_t col = (int64_t)j * g.nb + s;
-  T acc[kMaxF];
+// F checksums known at compile time (F <= 8; larger f takes the generic loop, F = -1): the
+// geometry in registers, per-column base pointers, eight tile loads in flight per chunk.
+template <typename T, int F>
+__device__ __forceinline__ void encode_vertical_f(const Geo& g, const T* __restrict__ A, int64_t lda,
+                                                  const T* __restrict__ Gt, T* __restrict__ Q,
+                                                  int bx, int by, int j) {
+  const int mb = (int)g.mb, nb = (int)g.nb, p_r = g.p_r;
+  const int f = F >= 0 ? F : g.f;
+  constexpr int NA = F > 0 ? F : (F == 0 ? 1 : kMaxF);
+  const int64_t m = g.m;
+  const int r = bx * 32 + threadIdx.x;
+  const int s = by * 8 + threadIdx.y;
+  if (r >= mb || s >= nb) return;
+  const int64_t col = (int64_t)j * nb + s;
+  const T* Ac = A + col * lda;
+  T* Qc = Q + col * g.ldq;
+  T acc[NA];
 #pragma unroll
-  for (int i = 0; i < kMaxF; ++i) acc[i] = T(0);
-  for (int t = 0; t < g.p_r; ++t) {
-    const int64_t row = (int64_t)t * g.mb + r;
-    const T a = (row < g.m) ? A[row + col * lda] : T(0);
-    Q[row + col * g.ldq] = a;
+  for (int i = 0; i < NA; ++i) acc[i] = T(0);
+  for (int t0 = 0; t0 < p_r; t0 += 8) {
+    T a[8];
 #pragma unroll
-    for (int i = 0; i < kMaxF; ++i)
-      if (i < g.f) acc[i] += Gt[i * g.p_r + t] * a;
+    for (int u = 0; u < 8; ++u) {
+      const int64_t row = (int64_t)(t0 + u) * mb + r;
+      a[u] = (t0 + u < p_r && row < m) ? Ac[row] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u;
+      if (t >= p_r) break;
+      Qc[(int64_t)t * mb + r] = a[u];
+#pragma unroll
+      for (int i = 0; i < NA; ++i)
+        if (i < f) acc[i] += Gt[i * p_r + t] * a[u];
+    }
   }
 #pragma unroll
-  for (int i = 0; i < kMaxF; ++i)
-    if (i < g.f) Q[g.m_pad + (int64_t)i * g.mb + r + col * g.ldq] = acc[i];
+  for (int i = 0; i < NA; ++i)
+    if (i < f) Qc[g.m_pad + (int64_t)i * mb + r] = acc[i];
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_encode_vertical(Geo g, const T* __restrict__ A, int64_t lda,
+// F bucket of a checksum count: the count itself up to 4, else -1 (generic)
+inline int f_bucket(int f) { return f <= 4 ? f : -1; }
+
+template <typename T, int F>
+__global__ void __launch_bounds__(256, 4) k_encode_vertical(Geo g, const T* __restrict__ A, int64_t lda,
                                                           const T* __restrict__ Gt, T* __restrict__ Q) {
-  encode_vertical_body<T>(g, A, lda, Gt, Q, blockIdx.x, blockIdx.y, blockIdx.z);
+  encode_vertical_f<T, F>(g, A, lda, Gt, Q, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-template <typename T>
-__device__ __forceinline__ void encode_horizontal_body(const Geo& g, const T* __restrict__ Gh,
-                                                       T* __restrict__ Q, int bx, int by, int t) {
-  const int64_t r = (int64_t)bx * 32 + threadIdx.x;
-  const int64_t s = (int64_t)by * 8 + threadIdx.y;
-  if (r >= g.mb || s >= g.nb) return;
-  const int64_t row = (int64_t)t * g.mb + r;
-  T acc[kMaxF];
+template <typename T, int F>
+__device__ __forceinline__ void encode_horizontal_f(const Geo& g, const T* __restrict__ Gh,
+                                                    T* __restrict__ Q, int bx, int by, int t) {
+  const int mb = (int)g.mb, nb = (int)g.nb, p_c = g.p_c;
+  const int f = F >= 0 ? F : g.f;
+  constexpr int NA = F > 0 ? F : (F == 0 ? 1 : kMaxF);
+  const int r = bx * 32 + threadIdx.x;
+  const int s = by * 8 + threadIdx.y;
+  if (r >= mb || s >= nb) return;
+  const int64_t ldq = g.ldq;
+  T* Qr = Q + (int64_t)t * mb + r + (int64_t)s * ldq;  // row (t, r), column s of tile column 0
+  const int64_t tcs = (int64_t)nb * ldq;                 // one tile column
+  T acc[NA];
 #pragma unroll
-  for (int l = 0; l < kMaxF; ++l) acc[l] = T(0);
-  for (int j = 0; j < g.p_c; ++j) {
-    const T a = Q[row + ((int64_t)j * g.nb + s) * g.ldq];
+  for (int l = 0; l < NA; ++l) acc[l] = T(0);
+  for (int j0 = 0; j0 < p_c; j0 += 8) {
+    T a[8];
 #pragma unroll
-    for (int l = 0; l < kMaxF; ++l)
-      if (l < g.f) acc[l] += Gh[j * g.f + l] * a;
+    for (int u = 0; u < 8; ++u) a[u] = (j0 + u < p_c) ? Qr[(int64_t)(j0 + u) * tcs] : T(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + u;
+      if (j >= p_c) break;
+#pragma unroll
+      for (int l = 0; l < NA; ++l)
+        if (l < f) acc[l] += Gh[j * f + l] * a[u];
+    }
   }
+  T* Qd = Q + (int64_t)t * mb + r + (g.n + (int64_t)s) * ldq;
 #pragma unroll
-  for (int l = 0; l < kMaxF; ++l)
-    if (l < g.f) Q[row + (g.n + (int64_t)l * g.nb + s) * g.ldq] = acc[l];
+  for (int l = 0; l < NA; ++l)
+    if (l < f) Qd[(int64_t)l * tcs] = acc[l];
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_encode_horizontal(Geo g, const T* __restrict__ Gh, T* __restrict__ Q) {
-  encode_horizontal_body<T>(g, Gh, Q, blockIdx.x, blockIdx.y, blockIdx.z);
+template <typename T, int F>
+__global__ void __launch_bounds__(256, 4) k_encode_horizontal(Geo g, const T* __restrict__ Gh, T* __restrict__ Q) {
+  encode_horizontal_f<T, F>(g, Gh, Q, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <typename T, int F>
+cudaError_t launch_encode_f(const Geo& g, const T* A, int64_t lda, const T* Gt, const T* Gh, T* Q,
+                            cudaStream_t st) {
+  dim3 blk(32, 8);
+  dim3 grd((unsigned)((g.mb + 31) / 32), (unsigned)((g.nb + 7) / 8), (unsigned)g.p_c);
+  k_encode_vertical<T, F><<<grd, blk, 0, st>>>(g, A, lda, Gt, Q);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !g.protect_r || g.f == 0) return e;
+  grd.z = (unsigned)(g.p_r + g.f);
+  k_encode_horizontal<T, F><<<grd, blk, 0, st>>>(g, Gh, Q);
+  return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_encode(const Geo& g, const T* A, int64_t lda, const T* Gt, const T* Gh, T* Q,
                           cudaStream_t st) {
-  dim3 blk(32, 8);
-  dim3 grd((unsigned)((g.mb + 31) / 32), (unsigned)((g.nb + 7) / 8), (unsigned)g.p_c);
-  k_encode_vertical<T><<<grd, blk, 0, st>>>(g, A, lda, Gt, Q);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || !g.protect_r || g.f == 0) return e;
-  grd.z = (unsigned)(g.p_r + g.f);
-  k_encode_horizontal<T><<<grd, blk, 0, st>>>(g, Gh, Q);
-  return cudaGetLastError();
+  switch (f_bucket(g.f)) {
+    case 0: return launch_encode_f<T, 0>(g, A, lda, Gt, Gh, Q, st);
+    case 1: return launch_encode_f<T, 1>(g, A, lda, Gt, Gh, Q, st);
+    case 2: return launch_encode_f<T, 2>(g, A, lda, Gt, Gh, Q, st);
+    case 3: return launch_encode_f<T, 3>(g, A, lda, Gt, Gh, Q, st);
+    case 4: return launch_encode_f<T, 4>(g, A, lda, Gt, Gh, Q, st);
+    default: return launch_encode_f<T, -1>(g, A, lda, Gt, Gh, Q, st);
+  }
 }
 
 // ===================================================================== a4/a5 SIMT GEMMs
@@ -1030,54 +1076,69 @@ int64_t batch_decode_blocks(const Geo& g, const DecodePlan& p) {
   return ((h + 31) / 32) * ((g.nb + 7) / 8);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_b_encode_vertical(const BatchInst<T>* __restrict__ inst,
-                                                            int count, const int64_t* __restrict__ off,
-                                                            const T* __restrict__ Gt) {
-  const int64_t total = off[count];
-  for (int64_t v = blockIdx.x; v < total; v += gridDim.x) {
-    const int i = find_instance(off, count, v);
+// Batched encode: grid.y strides over the instances, grid.x blocks over one instance's blocks
+// (no search of a flat block index, 32-bit block coordinates).
+constexpr int kBEncX = 32;
+
+template <typename T, int F>
+__global__ void __launch_bounds__(256, 4) k_b_encode_vertical(const BatchInst<T>* __restrict__ inst,
+                                                            int count, const T* __restrict__ Gt) {
+  for (int i = blockIdx.y; i < count; i += gridDim.y) {
     const BatchInst<T>& I = inst[i];
-    int64_t loc = v - off[i];
-    const int64_t nbx = (I.g.mb + 31) / 32, nby = (I.g.nb + 7) / 8;
-    const int bx = (int)(loc % nbx);
-    loc /= nbx;
-    encode_vertical_body<T>(I.g, I.A, I.lda, Gt, I.Q, bx, (int)(loc % nby), (int)(loc / nby));
+    const int nbx = (int)((I.g.mb + 31) / 32), nby = (int)((I.g.nb + 7) / 8);
+    const int total = nbx * nby * I.g.p_c;
+    for (int v = blockIdx.x; v < total; v += gridDim.x) {
+      const int bx = v % nbx, rest = v / nbx;
+      encode_vertical_f<T, F>(I.g, I.A, I.lda, Gt, I.Q, bx, rest % nby, rest / nby);
+    }
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_b_encode_horizontal(const BatchInst<T>* __restrict__ inst,
-                                                              int count, const int64_t* __restrict__ off,
-                                                              const T* __restrict__ Gh) {
-  const int64_t total = off[count];
-  for (int64_t v = blockIdx.x; v < total; v += gridDim.x) {
-    const int i = find_instance(off, count, v);
+template <typename T, int F>
+__global__ void __launch_bounds__(256, 4) k_b_encode_horizontal(const BatchInst<T>* __restrict__ inst,
+                                                              int count, const T* __restrict__ Gh) {
+  for (int i = blockIdx.y; i < count; i += gridDim.y) {
     const BatchInst<T>& I = inst[i];
-    int64_t loc = v - off[i];
-    const int64_t nbx = (I.g.mb + 31) / 32, nby = (I.g.nb + 7) / 8;
-    const int bx = (int)(loc % nbx);
-    loc /= nbx;
-    encode_horizontal_body<T>(I.g, Gh, I.Q, bx, (int)(loc % nby), (int)(loc / nby));
+    if (!I.g.protect_r || I.g.f == 0) continue;
+    const int nbx = (int)((I.g.mb + 31) / 32), nby = (int)((I.g.nb + 7) / 8);
+    const int total = nbx * nby * (I.g.p_r + I.g.f);
+    for (int v = blockIdx.x; v < total; v += gridDim.x) {
+      const int bx = v % nbx, rest = v / nbx;
+      encode_horizontal_f<T, F>(I.g, Gh, I.Q, bx, rest % nby, rest / nby);
+    }
   }
 }
 
-template <typename T>
-cudaError_t launch_b_encode(const BatchInst<T>* inst, int count, const int64_t* off_v,
-                            int64_t total_v, const int64_t* off_h, int64_t total_h,
-                            const T* Gt_t, const T* Gh_t, int num_sms, cudaStream_t st) {
+template <typename T, int F>
+cudaError_t launch_b_encode_f(const BatchInst<T>* inst, int count, int64_t total_v, int64_t total_h,
+                              const T* Gt_t, const T* Gh_t, cudaStream_t st) {
   const dim3 blk(32, 8);
-  const int64_t cap = (int64_t)num_sms * 16;
-  if (total_v > 0) {
-    k_b_encode_vertical<T><<<(unsigned)std::min(total_v, cap), blk, 0, st>>>(inst, count, off_v, Gt_t);
+  const dim3 grd(kBEncX, (unsigned)std::min(count, 65535));
+  if (total_v > 0 && count > 0) {
+    k_b_encode_vertical<T, F><<<grd, blk, 0, st>>>(inst, count, Gt_t);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (total_h > 0) {
-    k_b_encode_horizontal<T><<<(unsigned)std::min(total_h, cap), blk, 0, st>>>(inst, count, off_h, Gh_t);
+  if (total_h > 0 && count > 0) {
+    k_b_encode_horizontal<T, F><<<grd, blk, 0, st>>>(inst, count, Gh_t);
     return cudaGetLastError();
   }
   return cudaSuccess;
+}
+
+// f: the checksum count shared by every instance of the batch
+template <typename T>
+cudaError_t launch_b_encode(const BatchInst<T>* inst, int count, const int64_t* /*off_v*/,
+                            int64_t total_v, const int64_t* /*off_h*/, int64_t total_h,
+                            const T* Gt_t, const T* Gh_t, int f, cudaStream_t st) {
+  switch (f_bucket(f)) {
+    case 0: return launch_b_encode_f<T, 0>(inst, count, total_v, total_h, Gt_t, Gh_t, st);
+    case 1: return launch_b_encode_f<T, 1>(inst, count, total_v, total_h, Gt_t, Gh_t, st);
+    case 2: return launch_b_encode_f<T, 2>(inst, count, total_v, total_h, Gt_t, Gh_t, st);
+    case 3: return launch_b_encode_f<T, 3>(inst, count, total_v, total_h, Gt_t, Gh_t, st);
+    case 4: return launch_b_encode_f<T, 4>(inst, count, total_v, total_h, Gt_t, Gh_t, st);
+    default: return launch_b_encode_f<T, -1>(inst, count, total_v, total_h, Gt_t, Gh_t, st);
+  }
 }
 
 template <typename T>

@@ -160,7 +160,7 @@ int64_t batch_decode_blocks(const Geo& g, const DecodePlan& p);
 template <typename T>
 cudaError_t launch_b_encode(const BatchInst<T>* inst, int count, const int64_t* off_v,
                             int64_t total_v, const int64_t* off_h, int64_t total_h,
-                            const T* Gt_t, const T* Gh_t, int num_sms, cudaStream_t st);
+                            const T* Gt_t, const T* Gh_t, int f, cudaStream_t st);
 template <typename T>
 cudaError_t launch_b_poison(const BatchInst<T>* inst, const BatchTile* tiles, int count,
                             int64_t max_elems, int num_sms, cudaStream_t st);
