@@ -147,6 +147,10 @@ cqr_status enqueue_factor(cqr_batched bh, const int* d_range, int queue_slot,
   L.queue = bh->d_queue + queue_slot;
   L.tau2 = bh->tau2;
   L.panel_cap = bh->panel_cap;
+  L.tiles = bh->d_tiles;
+  L.plans = bh->d_plans;
+  L.Gt = bh->d_Gt;
+  L.Gh = bh->d_Gh;
   BK(launch_b_factor(L, bh->st));
   return CQR_OK;
 }
@@ -222,6 +226,7 @@ cqr_status check_inputs(cqr_batched bh, const void* const* A, const int64_t* lda
   for (int i = 0; i < bh->count; ++i) {
     bh->h_inst[i].A = static_cast<const float*>(A[i]);
     bh->h_inst[i].lda = lda[i];
+    bh->h_inst[i].rec_at = 0;  // no recovery inside a factor launch unless a run plans one
   }
   return upload(bh, bh->d_inst, bh->h_inst.data(), sizeof(BatchInst<float>) * bh->count);
 }
@@ -578,6 +583,38 @@ cqr_status coded_qr_batched_run(cqr_batched bh, const void* const* A, const int6
       return s;
     }
   }
+  // Recovery inside the factor launch when the coefficient tables fit the panel pool: every
+  // instance runs all its panels in one launch and its cluster poisons and decodes its own
+  // tiles at the start of its erasure panel (no second launch waiting for the slowest
+  // instance of the first).  Tiles and plans are grouped by instance.
+  const bool fused = !list.empty() && bh->panel_cap >= b_recover_floats();
+  if (fused) {
+    std::stable_sort(list.begin(), list.end(),
+                     [](const BatchTile& x, const BatchTile& y) { return x.inst < y.inst; });
+    for (int k = 0; k < bh->count; ++k) {
+      BatchInst<float>& I = bh->h_inst[k];
+      I.rec_at = 0;
+      I.tile0 = I.ntiles = I.plan0 = I.nplans = 0;
+    }
+    for (int e = 0; e < (int)list.size(); ++e) {
+      BatchInst<float>& I = bh->h_inst[list[e].inst];
+      if (I.ntiles == 0) I.tile0 = e;
+      ++I.ntiles;
+    }
+    for (int e = 0; e < (int)plans.size(); ++e) {
+      BatchInst<float>& I = bh->h_inst[plans[e].inst];
+      if (I.nplans == 0) I.plan0 = e;
+      ++I.nplans;
+    }
+    for (int k = 0; k < bh->count; ++k) {
+      BatchInst<float>& I = bh->h_inst[k];
+      if (t_of[k] >= 0 && (I.ntiles > 0 || I.nplans > 0)) I.rec_at = t_of[k] + 1;
+      ra[2 * k] = 0;
+      ra[2 * k + 1] = bh->geo[k].panels;
+    }
+    s = upload(bh, bh->d_inst, bh->h_inst.data(), sizeof(BatchInst<float>) * bh->count);
+    if (s != CQR_OK) return s;
+  }
   // work order of each factor phase: decreasing work of that phase (longest first), the work
   // of panel t being M bk (N - t b) (its panel and its trailing update)
   std::vector<int> ord(2 * bh->count);
@@ -598,6 +635,7 @@ cqr_status coded_qr_batched_run(cqr_batched bh, const void* const* A, const int6
   }
   std::vector<int64_t> key;
   key.push_back(flags);
+  key.push_back(fused ? 1 : 0);
   for (int e = 0; e < 4 * count; ++e) key.push_back(erasures[e]);
   for (int k = 0; k < bh->count; ++k) {
     key.push_back(reinterpret_cast<int64_t>(A[k]));
@@ -615,6 +653,13 @@ cqr_status coded_qr_batched_run(cqr_batched bh, const void* const* A, const int6
   }
   auto sequence = [&]() -> cqr_status {
     cqr_status r = enqueue_encode(bh);
+    if (fused) {
+      if (r == CQR_OK) r = enqueue_factor(bh, bh->d_range_a, 0, bh->d_order);
+      if (r == CQR_OK && (flags & CQR_BATCH_POST_ORTH))
+        BK(launch_b_post_orth<float>(bh->d_inst, bh->count, bh->d_off_p, bh->tot_p, bh->d_Gt_t,
+                                     bh->num_sms, bh->st));
+      return r;
+    }
     if (r == CQR_OK) r = enqueue_factor(bh, bh->d_range_a, 0, bh->d_order_ab);
     if (r == CQR_OK && !list.empty()) {
       BK(launch_b_poison<float>(bh->d_inst, bh->d_tiles, (int)list.size(), bh->max_tile_elems,

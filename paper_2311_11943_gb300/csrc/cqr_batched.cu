@@ -24,6 +24,7 @@
 #include <algorithm>
 
 #include "cqr_batched.cuh"
+#include "cqr_decode.cuh"
 #include "cqr_device.cuh"
 
 namespace cqr {
@@ -562,11 +563,48 @@ __device__ void b_update(BCtx<G>& c, const float* P, int64_t cs, int nr, int bk,
   __syncthreads();
 }
 
+// In-launch recovery of one instance (a6 + a7) by its cluster, at the start of its erasure
+// panel: the listed tiles are poisoned (NaN), then every code with lost tiles is decoded.  The
+// coefficient tables go in the panel pool, which is free between panels.  Cluster barriers
+// order the poisoning before the decode and the decode before the next panel.
+template <int G>
+__device__ void b_recover(BCtx<G>& c, const BatchInst<float>& I, const BatchTile* __restrict__ tiles,
+                          const BatchPlan* __restrict__ plans, const double* __restrict__ Gt,
+                          const double* __restrict__ Gh) {
+  const Geo& g = I.g;
+  for (int e = I.tile0; e < I.tile0 + I.ntiles; ++e) {
+    const BatchTile t = tiles[e];
+    float* X = t.isR ? I.R : I.Q;
+    const int64_t ld = t.isR ? g.ldr : g.ldq;
+    const int64_t th = t.isR ? g.nb : g.mb, tw = g.nb;
+    for (int64_t idx = (int64_t)c.rank * kBT + c.tid; idx < th * tw; idx += (int64_t)G * kBT) {
+      const int64_t r = idx % th, s = idx / th;
+      X[(int64_t)t.i * th + r + ((int64_t)t.j * tw + s) * ld] = nan_value<float>();
+    }
+  }
+  if (G > 1) cl_sync(); else __syncthreads();
+  DecodeScratch<float>& sh = *reinterpret_cast<DecodeScratch<float>*>(c.sm + ((c.L.pool + 3) & ~3));
+  for (int pi = I.plan0; pi < I.plan0 + I.nplans; ++pi) {
+    const DecodePlan& p = plans[pi].p;
+    if (decode_setup<float>(g, p, Gt, Gh, sh, c.tid, kBT, I.status, c.rank == 0)) {
+      const int64_t h = p.kind == 0 ? g.mb : g.nb;
+      for (int64_t e = (int64_t)c.rank * kBT + c.tid; e < h * g.nb; e += (int64_t)G * kBT)
+        decode_apply<float>(g, p, sh, I.Q, I.R, e % h, e / h);
+    }
+    __syncthreads();  // the next code's setup overwrites the tables
+  }
+  if (G > 1) cl_sync(); else __syncthreads();
+}
+
 template <int G>
 __global__ void __launch_bounds__(kBT, 1) k_b_factor(BatchInst<float>* __restrict__ inst, int count,
                                                      const int* __restrict__ order,
                                                      const int* __restrict__ range, int* queue,
-                                                     double tau2, int panel_cap) {
+                                                     double tau2, int panel_cap,
+                                                     const BatchTile* __restrict__ tiles,
+                                                     const BatchPlan* __restrict__ plans,
+                                                     const double* __restrict__ Gt,
+                                                     const double* __restrict__ Gh) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int s_item;
   BCtx<G> c;
@@ -601,6 +639,7 @@ __global__ void __launch_bounds__(kBT, 1) k_b_factor(BatchInst<float>* __restric
     float* Qs = I.Q + row0;
     bool ok = true;
     for (int k = pb; k < pe && ok; ++k) {
+      if (k == I.rec_at - 1) b_recover<G>(c, I, tiles, plans, Gt, Gh);
       const int kb = k * I.b;
       const int bk = (int)std::min<int64_t>(I.b, g.n - kb);
       // ICGS on the panel slice: in the shared-memory pool (after the panel's scratch) when it
@@ -654,7 +693,7 @@ cudaError_t launch_g(const BFactorLaunch& L, cudaStream_t st) {
   cfg.attrs = attr;
   cfg.numAttrs = G > 1 ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, fn, L.inst, L.count, L.order, L.range, L.queue, L.tau2,
-                            L.panel_cap);
+                            L.panel_cap, L.tiles, L.plans, L.Gt, L.Gh);
 }
 
 template <int G>
@@ -686,6 +725,8 @@ int max_clusters_g(int panel_cap) {
 }
 
 }  // namespace
+
+int b_recover_floats() { return (int)((sizeof(DecodeScratch<float>) + sizeof(float) - 1) / sizeof(float)) + 4; }
 
 int b_panel_cap_floats(int G) {
   const size_t cap = 227 * 1024 / sizeof(float) - 64;  // static shared and alignment slack

@@ -20,10 +20,18 @@ struct BFactorLaunch {
   int* queue;               // device counter, zero before the launch
   double tau2;              // ICGS test constant squared (0: no reorthogonalisation)
   int panel_cap;            // floats of shared memory for the panel slice
+  // recovery inside the launch (instances with rec_at > 0): poisoned-tile list, decode plans,
+  // FP64 generator blocks
+  const BatchTile* tiles = nullptr;
+  const BatchPlan* plans = nullptr;
+  const double* Gt = nullptr;
+  const double* Gh = nullptr;
 };
 
 // Shared-memory floats left for the panel slice when the CTAs form clusters of G.
 int b_panel_cap_floats(int G);
+// Shared-memory floats the in-launch recovery needs (its tables reuse the panel pool).
+int b_recover_floats();
 // Clusters of G CTAs that can be resident at once (0 if the configuration cannot launch).
 // Also sets the kernel's shared-memory attribute, which launch_b_factor relies on (so that a
 // launch can be recorded into a CUDA graph without further attribute calls).

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 
+#include "cqr_decode.cuh"
 #include "cqr_device.cuh"
 #include "cqr_kernels.cuh"
 
@@ -395,113 +396,23 @@ cudaError_t launch_poison(const Geo& g, const int* tiles, int count, T* Q, T* R,
 }
 
 // ===================================================================== a7 decode
-// Recovery Lemma (Appendix, Eq. (A_recov)), second form: each lost systematic tile is a
-// linear combination of the surviving systematic tiles and the used checksum tiles, with
-// coefficients from G^-1 (FP64 Gauss-Jordan with partial pivoting on the device, one thread
-// per CTA).  Lost checksum tiles are re-encoded from the systematic tiles (surviving and
-// rebuilt).  One CTA column per plan; the same kernel serves the vertical code of a Q grid
-// column (tile index along rows) and the horizontal code of an R block row (along columns).
+// The decode itself (setup of a code's coefficient tables, recovery of one position) is in
+// cqr_decode.cuh; here one CTA of 32 x 8 threads recovers a 32-row x 8-column block of
+// positions of one code.
 template <typename T>
 __device__ __forceinline__ void decode_body(const Geo& g, const DecodePlan& p,
                                             const double* __restrict__ Gt,
                                             const double* __restrict__ Gh, T* Q, T* R,
                                             int* status, int bx, int by) {
-  const bool isQ = (p.kind == 0);
-  const int nsys = p.nsys, f = g.f, f1 = p.f1, f2 = p.f2;
-  __shared__ double Ginv[kMaxF * kMaxF];
-  __shared__ T coef[kMaxF][kMaxCode];   // lost systematic b <- code tile t (nsys + f columns)
-  __shared__ T cenc[kMaxF][kMaxCode];   // lost checksum e <- systematic tile t
-  __shared__ int lost[kMaxCode];
-  __shared__ int s_bad;
-  __shared__ double a[kMaxF][2 * kMaxF];  // Gauss-Jordan tableau [G^ | I]
+  __shared__ DecodeScratch<T> sh;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  auto gen = [&](int i, int t) -> double { return isQ ? Gt[i * g.p_r + t] : Gh[t * f + i]; };
-  if (tid == 0) {
-    s_bad = 0;
-    for (int t = 0; t < nsys + f; ++t) lost[t] = 0;
-    for (int b = 0; b < f1; ++b) lost[p.A_fail[b]] = 1;
-    for (int e = 0; e < f2; ++e) lost[nsys + p.C_fail[e]] = 1;
-    // G^ = G~[C_use, A_fail]; invert by Gauss-Jordan (Golub & Van Loan 3.4), FP64
-    for (int r = 0; r < f1; ++r)
-      for (int q = 0; q < 2 * f1; ++q)
-        a[r][q] = (q < f1) ? gen(p.C_use[r], p.A_fail[q]) : (q - f1 == r ? 1.0 : 0.0);
-    for (int col = 0; col < f1 && !s_bad; ++col) {
-      int piv = col;
-      for (int r = col + 1; r < f1; ++r)
-        if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
-      if (!(fabs(a[piv][col]) > 0.0)) { s_bad = 1; break; }
-      if (piv != col)
-        for (int q = 0; q < 2 * f1; ++q) { double t = a[col][q]; a[col][q] = a[piv][q]; a[piv][q] = t; }
-      const double pv = a[col][col];
-      for (int q = 0; q < 2 * f1; ++q) a[col][q] = a[col][q] / pv;
-      for (int r = 0; r < f1; ++r) {
-        if (r == col) continue;
-        const double fc = a[r][col];
-        if (fc != 0.0)
-          for (int q = 0; q < 2 * f1; ++q) a[r][q] -= fc * a[col][q];
-      }
-    }
-    for (int r = 0; r < f1; ++r)
-      for (int q = 0; q < f1; ++q) Ginv[r * kMaxF + q] = a[r][f1 + q];
-    if (s_bad && bx == 0 && by == 0) set_status(status, CQR_EUNRECOVERABLE, p.idx);
-  }
-  __syncthreads();
-  if (s_bad) return;
-  for (int idx = tid; idx < f1 * (nsys + f); idx += blockDim.x * blockDim.y) {
-    const int b = idx / (nsys + f), t = idx % (nsys + f);
-    double cv = 0.0;
-    if (t < nsys) {
-      if (!lost[t])
-        for (int a = 0; a < f1; ++a) cv -= Ginv[b * kMaxF + a] * gen(p.C_use[a], t);
-    } else {
-      for (int a = 0; a < f1; ++a)
-        if (p.C_use[a] == t - nsys) cv = Ginv[b * kMaxF + a];
-    }
-    coef[b][t] = (T)cv;
-  }
-  for (int idx = tid; idx < f2 * nsys; idx += blockDim.x * blockDim.y) {
-    const int e = idx / nsys, t = idx % nsys;
-    cenc[e][t] = (T)gen(p.C_fail[e], t);
-  }
-  __syncthreads();
-  const int64_t h = isQ ? g.mb : g.nb;
+  if (!decode_setup<T>(g, p, Gt, Gh, sh, tid, blockDim.x * blockDim.y, status, bx == 0 && by == 0))
+    return;
+  const int64_t h = p.kind == 0 ? g.mb : g.nb;
   const int64_t r = (int64_t)bx * blockDim.x + threadIdx.x;
   const int64_t s = (int64_t)by * blockDim.y + threadIdx.y;
   if (r >= h || s >= g.nb) return;
-  T* base = isQ ? Q + (int64_t)p.idx * g.nb * g.ldq : R + (int64_t)p.idx * g.nb;
-  const int64_t tstride = isQ ? g.mb : g.nb * g.ldr;
-  const int64_t ld = isQ ? g.ldq : g.ldr;
-  T* ptr = base + r + s * ld;
-  T xb[kMaxF], ce[kMaxF];
-#pragma unroll
-  for (int k = 0; k < kMaxF; ++k) { xb[k] = T(0); ce[k] = T(0); }
-  for (int t = 0; t < nsys + f; ++t) {
-    if (lost[t]) continue;
-    bool used = (t < nsys);
-    if (!used)
-      for (int a = 0; a < f1; ++a) used |= (p.C_use[a] == t - nsys);
-    if (!used) continue;
-    const T val = ptr[(int64_t)t * tstride];
-#pragma unroll
-    for (int b = 0; b < kMaxF; ++b)
-      if (b < f1) xb[b] += coef[b][t] * val;
-    if (t < nsys) {
-#pragma unroll
-      for (int e = 0; e < kMaxF; ++e)
-        if (e < f2) ce[e] += cenc[e][t] * val;
-    }
-  }
-#pragma unroll
-  for (int b = 0; b < kMaxF; ++b)
-    if (b < f1) {
-      ptr[(int64_t)p.A_fail[b] * tstride] = xb[b];
-#pragma unroll
-      for (int e = 0; e < kMaxF; ++e)
-        if (e < f2) ce[e] += cenc[e][p.A_fail[b]] * xb[b];
-    }
-#pragma unroll
-  for (int e = 0; e < kMaxF; ++e)
-    if (e < f2) ptr[(int64_t)(nsys + p.C_fail[e]) * tstride] = ce[e];
+  decode_apply<T>(g, p, sh, Q, R, r, s);
 }
 
 template <typename T>

@@ -139,7 +139,12 @@ struct BatchInst {
   int64_t lda;
   int* status;      // this instance's status words
   int b;            // panel width
-  int pad_;
+  // recovery inside the batched factor launch: at the start of panel rec_at - 1 (0: none),
+  // the tiles [tile0, tile0 + ntiles) of the poisoned-tile list are poisoned and the codes
+  // [plan0, plan0 + nplans) of the decode-plan list decoded
+  int rec_at;
+  int tile0, ntiles;
+  int plan0, nplans;
 };
 
 struct BatchPlan {

@@ -75,8 +75,9 @@ def rel(a, b):
 
 # ----------------------------------------------------------------- a1 / a2
 @pytest.mark.parametrize("f,p_r,p_c,gdist", [(1, 4, 4, 0), (2, 8, 8, 0), (4, 16, 16, 0),
-                                             (3, 6, 8, 1)])
+                                             (3, 6, 8, 1), (6, 12, 12, 0)])
 def test_generator_and_encode(f, p_r, p_c, gdist):
+    # f = 6: the encode kernels' generic path (checksum counts above 4)
     m, n = 4 * p_r + 3, 2 * p_c
     A = synth.gaussian(m, n, 11)
     q = B.CodedQR(m, n, p_r, p_c, f, 4, dtype="f64", gdist=gdist, seed=1234 + f)
