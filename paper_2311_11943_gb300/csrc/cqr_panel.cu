@@ -623,12 +623,18 @@ PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_clu
         best_cl = true;
         break;
       }
+  // grid of CTAs with shared-memory slices: the largest slices that fit, so the fewest CTAs
+  // (a cheaper grid barrier, and more independent panels resident at once; at 9216 x 128 the
+  // per-column time is flat in the slice height while 16 concurrent problems run 3x faster
+  // with 24 CTAs each than with 72)
   if (best < 0)
-    for (int r : kRpl)
+    for (int q = (int)(sizeof(kRpl) / sizeof(kRpl[0])) - 1; q >= 0; --q) {
+      const int r = kRpl[q];
       if ((rpl_env == 0 || r == rpl_env) && fits(r, false) && (M + 32 * r - 1) / (32 * r) <= num_sms) {
         best = r;
         break;
       }
+    }
   if (best > 0) {
     p.smem = 1;
     p.cluster = best_cl ? 1 : 0;
