@@ -1147,24 +1147,58 @@ cqr_status adjoint_qr_t(cqr_handle h, const T* Q, int64_t ldq, const T* Qbar, in
   const Geo& g = h->g;
   const int64_t n = g.n, mp = g.m_pad;
   const size_t nn = (size_t)n * n;
-  cqr_status s = adj_scratch(h, sizeof(T) * (2 * nn + (size_t)mp * n));
+  // FP32 handles with tensor cores take the two large products (n x n x m_pad and m_pad x n
+  // x n) in 3xTF32 through the operand planes; the rest, and FP64, on the CUDA cores
+  bool tcq = false;
+  if constexpr (sizeof(T) == 4) tcq = h->tc != nullptr;
+  const size_t base_el = (2 * nn + (size_t)mp * n + 63) / 64 * 64;
+  const size_t plane_el = tcq ? std::max(tc_gemm_sub_planes(true, n, mp), tc_gemm_sub_planes(false, mp, n)) : 0;
+  cqr_status s = adj_scratch(h, sizeof(T) * (base_el + plane_el));
   if (s != CQR_OK) return s;
   T* Mm = static_cast<T*>(h->adj);
   T* S = Mm + nn;
   T* Bb = S + nn;
+  float* planes = reinterpret_cast<float*>(Mm + base_el);
   const T* R = ptr<T>(h->B.R);
+  // C -= op(A) B on the tensor cores; false when the operands break a tensor-map rule
+  auto tc_sub = [&](bool a_trans, const T* A_, int64_t lda_, const T* B_, int64_t ldb_, T* C_,
+                    int64_t ldc_, int64_t M_, int64_t N_, int64_t K_) -> int {
+    if (!tcq) return 0;
+    const cudaError_t e = tc_gemm_sub3(a_trans, reinterpret_cast<const float*>(A_), lda_,
+                                       reinterpret_cast<const float*>(B_), ldb_,
+                                       reinterpret_cast<float*>(C_), ldc_, M_, N_, K_, planes,
+                                       h->num_sms, h->B.status, h->st);
+    if (e == cudaSuccess) return 1;
+    cudaGetLastError();
+    return e == cudaErrorInvalidValue ? 0 : -1;
+  };
   // M = R Rbar^T - Qbar^T Q
   if (Rbar)
     CK(launch_gemm_general<T>(0, 1, n, n, n, T(1), R, g.ldr, Rbar, ldrb, T(0), Mm, n, h->st));
   else
     CK(cudaMemsetAsync(Mm, 0, sizeof(T) * nn, h->st));
-  if (Qbar)
-    CK(launch_gemm_general<T>(1, 0, n, n, mp, T(-1), Qbar, ldqb, Q, ldq, T(1), Mm, n, h->st));
+  if (Qbar) {
+    const int r = tc_sub(true, Qbar, ldqb, Q, ldq, Mm, n, n, n, mp);
+    if (r < 0) return CQR_ECUDA;
+    if (r == 0)
+      CK(launch_gemm_general<T>(1, 0, n, n, mp, T(-1), Qbar, ldqb, Q, ldq, T(1), Mm, n, h->st));
+  }
   CK(launch_copyltu<T>(Mm, n, S, h->st));
   // Bbar = Qbar + Q copyltu(M), then Bbar R^{-T}
   if (Qbar)
     CK(launch_axpy2d<T>(mp, n, T(1), Qbar, 1, ldqb, Bb, 1, mp, true, h->st));
-  CK(launch_gemm_general<T>(0, 0, mp, n, n, T(1), Q, ldq, S, n, Qbar ? T(1) : T(0), Bb, mp, h->st));
+  else
+    CK(cudaMemsetAsync(Bb, 0, sizeof(T) * (size_t)mp * n, h->st));
+  int r3 = 0;
+  if (tcq) {
+    // Bbar -= Q (-S)
+    CK(launch_axpy2d<T>(n, n, T(-1), S, 1, n, S, 1, n, true, h->st));
+    r3 = tc_sub(false, Q, ldq, S, n, Bb, mp, mp, n, n);
+    if (r3 < 0) return CQR_ECUDA;
+    if (r3 == 0) CK(launch_axpy2d<T>(n, n, T(-1), S, 1, n, S, 1, n, true, h->st));  // S back
+  }
+  if (r3 == 0)
+    CK(launch_gemm_general<T>(0, 0, mp, n, n, T(1), Q, ldq, S, n, T(1), Bb, mp, h->st));
   CK(launch_trsm_right<T>(1, R, g.ldr, n, Bb, 1, mp, mp, h->st));
   // Abar += G_0^T Bbar (G_0 is symmetric: its leading block I - V V^T / 2 is), rows < m
   if (g.f > 0) CK(launch_post_orth<T>(g, ptr<T>(h->B.Gt_t), Bb, mp, mp, n, Bb, mp, h->st));

@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(256) k_split_panel(const float* __restrict__ Q
     const int64_t rr = r0 + ty + 8 * i;
     if (rr >= M) continue;
     const P h = sh[tx][ty + 8 * i], l = sl[tx][ty + 8 * i];
-    if (k < bkp) {
+    if (At_hi && k < bkp) {
       At_hi[rr * bkp + k] = h;
       if (nplanes == 2) At_lo[rr * bkp + k] = l;
     }
@@ -1076,6 +1076,70 @@ cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr
   const bool pdl = st == t->pdl_st && st != nullptr;
   return launch_k(k_tc_sub_partials, dim3(blocks), dim3(256), 0, st, pdl, (const float*)t->P[0], splits2,
                   t->M, (int64_t)bk, t->Q + kb * t->ldq, t->ldq);
+}
+
+// General C -= op(A) B in 3xTF32 on the tensor cores (the large products of the reverse mode).
+// op(A) is A^T (A: K x M column-major) when a_trans, else A (M x K column-major); B is K x N
+// column-major, C is M x N column-major.  A goes through the operand split into hi / lo
+// planes (K-major: column-major for A^T, row-major for A); B is loaded raw and split in shared
+// memory.  One CTA per 128 x 128 output tile (at most the SMs, persistent), no split over K.
+// Returns cudaErrorInvalidValue (nothing launched) when a tensor-map rule is not met: B and C
+// 16-byte aligned, ldb a multiple of 4.
+size_t tc_gemm_sub_planes(bool a_trans, int64_t M, int64_t K) {
+  return a_trans ? 2 * (size_t)round_to(K, 32) * (size_t)M : 2 * (size_t)M * (size_t)round_to(K, 32);
+}
+
+cudaError_t tc_gemm_sub3(bool a_trans, const float* A, int64_t lda, const float* B, int64_t ldb,
+                         float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float* planes,
+                         int num_sms, int* status, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  if ((reinterpret_cast<uintptr_t>(B) & 15) || (ldb % 4) || (reinterpret_cast<uintptr_t>(planes) & 15))
+    return cudaErrorInvalidValue;
+  const int64_t kp = round_to(K, 32);
+  float* hi = planes;
+  TcMaps maps;
+  bool ok = true;
+  if (a_trans) {
+    // planes of A (K x M): column-major, ld kp; rows of op(A) are columns of A
+    float* lo = hi + kp * M;
+    const dim3 grd((unsigned)((K + 31) / 32), (unsigned)((M + 31) / 32));
+    k_split_panel<float><<<grd, 256, 0, st>>>(A, lda, K, (int)M, 0, (int)M, 2, hi, lo, kp, nullptr,
+                                              nullptr, nullptr, nullptr, 0, 0);
+    ok &= encode_2d(&maps.a[0], hi, false, (uint64_t)K, (uint64_t)M, (uint64_t)kp * 4, 32, BM);
+    ok &= encode_2d(&maps.a[1], lo, false, (uint64_t)K, (uint64_t)M, (uint64_t)kp * 4, 32, BM);
+  } else {
+    // planes of A (M x K): row-major, row stride kp
+    float* lo = hi + M * kp;
+    const dim3 grd((unsigned)((M + 31) / 32), (unsigned)((kp + 31) / 32));
+    k_split_panel<float><<<grd, 256, 0, st>>>(A, lda, M, (int)K, (int)kp, 0, 2, nullptr, nullptr, 0, hi,
+                                              lo, nullptr, nullptr, 0, 0);
+    ok &= encode_2d(&maps.a[0], hi, false, (uint64_t)kp, (uint64_t)M, (uint64_t)kp * 4, 32, BM);
+    ok &= encode_2d(&maps.a[1], lo, false, (uint64_t)kp, (uint64_t)M, (uint64_t)kp * 4, 32, BM);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ok &= encode_2d(&maps.b[0], const_cast<float*>(B), false, (uint64_t)K, (uint64_t)N, (uint64_t)ldb * 4, 32, BN);
+  maps.b[1] = maps.b[0];
+  if (!ok) return cudaErrorInvalidValue;
+  TcJob job{};
+  job.nprod = 3;
+  job.split_b_smem = 1;
+  job.epi = 1;
+  job.m_tiles = (int)((M + BM - 1) / BM);
+  job.n_tiles = (int)((N + BN - 1) / BN);
+  job.splits = 1;
+  job.a_row0 = 0;
+  job.b_row0 = 0;
+  job.k0 = 0;
+  job.kchunk = kp;
+  job.K = K;
+  job.mrows = M;
+  job.ncols = N;
+  job.out = C;
+  job.ldo = ldc;
+  job.split_stride = 0;
+  job.status = status;
+  return launch_gemm<false, 3, 2, 2>(maps, job, num_sms, st, false);
 }
 
 }  // namespace cqr

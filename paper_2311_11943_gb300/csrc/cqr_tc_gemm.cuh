@@ -42,4 +42,13 @@ cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr
                             cudaStream_t st, int* launches);
 cudaError_t tc_refresh_rows(TcGemm* t, int64_t ncols, cudaStream_t st);
 
+// General C -= op(A) B in 3xTF32 (op(A) = A^T for a_trans with A K x M, else A M x K; B K x N;
+// all column-major).  planes: tc_gemm_sub_planes(a_trans, M, K) floats of scratch, 16-byte
+// aligned.  cudaErrorInvalidValue, with nothing launched, when B is not 16-byte aligned or
+// ldb is not a multiple of 4 (the tensor-map rules).
+size_t tc_gemm_sub_planes(bool a_trans, int64_t M, int64_t K);
+cudaError_t tc_gemm_sub3(bool a_trans, const float* A, int64_t lda, const float* B, int64_t ldb,
+                         float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float* planes,
+                         int num_sms, int* status, cudaStream_t st);
+
 }  // namespace cqr
