@@ -150,7 +150,17 @@ cqr_status coded_qr_encode(cqr_handle h, const void* A, int64_t lda);
  * encoded matrix: ICGS on each panel (Algorithm CGS plus the reorthogonalisation of ICGS),
  * Rbar = Qbar^T Q[:, i+b : N], Q[:, i+b : N] -= Qbar Rbar, Rbar stored into R.
  * panel_begin must equal the next unfactored panel; panel_end = -1 means the last panel.
- * Returns CQR_ESTATE while erasures are pending (erased tiles hold NaN). */
+ * Returns CQR_ESTATE while erasures are pending (erased tiles hold NaN).
+ *
+ * Scheduling (FP32 tensor-core handles whose panel runs on one thread-block cluster): the
+ * trailing update of each panel is split into the next panel's columns, on an internal
+ * stream of the highest priority, and the rest, on an internal stream of the lowest
+ * priority that overlaps the next panel's factorisation; kernels on the first stream use
+ * programmatic dependent launch.  Both streams fork from and join into cfg.stream inside the
+ * call.  Environment switches, for comparisons only: CQR_LOOKAHEAD=0 (one stream, no
+ * split), CQR_PDL=0 (no programmatic dependent launch), CQR_PANEL_REG=0 (no register-
+ * resident panel kernel), CQR_PANEL_CLUSTER=0 (no single-cluster panel kernels),
+ * CQR_PANEL_RPL=r (rows per lane of the shared-memory / grid panel kernels). */
 cqr_status coded_qr_factor(cqr_handle h, int32_t panel_begin, int32_t panel_end);
 
 /* a6.  Fail-stop erasure of nodes (Section 2 "Failure model"): tiles (host) holds `count`
