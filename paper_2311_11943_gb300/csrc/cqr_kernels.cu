@@ -441,54 +441,68 @@ cudaError_t launch_decode(const Geo& g, const DecodePlan* plans_dev, int nplans,
 //   W_i = sum_{l<f} g~_{l,i} Z_l - Z_i                      (i >= f)
 // One thread per (local row, column): reads each Z_t once, writes each W_i once (in place
 // is safe: every thread owns one position across all block rows).
-template <typename T>
-__device__ __forceinline__ void post_orth_body(const Geo& g, const T* __restrict__ Gt, const T* Z,
-                                               int64_t ldz, int64_t zrows, int64_t k, T* W,
-                                               int64_t ldw, int bx, int by) {
+// F checksums known at compile time (F <= 4; -1: generic up to kMaxF), eight tile loads in
+// flight per chunk of the t loop; the order of every sum is unchanged.  W may alias Z: each
+// position is read before it is written.
+template <typename T, int F>
+__device__ __forceinline__ void post_orth_f(const Geo& g, const T* __restrict__ Gt, const T* Z,
+                                            int64_t ldz, int64_t zrows, int64_t k, T* W,
+                                            int64_t ldw, int bx, int by) {
+  constexpr int NA = F > 0 ? F : (F == 0 ? 1 : kMaxF);
   const int64_t s = (int64_t)bx * 32 + threadIdx.x;
   const int64_t col = (int64_t)by * 8 + threadIdx.y;
-  if (s >= g.mb || col >= k) return;
-  const int f = g.f, p_r = g.p_r;
+  const int64_t mb = g.mb;
+  if (s >= mb || col >= k) return;
+  const int f = F >= 0 ? F : g.f, p_r = g.p_r;
   const T* zc = Z + col * ldz;
   T* wc = W + col * ldw;
-  T zl[kMaxF], acc[kMaxF];
+  T zl[NA], acc[NA];
 #pragma unroll
-  for (int l = 0; l < kMaxF; ++l) {
-    const int64_t row = (int64_t)l * g.mb + s;
+  for (int l = 0; l < NA; ++l) {
+    const int64_t row = (int64_t)l * mb + s;
     zl[l] = (l < f && row < zrows) ? zc[row] : T(0);
   }
 #pragma unroll
-  for (int i = 0; i < kMaxF; ++i) {
+  for (int i = 0; i < NA; ++i) {
     T a = T(0);
     if (i < f) {
 #pragma unroll
-      for (int l = 0; l < kMaxF; ++l)
+      for (int l = 0; l < NA; ++l)
         if (l < f) a += ((l == i ? T(1) : T(0)) + Gt[i * p_r + l]) * zl[l];
     }
     acc[i] = a;
   }
-  for (int t = f; t < p_r; ++t) {
-    const int64_t row = (int64_t)t * g.mb + s;
-    const T z = row < zrows ? zc[row] : T(0);
+  for (int t0 = f; t0 < p_r; t0 += 8) {
+    T z[8];
 #pragma unroll
-    for (int i = 0; i < kMaxF; ++i)
-      if (i < f) acc[i] += Gt[i * p_r + t] * z;
-    T wv = T(0);
+    for (int u = 0; u < 8; ++u) {
+      const int64_t row = (int64_t)(t0 + u) * mb + s;
+      z[u] = (t0 + u < p_r && row < zrows) ? zc[row] : T(0);
+    }
 #pragma unroll
-    for (int l = 0; l < kMaxF; ++l)
-      if (l < f) wv += Gt[l * p_r + t] * zl[l];
-    wc[row] = wv - z;
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u;
+      if (t >= p_r) break;
+#pragma unroll
+      for (int i = 0; i < NA; ++i)
+        if (i < f) acc[i] += Gt[i * p_r + t] * z[u];
+      T wv = T(0);
+#pragma unroll
+      for (int l = 0; l < NA; ++l)
+        if (l < f) wv += Gt[l * p_r + t] * zl[l];
+      wc[(int64_t)t * mb + s] = wv - z[u];
+    }
   }
 #pragma unroll
-  for (int i = 0; i < kMaxF; ++i)
-    if (i < f) wc[(int64_t)i * g.mb + s] = acc[i];
+  for (int i = 0; i < NA; ++i)
+    if (i < f) wc[(int64_t)i * mb + s] = acc[i];
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_post_orth(Geo g, const T* __restrict__ Gt, const T* Z,
-                                                    int64_t ldz, int64_t zrows, int64_t k, T* W,
-                                                    int64_t ldw) {
-  post_orth_body<T>(g, Gt, Z, ldz, zrows, k, W, ldw, blockIdx.x, blockIdx.y);
+template <typename T, int F>
+__global__ void __launch_bounds__(256, 4) k_post_orth(Geo g, const T* __restrict__ Gt, const T* Z,
+                                                       int64_t ldz, int64_t zrows, int64_t k, T* W,
+                                                       int64_t ldw) {
+  post_orth_f<T, F>(g, Gt, Z, ldz, zrows, k, W, ldw, blockIdx.x, blockIdx.y);
 }
 
 template <typename T>
@@ -496,7 +510,14 @@ cudaError_t launch_post_orth(const Geo& g, const T* Gt_t, const T* Z, int64_t ld
                              int64_t zrows, int64_t k, T* W, int64_t ldw, cudaStream_t st) {
   dim3 blk(32, 8);
   dim3 grd((unsigned)((g.mb + 31) / 32), (unsigned)((k + 7) / 8));
-  k_post_orth<T><<<grd, blk, 0, st>>>(g, Gt_t, Z, ldz, zrows, k, W, ldw);
+  switch (f_bucket(g.f)) {
+    case 0: k_post_orth<T, 0><<<grd, blk, 0, st>>>(g, Gt_t, Z, ldz, zrows, k, W, ldw); break;
+    case 1: k_post_orth<T, 1><<<grd, blk, 0, st>>>(g, Gt_t, Z, ldz, zrows, k, W, ldw); break;
+    case 2: k_post_orth<T, 2><<<grd, blk, 0, st>>>(g, Gt_t, Z, ldz, zrows, k, W, ldw); break;
+    case 3: k_post_orth<T, 3><<<grd, blk, 0, st>>>(g, Gt_t, Z, ldz, zrows, k, W, ldw); break;
+    case 4: k_post_orth<T, 4><<<grd, blk, 0, st>>>(g, Gt_t, Z, ldz, zrows, k, W, ldw); break;
+    default: k_post_orth<T, -1><<<grd, blk, 0, st>>>(g, Gt_t, Z, ldz, zrows, k, W, ldw); break;
+  }
   return cudaGetLastError();
 }
 
@@ -1122,8 +1143,8 @@ __global__ void __launch_bounds__(256) k_b_post_orth(const BatchInst<T>* __restr
     const BatchInst<T>& I = inst[i];
     const int64_t nbx = (I.g.mb + 31) / 32;
     const int64_t loc = v - off[i];
-    post_orth_body<T>(I.g, Gt, I.Q, I.g.ldq, I.g.m_pad, I.g.n, I.Q, I.g.ldq, (int)(loc % nbx),
-                      (int)(loc / nbx));
+    post_orth_f<T, -1>(I.g, Gt, I.Q, I.g.ldq, I.g.m_pad, I.g.n, I.Q, I.g.ldq, (int)(loc % nbx),
+                       (int)(loc / nbx));
   }
 }
 
