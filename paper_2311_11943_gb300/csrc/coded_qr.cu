@@ -716,8 +716,7 @@ cqr_status solve_t(cqr_handle h, const T* y, int64_t ldy, T* x, int64_t ldx, int
       }
     }
     ProfScope ps(h, K_TRSV, nrhs);
-    CK(launch_trsv_upper<T>(ptr<T>(h->B.R), g.ldr, g.n, x, ldx, nrhs, h->B.bar, h->B.status,
-                            h->num_sms, h->st));
+    CK(launch_trsv_upper<T>(ptr<T>(h->B.R), g.ldr, g.n, x, ldx, nrhs, h->st));
     return CQR_OK;
   }
   cqr_status s = post_orth_q<T>(h, nullptr, 0);
@@ -731,8 +730,7 @@ cqr_status solve_t(cqr_handle h, const T* y, int64_t ldy, T* x, int64_t ldx, int
   }
   {
     ProfScope ps(h, K_TRSV, 1);
-    CK(launch_trsv_upper<T>(ptr<T>(h->B.R), g.ldr, g.n, x, ldx, nrhs, h->B.bar, h->B.status,
-                            h->num_sms, h->st));
+    CK(launch_trsv_upper<T>(ptr<T>(h->B.R), g.ldr, g.n, x, ldx, nrhs, h->st));
   }
   return CQR_OK;
 }

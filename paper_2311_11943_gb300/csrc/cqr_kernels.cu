@@ -806,7 +806,7 @@ bool trsv_cluster_fits(int C, size_t smem) {
 
 template <typename T>
 cudaError_t launch_trsv_upper(const T* R, int64_t ldr, int64_t n, T* x, int64_t ldx, int64_t k,
-                              unsigned* /*bar*/, int* /*status*/, int /*num_sms*/, cudaStream_t st) {
+                              cudaStream_t st) {
   if (n <= 0 || k <= 0) return cudaSuccess;
   constexpr size_t kSmemMax = 227 * 1024;
   const int64_t nblk = (n + kTrsvBS - 1) / kTrsvBS;
@@ -1176,7 +1176,7 @@ cudaError_t launch_b_post_orth(const BatchInst<T>* inst, int count, const int64_
   template cudaError_t launch_gemv_t<T>(const T*, int64_t, int64_t, int64_t, const T*, int64_t,  \
                                         int64_t, T*, int64_t, cudaStream_t);                      \
   template cudaError_t launch_trsv_upper<T>(const T*, int64_t, int64_t, T*, int64_t, int64_t,    \
-                                            unsigned*, int*, int, cudaStream_t);                   \
+                                            cudaStream_t);                                         \
   template cudaError_t launch_ls_cg<T>(const T*, int64_t, int64_t, int64_t, int64_t, int64_t,     \
                                        const T*, T*, double*, unsigned*, int*, int, cudaStream_t,  \
                                        const T*);

@@ -95,10 +95,12 @@ template <typename T>
 cudaError_t launch_gemv_t(const T* Qo, int64_t ldq, int64_t rows, int64_t n, const T* y,
                           int64_t ldy, int64_t k, T* z, int64_t ldz, cudaStream_t st);
 
-// In-place back substitution R x = z (R n x n upper), cooperative launch.
+// In-place back substitution R x = z (R n x n upper, k right-hand sides) on one thread-block
+// cluster; cudaErrorInvalidValue when the x blocks do not fit one cluster's shared memory
+// (n above about 300,000 in FP64, 700,000 in FP32).
 template <typename T>
 cudaError_t launch_trsv_upper(const T* R, int64_t ldr, int64_t n, T* x, int64_t ldx, int64_t k,
-                              unsigned* bar, int* status, int num_sms, cudaStream_t st);
+                              cudaStream_t st);
 
 // Tall least squares through the coded factors: x (n, one column) = (I - Q_2^T Q_2)^{-1} Q_1^T y
 // by conjugate gradients in FP64 (cooperative launch); ws holds 7 n + c + 2 #SMs doubles.
