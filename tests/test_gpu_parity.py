@@ -338,6 +338,28 @@ def test_register_and_shared_memory_panels_agree(shape, monkeypatch):
     assert rel(a["R"], ref["R"]) < n * U3X * kap
 
 
+@pytest.mark.parametrize("env", [{"CQR_LOOKAHEAD": "0"}, {"CQR_PDL": "0"}])
+def test_lookahead_and_pdl_change_rounding_only(env, monkeypatch):
+    # the look-ahead (narrow and wide trailing updates on two streams) and programmatic
+    # dependent launch are schedules of the same panels: the factors match the sequential
+    # schedule to rounding (the split-K factors of the two updates differ), with the same
+    # decode sets, erasures injected at a panel start
+    m, n, p_r, p_c, f, b = 1280, 1024, 8, 8, 2, 128
+    A = synth.kappa_matrix(m, n, 1e2, seed=41)
+    er = {3: synth.random_erasures(p_r + f, p_c + f, f, 2, seed=9)}
+    a = gpu_run(A, p_r, p_c, f, b, seed=6, erasures=er, dtype="f32", mma="3xtf32")
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    c = gpu_run(A, p_r, p_c, f, b, seed=6, erasures=er, dtype="f32", mma="3xtf32")
+    assert a["status"] == 0 and c["status"] == 0
+    assert a["sets"] == c["sets"]
+    tol = n * U3X * 1e2
+    assert rel(a["R"], c["R"]) < tol
+    assert rel(a["Qo"], c["Qo"]) < tol
+    ref = O.run(A, p_r, p_c, f, b, seed=6, erasures=er)
+    assert rel(c["R"], ref["R"]) < tol
+
+
 # BF16 operands (tcgen05 kind::f16): one product carries the BF16 rounding 2^-9; the hi/lo
 # split with three products leaves the lo rounding and the dropped lo*lo term, about 2^-17.
 UBF16 = 2.0 ** -8
