@@ -650,8 +650,16 @@ cqr_status recover_t(cqr_handle h, int32_t* n_recovered) {
   }
   (void)nq;
   if (h->tc && tc_has_block_reorth(h->tc) && !plans.empty()) {
-    // the row-major copy of the computed columns is part of the nodes' state: rebuild it
-    CK(tc_refresh_rows(h->tc, std::min<int64_t>((int64_t)h->next_panel * g.b, g.n), h->st));
+    // the row-major copy of the computed columns is part of the nodes' state: rebuild the
+    // recovered Q tiles of it (tile (i, j) holds rows i mb .., columns j nb ..)
+    const int64_t ncols = std::min<int64_t>((int64_t)h->next_panel * g.b, g.n);
+    for (int i = 0; i < g.grid_rows; ++i)
+      for (int j = 0; j < g.grid_cols; ++j) {
+        if (!h->mask[(size_t)i * g.grid_cols + j]) continue;
+        const int64_t c0 = (int64_t)j * g.nb;
+        if (c0 >= ncols) continue;
+        CK(tc_refresh_rect(h->tc, (int64_t)i * g.mb, g.mb, c0, std::min<int64_t>(g.nb, ncols - c0), h->st));
+      }
   }
   std::fill(h->mask.begin(), h->mask.end(), 0);
   h->pending = false;

@@ -573,6 +573,34 @@ __global__ void k_refresh_rows(const float* __restrict__ Q, int64_t ldq, int64_t
   }
 }
 
+// Row-major planes of the rectangle rows [r0, r0 + nr) x columns [c0, c0 + nc) from Q (after a
+// recovery rebuilt those tiles): 32 x 32 tiles through shared memory, coalesced both ways.
+template <typename P>
+__global__ void __launch_bounds__(256) k_refresh_rect(const float* __restrict__ Q, int64_t ldq,
+                                                      int64_t r0, int nr, int64_t c0, int nc,
+                                                      int nplanes, P* __restrict__ Qr_hi,
+                                                      P* __restrict__ Qr_lo, int64_t ldrow) {
+  __shared__ P sh[32][33], sl[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int rb = blockIdx.x * 32, cb = blockIdx.y * 32;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int r = rb + tx, c = cb + ty + 8 * u;
+    P h, l;
+    hilo((r < nr && c < nc) ? Q[r0 + r + (c0 + c) * ldq] : 0.f, nplanes, h, l);
+    sh[ty + 8 * u][tx] = h;
+    sl[ty + 8 * u][tx] = l;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int r = rb + ty + 8 * u, c = cb + tx;
+    if (r >= nr || c >= nc) continue;
+    Qr_hi[(r0 + r) * ldrow + c0 + c] = sh[tx][ty + 8 * u];
+    if (nplanes == 2) Qr_lo[(r0 + r) * ldrow + c0 + c] = sl[tx][ty + 8 * u];
+  }
+}
+
 // Block reorthogonalisation, reduce: the GEMM1 partials hold S^T = Qbar^T Q[:, 0:kb]
 // (P[s][i + j bkp]); R[j, kb+i] += S[j][i] and S (column-major, ld ldrow, rows >= kb zero)
 // goes into the B planes of the second product.  One 32 x 32 tile (i, j) per CTA: the
@@ -900,6 +928,21 @@ cudaError_t tc_refresh_rows(TcGemm* t, int64_t ncols, cudaStream_t st) {
   else
     k_refresh_rows<float><<<blocks, 256, 0, st>>>(t->Q, t->ldq, t->M, ncols, t->nplanes,
                                                   pl<float>(t->Qr_hi), pl<float>(t->Qr_lo), t->ldrow);
+  return cudaGetLastError();
+}
+
+// Row-major planes of one rectangle of Q (rows r0.., columns c0.. below the computed-column
+// count) rebuilt after a recovery changed it.
+cudaError_t tc_refresh_rect(TcGemm* t, int64_t r0, int64_t nr, int64_t c0, int64_t nc, cudaStream_t st) {
+  if (!t->Qr_hi || nr <= 0 || nc <= 0) return cudaSuccess;
+  const dim3 grd((unsigned)((nr + 31) / 32), (unsigned)((nc + 31) / 32));
+  if (t->bf)
+    k_refresh_rect<__nv_bfloat16><<<grd, 256, 0, st>>>(t->Q, t->ldq, r0, (int)nr, c0, (int)nc, t->nplanes,
+                                                      pl<__nv_bfloat16>(t->Qr_hi),
+                                                      pl<__nv_bfloat16>(t->Qr_lo), t->ldrow);
+  else
+    k_refresh_rect<float><<<grd, 256, 0, st>>>(t->Q, t->ldq, r0, (int)nr, c0, (int)nc, t->nplanes,
+                                              pl<float>(t->Qr_hi), pl<float>(t->Qr_lo), t->ldrow);
   return cudaGetLastError();
 }
 
