@@ -557,22 +557,6 @@ __global__ void k_tc_sub_partials(const float* __restrict__ P, int splits, int64
   }
 }
 
-// Row-major planes of the computed columns 0 .. ncols-1 from Q (after a recovery).
-template <typename P>
-__global__ void k_refresh_rows(const float* __restrict__ Q, int64_t ldq, int64_t M, int64_t ncols,
-                               int nplanes, P* __restrict__ Qr_hi, P* __restrict__ Qr_lo,
-                               int64_t ldrow) {
-  const int64_t total = M * ncols;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx % M, c = idx / M;
-    P h, l;
-    hilo(Q[r + c * ldq], nplanes, h, l);
-    Qr_hi[r * ldrow + c] = h;
-    if (nplanes == 2) Qr_lo[r * ldrow + c] = l;
-  }
-}
-
 // Row-major planes of the rectangle rows [r0, r0 + nr) x columns [c0, c0 + nc) from Q (after a
 // recovery rebuilt those tiles): 32 x 32 tiles through shared memory, coalesced both ways.
 template <typename P>
@@ -915,21 +899,6 @@ cudaError_t tc_split_panel(TcGemm* t, int64_t kb, int bk, bool finished, int buf
 }
 
 bool tc_has_block_reorth(const TcGemm* t) { return t->Qr_hi != nullptr; }
-
-// Row-major planes of columns 0 .. ncols-1 rebuilt from Q (after a recovery changed tiles).
-cudaError_t tc_refresh_rows(TcGemm* t, int64_t ncols, cudaStream_t st) {
-  if (!t->Qr_hi || ncols <= 0) return cudaSuccess;
-  const int64_t total = t->M * ncols;
-  const int blocks = (int)std::min<int64_t>(8192, (total + 255) / 256);
-  if (t->bf)
-    k_refresh_rows<__nv_bfloat16><<<blocks, 256, 0, st>>>(t->Q, t->ldq, t->M, ncols, t->nplanes,
-                                                          pl<__nv_bfloat16>(t->Qr_hi),
-                                                          pl<__nv_bfloat16>(t->Qr_lo), t->ldrow);
-  else
-    k_refresh_rows<float><<<blocks, 256, 0, st>>>(t->Q, t->ldq, t->M, ncols, t->nplanes,
-                                                  pl<float>(t->Qr_hi), pl<float>(t->Qr_lo), t->ldrow);
-  return cudaGetLastError();
-}
 
 // Row-major planes of one rectangle of Q (rows r0.., columns c0.. below the computed-column
 // count) rebuilt after a recovery changed it.

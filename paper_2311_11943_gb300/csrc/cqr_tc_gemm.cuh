@@ -40,8 +40,8 @@ cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, int buf, in
 bool tc_has_block_reorth(const TcGemm* t);
 cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr, int buf,
                             cudaStream_t st, int* launches);
-cudaError_t tc_refresh_rows(TcGemm* t, int64_t ncols, cudaStream_t st);
-// The same for one rectangle of Q only (rows r0 .. r0+nr-1, columns c0 .. c0+nc-1).
+// Row-major planes of one rectangle of Q (rows r0 .. r0+nr-1, columns c0 .. c0+nc-1) rebuilt
+// after a recovery changed it.
 cudaError_t tc_refresh_rect(TcGemm* t, int64_t r0, int64_t nr, int64_t c0, int64_t nc, cudaStream_t st);
 
 // General C -= op(A) B in 3xTF32 (op(A) = A^T for a_trans with A K x M, else A M x K; B K x N;
