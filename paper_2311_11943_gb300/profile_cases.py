@@ -6,8 +6,12 @@ library's public API.  Each case runs twice (the first run warms up the handle).
   python -m paper_2311_11943_gb300.profile_cases bfactor64  # 64 batched instances, no erasure
   python -m paper_2311_11943_gb300.profile_cases adjoint    # 8192 x 1024: forward + both adjoints
 
-Launch order per run (for ncu's --launch-skip):
-  tc_c2 / panel_c2: generator, encode (2), then per panel: panel, split, GEMM1, reduce, GEMM2
+Launch order per run (for ncu's --launch-skip; filter by kernel name with -k, as the commands
+in profiles/ do, since two streams interleave):
+  tc_c2 / panel_c2: generator, encode (2), then per panel: block reorthogonalisation (split,
+                    GEMM1, reduce, GEMM2 and, when split over K, a subtraction), panel, split,
+                    the next panel's columns (GEMM1, reduce, GEMM2); the rest of the trailing
+                    update (GEMM1, reduce, GEMM2) on the low-priority stream
   bfactor64:        encode (2), one k_b_factor
 """
 import sys
