@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
   const int64_t row0 = (int64_t)g * RPC;
   const int nr = (int)((M - row0) < RPC ? (M - row0) : RPC);
   float* eta = v + 256;
-  constexpr int GS = CPW < 4 ? CPW : 4;  // slots reduced per butterfly
+  constexpr int GS = CPW < 8 ? CPW : 8;  // slots reduced per butterfly
   constexpr int NG = CPW / GS;
   const int slot = slot_of<GS>(lane);
   const int lps = lanes_per_slot<GS>();
