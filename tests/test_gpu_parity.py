@@ -1,8 +1,8 @@
 """GPU path vs the FP64 oracle, element by element, through the C ABI (needs a GB300).
 
-Tolerances (derived in DESIGN.md, "Parity tolerances"): Gram-Schmidt factors carry a forward
-error of order n u kappa(A), u the unit roundoff of the storage precision; the decode adds
-kappa(G^) u per recovered tile.  Integer results (decode index sets) and the FP64 generator
+Tolerances: Gram-Schmidt factors carry a forward error of order n u kappa(A), u the unit
+roundoff of the storage precision (8 u for 3xTF32 products, whose hi/lo split leaves about
+2^-21 per product); the decode adds kappa(G^) u per recovered tile.  Integer results (decode index sets) and the FP64 generator
 (computed with explicitly rounded operations on both sides) are compared bit for bit.
 """
 import numpy as np
