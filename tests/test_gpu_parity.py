@@ -115,7 +115,9 @@ def test_c1_full_path_parity(dtype):
     assert rel(got["Q"][: g.M, :n], ref["Q"][:, :n]) < tol
     assert rel(got["R"], ref["R"]) < tol
     assert rel(got["Qo"], ref["Qo"]) < tol
-    assert rel(got["x"], ref["x"]) < tol * kappa ** 0  # x is O(kappa) sensitive: see DESIGN
+    # x is kappa times more sensitive than the factors, but both sides solve with the same
+    # (nearly equal) R, so their difference stays within the factors' tolerance
+    assert rel(got["x"], ref["x"]) < tol
     Qo = got["Qo"]
     assert np.abs(Qo.T @ Qo - np.eye(n)).max() < 8 * n * u * kappa
 
