@@ -52,6 +52,10 @@ EXTRA = {
 MODES = {"f64": ("f64", "simt"), "f32": ("f32", "simt"), "tf32": ("f32", "tf32"),
          "3xtf32": ("f32", "3xtf32"), "bf16": ("f32", "bf16"), "bf16x3": ("f32", "bf16x3")}
 L2_BYTES = 126 * 1024 * 1024
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a dominant kernel from
+# one ncu capture of the current kernel on the same workload, keyed by (config, mode, profile
+# class): profiles/k_panel_reg_c2.md for the C2 panel.  Absent: reported as null.
+NCU_TRAFFIC = {("c2", "3xtf32", "panel_icgs"): 2.750208e6}
 
 
 def coded_flops(m, n, p_r, p_c, f, b, protect_r=True):
@@ -106,6 +110,32 @@ def erasure_plan(cfg):
         for (i, j) in synth.random_erasures(gr, gc, cfg["f"], cfg["per_panel"], cfg["seed"] + t):
             plan.append((t, i, j))
     return plan
+
+
+def coded_factor(q, Ad, plan):
+    """The factorisation part of one step: encode, then factor(t, t1) over the segments between
+    erasure panels, with the panel's erasures injected and recovered before it runs."""
+    q.encode(Ad)
+    T = q.geo["panels"]
+    t = 0
+    while t < T:
+        tiles = [(i, j) for (tt, i, j) in plan if tt == t]
+        if tiles:
+            q.inject(tiles)
+            q.recover()
+        t1 = t + 1
+        while t1 < T and not any(tt == t1 for (tt, _, _) in plan):
+            t1 += 1
+        q.factor(t, t1)
+        t = t1
+
+
+def coded_step(q, Ad, yd, xd, plan):
+    """One timed step: the asynchronous verbs of the C ABI in the order of coded_qr_run
+    (factorisation, post-orthogonalisation of Q_1 inside the handle, the solve)."""
+    coded_factor(q, Ad, plan)
+    q.post_orth()
+    q.solve(yd, xd)
 
 
 class ClockSampler:
@@ -265,23 +295,7 @@ def run_ours(args, cfg):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step(q, with_plan):
-        # the async verbs of the C ABI, in the order of coded_qr_run
-        q.encode(Ad)
-        T = q.geo["panels"]
-        pl = plan if with_plan else []
-        t = 0
-        while t < T:
-            tiles = [(i, j) for (tt, i, j) in pl if tt == t]
-            if tiles:
-                q.inject(tiles)
-                q.recover()
-            t1 = t + 1
-            while t1 < T and not any(tt == t1 for (tt, _, _) in pl):
-                t1 += 1
-            q.factor(t, t1)
-            t = t1
-        q.post_orth()
-        q.solve(yd, xd)
+        coded_step(q, Ad, yd, xd, plan if with_plan else [])
 
     def timed(q, with_plan, steps, warmup, profile=False):
         for _ in range(warmup):
@@ -432,7 +446,8 @@ def run_ours(args, cfg):
               "frac": (achieved / peak) if achieved else None,
               "peak_source": "%s copy bandwidth" % peak_src}
     rl.update(kernel=dom_name, launches_per_step=dom_launches / args.steps,
-              avg_launch_ms=dom_ms / dom_launches, traffic=None)
+              avg_launch_ms=dom_ms / dom_launches,
+              traffic=NCU_TRAFFIC.get((args.config, args.mode, dom_name)))
     launches = int(sum(v[1] for v in prof.values()) / args.steps)
 
     cpu = None

@@ -270,6 +270,100 @@ def test_c2_fp64_full_size_sampled():
     assert np.abs(got["R"][:n, n:] - R1 @ Ghk).max() < 1e-12 * np.abs(R1).max()
 
 
+# ----------------------------------------------------------------- the timed C2 step at full size
+def test_c2_bench_step_full_size():
+    # The C2 step exactly as bench.py times it: 4096 x 4096 U diag(sigma) V^T with kappa 1e2,
+    # grid 8 x 8, f = 2, b = 128, FP32 storage, 3xTF32 trailing updates, block
+    # reorthogonalisation, factor segments between the two seeded erasure panels, Q_1
+    # post-orthogonalised inside the handle, then the solve; on the current stream.
+    import bench
+    cfg = bench.CONFIGS["c2"]
+    m, n, p, f, b, kap = (cfg[k] for k in ("m", "n", "p_r", "f", "b", "kappa"))
+    A, y = bench.make_inputs(cfg)
+    plan = bench.erasure_plan(cfg)
+    q = B.CodedQR(m, n, p, p, f, b, dtype="f32", mma="3xtf32", seed=cfg["seed"],
+                  stream=torch.cuda.current_stream(), reorth_block=True)
+    Ad, yd = to_dev(A, torch.float32), to_dev(y, torch.float32)
+    xd = B.colmajor_empty(n, 1, torch.float32)
+    bench.coded_factor(q, Ad, plan)
+    Qc, Rc = q.factors()
+    Qt, R = Qc.double(), Rc.double()      # the coded factors before post-orthogonalisation
+    q.post_orth()
+    q.solve(yd, xd)
+    Qo = Qc[:m, :n].double()              # G_0 Q_1, written over Q_1 by the step
+    x = to_np(xd)
+    torch.cuda.synchronize()
+    assert q.sync_status() == 0
+    sets = q.decode_sets()
+    Gt, Gh = q.generator()
+    q.close()
+    g = O.geom(m, n, p, p, f)
+    M = g.M
+
+    # the FP32 accuracy target (kappa <= 1e4): backward error and orthogonality at most 1e-5
+    dev = Qt.device
+    A64 = torch.from_numpy(A).to(dev)
+    eye = torch.eye(n, dtype=torch.float64, device=dev)
+    back = (torch.linalg.norm(A64 - Qt[:m, :n] @ R[:n, :n]) / torch.linalg.norm(A64)).item()
+    orth_coded = (Qt[:, :n].T @ Qt[:, :n] - eye).abs().max().item()
+    orth = (Qo.T @ Qo - eye).abs().max().item()
+    assert back <= 1e-5 and orth_coded <= 1e-5 and orth <= 1e-5, (back, orth_coded, orth)
+
+    # generator bit for bit; decode index sets from the oracle's plan logic (any tile size)
+    Gto, Gho = O.generator(f, p, p, cfg["seed"])
+    assert np.array_equal(Gt, Gto) and np.array_equal(Gh, Gho)
+    er = {}
+    for (t, i, j) in plan:
+        er.setdefault(t, []).append((i, j))
+    gs = O.geom(2 * p, p, p, p, f)
+    Qs = O.encode(gs, Gto, Gho, synth.gaussian(2 * p, p, 1))
+    Rs = np.zeros((gs.N, gs.N), order="F")
+    ref_sets = []
+    for t in sorted(er):
+        mask = np.zeros((gs.grid_rows, gs.grid_cols), np.uint8)
+        O.inject(gs, er[t], mask, Qs, Rs)
+        ref_sets += O.recover(gs, Gto, Gho, mask, Qs, Rs)[0]
+    assert sets == ref_sets
+
+    # sampled outputs the oracle computes exactly: panel 0's Q columns and R rows.  Outside
+    # the tiles rebuilt by recovery they carry only FP32 rounding and the 2^-21 of the 3xTF32
+    # products (64 u3x); the rebuilt tiles also carry the decode's kappa(G^) u (the file's
+    # n u kappa rule).  Later block reorthogonalisations add projections of rounding size
+    # to R's rows.
+    Qor = O.encode(g, Gto, Gho, A)
+    Ror = np.zeros((g.N, g.N), order="F")
+    O.factor(Qor, Ror, n, b, 0, 1, reorth_block=True)
+    Qp, Rp = Qt[:, :b].cpu().numpy(), R[:b, :].cpu().numpy()
+    keep_q = np.ones((M, b), bool)
+    keep_r = np.ones((b, g.N), bool)
+    for (_, i, j) in plan:
+        if j == 0:
+            keep_q[i * g.mb:(i + 1) * g.mb, :] = False
+        if i == 0:
+            keep_r[:, j * g.nb:(j + 1) * g.nb] = False
+    assert np.abs(Qp - Qor[:, :b])[keep_q].max() < 64 * U3X
+    assert np.abs(Rp - Ror[:b, :])[keep_r].max() < 64 * U3X * max(1.0, np.abs(Ror[:b]).max())
+    tol = n * U3X * kap
+    assert rel(Qp, Qor[:, :b]) < tol and rel(Rp, Ror[:b, :]) < tol
+
+    # post-orthogonalisation element by element against the oracle's block formula on the
+    # same Q_1: each output sums p_r products of a coefficient below p_r in magnitude with a
+    # Q entry below 1, so its FP32 rounding stays below p_r^3 u
+    W = O.post_orth(g, Gto, Qt[:m, :n].cpu().numpy())
+    assert np.abs(Qo.cpu().numpy() - W).max() < p ** 3 * U32
+
+    # properties at any size: the checksum rows follow the systematic rows (drift of the
+    # FP32 updates, u kappa scale); the solve's residual is within kappa times the 1e-5
+    # backward-error target
+    Gv = torch.kron(torch.from_numpy(Gto), torch.eye(g.mb, dtype=torch.float64)).to(dev)
+    drift = (Qt[m:M, :n] - Gv @ Qt[:m, :n]).abs().max().item()
+    assert drift < 100 * U3X * kap, drift
+    resid = np.linalg.norm(A @ x - y) / np.linalg.norm(y)
+    assert resid <= 1e-5 * kap, resid
+    print("c2 step: back %.3g orth_coded %.3g orth %.3g drift %.3g resid %.3g"
+          % (back, orth_coded, orth, drift, resid))
+
+
 # ----------------------------------------------------------------- tensor-core trailing update
 # 3xTF32 splits each FP32 operand into a TF32 head and tail (three tcgen05 products); its
 # products carry a relative error of about 2^-21 (8 u32).  Plain TF32 has unit roundoff 2^-11.
