@@ -38,6 +38,8 @@ CONFIGS = {
                per_panel=1),
 }
 # Configurations with their own bench legs (not the single-problem step above):
+#   ovh: coding overhead at n = 16384 (b = 256, N(0,1)) over the grid, the checksum count and
+#        the vertical-only code, and the cost of one erasure recovered at every panel
 #   c4: 512 independent coded QRs, m ~ U[256, 8192], n ~ U[32, 256] (multiples of p_c, m >= 4 n),
 #       N(0,1), grid 8 x 4, f = 2 per instance, up to two erased tiles per instance at one
 #       seeded panel; one persistent factor launch per phase, recorded into a CUDA graph
@@ -48,6 +50,7 @@ EXTRA = {
     "c5": dict(batch=16, m=8192, n=1024, p_r=8, p_c=8, f=1, b=128, kappa=1e3, seed=5),
     "e1": dict(),
     "f3": dict(),
+    "ovh": dict(m=16384, n=16384, b=256, seed=3),
 }
 MODES = {"f64": ("f64", "simt"), "f32": ("f32", "simt"), "tf32": ("f32", "tf32"),
          "3xtf32": ("f32", "3xtf32"), "bf16": ("f32", "bf16"), "bf16x3": ("f32", "bf16x3")}
@@ -703,6 +706,95 @@ def run_panels(args):
     return 0
 
 
+# ------------------------------------------------------------------------ ovh: overhead sweep
+# (p, f, protect_r, one erasure at every panel)
+OVH_ROWS = [(16, 4, True, False), (16, 4, False, False), (32, 1, True, False),
+            (32, 1, False, False), (64, 1, True, False), (32, 1, True, True)]
+
+
+def run_overhead(args):
+    """Coding overhead t_coded / t_uncoded - 1 of the whole step (encode, factor, post-orth,
+    solve) at n = 16384 over the grid p x p, the checksum count f and the code (two-way or
+    vertical only), against the flop-model floor (1 + f/p)(1 + 2f/p) - 1 (vertical only:
+    f/p); plus one row with one erased tile recovered at the start of every panel (the
+    every-iteration failure experiment on one GPU).  FP32 storage, 3xTF32 updates, block
+    reorthogonalisation.  The matrix is N(0,1): the step's time depends on the values only
+    through the ICGS criterion, whose reorthogonalisation counts are reported."""
+    import torch
+    from paper_2311_11943_gb300 import binding as B
+    from paper_2311_11943_gb300 import synth
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    cfg = EXTRA["ovh"]
+    m, n, b = cfg["m"], cfg["n"], cfg["b"]
+    A_np = synth.gaussian(m, n, cfg["seed"])
+    y_np = synth.rhs(m, 1, cfg["seed"])
+    stream = torch.cuda.current_stream()
+    Ad = B.colmajor_empty(m, n, torch.float32)
+    Ad.copy_(torch.from_numpy(np.ascontiguousarray(A_np)))
+    yd = B.colmajor_empty(m, 1, torch.float32)
+    yd.copy_(torch.from_numpy(np.ascontiguousarray(y_np)))
+    xd = B.colmajor_empty(n, 1, torch.float32)
+    del A_np
+
+    def time_steps(p, f, protect_r, plan):
+        q = B.CodedQR(m, n, p, p, f, b, dtype="f32", mma="3xtf32", seed=cfg["seed"],
+                      protect_r=protect_r, stream=stream, reorth_block=True)
+        for _ in range(args.warmup):
+            coded_step(q, Ad, yd, xd, plan)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            coded_step(q, Ad, yd, xd, plan)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        st = q.sync_status()
+        stats = q.stats()
+        q.close()
+        if st != 0:
+            raise RuntimeError("device status %d (%s)" % (st, B.errstr(st)))
+        return statistics.mean(times), stats
+
+    t_unc, _ = time_steps(16, 0, True, [])
+    rows = []
+    for (p, f, protect_r, every) in OVH_ROWS:
+        plan = []
+        if every:
+            T = -(-n // b)
+            for t in range(T):
+                for (i, j) in synth.random_erasures(p + f, p + (f if protect_r else 0), f, 1,
+                                                    cfg["seed"] + t):
+                    plan.append((t, i, j))
+        ms, stats = time_steps(p, f, protect_r, plan)
+        F = coded_flops(m, n, p, p, f, b, protect_r)
+        floor = (1.0 + f / p) * (1.0 + (2.0 * f / p if protect_r else 0.0)) - 1.0
+        rows.append({"p": p, "f": f, "code": "two-way" if protect_r else "vertical only",
+                     "erasures": "one tile at every panel" if every else "none",
+                     "ms_per_step": ms, "tflops_coded": F / (ms * 1e-3) / 1e12,
+                     "overhead_vs_uncoded": ms / t_unc - 1.0, "flop_model_floor": floor,
+                     "recovered_tiles_per_step": len(plan),
+                     "reorth_per_step": stats["n_reorth"] / (args.warmup + args.steps)})
+    free = [r for r in rows if r["erasures"] == "none"]
+    best = min(free, key=lambda r: r["overhead_vs_uncoded"])
+    line = {"metric": "coding overhead vs uncoded GPU QR at n = 16384 (whole step)",
+            "value": best["overhead_vs_uncoded"], "unit": "fraction", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms_per_step"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 storage, 3xtf32 tensor-core GEMMs",
+            "data": "synthetic (seeded N(0,1), generated on the host)",
+            "config": {"workload": "16384x16384 N(0,1), b=256, block reorthogonalisation; grids "
+                       "16x16 f=4, 32x32 f=1, 64x64 f=1; two-way and vertical-only codes; "
+                       "no erasure, and one erasure at every panel",
+                       "l2": "inputs (1 GB) larger than L2"},
+            "uncoded_ms_per_step": t_unc, "rows": rows, "cpu_baseline": None, "e2e": None}
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------------------ e1: MDS statistics
 def run_mds(args):
     """E1: least |det| and largest condition number over all square submatrices of the
@@ -896,6 +988,8 @@ def main():
             return 0
         if args.config == "e1":
             return run_mds(args)
+        if args.config == "ovh":
+            return run_overhead(args)
         if args.config == "f3":
             return run_panels(args)
         return run_batched(args) if args.config == "c4" else run_autograd(args)

@@ -564,6 +564,31 @@ def test_block_reorth_parity_and_orthogonality(dtype, mma, kappa):
         assert back < 1e-12 and orth < max(1e-12, 10 * orth_ref), (orth, orth_ref, back)
 
 
+# ----------------------------------------------------------------- vertical code alone
+@pytest.mark.parametrize("dtype,mma", [("f64", "simt"), ("f32", "3xtf32")])
+def test_vertical_only_code_parity(dtype, mma):
+    # R protection off (vertical code alone, d = 0): no checksum columns; only Q tiles are
+    # erased and rebuilt.  Q, R, G_0 Q_1 and x against the oracle, decode sets bit for bit.
+    m = n = 640
+    p, f, b = 8, 2, 64
+    A = synth.kappa_matrix(m, n, 1e2, seed=23)
+    y = synth.rhs(m, 1, 23)
+    er = {3: synth.random_erasures(p + f, p, f, 2, seed=11),
+          7: synth.random_erasures(p + f, p, f, 1, seed=12)}
+    ref = O.run(A, p, p, f, b, seed=5, erasures=er, y=y, protect_r=False)
+    got = gpu_run(A, p, p, f, b, seed=5, erasures=er, y=y, dtype=dtype, mma=mma,
+                  protect_r=False)
+    assert got["status"] == 0
+    assert got["geo"]["N"] == n
+    assert got["sets"] == ref["sets"]
+    g = ref["geom"]
+    tol = n * (U64 if dtype == "f64" else U3X) * 1e2
+    assert rel(got["Q"][: g.M, :n], ref["Q"][:, :n]) < tol
+    assert rel(got["R"], ref["R"]) < tol
+    assert rel(got["Qo"], ref["Qo"]) < tol
+    assert rel(got["x"], ref["x"]) < tol * 1e2
+
+
 # ----------------------------------------------------------------- square solve (a9)
 @pytest.mark.parametrize("dtype,mma", [("f64", "simt"), ("f32", "3xtf32")])
 def test_square_solve_ragged_block_count(dtype, mma):

@@ -364,6 +364,28 @@ def test_recovered_run_equals_fault_free_run():
         assert np.abs(out[k] - ref[k]).max() < 1e-10 * max(1, np.abs(ref[k]).max())
 
 
+def test_vertical_only_code():
+    # R protection off (Section 4.2 with the vertical code alone, d = 0): At = [A; G_v A], R is
+    # the sign-normalised Householder R of At, Q_2 = G_v Q_1 at the end, and a run whose Q
+    # tiles (systematic and checksum) are erased and recovered equals the fault-free run.
+    m, n, p, f, b = 48, 36, 4, 1, 6
+    A = synth.gaussian(m, n, 3)
+    ref = O.run(A, p, p, f, b, seed=2, protect_r=False)
+    g, At, Q, R = ref["geom"], ref["At"], ref["Q"], ref["R"]
+    assert g.d == 0 and g.N == n and g.grid_cols == p
+    Gv = np.kron(ref["Gt"], np.eye(g.mb))
+    assert np.array_equal(At[:m], A)
+    assert np.abs(At[m:] - Gv @ A).max() < 1e-14 * np.abs(Gv @ A).max()
+    Qh, Rh = _signfix(*np.linalg.qr(At))
+    assert np.abs(R - Rh).max() < 1e-12 * np.abs(Rh).max()
+    assert np.abs(Q - Qh).max() < 1e-11
+    assert np.abs(Q[m:] - Gv @ Q[:m]).max() < 1e-12
+    out = O.run(A, p, p, f, b, seed=2, protect_r=False, erasures={2: [(0, 1), (4, 2)], 4: [(3, 0)]})
+    assert out["n_recovered"] == 3
+    for k in ("Q", "R", "Qo"):
+        assert np.abs(out[k] - ref[k]).max() < 1e-10 * max(1, np.abs(ref[k]).max())
+
+
 # --------------------------------------------------------------------------- a8-a9
 @pytest.mark.parametrize("m,p,f", [(32, 4, 1), (48, 6, 3), (45, 5, 2)])
 def test_post_orth_block_equals_dense_and_is_orthogonal(m, p, f):
