@@ -5,6 +5,7 @@ library's public API.  Each case runs twice (the first run warms up the handle).
   python -m paper_2311_11943_gb300.profile_cases panel_c2   # same handle (register panel)
   python -m paper_2311_11943_gb300.profile_cases bfactor64  # 64 batched instances, no erasure
   python -m paper_2311_11943_gb300.profile_cases adjoint    # 8192 x 1024: forward + both adjoints
+  python -m paper_2311_11943_gb300.profile_cases bandwidth8192  # encode / decode / post-orth
 
 Launch order per run (for ncu's --launch-skip; filter by kernel name with -k, as the commands
 in profiles/ do, since two streams interleave):
@@ -13,6 +14,8 @@ in profiles/ do, since two streams interleave):
                     the next panel's columns (GEMM1, reduce, GEMM2); the rest of the trailing
                     update (GEMM1, reduce, GEMM2) on the low-priority stream
   bfactor64:        encode (2), one k_b_factor
+  bandwidth8192:    encode (vertical, horizontal), panels 0-15, poison, decode (Q, R),
+                    panels 16-31, post-orthogonalisation
 """
 import sys
 
@@ -86,7 +89,32 @@ def case_adjoint():
     q.close()
 
 
-CASES = {"tc_c2": case_c2, "panel_c2": case_c2, "bfactor64": case_bfactor, "adjoint": case_adjoint}
+def case_bandwidth():
+    """The bandwidth kernels on inputs larger than L2: 8192 x 8192 N(0,1), grid 16 x 16, f = 4,
+    b = 256, FP32 3xTF32; encode, four tiles erased at the start of panel 16 and recovered,
+    the rest of the factorisation, post-orthogonalisation into a separate buffer; twice."""
+    import torch
+    from . import binding as B
+    from . import synth
+    n = 8192
+    A = _cm(torch, B, synth.gaussian(n, n, 3, dtype=np.float32))
+    q = B.CodedQR(n, n, 16, 16, 4, 256, dtype="f32", mma="3xtf32", seed=3)
+    tiles = synth.random_erasures(20, 20, 4, 4, 3)
+    Qo = B.colmajor_empty(n, n, torch.float32)
+    for _ in range(2):
+        q.encode(A)
+        q.factor(0, 16)
+        q.inject(tiles)
+        q.recover()
+        q.factor(16, -1)
+        q.post_orth(Qo)
+    torch.cuda.synchronize()
+    assert q.sync_status() == 0
+    q.close()
+
+
+CASES = {"tc_c2": case_c2, "panel_c2": case_c2, "bfactor64": case_bfactor, "adjoint": case_adjoint,
+         "bandwidth8192": case_bandwidth}
 
 if __name__ == "__main__":
     CASES[sys.argv[1]]()
