@@ -107,8 +107,10 @@ __device__ __forceinline__ bool decode_setup(const Geo& g, const DecodePlan& p,
   return true;
 }
 
-// Position (r, s) of the code's tiles: r < mb (Q) or nb (R) within a tile, s < nb.
-template <typename T>
+// Position (r, s) of the code's tiles: r < mb (Q) or nb (R) within a tile, s < nb.  The code
+// tiles are read U at a time (U independent loads in flight per thread) and summed in
+// ascending order whatever U is, so every U gives the same bits.
+template <typename T, int U = 1>
 __device__ __forceinline__ void decode_apply(const Geo& g, const DecodePlan& p,
                                              const DecodeScratch<T>& sh, T* Q, T* R, int64_t r,
                                              int64_t s) {
@@ -124,9 +126,7 @@ __device__ __forceinline__ void decode_apply(const Geo& g, const DecodePlan& p,
     xb[k] = T(0);
     ce[k] = T(0);
   }
-  for (int u = 0; u < sh.nuse; ++u) {
-    const int t = sh.tuse[u];
-    const T val = ptr[(int64_t)t * tstride];
+  auto add = [&](int t, T val) {
 #pragma unroll
     for (int b = 0; b < kMaxF; ++b)
       if (b < f1) xb[b] += sh.coef[b][t] * val;
@@ -134,6 +134,25 @@ __device__ __forceinline__ void decode_apply(const Geo& g, const DecodePlan& p,
 #pragma unroll
       for (int e = 0; e < kMaxF; ++e)
         if (e < f2) ce[e] += sh.cenc[e][t] * val;
+    }
+  };
+  if constexpr (U == 1) {
+    for (int u = 0; u < sh.nuse; ++u) {
+      const int t = sh.tuse[u];
+      add(t, ptr[(int64_t)t * tstride]);
+    }
+  } else {
+    for (int u0 = 0; u0 < sh.nuse; u0 += U) {
+      int tt[U];
+      T v[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        tt[k] = (u0 + k < sh.nuse) ? sh.tuse[u0 + k] : -1;
+        v[k] = tt[k] >= 0 ? ptr[(int64_t)tt[k] * tstride] : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k)
+        if (tt[k] >= 0) add(tt[k], v[k]);
     }
   }
 #pragma unroll

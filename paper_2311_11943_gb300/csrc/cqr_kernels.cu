@@ -412,7 +412,7 @@ __device__ __forceinline__ void decode_body(const Geo& g, const DecodePlan& p,
   const int64_t r = (int64_t)bx * blockDim.x + threadIdx.x;
   const int64_t s = (int64_t)by * blockDim.y + threadIdx.y;
   if (r >= h || s >= g.nb) return;
-  decode_apply<T>(g, p, sh, Q, R, r, s);
+  decode_apply<T, 4>(g, p, sh, Q, R, r, s);
 }
 
 template <typename T>
