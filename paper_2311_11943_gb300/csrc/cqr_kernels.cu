@@ -397,22 +397,30 @@ cudaError_t launch_poison(const Geo& g, const int* tiles, int count, T* Q, T* R,
 
 // ===================================================================== a7 decode
 // The decode itself (setup of a code's coefficient tables, recovery of one position) is in
-// cqr_decode.cuh; here one CTA of 32 x 8 threads recovers a 32-row x 8-column block of
-// positions of one code.
-template <typename T>
+// cqr_decode.cuh; here one CTA of 32 x 8 threads builds the code's tables once and recovers
+// rows 32 bx .. 32 bx + 31 of the 8-column group by of one code, and with Strided also of the
+// groups by + sy, by + 2 sy, ...
+template <typename T, bool Strided>
 __device__ __forceinline__ void decode_body(const Geo& g, const DecodePlan& p,
                                             const double* __restrict__ Gt,
                                             const double* __restrict__ Gh, T* Q, T* R,
-                                            int* status, int bx, int by) {
+                                            int* status, int bx, int by, int sy) {
   __shared__ DecodeScratch<T> sh;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   if (!decode_setup<T>(g, p, Gt, Gh, sh, tid, blockDim.x * blockDim.y, status, bx == 0 && by == 0))
     return;
   const int64_t h = p.kind == 0 ? g.mb : g.nb;
   const int64_t r = (int64_t)bx * blockDim.x + threadIdx.x;
-  const int64_t s = (int64_t)by * blockDim.y + threadIdx.y;
-  if (r >= h || s >= g.nb) return;
-  decode_apply<T, 4>(g, p, sh, Q, R, r, s);
+  if (r >= h) return;
+  if constexpr (Strided) {
+    for (int64_t s = (int64_t)by * blockDim.y + threadIdx.y; s < g.nb;
+         s += (int64_t)sy * blockDim.y)
+      decode_apply<T, 4>(g, p, sh, Q, R, r, s);
+  } else {
+    (void)sy;
+    const int64_t s = (int64_t)by * blockDim.y + threadIdx.y;
+    if (s < g.nb) decode_apply<T, 4>(g, p, sh, Q, R, r, s);
+  }
 }
 
 template <typename T>
@@ -420,7 +428,8 @@ __global__ void __launch_bounds__(256) k_decode(Geo g, const DecodePlan* __restr
                                                  const double* __restrict__ Gt,
                                                  const double* __restrict__ Gh, T* Q, T* R,
                                                  int* status) {
-  decode_body<T>(g, plans[blockIdx.z], Gt, Gh, Q, R, status, blockIdx.x, blockIdx.y);
+  decode_body<T, true>(g, plans[blockIdx.z], Gt, Gh, Q, R, status, blockIdx.x, blockIdx.y,
+                       gridDim.y);
 }
 
 template <typename T>
@@ -428,8 +437,12 @@ cudaError_t launch_decode(const Geo& g, const DecodePlan* plans_dev, int nplans,
                           const double* Gt, const double* Gh, T* Q, T* R, int* status,
                           cudaStream_t st) {
   if (nplans == 0) return cudaSuccess;
+  // about one wave (768 CTAs over all codes), so that each CTA's table setup is amortised
+  // over several 8-column groups
   dim3 blk(32, 8);
-  dim3 grd((unsigned)((max_h + 31) / 32), (unsigned)((g.nb + 7) / 8), (unsigned)nplans);
+  const int64_t nbx = (max_h + 31) / 32, nby = (g.nb + 7) / 8;
+  const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(nby, 768 / std::max<int64_t>(1, nbx * nplans)));
+  dim3 grd((unsigned)nbx, (unsigned)gy, (unsigned)nplans);
   k_decode<T><<<grd, blk, 0, st>>>(g, plans_dev, Gt, Gh, Q, R, status);
   return cudaGetLastError();
 }
@@ -1119,7 +1132,8 @@ __global__ void __launch_bounds__(256) k_b_decode(const BatchInst<T>* __restrict
     const int64_t h = bp.p.kind == 0 ? I.g.mb : I.g.nb;
     const int64_t nbx = (h + 31) / 32;
     const int64_t loc = v - off[k];
-    decode_body<T>(I.g, bp.p, Gt, Gh, I.Q, I.R, I.status, (int)(loc % nbx), (int)(loc / nbx));
+    decode_body<T, false>(I.g, bp.p, Gt, Gh, I.Q, I.R, I.status, (int)(loc % nbx),
+                          (int)(loc / nbx), 1);
   }
 }
 
