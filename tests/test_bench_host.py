@@ -1,0 +1,67 @@
+"""Host logic of bench.py on the CPU: the flop model of the reported metric and the seeded
+erasure plans of the timed workloads."""
+import numpy as np
+import pytest
+
+import bench
+from oracle import oracle as O
+from paper_2311_11943_gb300 import synth
+
+
+@pytest.mark.parametrize("m,n,p_r,p_c,f,b,protect_r", [
+    (4096, 4096, 8, 8, 2, 128, True), (16384, 16384, 16, 16, 4, 256, True),
+    (1000, 480, 8, 4, 2, 100, True), (333, 96, 5, 4, 1, 40, False), (256, 256, 4, 4, 0, 32, True)])
+def test_flop_model_is_the_per_panel_work(m, n, p_r, p_c, f, b, protect_r):
+    # F_coded = 2 (m+c) n (n+2d) is the sum over panels k (width b_k, trailing width w_k) of
+    # the panel at one pass, 2 M b_k^2, and the two trailing GEMMs, 4 M b_k w_k (Algorithm
+    # PBMGS), with M and N from the oracle's geometry (m padded to a multiple of p_r)
+    g = O.geom(m, n, p_r, p_c, f, protect_r)
+    total, kb = 0, 0
+    while kb < n:
+        bk = min(b, n - kb)
+        wk = g.N - kb - bk
+        total += 2 * g.M * bk * bk + 4 * g.M * bk * wk
+        kb += bk
+    assert bench.coded_flops(m, n, p_r, p_c, f, b, protect_r) == total
+    assert total == 2 * g.M * n * (n + 2 * g.d)
+
+
+def _check_plan(plan, T, grid_rows, grid_cols, f):
+    assert all(0 <= t < T and 0 <= i < grid_rows and 0 <= j < grid_cols for (t, i, j) in plan)
+    for t in {t for (t, _, _) in plan}:
+        tiles = [(i, j) for (tt, i, j) in plan if tt == t]
+        assert len(set(tiles)) == len(tiles)
+        assert max(np.bincount([i for i, _ in tiles])) <= f
+        assert max(np.bincount([j for _, j in tiles])) <= f
+
+
+@pytest.mark.parametrize("name", ["c1", "c2", "c3"])
+def test_erasure_plans_are_recoverable_and_reproducible(name):
+    cfg = bench.CONFIGS[name]
+    T = -(-cfg["n"] // cfg["b"])
+    plan = bench.erasure_plan(cfg)
+    assert plan == bench.erasure_plan(cfg)
+    assert len(plan) == cfg["erasure_panels"] * cfg["per_panel"]
+    assert len({t for (t, _, _) in plan}) == cfg["erasure_panels"]
+    _check_plan(plan, T, cfg["p_r"] + cfg["f"], cfg["p_c"] + cfg["f"], cfg["f"])
+
+
+def test_every_panel_plan_of_the_overhead_sweep():
+    cfg = bench.EXTRA["ovh"]
+    T = -(-cfg["n"] // cfg["b"])
+    for (p, f, protect_r, every) in bench.OVH_ROWS:
+        if not every:
+            continue
+        gc = p + (f if protect_r else 0)
+        plan = [(t, i, j) for t in range(T)
+                for (i, j) in synth.random_erasures(p + f, gc, f, 1, cfg["seed"] + t)]
+        assert len(plan) == T
+        _check_plan(plan, T, p + f, gc, f)
+
+
+def test_both_arms_describe_the_same_workload():
+    cfg = bench.CONFIGS["c2"]
+    a = bench.step_config(cfg, "3xtf32", True, 1)
+    assert a == bench.step_config(dict(cfg), "3xtf32", True, 1)
+    assert a["erasures"] == [list(p) for p in bench.erasure_plan(cfg)]
+    assert "4096x4096" in a["workload"] and "f=2" in a["workload"]
