@@ -206,6 +206,92 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------------ CPU oracle legs
+def blas3_step(A, y, Gt, Gh, p_r, p_c, f, b, dtype, reorth_block=True, tau=1.0 / np.sqrt(2.0)):
+    """A BLAS-3 CPU baseline of the same step in torch on the host cores (context beside the
+    plain oracle, not a fallback: nothing in the library calls it).  Encode (Section 4.2), PBMGS
+    with the right-looking ICGS panel, the optional block reorthogonalisation pass, the
+    trailing GEMMs (Algorithm PBMGS), post-orthogonalisation G_0 Q_1 and the square solve
+    (Section 4.1), without erasures.  Q~ is held transposed (row j = column j) so that every
+    column operation is contiguous.  Gt (f x p_r) and Gh (p_c x f) are the generator.
+    Returns (Qt, R, x) with Qt the post-orthogonalised factor, N x M."""
+    import torch
+    m, n = A.shape
+    mb = -(-m // p_r)
+    m_pad, nb = mb * p_r, n // p_c
+    c, d = f * mb, f * nb
+    M, N = m_pad + c, n + d
+    Gt_t = torch.as_tensor(np.asarray(Gt), dtype=dtype)
+    Gh_t = torch.as_tensor(np.asarray(Gh), dtype=dtype)
+    Qt = torch.zeros(N, M, dtype=dtype)
+    Qt[:n, :m] = torch.as_tensor(np.ascontiguousarray(A.T), dtype=dtype)
+    if f > 0:
+        Qt[:n, m_pad:] = torch.einsum("nts,it->nis", Qt[:n, :m_pad].view(n, p_r, mb),
+                                      Gt_t).reshape(n, c)
+        Qt[n:] = torch.einsum("jsm,jl->lsm", Qt[:n].view(p_c, nb, M), Gh_t).reshape(d, M)
+    R = torch.zeros(N, N, dtype=dtype)
+    for kb in range(0, n, b):
+        bk = min(b, n - kb)
+        P = Qt[kb:kb + bk]
+        if reorth_block and kb > 0:
+            S = Qt[:kb] @ P.T
+            P -= S.T @ Qt[:kb]
+            R[:kb, kb:kb + bk] += S
+        eta = (P * P).sum(1)
+        for j in range(bk):
+            q = P[j]
+            v = P[j:] @ q
+            if j > 0 and v[0] < tau * tau * eta[j]:
+                sv = P[:j] @ q
+                q -= sv @ P[:j]
+                R[kb:kb + j, kb + j] += sv
+                v = P[j:] @ q
+            rjj = torch.sqrt(v[0])
+            if not rjj > 0:
+                raise RuntimeError("breakdown at column %d" % (kb + j))
+            R[kb + j, kb + j] = rjj
+            q /= rjj
+            r = v[1:] / rjj
+            R[kb + j, kb + j + 1:kb + bk] = r
+            P[j + 1:].addr_(r, q, alpha=-1.0)
+        if kb + bk < N:
+            Rbar = P @ Qt[kb + bk:].T
+            R[kb:kb + bk, kb + bk:] = Rbar
+            Qt[kb + bk:] -= Rbar.T @ P
+    # G_0 = [[I + G~_1, V], [V^T, -I]] on tile rows (Theorem G_0), applied to Q_1 and [y; 0]
+    G0 = -torch.eye(p_r, dtype=dtype)
+    if f > 0:
+        G0[:f, :f] = torch.eye(f, dtype=dtype) + Gt_t[:, :f]
+        G0[:f, f:] = Gt_t[:, f:]
+        G0[f:, :f] = Gt_t[:, f:].T
+    Qo = torch.einsum("nts,it->nis", Qt[:n, :m_pad].view(n, p_r, mb), G0).reshape(n, m_pad)
+    yp = torch.zeros(m_pad, dtype=dtype)
+    yp[:m] = torch.as_tensor(np.asarray(y).reshape(-1), dtype=dtype)
+    yo = torch.einsum("ts,it->is", yp.view(p_r, mb), G0).reshape(m_pad)
+    x = torch.linalg.solve_triangular(R[:n, :n], (Qo @ yo).reshape(n, 1), upper=True)
+    return Qo, R, x
+
+
+def blas3_baseline(cfg, A, y, rb):
+    """Times blas3_step on the whole workload in FP64 and FP32 on all host cores."""
+    import torch
+    from oracle import oracle as O
+    threads = os.cpu_count() or 1
+    torch.set_num_threads(threads)
+    Gt, Gh = O.generator(cfg["f"], cfg["p_r"], cfg["p_c"], cfg["seed"])
+    F = coded_flops(cfg["m"], cfg["n"], cfg["p_r"], cfg["p_c"], cfg["f"], cfg["b"])
+    out = []
+    for name, dt in (("f64", torch.float64), ("f32", torch.float32)):
+        t0 = time.perf_counter()
+        blas3_step(A, y, Gt, Gh, cfg["p_r"], cfg["p_c"], cfg["f"], cfg["b"], dt, reorth_block=rb)
+        sec = time.perf_counter() - t0
+        out.append({"dtype": name, "value": F / sec / 1e12, "unit": "TFLOP/s",
+                    "ms_per_step": sec * 1e3, "cores": threads,
+                    "kind": "torch CPU BLAS-3, same algorithm",
+                    "sample": "the whole step (encode, factor%s, post-orth, solve), no erasure"
+                    % (" with block reorthogonalisation" if rb else "")})
+    return out
+
+
 def oracle_sample(cfg, A, budget_s, max_panels=None):
     """Time the FP64 oracle on a bounded sample of the workload: encode plus as many PBMGS
     panels (full trailing updates) as fit in budget_s.  Returns (TFLOP/s, cores, sample)."""
@@ -454,10 +540,16 @@ def run_ours(args, cfg):
     launches = int(sum(v[1] for v in prof.values()) / args.steps)
 
     cpu = None
+    blas3 = None
     if rank == 0 and not args.no_cpu_baseline:
         os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
         v, cores, sample, _ = oracle_sample(cfg, A_np, budget_s=args.cpu_budget)
         cpu = {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample}
+        if not args.no_blas3:
+            try:
+                blas3 = blas3_baseline(cfg, A_np, y_np, rb)
+            except Exception as e:  # context only: recorded in the line, not fatal to it
+                blas3 = {"error": "%s: %s" % (type(e).__name__, e)}
 
     if rank == 0:
         line = {
@@ -486,6 +578,7 @@ def run_ours(args, cfg):
             "clocks": clk,
             "roofline": rl,
             "cpu_baseline": cpu,
+            "cpu_blas3": blas3,
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "ms_per_step": ms_e2e,
                     "h2d_bytes_per_step": m * n * es + m * es, "d2h_bytes_per_step": n * es},
         }
@@ -978,6 +1071,8 @@ def main():
                     choices=sorted(MODES))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-blas3", action="store_true",
+                    help="skip the torch CPU BLAS-3 baseline beside the oracle")
     ap.add_argument("--no-reorth-block", action="store_true",
                     help="skip the block reorthogonalisation pass (faster, orthogonality ~ u kappa)")
     args = ap.parse_args()

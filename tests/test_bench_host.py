@@ -65,3 +65,23 @@ def test_both_arms_describe_the_same_workload():
     assert a == bench.step_config(dict(cfg), "3xtf32", True, 1)
     assert a["erasures"] == [list(p) for p in bench.erasure_plan(cfg)]
     assert "4096x4096" in a["workload"] and "f=2" in a["workload"]
+
+
+@pytest.mark.parametrize("m,n,p_r,p_c,f,b,rb", [(256, 256, 4, 4, 1, 32, False),
+                                                (256, 256, 4, 4, 1, 32, True),
+                                                (203, 96, 8, 4, 2, 20, True)])
+def test_blas3_baseline_computes_the_oracles_step(m, n, p_r, p_c, f, b, rb):
+    # the torch CPU baseline timed beside the oracle runs the same algorithm: its R, G_0 Q_1
+    # and x agree with the oracle's in FP64 to the n u kappa forward-error scale
+    torch = pytest.importorskip("torch")
+    kappa = 1e2
+    A = synth.kappa_matrix(m, n, kappa, seed=5)
+    y = synth.rhs(m, 1, 5)
+    ref = O.run(A, p_r, p_c, f, b, seed=3, y=y if m == n else None, reorth_block=rb)
+    Qo, R, x = bench.blas3_step(A, y, ref["Gt"], ref["Gh"], p_r, p_c, f, b, torch.float64,
+                                reorth_block=rb)
+    tol = n * np.finfo(np.float64).eps * kappa
+    assert np.abs(R.numpy() - ref["R"]).max() < tol * np.abs(ref["R"]).max()
+    assert np.abs(Qo.numpy().T - ref["Qo"]).max() < tol
+    if m == n:
+        assert np.abs(x.numpy() - ref["x"]).max() < tol * kappa * np.abs(ref["x"]).max()
