@@ -62,3 +62,58 @@ def test_errstr_and_argument_validation_without_gpu(libpath):
     h = C.c_void_p()
     assert B.lib().coded_qr_create(None, C.byref(h)) == B.CQR_EINVAL
     assert B.lib().coded_qr_factor(None, 0, -1) == B.CQR_EINVAL
+
+
+def _cfg(B, **kw):
+    cfg = B.Config()
+    base = dict(m=64, n=64, p_r=4, p_c=4, f=1, b=8, dtype=B.CQR_F64, mma=B.CQR_MMA_SIMT,
+                protect_r=1, gdist=B.CQR_G_UNIF01, nrhs_max=1, reorth_block=0, panel=0,
+                in_node=0, seed=1, tau=0.0)
+    base.update(kw)
+    for k, v in base.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+# each configuration rule of coded_qr_create (header: argument errors return synchronously,
+# before any device call) with the status it must give
+RULES = [
+    (dict(m=0), "EINVAL"), (dict(n=0), "EINVAL"), (dict(m=32, n=64), "EINVAL"),   # m >= n >= 1
+    (dict(p_r=0), "EINVAL"), (dict(p_c=0), "EINVAL"), (dict(b=0), "EINVAL"),
+    (dict(f=-1), "EINVAL"), (dict(n=62), "EINVAL"),                             # p_c | n
+    (dict(f=3), "EINVAL"),                                                      # 2f <= p_r
+    (dict(p_r=8, f=3), "EINVAL"),                                               # 2f <= p_c (R protected)
+    (dict(m=4096, n=4096, p_r=64, p_c=64, f=17), "ENOTSUP"),                    # f <= 16
+    (dict(m=8192, n=8192, p_r=128, p_c=128, f=1), "ENOTSUP"),                   # p + f <= 128
+    (dict(m=6, n=4, p_r=8, p_c=4), "EINVAL"),                                   # p_r <= m
+    (dict(dtype=7), "EINVAL"), (dict(mma=9), "EINVAL"),
+    (dict(mma=1), "ENOTSUP"),                                                   # tensor cores need FP32
+    (dict(gdist=5), "EINVAL"), (dict(nrhs_max=-1), "EINVAL"), (dict(panel=4), "EINVAL"),
+    (dict(in_node=2), "EINVAL"), (dict(in_node=1, f=4), "EINVAL"),              # in-node: f < p_r
+    (dict(in_node=1, p_c=2, n=64), "ENOTSUP"),                                  # in-node R: p_c = p_r
+]
+
+
+@pytest.mark.parametrize("kw,status", RULES)
+def test_configuration_rules(libpath, kw, status):
+    from paper_2311_11943_gb300 import binding as B
+    n = C.c_size_t(0)
+    cfg = _cfg(B, **kw)
+    want = getattr(B, "CQR_" + status)
+    assert B.lib().coded_qr_workspace_size(C.byref(cfg), C.byref(n)) == want
+    h = C.c_void_p()
+    assert B.lib().coded_qr_create(C.byref(cfg), C.byref(h)) == want
+    assert not h.value
+
+
+def test_valid_configuration_without_a_device_is_a_cuda_error(libpath):
+    # no CPU fallback: a valid configuration on a machine without a GPU fails with CQR_ECUDA
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2311_11943_gb300 import binding as B
+    cfg = _cfg(B)
+    n = C.c_size_t(0)
+    assert B.lib().coded_qr_workspace_size(C.byref(cfg), C.byref(n)) == B.CQR_ECUDA
+    h = C.c_void_p()
+    assert B.lib().coded_qr_create(C.byref(cfg), C.byref(h)) == B.CQR_ECUDA
