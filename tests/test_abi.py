@@ -117,3 +117,28 @@ def test_valid_configuration_without_a_device_is_a_cuda_error(libpath):
     assert B.lib().coded_qr_workspace_size(C.byref(cfg), C.byref(n)) == B.CQR_ECUDA
     h = C.c_void_p()
     assert B.lib().coded_qr_create(C.byref(cfg), C.byref(h)) == B.CQR_ECUDA
+
+
+BATCH_RULES = [
+    (dict(), [(256, 32), (512, 64)], 0, "EINVAL"),                     # count >= 1
+    (dict(dtype=0), [(256, 32)], 1, "ENOTSUP"),                        # FP32 only
+    (dict(mma=2), [(256, 32)], 1, "ENOTSUP"),                          # CUDA-core products
+    (dict(b=-1), [(256, 32)], 1, "EINVAL"), (dict(b=65), [(256, 32)], 1, "ENOTSUP"),
+    (dict(reorth_block=1), [(256, 32)], 1, "ENOTSUP"),
+    (dict(), [(256, 32), (16, 32)], 2, "EINVAL"),                      # an instance with m < n
+    (dict(), [(256, 32), (256, 30)], 2, "EINVAL"),                     # p_c does not divide n
+]
+
+
+@pytest.mark.parametrize("kw,shapes,count,status", BATCH_RULES)
+def test_batched_configuration_rules(libpath, kw, shapes, count, status):
+    from paper_2311_11943_gb300 import binding as B
+    args = dict(dtype=B.CQR_F32, p_r=8, p_c=4, f=2, b=0)
+    args.update(kw)
+    cfg = _cfg(B, **args)
+    ms = (C.c_int64 * len(shapes))(*[s[0] for s in shapes])
+    ns = (C.c_int64 * len(shapes))(*[s[1] for s in shapes])
+    h = C.c_void_p()
+    assert B.lib().coded_qr_batched_create(C.byref(cfg), ms, ns, count, C.byref(h)) == \
+        getattr(B, "CQR_" + status)
+    assert not h.value
