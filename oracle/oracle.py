@@ -5,6 +5,7 @@ Every function forwards to a routine of cqr_oracle.c, which cites the passage of
 paper (arXiv 2311.11943) it follows.  Arrays are numpy float64, Fortran (column-major)
 order.  Nothing here imports the CUDA package.
 """
+import contextlib
 import ctypes as C
 import os
 
@@ -29,35 +30,51 @@ class Geom(C.Structure):
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(_build.build())
-        d = C.POINTER(C.c_double)
-        i64 = C.c_int64
-        L = _lib
-        L.cqro_geom_init.argtypes = [C.POINTER(Geom), i64, i64, C.c_int, C.c_int, C.c_int, C.c_int]
-        L.cqro_generator.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_int, d, d]
-        L.cqro_splitmix64.argtypes = [C.c_uint64, C.c_int, C.POINTER(C.c_uint64)]
-        L.cqro_encode.argtypes = [C.POINTER(Geom), d, d, d, i64, d, i64]
-        L.cqro_icgs_panel.argtypes = [i64, i64, i64, C.c_double, d, i64, d, i64, C.POINTER(i64)]
-        L.cqro_factor.argtypes = [i64, i64, i64, i64, C.c_int, C.c_int, C.c_double, d, i64, d,
-                                  i64, C.POINTER(i64)]
-        L.cqro_factor2.argtypes = [i64, i64, i64, i64, C.c_int, C.c_int, C.c_double, C.c_int, d,
-                                   i64, d, i64, C.POINTER(i64)]
-        L.cqro_factor3.argtypes = [i64, i64, i64, i64, C.c_int, C.c_int, C.c_double, C.c_int,
-                                   C.c_int, d, i64, d, i64, C.POINTER(i64)]
-        L.cqro_cgs_panel.argtypes = [i64, i64, i64, C.c_int, d, i64, d, i64]
-        L.cqro_inject.argtypes = [C.POINTER(Geom), C.POINTER(C.c_int), C.c_int,
-                                  C.POINTER(C.c_uint8), d, i64, d, i64]
-        L.cqro_invert_small.argtypes = [C.c_int, d, d]
-        L.cqro_recover.argtypes = [C.POINTER(Geom), d, d, C.POINTER(C.c_uint8), d, i64, d, i64,
-                                   C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int),
-                                   C.POINTER(C.c_int)]
-        L.cqro_build_G0.argtypes = [C.POINTER(Geom), d, d, i64]
-        L.cqro_post_orth_dense.argtypes = [C.POINTER(Geom), d, d, i64, i64, d, i64]
-        L.cqro_post_orth_block.argtypes = [C.POINTER(Geom), d, d, i64, i64, d, i64]
-        L.cqro_back_substitute.argtypes = [i64, d, i64, d, i64, i64]
-        L.cqro_solve_square.argtypes = [i64, i64, d, i64, d, i64, d, i64, i64, d, i64]
-        L.cqro_solve_ls.argtypes = [i64, i64, d, i64, d, i64, d, i64, i64, d, i64]
+        _lib = _bind(C.CDLL(_build.build()))
     return _lib
+
+
+@contextlib.contextmanager
+def library(path):
+    """Run the oracle from another build of cqr_oracle.c for the duration of the block (the
+    tests plant mistakes in copies of the source to show that the pins catch them)."""
+    global _lib
+    saved = _lib
+    _lib = _bind(C.CDLL(path))
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+def _bind(L):
+    d = C.POINTER(C.c_double)
+    i64 = C.c_int64
+    L.cqro_geom_init.argtypes = [C.POINTER(Geom), i64, i64, C.c_int, C.c_int, C.c_int, C.c_int]
+    L.cqro_generator.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_int, d, d]
+    L.cqro_splitmix64.argtypes = [C.c_uint64, C.c_int, C.POINTER(C.c_uint64)]
+    L.cqro_encode.argtypes = [C.POINTER(Geom), d, d, d, i64, d, i64]
+    L.cqro_icgs_panel.argtypes = [i64, i64, i64, C.c_double, d, i64, d, i64, C.POINTER(i64)]
+    L.cqro_factor.argtypes = [i64, i64, i64, i64, C.c_int, C.c_int, C.c_double, d, i64, d,
+                              i64, C.POINTER(i64)]
+    L.cqro_factor2.argtypes = [i64, i64, i64, i64, C.c_int, C.c_int, C.c_double, C.c_int, d,
+                               i64, d, i64, C.POINTER(i64)]
+    L.cqro_factor3.argtypes = [i64, i64, i64, i64, C.c_int, C.c_int, C.c_double, C.c_int,
+                               C.c_int, d, i64, d, i64, C.POINTER(i64)]
+    L.cqro_cgs_panel.argtypes = [i64, i64, i64, C.c_int, d, i64, d, i64]
+    L.cqro_inject.argtypes = [C.POINTER(Geom), C.POINTER(C.c_int), C.c_int,
+                              C.POINTER(C.c_uint8), d, i64, d, i64]
+    L.cqro_invert_small.argtypes = [C.c_int, d, d]
+    L.cqro_recover.argtypes = [C.POINTER(Geom), d, d, C.POINTER(C.c_uint8), d, i64, d, i64,
+                               C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int),
+                               C.POINTER(C.c_int)]
+    L.cqro_build_G0.argtypes = [C.POINTER(Geom), d, d, i64]
+    L.cqro_post_orth_dense.argtypes = [C.POINTER(Geom), d, d, i64, i64, d, i64]
+    L.cqro_post_orth_block.argtypes = [C.POINTER(Geom), d, d, i64, i64, d, i64]
+    L.cqro_back_substitute.argtypes = [i64, d, i64, d, i64, i64]
+    L.cqro_solve_square.argtypes = [i64, i64, d, i64, d, i64, d, i64, i64, d, i64]
+    L.cqro_solve_ls.argtypes = [i64, i64, d, i64, d, i64, d, i64, i64, d, i64]
+    return L
 
 
 def _p(a):
