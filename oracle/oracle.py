@@ -205,6 +205,18 @@ def post_orth(g, Gt, Z, dense=False):
     return W
 
 
+def post_orth_projected(g, Gt, Q1, Q2):
+    """a8, drift-robust reading: W = G_0^{-1} (Q_1 + G^T Q_2), G = G~ (x) I_mb.  With
+    G_0^2 = I + G^T G (G_0 symmetric, Theorem G_0) this is G_0 applied to the orthogonal
+    projection of [Q_1; Q_2] onto the range {[x; G x]} of the encoding, so it equals G_0 Q_1
+    whenever Q_2 = G Q_1 (the checksum-preservation Lemma); in floating point, where Q_2
+    drifts from G Q_1 by delta, its loss of orthogonality is of order delta^2 instead of
+    delta.  Plain definition: the dense G_0 and a library solve.  Q1 m_pad x k, Q2 c x k."""
+    G0 = build_G0(g, Gt)
+    G = np.kron(np.asarray(Gt, dtype=np.float64), np.eye(g.mb))
+    return np.asfortranarray(np.linalg.solve(G0, np.asarray(Q1) + G.T @ np.asarray(Q2)))
+
+
 def back_substitute(R, rhs):
     x = np.asfortranarray(rhs, dtype=np.float64).copy(order="F")
     if x.ndim == 1:

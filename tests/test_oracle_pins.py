@@ -405,6 +405,38 @@ def test_post_orth_block_equals_dense_and_is_orthogonal(m, p, f):
     assert np.abs(Q1.T @ Q1 - np.eye(n_eff)).max() > 1e-3  # Q_1 alone is not orthogonal
 
 
+def test_projected_post_orth_equals_G0_Q1_on_consistent_checksums():
+    # when Q_2 = G Q_1 exactly, G_0^{-1} (Q_1 + G^T Q_2) = G_0^{-1} (I + G^T G) Q_1 = G_0 Q_1
+    m, p, f = 48, 6, 2
+    g = O.geom(m, 12, p, p, f)
+    Gt, _ = O.generator(f, p, p, 3)
+    Q1 = synth.gaussian(m, 12, 4)
+    Q2 = np.kron(Gt, np.eye(g.mb)) @ Q1
+    W = O.post_orth_projected(g, Gt, Q1, Q2)
+    assert np.abs(W - O.post_orth(g, Gt, Q1, dense=True)).max() < 1e-12 * np.abs(W).max()
+
+
+@pytest.mark.parametrize("delta", [1e-5, 1e-3])
+def test_projected_post_orth_loses_orthogonality_to_second_order(delta):
+    # an orthonormal coded factor whose checksum rows drifted by delta from G Q_1: G_0 Q_1
+    # loses orthogonality to first order in the drift, the projected form to second order
+    m = n = 64
+    p, f, b = 4, 1, 8
+    ref = O.run(synth.gaussian(m, n, 6), p, p, f, b, seed=2)
+    g, Gt = ref["geom"], ref["Gt"]
+    Q = ref["Q"][:, :n].copy()
+    Q[m:] += delta * synth.gaussian(g.c, n, 7) / np.sqrt(m)
+    Q, _ = np.linalg.qr(Q)
+    Q1, Q2 = Q[:m], Q[m:]
+    drift = np.abs(Q2 - np.kron(Gt, np.eye(g.mb)) @ Q1).max()
+    W0 = O.post_orth(g, Gt, Q1)
+    W1 = O.post_orth_projected(g, Gt, Q1, Q2)
+    e0 = np.abs(W0.T @ W0 - np.eye(n)).max()
+    e1 = np.abs(W1.T @ W1 - np.eye(n)).max()
+    assert e0 > 0.1 * drift
+    assert e1 < n * drift ** 2 + 1e-13
+
+
 @pytest.mark.parametrize("n,p,f,b", [(32, 4, 1, 8), (60, 6, 2, 10), (64, 4, 2, 16)])
 def test_solve_square_matches_numpy(n, p, f, b):
     # Eqs. (linearsolve1)-(linearsolve3): R x = (G_0 Q_1)^T (G_0 y)
