@@ -1,5 +1,7 @@
-"""Host logic of bench.py on the CPU: the flop model of the reported metric and the seeded
-erasure plans of the timed workloads."""
+"""Host logic of bench.py on the CPU: the flop model of the reported metric, the seeded
+erasure plans of the timed workloads, the BLAS-3 CPU baseline and the reference arm's line."""
+import os
+
 import numpy as np
 import pytest
 
@@ -85,3 +87,36 @@ def test_blas3_baseline_computes_the_oracles_step(m, n, p_r, p_c, f, b, rb):
     assert np.abs(Qo.numpy().T - ref["Qo"]).max() < tol
     if m == n:
         assert np.abs(x.numpy() - ref["x"]).max() < tol * kappa * np.abs(ref["x"]).max()
+
+
+def _bench_line(*args):
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py")] + list(args),
+                         capture_output=True, text=True, timeout=600, cwd=root,
+                         env=dict(os.environ, RANK="0", WORLD_SIZE="1"))
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    return json.loads(lines[0])
+
+
+def test_reference_arm_prints_the_contract_line():
+    # the oracle arm (CPU): one JSON line with the GPU arm's metric, unit and config
+    line = _bench_line("--impl", "reference", "--steps", "1", "--warmup", "0")
+    cfg = bench.CONFIGS["c2"]
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == "TFLOP/s" and line["higher_is_better"] is True
+    assert line["config"] == bench.step_config(cfg, "3xtf32", True, 1)
+    assert line["steps"] == 1 and line["warmup"] == 0 and line["value"] > 0
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "TFLOP/s",
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_of_the_other_legs_says_unavailable():
+    line = _bench_line("--impl", "reference", "--config", "c4")
+    assert line["impl"] == "reference" and "unavailable" in line
