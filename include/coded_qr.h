@@ -21,6 +21,9 @@
  *    enqueued.  Errors detected on the device (pivot breakdown, a barrier wait that ran
  *    out) are recorded in a device status word and returned by coded_qr_sync_status and
  *    by coded_qr_run, which synchronise the stream.
+ *  - Threads: a handle is not internally locked.  Calls on one handle must come from one
+ *    host thread at a time (or be serialised by the caller); distinct handles are
+ *    independent and may be driven from different threads and streams.
  *  - State machine: create -> encode -> factor* -> [inject_erasure -> recover]* ->
  *    post_orth / solve.  factor runs panels in order and may be split into ranges
  *    (resume from any panel boundary).  Calls out of order return CQR_ESTATE.
