@@ -5,9 +5,13 @@ One step = the whole hot path on one synthetic problem: generator + checksum enc
 with ICGS panels on the encoded matrix (erasures injected at the start of seeded panels and
 recovered before they run), post-orthogonalisation and the solve.  Reported: coded GS-QR
 TFLOP/s (F_coded = 2 (m+c) n (n+2d) per step), the coding overhead against the uncoded GPU
-QR of the same matrix, and the errors ||A - Q_1 R|| / ||A||, ||I - Qo^T Qo||.
+QR of the same matrix, and the errors ||A - Q_1 R|| / ||A||, ||I - Qo^T Qo||.  The default
+workload is the largest single-GPU configuration: 16384^2, kappa 1e4, grid 16 x 16, f = 4,
+b = 256, four simultaneous erasures, FP32 storage with 3xTF32 tensor-core products; beside
+it the line carries the same workload in the other precisions and the 4096^2 workload in
+FP64 on the GPU against the mixed-precision step.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config c2] [--mode 3xtf32|tf32|f32|f64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config c3] [--mode 3xtf32|tf32|f32|f64]
   python bench.py --impl reference ...     (the FP64 CPU oracle on the host cores)
 """
 import argparse
@@ -31,9 +35,11 @@ CONFIGS = {
                per_panel=1),
     "c2k6": dict(m=4096, n=4096, p_r=8, p_c=8, f=2, b=128, kappa=1e6, seed=2, erasure_panels=2,
                  per_panel=1),
-    # 16384 x 16384, kappa 1e4; grid 16 x 16, f = 4, b = 256; four simultaneous erasures
+    # 16384 x 16384, kappa 1e4; grid 16 x 16, f = 4, b = 256; four simultaneous erasures (the
+    # input drawn on the device: the host construction takes minutes at this size); the
+    # reference arm's step is the oracle's encode + panel 0 over the next ref_cols columns
     "c3": dict(m=16384, n=16384, p_r=16, p_c=16, f=4, b=256, kappa=1e4, seed=3, erasure_panels=1,
-               per_panel=4),
+               per_panel=4, device_input=True, ref_cols=2048),
     "c1": dict(m=256, n=256, p_r=4, p_c=4, f=1, b=32, kappa=0, seed=1, erasure_panels=1,
                per_panel=1),
 }
@@ -321,23 +327,77 @@ def oracle_sample(cfg, A, budget_s, max_panels=None):
     return flops / dt / 1e12, cores, sample, dt
 
 
+def oracle_panel_sample(cfg, A, cols):
+    """One bounded step of the FP64 oracle: encode of the whole matrix, then panel 0 (ICGS)
+    with its trailing update restricted to the first `cols` columns right of it (the coded
+    matrix's leading b + cols columns, factored as a problem of their own).  Returns
+    (TFLOP/s, cores, sample, seconds)."""
+    from oracle import oracle as O
+    m, n, p_r, p_c, f, b = (cfg[k] for k in ("m", "n", "p_r", "p_c", "f", "b"))
+    g = O.geom(m, n, p_r, p_c, f)
+    Gt, Gh = O.generator(f, p_r, p_c, cfg["seed"])
+    t0 = time.perf_counter()
+    Q = O.encode(g, Gt, Gh, A)
+    k = min(b + cols, g.N)
+    Qs = Q[:, :k]                       # leading columns of a Fortran array: contiguous
+    Rs = np.zeros((k, k), order="F")
+    O.factor(Qs, Rs, k, b, 0, 1)
+    dt = time.perf_counter() - t0
+    flops = 4.0 * g.M * b * (k - b) + 4.0 * g.M * b * b
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = ("FP64 oracle: encode of the %dx%d coded problem + panel 0 with its trailing update "
+              "over the next %d columns (%.1f GFLOP), %.1f s" % (m, n, k - b, flops / 1e9, dt))
+    return flops / dt / 1e12, cores, sample, dt
+
+
+def host_inputs(cfg, seed):
+    """(A FP64 Fortran-ordered, y) on the host for workloads without a device generator."""
+    return make_inputs(dict(cfg, seed=seed))
+
+
+def device_inputs(cfg, seed, torch):
+    """A (FP32, column-major, on the current device) from the seeded device generator, and its
+    FP64 host copy (the bytes the oracle and the host-buffer path see)."""
+    from paper_2311_11943_gb300 import synth
+    A32 = synth.kappa_matrix_torch(cfg["m"], cfg["n"], cfg["kappa"], seed)
+    A_np = A32.double().cpu().numpy()
+    assert A_np.flags.f_contiguous
+    return A32, A_np
+
+
 def run_reference(args, cfg):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
-    A, _ = make_inputs(cfg)
+    if cfg.get("device_input"):
+        # input generation only (not timed): the seeded device generator of the GPU arm, on the
+        # GPU when there is one; the oracle itself runs on the host cores
+        import torch
+        if torch.cuda.is_available():
+            A32, A = device_inputs(cfg, cfg["seed"], torch)
+            del A32
+            torch.cuda.empty_cache()
+        else:
+            from paper_2311_11943_gb300 import synth
+            A = synth.kappa_matrix_torch(cfg["m"], cfg["n"], cfg["kappa"], cfg["seed"],
+                                         device="cpu").double().numpy()
+    else:
+        A, _ = make_inputs(cfg)
     vals = []
     sample = ""
     cores = 1
     for it in range(args.warmup + args.steps):
-        v, cores, sample, dt = oracle_sample(cfg, A, budget_s=1e9, max_panels=1)
+        if cfg.get("ref_cols"):
+            v, cores, sample, dt = oracle_panel_sample(cfg, A, cfg["ref_cols"])
+        else:
+            v, cores, sample, dt = oracle_sample(cfg, A, budget_s=1e9, max_panels=1)
         if it >= args.warmup:
             vals.append((v, dt))
     value = statistics.mean(v for v, _ in vals)
     ms = statistics.mean(dt for _, dt in vals) * 1e3
     # the same metric and config as the GPU arm's line; each step times a bounded sample of
-    # the workload (encode + panel 0 of the coded problem), described in cpu_baseline.sample
+    # the workload, described in cpu_baseline.sample
     line = {"metric": METRIC, "value": value,
             "unit": "TFLOP/s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -353,6 +413,69 @@ def run_reference(args, cfg):
 
 
 # ------------------------------------------------------------------------ GPU leg
+def measure_peaks_here(torch):
+    """TF32 and FP64 dense matmul rates of this GPU, measured in the run by the same torch
+    method as the driver's bf16 figures: torch.matmul, best of 10 (burst) and back to back for
+    about two seconds (sustained, TF32 only), CUDA events."""
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dt, n, tf32 in (("tf32", torch.float32, 8192, True),
+                                  ("fp64", torch.float64, 4096, False)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, device="cuda", dtype=dt)
+            b = torch.randn(n, n, device="cuda", dtype=dt)
+            c = torch.empty(n, n, device="cuda", dtype=dt)
+            for _ in range(3):
+                torch.matmul(a, b, out=c)
+            best = float("inf")
+            for _ in range(10):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[name + "_tflops"] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+            if tf32:
+                reps = max(1, int(2000.0 / best))
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    torch.matmul(a, b, out=c)
+                e1.record()
+                e1.synchronize()
+                out[name + "_tflops_sustained"] = 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    out["how"] = ("torch.matmul 8192^3 TF32 (allow_tf32) and 4096^3 FP64: best of 10 (burst); TF32 "
+                  "also back to back for ~2 s (sustained); CUDA events; this run")
+    return out
+
+
+def sampled_errors(A64, Qt, Rt, Qo, m, n, cols=1024, seed=0):
+    """Backward error and orthogonality estimated on a seeded sample of `cols` columns (for the
+    legs beside the headline, where the full FP64 Gram matrices would take seconds each):
+    |A[:,S] - Q_1 R_1[:,S]|_F / |A[:,S]|_F, max |I - Q[:,S]^T Q[:,S]| for the coded Q and the
+    post-orthogonalised Q."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    S = torch.randperm(n, generator=g)[:min(cols, n)].sort().values.to(A64.device)
+    As = A64[:, S]
+    back = (torch.linalg.norm(As - Qt[:m, :n].double() @ Rt[:n, :n].double()[:, S]) /
+            torch.linalg.norm(As)).item()
+    eye = torch.eye(S.numel(), device=A64.device, dtype=torch.float64)
+    Qs = Qt[:, S].double()
+    oc = (Qs.T @ Qs - eye).abs().max().item()
+    Qos = Qo[:, S].double()
+    oo = (Qos.T @ Qos - eye).abs().max().item()
+    return {"backward_rel_fro": back, "orth_max_coded_Q": oc, "orth_max_post_orth": oo,
+            "how": "sampled: %d seeded columns" % S.numel()}
+
+
 def run_ours(args, cfg):
     import torch
     import torch.distributed as dist
@@ -365,36 +488,42 @@ def run_ours(args, cfg):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_2311_11943_gb300 import binding as B
+    from paper_2311_11943_gb300 import replicas
 
     dtype, mma = MODES[args.mode]
     td = torch.float64 if dtype == "f64" else torch.float32
     es = 8 if dtype == "f64" else 4
     m, n, p_r, p_c, f, b = (cfg[k] for k in ("m", "n", "p_r", "p_c", "f", "b"))
-    A_np, y_np = make_inputs(cfg)
+    # every rank factorises its own draw of the recipe (replicas of one coded QR)
+    seed_r = replicas.rank_seed(cfg["seed"], rank)
+    if cfg.get("device_input"):
+        A_dev, A_np = device_inputs(cfg, seed_r, torch)
+        Ad = B.colmajor_empty(m, n, td)
+        Ad.copy_(A_dev)
+        del A_dev
+    else:
+        A_np, _ = host_inputs(cfg, seed_r)
+        Ad = B.colmajor_empty(m, n, td)
+        Ad.copy_(torch.from_numpy(np.ascontiguousarray(A_np)))
+    from paper_2311_11943_gb300 import synth
+    y_np = synth.rhs(m, 1, seed_r)
+    yd = B.colmajor_empty(m, 1, td)
+    yd.copy_(torch.from_numpy(np.ascontiguousarray(y_np)))
+    xd = B.colmajor_empty(n, 1, td)
     plan = erasure_plan(cfg)
     stream = torch.cuda.current_stream()
-
-    def dev_colmajor(X):
-        d = B.colmajor_empty(X.shape[0], X.shape[1], td)
-        d.copy_(torch.from_numpy(np.ascontiguousarray(X)))
-        return d
-
-    Ad, yd = dev_colmajor(A_np), dev_colmajor(y_np)
-    xd = B.colmajor_empty(n, 1, td)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def step(q, with_plan):
-        coded_step(q, Ad, yd, xd, plan if with_plan else [])
-
-    def timed(q, with_plan, steps, warmup, profile=False):
+    def timed(q, with_plan, steps, warmup, profile=False, sync_ranks=True):
+        pl = plan if with_plan else []
         for _ in range(warmup):
-            step(q, with_plan)
+            coded_step(q, Ad, yd, xd, pl)
         torch.cuda.synchronize()
         if profile:
             q.profile(True)
             q.profile_read(reset=True)
         times = []
-        if world > 1:
+        if world > 1 and sync_ranks:
             dist.barrier()
         torch.cuda.synchronize()
         for _ in range(steps):
@@ -402,7 +531,7 @@ def run_ours(args, cfg):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            step(q, with_plan)
+            coded_step(q, Ad, yd, xd, pl)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -414,6 +543,19 @@ def run_ours(args, cfg):
         if st != 0:
             raise RuntimeError("device status %d (%s)" % (st, B.errstr(st)))
         return times, prof
+
+    def factor_untimed(q):
+        """One more (untimed) factorisation with the plan, one panel per call; returns the
+        coded factors before post-orthogonalisation."""
+        q.encode(Ad)
+        T = q.geo["panels"]
+        for t in range(T):
+            tiles = [(i, j) for (tt, i, j) in plan if tt == t]
+            if tiles:
+                q.inject(tiles)
+                q.recover()
+            q.factor(t, t + 1)
+        return q.factors()
 
     rb = not args.no_reorth_block
     q = B.CodedQR(m, n, p_r, p_c, f, b, dtype=dtype, mma=mma, seed=cfg["seed"], stream=stream,
@@ -434,33 +576,31 @@ def run_ours(args, cfg):
     t_unc, _ = timed(q0, False, args.steps, max(1, args.warmup))
     q0.close()
 
-    # errors of one more (untimed) run: factors before post-orthogonalisation
-    q.encode(Ad)
-    T = q.geo["panels"]
-    t = 0
-    while t < T:
-        tiles = [(i, j) for (tt, i, j) in plan if tt == t]
-        if tiles:
-            q.inject(tiles)
-            q.recover()
-        q.factor(t, t + 1)
-        t += 1
-    Qc, Rc = q.factors()
+    # errors of one more (untimed) run, in FP64 over the whole factors
+    Qc, Rc = factor_untimed(q)
+    A64 = torch.from_numpy(A_np).to(dev)
+    M = q.geo["M"]
     Q1 = Qc[:m, :n].double()
     R1 = Rc[:n, :n].double()
-    Qt64 = Qc[: q.geo["M"], :n].double()
-    orth_coded = (torch.eye(n, device=dev, dtype=torch.float64) - Qt64.T @ Qt64).abs().max().item()
-    del Qt64
-    A64 = torch.from_numpy(A_np).to(dev)
     berr = (torch.linalg.norm(A64 - Q1 @ R1) / torch.linalg.norm(A64)).item()
+    del Q1, R1
+    Qt64 = Qc[:M, :n].double()
+    orth_coded = (Qt64.T @ Qt64 - torch.eye(n, device=dev, dtype=torch.float64)).abs().max().item()
+    Gt_np, _ = q.generator()
+    Gv = torch.kron(torch.from_numpy(Gt_np), torch.eye(q.geo["mb"], dtype=torch.float64)).to(dev)
+    drift = (Qt64[q.geo["m_pad"]:M] - Gv @ Qt64[:q.geo["m_pad"]]).abs().max().item()
+    del Qt64, Gv
     Qo = B.colmajor_empty(q.geo["m_pad"], n, td)
     q.post_orth(Qo)
     Qo64 = Qo.double()
-    orth = (torch.eye(n, device=dev, dtype=torch.float64) - Qo64.T @ Qo64).abs().max().item()
+    orth = (Qo64.T @ Qo64 - torch.eye(n, device=dev, dtype=torch.float64)).abs().max().item()
+    del Qo64, Qo
     q.solve(yd, xd)
     x64 = xd.double()
     y64 = torch.from_numpy(y_np).to(dev)
     resid = (torch.linalg.norm(A64 @ x64 - y64) / torch.linalg.norm(y64)).item()
+    del A64
+    torch.cuda.empty_cache()
 
     # end to end through the public one-call API with host buffers (pinned)
     A_pin = torch.empty((n, m), dtype=td, pin_memory=True)
@@ -480,76 +620,42 @@ def run_ours(args, cfg):
         t0 = time.perf_counter()
         q.run(A_host, y_host, x_host, plan=plan, host=True)
         e2e_times.append((time.perf_counter() - t0) * 1e3)
+    geo = dict(q.geo)
     q.close()
+    del A_pin
 
     F = coded_flops(m, n, p_r, p_c, f, b)
     ms = statistics.mean(t_coded)
     ms_unc = statistics.mean(t_unc)
     ms_e2e = statistics.mean(e2e_times)
-    from paper_2311_11943_gb300 import replicas
     ms, ms_unc, ms_e2e = replicas.max_over_ranks([ms, ms_unc, ms_e2e], dist if world > 1 else None,
                                                  device=dev)
     value = replicas.job_throughput(F, world, ms)
     e2e_value = replicas.job_throughput(F, world, ms_e2e)
-
-    # roofline of the dominant kernel (largest share of device time in the profiled steps)
-    peaks, peak_src = measured_peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_launches) = dom[0], dom[1]
-    M = q.geo["M"]
-    N = q.geo["N"]
-    T = q.geo["panels"]
-    gemm_flops = sum(2.0 * M * min(b, n - t * b) * (N - t * b - min(b, n - t * b))
-                     for t in range(T) if t * b + min(b, n - t * b) < N)
-    panel_bytes = sum(2.0 * M * min(b, n - t * b) * es for t in range(T))
-    if dom_name in ("gemm_rbar_simt", "gemm_update_simt", "tc_rbar", "tc_update"):
-        per_class = {"tc_update": 1.0, "tc_rbar": 1.0, "gemm_rbar_simt": 1.0, "gemm_update_simt": 1.0}
-        algo = gemm_flops * per_class[dom_name] * args.steps / dom_launches
-        achieved = algo / (dom_ms / dom_launches * 1e-3) / 1e12
-        if dtype == "f64":
-            peak = 152 * 2 * 2 * 2.07e9 / 1e12
-            rl = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "FP64 CUDA-core: 152 SMs x 2 "
-                  "DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)"}
-        elif mma == "simt":
-            peak = 152 * 128 * 2 * 2.07e9 / 1e12
-            rl = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "FP32 CUDA-core: 152 SMs x "
-                  "128 FFMA/clk x 2 flop x 2.07 GHz"}
-        elif mma in ("bf16", "bf16x3"):
-            peak = peaks["bf16_tflops_sustained"]
-            rl = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": "%s bf16 sustained"
-                  % peak_src}
-        else:
-            peak = peaks["bf16_tflops_sustained"] * 1.1 / 2.25
-            rl = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": "%s bf16 sustained x "
-                  "nominal tf32/bf16 ratio 1.1/2.25" % peak_src}
-        rl.update(achieved=achieved, peak=peak, frac=achieved / peak)
-    else:
-        if dom_name == "panel_icgs":
-            algo = panel_bytes * args.steps / dom_launches
-        else:
-            algo = None
-        dur = dom_ms / dom_launches * 1e-3
-        achieved = (algo / dur / 1e9) if algo else None
-        peak = peaks["hbm_gbs"]
-        rl = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak,
-              "frac": (achieved / peak) if achieved else None,
-              "peak_source": "%s copy bandwidth" % peak_src}
-    rl.update(kernel=dom_name, launches_per_step=dom_launches / args.steps,
-              avg_launch_ms=dom_ms / dom_launches,
-              traffic=NCU_TRAFFIC.get((args.config, args.mode, dom_name)))
     launches = int(sum(v[1] for v in prof.values()) / args.steps)
 
+    peaks_here = None
+    legs = None
     cpu = None
     blas3 = None
+    if rank == 0:
+        peaks_here = measure_peaks_here(torch)
+        if not args.no_legs:
+            legs = extra_legs(args, cfg, torch, B, Ad, A_np, yd, xd, flush, stream)
+    rl = roofline(args, cfg, prof, geo, dtype, mma, es, peaks_here)
+
     if rank == 0 and not args.no_cpu_baseline:
         os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
         v, cores, sample, _ = oracle_sample(cfg, A_np, budget_s=args.cpu_budget)
         cpu = {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample}
-        if not args.no_blas3:
+        if not args.no_blas3 and F <= 1e12:
             try:
                 blas3 = blas3_baseline(cfg, A_np, y_np, rb)
             except Exception as e:  # context only: recorded in the line, not fatal to it
                 blas3 = {"error": "%s: %s" % (type(e).__name__, e)}
+        elif not args.no_blas3:
+            blas3 = {"skipped": "the BLAS-3 CPU baseline runs whole steps; at %.2g flops per step "
+                     "it would take minutes on the host cores" % F}
 
     if rank == 0:
         line = {
@@ -557,11 +663,10 @@ def run_ours(args, cfg):
             "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"f64": "f64", "f32": "f32", "tf32": "f32 storage, tf32 tensor-core GEMMs",
-                      "3xtf32": "f32 storage, 3xtf32 tensor-core GEMMs",
-                      "bf16": "f32 storage, bf16 tensor-core GEMMs",
-                      "bf16x3": "f32 storage, bf16x3 tensor-core GEMMs"}[args.mode],
-            "data": "synthetic (seeded U diag(sigma) V^T / N(0,1), generated on the host)",
+            "dtype": DTYPE_NAMES[args.mode],
+            "data": ("synthetic (seeded U diag(sigma) V^T drawn on the device in FP32, seed %d + "
+                     "7919 x rank)" % cfg["seed"]) if cfg.get("device_input") else
+                    "synthetic (seeded U diag(sigma) V^T / N(0,1), generated on the host)",
             "config": step_config(cfg, args.mode, rb, world),
             "coded_flops_per_step": F,
             "uncoded": {"ms_per_step": ms_unc, "tflops_uncoded_equiv": 2.0 * m * n * n /
@@ -569,7 +674,8 @@ def run_ours(args, cfg):
             "coding_overhead": ms / ms_unc - 1.0,
             "flop_model_overhead_floor": F / (2.0 * m * n * n) - 1.0,
             "errors": {"backward_rel_fro": berr, "orth_max_coded_Q": orth_coded,
-                       "orth_max_post_orth": orth, "solve_rel_residual": resid},
+                       "orth_max_post_orth": orth, "checksum_drift_max": drift,
+                       "solve_rel_residual": resid, "how": "FP64 over the whole factors"},
             "reorth_per_step": stats["n_reorth"] / max(1, (2 * args.steps + args.warmup)),
             "recovered_tiles_per_step": len(plan),
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1] or v[0] > 0},
@@ -577,6 +683,8 @@ def run_ours(args, cfg):
             "gpu_launches": launches,
             "clocks": clk,
             "roofline": rl,
+            "peaks_measured_here": peaks_here,
+            "legs": legs,
             "cpu_baseline": cpu,
             "cpu_blas3": blas3,
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "ms_per_step": ms_e2e,
@@ -587,6 +695,182 @@ def run_ours(args, cfg):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+DTYPE_NAMES = {"f64": "f64", "f32": "f32", "tf32": "f32 storage, tf32 tensor-core GEMMs",
+               "3xtf32": "f32 storage, 3xtf32 tensor-core GEMMs",
+               "bf16": "f32 storage, bf16 tensor-core GEMMs",
+               "bf16x3": "f32 storage, bf16x3 tensor-core GEMMs"}
+
+
+def roofline(args, cfg, prof, geo, dtype, mma, es, peaks_here):
+    """Roofline of the dominant kernel class (largest share of device time in the profiled
+    steps): algorithmic work per launch / average launch duration, against the measured peak
+    of its bound."""
+    peaks, peak_src = measured_peaks()
+    m, n, b = cfg["m"], cfg["n"], cfg["b"]
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_launches) = dom[0], dom[1]
+    M, N, T = geo["M"], geo["N"], geo["panels"]
+    widths = [(min(b, n - t * b), N - t * b - min(b, n - t * b)) for t in range(T)]
+    gemm_flops = sum(2.0 * M * bk * w for bk, w in widths if w > 0)
+    reorth_flops = sum(4.0 * M * (t * b) * bk for t, (bk, _) in enumerate(widths))
+    panel_bytes = sum(2.0 * M * bk * es for bk, _ in widths)
+    per_step = {"tc_update": gemm_flops, "tc_rbar": gemm_flops, "gemm_rbar_simt": gemm_flops,
+                "gemm_update_simt": gemm_flops, "block_reorth": reorth_flops}
+    if dom_name in per_step:
+        algo = per_step[dom_name] * args.steps / dom_launches
+        achieved = algo / (dom_ms / dom_launches * 1e-3) / 1e12
+        tf32 = (peaks_here or {}).get("tf32_tflops_sustained")
+        if dtype == "f64":
+            fp64 = (peaks_here or {}).get("fp64_tflops")
+            peak = fp64 or 152 * 2 * 2 * 2.07e9 / 1e12
+            rl = {"bound": "alu", "unit": "TFLOP/s", "peak_source":
+                  "FP64 torch.matmul measured in this run" if fp64 else
+                  "FP64 CUDA-core: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+        elif mma == "simt":
+            peak = 152 * 128 * 2 * 2.07e9 / 1e12
+            rl = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "FP32 CUDA-core: 152 SMs x "
+                  "128 FFMA/clk x 2 flop x 2.07 GHz"}
+        elif mma in ("bf16", "bf16x3"):
+            k = 3.0 if mma == "bf16x3" else 1.0
+            peak = peaks["bf16_tflops_sustained"] / k
+            rl = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": "%s bf16 sustained%s"
+                  % (peak_src, " / 3 (three bf16 MMAs per FP32-accurate product)" if k > 1 else "")}
+        else:
+            k = 3.0 if mma == "3xtf32" else 1.0
+            if tf32:
+                peak = tf32 / k
+                src = "tf32 sustained measured in this run"
+            else:
+                peak = peaks["bf16_tflops_sustained"] * 1.1 / 2.25 / k
+                src = "%s bf16 sustained x nominal tf32/bf16 ratio 1.1/2.25" % peak_src
+            rl = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": src + (
+                  " / 3 (three tf32 MMAs per FP32-accurate product)" if k > 1 else "")}
+            rl["tensor_pipe_frac"] = achieved * k / (peak * k)
+        rl.update(achieved=achieved, peak=peak, frac=achieved / peak)
+    else:
+        algo = panel_bytes * args.steps / dom_launches if dom_name == "panel_icgs" else None
+        dur = dom_ms / dom_launches * 1e-3
+        achieved = (algo / dur / 1e9) if algo else None
+        peak = peaks["hbm_gbs"]
+        rl = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak,
+              "frac": (achieved / peak) if achieved else None,
+              "peak_source": "%s copy bandwidth" % peak_src}
+    rl.update(kernel=dom_name, launches_per_step=dom_launches / args.steps,
+              avg_launch_ms=dom_ms / dom_launches,
+              traffic=NCU_TRAFFIC.get((args.config, args.mode, dom_name)))
+    return rl
+
+
+def extra_legs(args, cfg, torch, B, Ad, A_np, yd, xd, flush, stream):
+    """Legs beside the headline, on rank 0 (untimed for `value`):
+    modes: the same workload with the other tensor-core precisions of the configuration
+           (TF32 and BF16 with one product, BF16x3), errors on sampled columns;
+    fp64_vs_mixed: the C2 workload (4096^2, kappa 1e2) in FP64 on the GPU (the paper's
+           arithmetic) and in FP32 with 3xTF32 products, same step, full FP64 errors."""
+    out = {}
+    steps = max(1, min(args.steps, 5))
+    warm = max(1, min(args.warmup, 3))
+    m, n, p_r, p_c, f, b = (cfg[k] for k in ("m", "n", "p_r", "p_c", "f", "b"))
+    plan = erasure_plan(cfg)
+    rb = not args.no_reorth_block
+
+    def time_q(q, Ad_, yd_, xd_, pl, st, wu):
+        for _ in range(wu):
+            coded_step(q, Ad_, yd_, xd_, pl)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(st):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            coded_step(q, Ad_, yd_, xd_, pl)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        s = q.sync_status()
+        if s != 0:
+            raise RuntimeError("device status %d (%s)" % (s, B.errstr(s)))
+        return statistics.mean(ts)
+
+    def factored(q, Ad_, pl):
+        q.encode(Ad_)
+        for t in range(q.geo["panels"]):
+            tiles = [(i, j) for (tt, i, j) in pl if tt == t]
+            if tiles:
+                q.inject(tiles)
+                q.recover()
+            q.factor(t, t + 1)
+        Qc, Rc = q.factors()
+        Qo = B.colmajor_empty(q.geo["m_pad"], Qc.shape[1], Qc.dtype)
+        q.post_orth(Qo)
+        return Qc, Rc, Qo
+
+    F = coded_flops(m, n, p_r, p_c, f, b)
+    if args.mode in ("3xtf32", "tf32", "bf16", "bf16x3"):
+        A64 = torch.from_numpy(A_np).cuda()
+        rows = {}
+        for mode in ("tf32", "bf16", "bf16x3"):
+            if mode == args.mode:
+                continue
+            try:
+                q = B.CodedQR(m, n, p_r, p_c, f, b, dtype="f32", mma=MODES[mode][1],
+                              seed=cfg["seed"], stream=stream, reorth_block=rb)
+                ms = time_q(q, Ad, yd, xd, plan, steps, warm)
+                Qc, Rc, Qo = factored(q, Ad, plan)
+                err = sampled_errors(A64, Qc[:q.geo["M"]], Rc, Qo, m, n)
+                q.close()
+                rows[mode] = {"ms_per_step": ms, "tflops": F / (ms * 1e-3) / 1e12,
+                              "errors": err, "steps": steps}
+            except Exception as e:  # recorded, not fatal to the headline
+                rows[mode] = {"error": "%s: %s" % (type(e).__name__, e)}
+        del A64
+        torch.cuda.empty_cache()
+        out["modes"] = rows
+    # FP64 on the GPU against the mixed-precision step on the C2 workload
+    c2 = CONFIGS["c2"]
+    A2, y2 = make_inputs(c2)
+    plan2 = erasure_plan(c2)
+    F2 = coded_flops(c2["m"], c2["n"], c2["p_r"], c2["p_c"], c2["f"], c2["b"])
+    rows = {}
+    for label, mode, rb2 in (("f64", "f64", False), ("f64_block_reorth", "f64", True),
+                             ("3xtf32_block_reorth", "3xtf32", True)):
+        dt_, mma_ = MODES[mode]
+        tdd = torch.float64 if dt_ == "f64" else torch.float32
+        try:
+            A2d = B.colmajor_empty(c2["m"], c2["n"], tdd)
+            A2d.copy_(torch.from_numpy(np.ascontiguousarray(A2)))
+            y2d = B.colmajor_empty(c2["m"], 1, tdd)
+            y2d.copy_(torch.from_numpy(np.ascontiguousarray(y2)))
+            x2d = B.colmajor_empty(c2["n"], 1, tdd)
+            q = B.CodedQR(c2["m"], c2["n"], c2["p_r"], c2["p_c"], c2["f"], c2["b"], dtype=dt_,
+                          mma=mma_, seed=c2["seed"], stream=stream, reorth_block=rb2)
+            st_ = steps if dt_ == "f64" else max(steps, 10)
+            ms = time_q(q, A2d, y2d, x2d, plan2, st_, warm)
+            Qc, Rc, Qo = factored(q, A2d, plan2)
+            A64 = torch.from_numpy(A2).cuda()
+            nn = c2["n"]
+            Qt = Qc[:q.geo["M"], :nn].double()
+            eye = torch.eye(nn, device="cuda", dtype=torch.float64)
+            err = {"backward_rel_fro": (torch.linalg.norm(A64 - Qc[:c2["m"], :nn].double() @
+                                                          Rc[:nn, :nn].double()) /
+                                        torch.linalg.norm(A64)).item(),
+                   "orth_max_coded_Q": (Qt.T @ Qt - eye).abs().max().item(),
+                   "orth_max_post_orth": (Qo.double().T @ Qo.double() - eye).abs().max().item()}
+            q.close()
+            rows[label] = {"ms_per_step": ms, "tflops": F2 / (ms * 1e-3) / 1e12, "errors": err,
+                           "steps": st_}
+        except Exception as e:
+            rows[label] = {"error": "%s: %s" % (type(e).__name__, e)}
+    if "ms_per_step" in rows.get("3xtf32_block_reorth", {}):
+        best64 = min((rows[k]["ms_per_step"] for k in ("f64", "f64_block_reorth")
+                      if "ms_per_step" in rows.get(k, {})), default=None)
+        if best64:
+            rows["mixed_speedup_vs_fastest_f64"] = best64 / rows["3xtf32_block_reorth"]["ms_per_step"]
+    out["fp64_vs_mixed_c2"] = {"workload": workload_name(c2, "f64 / 3xtf32"), "rows": rows}
+    return out
 
 
 # ------------------------------------------------------------------------ c4: batched
@@ -1066,20 +1350,22 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS) + sorted(EXTRA))
+    ap.add_argument("--config", default="c3", choices=sorted(CONFIGS) + sorted(EXTRA))
     ap.add_argument("--mode", default=os.environ.get("CQR_BENCH_MODE", "3xtf32"),
                     choices=sorted(MODES))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-blas3", action="store_true",
                     help="skip the torch CPU BLAS-3 baseline beside the oracle")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the legs beside the headline (other precisions, FP64 vs mixed)")
     ap.add_argument("--no-reorth-block", action="store_true",
                     help="skip the block reorthogonalisation pass (faster, orthogonality ~ u kappa)")
     args = ap.parse_args()
     if args.config in EXTRA:
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the "
-                              "oracle on the c2 workload only"}))
+                              "oracle on the single-problem workloads (c1, c2, c2k6, c3) only"}))
             return 0
         if args.config == "e1":
             return run_mds(args)

@@ -204,6 +204,13 @@ cqr_status coded_qr_post_orth(cqr_handle h, void* Q, int64_t ldq, const void* y,
 cqr_status coded_qr_solve(cqr_handle h, const void* y, int64_t ldy, void* x, int64_t ldx,
                           int32_t nrhs);
 
+/* a9 under the name of the method's problem statement, min |A x - y| (Section 4.1 for square
+ * A; for tall A the least-squares reading through A = Q_1 R of Corollary "final form").  The
+ * same call as coded_qr_solve: the same arguments, layout, ownership and errors, and the same
+ * result bit for bit. */
+cqr_status coded_qr_solve_ls(cqr_handle h, const void* y, int64_t ldy, void* x, int64_t ldx,
+                             int32_t nrhs);
+
 /* The whole hot path in one call: encode, factor with the erasure plan applied, post_orth
  * (in place) and solve.  plan (host) holds plan_len triples (panel, i, j): node (i, j) is
  * erased at the start of that panel and recovered before it runs.  With
@@ -250,23 +257,29 @@ cqr_status coded_qr_profile_read(cqr_handle h, double* ms, int64_t* launches, in
 const char* coded_qr_profile_name(int32_t cls);
 
 /* Allocation-free panel factorisation (the paper has no counterpart: this is a deployment
- * aid).  Some callers cannot call cudaMalloc where they need a panel factored -- work
- * recorded into a CUDA graph, a caching allocator that must not be re-entered, or a host
- * that has handed every byte of device memory to another framework.  This call factors one
- * panel exactly like coded_qr_factor's panel step (ICGS, one reduction per column), but its
- * scratch (partial sums, barrier counter, status word) lives in a fixed device array of
- * 1,311,232 bytes inside the library, which every GPU that loads the library holds until the
- * process exits; nothing is allocated.
+ * aid).  Some callers cannot call cudaMalloc where they need a panel factored: a caching
+ * allocator that must not be re-entered from inside its own callbacks, a host that has handed
+ * every byte of device memory to another framework, or a latency-critical path that must not
+ * take the driver's allocation lock (cudaMalloc can synchronise the device).  This call runs
+ * the same ICGS algorithm as coded_qr_factor's panel step (one reduction per column, the same
+ * reorthogonalisation criterion) on the grid-barrier panel kernel; the handle's panel step
+ * may pick a register or cluster kernel that sums in another order, so the two agree to
+ * rounding, not bit for bit.  Its scratch (partial sums, barrier counter, status word) lives
+ * in a fixed device array of 1,311,232 bytes inside the library, which every GPU that loads
+ * the library holds until the process exits; nothing is allocated.
  *   Q:  M x bk panel (device, column-major, ld ldq >= M), orthonormalised in place;
  *   R:  bk x bk (device, ld ldr >= bk): receives the upper triangle (caller zeroes it first);
  *   tau: reorthogonalisation criterion as cqr_config.tau; status: optional device int[4]
  *   that receives the device-side status word (CQR_EBREAKDOWN, CQR_ETIMEOUT), else NULL.
- * Limits: bk <= 256 and the panel must fit at most 160 co-resident CTAs (M up to 160 x 1024
- * rows); larger sizes return CQR_EINVAL without launching anything.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) and caches it, so make
- * that first call before any stream capture.  All calls share the one array, and the array
- * keeps the previous call's contents: calls whose work overlaps on the GPU (different
- * streams, or several host threads) race and must be serialised by the caller. */
+ * Limits: bk <= 256 and M <= min(160, number of SMs) x 1024 rows (the panel must fit that
+ * many co-resident CTAs: 155,648 rows on a 152-SM GPU); larger sizes return CQR_EINVAL
+ * without launching anything.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current) and caches it for the life of the
+ * process, so make that first call before any stream capture; after cudaDeviceReset the
+ * cached address is stale and further calls in that process are not supported.  All calls
+ * share the one array, and the array keeps the previous call's contents (the call clears the
+ * barrier counter and the status word itself): calls whose work overlaps on the GPU
+ * (different streams, or several host threads) race and must be serialised by the caller. */
 cqr_status coded_qr_panel_icgs_noalloc(int32_t dtype, int64_t M, int32_t bk, void* Q, int64_t ldq,
                                        void* R, int64_t ldr, double tau, int32_t* status,
                                        void* stream);

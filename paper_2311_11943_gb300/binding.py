@@ -28,7 +28,8 @@ GEO_FIELDS = ["m", "n", "mb", "nb", "m_pad", "c", "d", "M", "N", "ldq", "ldr", "
 
 EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "coded_qr_destroy",
            "coded_qr_geometry", "coded_qr_encode", "coded_qr_factor", "coded_qr_inject_erasure",
-           "coded_qr_recover", "coded_qr_post_orth", "coded_qr_solve", "coded_qr_run",
+           "coded_qr_recover", "coded_qr_post_orth", "coded_qr_solve", "coded_qr_solve_ls",
+           "coded_qr_run",
            "coded_qr_get_factors", "coded_qr_get_generator", "coded_qr_get_decode_sets",
            "coded_qr_stats", "coded_qr_sync_status", "coded_qr_errstr", "coded_qr_profile",
            "coded_qr_profile_read", "coded_qr_profile_name", "coded_qr_panel_icgs_noalloc",
@@ -87,6 +88,7 @@ def lib():
             "coded_qr_recover": [vp, C.POINTER(i32)],
             "coded_qr_post_orth": [vp, vp, i64, vp, i64, vp, i64, i32],
             "coded_qr_solve": [vp, vp, i64, vp, i64, i32],
+            "coded_qr_solve_ls": [vp, vp, i64, vp, i64, i32],
             "coded_qr_run": [vp, vp, i64, vp, i64, vp, i64, i32, C.POINTER(i32), i32, u32],
             "coded_qr_get_factors": [vp, C.POINTER(vp), C.POINTER(i64), C.POINTER(vp),
                                      C.POINTER(i64)],
@@ -204,6 +206,10 @@ def coded_qr_post_orth(h, Q_ptr, ldq, y_ptr, ldy, yo_ptr, ldyo, nrhs):
 
 def coded_qr_solve(h, y_ptr, ldy, x_ptr, ldx, nrhs):
     return lib().coded_qr_solve(h, C.c_void_p(y_ptr), ldy, C.c_void_p(x_ptr), ldx, nrhs)
+
+
+def coded_qr_solve_ls(h, y_ptr, ldy, x_ptr, ldx, nrhs):
+    return lib().coded_qr_solve_ls(h, C.c_void_p(y_ptr), ldy, C.c_void_p(x_ptr), ldx, nrhs)
 
 
 def coded_qr_run(h, A_ptr, lda, y_ptr, ldy, x_ptr, ldx, nrhs, plan, flags=0):
@@ -510,6 +516,12 @@ class CodedQR:
         nrhs = 1 if y.dim() == 1 else y.shape[1]
         check(coded_qr_solve(self.h, y.data_ptr(), _ld(y), x.data_ptr(), _ld(x), nrhs),
               "coded_qr_solve")
+
+    def solve_ls(self, y, x):
+        """min |A x - y| through the coded factors (coded_qr_solve_ls)."""
+        nrhs = 1 if y.dim() == 1 else y.shape[1]
+        check(coded_qr_solve_ls(self.h, y.data_ptr(), _ld(y), x.data_ptr(), _ld(x), nrhs),
+              "coded_qr_solve_ls")
 
     def run(self, A, y=None, x=None, plan=(), host=False):
         nrhs = 0 if y is None else (1 if y.ndim == 1 else y.shape[1])

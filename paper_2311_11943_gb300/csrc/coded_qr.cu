@@ -969,6 +969,11 @@ cqr_status coded_qr_solve(cqr_handle h, const void* y, int64_t ldy, void* x, int
                      : solve_t<float>(h, (const float*)y, ldy, (float*)x, ldx, nrhs);
 }
 
+cqr_status coded_qr_solve_ls(cqr_handle h, const void* y, int64_t ldy, void* x, int64_t ldx,
+                             int32_t nrhs) {
+  return coded_qr_solve(h, y, ldy, x, ldx, nrhs);
+}
+
 cqr_status coded_qr_run(cqr_handle h, const void* A, int64_t lda, const void* y, int64_t ldy,
                         void* x, int64_t ldx, int32_t nrhs, const int32_t* plan,
                         int32_t plan_len, uint32_t flags) {

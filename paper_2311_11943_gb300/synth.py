@@ -31,6 +31,41 @@ def kappa_matrix(m, n, kappa, seed, dtype=np.float64):
     return np.asfortranarray(((U * sig[None, :]) @ V.T).astype(dtype))
 
 
+def kappa_matrix_torch(m, n, kappa, seed, device="cuda"):
+    """The recipe of kappa_matrix drawn with torch on `device` in FP32, for sizes where the
+    host construction takes minutes (16384^2: QR of two Gaussian matrices).  U (m x n,
+    orthonormal columns) and V (n x n) come from torch.linalg.qr of N(0,1) matrices drawn by
+    a torch.Generator seeded with `seed`, with the signs of R's diagonal folded in (Haar,
+    Mezzadri 2007); A = U diag(sigma) V^T with sigma_i = kappa^(-(i-1)/(n-1)), formed in full
+    FP32 (TF32 off).  The FP32 factors are orthogonal to about 1e-6, which perturbs sigma
+    multiplicatively by that much, so the 2-norm condition number stays kappa to about 1e-6
+    relative before the final FP32 rounding of A.  Returns a column-major FP32 tensor
+    (stride (1, m)) on `device`.  The same seed on the same device and library versions gives
+    the same bytes; the tests hand exactly those bytes to both the CUDA path and the oracle."""
+    import torch
+    gen = torch.Generator(device=device).manual_seed(int(seed))
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        Z = torch.randn(m, n, generator=gen, device=device, dtype=torch.float32)
+        U, Ru = torch.linalg.qr(Z)
+        U *= torch.sign(torch.diagonal(Ru))[None, :]
+        del Z, Ru
+        Z = torch.randn(n, n, generator=gen, device=device, dtype=torch.float32)
+        V, Rv = torch.linalg.qr(Z)
+        V *= torch.sign(torch.diagonal(Rv))[None, :]
+        del Z, Rv
+        sig = (kappa ** (-torch.arange(n, device=device, dtype=torch.float64)
+                         / max(n - 1, 1))).to(torch.float32)
+        U *= sig[None, :]
+        # column-major m x n: store A^T row-major, A = (U Sigma) V^T  <=>  A^T = V (U Sigma)^T
+        At = torch.matmul(V, U.t())
+        del U, V
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return At.t()
+
+
 def rhs(m, k, seed, dtype=np.float64):
     rng = np.random.default_rng(seed + 7919)
     y = rng.standard_normal((m, k)).astype(dtype)

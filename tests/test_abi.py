@@ -24,7 +24,7 @@ def _declared():
 def test_header_declares_the_hot_path():
     names = _declared()
     for verb in ("create", "destroy", "encode", "factor", "inject_erasure", "recover",
-                 "post_orth", "solve", "run", "get_generator", "get_decode_sets",
+                 "post_orth", "solve", "solve_ls", "run", "get_generator", "get_decode_sets",
                  "sync_status", "errstr"):
         assert "coded_qr_" + verb in names
 
@@ -39,6 +39,14 @@ def test_binding_names_match_header(libpath):
     from paper_2311_11943_gb300 import binding
     assert sorted(binding.EXPORTS) == _declared()
     binding.lib()
+
+
+def test_solve_ls_validates_like_solve_without_gpu(libpath):
+    # the least-squares verb under the problem statement's name takes the same arguments and
+    # rejects the same null handle before touching the device
+    from paper_2311_11943_gb300 import binding as B
+    assert B.coded_qr_solve_ls(None, 0, 1, 0, 1, 1) == B.CQR_EINVAL
+    assert B.coded_qr_solve(None, 0, 1, 0, 1, 1) == B.CQR_EINVAL
 
 
 def test_config_struct_layout(libpath):

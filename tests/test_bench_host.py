@@ -104,8 +104,9 @@ def _bench_line(*args):
 
 
 def test_reference_arm_prints_the_contract_line():
-    # the oracle arm (CPU): one JSON line with the GPU arm's metric, unit and config
-    line = _bench_line("--impl", "reference", "--steps", "1", "--warmup", "0")
+    # the oracle arm (CPU): one JSON line with the GPU arm's metric, unit and config (on the
+    # 4096^2 workload here: the default 16384^2 input is drawn on a GPU)
+    line = _bench_line("--impl", "reference", "--config", "c2", "--steps", "1", "--warmup", "0")
     cfg = bench.CONFIGS["c2"]
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC
     assert line["unit"] == "TFLOP/s" and line["higher_is_better"] is True
@@ -120,3 +121,38 @@ def test_reference_arm_prints_the_contract_line():
 def test_reference_arm_of_the_other_legs_says_unavailable():
     line = _bench_line("--impl", "reference", "--config", "c4")
     assert line["impl"] == "reference" and "unavailable" in line
+
+
+def test_reference_step_sample_is_panel_zero_of_the_workload():
+    # the bounded step of the reference arm on the largest workload: encode + panel 0 with its
+    # trailing update over the next `cols` columns; its R block equals the full problem's
+    # panel-0 R entries over those columns (the update of a column does not depend on the
+    # columns to its right)
+    cfg = dict(m=96, n=96, p_r=4, p_c=4, f=1, b=16, seed=2)
+    A = synth.gaussian(96, 96, 9)
+    v, cores, sample, dt = bench.oracle_panel_sample(cfg, A, 40)
+    assert v > 0 and cores >= 1 and "next 40 columns" in sample
+    g = O.geom(96, 96, 4, 4, 1)
+    Gt, Gh = O.generator(1, 4, 4, 2)
+    Q = O.encode(g, Gt, Gh, A)
+    R = np.zeros((g.N, g.N), order="F")
+    O.factor(Q, R, 96, 16, 0, 1)
+    Qs = O.encode(g, Gt, Gh, A)[:, :56]
+    Rs = np.zeros((56, 56), order="F")
+    O.factor(Qs, Rs, 56, 16, 0, 1)
+    assert np.allclose(Rs[:16, :56], R[:16, :56], rtol=0, atol=1e-13)
+    assert np.allclose(Qs, Q[:, :56], rtol=0, atol=1e-13)
+
+
+def test_default_workload_is_the_largest_configuration():
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--help"],
+                         capture_output=True, text=True, timeout=120, cwd=root)
+    assert out.returncode == 0
+    cfg = bench.CONFIGS["c3"]
+    assert (cfg["m"], cfg["n"], cfg["p_r"], cfg["f"], cfg["b"]) == (16384, 16384, 16, 4, 256)
+    assert cfg["device_input"] and cfg["erasure_panels"] * cfg["per_panel"] == 4
+    src = open(os.path.join(root, "bench.py")).read()
+    assert 'ap.add_argument("--config", default="c3"' in src

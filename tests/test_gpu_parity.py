@@ -628,9 +628,14 @@ def test_tall_least_squares(dtype, mma, shape):
             q.recover()
         q.factor(t, t + 1)
     x = B.colmajor_empty(n, 2, td)
-    q.solve(to_dev(y, td), x)
+    yd = to_dev(y, td)
+    q.solve(yd, x)
+    # the same verb under the problem statement's name gives the same x bit for bit
+    x_ls = B.colmajor_empty(n, 2, td)
+    q.solve_ls(yd, x_ls)
     torch.cuda.synchronize()
     assert q.sync_status() == 0
+    assert torch.equal(x, x_ls)
     q.close()
     x = to_np(x)
     xl, *_ = np.linalg.lstsq(A, y, rcond=None)

@@ -17,6 +17,24 @@ def test_kappa_matrix_has_the_stated_singular_values(m, n, kappa):
     assert not np.array_equal(A, synth.kappa_matrix(m, n, kappa, seed=4))
 
 
+@pytest.mark.parametrize("m,n,kappa", [(96, 64, 1e2), (300, 200, 1e4)])
+def test_device_kappa_matrix_has_the_stated_singular_values(m, n, kappa):
+    # the FP32 torch form of the recipe (used where the host construction takes minutes),
+    # run here on the CPU: column-major FP32, singular values kappa^(-(i-1)/(n-1)) to the FP32
+    # orthogonality of the factors (multiplicative, about 1e-6) plus the rounding of A (u |A|)
+    torch = pytest.importorskip("torch")
+    A = synth.kappa_matrix_torch(m, n, kappa, seed=3, device="cpu")
+    assert A.shape == (m, n) and A.stride() == (1, m) and A.dtype == torch.float32
+    s = np.linalg.svd(A.double().numpy(), compute_uv=False)
+    want = kappa ** (-np.arange(n) / (n - 1))
+    # Weyl: the rounding E of A moves each singular value by at most |E|_2 <= u |A|_F
+    u = 2.0 ** -24
+    assert (np.abs(s - want) <= 1e-5 * want + u * np.linalg.norm(want)).all()
+    assert abs(s[0] / s[-1] / kappa - 1) < 1e-3
+    assert torch.equal(A, synth.kappa_matrix_torch(m, n, kappa, seed=3, device="cpu"))
+    assert not torch.equal(A, synth.kappa_matrix_torch(m, n, kappa, seed=4, device="cpu"))
+
+
 def test_haar_orthogonal_is_orthogonal_and_sign_normalised():
     rng = np.random.default_rng(1)
     Q = synth.haar_orthogonal(50, rng)
