@@ -95,6 +95,9 @@ typedef struct {
                           vertical generator is the K x p_r structured matrix of Construction
                           in_node_qr, encoded conventionally (Remark alt_in_node); needs
                           2 K <= p_r and, with protect_r, p_c = p_r */
+  int32_t post_orth;   /* CQR_POST_ORTH_*: which form of the post-orthogonalisation (a8) the
+                          single-problem verbs apply */
+  int32_t reserved;    /* must be 0 */
   uint64_t seed;       /* seed of the generator's SplitMix64 stream */
   double tau;          /* ICGS criterion: reorthogonalise column j when its norm fell below
                           tau times its norm at the panel start.  0 selects 1/sqrt(2);
@@ -115,6 +118,21 @@ enum {
   CQR_PANEL_CGS1 = 2,
   CQR_PANEL_CGS2 = 3
 };
+
+/* Post-orthogonalisation forms (a8).  G0 is the paper's Qo = G_0 Q_1 (Theorem "G_0", the
+ * sparse block pipeline of the overhead proof).  PROJECTED is Qo = G_0^{-1} (Q_1 + G^T Q_2),
+ * G = G~ (x) I_mb: G_0 applied to the orthogonal projection of the coded Q's columns onto the
+ * range {[x; G x]} of the encoding (G_0^2 = I + G^T G, G_0 symmetric).  It equals G_0 Q_1
+ * whenever the checksum rows satisfy Q_2 = G Q_1 (Lemma "2way_checksum"), so in exact
+ * arithmetic it is the paper's matrix; in floating point, where Q_2 drifts from G Q_1 by
+ * delta (about u kappa(A) in the storage precision), its loss of orthogonality is of order
+ * delta^2 instead of delta.  It is computed per tile position as h = z + G~^T c,
+ * U = (I_f + G~ G~^T)^{-1} G~ h (an f x f Cholesky inverse in FP64 on the device),
+ * Qo = G_0 (h - G~^T U), reading Q_1 and Q_2 once.  AUTO picks PROJECTED for CQR_F32 and G0
+ * for CQR_F64.  The right-hand side is always transformed as G_0 y, and the square solve
+ * uses the selected Qo: Qo^T (G_0 y) = (Q_1 + G^T Q_2)^T y for PROJECTED.  Batches always
+ * apply G0. */
+enum { CQR_POST_ORTH_AUTO = 0, CQR_POST_ORTH_G0 = 1, CQR_POST_ORTH_PROJECTED = 2 };
 
 /* Geometry record filled by coded_qr_geometry (all int64). */
 enum {
@@ -242,6 +260,18 @@ cqr_status coded_qr_stats(cqr_handle h, int64_t* out);
 /* Synchronise the stream and return the first device-side error since encode (CQR_OK when
  * none), clearing it. */
 cqr_status coded_qr_sync_status(cqr_handle h);
+
+/* Bound of the waits between the CTAs of one panel factorisation (instrumentation, no
+ * counterpart in the paper; the paper assumes fail-stop nodes and an external failure
+ * detector).  Every such wait -- the partial-vector exchange of the cluster panel, the
+ * grid barrier of the cooperative panel -- gives up after `cycles` SM clock cycles
+ * (0 restores the default, about one second): the CTA records CQR_ETIMEOUT in the device
+ * status word, every CTA of the launch leaves at its next wait, and coded_qr_sync_status
+ * returns CQR_ETIMEOUT.  The factors computed after that are not meaningful; a new encode
+ * clears the status.  The tensor-core GEMMs keep their own fixed bound.  A deployment may
+ * shorten the bound to detect a stalled launch sooner; the tests set it to a few cycles so
+ * that every exchange of a correct launch runs out.  Takes effect for the next launches. */
+cqr_status coded_qr_set_wait_limit(cqr_handle h, int64_t cycles);
 
 /* Profile of the library's own kernels (instrumentation, no counterpart in the paper).
  * Launch counts per kernel class are always kept; with enable != 0 every launch site is

@@ -22,6 +22,7 @@ MMA_NAMES = {"simt": CQR_MMA_SIMT, "tf32": CQR_MMA_TF32, "3xtf32": CQR_MMA_3XTF3
              "bf16": CQR_MMA_BF16, "bf16x3": CQR_MMA_BF16X3}
 CQR_G_UNIF01, CQR_G_NORMAL = 0, 1
 PANEL_NAMES = {"icgs": 0, "mgs": 1, "cgs1": 2, "cgs2": 3}
+POST_ORTH_NAMES = {"auto": 0, "g0": 1, "projected": 2}
 CQR_RUN_HOST_BUFFERS = 1
 GEO_FIELDS = ["m", "n", "mb", "nb", "m_pad", "c", "d", "M", "N", "ldq", "ldr", "grid_rows",
               "grid_cols", "panels", "code_blocks"]
@@ -41,7 +42,7 @@ EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "
            "coded_qr_batched_get_factors", "coded_qr_batched_get_decode_sets",
            "coded_qr_batched_sync_status", "coded_qr_batched_last_error",
            "coded_qr_adjoint_qr", "coded_qr_adjoint_lstsq", "coded_qr_mds_stats",
-           "coded_qr_inject_node_failure"]
+           "coded_qr_inject_node_failure", "coded_qr_set_wait_limit"]
 CQR_BATCH_GRAPH, CQR_BATCH_POST_ORTH = 1, 2
 PROF_CLASSES = 16
 
@@ -51,6 +52,7 @@ class Config(C.Structure):
                 ("f", C.c_int32), ("b", C.c_int32), ("dtype", C.c_int32), ("mma", C.c_int32),
                 ("protect_r", C.c_int32), ("gdist", C.c_int32), ("nrhs_max", C.c_int32),
                 ("reorth_block", C.c_int32), ("panel", C.c_int32), ("in_node", C.c_int32),
+                ("post_orth", C.c_int32), ("reserved", C.c_int32),
                 ("seed", C.c_uint64), ("tau", C.c_double),
                 ("stream", C.c_void_p)]
 
@@ -96,6 +98,7 @@ def lib():
             "coded_qr_get_decode_sets": [vp, C.POINTER(i32), i32, C.POINTER(i32)],
             "coded_qr_stats": [vp, C.POINTER(i64)],
             "coded_qr_sync_status": [vp],
+            "coded_qr_set_wait_limit": [vp, i64],
             "coded_qr_profile": [vp, i32],
             "coded_qr_profile_read": [vp, C.POINTER(C.c_double), C.POINTER(i64), i32, i32],
             "coded_qr_panel_icgs_noalloc": [i32, i64, i32, vp, i64, vp, i64, C.c_double, vp, vp],
@@ -443,7 +446,7 @@ class CodedQR:
 
     def __init__(self, m, n, p_r, p_c, f, b, dtype="f64", mma="simt", protect_r=True,
                  gdist=CQR_G_UNIF01, nrhs_max=1, seed=1, tau=0.0, stream=None, workspace=None,
-                 reorth_block=False, panel="icgs", in_node=False):
+                 reorth_block=False, panel="icgs", in_node=False, post_orth="auto"):
         import torch
         self.torch = torch
         self.tdtype = torch.float64 if dtype in ("f64", "float64") else torch.float32
@@ -457,6 +460,7 @@ class CodedQR:
         cfg.reorth_block = int(bool(reorth_block))
         cfg.panel = PANEL_NAMES[panel]
         cfg.in_node = int(bool(in_node))
+        cfg.post_orth = POST_ORTH_NAMES[post_orth]
         cfg.seed = seed
         cfg.tau = tau
         if stream is None:
@@ -564,6 +568,10 @@ class CodedQR:
 
     def sync_status(self):
         return coded_qr_sync_status(self.h)
+
+    def set_wait_limit(self, cycles):
+        """Bound (SM cycles) of the panel's waits between CTAs; 0 restores the default."""
+        check(lib().coded_qr_set_wait_limit(self.h, int(cycles)), "coded_qr_set_wait_limit")
 
     def profile(self, enable=True):
         check(coded_qr_profile(self.h, enable), "coded_qr_profile")

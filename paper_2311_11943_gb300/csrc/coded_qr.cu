@@ -27,7 +27,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-  size_t Q, R, Gt, Gh, Gt_t, Gh_t, part, bar, status, P, Rb, Pt, yw, xw, plans, cg, tc, total;
+  size_t Q, R, Gt, Gh, Gt_t, Gh_t, Kpo, part, bar, status, P, Rb, Pt, yw, xw, plans, cg, tc, total;
 };
 
 struct Buffers {
@@ -37,6 +37,7 @@ struct Buffers {
   double* Gh;
   void* Gt_t;
   void* Gh_t;
+  void* Kpo;  // (I_f + G~ G~^T)^{-1}: f x f doubles, then f x f in the storage type
   void* part;
   unsigned* bar;
   int* status;
@@ -78,6 +79,8 @@ cqr_status validate(const cqr_config* c) {
   if (c->gdist != CQR_G_UNIF01 && c->gdist != CQR_G_NORMAL) return CQR_EINVAL;
   if (c->nrhs_max < 0) return CQR_EINVAL;
   if (c->panel < CQR_PANEL_ICGS || c->panel > CQR_PANEL_CGS2) return CQR_EINVAL;
+  if (c->post_orth < CQR_POST_ORTH_AUTO || c->post_orth > CQR_POST_ORTH_PROJECTED) return CQR_EINVAL;
+  if (c->reserved != 0) return CQR_EINVAL;
   return CQR_OK;
 }
 
@@ -119,6 +122,7 @@ Layout make_layout(const cqr_config* c, const Geo& g, int num_sms) {
   L.Gh = take((size_t)(g.f * c->p_c + 1) * 8);
   L.Gt_t = take((size_t)(g.f * c->p_r + 1) * s);
   L.Gh_t = take((size_t)(g.f * c->p_c + 1) * s);
+  L.Kpo = take((size_t)kMaxF * kMaxF * (8 + s));
   L.part = take(panel_partial_bytes(bmax, s, num_sms));
   L.bar = take(256);
   L.status = take(256);
@@ -195,6 +199,7 @@ struct cqr_handle_s {
   cudaStream_t la_st[2] = {nullptr, nullptr};
   cudaEvent_t la_ev[3] = {nullptr, nullptr, nullptr};
   bool la_pdl = false;  // programmatic dependent launch on the critical stream
+  long long wait_limit = 0;  // panel exchange / grid-barrier wait bound (0: the default)
 };
 
 namespace {
@@ -260,6 +265,7 @@ cqr_status setup(cqr_handle h) {
   h->B.Gh = reinterpret_cast<double*>(base + L.Gh);
   h->B.Gt_t = base + L.Gt_t;
   h->B.Gh_t = base + L.Gh_t;
+  h->B.Kpo = base + L.Kpo;
   h->B.part = base + L.part;
   h->B.bar = reinterpret_cast<unsigned*>(base + L.bar);
   h->B.status = reinterpret_cast<int*>(base + L.status);
@@ -412,11 +418,12 @@ cqr_status panel_kernel_step(cqr_handle h, int64_t kb, int bk, cudaStream_t st) 
   if (sizeof(T) == 4 && h->reg_ok) {
     CK(launch_panel_reg(h->reg_rpl, h->reg_cpw, h->reg_G, reinterpret_cast<float*>(Q + kb * g.ldq),
                         g.ldq, reinterpret_cast<float*>(R + kb + kb * g.ldr), g.ldr, g.M, bk, h->tau,
-                        h->B.status, (int)kb, st, h->la_pdl && st == h->la_st[0]));
+                        h->B.status, (int)kb, st, h->la_pdl && st == h->la_st[0], h->wait_limit));
   } else {
     const int variant = h->cfg.panel == CQR_PANEL_CGS1 ? 1 : (h->cfg.panel == CQR_PANEL_CGS2 ? 2 : 0);
     CK(launch_panel<T>(h->plan, Q + kb * g.ldq, g.ldq, R + kb + kb * g.ldr, g.ldr, g.M, bk, h->tau,
-                       ptr<T>(h->B.part), h->B.bar, h->B.status, (int)kb, st, variant));
+                       ptr<T>(h->B.part), h->B.bar, h->B.status, (int)kb, st, variant,
+                       h->wait_limit));
   }
   return CQR_OK;
 }
@@ -689,8 +696,16 @@ cqr_status post_orth_q(cqr_handle h, T* Qout, int64_t ldqo) {
     if (Qout) return copy_pad<T>(h, Q, g.ldq, g.m_pad, g.m_pad, g.n, Qout, ldqo);
     return CQR_OK;
   }
+  const bool projected = h->cfg.post_orth == CQR_POST_ORTH_PROJECTED ||
+                         (h->cfg.post_orth == CQR_POST_ORTH_AUTO && h->esz == 4);
   if (g.f == 0) {
     if (Qout) return copy_pad<T>(h, Q, g.ldq, g.m_pad, g.m_pad, g.n, Qout, ldqo);
+  } else if (projected) {
+    ProfScope ps(h, K_POST_ORTH, 2);
+    double* K64 = reinterpret_cast<double*>(h->B.Kpo);
+    T* Kt = reinterpret_cast<T*>(K64 + kMaxF * kMaxF);
+    CK(launch_post_orth_projected<T>(g, h->B.Gt, ptr<T>(h->B.Gt_t), K64, Kt, Q, g.ldq, g.n, dst,
+                                     ldd, h->st));
   } else {
     ProfScope ps(h, K_POST_ORTH, 1);
     CK(launch_post_orth<T>(g, ptr<T>(h->B.Gt_t), Q, g.ldq, g.m_pad, g.n, dst, ldd, h->st));
@@ -1080,6 +1095,12 @@ cqr_status coded_qr_stats(cqr_handle h, int64_t* out) {
   out[1] = h->n_recovered;
   out[2] = h->panels_run;
   out[3] = h->n_injected;
+  return CQR_OK;
+}
+
+cqr_status coded_qr_set_wait_limit(cqr_handle h, int64_t cycles) {
+  if (!h || cycles < 0) return CQR_EINVAL;
+  h->wait_limit = (long long)cycles;
   return CQR_OK;
 }
 

@@ -32,6 +32,12 @@ __device__ __forceinline__ int ld_relaxed_i32(const int* p) {
 // Upper bound of one barrier wait, in SM clock cycles (about one second at 2 GHz).  A wait
 // that runs out records CQR_ETIMEOUT and returns false; every CTA then leaves the kernel.
 constexpr long long kWaitLimitCycles = 2000000000LL;
+// A CTA whose wait on its peers has lasted this long also polls the status word and leaves
+// once any CTA has recorded an error (so that one expired wait ends the whole launch soon).
+constexpr long long kPollAfterCycles = 20000LL;
+// After an abandoned exchange of distributed-shared-memory stores, the pause before a CTA
+// releases its shared memory (every peer has issued its last store by then).
+constexpr long long kDrainCycles = 20000LL;
 
 // Grid-wide barrier for a cooperative launch of `nblocks` CTAs.  `bar` is a global counter
 // zeroed before the launch; `target` is a per-CTA running target (start at 0).  Ordering:

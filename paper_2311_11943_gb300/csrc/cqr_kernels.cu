@@ -534,6 +534,235 @@ cudaError_t launch_post_orth(const Geo& g, const T* Gt_t, const T* Z, int64_t ld
   return cudaGetLastError();
 }
 
+// ===================================================================== a8, drift-robust form
+// W = G_0^{-1} (Q_1 + G^T Q_2) with G = G~ (x) I_mb (reading of Theorem G_0 for checksum rows
+// that drift from G Q_1 in floating point).  Per tile position s and column j, with z_t the
+// entry of block row t of Q_1 and c_i that of block row i of Q_2:
+//   h = z + G~^T c,   Y = G~ h,   U = K Y,   Z = h - G~^T U,   W = G_0 Z,
+// K = (I_f + G~ G~^T)^{-1}.  Since G_0^2 = I + G~^T G~ (G_0 symmetric) and, by Woodbury,
+// (I + G~^T G~)^{-1} = I - G~^T K G~, the pipeline is G_0 (I + G~^T G~)^{-1} h = G_0^{-1} h.
+// G_0 Z is the block pipeline of post_orth_f: W_i = Z_i + (G~ Z)_i (i < f) and
+// W_t = sum_{l<f} g~_{l,t} Z_l - Z_t (t >= f).
+
+// K from the FP64 generator: Cholesky L L^T = I_f + G~ G~^T (Golub and Van Loan, the outer
+// product form), then K = L^{-T} L^{-1} column by column; one thread (f <= kMaxF).
+template <typename T>
+__global__ void k_post_orth_coef(int f, int p_r, const double* __restrict__ Gt, double* K64, T* Kt) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double A[kMaxF][kMaxF];
+  for (int i = 0; i < f; ++i)
+    for (int l = 0; l <= i; ++l) {
+      double a = (i == l) ? 1.0 : 0.0;
+      for (int t = 0; t < p_r; ++t) a += Gt[i * p_r + t] * Gt[l * p_r + t];
+      A[i][l] = a;
+    }
+  // lower triangle of A overwritten by L
+  for (int j = 0; j < f; ++j) {
+    double d = A[j][j];
+    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+    d = sqrt(d);
+    A[j][j] = d;
+    for (int i = j + 1; i < f; ++i) {
+      double v = A[i][j];
+      for (int k = 0; k < j; ++k) v -= A[i][k] * A[j][k];
+      A[i][j] = v / d;
+    }
+  }
+  for (int col = 0; col < f; ++col) {
+    double x[kMaxF];
+    for (int i = 0; i < f; ++i) {          // L x = e_col
+      double v = (i == col) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) v -= A[i][k] * x[k];
+      x[i] = v / A[i][i];
+    }
+    for (int i = f - 1; i >= 0; --i) {     // L^T x = x
+      double v = x[i];
+      for (int k = i + 1; k < f; ++k) v -= A[k][i] * x[k];
+      x[i] = v / A[i][i];
+    }
+    for (int i = 0; i < f; ++i) {
+      K64[i * f + col] = x[i];
+      Kt[i * f + col] = (T)x[i];
+    }
+  }
+}
+
+// One thread per (position s, column j), 32 x 8 threads per CTA.  ONE: every block row of the
+// position in registers (p_r <= 32), Q_1 and Q_2 read once; otherwise two passes over Q_1
+// (Y first, then Z and W), the f values Z_0 .. Z_{f-1} kept between them.  Coefficients in
+// shared memory.  W may alias Q_1: each thread reads its own position before writing it.
+template <typename T, int F, bool ONE>
+__global__ void __launch_bounds__(256) k_post_orth_proj(Geo g, const T* __restrict__ Gt,
+                                                        const T* __restrict__ Kt, const T* Q,
+                                                        int64_t ldq, int64_t k, T* W,
+                                                        int64_t ldw) {
+  constexpr int NF = F > 0 ? F : kMaxF;
+  constexpr int PR = 32;
+  __shared__ T sG[kMaxF * kMaxCode];
+  __shared__ T sK[kMaxF * kMaxF];
+  const int f = F > 0 ? F : g.f, p_r = g.p_r;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int e = tid; e < f * p_r; e += 256) sG[e] = Gt[e];
+  for (int e = tid; e < f * f; e += 256) sK[e] = Kt[e];
+  __syncthreads();
+  const int64_t s = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  const int64_t col = (int64_t)blockIdx.y * 8 + threadIdx.y;
+  const int64_t mb = g.mb;
+  if (s >= mb || col >= k) return;
+  const T* qc = Q + col * ldq;
+  T* wc = W + col * ldw;
+  T c[NF], Y[NF], U[NF], a[NF];
+#pragma unroll
+  for (int i = 0; i < NF; ++i) {
+    c[i] = (i < f) ? qc[g.m_pad + (int64_t)i * mb + s] : T(0);
+    Y[i] = T(0);
+    a[i] = T(0);
+  }
+  if constexpr (ONE) {
+    T z[PR];
+#pragma unroll
+    for (int t = 0; t < PR; ++t) z[t] = (t < p_r) ? qc[(int64_t)t * mb + s] : T(0);
+#pragma unroll
+    for (int t = 0; t < PR; ++t) {
+      if (t < p_r) {
+        T h = z[t];
+#pragma unroll
+        for (int i = 0; i < NF; ++i)
+          if (i < f) h += sG[i * p_r + t] * c[i];
+        z[t] = h;
+#pragma unroll
+        for (int i = 0; i < NF; ++i)
+          if (i < f) Y[i] += sG[i * p_r + t] * h;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+      T u = T(0);
+#pragma unroll
+      for (int l = 0; l < NF; ++l)
+        if (l < f) u += sK[i * f + l] * Y[l];
+      U[i] = u;
+    }
+#pragma unroll
+    for (int t = 0; t < PR; ++t) {
+      if (t < p_r) {
+        T zv = z[t];
+#pragma unroll
+        for (int i = 0; i < NF; ++i)
+          if (i < f) zv -= sG[i * p_r + t] * U[i];
+        z[t] = zv;
+#pragma unroll
+        for (int i = 0; i < NF; ++i)
+          if (i < f) a[i] += sG[i * p_r + t] * zv;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < PR; ++t) {
+      if (t < p_r) {
+        T w;
+        if (t < f) {
+          w = z[t] + a[t < NF ? t : 0];
+        } else {
+          w = T(0);
+#pragma unroll
+          for (int l = 0; l < NF; ++l)
+            if (l < f) w += sG[l * p_r + t] * z[l];
+          w -= z[t];
+        }
+        wc[(int64_t)t * mb + s] = w;
+      }
+    }
+  } else {
+  // two passes: Y over every block row, then Z, a and the rows t >= f of W
+  for (int t0 = 0; t0 < p_r; t0 += 8) {
+    T z[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) z[u] = (t0 + u < p_r) ? qc[(int64_t)(t0 + u) * mb + s] : T(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u;
+      if (t < p_r) {
+        T h = z[u];
+#pragma unroll
+        for (int i = 0; i < NF; ++i)
+          if (i < f) h += sG[i * p_r + t] * c[i];
+#pragma unroll
+        for (int i = 0; i < NF; ++i)
+          if (i < f) Y[i] += sG[i * p_r + t] * h;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NF; ++i) {
+    T u = T(0);
+#pragma unroll
+    for (int l = 0; l < NF; ++l)
+      if (l < f) u += sK[i * f + l] * Y[l];
+    U[i] = u;
+  }
+  T zf[NF];
+#pragma unroll
+  for (int i = 0; i < NF; ++i) zf[i] = T(0);
+  for (int t0 = 0; t0 < p_r; t0 += 8) {
+    T z[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) z[u] = (t0 + u < p_r) ? qc[(int64_t)(t0 + u) * mb + s] : T(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u;
+      if (t < p_r) {
+        T zv = z[u];
+#pragma unroll
+        for (int i = 0; i < NF; ++i)
+          if (i < f) zv += sG[i * p_r + t] * (c[i] - U[i]);
+#pragma unroll
+        for (int i = 0; i < NF; ++i)
+          if (i < f) a[i] += sG[i * p_r + t] * zv;
+        if (t < f) {
+#pragma unroll
+          for (int i = 0; i < NF; ++i)
+            if (i == t) zf[i] = zv;
+        } else {
+          T w = T(0);
+#pragma unroll
+          for (int l = 0; l < NF; ++l)
+            if (l < f) w += sG[l * p_r + t] * zf[l];
+          wc[(int64_t)t * mb + s] = w - zv;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NF; ++i)
+    if (i < f) wc[(int64_t)i * mb + s] = zf[i] + a[i];
+  }
+}
+
+template <typename T>
+cudaError_t launch_post_orth_projected(const Geo& g, const double* Gt, const T* Gt_t, double* K64,
+                                       T* Kt, const T* Q, int64_t ldq, int64_t k, T* W, int64_t ldw,
+                                       cudaStream_t st) {
+  if (g.f < 1 || g.f > kMaxF || g.p_r + g.f > kMaxCode) return cudaErrorInvalidValue;
+  k_post_orth_coef<T><<<1, 32, 0, st>>>(g.f, g.p_r, Gt, K64, Kt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 blk(32, 8);
+  dim3 grd((unsigned)((g.mb + 31) / 32), (unsigned)((k + 7) / 8));
+  const bool one = g.p_r <= 32;
+#define CQR_PO_PROJ(FF)                                                                         \
+  if (one) k_post_orth_proj<T, FF, true><<<grd, blk, 0, st>>>(g, Gt_t, Kt, Q, ldq, k, W, ldw);  \
+  else k_post_orth_proj<T, FF, false><<<grd, blk, 0, st>>>(g, Gt_t, Kt, Q, ldq, k, W, ldw);
+  switch (f_bucket(g.f)) {
+    case 1: CQR_PO_PROJ(1) break;
+    case 2: CQR_PO_PROJ(2) break;
+    case 3: CQR_PO_PROJ(3) break;
+    case 4: CQR_PO_PROJ(4) break;
+    default: CQR_PO_PROJ(-1) break;
+  }
+#undef CQR_PO_PROJ
+  return cudaGetLastError();
+}
+
 // ===================================================================== a9 solve
 // z = Qo^T yo (Eq. (linearsolve3)), one warp per output entry.
 template <typename T>
@@ -1187,6 +1416,9 @@ cudaError_t launch_b_post_orth(const BatchInst<T>* inst, int count, const int64_
                                         const double*, T*, T*, int*, cudaStream_t);               \
   template cudaError_t launch_post_orth<T>(const Geo&, const T*, const T*, int64_t, int64_t,     \
                                            int64_t, T*, int64_t, cudaStream_t);                   \
+  template cudaError_t launch_post_orth_projected<T>(const Geo&, const double*, const T*,        \
+                                                     double*, T*, const T*, int64_t, int64_t, T*, \
+                                                     int64_t, cudaStream_t);                      \
   template cudaError_t launch_gemv_t<T>(const T*, int64_t, int64_t, int64_t, const T*, int64_t,  \
                                         int64_t, T*, int64_t, cudaStream_t);                      \
   template cudaError_t launch_trsv_upper<T>(const T*, int64_t, int64_t, T*, int64_t, int64_t,    \

@@ -52,16 +52,17 @@ size_t panel_partial_bytes(int bk, size_t elem, int num_sms);
 bool plan_panel_reg(int64_t M, int bk, int* rpl, int* cpw, int* G);
 bool panel_reg_cluster_fits(int rpl, int cpw, int G);
 // pdl: launch with programmatic stream serialization (the kernel waits for its predecessor).
+// wait_limit: bound of each exchange wait in SM cycles (<= 0: kWaitLimitCycles).
 cudaError_t launch_panel_reg(int rpl, int cpw, int G, float* Q, int64_t ldq, float* R, int64_t ldr,
                              int64_t M, int bk, double tau, int* status, int col0, cudaStream_t st,
-                             bool pdl = false);
+                             bool pdl = false, long long wait_limit = 0);
 
 // variant: 0 the paper's ICGS panel (MGS order; no reorthogonalisation when tau <= 0),
 // 1 left-looking CGS with one reduction per column, 2 CGS2.
 template <typename T>
 cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t ldr, int64_t M,
                          int bk, double tau, T* part, unsigned* bar, int* status, int col0,
-                         cudaStream_t st, int variant = 0);
+                         cudaStream_t st, int variant = 0, long long wait_limit = 0);
 
 // Rbar partials: P[s] (bk x w, col-major) = Qbar^T Qtrail over K-split s.
 template <typename T>
@@ -89,6 +90,16 @@ cudaError_t launch_decode(const Geo& g, const DecodePlan* plans_dev, int nplans,
 template <typename T>
 cudaError_t launch_post_orth(const Geo& g, const T* Gt_t, const T* Z, int64_t ldz,
                              int64_t zrows, int64_t k, T* W, int64_t ldw, cudaStream_t st);
+
+// Drift-robust post-orthogonalisation W = G_0^{-1} (Q_1 + G^T Q_2) (coded_qr.h,
+// CQR_POST_ORTH_PROJECTED) of the first k columns of the coded Q (Q_1 rows 0 .. m_pad-1, Q_2
+// rows m_pad .. m_pad+c-1, ld ldq) into W (m_pad x k; W may alias Q_1).  Two launches: the
+// f x f FP64 inverse K = (I_f + G~ G~^T)^{-1} from the FP64 generator Gt into K64 and its
+// storage-type copy Kt (kMaxF^2 entries each), then the tile pipeline.
+template <typename T>
+cudaError_t launch_post_orth_projected(const Geo& g, const double* Gt, const T* Gt_t, double* K64,
+                                       T* Kt, const T* Q, int64_t ldq, int64_t k, T* W, int64_t ldw,
+                                       cudaStream_t st);
 
 // z (n x k) = Qo^T yo, Qo rows x n.
 template <typename T>

@@ -61,7 +61,7 @@ __device__ __forceinline__ double ld_peer(uint32_t addr, double) {
 // Thread 0 arrives with a release add (ordered after the CTA barrier, hence after every
 // thread's prior writes) and polls with acquire loads; the wait is bounded.
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& target,
-                                             int* status, int site) {
+                                             int* status, int site, long long limit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -71,7 +71,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
     const long long t0 = clock64();
     while (ld_acquire_u32(bar) < target) {
       if (ld_relaxed_i32(status + ST_CODE) == CQR_ETIMEOUT) { ok = 0; break; }
-      if (clock64() - t0 > kWaitLimitCycles) {
+      if (clock64() - t0 > limit) {
         set_status(status, CQR_ETIMEOUT, site);
         status[ST_SITE] = site;
         ok = 0;
@@ -96,6 +96,7 @@ struct Ctx {
   unsigned* bar;
   int* status;
   unsigned target;
+  long long wait_limit;  // bound of each grid-barrier wait, SM cycles
 };
 
 template <typename T, bool CL>
@@ -133,7 +134,7 @@ __device__ __forceinline__ bool sync_reduce(Ctx<T>& c, int lo, int hi, T* out, i
     __syncthreads();
     return true;
   }
-  if (!grid_barrier(c.bar, G, c.target, c.status, site)) return false;
+  if (!grid_barrier(c.bar, G, c.target, c.status, site, c.wait_limit)) return false;
   hook();
   const T* P = c.gpart + (size_t)(step & 1) * G * 2 * c.pld;
   const int n = hi - lo;
@@ -222,7 +223,8 @@ template <typename T, int RPL, bool CL, bool SMEM>
 __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq, T* __restrict__ R,
                                                    int64_t ldr, int64_t M, int bk, int rpc,
                                                    int rpc_pad, double tau2, T* gpart,
-                                                   unsigned* bar, int* status, int col0) {
+                                                   unsigned* bar, int* status, int col0,
+                                                   long long wait_limit) {
   constexpr int VW = (SMEM && sizeof(T) == 4 && RPL % 2 == 0) ? 2 : 1;
   constexpr int NV = RPL / VW;  // vectors per lane
   using L = LaneOps<T, VW>;
@@ -249,6 +251,7 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
   c.bar = bar;
   c.status = status;
   c.target = 0;
+  c.wait_limit = wait_limit;
   int step = 0;
   auto ok_row = [&](int r) { return SMEM ? true : (r < nr); };
 
@@ -466,7 +469,8 @@ template <typename T, int RPL, bool CL, bool SMEM, int PASSES>
 __global__ void __launch_bounds__(kNT, 1) k_panel_cgs(T* __restrict__ Q, int64_t ldq, T* __restrict__ R,
                                                        int64_t ldr, int64_t M, int bk, int rpc,
                                                        int rpc_pad, double tau2, T* gpart,
-                                                       unsigned* bar, int* status, int col0) {
+                                                       unsigned* bar, int* status, int col0,
+                                                   long long wait_limit) {
   constexpr int VW = (SMEM && sizeof(T) == 4 && RPL % 2 == 0) ? 2 : 1;
   constexpr int NV = RPL / VW;
   using L = LaneOps<T, VW>;
@@ -491,6 +495,7 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_cgs(T* __restrict__ Q, int64_t
   c.bar = bar;
   c.status = status;
   c.target = 0;
+  c.wait_limit = wait_limit;
   (void)tau2;
   int step = 0;
   auto ok_row = [&](int r) { return SMEM ? true : (r < nr); };
@@ -660,7 +665,7 @@ PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_clu
 template <typename T>
 cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t ldr, int64_t M,
                          int bk, double tau, T* part, unsigned* bar, int* status, int col0,
-                         cudaStream_t st, int variant) {
+                         cudaStream_t st, int variant, long long wait_limit) {
   if (pp.G > 1 && !pp.cluster) {
     cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
@@ -668,7 +673,9 @@ cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t l
   const int rpl = rpl_for_rows(pp.rpc);
   double tau2 = tau > 0.0 ? tau * tau : -1.0;
   int rpc = pp.rpc, rpc_pad = pp.rpc_pad;
-  void* args[] = {&Q, &ldq, &R, &ldr, &M, &bk, &rpc, &rpc_pad, &tau2, &part, &bar, &status, &col0};
+  long long wl = wait_limit > 0 ? wait_limit : kWaitLimitCycles;
+  void* args[] = {&Q, &ldq, &R, &ldr, &M, &bk, &rpc, &rpc_pad, &tau2, &part, &bar, &status, &col0,
+                  &wl};
   const void* fn = pick_kernel<T>(rpl, pp.cluster != 0, pp.smem != 0, variant);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)pp.smem_bytes);
@@ -731,10 +738,10 @@ size_t panel_partial_bytes(int bk, size_t elem, int num_sms) {
 
 template cudaError_t launch_panel<float>(const PanelPlan&, float*, int64_t, float*, int64_t, int64_t,
                                          int, double, float*, unsigned*, int*, int, cudaStream_t,
-                                         int);
+                                         int, long long);
 template cudaError_t launch_panel<double>(const PanelPlan&, double*, int64_t, double*, int64_t,
                                           int64_t, int, double, double*, unsigned*, int*, int,
-                                          cudaStream_t, int);
+                                          cudaStream_t, int, long long);
 template bool panel_cluster_fits<float>(const PanelPlan&);
 template bool panel_cluster_fits<double>(const PanelPlan&);
 

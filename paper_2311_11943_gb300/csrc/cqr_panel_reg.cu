@@ -139,7 +139,7 @@ template <int RPL, int CPW>
 __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int64_t ldq,
                                                        float* __restrict__ R, int64_t ldr,
                                                        int64_t M, int bk, double tau2, int* status,
-                                                       int col0) {
+                                                       int col0, long long wait_limit) {
   constexpr int NP = RPL / 2;            // row pairs per lane
   constexpr int RPC = 32 * RPL;          // rows per CTA
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -204,9 +204,13 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
     if (active_slot && sub == 0) lpart[par * 512 + base + a] = s;
   };
   // exchange of the partial vectors, entries lo .. hi-1 (whole 4-entry chunks): this CTA's
-  // chunks go into receive buffer [par][g] of every CTA; then the wait for all G vectors
+  // chunks go into receive buffer [par][g] of every CTA; then the wait for all G vectors.
+  // The wait is bounded by wait_limit cycles; when it runs out, the CTA records CQR_ETIMEOUT
+  // and returns false, and a CTA whose wait is long overdue also gives up once any CTA has
+  // recorded an error: every CTA then leaves the column loop (the decision is uniform within
+  // a CTA) and meets the others at the kernel's final cluster barrier.
   unsigned phases = 0u;  // bit p: the phase parity of mbarrier p
-  auto exchange = [&](int par, int lo, int hi) {
+  auto exchange = [&](int par, int lo, int hi) -> bool {
     const int c0 = lo / 4, nch = (hi + 3) / 4 - c0;
     __syncthreads();  // this CTA's partials are complete
     if (tid == 0) mbar_expect(mbar + par, (unsigned)(G * nch * 16));
@@ -227,14 +231,23 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
         st_async4(peer_addr(dst0, peer) + 16u * ch, x, peer_addr(bar0, peer));
       }
     }
+    bool ok = true;
     const long long t0 = clock64();
+    unsigned spins = 0u;
     while (!mbar_try_wait(mbar + par, (phases >> par) & 1u)) {
-      if (clock64() - t0 > kWaitLimitCycles) {  // never expected: report and go on
+      const long long el = clock64() - t0;
+      if (el > wait_limit) {
         set_status(status, CQR_ETIMEOUT, 40);
+        ok = false;
+        break;
+      }
+      if (el > kPollAfterCycles && (++spins & 63u) == 0u && ld_relaxed_i32(status + ST_CODE) != 0) {
+        ok = false;
         break;
       }
     }
     phases ^= 1u << par;
+    return __syncthreads_and(ok) != 0;
   };
   // out[a] (lo <= a < hi) = sum over the G CTAs of their partial vectors, in a fixed order
   auto gather = [&](int par, int lo, int hi, float* out) {
@@ -283,13 +296,13 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
   }
   // columns 0 and 1 go to staging buffer 0 (column 0 is still there)
   owner_write(1, stage + RPC);
-  exchange(par, 0, 256 + bk);
+  bool aborted = !exchange(par, 0, 256 + bk);
   gather(par, 0, bk, v);
   gather(par, 256, 256 + bk, v);
   __syncthreads();
   par ^= 1;
 
-  for (int j = 0; j < bk; ++j) {
+  for (int j = 0; j < bk && !aborted; ++j) {
     float* st_cur = stage + (size_t)(j & 1) * 2 * RPC;   // p_j, p_{j+1}
     float* st_nxt = stage + (size_t)((j + 1) & 1) * 2 * RPC;
     if (j > 0 && tau2 > 0.0 && (double)v[j] < tau2 * (double)eta[j]) {
@@ -311,7 +324,10 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
         const int a = warp + kNW * (gr * GS + slot);
         push(e, par, 0, a < j, a);
       }
-      exchange(par, 0, j);
+      if (!exchange(par, 0, j)) {
+        aborted = true;
+        break;
+      }
       gather(par, 0, j, sv);
       __syncthreads();
       par ^= 1;
@@ -374,7 +390,10 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
         const int a = warp + kNW * (gr * GS + slot);
         push(e, par, 0, a >= j && a < bk, a);
       }
-      exchange(par, j, bk);
+      if (!exchange(par, j, bk)) {
+        aborted = true;
+        break;
+      }
       gather(par, j, bk, v);
       __syncthreads();
       par ^= 1;
@@ -442,12 +461,23 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
     if (!nxt) break;
     owner_write(j + 1, st_nxt);
     owner_write(j + 2, st_nxt + RPC);
-    exchange(par, j + 1, bk);
+    if (!exchange(par, j + 1, bk)) {
+      aborted = true;
+      break;
+    }
     gather(par, j + 1, bk, v);
     __syncthreads();
     par ^= 1;
   }
   cl_sync();  // uniform end
+  if (aborted) {
+    // every CTA issued its last partial-vector stores before it arrived at the barrier above;
+    // leave them time to land in this CTA's shared memory before it is released
+    const long long t0 = clock64();
+    while (clock64() - t0 < kDrainCycles) {
+    }
+    return;
+  }
   // write the finished slice back
 #pragma unroll
   for (int k = 0; k < CPW; ++k) {
@@ -507,7 +537,7 @@ bool plan_panel_reg(int64_t M, int bk, int* rpl_out, int* cpw_out, int* G_out) {
 
 cudaError_t launch_panel_reg(int rpl, int cpw, int G, float* Q, int64_t ldq, float* R, int64_t ldr,
                              int64_t M, int bk, double tau, int* status, int col0, cudaStream_t st,
-                             bool pdl) {
+                             bool pdl, long long wait_limit) {
   const void* fn = pick_reg(rpl, cpw);
   if (!fn) return cudaErrorInvalidValue;
   const size_t smem = reg_smem_bytes(rpl);
@@ -518,7 +548,8 @@ cudaError_t launch_panel_reg(int rpl, int cpw, int G, float* Q, int64_t ldq, flo
     if (e != cudaSuccess) return e;
   }
   double tau2 = tau > 0.0 ? tau * tau : -1.0;
-  void* args[] = {&Q, &ldq, &R, &ldr, &M, &bk, &tau2, &status, &col0};
+  long long wl = wait_limit > 0 ? wait_limit : kWaitLimitCycles;
+  void* args[] = {&Q, &ldq, &R, &ldr, &M, &bk, &tau2, &status, &col0, &wl};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(G);
   cfg.blockDim = dim3(kNT);

@@ -47,13 +47,15 @@ def test_solve_ls_validates_like_solve_without_gpu(libpath):
     from paper_2311_11943_gb300 import binding as B
     assert B.coded_qr_solve_ls(None, 0, 1, 0, 1, 1) == B.CQR_EINVAL
     assert B.coded_qr_solve(None, 0, 1, 0, 1, 1) == B.CQR_EINVAL
+    assert B.lib().coded_qr_set_wait_limit(None, 100) == B.CQR_EINVAL
 
 
 def test_config_struct_layout(libpath):
     from paper_2311_11943_gb300 import binding
-    assert C.sizeof(binding.Config) == 88
+    assert C.sizeof(binding.Config) == 96
     assert binding.Config.panel.offset == 56 and binding.Config.in_node.offset == 60
-    assert binding.Config.seed.offset == 64 and binding.Config.stream.offset == 80
+    assert binding.Config.post_orth.offset == 64 and binding.Config.reserved.offset == 68
+    assert binding.Config.seed.offset == 72 and binding.Config.stream.offset == 88
 
 
 def test_errstr_and_argument_validation_without_gpu(libpath):

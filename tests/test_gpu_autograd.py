@@ -123,10 +123,21 @@ def test_c5_shape_against_cpu_fp64_reference(dtype):
     gA_ref, gy_ref = reference_grad(A, y, W, p_r, p_c, f, seed)
     gA = Ad.grad.double().cpu().numpy()
     gy = yd.grad.double().cpu().numpy()
-    # the gradient of x carries z = (A^T A)^{-1} xbar, whose forward error through a
-    # backward-stable R is of order kappa^2 u: the bound used is 2 kappa^2 u
-    u = np.finfo(np.float64 if dtype == "f64" else np.float32).eps / 2
-    tol = 2 * kappa ** 2 * u
+    # Tolerance from the gradient's own sensitivity: the path's backward-error target eps
+    # (1e-12 in FP64, 1e-5 in FP32 storage) is a relative perturbation of the inputs, so the
+    # reference gradient at a seeded perturbation of that size shows how far a gradient of a
+    # computation meeting the target may move (linearly in eps; about 6e-4 for A and 2e-3 for
+    # y at 1e-5 here, where the kappa^2 worst case would allow 1e-1); twice that is the bound,
+    # and it stays below 1%, so a gradient wrong by 1% fails
+    eps = 1e-12 if dtype == "f64" else 1e-5
+    E = synth.gaussian(m, n, 99)[None]
+    E *= eps * np.linalg.norm(A) / np.linalg.norm(E)
+    e = synth.rhs(m, k, 98)[None]
+    e *= eps * np.linalg.norm(y) / np.linalg.norm(e)
+    gA_p, gy_p = reference_grad(A + E, y + e, W, p_r, p_c, f, seed)
+    tolA = 2 * np.linalg.norm(gA_p - gA_ref) / np.linalg.norm(gA_ref)
+    toly = 2 * np.linalg.norm(gy_p - gy_ref) / np.linalg.norm(gy_ref)
+    assert tolA < 1e-2 and toly < 1e-2
     relA = np.linalg.norm(gA - gA_ref) / np.linalg.norm(gA_ref)
     rely = np.linalg.norm(gy - gy_ref) / np.linalg.norm(gy_ref)
-    assert relA < tol and rely < tol, (relA, rely, tol)
+    assert relA < tolA and rely < toly, (relA, rely, tolA, toly)
