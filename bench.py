@@ -804,7 +804,7 @@ def extra_legs(args, cfg, torch, B, Ad, A_np, yd, xd, flush, stream):
                 q.recover()
             q.factor(t, t + 1)
         Qc, Rc = q.factors()
-        Qo = B.colmajor_empty(q.geo["m_pad"], Qc.shape[1], Qc.dtype)
+        Qo = B.colmajor_empty(q.geo["m_pad"], q.geo["n"], Qc.dtype)
         q.post_orth(Qo)
         return Qc, Rc, Qo
 

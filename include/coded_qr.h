@@ -126,9 +126,10 @@ enum {
  * whenever the checksum rows satisfy Q_2 = G Q_1 (Lemma "2way_checksum"), so in exact
  * arithmetic it is the paper's matrix; in floating point, where Q_2 drifts from G Q_1 by
  * delta (about u kappa(A) in the storage precision), its loss of orthogonality is of order
- * delta^2 instead of delta.  It is computed per tile position as h = z + G~^T c,
- * U = (I_f + G~ G~^T)^{-1} G~ h (an f x f Cholesky inverse in FP64 on the device),
- * Qo = G_0 (h - G~^T U), reading Q_1 and Q_2 once.  AUTO picks PROJECTED for CQR_F32 and G0
+ * delta^2 instead of delta.  With the drift D = Q_2 - G Q_1 it equals
+ * G_0 (Q_1 + G^T K D), K = (I_f + G~ G~^T)^{-1} acting on block rows (an f x f Cholesky
+ * inverse in FP64 on the device), and is computed in that form per tile position, reading
+ * Q_1 and Q_2 once: the correction comes from the drift itself, so no large terms cancel.  AUTO picks PROJECTED for CQR_F32 and G0
  * for CQR_F64.  The right-hand side is always transformed as G_0 y, and the square solve
  * uses the selected Qo: Qo^T (G_0 y) = (Q_1 + G^T Q_2)^T y for PROJECTED.  Batches always
  * apply G0. */

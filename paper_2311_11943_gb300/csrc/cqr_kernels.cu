@@ -536,13 +536,18 @@ cudaError_t launch_post_orth(const Geo& g, const T* Gt_t, const T* Z, int64_t ld
 
 // ===================================================================== a8, drift-robust form
 // W = G_0^{-1} (Q_1 + G^T Q_2) with G = G~ (x) I_mb (reading of Theorem G_0 for checksum rows
-// that drift from G Q_1 in floating point).  Per tile position s and column j, with z_t the
-// entry of block row t of Q_1 and c_i that of block row i of Q_2:
-//   h = z + G~^T c,   Y = G~ h,   U = K Y,   Z = h - G~^T U,   W = G_0 Z,
-// K = (I_f + G~ G~^T)^{-1}.  Since G_0^2 = I + G~^T G~ (G_0 symmetric) and, by Woodbury,
-// (I + G~^T G~)^{-1} = I - G~^T K G~, the pipeline is G_0 (I + G~^T G~)^{-1} h = G_0^{-1} h.
-// G_0 Z is the block pipeline of post_orth_f: W_i = Z_i + (G~ Z)_i (i < f) and
-// W_t = sum_{l<f} g~_{l,t} Z_l - Z_t (t >= f).
+// that drift from G Q_1 in floating point).  Write Q_2 = G Q_1 + D (D the drift).  Since
+// G_0^2 = I + G^T G (G_0 symmetric), G_0^{-1}(I + G^T G) = G_0, and by the push-through
+// identity (I + G~^T G~)^{-1} G~^T = G~^T K with K = (I_f + G~ G~^T)^{-1}:
+//   W = G_0 Q_1 + G_0^{-1} G^T D = G_0 (Q_1 + G^T K D)   (K acting on block rows).
+// Per tile position s and column j, with z_t the entry of block row t of Q_1 and c_i that of
+// block row i of Q_2:
+//   d = c - G~ z,   e = K d,   Z = z + G~^T e,   W = G_0 Z   (the block pipeline of post_orth_f:
+//   W_i = Z_i + (G~ Z)_i for i < f, W_t = sum_{l<f} g~_{l,t} Z_l - Z_t for t >= f).
+// The correction is formed from the drift itself, so the coefficients' rounding in the
+// storage type perturbs W only by that rounding times |G~^T K| <= 1/2 (no cancellation of
+// the large (I + G~^T G~) z against G~^T G~ z); with D = 0, W is G_0 Q_1 computed as the
+// paper's pipeline.
 
 // K from the FP64 generator: Cholesky L L^T = I_f + G~ G~^T (Golub and Van Loan, the outer
 // product form), then K = L^{-T} L^{-1} column by column; one thread (f <= kMaxF).
@@ -589,8 +594,9 @@ __global__ void k_post_orth_coef(int f, int p_r, const double* __restrict__ Gt, 
 
 // One thread per (position s, column j), 32 x 8 threads per CTA.  ONE: every block row of the
 // position in registers (p_r <= 32), Q_1 and Q_2 read once; otherwise two passes over Q_1
-// (Y first, then Z and W), the f values Z_0 .. Z_{f-1} kept between them.  Coefficients in
-// shared memory.  W may alias Q_1: each thread reads its own position before writing it.
+// (d first, then Z, G~ Z and the rows t >= f of W), the f values Z_0 .. Z_{f-1} kept between
+// them.  Coefficients in shared memory.  W may alias Q_1: each thread reads its own position
+// before writing it.
 template <typename T, int F, bool ONE>
 __global__ void __launch_bounds__(256) k_post_orth_proj(Geo g, const T* __restrict__ Gt,
                                                         const T* __restrict__ Kt, const T* Q,
@@ -611,51 +617,47 @@ __global__ void __launch_bounds__(256) k_post_orth_proj(Geo g, const T* __restri
   if (s >= mb || col >= k) return;
   const T* qc = Q + col * ldq;
   T* wc = W + col * ldw;
-  T c[NF], Y[NF], U[NF], a[NF];
+  T d[NF], e[NF], a[NF];
 #pragma unroll
   for (int i = 0; i < NF; ++i) {
-    c[i] = (i < f) ? qc[g.m_pad + (int64_t)i * mb + s] : T(0);
-    Y[i] = T(0);
+    d[i] = (i < f) ? qc[g.m_pad + (int64_t)i * mb + s] : T(0);
     a[i] = T(0);
   }
   if constexpr (ONE) {
     T z[PR];
 #pragma unroll
     for (int t = 0; t < PR; ++t) z[t] = (t < p_r) ? qc[(int64_t)t * mb + s] : T(0);
+    // d = c - G~ z
 #pragma unroll
-    for (int t = 0; t < PR; ++t) {
-      if (t < p_r) {
-        T h = z[t];
-#pragma unroll
-        for (int i = 0; i < NF; ++i)
-          if (i < f) h += sG[i * p_r + t] * c[i];
-        z[t] = h;
+    for (int t = 0; t < PR; ++t)
+      if (t < p_r)
 #pragma unroll
         for (int i = 0; i < NF; ++i)
-          if (i < f) Y[i] += sG[i * p_r + t] * h;
-      }
-    }
+          if (i < f) d[i] -= sG[i * p_r + t] * z[t];
+    // e = K d
 #pragma unroll
     for (int i = 0; i < NF; ++i) {
       T u = T(0);
 #pragma unroll
       for (int l = 0; l < NF; ++l)
-        if (l < f) u += sK[i * f + l] * Y[l];
-      U[i] = u;
+        if (l < f) u += sK[i * f + l] * d[l];
+      e[i] = u;
     }
+    // Z = z + G~^T e, a = G~ Z
 #pragma unroll
     for (int t = 0; t < PR; ++t) {
       if (t < p_r) {
-        T zv = z[t];
+        T zt = z[t];
 #pragma unroll
         for (int i = 0; i < NF; ++i)
-          if (i < f) zv -= sG[i * p_r + t] * U[i];
-        z[t] = zv;
+          if (i < f) zt += sG[i * p_r + t] * e[i];
+        z[t] = zt;
 #pragma unroll
         for (int i = 0; i < NF; ++i)
-          if (i < f) a[i] += sG[i * p_r + t] * zv;
+          if (i < f) a[i] += sG[i * p_r + t] * zt;
       }
     }
+    // W = G_0 Z
 #pragma unroll
     for (int t = 0; t < PR; ++t) {
       if (t < p_r) {
@@ -673,68 +675,62 @@ __global__ void __launch_bounds__(256) k_post_orth_proj(Geo g, const T* __restri
       }
     }
   } else {
-  // two passes: Y over every block row, then Z, a and the rows t >= f of W
-  for (int t0 = 0; t0 < p_r; t0 += 8) {
-    T z[8];
+    // pass 1: d = c - G~ z over every block row
+    for (int t0 = 0; t0 < p_r; t0 += 8) {
+      T z[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) z[u] = (t0 + u < p_r) ? qc[(int64_t)(t0 + u) * mb + s] : T(0);
+      for (int u = 0; u < 8; ++u) z[u] = (t0 + u < p_r) ? qc[(int64_t)(t0 + u) * mb + s] : T(0);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int t = t0 + u;
-      if (t < p_r) {
-        T h = z[u];
-#pragma unroll
-        for (int i = 0; i < NF; ++i)
-          if (i < f) h += sG[i * p_r + t] * c[i];
-#pragma unroll
-        for (int i = 0; i < NF; ++i)
-          if (i < f) Y[i] += sG[i * p_r + t] * h;
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < NF; ++i) {
-    T u = T(0);
-#pragma unroll
-    for (int l = 0; l < NF; ++l)
-      if (l < f) u += sK[i * f + l] * Y[l];
-    U[i] = u;
-  }
-  T zf[NF];
-#pragma unroll
-  for (int i = 0; i < NF; ++i) zf[i] = T(0);
-  for (int t0 = 0; t0 < p_r; t0 += 8) {
-    T z[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) z[u] = (t0 + u < p_r) ? qc[(int64_t)(t0 + u) * mb + s] : T(0);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int t = t0 + u;
-      if (t < p_r) {
-        T zv = z[u];
-#pragma unroll
-        for (int i = 0; i < NF; ++i)
-          if (i < f) zv += sG[i * p_r + t] * (c[i] - U[i]);
-#pragma unroll
-        for (int i = 0; i < NF; ++i)
-          if (i < f) a[i] += sG[i * p_r + t] * zv;
-        if (t < f) {
+      for (int u = 0; u < 8; ++u)
+        if (t0 + u < p_r)
 #pragma unroll
           for (int i = 0; i < NF; ++i)
-            if (i == t) zf[i] = zv;
-        } else {
-          T w = T(0);
+            if (i < f) d[i] -= sG[i * p_r + t0 + u] * z[u];
+    }
 #pragma unroll
-          for (int l = 0; l < NF; ++l)
-            if (l < f) w += sG[l * p_r + t] * zf[l];
-          wc[(int64_t)t * mb + s] = w - zv;
+    for (int i = 0; i < NF; ++i) {
+      T u = T(0);
+#pragma unroll
+      for (int l = 0; l < NF; ++l)
+        if (l < f) u += sK[i * f + l] * d[l];
+      e[i] = u;
+    }
+    // pass 2: Z, a = G~ Z, and the rows t >= f of W (Z_0 .. Z_{f-1} come first)
+    T zf[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) zf[i] = T(0);
+    for (int t0 = 0; t0 < p_r; t0 += 8) {
+      T z[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) z[u] = (t0 + u < p_r) ? qc[(int64_t)(t0 + u) * mb + s] : T(0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u;
+        if (t < p_r) {
+          T zt = z[u];
+#pragma unroll
+          for (int i = 0; i < NF; ++i)
+            if (i < f) zt += sG[i * p_r + t] * e[i];
+#pragma unroll
+          for (int i = 0; i < NF; ++i)
+            if (i < f) a[i] += sG[i * p_r + t] * zt;
+          if (t < f) {
+#pragma unroll
+            for (int i = 0; i < NF; ++i)
+              if (i == t) zf[i] = zt;
+          } else {
+            T w = T(0);
+#pragma unroll
+            for (int l = 0; l < NF; ++l)
+              if (l < f) w += sG[l * p_r + t] * zf[l];
+            wc[(int64_t)t * mb + s] = w - zt;
+          }
         }
       }
     }
-  }
 #pragma unroll
-  for (int i = 0; i < NF; ++i)
-    if (i < f) wc[(int64_t)i * mb + s] = zf[i] + a[i];
+    for (int i = 0; i < NF; ++i)
+      if (i < f) wc[(int64_t)i * mb + s] = zf[i] + a[i];
   }
 }
 

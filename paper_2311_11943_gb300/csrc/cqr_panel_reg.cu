@@ -57,6 +57,16 @@ __device__ __forceinline__ void mbar_expect(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
                ::"r"(saddr(bar)), "r"(bytes) : "memory");
 }
+// non-blocking probe of the phase (the waits below use it when a bound shorter than the
+// hardware's own suspend interval of try_wait is set)
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\t"
+               "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(ok) : "r"(saddr(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   uint32_t ok;
   asm volatile("{\n\t.reg .pred p;\n\t"
@@ -234,7 +244,11 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
     bool ok = true;
     const long long t0 = clock64();
     unsigned spins = 0u;
-    while (!mbar_try_wait(mbar + par, (phases >> par) & 1u)) {
+    // try_wait may suspend the thread for the hardware's own interval before it returns; a
+    // bound shorter than that (set by coded_qr_set_wait_limit) polls with test_wait instead
+    const bool short_bound = wait_limit < kPollAfterCycles;
+    while (!(short_bound ? mbar_test_wait(mbar + par, (phases >> par) & 1u)
+                         : mbar_try_wait(mbar + par, (phases >> par) & 1u))) {
       const long long el = clock64() - t0;
       if (el > wait_limit) {
         set_status(status, CQR_ETIMEOUT, 40);

@@ -105,6 +105,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm,
       : "memory");
 }
 
+// L2 prefetch of one tensor-map box (no shared memory, no completion to wait for)
+__device__ __forceinline__ void tma_prefetch_l2(const CUtensorMap* tm, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];"
+               ::"l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y)
+               : "memory");
+}
+
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* tm) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
 }
@@ -186,12 +193,15 @@ __device__ __forceinline__ float tf32_hi(float x) {
 struct TcMaps {
   CUtensorMap a[2];  // A hi / lo (lo unused for one product)
   CUtensorMap b[2];  // B hi / lo; with an in-smem split only b[0] (raw FP32) is loaded
+  CUtensorMap c;     // subtract epilogue: the FP32 output (Q), boxes of 32 rows x BN columns
 };
 
 struct TcJob {
   int nprod;          // 1 (TF32) or 3 (3xTF32)
   int split_b_smem;   // 1: B arrives raw and is split in shared memory
   int epi;            // 0: store partial P[s] ; 1: C -= D
+  int prefetch_c;     // epi 1: prefetch each output tile into L2 when its loads start
+  int64_t c_col0;     // epi 1: column of `out` in the tensor map of C
   int m_tiles, n_tiles, splits;
   int64_t a_row0;     // A tile y coordinate offset (rows of the MMA M dimension)
   int64_t b_row0;     // B tile y coordinate offset
@@ -292,6 +302,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
         const int mt = mn % job.m_tiles, nt = mn / job.m_tiles;
         const int nk = kblocks(split);
         const int64_t kbase = job.k0 + (int64_t)split * job.kchunk;
+        if (job.prefetch_c) {
+          // the output tile (BM rows x BN columns of C) is read by the epilogue once this
+          // tile's products are done: start bringing it into L2 now
+          const int y = (int)(job.c_col0 + (int64_t)nt * BN);
+          for (int r = 0; r < BM; r += 32) tma_prefetch_l2(&maps.c, mt * BM + r, y);
+        }
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = it % STAGES;
           if (!mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag)) break;
@@ -866,12 +882,32 @@ void tc_set_status(TcGemm* t, int* status) { t->status = status; }
 void tc_set_pdl_stream(TcGemm* t, cudaStream_t st) { t->pdl_st = st; }
 
 namespace {
+// Split-K factor of a product with m1 x n1 output tiles and K = M rows: the count s whose
+// launch finishes first on `ctas` persistent CTAs, i.e. the least (waves of work units) x
+// (K blocks per unit), each unit one tile and one K chunk; a split adds partial-sum traffic,
+// so each split costs 2% more and ties go to fewer splits.
+// K blocks per work unit for `tiles` output tiles and `kblocks` K blocks on `ctas` CTAs, at
+// most max_splits chunks (see tc_splits).
+int64_t best_kchunk(int64_t tiles, int64_t kblocks, int ctas, int max_splits) {
+  int64_t best_kc = kblocks;
+  double best = -1.0;
+  for (int s = 1; s <= max_splits && s <= kblocks; ++s) {
+    const int64_t kc = (kblocks + s - 1) / s;
+    const int64_t units = tiles * ((kblocks + kc - 1) / kc);
+    const int64_t waves = (units + ctas - 1) / ctas;
+    const double cost = (double)waves * (double)kc * (1.0 + 0.02 * s);
+    if (best < 0.0 || cost < best) {
+      best = cost;
+      best_kc = kc;
+    }
+  }
+  return best_kc;
+}
+
 int tc_splits(const TcGemm* t, int m1, int n1, int64_t* kchunk, int max_ctas = 0) {
   const int ctas = max_ctas > 0 ? std::min(max_ctas, t->num_sms) : t->num_sms;
-  int splits = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplits, (ctas + m1 * n1 - 1) / (m1 * n1)));
   const int64_t kblocks = (t->M + t->KE - 1) / t->KE;
-  if (splits > kblocks) splits = (int)kblocks;
-  *kchunk = (kblocks + splits - 1) / splits * t->KE;
+  *kchunk = best_kchunk((int64_t)m1 * n1, kblocks, ctas, kMaxSplits) * t->KE;
   return (int)((t->M + *kchunk - 1) / *kchunk);
 }
 }  // namespace
@@ -1002,6 +1038,9 @@ cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, int buf, in
   job.ldo = t->ldq;
   job.split_stride = 0;
   job.status = t->status;
+  maps.c = t->tm_q_b;
+  job.prefetch_c = 1;
+  job.c_col0 = j0;
   return launch_mode(t, false, maps, job, st, max_ctas);
 }
 
@@ -1049,16 +1088,15 @@ cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr
   job.epi = 1;
   job.m_tiles = (int)((t->M + BM - 1) / BM);
   job.n_tiles = (bk + BN - 1) / BN;
-  // Split K (the kb computed columns) when the M x bk output has too few tiles to fill the
-  // SMs; the partials go to P (capacity kMaxSplits * bkp * N floats) and are subtracted in
-  // a fixed order, so the result does not depend on the schedule.
+  // Split K (the kb computed columns) when that makes the launch finish sooner on the SMs
+  // (too few M x bk output tiles, or a last wave mostly idle); the partials go to P (capacity
+  // kMaxSplits * bkp * N floats) and are subtracted in a fixed order, so the result does not
+  // depend on the schedule.
   const int64_t kblk = kbp / KE;
   const int tiles2 = job.m_tiles * job.n_tiles;
-  int64_t want = std::min<int64_t>(std::min<int64_t>(kMaxSplits, kblk), t->num_sms / std::max(1, tiles2));
-  const int64_t cap = (int64_t)kMaxSplits * t->bkp * t->N / (t->M * (int64_t)bk);
-  want = std::min<int64_t>(want, cap);
-  int64_t kchunk2 = kbp;
-  if (want > 1) kchunk2 = (kblk + want - 1) / want * KE;
+  const int64_t cap = std::min<int64_t>(kMaxSplits, (int64_t)kMaxSplits * t->bkp * t->N /
+                                                        (t->M * (int64_t)bk));
+  const int64_t kchunk2 = best_kchunk(tiles2, kblk, t->num_sms, (int)std::max<int64_t>(1, cap)) * KE;
   const int splits2 = (int)((kbp + kchunk2 - 1) / kchunk2);
   job.splits = splits2;
   job.a_row0 = 0;

@@ -6,6 +6,7 @@ library's public API.  Each case runs twice (the first run warms up the handle).
   python -m paper_2311_11943_gb300.profile_cases bfactor64  # 64 batched instances, no erasure
   python -m paper_2311_11943_gb300.profile_cases adjoint    # 8192 x 1024: forward + both adjoints
   python -m paper_2311_11943_gb300.profile_cases bandwidth8192  # encode / decode / post-orth
+  python -m paper_2311_11943_gb300.profile_cases c3_tall    # the 16384^2 workload's panel shape
 
 Launch order per run (for ncu's --launch-skip; filter by kernel name with -k, as the commands
 in profiles/ do, since two streams interleave):
@@ -16,6 +17,8 @@ in profiles/ do, since two streams interleave):
   bfactor64:        encode (2), one k_b_factor
   bandwidth8192:    encode (vertical, horizontal), panels 0-15, poison, decode (Q, R),
                     panels 16-31, post-orthogonalisation
+  c3_tall:          generator, encode (2), then per panel in one stream: block
+                    reorthogonalisation (from panel 1), panel, split, GEMM1, reduce, GEMM2
 """
 import sys
 
@@ -113,8 +116,27 @@ def case_bandwidth():
     q.close()
 
 
+def case_c3_tall(panels=2):
+    """Panels 0 and 1 of a 16384 x 8192 N(0,1) problem on the 16384^2 workload's grid (16 x 16,
+    f = 4, b = 256): the panel is the same 20480 x 256 block as in the full problem, GEMM1 has
+    156 output tiles (the full problem: 316), about 2 GB on the device; FP32 3xTF32 with
+    block reorthogonalisation; twice."""
+    import torch
+    from . import binding as B
+    from . import synth
+    A = _cm(torch, B, synth.gaussian(16384, 8192, 3, dtype=np.float32))
+    q = B.CodedQR(16384, 8192, 16, 16, 4, 256, dtype="f32", mma="3xtf32", seed=3,
+                  reorth_block=True)
+    for _ in range(2):
+        q.encode(A)
+        q.factor(0, panels)
+    torch.cuda.synchronize()
+    assert q.sync_status() == 0
+    q.close()
+
+
 CASES = {"tc_c2": case_c2, "panel_c2": case_c2, "bfactor64": case_bfactor, "adjoint": case_adjoint,
-         "bandwidth8192": case_bandwidth}
+         "bandwidth8192": case_bandwidth, "c3_tall": case_c3_tall}
 
 if __name__ == "__main__":
     CASES[sys.argv[1]]()
