@@ -371,6 +371,8 @@ void ensure_panel_plan(cqr_handle h, int bk) {
   h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, true);
   if (h->plan.cluster && !panel_cluster_fits<T>(h->plan))
     h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, false);
+  if (h->plan.hier && !panel_hier_fits<T>(h->plan))
+    h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, h->plan.cluster != 0, false);
   h->reg_ok = false;
   const char* env = getenv("CQR_PANEL_REG");
   const bool left_looking = h->cfg.panel == CQR_PANEL_CGS1 || h->cfg.panel == CQR_PANEL_CGS2;

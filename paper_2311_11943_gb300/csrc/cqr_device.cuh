@@ -71,6 +71,71 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nblocks, unsig
   return s_ok != 0;
 }
 
+// ---- distributed shared memory exchanges within a thread-block cluster
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint32_t peer_addr(uint32_t local_addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
+  return r;
+}
+// 16 bytes into a peer's shared memory, completing 16 transaction bytes on its mbarrier
+__device__ __forceinline__ void st_async4(uint32_t dst, float4 v, uint32_t mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+               ::"r"(dst), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
+               ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+// non-blocking probe of the phase (the waits below use it when a bound shorter than the
+// hardware's own suspend interval of try_wait is set)
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\t"
+               "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(ok) : "r"(saddr(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\t"
+               "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(ok) : "r"(saddr(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+
+// Bounded wait for phase `parity` of a shared-memory mbarrier completed by peers' st.async
+// transactions.  Returns false after recording CQR_ETIMEOUT (detail `site`) when `limit`
+// cycles pass, or once any CTA has recorded an error while this wait is long overdue
+// (kPollAfterCycles).  try_wait may suspend the thread for the hardware's own interval before
+// it returns, so a bound shorter than kPollAfterCycles (set by coded_qr_set_wait_limit) polls
+// with test_wait instead.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long limit,
+                                                  int* status, int site) {
+  const long long t0 = clock64();
+  unsigned spins = 0u;
+  const bool short_bound = limit < kPollAfterCycles;
+  while (!(short_bound ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity))) {
+    const long long el = clock64() - t0;
+    if (el > limit) {
+      set_status(status, CQR_ETIMEOUT, site);
+      return false;
+    }
+    if (el > kPollAfterCycles && (++spins & 63u) == 0u && ld_relaxed_i32(status + ST_CODE) != 0)
+      return false;
+  }
+  return true;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

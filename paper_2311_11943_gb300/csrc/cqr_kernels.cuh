@@ -32,6 +32,7 @@ struct PanelPlan {
   int rpc_pad;    // shared-memory column stride
   int smem;       // 1: panel slice resident in shared memory
   int cluster;    // 1: one thread-block cluster (distributed shared memory reductions)
+  int hier;       // 1: grid of clusters with the two-level exchange (FP32, shared-memory slices)
   size_t smem_bytes;
 };
 
@@ -43,9 +44,14 @@ template <typename T>
 cudaError_t launch_encode(const Geo& g, const T* A, int64_t lda, const T* Gt, const T* Gh, T* Q,
                           cudaStream_t st);
 
-PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_cluster);
+// allow_hier: a grid of more than 48 FP32 CTAs may use the two-level exchange (clusters of 8)
+PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_cluster,
+                     bool allow_hier = true);
 template <typename T>
 bool panel_cluster_fits(const PanelPlan& pp);
+// Whether every cluster of a two-level plan can be resident at once.
+template <typename T>
+bool panel_hier_fits(const PanelPlan& pp);
 size_t panel_partial_bytes(int bk, size_t elem, int num_sms);
 
 // Register-resident FP32 panel in one cluster (cqr_panel_reg.cu).

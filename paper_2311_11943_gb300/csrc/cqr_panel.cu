@@ -30,6 +30,10 @@ constexpr int kNT = 512;
 constexpr int kNW = kNT / 32;
 constexpr size_t kSmemCap = 227 * 1024;
 constexpr int kMaxCluster = 16;
+// Two-level exchange of the grid variant: clusters of kHierCS CTAs, used for FP32 panels
+// that need more than kHierMinG CTAs.
+constexpr int kHierCS = 8;
+constexpr int kHierMinG = 48;
 
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
@@ -90,33 +94,147 @@ struct Ctx {
   int64_t cs;    // column stride of the slice
   int nr;        // rows owned
   int pld;       // padded panel width
-  T* gpart;      // grid variant: [2][G][2*pld]
-  T* lpart;      // cluster variant: this CTA's [2][2*pld] in shared memory
+  T* gpart;      // grid variant: [2][G][2*pld]; two-level: [G][2*pld] (first reduction) then
+                 // [2][clusters][2*pld] cluster sums
+  T* lpart;      // cluster and two-level variants: this CTA's [2][2*pld] in shared memory
   T* red;        // grid variant: shared [8][2*pld] scratch
+  T* rbuf;       // two-level, cluster leader: receive buffer [2][kHierCS][pld]
+  uint64_t* mbar;  // two-level: [2] mbarriers of rbuf (used in the leader)
   unsigned* bar;
   int* status;
   unsigned target;
-  long long wait_limit;  // bound of each grid-barrier wait, SM cycles
+  unsigned phases;   // two-level: bit p = phase parity of mbar[p]
+  int crank, cl, ncl;  // two-level: rank in the cluster, cluster index, clusters
+  long long wait_limit;  // bound of each wait on other CTAs, SM cycles
 };
 
-template <typename T, bool CL>
+// SMP: the partial vectors live in shared memory (cluster and two-level variants)
+template <typename T, bool SMP>
 __device__ __forceinline__ void put_partial(const Ctx<T>& c, int idx, T val, int step) {
-  if (CL)
+  if (SMP)
     c.lpart[(step & 1) * 2 * c.pld + idx] = val;
   else
     c.gpart[((size_t)(step & 1) * gridDim.x + blockIdx.x) * 2 * c.pld + idx] = val;
+}
+
+// out[a] = sum over r < rows of P[r * stride + a] for lo <= a < hi, with P in global memory
+// (L2).  Each entry is summed by gr adjacent lanes (rows gr apart, four loads in flight) and
+// combined by a butterfly over those lanes: a fixed order, the same in every CTA.  Every
+// thread of the CTA must call it.
+template <typename T>
+__device__ __forceinline__ void reduce_rows(const T* P, int rows, size_t stride, int lo, int hi,
+                                            T* out) {
+  const int n = hi - lo, tid = threadIdx.x;
+  if (n <= 0) return;
+  int gr = 1;
+  while (gr < 8 && gr * 2 * n <= kNT && gr * 2 <= rows) gr *= 2;
+  const int total = n * gr;
+  for (int base = 0; base < total; base += kNT) {
+    const int idx = base + tid;
+    const int e = idx / gr, m = idx - e * gr;
+    T acc = T(0);
+    if (idx < total) {
+      const int a = lo + e;
+      int r = m;
+      for (; r + 3 * gr < rows; r += 4 * gr) {
+        const T x0 = __ldcg(P + (size_t)r * stride + a);
+        const T x1 = __ldcg(P + (size_t)(r + gr) * stride + a);
+        const T x2 = __ldcg(P + (size_t)(r + 2 * gr) * stride + a);
+        const T x3 = __ldcg(P + (size_t)(r + 3 * gr) * stride + a);
+        acc += x0; acc += x1; acc += x2; acc += x3;
+      }
+      for (; r < rows; r += gr) acc += __ldcg(P + (size_t)r * stride + a);
+    }
+    for (int o = 1; o < gr; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (idx < total && m == 0) out[lo + e] = acc;
+  }
 }
 
 struct NoHook {
   __device__ void operator()() const {}
 };
 
+// Wait (thread 0, bounded) until the global counter has received `count` more arrivals,
+// without arriving: the two-level exchange, where only cluster leaders arrive.
+__device__ __forceinline__ bool wait_count(unsigned* bar, unsigned count, unsigned& target,
+                                           int* status, int site, long long limit) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    target += count;
+    int ok = 1;
+    const long long t0 = clock64();
+    while (ld_acquire_u32(bar) < target) {
+      if (ld_relaxed_i32(status + ST_CODE) == CQR_ETIMEOUT) { ok = 0; break; }
+      if (clock64() - t0 > limit) {
+        set_status(status, CQR_ETIMEOUT, site);
+        status[ST_SITE] = site;
+        ok = 0;
+        break;
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // Synchronise and reduce entries [lo, hi) of the partial vectors into out[].  `hook` runs
 // right after the barrier, when every thread of this CTA has finished the step's reads.
-template <typename T, bool CL, typename Hook = NoHook>
+// HIER (two-level, FP32): the CTAs of each cluster push their partials (16-byte st.async) into
+// the leader's receive buffer; the leader sums them in rank order, writes the cluster sum to
+// global memory and arrives on the counter; every CTA waits for all leaders and sums the
+// cluster sums in cluster order.  The first reduction (v and eta, wider than one buffer row)
+// goes through global memory from every CTA, as in the grid variant.
+template <typename T, bool CL, bool HIER = false, typename Hook = NoHook>
 __device__ __forceinline__ bool sync_reduce(Ctx<T>& c, int lo, int hi, T* out, int step, int site,
                                             Hook hook = Hook()) {
   const int G = gridDim.x, tid = threadIdx.x;
+  if constexpr (HIER) {
+    const int par = step & 1;
+    if (hi <= c.pld) {
+      const int c0 = lo / 4, c1 = (hi + 3) / 4;
+      __syncthreads();  // this CTA's partials are complete; no thread reads the step's columns
+      hook();
+      const uint32_t lead_buf =
+          map_peer(smem_addr(c.rbuf + ((size_t)par * kHierCS + c.crank) * c.pld), 0);
+      const uint32_t lead_bar = map_peer(smem_addr(c.mbar + par), 0);
+      if (c.crank == 0 && tid == 0) mbar_expect(c.mbar + par, (unsigned)(kHierCS * (c1 - c0) * 16));
+      for (int ch = c0 + tid; ch < c1; ch += kNT)
+        st_async4(lead_buf + 16u * ch,
+                  *reinterpret_cast<const float4*>(c.lpart + par * 2 * c.pld + 4 * ch), lead_bar);
+      if (c.crank == 0) {
+        const bool ok = mbar_wait_bounded(c.mbar + par, (c.phases >> par) & 1u, c.wait_limit,
+                                          c.status, site);
+        c.phases ^= 1u << par;
+        if (!__syncthreads_and(ok)) return false;
+        // cluster sums: rows G + par ncl + cl of the partial buffer (rows below G hold the
+        // first reduction's per-CTA partials, which slower CTAs may still be reading)
+        T* dst = c.gpart + ((size_t)G + par * c.ncl + c.cl) * 2 * c.pld;
+        for (int a = lo + tid; a < hi; a += kNT) {
+          T sum = T(0);
+#pragma unroll
+          for (int k = 0; k < kHierCS; ++k) sum += c.rbuf[((size_t)par * kHierCS + k) * c.pld + a];
+          dst[a] = sum;
+        }
+        __syncthreads();
+        if (tid == 0)
+          asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(c.bar), "r"(1u) : "memory");
+      }
+      if (!wait_count(c.bar, (unsigned)c.ncl, c.target, c.status, site, c.wait_limit)) return false;
+      reduce_rows(c.gpart + ((size_t)G + par * c.ncl) * 2 * c.pld, c.ncl, (size_t)2 * c.pld, lo,
+                  hi, out);
+      __syncthreads();
+      return true;
+    }
+    __syncthreads();
+    T* dst = c.gpart + ((size_t)par * G + blockIdx.x) * 2 * c.pld;
+    for (int a = lo + tid; a < hi; a += kNT) dst[a] = c.lpart[par * 2 * c.pld + a];
+    if (!grid_barrier(c.bar, G, c.target, c.status, site, c.wait_limit)) return false;
+    hook();
+    reduce_rows(c.gpart + (size_t)par * G * 2 * c.pld, G, (size_t)2 * c.pld, lo, hi, out);
+    __syncthreads();
+    return true;
+  }
   if (CL) {
     cluster_sync_all();
     hook();
@@ -219,7 +337,7 @@ struct LaneOps<T, 1> {
   __device__ static T sum(V v) { return v; }
 };
 
-template <typename T, int RPL, bool CL, bool SMEM>
+template <typename T, int RPL, bool CL, bool SMEM, bool HIER>
 __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq, T* __restrict__ R,
                                                    int64_t ldr, int64_t M, int bk, int rpc,
                                                    int rpc_pad, double tau2, T* gpart,
@@ -248,12 +366,37 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
   c.gpart = gpart;
   c.red = sv + 2 * pld;
   c.lpart = c.red + (CL ? 0 : 8 * 2 * pld);
+  c.rbuf = c.red;
+  c.mbar = reinterpret_cast<uint64_t*>(c.lpart + 4 * pld);
   c.bar = bar;
   c.status = status;
   c.target = 0;
+  c.phases = 0u;
+  c.crank = g % kHierCS;
+  c.cl = g / kHierCS;
+  c.ncl = gridDim.x / kHierCS;
   c.wait_limit = wait_limit;
   int step = 0;
   auto ok_row = [&](int r) { return SMEM ? true : (r < nr); };
+  // leaving after an abandoned exchange: the two-level variant first meets the rest of its
+  // cluster (whose stores into the leader's shared memory were all issued before it arrived)
+  // and leaves them time to land
+  auto leave = [&]() {
+    if (HIER) {
+      cluster_sync_all();
+      const long long t0 = clock64();
+      while (clock64() - t0 < kDrainCycles) {
+      }
+    }
+  };
+  if (HIER) {
+    if (tid == 0) {
+      mbar_init(c.mbar, 1);
+      mbar_init(c.mbar + 1, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cluster_sync_all();  // the leader's mbarriers are initialised before any CTA sends
+  }
 
   if (SMEM)
     for (int a = 0; a < bk; ++a)
@@ -284,11 +427,11 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
       }
       T s0 = warp_sum(L::sum(d0)), s1 = warp_sum(L::sum(d1));
       if (lane == 0) {
-        put_partial<T, CL>(c, a, s0, step);
-        put_partial<T, CL>(c, pld + a, s1, step);
+        put_partial<T, CL || HIER>(c, a, s0, step);
+        put_partial<T, CL || HIER>(c, pld + a, s1, step);
       }
     }
-    if (!sync_reduce<T, CL>(c, 0, 2 * pld, v, step++, 1)) return;
+    if (!sync_reduce<T, CL, HIER>(c, 0, 2 * pld, v, step++, 1)) { leave(); return; }
   }
 
   for (int j = 0; j < bk; ++j) {
@@ -309,9 +452,9 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
           if (ok_row(r)) d = L::fma(L::ld(pa + r), pn[i], d);
         }
         const T s0 = warp_sum(L::sum(d));
-        if (lane == 0) put_partial<T, CL>(c, a, s0, step);
+        if (lane == 0) put_partial<T, CL || HIER>(c, a, s0, step);
       }
-      if (!sync_reduce<T, CL>(c, 0, j, sv, step++, 3)) return;
+      if (!sync_reduce<T, CL, HIER>(c, 0, j, sv, step++, 3)) { leave(); return; }
       T* pjw = c.base + j * c.cs;
       for (int r = tid; r < (SMEM ? rpc : nr); r += kNT) {
         T acc = pjw[r];
@@ -337,14 +480,14 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
           if (ok_row(r)) d = L::fma(L::ld(pa + r), pn[i], d);
         }
         const T s0 = warp_sum(L::sum(d));
-        if (lane == 0) put_partial<T, CL>(c, a, s0, step);
+        if (lane == 0) put_partial<T, CL || HIER>(c, a, s0, step);
       }
-      if (!sync_reduce<T, CL>(c, j, bk, v, step++, 4)) return;
+      if (!sync_reduce<T, CL, HIER>(c, j, bk, v, step++, 4)) { leave(); return; }
     }
     const T v0 = v[j];
     if (!(v0 > T(0)) || !isfinite(v0)) {
       if (g == 0 && tid == 0) set_status(status, CQR_EBREAKDOWN, col0 + j);
-      if (CL) cluster_sync_all();
+      if (CL || HIER) cluster_sync_all();
       return;
     }
     const T rjj = sqrt(v0);
@@ -401,8 +544,8 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
         sb += __shfl_xor_sync(0xffffffffu, sb, o);
       }
       if (lane == 0) {
-        put_partial<T, CL>(c, a, sa, step);
-        put_partial<T, CL>(c, b2, sb, step);
+        put_partial<T, CL || HIER>(c, a, sa, step);
+        put_partial<T, CL || HIER>(c, b2, sb, step);
       }
     }
     if (a < bk) {
@@ -426,7 +569,7 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
         }
       }
       const T sa = warp_sum(L::sum(da));
-      if (lane == 0) put_partial<T, CL>(c, a, sa, step);
+      if (lane == 0) put_partial<T, CL || HIER>(c, a, sa, step);
     }
     T* pjw = c.base + j * c.cs;
     T* pj1w = c.base + (j + 1) * c.cs;
@@ -451,13 +594,13 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
           }
         }
     };
-    if (!sync_reduce<T, CL>(c, j + 1, bk, v, step++, 2, publish)) return;
+    if (!sync_reduce<T, CL, HIER>(c, j + 1, bk, v, step++, 2, publish)) { leave(); return; }
   }
   __syncthreads();
   if (SMEM)
     for (int a = 0; a < bk; ++a)
       for (int r = tid; r < nr; r += kNT) Q[row0 + r + a * ldq] = sm[(size_t)a * rpc_pad + r];
-  if (CL) cluster_sync_all();  // peers may still read this CTA's partials
+  if (CL || HIER) cluster_sync_all();  // peers may still read this CTA's partials
 }
 
 // Left-looking classical Gram-Schmidt on the panel (the variants compared in NEXT f3):
@@ -556,9 +699,11 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_cgs(T* __restrict__ Q, int64_t
   if (CL) cluster_sync_all();  // peers may still read this CTA's partials
 }
 
-size_t small_bytes(int bk, size_t elem, bool cl) {
+size_t small_bytes(int bk, size_t elem, bool cl, bool hier = false) {
   const int pld = (bk + 3) / 4 * 4;
-  // v (2 pld, includes eta), sv (2 pld), then either red [8][2 pld] or lpart [2][2 pld]
+  // v (2 pld, includes eta), sv (2 pld), then either red [8][2 pld] or lpart [2][2 pld];
+  // two-level: red (the leader's receive buffer), lpart and two mbarriers
+  if (hier) return (size_t)(2 * pld + 2 * pld + 16 * pld + 4 * pld) * elem + 16 + 256;
   return (size_t)(2 * pld + 2 * pld + (cl ? 4 * pld : 16 * pld)) * elem + 256;
 }
 
@@ -579,9 +724,28 @@ template <typename T, int RPL>
 const void* kernel_of(bool cl, bool smem, int variant) {
   if (variant == 1) return cgs_of<T, RPL, 1>(cl, smem);
   if (variant == 2) return cgs_of<T, RPL, 2>(cl, smem);
-  if (cl) return (const void*)k_panel<T, RPL, true, true>;
-  if (smem) return (const void*)k_panel<T, RPL, false, true>;
-  return (const void*)k_panel<T, RPL, false, false>;
+  if (cl) return (const void*)k_panel<T, RPL, true, true, false>;
+  if (smem) return (const void*)k_panel<T, RPL, false, true, false>;
+  return (const void*)k_panel<T, RPL, false, false, false>;
+}
+
+template <typename T, int RPL>
+const void* hier_of() {
+  if constexpr (sizeof(T) == 4) return (const void*)k_panel<T, RPL, false, true, true>;
+  return nullptr;
+}
+
+template <typename T>
+const void* pick_hier(int rpl) {
+  switch (rpl) {
+    case 4: return hier_of<T, 4>();
+    case 6: return hier_of<T, 6>();
+    case 8: return hier_of<T, 8>();
+    case 12: return hier_of<T, 12>();
+    case 16: return hier_of<T, 16>();
+    case 24: return hier_of<T, 24>();
+    default: return hier_of<T, 32>();
+  }
 }
 
 template <typename T>
@@ -611,7 +775,8 @@ int rpl_for_rows(int rpc) {
 // smallest RPL whose slices fit shared memory and give G <= 16 CTAs (one cluster); otherwise
 // the smallest RPL that fits shared memory with G <= #SMs (grid barrier); otherwise slices in
 // global memory.  CQR_PANEL_RPL / CQR_PANEL_CLUSTER override the choice (tuning).
-PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_cluster) {
+PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_cluster,
+                     bool allow_hier) {
   PanelPlan p{};
   const int rpl_env = env_int("CQR_PANEL_RPL", 0);
   const int cl_env = env_int("CQR_PANEL_CLUSTER", -1);
@@ -647,6 +812,17 @@ PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_clu
     p.G = (int)((M + p.rpc - 1) / p.rpc);
     p.rpc_pad = p.rpc;
     p.smem_bytes = (size_t)bk * p.rpc_pad * elem + small_bytes(bk, elem, best_cl);
+    // many CTAs (FP32): the two-level exchange, the grid padded to whole clusters (the extra
+    // CTAs own no rows)
+    if (!best_cl && allow_hier && elem == 4 && p.G > kHierMinG && env_int("CQR_PANEL_HIER", 1) != 0) {
+      const int Gh = (p.G + kHierCS - 1) / kHierCS * kHierCS;
+      const size_t sb = (size_t)bk * p.rpc_pad * elem + small_bytes(bk, elem, false, true);
+      if (Gh <= num_sms && sb + 1024 <= kSmemCap) {
+        p.hier = 1;
+        p.G = Gh;
+        p.smem_bytes = sb;
+      }
+    }
     return p;
   }
   // slices stay in global memory (L2): at most 32 rows per lane
@@ -660,6 +836,57 @@ PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_clu
   p.rpc_pad = p.rpc;
   p.smem_bytes = small_bytes(bk, elem, false);
   return p;
+}
+
+// Launch configuration of the two-level variant: clusters of kHierCS CTAs over the whole
+// grid.  Its leaders wait for one another, so every cluster must be resident at once: the
+// plan is taken only when the occupancy query says they fit (panel_hier_fits), and the
+// launch asks for the cooperative guarantee as well where the runtime accepts it together
+// with clusters (remembered after the first attempt).
+template <typename T>
+void hier_config(const PanelPlan& pp, const void* fn, cudaStream_t st, cudaLaunchConfig_t* cfg,
+                 cudaLaunchAttribute* attr, bool coop) {
+  *cfg = cudaLaunchConfig_t{};
+  cfg->gridDim = dim3(pp.G);
+  cfg->blockDim = dim3(kNT);
+  cfg->dynamicSmemBytes = pp.smem_bytes;
+  cfg->stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kHierCS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeCooperative;
+  attr[1].val.cooperative = 1;
+  cfg->attrs = attr;
+  cfg->numAttrs = coop ? 2 : 1;
+  (void)fn;
+}
+
+int g_hier_coop = -1;  // -1 not tried, 1 cooperative cluster launches accepted, 0 refused
+
+template <typename T>
+cudaError_t launch_hier(const PanelPlan& pp, int rpl, void** args, cudaStream_t st) {
+  const void* fn = pick_hier<T>(rpl);
+  if (!fn) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)pp.smem_bytes);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[2];
+  const int coop = __atomic_load_n(&g_hier_coop, __ATOMIC_RELAXED);
+  if (coop != 0) {
+    hier_config<T>(pp, fn, st, &cfg, attr, true);
+    e = cudaLaunchKernelExC(&cfg, fn, args);
+    if (e == cudaSuccess) {
+      __atomic_store_n(&g_hier_coop, 1, __ATOMIC_RELAXED);
+      return e;
+    }
+    if (coop == 1) return e;
+    cudaGetLastError();
+    __atomic_store_n(&g_hier_coop, 0, __ATOMIC_RELAXED);
+  }
+  hier_config<T>(pp, fn, st, &cfg, attr, false);
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 template <typename T>
@@ -676,6 +903,7 @@ cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t l
   long long wl = wait_limit > 0 ? wait_limit : kWaitLimitCycles;
   void* args[] = {&Q, &ldq, &R, &ldr, &M, &bk, &rpc, &rpc_pad, &tau2, &part, &bar, &status, &col0,
                   &wl};
+  if (pp.hier && variant == 0) return launch_hier<T>(pp, rpl, args, st);
   const void* fn = pick_kernel<T>(rpl, pp.cluster != 0, pp.smem != 0, variant);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)pp.smem_bytes);
@@ -731,6 +959,27 @@ bool panel_cluster_fits(const PanelPlan& pp) {
   return n >= 1;
 }
 
+template <typename T>
+bool panel_hier_fits(const PanelPlan& pp) {
+  if (!pp.hier) return false;
+  const void* fn = pick_hier<T>(rpl_for_rows(pp.rpc));
+  if (!fn) return false;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp.smem_bytes) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[2];
+  hier_config<T>(pp, fn, nullptr, &cfg, attr, false);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n >= pp.G / kHierCS;
+}
+
 size_t panel_partial_bytes(int bk, size_t elem, int num_sms) {
   const int pld = (bk + 3) / 4 * 4;
   return (size_t)2 * (num_sms + 1) * 2 * pld * elem;
@@ -744,6 +993,8 @@ template cudaError_t launch_panel<double>(const PanelPlan&, double*, int64_t, do
                                           cudaStream_t, int, long long);
 template bool panel_cluster_fits<float>(const PanelPlan&);
 template bool panel_cluster_fits<double>(const PanelPlan&);
+template bool panel_hier_fits<float>(const PanelPlan&);
+template bool panel_hier_fits<double>(const PanelPlan&);
 
 }  // namespace cqr
 
@@ -797,7 +1048,7 @@ cqr_status noalloc_run(int64_t M, int bk, T* Q, int64_t ldq, T* R, int64_t ldr, 
     cudaGetLastError();
     return CQR_ECUDA;
   }
-  PanelPlan pp = plan_panel(M, bk, sizeof(T), sms, false);
+  PanelPlan pp = plan_panel(M, bk, sizeof(T), sms, false, false);
   if (pp.G > kNoallocMaxG || pp.G > sms) return CQR_EINVAL;
   void* base = nullptr;
   if (noalloc_scratch(&base) != cudaSuccess) {

@@ -36,46 +36,6 @@ __device__ __forceinline__ void cl_sync() {
                ::: "memory");
 }
 
-__device__ __forceinline__ uint32_t saddr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint32_t peer_addr(uint32_t local_addr, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
-  return r;
-}
-// 16 bytes into a peer's shared memory, completing 16 transaction bytes on its mbarrier
-__device__ __forceinline__ void st_async4(uint32_t dst, float4 v, uint32_t mbar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
-               ::"r"(dst), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(mbar) : "memory");
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
-               ::"r"(saddr(bar)), "r"(bytes) : "memory");
-}
-// non-blocking probe of the phase (the waits below use it when a bound shorter than the
-// hardware's own suspend interval of try_wait is set)
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
-  uint32_t ok;
-  asm volatile("{\n\t.reg .pred p;\n\t"
-               "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-               "selp.u32 %0, 1, 0, p;\n\t}"
-               : "=r"(ok) : "r"(saddr(bar)), "r"(parity) : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  uint32_t ok;
-  asm volatile("{\n\t.reg .pred p;\n\t"
-               "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-               "selp.u32 %0, 1, 0, p;\n\t}"
-               : "=r"(ok) : "r"(saddr(bar)), "r"(parity) : "memory");
-  return ok != 0;
-}
-
 __device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
   uint64_t d;
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
@@ -241,25 +201,7 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
         st_async4(peer_addr(dst0, peer) + 16u * ch, x, peer_addr(bar0, peer));
       }
     }
-    bool ok = true;
-    const long long t0 = clock64();
-    unsigned spins = 0u;
-    // try_wait may suspend the thread for the hardware's own interval before it returns; a
-    // bound shorter than that (set by coded_qr_set_wait_limit) polls with test_wait instead
-    const bool short_bound = wait_limit < kPollAfterCycles;
-    while (!(short_bound ? mbar_test_wait(mbar + par, (phases >> par) & 1u)
-                         : mbar_try_wait(mbar + par, (phases >> par) & 1u))) {
-      const long long el = clock64() - t0;
-      if (el > wait_limit) {
-        set_status(status, CQR_ETIMEOUT, 40);
-        ok = false;
-        break;
-      }
-      if (el > kPollAfterCycles && (++spins & 63u) == 0u && ld_relaxed_i32(status + ST_CODE) != 0) {
-        ok = false;
-        break;
-      }
-    }
+    const bool ok = mbar_wait_bounded(mbar + par, (phases >> par) & 1u, wait_limit, status, 40);
     phases ^= 1u << par;
     return __syncthreads_and(ok) != 0;
   };

@@ -26,9 +26,11 @@ from paper_2311_11943_gb300 import binding as B  # noqa: E402
 
 
 # (m, n, p_r, p_c, f, b, dtype, mma): the register-resident cluster panel (FP32, its exchange
-# of partial vectors by st.async into every CTA, bounded mbarrier waits) and the cooperative
-# grid-barrier panel (FP64, 10240 rows: too tall for one cluster's shared memory)
-CASES = [(1024, 1024, 8, 8, 2, 64, "f32", "3xtf32"), (8192, 256, 8, 4, 2, 64, "f64", "simt")]
+# of partial vectors by st.async into every CTA, bounded mbarrier waits), the cooperative
+# grid-barrier panel (FP64, 10240 rows: too tall for one cluster's shared memory) and the
+# two-level exchange (FP32, 20480 x 256: clusters of 8 whose leaders meet at a grid barrier)
+CASES = [(1024, 1024, 8, 8, 2, 64, "f32", "3xtf32"), (8192, 256, 8, 4, 2, 64, "f64", "simt"),
+         (16384, 1024, 16, 8, 4, 256, "f32", "3xtf32")]
 
 
 @pytest.mark.parametrize("case", CASES)
