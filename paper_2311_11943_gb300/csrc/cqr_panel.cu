@@ -390,6 +390,14 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
     }
   };
   if (HIER) {
+    // the exchange addresses rank 0 of a cluster of kHierCS CTAs: a launch of any other shape
+    // (the same for every CTA) records an error and leaves before touching another CTA
+    unsigned ncta;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
+    if (ncta != (unsigned)kHierCS || gridDim.x % kHierCS != 0) {
+      if (g == 0 && tid == 0) set_status(status, CQR_ECUDA, 50);
+      return;
+    }
     if (tid == 0) {
       mbar_init(c.mbar, 1);
       mbar_init(c.mbar + 1, 1);
@@ -840,12 +848,11 @@ PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_clu
 
 // Launch configuration of the two-level variant: clusters of kHierCS CTAs over the whole
 // grid.  Its leaders wait for one another, so every cluster must be resident at once: the
-// plan is taken only when the occupancy query says they fit (panel_hier_fits), and the
-// launch asks for the cooperative guarantee as well where the runtime accepts it together
-// with clusters (remembered after the first attempt).
-template <typename T>
-void hier_config(const PanelPlan& pp, const void* fn, cudaStream_t st, cudaLaunchConfig_t* cfg,
-                 cudaLaunchAttribute* attr, bool coop) {
+// plan is taken only when the occupancy query says they all fit (panel_hier_fits), and the
+// variant is used only on the sequential schedule, where the panel is the only work on the
+// GPU when it runs.
+void hier_config(const PanelPlan& pp, cudaStream_t st, cudaLaunchConfig_t* cfg,
+                 cudaLaunchAttribute* attr) {
   *cfg = cudaLaunchConfig_t{};
   cfg->gridDim = dim3(pp.G);
   cfg->blockDim = dim3(kNT);
@@ -855,14 +862,9 @@ void hier_config(const PanelPlan& pp, const void* fn, cudaStream_t st, cudaLaunc
   attr[0].val.clusterDim.x = kHierCS;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  attr[1].id = cudaLaunchAttributeCooperative;
-  attr[1].val.cooperative = 1;
   cfg->attrs = attr;
-  cfg->numAttrs = coop ? 2 : 1;
-  (void)fn;
+  cfg->numAttrs = 1;
 }
-
-int g_hier_coop = -1;  // -1 not tried, 1 cooperative cluster launches accepted, 0 refused
 
 template <typename T>
 cudaError_t launch_hier(const PanelPlan& pp, int rpl, void** args, cudaStream_t st) {
@@ -872,20 +874,8 @@ cudaError_t launch_hier(const PanelPlan& pp, int rpl, void** args, cudaStream_t 
                                        (int)pp.smem_bytes);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
-  cudaLaunchAttribute attr[2];
-  const int coop = __atomic_load_n(&g_hier_coop, __ATOMIC_RELAXED);
-  if (coop != 0) {
-    hier_config<T>(pp, fn, st, &cfg, attr, true);
-    e = cudaLaunchKernelExC(&cfg, fn, args);
-    if (e == cudaSuccess) {
-      __atomic_store_n(&g_hier_coop, 1, __ATOMIC_RELAXED);
-      return e;
-    }
-    if (coop == 1) return e;
-    cudaGetLastError();
-    __atomic_store_n(&g_hier_coop, 0, __ATOMIC_RELAXED);
-  }
-  hier_config<T>(pp, fn, st, &cfg, attr, false);
+  cudaLaunchAttribute attr[1];
+  hier_config(pp, st, &cfg, attr);
   return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
@@ -970,8 +960,8 @@ bool panel_hier_fits(const PanelPlan& pp) {
     return false;
   }
   cudaLaunchConfig_t cfg;
-  cudaLaunchAttribute attr[2];
-  hier_config<T>(pp, fn, nullptr, &cfg, attr, false);
+  cudaLaunchAttribute attr[1];
+  hier_config(pp, nullptr, &cfg, attr);
   int n = 0;
   if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
     cudaGetLastError();
