@@ -154,36 +154,83 @@ struct NoHook {
   __device__ void operator()() const {}
 };
 
-// Wait (thread 0, bounded) until the global counter has received `count` more arrivals,
-// without arriving: the two-level exchange, where only cluster leaders arrive.
-__device__ __forceinline__ bool wait_count(unsigned* bar, unsigned count, unsigned& target,
-                                           int* status, int site, long long limit) {
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    target += count;
-    int ok = 1;
-    const long long t0 = clock64();
-    while (ld_acquire_u32(bar) < target) {
-      if (ld_relaxed_i32(status + ST_CODE) == CQR_ETIMEOUT) { ok = 0; break; }
-      if (clock64() - t0 > limit) {
-        set_status(status, CQR_ETIMEOUT, site);
-        status[ST_SITE] = site;
-        ok = 0;
-        break;
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// out[a] = sum over r < rows of the FP32 values of tagged words P[r * stride + a] (value in the
+// low half, `tag` in the high half) for lo <= a < hi, each word polled (bounded) until it
+// carries the tag: a word is written whole by one aligned 64-bit store, so a matching tag
+// certifies its value, and no separate flag or barrier is needed.  Summation as in
+// reduce_rows (gr adjacent lanes, rows gr apart, then a butterfly): a fixed order.  Every
+// thread of the CTA must call it; returns false (the same in every thread) when a wait ran
+// out or another CTA recorded an error.
+__device__ __forceinline__ bool reduce_tagged(const unsigned long long* P, int rows, size_t stride,
+                                              int lo, int hi, unsigned tag, float* out, int* status,
+                                              int site, long long limit) {
+  const int n = hi - lo, tid = threadIdx.x;
+  bool ok = true;
+  if (n > 0) {
+    int gr = 1;
+    while (gr < 8 && gr * 2 * n <= kNT && gr * 2 <= rows) gr *= 2;
+    const int total = n * gr;
+    for (int base = 0; base < total; base += kNT) {
+      const int idx = base + tid;
+      const int e = idx / gr, m = idx - e * gr;
+      float acc = 0.f;
+      if (idx < total && ok) {
+        const int a = lo + e;
+        for (int r0 = m; r0 < rows && ok; r0 += 4 * gr) {
+          unsigned long long x[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = r0 + u * gr;
+            x[u] = r < rows ? ld_relaxed_u64(P + (size_t)r * stride + a) : 0ull;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = r0 + u * gr;
+            if (r >= rows || !ok) continue;
+            if ((unsigned)(x[u] >> 32) != tag) {
+              const long long t0 = clock64();
+              unsigned spins = 0u;
+              do {
+                x[u] = ld_relaxed_u64(P + (size_t)r * stride + a);
+                const long long el = clock64() - t0;
+                if (el > limit) {
+                  set_status(status, CQR_ETIMEOUT, site);
+                  ok = false;
+                  break;
+                }
+                if (el > kPollAfterCycles && (++spins & 63u) == 0u &&
+                    ld_relaxed_i32(status + ST_CODE) != 0) {
+                  ok = false;
+                  break;
+                }
+              } while ((unsigned)(x[u] >> 32) != tag);
+            }
+            if (ok) acc += __uint_as_float((unsigned)x[u]);
+          }
+        }
       }
+      for (int o = 1; o < gr; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (idx < total && m == 0) out[lo + e] = acc;
     }
-    s_ok = ok;
   }
-  __syncthreads();
-  return s_ok != 0;
+  return __syncthreads_and(ok) != 0;
 }
 
 // Synchronise and reduce entries [lo, hi) of the partial vectors into out[].  `hook` runs
 // right after the barrier, when every thread of this CTA has finished the step's reads.
 // HIER (two-level, FP32): the CTAs of each cluster push their partials (16-byte st.async) into
-// the leader's receive buffer; the leader sums them in rank order, writes the cluster sum to
-// global memory and arrives on the counter; every CTA waits for all leaders and sums the
-// cluster sums in cluster order.  The first reduction (v and eta, wider than one buffer row)
+// the leader's receive buffer; the leader sums them in rank order and writes the cluster sum
+// to global memory as tagged words; every CTA polls the words of all clusters and sums them
+// in cluster order.  The first reduction (v and eta, wider than one buffer row)
 // goes through global memory from every CTA, as in the grid variant.
 template <typename T, bool CL, bool HIER = false, typename Hook = NoHook>
 __device__ __forceinline__ bool sync_reduce(Ctx<T>& c, int lo, int hi, T* out, int step, int site,
@@ -207,24 +254,25 @@ __device__ __forceinline__ bool sync_reduce(Ctx<T>& c, int lo, int hi, T* out, i
                                           c.status, site);
         c.phases ^= 1u << par;
         if (!__syncthreads_and(ok)) return false;
-        // cluster sums: rows G + par ncl + cl of the partial buffer (rows below G hold the
-        // first reduction's per-CTA partials, which slower CTAs may still be reading)
-        T* dst = c.gpart + ((size_t)G + par * c.ncl + c.cl) * 2 * c.pld;
+        // cluster sums as tagged words (value, step + 1): rows G + par ncl + cl of the partial
+        // buffer, each row 2 pld floats = pld words (rows below G hold the first reduction's
+        // per-CTA partials, which slower CTAs may still be reading); cleared before the launch
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(
+            c.gpart + ((size_t)G + par * c.ncl + c.cl) * 2 * c.pld);
+        const unsigned long long tag = (unsigned long long)(step + 1) << 32;
         for (int a = lo + tid; a < hi; a += kNT) {
-          T sum = T(0);
+          float sum = 0.f;
 #pragma unroll
-          for (int k = 0; k < kHierCS; ++k) sum += c.rbuf[((size_t)par * kHierCS + k) * c.pld + a];
-          dst[a] = sum;
+          for (int k = 0; k < kHierCS; ++k)
+            sum += (float)c.rbuf[((size_t)par * kHierCS + k) * c.pld + a];
+          st_relaxed_u64(dst + a, tag | __float_as_uint(sum));
         }
-        __syncthreads();
-        if (tid == 0)
-          asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(c.bar), "r"(1u) : "memory");
       }
-      if (!wait_count(c.bar, (unsigned)c.ncl, c.target, c.status, site, c.wait_limit)) return false;
-      reduce_rows(c.gpart + ((size_t)G + par * c.ncl) * 2 * c.pld, c.ncl, (size_t)2 * c.pld, lo,
-                  hi, out);
-      __syncthreads();
-      return true;
+      const bool ok = reduce_tagged(
+          reinterpret_cast<const unsigned long long*>(c.gpart + ((size_t)G + par * c.ncl) * 2 * c.pld),
+          c.ncl, (size_t)c.pld, lo, hi, (unsigned)(step + 1), reinterpret_cast<float*>(out),
+          c.status, site, c.wait_limit);
+      return ok;
     }
     __syncthreads();
     T* dst = c.gpart + ((size_t)par * G + blockIdx.x) * 2 * c.pld;
@@ -893,7 +941,16 @@ cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t l
   long long wl = wait_limit > 0 ? wait_limit : kWaitLimitCycles;
   void* args[] = {&Q, &ldq, &R, &ldr, &M, &bk, &rpc, &rpc_pad, &tau2, &part, &bar, &status, &col0,
                   &wl};
-  if (pp.hier && variant == 0) return launch_hier<T>(pp, rpl, args, st);
+  if (pp.hier && variant == 0) {
+    // the tagged cluster-sum rows (G .. G + 2 clusters) start cleared: no tag of an earlier
+    // launch can match
+    const int pld = (bk + 3) / 4 * 4;
+    const size_t row = (size_t)2 * pld * sizeof(T);
+    cudaError_t e = cudaMemsetAsync(reinterpret_cast<char*>(part) + (size_t)pp.G * row, 0,
+                                    (size_t)2 * (pp.G / kHierCS) * row, st);
+    if (e != cudaSuccess) return e;
+    return launch_hier<T>(pp, rpl, args, st);
+  }
   const void* fn = pick_kernel<T>(rpl, pp.cluster != 0, pp.smem != 0, variant);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)pp.smem_bytes);
