@@ -281,7 +281,7 @@ cqr_status coded_qr_set_wait_limit(cqr_handle h, int64_t cycles);
  * synchronises the stream and fills (host) ms[k] (device milliseconds) and launches[k]
  * for the first cap classes (CQR_PROF_CLASSES in total) since the last reset; reset != 0
  * clears the accumulators.  coded_qr_profile_name gives the class name (NULL past the end). */
-#define CQR_PROF_CLASSES 16
+#define CQR_PROF_CLASSES 17
 cqr_status coded_qr_profile(cqr_handle h, int32_t enable);
 cqr_status coded_qr_profile_read(cqr_handle h, double* ms, int64_t* launches, int32_t cap,
                                  int32_t reset);

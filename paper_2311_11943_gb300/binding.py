@@ -44,7 +44,7 @@ EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "
            "coded_qr_adjoint_qr", "coded_qr_adjoint_lstsq", "coded_qr_mds_stats",
            "coded_qr_inject_node_failure", "coded_qr_set_wait_limit"]
 CQR_BATCH_GRAPH, CQR_BATCH_POST_ORTH = 1, 2
-PROF_CLASSES = 16
+PROF_CLASSES = 17
 
 
 class Config(C.Structure):

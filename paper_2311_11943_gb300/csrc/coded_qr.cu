@@ -54,6 +54,10 @@ struct Buffers {
 // Checksum blocks per code.  Out-of-node storage: f (one per tolerated failure, on f extra
 // nodes).  In-node storage (Section 5): K = f + f ceil(f / (P - f)) with P = p_r nodes per code
 // and L = P data blocks, the equality case of Theorem in_node_opt.
+// Sub-panel width of panels too tall for one thread-block cluster (FP32): a 20480-row panel
+// of 32 columns takes 1280-row slices on 16 CTAs.
+constexpr int kSubPanel = 32;
+
 int code_blocks(const cqr_config* c) {
   if (!c->in_node || c->f == 0) return c->f;
   return c->f + c->f * ((c->f + (c->p_r - c->f) - 1) / (c->p_r - c->f));
@@ -146,12 +150,12 @@ Layout make_layout(const cqr_config* c, const Geo& g, int num_sms) {
 enum KClass {
   K_GENERATOR = 0, K_ENCODE, K_PANEL, K_GEMM_RBAR, K_SPLITK_REDUCE, K_GEMM_UPDATE, K_POISON,
   K_DECODE, K_POST_ORTH, K_SOLVE_GEMV, K_TRSV, K_TC_RBAR, K_TC_UPDATE, K_TC_SPLIT,
-  K_BLOCK_REORTH, K_TC_NARROW, K_COUNT
+  K_BLOCK_REORTH, K_TC_NARROW, K_PANEL_SUB_UPDATE, K_COUNT
 };
 static const char* kClassNames[K_COUNT] = {
     "generator", "encode", "panel_icgs", "gemm_rbar_simt", "splitk_reduce", "gemm_update_simt",
     "erasure_poison", "decode", "post_orth", "solve_gemv", "trsv", "tc_rbar", "tc_update",
-    "tc_split_panel", "block_reorth", "tc_narrow_update"};
+    "tc_split_panel", "block_reorth", "tc_narrow_update", "panel_sub_update"};
 
 struct ProfRec {
   int cls;
@@ -184,6 +188,9 @@ struct cqr_handle_s {
   PanelPlan plan{};
   int plan_bk = -1;
   bool reg_ok = false;
+  // sub-panel schedule of panels too tall for one cluster (FP32): width and cluster plan
+  int sub_bs = 0;
+  PanelPlan sub_plan{};
   int reg_rpl = 0, reg_cpw = 0, reg_G = 0;
   // profile: launch counts always, event-pair device times when enabled
   bool prof_on = false;
@@ -379,7 +386,54 @@ void ensure_panel_plan(cqr_handle h, int bk) {
   if (sizeof(T) == 4 && !(env && env[0] == '0') && !left_looking &&
       plan_panel_reg(g.M, bk, &h->reg_rpl, &h->reg_cpw, &h->reg_G))
     h->reg_ok = panel_reg_cluster_fits(h->reg_rpl, h->reg_cpw, h->reg_G);
+  // an FP32 panel too tall for one cluster is factored as sub-panels of kSubPanel columns that
+  // each fit one cluster, when they do (CQR_PANEL_SUB=0 keeps the grid exchange)
+  h->sub_bs = 0;
+  const char* se = getenv("CQR_PANEL_SUB");
+  if (sizeof(T) == 4 && !h->reg_ok && !h->plan.cluster && !left_looking && bk > kSubPanel &&
+      !(se && se[0] == '0')) {
+    const PanelPlan sp = plan_panel(g.M, kSubPanel, sizeof(T), h->num_sms, true, false);
+    if (sp.cluster && panel_cluster_fits<T>(sp)) {
+      h->sub_bs = kSubPanel;
+      h->sub_plan = sp;
+    }
+  }
   h->plan_bk = bk;
+}
+
+// The panel of columns kb .. kb+bk-1 as sub-panels of sub_bs columns (the blocked schedule of
+// the same Gram-Schmidt: reading "sub-panels" of the design notes).  Each sub-panel runs the
+// panel kernel (ICGS, the criterion within the sub-panel) on one thread-block cluster; the
+// panel's columns to its right are then projected once on it, R[sub rows, right] = Qs^T P and
+// P -= Qs R, by the split-K CUDA-core kernels in the storage precision.
+template <typename T>
+cqr_status sub_panel_step(cqr_handle h, int64_t kb, int bk, cudaStream_t st) {
+  const Geo& g = h->g;
+  T* Q = ptr<T>(h->B.Q);
+  T* R = ptr<T>(h->B.R);
+  const int bs = h->sub_bs;
+  for (int s0 = 0; s0 < bk; s0 += bs) {
+    const int w0 = std::min(bs, bk - s0);
+    const int64_t ks = kb + s0;
+    {
+      ProfScope ps(h, K_PANEL, 1, st);
+      CK(launch_panel<T>(h->sub_plan, Q + ks * g.ldq, g.ldq, R + ks + ks * g.ldr, g.ldr, g.M, w0,
+                         h->tau, ptr<T>(h->B.part), h->B.bar, h->B.status, (int)ks, st, 0,
+                         h->wait_limit));
+    }
+    const int64_t j0 = ks + w0;
+    const int64_t w = kb + bk - j0;
+    if (w <= 0) break;
+    ProfScope ps(h, K_PANEL_SUB_UPDATE, 3, st);
+    const int splits = choose_splits(w0, w, g.M, h->num_sms);
+    CK(launch_gemm_tn_splitk<T>(Q + ks * g.ldq, g.ldq, Q + j0 * g.ldq, g.ldq, g.M, w0, w, splits,
+                                ptr<T>(h->B.P), st));
+    CK(launch_splitk_reduce<T>(ptr<T>(h->B.P), splits, w0, w, R + ks + j0 * g.ldr, g.ldr,
+                               ptr<T>(h->B.Rb), st));
+    CK(launch_gemm_nn_sub<T>(Q + ks * g.ldq, g.ldq, ptr<T>(h->B.Rb), w0, Q + j0 * g.ldq, g.ldq,
+                             g.M, w0, w, st));
+  }
+  return CQR_OK;
 }
 
 // Block reorthogonalisation of panel columns kb .. kb+bk-1 against columns 0 .. kb-1:
@@ -416,6 +470,7 @@ cqr_status panel_kernel_step(cqr_handle h, int64_t kb, int bk, cudaStream_t st) 
   T* Q = ptr<T>(h->B.Q);
   T* R = ptr<T>(h->B.R);
   ensure_panel_plan<T>(h, bk);
+  if (h->sub_bs > 0) return sub_panel_step<T>(h, kb, bk, st);
   ProfScope ps(h, K_PANEL, 1, st);
   if (sizeof(T) == 4 && h->reg_ok) {
     CK(launch_panel_reg(h->reg_rpl, h->reg_cpw, h->reg_G, reinterpret_cast<float*>(Q + kb * g.ldq),

@@ -813,11 +813,14 @@ const void* pick_kernel(int rpl, bool cl, bool smem, int variant = 0) {
     case 12: return kernel_of<T, 12>(cl, smem, variant);
     case 16: return kernel_of<T, 16>(cl, smem, variant);
     case 24: return kernel_of<T, 24>(cl, smem, variant);
+    case 40: return kernel_of<T, 40>(cl, smem, variant);
     default: return kernel_of<T, 32>(cl, smem, variant);
   }
 }
 
 constexpr int kRpl[] = {4, 6, 8, 12, 16, 24, 32};
+// one cluster of 16 CTAs may also take 1280-row slices (a 20480-row panel of 32 FP32 columns)
+constexpr int kRplCluster[] = {4, 6, 8, 12, 16, 24, 32, 40};
 
 int rpl_for_rows(int rpc) {
   for (int r : kRpl)
@@ -843,7 +846,7 @@ PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_clu
   int best = -1;
   bool best_cl = false;
   if (allow_cluster && cl_env != 0)
-    for (int r : kRpl)
+    for (int r : kRplCluster)
       if ((rpl_env == 0 || r == rpl_env) && fits(r, true) && (M + 32 * r - 1) / (32 * r) <= kMaxCluster) {
         best = r;
         best_cl = true;
@@ -935,7 +938,7 @@ cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t l
     cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
   }
-  const int rpl = rpl_for_rows(pp.rpc);
+  const int rpl = (pp.rpc / 32);
   double tau2 = tau > 0.0 ? tau * tau : -1.0;
   int rpc = pp.rpc, rpc_pad = pp.rpc_pad;
   long long wl = wait_limit > 0 ? wait_limit : kWaitLimitCycles;
@@ -980,7 +983,7 @@ cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t l
 // Whether a cluster of pp.G CTAs with this shared-memory footprint can be scheduled.
 template <typename T>
 bool panel_cluster_fits(const PanelPlan& pp) {
-  const void* fn = pick_kernel<T>(rpl_for_rows(pp.rpc), true, true);
+  const void* fn = pick_kernel<T>((pp.rpc / 32), true, true);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp.smem_bytes) !=
       cudaSuccess)
     return false;
@@ -1009,7 +1012,7 @@ bool panel_cluster_fits(const PanelPlan& pp) {
 template <typename T>
 bool panel_hier_fits(const PanelPlan& pp) {
   if (!pp.hier) return false;
-  const void* fn = pick_hier<T>(rpl_for_rows(pp.rpc));
+  const void* fn = pick_hier<T>((pp.rpc / 32));
   if (!fn) return false;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp.smem_bytes) !=
       cudaSuccess) {

@@ -56,21 +56,29 @@ def test_panel_variant_matches_oracle(panel, dtype):
     assert rel(R, ref["R"]) < tol
 
 
+SCHEDULES = {"sub-panels": {}, "two-level": {"CQR_PANEL_SUB": "0"},
+             "flat grid": {"CQR_PANEL_SUB": "0", "CQR_PANEL_HIER": "0"}}
+
+
 @pytest.mark.parametrize("mma", ["3xtf32", "simt"])
-def test_two_level_exchange_matches_oracle_and_flat_grid(mma, monkeypatch):
+def test_tall_panel_schedules_match_oracle_and_each_other(mma, monkeypatch):
     # The panel of the 16384^2 workload's shape (20480 x 256, FP32) needs more CTAs than one
-    # cluster holds: it runs on clusters of 8 whose leaders meet at a grid barrier (the
-    # two-level exchange).  A 16384 x 1024 problem on that grid (16 x 8, f = 4, b = 256) has
-    # the same panel; its factors are compared with the oracle (n u kappa, with u = 8 u32 for
-    # 3xTF32 products) and with the flat grid exchange (CQR_PANEL_HIER=0), which sums the
-    # same partial products in another fixed order (agreement to n u kappa as well).
+    # cluster holds.  Three schedules factor it: 32-column sub-panels that each fit one
+    # cluster, with the panel's remaining columns projected on each (the default); the
+    # two-level exchange (clusters of 8 whose leaders publish tagged sums); the flat grid
+    # barrier.  A 16384 x 1024 problem on that grid (16 x 8, f = 4, b = 256) has the same
+    # panel; each schedule is compared with the oracle (n u kappa, with u = 8 u32 for 3xTF32
+    # products) and with the others (the same arithmetic in another order, n u kappa).
     m, n, p_r, p_c, f, b, kappa = 16384, 1024, 16, 8, 4, 256, 10.0
     A = synth.kappa_matrix(m, n, kappa, seed=61)
     er = {2: [(3, 5), (17, 2)]}
     ref = O.run(A, p_r, p_c, f, b, seed=4, erasures=er)
     out = {}
-    for hier in ("1", "0"):
-        monkeypatch.setenv("CQR_PANEL_HIER", hier)
+    for name, env in SCHEDULES.items():
+        for k in ("CQR_PANEL_SUB", "CQR_PANEL_HIER"):
+            monkeypatch.delenv(k, raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
         q = B.CodedQR(m, n, p_r, p_c, f, b, dtype="f32", mma=mma, seed=4)
         q.encode(_dev(A, torch.float32))
         for t in range(q.geo["panels"]):
@@ -82,11 +90,12 @@ def test_two_level_exchange_matches_oracle_and_flat_grid(mma, monkeypatch):
         torch.cuda.synchronize()
         assert q.sync_status() == 0
         assert q.decode_sets() == ref["sets"]
-        out[hier] = (Qc.double().cpu().numpy(), Rc.double().cpu().numpy())
+        out[name] = (Qc.double().cpu().numpy(), Rc.double().cpu().numpy())
         q.close()
     u = np.finfo(np.float32).eps / 2 * (8 if mma == "3xtf32" else 1)
     tol = n * u * kappa
-    for hier in ("1", "0"):
-        Q, R = out[hier]
-        assert rel(Q, ref["Q"]) < tol and rel(R, ref["R"]) < tol
-    assert rel(out["1"][0], out["0"][0]) < tol and rel(out["1"][1], out["0"][1]) < tol
+    for name in SCHEDULES:
+        Q, R = out[name]
+        assert rel(Q, ref["Q"]) < tol and rel(R, ref["R"]) < tol, name
+    for x, y in (("sub-panels", "two-level"), ("two-level", "flat grid")):
+        assert rel(out[x][0], out[y][0]) < tol and rel(out[x][1], out[y][1]) < tol, (x, y)

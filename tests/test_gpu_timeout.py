@@ -28,14 +28,16 @@ from paper_2311_11943_gb300 import binding as B  # noqa: E402
 # (m, n, p_r, p_c, f, b, dtype, mma): the register-resident cluster panel (FP32, its exchange
 # of partial vectors by st.async into every CTA, bounded mbarrier waits), the cooperative
 # grid-barrier panel (FP64, 10240 rows: too tall for one cluster's shared memory) and the
-# two-level exchange (FP32, 20480 x 256: clusters of 8 whose leaders meet at a grid barrier)
+# two-level exchange (FP32, 20480 x 256 with the sub-panel schedule off: clusters of 8 whose
+# leaders publish tagged sums that every CTA polls)
 CASES = [(1024, 1024, 8, 8, 2, 64, "f32", "3xtf32"), (8192, 256, 8, 4, 2, 64, "f64", "simt"),
          (16384, 1024, 16, 8, 4, 256, "f32", "3xtf32")]
 
 
 @pytest.mark.parametrize("case", CASES)
-def test_expired_waits_leave_and_report_timeout(case):
+def test_expired_waits_leave_and_report_timeout(case, monkeypatch):
     m, n, p_r, p_c, f, b, dtype, mma = case
+    monkeypatch.setenv("CQR_PANEL_SUB", "0")
     td = torch.float64 if dtype == "f64" else torch.float32
     A = synth.kappa_matrix(m, n, 1e2, seed=41)
     Ad = B.colmajor_empty(m, n, td)
