@@ -57,7 +57,9 @@ typedef enum {
   CQR_EUNRECOVERABLE = 5,  /* more than f erasures in a grid row/column, or singular G^ */
   CQR_EBREAKDOWN = 6,      /* zero or non-finite pivot r_jj in the panel factorisation */
   CQR_ETIMEOUT = 7,        /* a device-side wait exceeded its limit; the kernel gave up */
-  CQR_ENOTSUP = 8          /* configuration not supported by this build */
+  CQR_ENOTSUP = 8,         /* configuration not supported by this build */
+  CQR_EBOUNDS = 9          /* bounds-checked build only: a kernel found an index outside the
+                              extent it was given, recorded it and returned without the access */
 } cqr_status;
 
 enum { CQR_F64 = 0, CQR_F32 = 1 };

@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libcoded_qr.so")
 
 CQR_OK, CQR_EINVAL, CQR_ENOMEM, CQR_ECUDA, CQR_ESTATE = 0, 1, 2, 3, 4
-CQR_EUNRECOVERABLE, CQR_EBREAKDOWN, CQR_ETIMEOUT, CQR_ENOTSUP = 5, 6, 7, 8
+CQR_EUNRECOVERABLE, CQR_EBREAKDOWN, CQR_ETIMEOUT, CQR_ENOTSUP, CQR_EBOUNDS = 5, 6, 7, 8, 9
 CQR_F64, CQR_F32 = 0, 1
 CQR_MMA_SIMT, CQR_MMA_TF32, CQR_MMA_3XTF32, CQR_MMA_BF16, CQR_MMA_BF16X3 = 0, 1, 2, 3, 4
 MMA_NAMES = {"simt": CQR_MMA_SIMT, "tf32": CQR_MMA_TF32, "3xtf32": CQR_MMA_3XTF32,

@@ -386,12 +386,13 @@ void ensure_panel_plan(cqr_handle h, int bk) {
   if (sizeof(T) == 4 && !(env && env[0] == '0') && !left_looking &&
       plan_panel_reg(g.M, bk, &h->reg_rpl, &h->reg_cpw, &h->reg_G))
     h->reg_ok = panel_reg_cluster_fits(h->reg_rpl, h->reg_cpw, h->reg_G);
-  // an FP32 panel too tall for one cluster is factored as sub-panels of kSubPanel columns that
-  // each fit one cluster, when they do (CQR_PANEL_SUB=0 keeps the grid exchange)
+  // on request (CQR_PANEL_SUB=1), an FP32 panel too tall for one cluster is factored as
+  // sub-panels of kSubPanel columns that each fit one cluster (measured slower than the
+  // two-level exchange at 20480 x 256: its in-panel updates are skinny CUDA-core products)
   h->sub_bs = 0;
   const char* se = getenv("CQR_PANEL_SUB");
   if (sizeof(T) == 4 && !h->reg_ok && !h->plan.cluster && !left_looking && bk > kSubPanel &&
-      !(se && se[0] == '0')) {
+      se && se[0] == '1') {
     const PanelPlan sp = plan_panel(g.M, kSubPanel, sizeof(T), h->num_sms, true, false);
     if (sp.cluster && panel_cluster_fits<T>(sp)) {
       h->sub_bs = kSubPanel;
@@ -1207,6 +1208,7 @@ const char* coded_qr_errstr(cqr_status s) {
     case CQR_EBREAKDOWN: return "Gram-Schmidt breakdown (zero or non-finite pivot)";
     case CQR_ETIMEOUT: return "device wait timed out";
     case CQR_ENOTSUP: return "not supported";
+    case CQR_EBOUNDS: return "index check failed on the device (bounds-checked build)";
   }
   return "unknown status";
 }

@@ -17,6 +17,29 @@ __device__ __forceinline__ void set_status(int* st, int code, int detail) {
   if (atomicCAS(st + ST_CODE, 0, code) == 0) st[ST_DETAIL] = detail;
 }
 
+// Index checks of the bounds-checked build (compiled with -DCQR_DEBUG_BOUNDS; nothing in the
+// normal build).  CQR_CHECK(cond, status, site): when cond is false the thread records
+// CQR_EBOUNDS with the site number (when a status word is at hand) and returns from the
+// kernel before the access the condition guards; it never traps.  Used only where a return
+// cannot strand other threads at a barrier (element-wise kernels, after a kernel's last
+// barrier), or with CQR_CHECK_SKIP, which skips the guarded access instead of returning.
+#ifdef CQR_DEBUG_BOUNDS
+#define CQR_CHECK(cond, status, site)                                \
+  do {                                                               \
+    if (!(cond)) {                                                   \
+      if (status) ::cqr::set_status((status), CQR_EBOUNDS, (site));  \
+      return;                                                        \
+    }                                                                \
+  } while (0)
+#define CQR_CHECK_OK(cond, status, site) \
+  ((cond) ? true : ((status) ? (::cqr::set_status((status), CQR_EBOUNDS, (site)), false) : false))
+#else
+#define CQR_CHECK(cond, status, site) \
+  do {                                \
+  } while (0)
+#define CQR_CHECK_OK(cond, status, site) true
+#endif
+
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

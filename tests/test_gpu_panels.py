@@ -56,17 +56,17 @@ def test_panel_variant_matches_oracle(panel, dtype):
     assert rel(R, ref["R"]) < tol
 
 
-SCHEDULES = {"sub-panels": {}, "two-level": {"CQR_PANEL_SUB": "0"},
-             "flat grid": {"CQR_PANEL_SUB": "0", "CQR_PANEL_HIER": "0"}}
+SCHEDULES = {"sub-panels": {"CQR_PANEL_SUB": "1"}, "two-level": {},
+             "flat grid": {"CQR_PANEL_HIER": "0"}}
 
 
 @pytest.mark.parametrize("mma", ["3xtf32", "simt"])
 def test_tall_panel_schedules_match_oracle_and_each_other(mma, monkeypatch):
     # The panel of the 16384^2 workload's shape (20480 x 256, FP32) needs more CTAs than one
-    # cluster holds.  Three schedules factor it: 32-column sub-panels that each fit one
-    # cluster, with the panel's remaining columns projected on each (the default); the
-    # two-level exchange (clusters of 8 whose leaders publish tagged sums); the flat grid
-    # barrier.  A 16384 x 1024 problem on that grid (16 x 8, f = 4, b = 256) has the same
+    # cluster holds.  Three schedules factor it: the two-level exchange (clusters of 8 whose
+    # leaders publish tagged sums; the default); 32-column sub-panels that each fit one
+    # cluster, with the panel's remaining columns projected on each (on request); the flat
+    # grid barrier.  A 16384 x 1024 problem on that grid (16 x 8, f = 4, b = 256) has the same
     # panel; each schedule is compared with the oracle (n u kappa, with u = 8 u32 for 3xTF32
     # products) and with the others (the same arithmetic in another order, n u kappa).
     m, n, p_r, p_c, f, b, kappa = 16384, 1024, 16, 8, 4, 256, 10.0
