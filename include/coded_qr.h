@@ -276,6 +276,20 @@ cqr_status coded_qr_sync_status(cqr_handle h);
  * that every exchange of a correct launch runs out.  Takes effect for the next launches. */
 cqr_status coded_qr_set_wait_limit(cqr_handle h, int64_t cycles);
 
+/* Bounds-checked build (instrumentation, no counterpart in the paper; the stand-in for a
+ * memory checker on GPUs where none can run).  The library built with -DCQR_DEBUG_BOUNDS
+ * (libcoded_qr_debug.so) checks, in each kernel of the hot path, that the indices it is about to
+ * use stay inside the extents it was given (leading dimensions against row counts, tile and
+ * plan indices against the grid, slices against the panel).  A failed check records
+ * CQR_EBOUNDS and the check's site number in a device word of its source file and returns
+ * without the access: it never traps.  coded_qr_debug_bounds synchronises the device, collects
+ * and clears those words and returns CQR_EBOUNDS with *site (host, may be NULL) set to the
+ * first failed site, else CQR_OK; coded_qr_debug_bounds_selftest enqueues on `stream` one
+ * guarded write past a four-element array (site 199), which the check must catch.  In the
+ * normal build both return CQR_ENOTSUP and launch nothing. */
+cqr_status coded_qr_debug_bounds(int32_t* site);
+cqr_status coded_qr_debug_bounds_selftest(void* stream);
+
 /* Profile of the library's own kernels (instrumentation, no counterpart in the paper).
  * Launch counts per kernel class are always kept; with enable != 0 every launch site is
  * also bracketed by a pair of CUDA events on the stream its launches go to (cfg.stream, or

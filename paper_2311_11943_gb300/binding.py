@@ -12,7 +12,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libcoded_qr.so")
+# CQR_LIBRARY=debug loads the bounds-checked build (build.build(debug_bounds=True)) instead
+LIB_PATH = (os.path.join(_HERE, "_build_debug", "libcoded_qr_debug.so")
+            if os.environ.get("CQR_LIBRARY") == "debug"
+            else os.path.join(_HERE, "_build", "libcoded_qr.so"))
 
 CQR_OK, CQR_EINVAL, CQR_ENOMEM, CQR_ECUDA, CQR_ESTATE = 0, 1, 2, 3, 4
 CQR_EUNRECOVERABLE, CQR_EBREAKDOWN, CQR_ETIMEOUT, CQR_ENOTSUP, CQR_EBOUNDS = 5, 6, 7, 8, 9
@@ -42,7 +45,8 @@ EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "
            "coded_qr_batched_get_factors", "coded_qr_batched_get_decode_sets",
            "coded_qr_batched_sync_status", "coded_qr_batched_last_error",
            "coded_qr_adjoint_qr", "coded_qr_adjoint_lstsq", "coded_qr_mds_stats",
-           "coded_qr_inject_node_failure", "coded_qr_set_wait_limit"]
+           "coded_qr_inject_node_failure", "coded_qr_set_wait_limit", "coded_qr_debug_bounds",
+           "coded_qr_debug_bounds_selftest"]
 CQR_BATCH_GRAPH, CQR_BATCH_POST_ORTH = 1, 2
 PROF_CLASSES = 17
 
@@ -99,6 +103,8 @@ def lib():
             "coded_qr_stats": [vp, C.POINTER(i64)],
             "coded_qr_sync_status": [vp],
             "coded_qr_set_wait_limit": [vp, i64],
+            "coded_qr_debug_bounds": [C.POINTER(i32)],
+            "coded_qr_debug_bounds_selftest": [vp],
             "coded_qr_profile": [vp, i32],
             "coded_qr_profile_read": [vp, C.POINTER(C.c_double), C.POINTER(i64), i32, i32],
             "coded_qr_panel_icgs_noalloc": [i32, i64, i32, vp, i64, vp, i64, C.c_double, vp, vp],
@@ -690,3 +696,16 @@ class CodedQRBatch:
 
     def sync_status(self):
         return coded_qr_batched_sync_status(self.h)
+
+
+def debug_bounds():
+    """(status, site) of the bounds-checked build's index checks since the last call
+    (coded_qr_debug_bounds; CQR_ENOTSUP from the normal build)."""
+    site = C.c_int32(0)
+    st = lib().coded_qr_debug_bounds(C.byref(site))
+    return st, site.value
+
+
+def debug_bounds_selftest(stream=None):
+    """Enqueue the bounds-checked build's self-test (one guarded write out of range)."""
+    return lib().coded_qr_debug_bounds_selftest(C.c_void_p(stream))

@@ -16,6 +16,9 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcoded_qr.so")
+# the bounds-checked variant (-DCQR_DEBUG_BOUNDS: index checks that record CQR_EBOUNDS and return)
+OUT_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(OUT_DEBUG, "libcoded_qr_debug.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -26,8 +29,9 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _digest():
+def _digest(extra=()):
     h = hashlib.sha256()
+    h.update(" ".join(extra).encode())
     for p in sorted(glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INC, "*.h"))):
         with open(p, "rb") as fh:
             h.update(os.path.basename(p).encode())
@@ -36,8 +40,8 @@ def _digest():
     return h.hexdigest()
 
 
-def _compile(src, extra):
-    obj = os.path.join(OUT, os.path.basename(src) + ".o")
+def _compile(src, extra, out=OUT):
+    obj = os.path.join(out, os.path.basename(src) + ".o")
     cmd = [NVCC] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -45,32 +49,36 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(force=False, verbose=False, ptxas_info=False):
-    os.makedirs(OUT, exist_ok=True)
-    stamp = os.path.join(OUT, "stamp")
-    dig = _digest()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+def build(force=False, verbose=False, ptxas_info=False, debug_bounds=False):
+    """Compile the library (debug_bounds: the bounds-checked variant, in its own folder)."""
+    out, lib = (OUT_DEBUG, LIB_DEBUG) if debug_bounds else (OUT, LIB)
+    defs = ["-DCQR_DEBUG_BOUNDS"] if debug_bounds else []
+    os.makedirs(out, exist_ok=True)
+    stamp = os.path.join(out, "stamp")
+    dig = _digest(defs)
+    if not force and os.path.exists(lib) and os.path.exists(stamp):
         with open(stamp) as fh:
             if fh.read().strip() == dig:
-                return LIB
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+                return lib
+    extra = defs + (["-Xptxas", "-v"] if ptxas_info else [])
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        results = list(ex.map(lambda s: _compile(s, extra), srcs))
+        results = list(ex.map(lambda s: _compile(s, extra, out), srcs))
     if verbose or ptxas_info:
         for obj, err in results:
             if err.strip():
                 print(err, file=sys.stderr)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp, "w") as fh:
         fh.write(dig)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                debug_bounds="--debug-bounds" in sys.argv))

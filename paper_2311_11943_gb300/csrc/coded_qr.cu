@@ -1156,6 +1156,36 @@ cqr_status coded_qr_stats(cqr_handle h, int64_t* out) {
   return CQR_OK;
 }
 
+cqr_status coded_qr_debug_bounds(int32_t* site) {
+  if (site) *site = 0;
+#ifndef CQR_DEBUG_BOUNDS
+  return CQR_ENOTSUP;
+#else
+  cudaError_t (*const takes[])(int*, int*) = {bounds_take_kernels, bounds_take_panel,
+                                              bounds_take_panel_reg, bounds_take_tc};
+  cqr_status out = CQR_OK;
+  for (auto take : takes) {
+    int code = 0, where = 0;
+    CK(take(&code, &where));
+    if (code != 0 && out == CQR_OK) {
+      out = CQR_EBOUNDS;
+      if (site) *site = where;
+    }
+  }
+  return out;
+#endif
+}
+
+cqr_status coded_qr_debug_bounds_selftest(void* stream) {
+#ifndef CQR_DEBUG_BOUNDS
+  (void)stream;
+  return CQR_ENOTSUP;
+#else
+  CK(launch_bounds_selftest(4, reinterpret_cast<cudaStream_t>(stream)));
+  return CQR_OK;
+#endif
+}
+
 cqr_status coded_qr_set_wait_limit(cqr_handle h, int64_t cycles) {
   if (!h || cycles < 0) return CQR_EINVAL;
   h->wait_limit = (long long)cycles;

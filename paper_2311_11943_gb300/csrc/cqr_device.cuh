@@ -18,26 +18,46 @@ __device__ __forceinline__ void set_status(int* st, int code, int detail) {
 }
 
 // Index checks of the bounds-checked build (compiled with -DCQR_DEBUG_BOUNDS; nothing in the
-// normal build).  CQR_CHECK(cond, status, site): when cond is false the thread records
-// CQR_EBOUNDS with the site number (when a status word is at hand) and returns from the
-// kernel before the access the condition guards; it never traps.  Used only where a return
-// cannot strand other threads at a barrier (element-wise kernels, after a kernel's last
-// barrier), or with CQR_CHECK_SKIP, which skips the guarded access instead of returning.
+// normal build).  CQR_CHECK(cond, site): when cond is false the thread records CQR_EBOUNDS with
+// the site number in this file's bounds word and returns from the kernel before the access the
+// condition guards; it never traps.  CQR_CHECK_OK(cond, site) records the same and yields false
+// (for accesses that are skipped instead, where a return would strand other threads at a
+// barrier).  Each source file has its own word; coded_qr_debug_bounds collects them.
 #ifdef CQR_DEBUG_BOUNDS
-#define CQR_CHECK(cond, status, site)                                \
-  do {                                                               \
-    if (!(cond)) {                                                   \
-      if (status) ::cqr::set_status((status), CQR_EBOUNDS, (site));  \
-      return;                                                        \
-    }                                                                \
+static __device__ int g_bounds[2];  // [0] CQR_EBOUNDS once a check failed, [1] its site
+__device__ __forceinline__ bool bounds_fail(int site) {
+  if (atomicCAS(&g_bounds[0], 0, CQR_EBOUNDS) == 0) g_bounds[1] = site;
+  return false;
+}
+#define CQR_CHECK(cond, site) \
+  do {                        \
+    if (!(cond)) {            \
+      ::cqr::bounds_fail(site); \
+      return;                 \
+    }                         \
   } while (0)
-#define CQR_CHECK_OK(cond, status, site) \
-  ((cond) ? true : ((status) ? (::cqr::set_status((status), CQR_EBOUNDS, (site)), false) : false))
+#define CQR_CHECK_OK(cond, site) ((cond) ? true : ::cqr::bounds_fail(site))
+// This file's bounds word (code, site), cleared after the read.
+static inline cudaError_t bounds_take_here(int* code, int* site) {
+  int v[2] = {0, 0};
+  cudaError_t e = cudaMemcpyFromSymbol(v, g_bounds, sizeof(v));
+  if (e != cudaSuccess) return e;
+  const int z[2] = {0, 0};
+  e = cudaMemcpyToSymbol(g_bounds, z, sizeof(z));
+  *code = v[0];
+  *site = v[1];
+  return e;
+}
 #else
-#define CQR_CHECK(cond, status, site) \
-  do {                                \
+#define CQR_CHECK(cond, site) \
+  do {                        \
   } while (0)
-#define CQR_CHECK_OK(cond, status, site) true
+#define CQR_CHECK_OK(cond, site) true
+static inline cudaError_t bounds_take_here(int* code, int* site) {
+  *code = 0;
+  *site = 0;
+  return cudaSuccess;
+}
 #endif
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {

@@ -88,6 +88,8 @@ __device__ __forceinline__ void encode_vertical_f(const Geo& g, const T* __restr
   const int s = by * 8 + threadIdx.y;
   if (r >= mb || s >= nb) return;
   const int64_t col = (int64_t)j * nb + s;
+  // A: m rows below lda; the encoded column: m_pad + f mb rows below ldq
+  CQR_CHECK(col < g.n && lda >= m && g.m_pad + (int64_t)f * mb <= g.ldq, 101);
   const T* Ac = A + col * lda;
   T* Qc = Q + col * g.ldq;
   T acc[NA];
@@ -134,6 +136,8 @@ __device__ __forceinline__ void encode_horizontal_f(const Geo& g, const T* __res
   const int s = by * 8 + threadIdx.y;
   if (r >= mb || s >= nb) return;
   const int64_t ldq = g.ldq;
+  // row (t, r) inside the encoded matrix; the checksum columns n + l nb + s inside N
+  CQR_CHECK((int64_t)t * mb + r < g.M && g.M <= ldq && g.n + (int64_t)f * nb <= g.N, 102);
   T* Qr = Q + (int64_t)t * mb + r + (int64_t)s * ldq;  // row (t, r), column s of tile column 0
   const int64_t tcs = (int64_t)nb * ldq;                 // one tile column
   T acc[NA];
@@ -201,6 +205,7 @@ __global__ void __launch_bounds__(256) k_gemm_tn_splitk(const T* __restrict__ A,
   __shared__ T As[32][65];
   __shared__ T Bs[32][65];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  CQR_CHECK(lda >= K && ldb >= K, 103);  // uniform over the launch: before any barrier
   const int i0 = blockIdx.x * 64;
   const int64_t j0 = (int64_t)blockIdx.y * 64;
   const int64_t k0 = (int64_t)blockIdx.z * kchunk;
@@ -260,6 +265,7 @@ cudaError_t launch_gemm_tn_splitk(const T* A, int64_t lda, const T* B, int64_t l
 template <typename T>
 __global__ void k_splitk_reduce(const T* __restrict__ P, int splits, int bk, int64_t w,
                                 T* __restrict__ R, int64_t ldr, T* __restrict__ Rb, int accumulate) {
+  CQR_CHECK(ldr >= bk, 104);
   const int64_t total = (int64_t)bk * w;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -292,6 +298,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn_sub(const T* __restrict__ A, in
   __shared__ T As[32][65];
   __shared__ T Bs[32][65];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  CQR_CHECK(lda >= M && ldc >= M && ldb >= bk, 105);  // uniform: before any barrier
   const int64_t i0 = (int64_t)blockIdx.x * 64;
   const int64_t j0 = (int64_t)blockIdx.y * 64;
   T acc[4][4];
@@ -354,6 +361,7 @@ template <typename T>
 __global__ void k_poison(T* __restrict__ X, int64_t ld, int64_t th, int64_t tw, TileList tl) {
   const int e = blockIdx.y;
   const int i = tl.ij[2 * e], j = tl.ij[2 * e + 1];
+  CQR_CHECK(e < tl.count && i >= 0 && j >= 0 && (int64_t)(i + 1) * th <= ld, 106);
   const int64_t total = th * tw;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -407,6 +415,9 @@ __device__ __forceinline__ void decode_body(const Geo& g, const DecodePlan& p,
                                             int* status, int bx, int by, int sy) {
   __shared__ DecodeScratch<T> sh;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  // the plan names a code of the grid and at most f lost tiles (uniform over the CTA)
+  CQR_CHECK(p.f1 + p.f2 <= g.f && p.idx >= 0 &&
+                p.idx < (p.kind == 0 ? g.grid_cols : g.p_c + g.f) && g.M <= g.ldq, 107);
   if (!decode_setup<T>(g, p, Gt, Gh, sh, tid, blockDim.x * blockDim.y, status, bx == 0 && by == 0))
     return;
   const int64_t h = p.kind == 0 ? g.mb : g.nb;
@@ -467,6 +478,8 @@ __device__ __forceinline__ void post_orth_f(const Geo& g, const T* __restrict__ 
   const int64_t mb = g.mb;
   if (s >= mb || col >= k) return;
   const int f = F >= 0 ? F : g.f, p_r = g.p_r;
+  // every block row t < p_r of W lies below ldw; Z is read below zrows <= ldz
+  CQR_CHECK((int64_t)p_r * mb <= ldw && zrows <= ldz, 108);
   const T* zc = Z + col * ldz;
   T* wc = W + col * ldw;
   T zl[NA], acc[NA];
@@ -615,6 +628,8 @@ __global__ void __launch_bounds__(256) k_post_orth_proj(Geo g, const T* __restri
   const int64_t col = (int64_t)blockIdx.y * 8 + threadIdx.y;
   const int64_t mb = g.mb;
   if (s >= mb || col >= k) return;
+  // Q_1 and Q_2 (m_pad + f mb rows) below ldq; W's m_pad rows below ldw
+  CQR_CHECK(g.m_pad + (int64_t)f * mb <= ldq && g.m_pad <= ldw && p_r * mb == g.m_pad, 109);
   const T* qc = Q + col * ldq;
   T* wc = W + col * ldw;
   T d[NF], e[NF], a[NF];
@@ -769,6 +784,7 @@ __global__ void __launch_bounds__(256) k_gemv_t(const T* __restrict__ Qo, int64_
   const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int64_t col = blockIdx.y;
   if (j >= n) return;
+  CQR_CHECK(rows <= ldq && rows <= ldy && n <= ldz, 110);
   const T* q = Qo + j * ldq;
   const T* yy = y + col * ldy;
   T acc = T(0);
@@ -1395,6 +1411,22 @@ cudaError_t launch_b_post_orth(const BatchInst<T>* inst, int count, const int64_
   k_b_post_orth<T><<<grid, dim3(32, 8), 0, st>>>(inst, count, off, Gt_t);
   return cudaGetLastError();
 }
+
+// Self-test of the bounds-checked build: a write to element idx of a four-element array,
+// guarded by its index check (site 199); with idx >= 4 the check records CQR_EBOUNDS and the
+// thread returns without the write.  Launched only by the bounds-checked build.
+static __device__ float g_selftest[4];
+__global__ void k_bounds_selftest(int idx) {
+  CQR_CHECK(idx >= 0 && idx < 4, 199);
+  g_selftest[idx] = 1.f;
+}
+
+cudaError_t launch_bounds_selftest(int idx, cudaStream_t st) {
+  k_bounds_selftest<<<1, 1, 0, st>>>(idx);
+  return cudaGetLastError();
+}
+
+cudaError_t bounds_take_kernels(int* code, int* site) { return bounds_take_here(code, site); }
 
 #define CQR_INSTANTIATE(T)                                                                        \
   template cudaError_t launch_generator<T>(int, int, int, uint64_t, int, double*, double*, T*,   \

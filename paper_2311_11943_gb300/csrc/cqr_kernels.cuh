@@ -54,6 +54,15 @@ template <typename T>
 bool panel_hier_fits(const PanelPlan& pp);
 size_t panel_partial_bytes(int bk, size_t elem, int num_sms);
 
+// Bounds words of the bounds-checked build (-DCQR_DEBUG_BOUNDS), one per source file: read and
+// cleared; (0, 0) in the normal build.
+cudaError_t bounds_take_kernels(int* code, int* site);
+cudaError_t bounds_take_panel(int* code, int* site);
+cudaError_t bounds_take_panel_reg(int* code, int* site);
+cudaError_t bounds_take_tc(int* code, int* site);
+// A guarded write past a four-element array (the bounds-checked build's self-test).
+cudaError_t launch_bounds_selftest(int idx, cudaStream_t st);
+
 // Register-resident FP32 panel in one cluster (cqr_panel_reg.cu).
 bool plan_panel_reg(int64_t M, int bk, int* rpl, int* cpw, int* G);
 bool panel_reg_cluster_fits(int rpl, int cpw, int G);

@@ -398,6 +398,10 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
   extern __shared__ __align__(16) unsigned char smraw[];
   const int g = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
+  // the slices and R rows stay inside their buffers (the same for every CTA: before any
+  // barrier)
+  CQR_CHECK(ldq >= M && ldr >= bk && rpc == 32 * RPL && rpc_pad >= rpc &&
+                (int64_t)gridDim.x * rpc >= M, 201);
   const int pld = (bk + 3) / 4 * 4;
   const int64_t row0 = (int64_t)g * rpc;
   const int nr = (int)((M - row0) < rpc ? (M - row0) : rpc);
@@ -1045,6 +1049,8 @@ template bool panel_cluster_fits<float>(const PanelPlan&);
 template bool panel_cluster_fits<double>(const PanelPlan&);
 template bool panel_hier_fits<float>(const PanelPlan&);
 template bool panel_hier_fits<double>(const PanelPlan&);
+
+cudaError_t bounds_take_panel(int* code, int* site) { return bounds_take_here(code, site); }
 
 }  // namespace cqr
 

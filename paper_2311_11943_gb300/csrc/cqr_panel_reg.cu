@@ -122,6 +122,10 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
   uint64_t* mbar = reinterpret_cast<uint64_t*>(racc + kNW * RPC);  // [2 parity]
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
+  // the panel's columns fit the owned slots and its rows the cluster's slices (uniform:
+  // before any barrier)
+  CQR_CHECK(ldq >= M && ldr >= bk && bk <= kNW * CPW && bk <= 256 && G <= kMaxG &&
+                (int64_t)G * RPC >= M, 301);
   const int64_t row0 = (int64_t)g * RPC;
   const int nr = (int)((M - row0) < RPC ? (M - row0) : RPC);
   float* eta = v + 256;
@@ -549,5 +553,7 @@ bool panel_reg_cluster_fits(int rpl, int cpw, int G) {
   }
   return n >= 1;
 }
+
+cudaError_t bounds_take_panel_reg(int* code, int* site) { return bounds_take_here(code, site); }
 
 }  // namespace cqr

@@ -252,6 +252,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the output tiles stay inside `out` (uniform over the launch: before any barrier or TMEM
+  // allocation)
+  CQR_CHECK(job.ldo >= job.mrows && (int64_t)job.m_tiles * BM >= job.mrows &&
+                (int64_t)job.n_tiles * BN >= job.ncols, 401);
   const int total_tiles = job.m_tiles * job.n_tiles * job.splits;
   const int nkb_full = (int)(job.kchunk / BK);
 
@@ -444,54 +448,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
       const int64_t row = (int64_t)mt * BM + ew * 32 + lane;
       const bool row_ok = row < job.mrows;
       const bool has_k = kblocks(split) > 0;
-      if (job.epi == 0) {
 #pragma unroll 1
-        for (int c = 0; c < BN / 32; ++c) {
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
-          if (!has_k)
+      for (int c = 0; c < BN / 32; ++c) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
+        if (!has_k)
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = 0.f;
-          const int64_t col0 = (int64_t)nt * BN + c * 32;
+          for (int i = 0; i < 32; ++i) v[i] = 0.f;
+        const int64_t col0 = (int64_t)nt * BN + c * 32;
+        if (job.epi == 0) {
           float* o = job.out + (int64_t)split * job.split_stride;
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
             const int64_t col = col0 + i;
             if (row_ok && col < job.ncols) o[row + col * job.ldo] = v[i];
           }
-        }
-      } else {
-        // C -= D in chunks of 32 columns; the loads of chunk c + 1 are issued before chunk c
-        // is read from TMEM and subtracted, so their latency overlaps that work
-        float* crow = job.out + row;
-        float nxt[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int64_t col = (int64_t)nt * BN + i;
-          nxt[i] = (row_ok && col < job.ncols) ? crow[col * job.ldo] : 0.f;
-        }
-#pragma unroll
-        for (int c = 0; c < BN / 32; ++c) {
-          float cur[32];
-#pragma unroll
-          for (int i = 0; i < 32; ++i) cur[i] = nxt[i];
-          const int64_t col0 = (int64_t)nt * BN + c * 32;
-          if (c + 1 < BN / 32) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const int64_t col = col0 + 32 + i;
-              nxt[i] = (row_ok && col < job.ncols) ? crow[col * job.ldo] : 0.f;
-            }
-          }
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
-          if (!has_k)
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = 0.f;
+        } else {
+          float old[32];
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
             const int64_t col = col0 + i;
-            if (row_ok && col < job.ncols) crow[col * job.ldo] = cur[i] - v[i];
+            old[i] = (row_ok && col < job.ncols) ? job.out[row + col * job.ldo] : 0.f;
+          }
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int64_t col = col0 + i;
+            if (row_ok && col < job.ncols) job.out[row + col * job.ldo] = old[i] - v[i];
           }
         }
       }
@@ -904,20 +886,12 @@ void tc_set_status(TcGemm* t, int* status) { t->status = status; }
 void tc_set_pdl_stream(TcGemm* t, cudaStream_t st) { t->pdl_st = st; }
 
 namespace {
-// GEMM2 (3xTF32) may take Rbar raw and split it in shared memory like GEMM1 (CQR_GEMM2_SPLITB=1):
-// 48 instead of 64 KB of operands per stage from L2, the same hi / lo values
-bool gemm2_split_b(const TcGemm* t) {
-  static const int on = [] {
-    const char* e = getenv("CQR_GEMM2_SPLITB");
-    return e && e[0] == '1' ? 1 : 0;
-  }();
-  return on && t->nplanes == 2 && !t->bf;
-}
-
-// K blocks per work unit for `tiles` output tiles and `kblocks` K blocks on `ctas` persistent
-// CTAs, at most max_splits chunks: the count whose launch finishes first, i.e. the least
-// (waves of work units) x (K blocks per unit), each unit one tile and one K chunk; a split
-// adds partial-sum traffic, so each split costs 2% more and ties go to fewer splits.
+// Split-K factor of a product with m1 x n1 output tiles and K = M rows: the count s whose
+// launch finishes first on `ctas` persistent CTAs, i.e. the least (waves of work units) x
+// (K blocks per unit), each unit one tile and one K chunk; a split adds partial-sum traffic,
+// so each split costs 2% more and ties go to fewer splits.
+// K blocks per work unit for `tiles` output tiles and `kblocks` K blocks on `ctas` CTAs, at
+// most max_splits chunks (see tc_splits).
 int64_t best_kchunk(int64_t tiles, int64_t kblocks, int ctas, int max_splits) {
   int64_t best_kc = kblocks;
   double best = -1.0;
@@ -1031,14 +1005,12 @@ cudaError_t tc_reduce(TcGemm* t, int64_t kb, int bk, int64_t j0, int64_t w, floa
   const bool pdl = st == t->pdl_st && st != nullptr;
   const float* P = t->P[ctx];
   float* Rd = R + kb + j0 * ldr;
-  // with GEMM2 splitting its B operand in shared memory, Rbar goes out raw (one plane)
-  const int np = gemm2_split_b(t) ? 1 : t->nplanes;
   if (t->bf)
     return launch_k(k_tc_reduce<__nv_bfloat16>, dim3(blocks), dim3(256), 0, st, pdl, P, splits,
                     (int64_t)bkp * w, (int64_t)bkp, bk, bkp, w, Rd, ldr, t->nplanes,
                     pl<__nv_bfloat16>(t->Bh[ctx]), pl<__nv_bfloat16>(t->Bl[ctx]));
   return launch_k(k_tc_reduce<float>, dim3(blocks), dim3(256), 0, st, pdl, P, splits, (int64_t)bkp * w,
-                  (int64_t)bkp, bk, bkp, w, Rd, ldr, np, pl<float>(t->Bh[ctx]),
+                  (int64_t)bkp, bk, bkp, w, Rd, ldr, t->nplanes, pl<float>(t->Bh[ctx]),
                   pl<float>(t->Bl[ctx]));
 }
 
@@ -1054,7 +1026,7 @@ cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, int buf, in
   maps.b[1] = t->tm_bh[ctx][1];
   TcJob job{};
   job.nprod = three ? 3 : 1;
-  job.split_b_smem = gemm2_split_b(t) ? 1 : 0;
+  job.split_b_smem = 0;
   job.epi = 1;
   job.m_tiles = (int)((t->M + BM - 1) / BM);
   job.n_tiles = (int)((w + BN - 1) / BN);
@@ -1073,7 +1045,7 @@ cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, int buf, in
   maps.c = t->tm_q_b;
   job.prefetch_c = 1;
   job.c_col0 = j0;
-  return launch_mode(t, job.split_b_smem != 0, maps, job, st, max_ctas);
+  return launch_mode(t, false, maps, job, st, max_ctas);
 }
 
 // Block reorthogonalisation of panel kb .. kb+bk-1 against columns 0 .. kb-1 (four
@@ -1223,5 +1195,7 @@ cudaError_t tc_gemm_sub3(bool a_trans, const float* A, int64_t lda, const float*
   job.status = status;
   return launch_gemm<false, 3, 2, 2>(maps, job, num_sms, st, false);
 }
+
+cudaError_t bounds_take_tc(int* code, int* site) { return bounds_take_here(code, site); }
 
 }  // namespace cqr
