@@ -168,4 +168,67 @@ __device__ __forceinline__ void decode_apply(const Geo& g, const DecodePlan& p,
     if (e < f2) ptr[(int64_t)(nsys + p.C_fail[e]) * tstride] = ce[e];
 }
 
+// Four consecutive rows r4 .. r4+3 of position column s in one thread, FP32, with 16-byte
+// loads and stores (a warp reads 512 contiguous bytes of each code tile); f <= 4.  The
+// caller guarantees 16-byte alignment: the tile height and the leading dimension are
+// multiples of four and r4 is.  Every element is summed in the same order as decode_apply,
+// so the result has the same bits.
+__device__ __forceinline__ void decode_apply4(const Geo& g, const DecodePlan& p,
+                                              const DecodeScratch<float>& sh, float* Q, float* R,
+                                              int64_t r4, int64_t s) {
+  constexpr int NF = 4;
+  const bool isQ = (p.kind == 0);
+  const int nsys = p.nsys, f1 = p.f1, f2 = p.f2;
+  float* base = isQ ? Q + (int64_t)p.idx * g.nb * g.ldq : R + (int64_t)p.idx * g.nb;
+  const int64_t tstride = isQ ? g.mb : g.nb * g.ldr;
+  const int64_t ld = isQ ? g.ldq : g.ldr;
+  float* ptr = base + r4 + s * ld;
+  float4 xb[NF], ce[NF];
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    xb[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    ce[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  auto fma4 = [](float4& acc, float c, const float4& v) {
+    acc.x += c * v.x;
+    acc.y += c * v.y;
+    acc.z += c * v.z;
+    acc.w += c * v.w;
+  };
+  auto add = [&](int t, const float4& val) {
+#pragma unroll
+    for (int b = 0; b < NF; ++b)
+      if (b < f1) fma4(xb[b], sh.coef[b][t], val);
+    if (t < nsys) {
+#pragma unroll
+      for (int e = 0; e < NF; ++e)
+        if (e < f2) fma4(ce[e], sh.cenc[e][t], val);
+    }
+  };
+  for (int u0 = 0; u0 < sh.nuse; u0 += 4) {
+    int tt[4];
+    float4 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      tt[k] = (u0 + k < sh.nuse) ? sh.tuse[u0 + k] : -1;
+      v[k] = tt[k] >= 0 ? *reinterpret_cast<const float4*>(ptr + (int64_t)tt[k] * tstride)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (tt[k] >= 0) add(tt[k], v[k]);
+  }
+#pragma unroll
+  for (int b = 0; b < NF; ++b)
+    if (b < f1) {
+      *reinterpret_cast<float4*>(ptr + (int64_t)p.A_fail[b] * tstride) = xb[b];
+#pragma unroll
+      for (int e = 0; e < NF; ++e)
+        if (e < f2) fma4(ce[e], sh.cenc[e][p.A_fail[b]], xb[b]);
+    }
+#pragma unroll
+  for (int e = 0; e < NF; ++e)
+    if (e < f2) *reinterpret_cast<float4*>(ptr + (int64_t)(nsys + p.C_fail[e]) * tstride) = ce[e];
+}
+
 }  // namespace cqr

@@ -167,9 +167,116 @@ __global__ void __launch_bounds__(256, 4) k_encode_horizontal(Geo g, const T* __
   encode_horizontal_f<T, F>(g, Gh, Q, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// Both codes in one pass (R protected, F <= 4 checksums, p_c <= 16 tile columns).  A block of
+// 32 x 4 x 2 threads covers 32 rows r and 2 columns s of a tile position; the four threads of
+// a position (r, s) split the p_c tile columns into four contiguous groups of at most four.
+// Each walks its tiles A_{t,j}(r, s) once, tile row by tile row (two rows' loads in flight),
+// writes them into the encoded matrix and keeps the vertical checksums of its columns in
+// registers; the four partial horizontal checksums of a row, and at the end the four partial
+// corners (G_h applied to the vertical checksums), are added through shared memory in group
+// order.  A is read once and the encoded matrix written once.  Vertical sums run over t
+// ascending, as in the oracle; horizontal sums over j ascending within a group, groups in order.
+template <typename T, int F>
+__global__ void __launch_bounds__(256) k_encode_fused(Geo g, const T* __restrict__ A, int64_t lda,
+                                                     const T* __restrict__ Gt,
+                                                     const T* __restrict__ Gh, T* __restrict__ Q) {
+  constexpr int KMAX = 4;  // tile columns per thread
+  __shared__ T hs[2][2][4][F][32];  // [row parity][s][group][l][r]
+  const int mb = (int)g.mb, nb = (int)g.nb, p_r = g.p_r, p_c = g.p_c;
+  const int64_t m = g.m, ldq = g.ldq;
+  const int tx = threadIdx.x, jg = threadIdx.y, sz = threadIdx.z;
+  const int r = blockIdx.x * 32 + tx;
+  const int s = blockIdx.y * 2 + sz;
+  const bool live = r < mb && s < nb;
+  const int cpg = (p_c + 3) / 4;
+  const int j0 = jg * cpg;
+  const int nj = max(0, min(cpg, p_c - j0));
+  // uniform over the launch, before the barriers: the geometry the indexing below assumes
+  CQR_CHECK(p_c <= 4 * KMAX && lda >= m && g.M <= ldq && g.n + (int64_t)F * nb <= g.N &&
+                g.m_pad + (int64_t)F * mb <= g.M, 112);
+  T vacc[KMAX][F];
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+    for (int i = 0; i < F; ++i) vacc[k][i] = T(0);
+  for (int t0 = 0; t0 < p_r; t0 += 2) {
+    T a[2][KMAX];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const int64_t row = (int64_t)(t0 + d) * mb + r;
+      const bool in = live && t0 + d < p_r && row < m;
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+        a[d][k] = (in && k < nj) ? A[row + ((int64_t)(j0 + k) * nb + s) * lda] : T(0);
+    }
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const int t = t0 + d;
+      if (t >= p_r) break;
+      const int64_t row = (int64_t)t * mb + r;
+      T h[F];
+#pragma unroll
+      for (int l = 0; l < F; ++l) h[l] = T(0);
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k)
+        if (k < nj) {
+          const int j = j0 + k;
+          if (live) Q[row + ((int64_t)j * nb + s) * ldq] = a[d][k];
+#pragma unroll
+          for (int i = 0; i < F; ++i) vacc[k][i] += Gt[i * p_r + t] * a[d][k];
+#pragma unroll
+          for (int l = 0; l < F; ++l) h[l] += Gh[j * F + l] * a[d][k];
+        }
+#pragma unroll
+      for (int l = 0; l < F; ++l) hs[t & 1][sz][jg][l][tx] = h[l];
+      __syncthreads();
+      if (jg < F && live) {  // thread group jg writes checksum l = jg of this row
+        const int l = jg;
+        T sum = hs[t & 1][sz][0][l][tx];
+        for (int q = 1; q < 4; ++q) sum += hs[t & 1][sz][q][l][tx];
+        Q[row + (g.n + (int64_t)l * nb + s) * ldq] = sum;
+      }
+    }
+  }
+  // vertical checksums of this thread's columns, then the corner through shared memory
+#pragma unroll
+  for (int i = 0; i < F; ++i) {
+    const int64_t row = g.m_pad + (int64_t)i * mb + r;
+    T c[F];
+#pragma unroll
+    for (int l = 0; l < F; ++l) c[l] = T(0);
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+      if (k < nj) {
+        const int j = j0 + k;
+        if (live) Q[row + ((int64_t)j * nb + s) * ldq] = vacc[k][i];
+#pragma unroll
+        for (int l = 0; l < F; ++l) c[l] += Gh[j * F + l] * vacc[k][i];
+      }
+    __syncthreads();  // the previous round's reads of hs are done
+#pragma unroll
+    for (int l = 0; l < F; ++l) hs[0][sz][jg][l][tx] = c[l];
+    __syncthreads();
+    if (jg < F && live) {
+      const int l = jg;
+      T sum = hs[0][sz][0][l][tx];
+      for (int q = 1; q < 4; ++q) sum += hs[0][sz][q][l][tx];
+      Q[row + (g.n + (int64_t)l * nb + s) * ldq] = sum;
+    }
+  }
+}
+
 template <typename T, int F>
 cudaError_t launch_encode_f(const Geo& g, const T* A, int64_t lda, const T* Gt, const T* Gh, T* Q,
                             cudaStream_t st) {
+  if constexpr (F > 0) {
+    if (g.protect_r && g.p_c <= 16) {
+      dim3 blk(32, 4, 2);
+      dim3 grd((unsigned)((g.mb + 31) / 32), (unsigned)((g.nb + 1) / 2));
+      k_encode_fused<T, F><<<grd, blk, 0, st>>>(g, A, lda, Gt, Gh, Q);
+      return cudaGetLastError();
+    }
+  }
   dim3 blk(32, 8);
   dim3 grd((unsigned)((g.mb + 31) / 32), (unsigned)((g.nb + 7) / 8), (unsigned)g.p_c);
   k_encode_vertical<T, F><<<grd, blk, 0, st>>>(g, A, lda, Gt, Q);
@@ -434,6 +541,29 @@ __device__ __forceinline__ void decode_body(const Geo& g, const DecodePlan& p,
   }
 }
 
+// Four rows per thread (FP32, f <= 4, tile heights and leading dimensions multiples of four):
+// a 32 x 8 block covers 128 rows of 8 position columns, strided over the grid's y.
+__global__ void __launch_bounds__(256) k_decode4(Geo g, const DecodePlan* __restrict__ plans,
+                                                  const double* __restrict__ Gt,
+                                                  const double* __restrict__ Gh, float* Q,
+                                                  float* R, int* status) {
+  __shared__ DecodeScratch<float> sh;
+  const DecodePlan& p = plans[blockIdx.z];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  CQR_CHECK(p.f1 + p.f2 <= g.f && g.f <= 4 && p.idx >= 0 &&
+                p.idx < (p.kind == 0 ? g.grid_cols : g.p_c + g.f) && g.M <= g.ldq &&
+                g.mb % 4 == 0 && g.nb % 4 == 0 && g.ldq % 4 == 0 && g.ldr % 4 == 0, 111);
+  if (!decode_setup<float>(g, p, Gt, Gh, sh, tid, blockDim.x * blockDim.y, status,
+                           blockIdx.x == 0 && blockIdx.y == 0))
+    return;
+  const int64_t h = p.kind == 0 ? g.mb : g.nb;
+  const int64_t r4 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (r4 >= h) return;
+  for (int64_t s = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; s < g.nb;
+       s += (int64_t)gridDim.y * blockDim.y)
+    decode_apply4(g, p, sh, Q, R, r4, s);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_decode(Geo g, const DecodePlan* __restrict__ plans,
                                                  const double* __restrict__ Gt,
@@ -451,7 +581,18 @@ cudaError_t launch_decode(const Geo& g, const DecodePlan* plans_dev, int nplans,
   // about one wave (768 CTAs over all codes), so that each CTA's table setup is amortised
   // over several 8-column groups
   dim3 blk(32, 8);
-  const int64_t nbx = (max_h + 31) / 32, nby = (g.nb + 7) / 8;
+  const int64_t nby = (g.nb + 7) / 8;
+  if (sizeof(T) == 4 && g.f <= 4 && g.mb % 4 == 0 && g.nb % 4 == 0 && g.ldq % 4 == 0 &&
+      g.ldr % 4 == 0) {
+    // 16-byte accesses, four rows per thread: a block covers 128 rows
+    const int64_t nbx = (max_h + 127) / 128;
+    const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(nby, 1216 / std::max<int64_t>(1, nbx * nplans)));
+    dim3 grd((unsigned)nbx, (unsigned)gy, (unsigned)nplans);
+    k_decode4<<<grd, blk, 0, st>>>(g, plans_dev, Gt, Gh, reinterpret_cast<float*>(Q),
+                                   reinterpret_cast<float*>(R), status);
+    return cudaGetLastError();
+  }
+  const int64_t nbx = (max_h + 31) / 32;
   const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(nby, 768 / std::max<int64_t>(1, nbx * nplans)));
   dim3 grd((unsigned)nbx, (unsigned)gy, (unsigned)nplans);
   k_decode<T><<<grd, blk, 0, st>>>(g, plans_dev, Gt, Gh, Q, R, status);
