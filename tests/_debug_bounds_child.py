@@ -58,7 +58,7 @@ def run_case(m, n, p_r, p_c, f, b, dtype, mma, er, form):
     tol = n * u * 10.0 * (1e4 if mma == "tf32" else (8 if mma == "3xtf32" else 1))
     err = float(np.abs(R - ref["R"]).max() / np.abs(ref["R"]).max())
     bst, site = B.debug_bounds()
-    return {"status": st, "bounds": bst, "site": site, "err": err, "tol": tol}
+    return {"status": int(st), "bounds": int(bst), "site": int(site), "err": err, "tol": float(tol)}
 
 
 out = {"cases": [run_case(*c) for c in CASES]}
