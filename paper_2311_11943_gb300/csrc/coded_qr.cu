@@ -355,7 +355,8 @@ cqr_status encode_t(cqr_handle h, const T* A, int64_t lda) {
   }
   {
     ProfScope ps(h, K_ENCODE, (g.protect_r && g.f > 0) ? 2 : 1);
-    CK(launch_encode<T>(g, A, lda, ptr<T>(h->B.Gt_t), ptr<T>(h->B.Gh_t), ptr<T>(h->B.Q), h->st));
+    CK(launch_encode<T>(g, A, lda, ptr<T>(h->B.Gt_t), ptr<T>(h->B.Gh_t), ptr<T>(h->B.Q),
+                      h->B.status, h->st));
   }
   CK(cudaMemsetAsync(h->B.R, 0, (size_t)g.ldr * g.N * sizeof(T), h->st));
   return CQR_OK;

@@ -289,7 +289,14 @@ cudaError_t launch_encode_f(const Geo& g, const T* A, int64_t lda, const T* Gt, 
 
 template <typename T>
 cudaError_t launch_encode(const Geo& g, const T* A, int64_t lda, const T* Gt, const T* Gh, T* Q,
-                          cudaStream_t st) {
+                          int* status, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    const float* Af = reinterpret_cast<const float*>(A);
+    if (encode_tma_applies(g, Af, lda, reinterpret_cast<const float*>(Q)))
+      return launch_encode_tma(g, Af, lda, reinterpret_cast<const float*>(Gt),
+                               reinterpret_cast<const float*>(Gh), reinterpret_cast<float*>(Q),
+                               status, st);
+  }
   switch (f_bucket(g.f)) {
     case 0: return launch_encode_f<T, 0>(g, A, lda, Gt, Gh, Q, st);
     case 1: return launch_encode_f<T, 1>(g, A, lda, Gt, Gh, Q, st);
@@ -580,6 +587,13 @@ cudaError_t launch_decode(const Geo& g, const DecodePlan* plans_dev, int nplans,
   if (nplans == 0) return cudaSuccess;
   // about one wave (768 CTAs over all codes), so that each CTA's table setup is amortised
   // over several 8-column groups
+  if constexpr (sizeof(T) == 4) {
+    const int maxuse = std::max(g.p_r, g.p_c);  // tiles a code reads: its systematic count
+    float* Qf = reinterpret_cast<float*>(Q);
+    float* Rf = reinterpret_cast<float*>(R);
+    if (decode_tma_applies(g, Qf, Rf, maxuse))
+      return launch_decode_tma(g, plans_dev, nplans, maxuse, Gt, Gh, Qf, Rf, status, st);
+  }
   dim3 blk(32, 8);
   const int64_t nby = (g.nb + 7) / 8;
   if (sizeof(T) == 4 && g.f <= 4 && g.mb % 4 == 0 && g.nb % 4 == 0 && g.ldq % 4 == 0 &&
@@ -704,42 +718,70 @@ cudaError_t launch_post_orth(const Geo& g, const T* Gt_t, const T* Z, int64_t ld
 // paper's pipeline.
 
 // K from the FP64 generator: Cholesky L L^T = I_f + G~ G~^T (Golub and Van Loan, the outer
-// product form), then K = L^{-T} L^{-1} column by column; one thread (f <= kMaxF).
-template <typename T>
-__global__ void k_post_orth_coef(int f, int p_r, const double* __restrict__ Gt, double* K64, T* Kt) {
+// product form), then K = L^{-T} L^{-1} column by column; one thread.  F > 0: f = F known at
+// compile time, every loop unrolled and the f x f work in registers (F = -1: generic f <=
+// kMaxF).
+template <typename T, int F>
+__global__ void k_post_orth_coef(int f_rt, int p_r, const double* __restrict__ Gt, double* K64,
+                                 T* Kt) {
+  constexpr int NF = F > 0 ? F : kMaxF;
+  const int f = F > 0 ? F : f_rt;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double A[kMaxF][kMaxF];
-  for (int i = 0; i < f; ++i)
-    for (int l = 0; l <= i; ++l) {
+  double A[NF][NF];
+#pragma unroll
+  for (int i = 0; i < NF; ++i)
+#pragma unroll
+    for (int l = 0; l < NF; ++l) {
+      if (i >= f || l > i) continue;
       double a = (i == l) ? 1.0 : 0.0;
       for (int t = 0; t < p_r; ++t) a += Gt[i * p_r + t] * Gt[l * p_r + t];
       A[i][l] = a;
     }
   // lower triangle of A overwritten by L
-  for (int j = 0; j < f; ++j) {
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    if (j >= f) continue;
     double d = A[j][j];
-    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+#pragma unroll
+    for (int k = 0; k < NF; ++k)
+      if (k < j) d -= A[j][k] * A[j][k];
     d = sqrt(d);
     A[j][j] = d;
-    for (int i = j + 1; i < f; ++i) {
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+      if (i <= j || i >= f) continue;
       double v = A[i][j];
-      for (int k = 0; k < j; ++k) v -= A[i][k] * A[j][k];
+#pragma unroll
+      for (int k = 0; k < NF; ++k)
+        if (k < j) v -= A[i][k] * A[j][k];
       A[i][j] = v / d;
     }
   }
-  for (int col = 0; col < f; ++col) {
-    double x[kMaxF];
-    for (int i = 0; i < f; ++i) {          // L x = e_col
+#pragma unroll
+  for (int col = 0; col < NF; ++col) {
+    if (col >= f) continue;
+    double x[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {          // L x = e_col
+      if (i >= f) continue;
       double v = (i == col) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) v -= A[i][k] * x[k];
+#pragma unroll
+      for (int k = 0; k < NF; ++k)
+        if (k < i) v -= A[i][k] * x[k];
       x[i] = v / A[i][i];
     }
-    for (int i = f - 1; i >= 0; --i) {     // L^T x = x
+#pragma unroll
+    for (int i = NF - 1; i >= 0; --i) {     // L^T x = x
+      if (i >= f) continue;
       double v = x[i];
-      for (int k = i + 1; k < f; ++k) v -= A[k][i] * x[k];
+#pragma unroll
+      for (int k = 0; k < NF; ++k)
+        if (k > i && k < f) v -= A[k][i] * x[k];
       x[i] = v / A[i][i];
     }
-    for (int i = 0; i < f; ++i) {
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+      if (i >= f) continue;
       K64[i * f + col] = x[i];
       Kt[i * f + col] = (T)x[i];
     }
@@ -895,7 +937,13 @@ cudaError_t launch_post_orth_projected(const Geo& g, const double* Gt, const T* 
                                        T* Kt, const T* Q, int64_t ldq, int64_t k, T* W, int64_t ldw,
                                        cudaStream_t st) {
   if (g.f < 1 || g.f > kMaxF || g.p_r + g.f > kMaxCode) return cudaErrorInvalidValue;
-  k_post_orth_coef<T><<<1, 32, 0, st>>>(g.f, g.p_r, Gt, K64, Kt);
+  switch (f_bucket(g.f)) {
+    case 1: k_post_orth_coef<T, 1><<<1, 32, 0, st>>>(g.f, g.p_r, Gt, K64, Kt); break;
+    case 2: k_post_orth_coef<T, 2><<<1, 32, 0, st>>>(g.f, g.p_r, Gt, K64, Kt); break;
+    case 3: k_post_orth_coef<T, 3><<<1, 32, 0, st>>>(g.f, g.p_r, Gt, K64, Kt); break;
+    case 4: k_post_orth_coef<T, 4><<<1, 32, 0, st>>>(g.f, g.p_r, Gt, K64, Kt); break;
+    default: k_post_orth_coef<T, -1><<<1, 32, 0, st>>>(g.f, g.p_r, Gt, K64, Kt); break;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 blk(32, 8);
@@ -1573,7 +1621,7 @@ cudaError_t bounds_take_kernels(int* code, int* site) { return bounds_take_here(
   template cudaError_t launch_generator<T>(int, int, int, uint64_t, int, double*, double*, T*,   \
                                            T*, cudaStream_t);                                     \
   template cudaError_t launch_encode<T>(const Geo&, const T*, int64_t, const T*, const T*, T*,   \
-                                        cudaStream_t);                                            \
+                                        int*, cudaStream_t);                                      \
   template cudaError_t launch_gemm_tn_splitk<T>(const T*, int64_t, const T*, int64_t, int64_t,   \
                                                 int, int64_t, int, T*, cudaStream_t);             \
   template cudaError_t launch_splitk_reduce<T>(const T*, int, int, int64_t, T*, int64_t, T*,     \

@@ -12,8 +12,9 @@
 //               back to the producer and each finished tile to the epilogue
 //   warps 2-3   3xTF32 only: split the streamed B tile in shared memory into hi = rna_tf32(x)
 //               (in place) and lo = x - hi (second buffer)
-//   warps 4-7   epilogue: tcgen05.ld 32 lanes x 32 columns per warp, then either store the
-//               FP32 partial (GEMM1) or subtract it from Q in place (GEMM2)
+//   warps 4-11  epilogue, two warps per quarter of the TMEM lanes: tcgen05.ld 32 lanes x 32
+//               columns per warp (alternate column chunks), then either store the FP32
+//               partial (GEMM1) or subtract it from Q in place (GEMM2)
 // 3xTF32 (hi*hi + hi*lo + lo*hi) recovers about FP32 accuracy from TF32 products.  The small
 // operands (panel and Rbar) are split into hi/lo planes in global memory by helper kernels.
 // Every mbarrier wait is bounded: on expiry the kernel records CQR_ETIMEOUT, stops issuing,
@@ -39,7 +40,8 @@ namespace {
 constexpr int BM = 128;       // UMMA M (TMEM lanes)
 constexpr int BN = 128;       // UMMA N (TMEM columns)
 constexpr int kTmemCols = 2 * BN;  // two accumulator buffers (power of two, <= 512)
-constexpr int kThreads = 256;
+constexpr int kEpiWarps = 8;  // two per TMEM lane quarter, each draining half the columns
+constexpr int kThreads = 32 * (4 + kEpiWarps);
 constexpr int kMaxSplits = 16;
 constexpr uint32_t kTileBytesA = BM * 128;  // 16 KB: 128 rows of one 128-byte swizzle row
 constexpr uint32_t kTileBytesB = BN * 128;  // 16 KB
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);
+      mbar_init(&acc_empty[b], kEpiWarps);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -435,8 +437,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
       }
     }
   } else {
-    // epilogue warps 4..7: TMEM lanes 32 (warp % 4) .. +32
+    // epilogue warps 4 .. 4+kEpiWarps-1: TMEM lanes 32 (warp % 4) .. +32 (a warp may only
+    // read its own quarter of the lanes); the two warps of a quarter take alternate 32-column
+    // chunks, so twice as many loads of the output tile are in flight
     const int ew = warp & 3;
+    const int half = (warp - 4) >> 2;
     int tl = 0;
     for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x, ++tl) {
       const int split = t % job.splits;
@@ -449,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
       const bool row_ok = row < job.mrows;
       const bool has_k = kblocks(split) > 0;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = half; c < BN / 32; c += kEpiWarps / 4) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
         if (!has_k)
@@ -783,6 +788,23 @@ P* pl(void* p) { return static_cast<P*>(p); }
 int64_t round_to(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
+
+// Plain (unswizzled) FP32 2-D tensor map for the streamed bandwidth kernels: `inner` contiguous
+// elements per line, `outer` lines row_bytes apart, boxes of box_inner x box_outer elements;
+// elements outside the extents read as zero.
+bool tmap_f32_plain(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t outer,
+                    uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides,
+                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
 
 bool tc_available() { return true; }
 
