@@ -290,6 +290,24 @@ cqr_status coded_qr_set_wait_limit(cqr_handle h, int64_t cycles);
 cqr_status coded_qr_debug_bounds(int32_t* site);
 cqr_status coded_qr_debug_bounds_selftest(void* stream);
 
+/* Exchange-latency probe (a measurement aid: the paper has no counterpart).  The panel of
+ * Appendix A's Algorithm CGS (right-looking, with the ICGS criterion) performs one reduction
+ * across its CTAs per column; with everything else on chip, those reductions bound how fast a
+ * column can go.  This call runs the reductions of one M x bk FP32 panel -- a first one of
+ * 2 bk entries, then bk - 1 - j entries for column j -- with the panel kernel's own exchange
+ * code, launch shape and shared-memory footprint but no column arithmetic, `reps` times in one
+ * launch after a one-launch warm-up, and stores the mean device time per panel column in
+ * microseconds (CUDA events on `stream`; the call synchronises the stream).
+ *   kind 0: the register panel (one cluster; bk <= 128 and M within its registers);
+ *   kind 1: the shared-memory panel as the handle plans it for M rows (one cluster of up to
+ *           16 CTAs, the two-level exchange over clusters of 8, or the grid barrier).
+ * It allocates its scratch with cudaMalloc and frees it.  Returns CQR_EINVAL when the panel does
+ * not fit the chosen kind (or its slices would not be in shared memory), the device status
+ * (CQR_ETIMEOUT) when an exchange wait ran out, CQR_ECUDA when a sum came back wrong or a CUDA
+ * call failed. */
+cqr_status coded_qr_probe_exchange(int32_t kind, int64_t M, int32_t bk, int32_t reps,
+                                   double* us_per_column, void* stream);
+
 /* Profile of the library's own kernels (instrumentation, no counterpart in the paper).
  * Launch counts per kernel class are always kept; with enable != 0 every launch site is
  * also bracketed by a pair of CUDA events on the stream its launches go to (cfg.stream, or

@@ -46,7 +46,7 @@ EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "
            "coded_qr_batched_sync_status", "coded_qr_batched_last_error",
            "coded_qr_adjoint_qr", "coded_qr_adjoint_lstsq", "coded_qr_mds_stats",
            "coded_qr_inject_node_failure", "coded_qr_set_wait_limit", "coded_qr_debug_bounds",
-           "coded_qr_debug_bounds_selftest"]
+           "coded_qr_debug_bounds_selftest", "coded_qr_probe_exchange"]
 CQR_BATCH_GRAPH, CQR_BATCH_POST_ORTH = 1, 2
 PROF_CLASSES = 17
 
@@ -105,6 +105,7 @@ def lib():
             "coded_qr_set_wait_limit": [vp, i64],
             "coded_qr_debug_bounds": [C.POINTER(i32)],
             "coded_qr_debug_bounds_selftest": [vp],
+            "coded_qr_probe_exchange": [i32, i64, i32, i32, C.POINTER(C.c_double), vp],
             "coded_qr_profile": [vp, i32],
             "coded_qr_profile_read": [vp, C.POINTER(C.c_double), C.POINTER(i64), i32, i32],
             "coded_qr_panel_icgs_noalloc": [i32, i64, i32, vp, i64, vp, i64, C.c_double, vp, vp],
@@ -704,6 +705,16 @@ def debug_bounds():
     site = C.c_int32(0)
     st = lib().coded_qr_debug_bounds(C.byref(site))
     return st, site.value
+
+
+def probe_exchange(kind, M, bk, reps=8, stream=None):
+    """Mean device time per panel column (microseconds) of the per-column reductions alone, for
+    an M x bk FP32 panel: kind 0 the register panel, 1 the shared-memory panel
+    (coded_qr_probe_exchange)."""
+    us = C.c_double(0.0)
+    check(lib().coded_qr_probe_exchange(kind, M, bk, reps, C.byref(us), C.c_void_p(stream)),
+          "coded_qr_probe_exchange")
+    return us.value
 
 
 def debug_bounds_selftest(stream=None):

@@ -1187,6 +1187,65 @@ cqr_status coded_qr_debug_bounds_selftest(void* stream) {
 #endif
 }
 
+cqr_status coded_qr_probe_exchange(int32_t kind, int64_t M, int32_t bk, int32_t reps,
+                                   double* us_per_column, void* stream) {
+  if (!us_per_column || M < 1 || bk < 1 || bk > 256 || reps < 1 || (kind != 0 && kind != 1))
+    return CQR_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PanelPlan pp{};
+  if (kind == 0) {
+    int rpl = 0, cpw = 0, G = 0;
+    if (!plan_panel_reg(M, bk, &rpl, &cpw, &G) || !panel_reg_cluster_fits(rpl, cpw, G))
+      return CQR_EINVAL;
+  } else {
+    // the plan the handle's panel step takes for an FP32 panel of M rows (ensure_panel_plan)
+    pp = plan_panel(M, bk, sizeof(float), sms, true);
+    if (pp.cluster && !panel_cluster_fits<float>(pp)) pp = plan_panel(M, bk, sizeof(float), sms, false);
+    if (pp.hier && !panel_hier_fits<float>(pp))
+      pp = plan_panel(M, bk, sizeof(float), sms, pp.cluster != 0, false);
+    if (!pp.smem) return CQR_EINVAL;  // slices in global memory: no exchange-only floor
+  }
+  const size_t part_bytes = align256(panel_partial_bytes(bk, sizeof(float), sms));
+  unsigned char* ws = nullptr;
+  CK(cudaMalloc(&ws, part_bytes + 256));
+  float* part = reinterpret_cast<float*>(ws);
+  unsigned* bar = reinterpret_cast<unsigned*>(ws + part_bytes);
+  int* status = reinterpret_cast<int*>(ws + part_bytes + 64);
+  int* bad = reinterpret_cast<int*>(ws + part_bytes + 128);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMemsetAsync(ws, 0, part_bytes + 256, st);
+  auto launch = [&](int r) {
+    return kind == 0 ? launch_exchange_probe_reg(M, bk, r, status, bad, st)
+                     : launch_exchange_probe(pp, bk, r, part, bar, status, bad, st);
+  };
+  if (e == cudaSuccess) e = launch(1);  // warm-up
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) e = launch(reps);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  int hs[4] = {0, 0, 0, 0}, hbad = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(hs, status, sizeof(hs), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(ws);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return CQR_ECUDA;
+  }
+  if (hs[0] != 0) return (cqr_status)hs[0];
+  if (hbad != 0) return CQR_ECUDA;
+  *us_per_column = 1000.0 * ms / ((double)reps * bk);
+  return CQR_OK;
+}
+
 cqr_status coded_qr_set_wait_limit(cqr_handle h, int64_t cycles) {
   if (!h || cycles < 0) return CQR_EINVAL;
   h->wait_limit = (long long)cycles;

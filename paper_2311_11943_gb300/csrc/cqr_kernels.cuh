@@ -90,6 +90,16 @@ cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t l
                          int bk, double tau, T* part, unsigned* bar, int* status, int col0,
                          cudaStream_t st, int variant = 0, long long wait_limit = 0);
 
+// Exchange probes (measurement aids): `reps` times the per-column reductions of a panel of
+// bk FP32 columns, without the column arithmetic, with the exchange code, launch shape and
+// shared memory of the shared-memory panel on plan pp (cqr_panel.cu) or of the register panel
+// for M rows (cqr_panel_reg.cu); *bad counts sums that came back wrong.  part, bar: the
+// panel's partial buffer (panel_partial_bytes) and barrier counter.
+cudaError_t launch_exchange_probe(const PanelPlan& pp, int bk, int reps, float* part,
+                                  unsigned* bar, int* status, int* bad, cudaStream_t st);
+cudaError_t launch_exchange_probe_reg(int64_t M, int bk, int reps, int* status, int* bad,
+                                      cudaStream_t st);
+
 // Rbar partials: P[s] (bk x w, col-major) = Qbar^T Qtrail over K-split s.
 template <typename T>
 cudaError_t launch_gemm_tn_splitk(const T* A, int64_t lda, const T* B, int64_t ldb, int64_t K,

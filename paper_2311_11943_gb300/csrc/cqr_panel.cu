@@ -759,6 +759,77 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_cgs(T* __restrict__ Q, int64_t
   if (CL) cluster_sync_all();  // peers may still read this CTA's partials
 }
 
+// Latency floor of k_panel's per-column exchange (a measurement aid; the paper has no
+// counterpart): the reductions one panel of bk FP32 columns performs -- the first one of 2 pld
+// entries, then entries j+1 .. bk-1 for j = 0 .. bk-2 -- `reps` times, through the same
+// sync_reduce with the same launch shape and shared-memory footprint, and no column
+// arithmetic around them.  Each CTA's partial of entry a is a + 1, so every sum must come
+// back as G (a + 1) exactly; *bad counts the entries that did not.
+template <bool CL, bool HIER>
+__global__ void __launch_bounds__(kNT, 1) k_exchange_probe(int bk, int reps, float* gpart,
+                                                           unsigned* bar, int* status, int* bad,
+                                                           long long wait_limit) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int g = blockIdx.x, tid = threadIdx.x;
+  const int pld = (bk + 3) / 4 * 4;
+  float* v = reinterpret_cast<float*>(smraw);
+  float* sv = v + 2 * pld;
+  Ctx<float> c;
+  c.base = nullptr;
+  c.cs = 0;
+  c.nr = 0;
+  c.pld = pld;
+  c.gpart = gpart;
+  c.red = sv + 2 * pld;
+  c.lpart = c.red + (CL ? 0 : 8 * 2 * pld);
+  c.rbuf = c.red;
+  c.mbar = reinterpret_cast<uint64_t*>(c.lpart + 4 * pld);
+  c.bar = bar;
+  c.status = status;
+  c.target = 0;
+  c.phases = 0u;
+  c.crank = g % kHierCS;
+  c.cl = g / kHierCS;
+  c.ncl = gridDim.x / kHierCS;
+  c.wait_limit = wait_limit;
+  if (HIER) {
+    unsigned ncta;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
+    if (ncta != (unsigned)kHierCS || gridDim.x % kHierCS != 0) {
+      if (g == 0 && tid == 0) set_status(status, CQR_ECUDA, 51);
+      return;
+    }
+    if (tid == 0) {
+      mbar_init(c.mbar, 1);
+      mbar_init(c.mbar + 1, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cluster_sync_all();
+  }
+  const float G = (float)gridDim.x;
+  int wrong = 0, step = 0;
+  bool ok = true;
+  for (int rep = 0; rep < reps && ok; ++rep)
+    for (int j = -1; j < bk - 1 && ok; ++j) {
+      const int lo = j < 0 ? 0 : j + 1, hi = j < 0 ? 2 * pld : bk;
+      for (int a = lo + tid; a < hi; a += kNT)
+        put_partial<float, CL || HIER>(c, a, (float)(a + 1), step);
+      ok = sync_reduce<float, CL, HIER>(c, lo, hi, v, step++, 70);
+      if (ok)
+        for (int a = lo + tid; a < hi; a += kNT) wrong += v[a] != G * (float)(a + 1);
+      __syncthreads();  // v is read before the next step overwrites it
+    }
+  if (wrong) atomicAdd(bad, wrong);
+  if (CL || HIER) {
+    cluster_sync_all();  // peers may still read this CTA's partials or push into it
+    if (!ok) {
+      const long long t0 = clock64();
+      while (clock64() - t0 < kDrainCycles) {
+      }
+    }
+  }
+}
+
 size_t small_bytes(int bk, size_t elem, bool cl, bool hier = false) {
   const int pld = (bk + 3) / 4 * 4;
   // v (2 pld, includes eta), sv (2 pld), then either red [8][2 pld] or lpart [2][2 pld];
@@ -1050,6 +1121,45 @@ template bool panel_cluster_fits<double>(const PanelPlan&);
 template bool panel_hier_fits<float>(const PanelPlan&);
 template bool panel_hier_fits<double>(const PanelPlan&);
 
+// One launch of the exchange probe on the plan of a panel (the same grid, clusters and dynamic
+// shared memory as launch_panel; the tagged rows and the barrier counter cleared first).
+cudaError_t launch_exchange_probe(const PanelPlan& pp, int bk, int reps, float* part,
+                                  unsigned* bar, int* status, int* bad, cudaStream_t st) {
+  const void* fn = pp.hier      ? (const void*)k_exchange_probe<false, true>
+                   : pp.cluster ? (const void*)k_exchange_probe<true, false>
+                                : (const void*)k_exchange_probe<false, false>;
+  const int pld = (bk + 3) / 4 * 4;
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess && pp.hier) {
+    const size_t row = (size_t)2 * pld * sizeof(float);
+    e = cudaMemsetAsync(reinterpret_cast<char*>(part) + (size_t)pp.G * row, 0,
+                        (size_t)2 * (pp.G / kHierCS) * row, st);
+  }
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp.smem_bytes);
+  if (e == cudaSuccess && pp.cluster && pp.G > 8)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  long long wl = kWaitLimitCycles;
+  void* args[] = {&bk, &reps, &part, &bar, &status, &bad, &wl};
+  if (pp.hier || pp.cluster) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(pp.G);
+    cfg.blockDim = dim3(kNT);
+    cfg.dynamicSmemBytes = pp.smem_bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = pp.hier ? kHierCS : pp.G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+  }
+  return cudaLaunchCooperativeKernel(fn, dim3(pp.G), dim3(kNT), args, pp.smem_bytes, st);
+}
+
 cudaError_t bounds_take_panel(int* code, int* site) { return bounds_take_here(code, site); }
 
 }  // namespace cqr
@@ -1058,8 +1168,9 @@ cudaError_t bounds_take_panel(int* code, int* site) { return bounds_take_here(co
 // Allocation-free panel factorisation (coded_qr_panel_icgs_noalloc in coded_qr.h).
 //
 // Some callers cannot allocate device memory at the point where they need one panel
-// factored: code running inside a CUDA graph capture, a custom allocator that must not be
-// re-entered, or a host that has handed all device memory to another framework.  For them
+// factored: a caching allocator that must not be re-entered from its own callbacks, a host
+// that has handed all device memory to another framework, or a latency-critical path that
+// must not take the driver's allocation lock.  For them
 // the grid-barrier panel kernel above runs with its scratch (per-CTA partial sums, the
 // barrier counter and the status word) in the file-scope device array below instead of a
 // handle's workspace.  Every GPU that loads the library keeps this array until exit.

@@ -105,6 +105,59 @@ __device__ __forceinline__ int lanes_per_slot() {
   return 32 / CPW;
 }
 
+// The cluster exchange of the partial vectors, shared by k_panel_reg and the exchange probe.
+// Entries lo .. hi-1 (whole 4-entry chunks) of this CTA's partial vector lpart[par] go into
+// receive buffer [par][g] of every CTA of the cluster (16-byte st.async that count their bytes
+// on the receiver's mbarrier); then the wait for all G vectors.  The wait is bounded by
+// wait_limit cycles; when it runs out, the CTA records CQR_ETIMEOUT and returns false, and a
+// CTA whose wait is long overdue also gives up once any CTA has recorded an error.  The result
+// is the same in every thread of the CTA.  phases: bit p is the phase parity of mbarrier p.
+__device__ __forceinline__ bool reg_exchange(const float* lpart, float* rbuf, uint64_t* mbar,
+                                             unsigned& phases, int par, int lo, int hi,
+                                             long long wait_limit, int* status) {
+  const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, warp = tid >> 5;
+  const int c0 = lo / 4, nch = (hi + 3) / 4 - c0;
+  __syncthreads();  // this CTA's partials are complete
+  if (tid == 0) mbar_expect(mbar + par, (unsigned)(G * nch * 16));
+  const uint32_t dst0 = saddr(rbuf + ((size_t)par * kMaxG + g) * 512);
+  const uint32_t bar0 = saddr(mbar + par);
+  if (nch <= 32) {
+    // lane l sends chunk c0 + l to the peers warp, warp + 8 (one float4 read, G <= 16)
+    const int l = tid & 31;
+    if (l < nch) {
+      const float4 x = *reinterpret_cast<const float4*>(lpart + par * 512 + 4 * (c0 + l));
+      for (int peer = warp; peer < G; peer += kNW)
+        st_async4(peer_addr(dst0, peer) + 16u * (c0 + l), x, peer_addr(bar0, peer));
+    }
+  } else {
+    for (int it = tid; it < G * nch; it += kNT) {
+      const int peer = it / nch, ch = c0 + it % nch;
+      const float4 x = *reinterpret_cast<const float4*>(lpart + par * 512 + 4 * ch);
+      st_async4(peer_addr(dst0, peer) + 16u * ch, x, peer_addr(bar0, peer));
+    }
+  }
+  const bool ok = mbar_wait_bounded(mbar + par, (phases >> par) & 1u, wait_limit, status, 40);
+  phases ^= 1u << par;
+  return __syncthreads_and(ok) != 0;
+}
+
+// out[a] (lo <= a < hi) = sum over the G CTAs of their partial vectors in receive buffer par,
+// a fixed-shape tree over kMaxG senders (absent ones add zero): the same order in every CTA.
+__device__ __forceinline__ void reg_gather(const float* rbuf, int par, int lo, int hi, float* out) {
+  const int G = gridDim.x;
+  const float* rb = rbuf + (size_t)par * kMaxG * 512;
+  for (int a = lo + (int)threadIdx.x; a < hi; a += kNT) {
+    float x[kMaxG];
+#pragma unroll
+    for (int q = 0; q < kMaxG; ++q) x[q] = q < G ? rb[q * 512 + a] : 0.f;
+#pragma unroll
+    for (int w = kMaxG / 2; w > 0; w /= 2)
+#pragma unroll
+      for (int q = 0; q < w; ++q) x[q] += x[q + w];
+    out[a] = x[0];
+  }
+}
+
 template <int RPL, int CPW>
 __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int64_t ldq,
                                                        float* __restrict__ R, int64_t ldr,
@@ -177,53 +230,14 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
   auto push = [&](float s, int par, int base, bool active_slot, int a) {
     if (active_slot && sub == 0) lpart[par * 512 + base + a] = s;
   };
-  // exchange of the partial vectors, entries lo .. hi-1 (whole 4-entry chunks): this CTA's
-  // chunks go into receive buffer [par][g] of every CTA; then the wait for all G vectors.
-  // The wait is bounded by wait_limit cycles; when it runs out, the CTA records CQR_ETIMEOUT
-  // and returns false, and a CTA whose wait is long overdue also gives up once any CTA has
-  // recorded an error: every CTA then leaves the column loop (the decision is uniform within
-  // a CTA) and meets the others at the kernel's final cluster barrier.
+  // exchange and gather (reg_exchange, reg_gather): when an exchange gives up, every CTA
+  // leaves the column loop (the decision is uniform within a CTA) and meets the others at the
+  // kernel's final cluster barrier
   unsigned phases = 0u;  // bit p: the phase parity of mbarrier p
   auto exchange = [&](int par, int lo, int hi) -> bool {
-    const int c0 = lo / 4, nch = (hi + 3) / 4 - c0;
-    __syncthreads();  // this CTA's partials are complete
-    if (tid == 0) mbar_expect(mbar + par, (unsigned)(G * nch * 16));
-    const uint32_t dst0 = saddr(rbuf + ((size_t)par * kMaxG + g) * 512);
-    const uint32_t bar0 = saddr(mbar + par);
-    if (nch <= 32) {
-      // lane l sends chunk c0 + l to the peers warp, warp + 8 (one float4 read, G <= 16)
-      const int l = tid & 31;
-      if (l < nch) {
-        const float4 x = *reinterpret_cast<const float4*>(lpart + par * 512 + 4 * (c0 + l));
-        for (int peer = warp; peer < G; peer += kNW)
-          st_async4(peer_addr(dst0, peer) + 16u * (c0 + l), x, peer_addr(bar0, peer));
-      }
-    } else {
-      for (int it = tid; it < G * nch; it += kNT) {
-        const int peer = it / nch, ch = c0 + it % nch;
-        const float4 x = *reinterpret_cast<const float4*>(lpart + par * 512 + 4 * ch);
-        st_async4(peer_addr(dst0, peer) + 16u * ch, x, peer_addr(bar0, peer));
-      }
-    }
-    const bool ok = mbar_wait_bounded(mbar + par, (phases >> par) & 1u, wait_limit, status, 40);
-    phases ^= 1u << par;
-    return __syncthreads_and(ok) != 0;
+    return reg_exchange(lpart, rbuf, mbar, phases, par, lo, hi, wait_limit, status);
   };
-  // out[a] (lo <= a < hi) = sum over the G CTAs of their partial vectors, in a fixed order
-  auto gather = [&](int par, int lo, int hi, float* out) {
-    const float* rb = rbuf + (size_t)par * kMaxG * 512;
-    for (int a = lo + tid; a < hi; a += kNT) {
-      // fixed-shape tree over kMaxG senders (absent ones add zero)
-      float x[kMaxG];
-#pragma unroll
-      for (int q = 0; q < kMaxG; ++q) x[q] = q < G ? rb[q * 512 + a] : 0.f;
-#pragma unroll
-      for (int w = kMaxG / 2; w > 0; w /= 2)
-#pragma unroll
-        for (int q = 0; q < w; ++q) x[q] += x[q + w];
-      out[a] = x[0];
-    }
-  };
+  auto gather = [&](int par, int lo, int hi, float* out) { reg_gather(rbuf, par, lo, hi, out); };
 
   int par = 0;
   // ---- step 0: v_a = p_a^T p_0, eta_a = p_a^T p_a
@@ -454,6 +468,53 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
   }
 }
 
+// Latency floor of k_panel_reg's per-column exchange (a measurement aid; the paper has no
+// counterpart): the exchanges one panel of bk columns performs -- the first one of 256 + bk
+// entries, then entries j+1 .. bk-1 for j = 0 .. bk-2 -- `reps` times, through the same
+// reg_exchange and reg_gather with the panel's launch shape and shared-memory footprint, and
+// no column arithmetic.  Each CTA's partial of entry a is a + 1, so every sum must come back
+// as G (a + 1) exactly; *bad counts the entries that did not.
+__global__ void __launch_bounds__(kNT, 1) k_exchange_probe_reg(int bk, int reps, int rpc,
+                                                               int* status, int* bad,
+                                                               long long wait_limit) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* lpart = reinterpret_cast<float*>(smraw) + 4 * (size_t)rpc;  // the panel's layout
+  float* rbuf = lpart + 2 * 512;
+  float* v = rbuf + 2 * kMaxG * 512;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(v + 512 + 256 + (size_t)kNW * rpc);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    mbar_init(mbar + 1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  cl_sync();
+  const float G = (float)gridDim.x;
+  unsigned phases = 0u;
+  int par = 0, wrong = 0;
+  bool ok = true;
+  for (int rep = 0; rep < reps && ok; ++rep)
+    for (int j = -1; j < bk - 1 && ok; ++j) {
+      const int lo = j < 0 ? 0 : j + 1, hi = j < 0 ? 256 + bk : bk;
+      for (int a = lo + tid; a < hi; a += kNT) lpart[par * 512 + a] = (float)(a + 1);
+      ok = reg_exchange(lpart, rbuf, mbar, phases, par, lo, hi, wait_limit, status);
+      if (ok) {
+        reg_gather(rbuf, par, lo, hi, v);
+        __syncthreads();
+        for (int a = lo + tid; a < hi; a += kNT) wrong += v[a] != G * (float)(a + 1);
+      }
+      __syncthreads();
+      par ^= 1;
+    }
+  if (wrong) atomicAdd(bad, wrong);
+  cl_sync();  // uniform end
+  if (!ok) {
+    const long long t0 = clock64();
+    while (clock64() - t0 < kDrainCycles) {
+    }
+  }
+}
+
 size_t reg_smem_bytes(int rpl) {
   const size_t rpc = 32 * (size_t)rpl;
   return (4 * rpc + 2 * 512 + 2 * (size_t)kMaxG * 512 + 512 + 256 + (size_t)kNW * rpc) * sizeof(float) +
@@ -552,6 +613,37 @@ bool panel_reg_cluster_fits(int rpl, int cpw, int G) {
     return false;
   }
   return n >= 1;
+}
+
+// One launch of the register-panel exchange probe for a panel of M rows and bk columns (the
+// register panel's plan: its cluster of G CTAs and its shared-memory footprint).
+cudaError_t launch_exchange_probe_reg(int64_t M, int bk, int reps, int* status, int* bad,
+                                      cudaStream_t st) {
+  int rpl = 0, cpw = 0, G = 0;
+  if (!plan_panel_reg(M, bk, &rpl, &cpw, &G) || !panel_reg_cluster_fits(rpl, cpw, G))
+    return cudaErrorInvalidValue;
+  const void* fn = (const void*)k_exchange_probe_reg;
+  const size_t smem = reg_smem_bytes(rpl);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && G > 8)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  int rpc = 32 * rpl;
+  long long wl = kWaitLimitCycles;
+  void* args[] = {&bk, &reps, &rpc, &status, &bad, &wl};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(kNT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = G;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 cudaError_t bounds_take_panel_reg(int* code, int* site) { return bounds_take_here(code, site); }

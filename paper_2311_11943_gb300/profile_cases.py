@@ -7,6 +7,7 @@ library's public API.  Each case runs twice (the first run warms up the handle).
   python -m paper_2311_11943_gb300.profile_cases adjoint    # 8192 x 1024: forward + both adjoints
   python -m paper_2311_11943_gb300.profile_cases bandwidth8192  # encode / decode / post-orth
   python -m paper_2311_11943_gb300.profile_cases c3_tall    # the 16384^2 workload's panel shape
+  python -m paper_2311_11943_gb300.profile_cases exchange_floor  # per-column exchange floor
 
 Launch order per run (for ncu's --launch-skip; filter by kernel name with -k, as the commands
 in profiles/ do, since two streams interleave):
@@ -135,8 +136,48 @@ def case_c3_tall(panels=2):
     q.close()
 
 
+def case_exchange_floor(reps=8):
+    """The latency floor of the panel's per-column reduction (coded_qr_probe_exchange) beside
+    the panel's own time per column, for the panels of the 4096^2 workload (5120 x 128, the
+    register panel in one cluster) and of the 16384^2 workload (20480 x 256, the shared-memory
+    panel with the two-level exchange).  The panel time comes from the handle's event profile
+    over factor(0, 4), after a warm-up run; one JSON line per panel."""
+    import json
+
+    import torch
+    from . import binding as B
+    from . import synth
+    rows = []
+    for (m, n, p, f, b, kind, name) in [(4096, 4096, 8, 2, 128, 0, "5120x128 register panel"),
+                                        (16384, 8192, 16, 4, 256, 1,
+                                         "20480x256 two-level shared-memory panel")]:
+        M = m + f * (m // p)
+        floor = B.probe_exchange(kind, M, b, reps)
+        A = _cm(torch, B, synth.gaussian(m, n, 3, dtype=np.float32))
+        q = B.CodedQR(m, n, p, p, f, b, dtype="f32", mma="3xtf32", seed=3, reorth_block=True)
+        q.encode(A)
+        q.factor(0, 4)
+        q.profile(True)
+        q.profile_read(reset=True)
+        q.encode(A)
+        q.factor(0, 4)
+        torch.cuda.synchronize()
+        ms, launches = q.profile_read(reset=True)["panel_icgs"]
+        assert q.sync_status() == 0
+        q.close()
+        per_col = 1000.0 * ms / max(1, launches * b)
+        rows.append({"panel": name, "rows": M, "columns": b,
+                     "exchange_floor_us_per_column": floor,
+                     "panel_us_per_column": per_col,
+                     "panel_launches": launches,
+                     "floor_share": floor / per_col if per_col > 0 else None})
+    for r in rows:
+        print(json.dumps(r))
+
+
 CASES = {"tc_c2": case_c2, "panel_c2": case_c2, "bfactor64": case_bfactor, "adjoint": case_adjoint,
-         "bandwidth8192": case_bandwidth, "c3_tall": case_c3_tall}
+         "bandwidth8192": case_bandwidth, "c3_tall": case_c3_tall,
+         "exchange_floor": case_exchange_floor}
 
 if __name__ == "__main__":
     CASES[sys.argv[1]]()

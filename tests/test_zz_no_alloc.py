@@ -1,6 +1,6 @@
 """coded_qr_panel_icgs_noalloc: the panel factorisation for callers that cannot allocate device
-memory (work recorded into a CUDA graph, allocators that must not be re-entered, hosts that
-gave all device memory to another framework).  Its scratch is a fixed array inside the
+memory (caching allocators that must not be re-entered, hosts that gave all device memory to
+another framework, latency-critical paths that must not take the allocation lock).  Its scratch is a fixed array inside the
 library, so these tests check that two calls in a row -- the second one seeing the array as
 the first left it -- give the same panel as the allocating path (coded_qr_factor's first
 panel step), within the parity tolerance of the other GPU tests.  This file is collected last.
