@@ -30,20 +30,13 @@ struct DecodeScratch {
   int bad;
 };
 
-struct NoTileHook {
-  __device__ void operator()() const {}
-};
-
 // Every thread of the CTA (nthr threads, index tid) calls it; false when G^ is singular (then
-// status gets CQR_EUNRECOVERABLE when report is set).  Thread 0 calls on_tiles() as soon as the
-// list of code tiles to read (tuse, nuse) is known, before the inversion, so that a caller can
-// start fetching them.
-template <typename T, typename Hook = NoTileHook>
+// status gets CQR_EUNRECOVERABLE when report is set).
+template <typename T>
 __device__ __forceinline__ bool decode_setup(const Geo& g, const DecodePlan& p,
                                              const double* __restrict__ Gt,
                                              const double* __restrict__ Gh, DecodeScratch<T>& sh,
-                                             int tid, int nthr, int* status, bool report,
-                                             Hook on_tiles = Hook()) {
+                                             int tid, int nthr, int* status, bool report) {
   const bool isQ = (p.kind == 0);
   const int nsys = p.nsys, f = g.f, f1 = p.f1, f2 = p.f2;
   auto gen = [&](int i, int t) -> double { return isQ ? Gt[i * g.p_r + t] : Gh[t * f + i]; };
@@ -61,7 +54,6 @@ __device__ __forceinline__ bool decode_setup(const Geo& g, const DecodePlan& p,
       if (used) sh.tuse[nu++] = t;
     }
     sh.nuse = nu;
-    on_tiles();
     // G^ = G~[C_use, A_fail]; invert by Gauss-Jordan (Golub & Van Loan 3.4), FP64
     for (int r = 0; r < f1; ++r)
       for (int q = 0; q < 2 * f1; ++q)
@@ -180,7 +172,7 @@ __device__ __forceinline__ void decode_apply(const Geo& g, const DecodePlan& p,
 // code tile tuse[u] at the position; the rebuilt tiles are stored through ptr (tile k at
 // ptr + k * tstride, 16-byte aligned).  Every element is summed in the same order as
 // decode_apply, so the result has the same bits whatever supplies the values.
-template <typename Fetch>
+template <int UG = 4, typename Fetch>
 __device__ __forceinline__ void decode_combine4(const DecodePlan& p,
                                                 const DecodeScratch<float>& sh, float* ptr,
                                                 int64_t tstride, Fetch fetch) {
@@ -208,16 +200,16 @@ __device__ __forceinline__ void decode_combine4(const DecodePlan& p,
         if (e < f2) fma4(ce[e], sh.cenc[e][t], val);
     }
   };
-  for (int u0 = 0; u0 < sh.nuse; u0 += 4) {
-    int tt[4];
-    float4 v[4];
+  for (int u0 = 0; u0 < sh.nuse; u0 += UG) {  // UG tile loads in flight
+    int tt[UG];
+    float4 v[UG];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < UG; ++k) {
       tt[k] = (u0 + k < sh.nuse) ? sh.tuse[u0 + k] : -1;
       v[k] = tt[k] >= 0 ? fetch(u0 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < UG; ++k)
       if (tt[k] >= 0) add(tt[k], v[k]);
   }
 #pragma unroll
@@ -234,7 +226,8 @@ __device__ __forceinline__ void decode_combine4(const DecodePlan& p,
 }
 
 // Four consecutive rows r4 .. r4+3 of position column s in one thread, FP32, with 16-byte
-// loads and stores (a warp reads 512 contiguous bytes of each code tile); f <= 4.  The
+// loads and stores (a warp reads 512 contiguous bytes of each code tile, eight tiles in
+// flight); f <= 4.  The
 // caller guarantees 16-byte alignment: the tile height and the leading dimension are
 // multiples of four and r4 is.
 __device__ __forceinline__ void decode_apply4(const Geo& g, const DecodePlan& p,
@@ -245,7 +238,7 @@ __device__ __forceinline__ void decode_apply4(const Geo& g, const DecodePlan& p,
   const int64_t tstride = isQ ? g.mb : g.nb * g.ldr;
   const int64_t ld = isQ ? g.ldq : g.ldr;
   float* ptr = base + r4 + s * ld;
-  decode_combine4(p, sh, ptr, tstride, [&](int u) {
+  decode_combine4<8>(p, sh, ptr, tstride, [&](int u) {
     return *reinterpret_cast<const float4*>(ptr + (int64_t)sh.tuse[u] * tstride);
   });
 }

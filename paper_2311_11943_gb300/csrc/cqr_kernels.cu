@@ -271,8 +271,8 @@ cudaError_t launch_encode_f(const Geo& g, const T* A, int64_t lda, const T* Gt, 
                             cudaStream_t st) {
   if constexpr (F > 0) {
     if (g.protect_r && g.p_c <= 16) {
-      dim3 blk(32, 4, 2);
       dim3 grd((unsigned)((g.mb + 31) / 32), (unsigned)((g.nb + 1) / 2));
+      dim3 blk(32, 4, 2);
       k_encode_fused<T, F><<<grd, blk, 0, st>>>(g, A, lda, Gt, Gh, Q);
       return cudaGetLastError();
     }
@@ -290,13 +290,7 @@ cudaError_t launch_encode_f(const Geo& g, const T* A, int64_t lda, const T* Gt, 
 template <typename T>
 cudaError_t launch_encode(const Geo& g, const T* A, int64_t lda, const T* Gt, const T* Gh, T* Q,
                           int* status, cudaStream_t st) {
-  if constexpr (sizeof(T) == 4) {
-    const float* Af = reinterpret_cast<const float*>(A);
-    if (encode_tma_applies(g, Af, lda, reinterpret_cast<const float*>(Q)))
-      return launch_encode_tma(g, Af, lda, reinterpret_cast<const float*>(Gt),
-                               reinterpret_cast<const float*>(Gh), reinterpret_cast<float*>(Q),
-                               status, st);
-  }
+  (void)status;
   switch (f_bucket(g.f)) {
     case 0: return launch_encode_f<T, 0>(g, A, lda, Gt, Gh, Q, st);
     case 1: return launch_encode_f<T, 1>(g, A, lda, Gt, Gh, Q, st);
@@ -587,20 +581,25 @@ cudaError_t launch_decode(const Geo& g, const DecodePlan* plans_dev, int nplans,
   if (nplans == 0) return cudaSuccess;
   // about one wave (768 CTAs over all codes), so that each CTA's table setup is amortised
   // over several 8-column groups
-  if constexpr (sizeof(T) == 4) {
-    const int maxuse = std::max(g.p_r, g.p_c);  // tiles a code reads: its systematic count
-    float* Qf = reinterpret_cast<float*>(Q);
-    float* Rf = reinterpret_cast<float*>(R);
-    if (decode_tma_applies(g, Qf, Rf, maxuse))
-      return launch_decode_tma(g, plans_dev, nplans, maxuse, Gt, Gh, Qf, Rf, status, st);
-  }
   dim3 blk(32, 8);
   const int64_t nby = (g.nb + 7) / 8;
   if (sizeof(T) == 4 && g.f <= 4 && g.mb % 4 == 0 && g.nb % 4 == 0 && g.ldq % 4 == 0 &&
       g.ldr % 4 == 0) {
     // 16-byte accesses, four rows per thread: a block covers 128 rows
     const int64_t nbx = (max_h + 127) / 128;
-    const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(nby, 1216 / std::max<int64_t>(1, nbx * nplans)));
+    // one wave of resident CTAs over all codes, so that each CTA builds its tables once and
+    // then streams several 8-column groups
+    int occ = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_decode4, 256, 0) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      occ = 4;
+      sms = 152;
+    }
+    const int64_t resident = (int64_t)std::max(1, occ) * std::max(1, sms);
+    const int64_t gy = std::max<int64_t>(
+        1, std::min<int64_t>(nby, resident / std::max<int64_t>(1, nbx * nplans)));
     dim3 grd((unsigned)nbx, (unsigned)gy, (unsigned)nplans);
     k_decode4<<<grd, blk, 0, st>>>(g, plans_dev, Gt, Gh, reinterpret_cast<float*>(Q),
                                    reinterpret_cast<float*>(R), status);

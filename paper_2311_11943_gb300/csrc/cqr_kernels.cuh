@@ -40,20 +40,11 @@ template <typename T>
 cudaError_t launch_generator(int f, int p_r, int p_c, uint64_t seed, int gdist, double* Gt,
                              double* Gh, T* Gt_t, T* Gh_t, cudaStream_t st);
 
-// status: the device status word (the streamed FP32 encode records CQR_ETIMEOUT there).
+// status: the device status word (unused by the current encode kernels, which do not wait).
 template <typename T>
 cudaError_t launch_encode(const Geo& g, const T* A, int64_t lda, const T* Gt, const T* Gh, T* Q,
                           int* status, cudaStream_t st);
 
-// The TMA-streamed FP32 encode and decode (cqr_stream.cu); *_applies tells whether the
-// geometry and alignment allow them (the launchers above use them when they do).
-bool encode_tma_applies(const Geo& g, const float* A, int64_t lda, const float* Q);
-cudaError_t launch_encode_tma(const Geo& g, const float* A, int64_t lda, const float* Gt,
-                              const float* Gh, float* Q, int* status, cudaStream_t st);
-bool decode_tma_applies(const Geo& g, const float* Q, const float* R, int maxuse);
-cudaError_t launch_decode_tma(const Geo& g, const DecodePlan* plans_dev, int nplans, int maxuse,
-                              const double* Gt, const double* Gh, float* Q, float* R, int* status,
-                              cudaStream_t st);
 
 // allow_hier: a grid of more than 48 FP32 CTAs may use the two-level exchange (clusters of 8)
 PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_cluster,

@@ -789,22 +789,6 @@ int64_t round_to(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
-// Plain (unswizzled) FP32 2-D tensor map for the streamed bandwidth kernels: `inner` contiguous
-// elements per line, `outer` lines row_bytes apart, boxes of box_inner x box_outer elements;
-// elements outside the extents read as zero.
-bool tmap_f32_plain(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t outer,
-                    uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
-  if (!enc) return false;
-  cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {row_bytes};
-  cuuint32_t box[2] = {box_inner, box_outer};
-  cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides,
-                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
 
 bool tc_available() { return true; }
 

@@ -1,7 +1,6 @@
 // cqr_tc_gemm.cuh -- tensor-core (tcgen05, sm_103a) trailing update of PBMGS for FP32 storage:
 // TF32 or BF16 operands (one product, or hi/lo splits with three products), FP32 accumulation.
 #pragma once
-#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -11,11 +10,6 @@ namespace cqr {
 struct TcGemm;
 
 bool tc_available();
-// Plain (unswizzled) FP32 2-D tensor map: `inner` contiguous elements per line, `outer` lines
-// row_bytes apart (a multiple of 16), boxes box_inner x box_outer; out-of-range reads are zero.
-// false when the driver's encoder is missing or refuses the arguments.
-bool tmap_f32_plain(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t outer,
-                    uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);
 size_t tc_panel_bytes(int64_t M, int b);
 size_t tc_workspace_bytes(int mode, int64_t M, int64_t N, int64_t n, int b, int reorth_block);
 TcGemm* tc_create(int mode, int64_t M, int64_t N, int64_t n, int64_t b, float* Q, int64_t ldq,
