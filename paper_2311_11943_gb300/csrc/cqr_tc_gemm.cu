@@ -15,6 +15,9 @@
 //   warps 4-11  epilogue, two warps per quarter of the TMEM lanes: tcgen05.ld 32 lanes x 32
 //               columns per warp (alternate column chunks), then either store the FP32
 //               partial (GEMM1) or subtract it from Q in place (GEMM2)
+// A work unit is one 128 x 128 output tile, or, for GEMM1 in 3xTF32 with a 256-column panel,
+// the two vertically adjacent tiles of one B tile (two accumulators; B is loaded and split
+// once for both).
 // 3xTF32 (hi*hi + hi*lo + lo*hi) recovers about FP32 accuracy from TF32 products.  The small
 // operands (panel and Rbar) are split into hi/lo planes in global memory by helper kernels.
 // Every mbarrier wait is bounded: on expiry the kernel records CQR_ETIMEOUT, stops issuing,
@@ -24,6 +27,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -39,7 +43,9 @@ namespace {
 
 constexpr int BM = 128;       // UMMA M (TMEM lanes)
 constexpr int BN = 128;       // UMMA N (TMEM columns)
-constexpr int kTmemCols = 2 * BN;  // two accumulator buffers (power of two, <= 512)
+// TMEM columns: two accumulator buffers of MP 128 x 128 accumulators (a power of two, <= 512)
+template <int MP>
+constexpr int tmem_cols() { return 2 * MP * BN; }
 constexpr int kEpiWarps = 8;  // two per TMEM lane quarter, each draining half the columns
 constexpr int kThreads = 32 * (4 + kEpiWarps);
 constexpr int kMaxSplits = 16;
@@ -218,10 +224,11 @@ struct TcJob {
   int* status;
 };
 
-template <int STAGES, int NA, int NB>
+template <int STAGES, int NA, int NB, int MP = 1>
 struct Smem {
-  // per stage: NA A tiles then NB B tiles (each 1024-byte aligned, 16 KB)
-  static constexpr uint32_t kStageBytes = NA * kTileBytesA + NB * kTileBytesB;
+  // per stage: NA A tiles for each of the MP M tiles, then NB B tiles (each 1024-byte aligned,
+  // 16 KB)
+  static constexpr uint32_t kStageBytes = MP * NA * kTileBytesA + NB * kTileBytesB;
   static constexpr uint32_t kTiles = STAGES * kStageBytes;
   static constexpr uint32_t kTotal = kTiles + 1024 /*alignment*/ + 256 /*barriers*/;
   // full/ready/empty per stage, acc_full[2], acc_empty[2], TMEM slot, abort flag
@@ -235,10 +242,13 @@ struct Smem {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-template <bool BF, int STAGES, int NA, int NB>
+// MP = 2: a work unit is a pair of vertically adjacent M tiles on the same N tile (m_tiles
+// even): the B tile is loaded (and split) once for both, and two accumulators are formed.
+template <bool BF, int STAGES, int NA, int NB, int MP>
 __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__ TcMaps maps,
                                                           const TcJob job) {
-  using S = Smem<STAGES, NA, NB>;
+  using S = Smem<STAGES, NA, NB, MP>;
+  constexpr int kTmemCols = tmem_cols<MP>();
   constexpr int BK = Op<BF>::KE;
   constexpr int UMMA_K = Op<BF>::UK;
   extern __shared__ __align__(1024) unsigned char smraw[];
@@ -257,8 +267,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
   // the output tiles stay inside `out` (uniform over the launch: before any barrier or TMEM
   // allocation)
   CQR_CHECK(job.ldo >= job.mrows && (int64_t)job.m_tiles * BM >= job.mrows &&
-                (int64_t)job.n_tiles * BN >= job.ncols, 401);
-  const int total_tiles = job.m_tiles * job.n_tiles * job.splits;
+                (int64_t)job.n_tiles * BN >= job.ncols && job.m_tiles % MP == 0, 401);
+  const int mu = job.m_tiles / MP;  // work units along M
+  const int total_tiles = mu * job.n_tiles * job.splits;
   const int nkb_full = (int)(job.kchunk / BK);
 
   if (threadIdx.x == 0) {
@@ -305,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
       for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x) {
         const int split = t % job.splits;
         const int mn = t / job.splits;
-        const int mt = mn % job.m_tiles, nt = mn / job.m_tiles;
+        const int mt = (mn % mu) * MP, nt = mn / mu;  // first M tile of the unit
         const int nk = kblocks(split);
         const int64_t kbase = job.k0 + (int64_t)split * job.kchunk;
         if (job.prefetch_c) {
@@ -324,11 +335,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
           // raw FP32 B for the in-smem split: one 32-element box (TF32) or two (BF16: 64
           // elements of K, split in place into the BF16 hi and lo tiles)
           const int nb_load = job.split_b_smem ? (BF ? 2 : 1) : NB;
-          mbar_expect_tx(&full[s], NA * kTileBytesA + nb_load * kTileBytesB);
-          for (int p = 0; p < NA; ++p) tma_load_2d(st + p * kTileBytesA, &maps.a[p], x, ya, &full[s]);
+          mbar_expect_tx(&full[s], MP * NA * kTileBytesA + nb_load * kTileBytesB);
+#pragma unroll
+          for (int m = 0; m < MP; ++m)
+            for (int p = 0; p < NA; ++p)
+              tma_load_2d(st + (m * NA + p) * kTileBytesA, &maps.a[p], x, ya + m * BM, &full[s]);
           for (int p = 0; p < nb_load; ++p) {
             const bool raw = job.split_b_smem;
-            tma_load_2d(st + NA * kTileBytesA + p * kTileBytesB, raw ? &maps.b[0] : &maps.b[p],
+            tma_load_2d(st + MP * NA * kTileBytesA + p * kTileBytesB, raw ? &maps.b[0] : &maps.b[p],
                         raw ? x + 32 * p : x, yb, &full[s]);
           }
         }
@@ -346,9 +360,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
       for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x, ++tl) {
         const int split = t % job.splits;
         const int nk = kblocks(split);
-        // two accumulators: the epilogue drains tile tl-1 while tile tl accumulates
+        // two accumulator buffers: the epilogue drains unit tl-1 while unit tl accumulates;
+        // a buffer holds MP accumulators of BN columns
         const int buf = tl & 1;
-        const uint32_t acc = tmem + (uint32_t)(buf * BN);
+        const uint32_t acc = tmem + (uint32_t)(buf * MP * BN);
         if (!mbar_wait(&acc_empty[buf], ((tl >> 1) & 1) ^ 1, abort_flag)) break;
         tc_fence_after();
         bool ok = true;
@@ -358,16 +373,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
           if (!mbar_wait(gate, (it / STAGES) & 1, abort_flag)) { ok = false; break; }
           tc_fence_after();
           const uint32_t st = tiles_u + s * S::kStageBytes;
-          const uint32_t a_hi = st, a_lo = st + kTileBytesA;
-          const uint32_t b_hi = st + NA * kTileBytesA, b_lo = b_hi + kTileBytesB;
+          const uint32_t b_hi = st + MP * NA * kTileBytesA, b_lo = b_hi + kTileBytesB;
 #pragma unroll
           for (int ks = 0; ks < BK / UMMA_K; ++ks) {
             const uint32_t off = ks * 32;  // 32 bytes of K per instruction
             const uint32_t acc0 = (kb > 0 || ks > 0) ? 1u : 0u;
-            mma_op<BF>(acc, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
-            if (job.nprod == 3) {
-              mma_op<BF>(acc, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
-              mma_op<BF>(acc, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
+#pragma unroll
+            for (int m = 0; m < MP; ++m) {
+              const uint32_t am = acc + (uint32_t)(m * BN);
+              const uint32_t a_hi = st + m * NA * kTileBytesA, a_lo = a_hi + kTileBytesA;
+              mma_op<BF>(am, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
+              if (job.nprod == 3) {
+                mma_op<BF>(am, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
+                mma_op<BF>(am, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
+              }
             }
           }
           mma_commit(&empty[s]);
@@ -387,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = it % STAGES;
           if (!mbar_wait(&full[s], (it / STAGES) & 1, abort_flag)) { ok = false; break; }
-          float4* raw = reinterpret_cast<float4*>(tiles + s * S::kStageBytes + NA * kTileBytesA);
+          float4* raw = reinterpret_cast<float4*>(tiles + s * S::kStageBytes + MP * NA * kTileBytesA);
           float4* lo = raw + kTileBytesB / 16;
           if (!BF) {
             for (int e = tt; e < (int)(kTileBytesB / 16); e += 64) {
@@ -439,24 +458,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
   } else {
     // epilogue warps 4 .. 4+kEpiWarps-1: TMEM lanes 32 (warp % 4) .. +32 (a warp may only
     // read its own quarter of the lanes); the two warps of a quarter take alternate 32-column
-    // chunks, so twice as many loads of the output tile are in flight
+    // chunks (of each of the unit's MP accumulators), so twice as many loads of the output
+    // tile are in flight
     const int ew = warp & 3;
     const int half = (warp - 4) >> 2;
+    constexpr int kChunks = BN / 32;
     int tl = 0;
     for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x, ++tl) {
       const int split = t % job.splits;
       const int mn = t / job.splits;
-      const int mt = mn % job.m_tiles, nt = mn / job.m_tiles;
+      const int mt = (mn % mu) * MP, nt = mn / mu;
       const int buf = tl & 1;
       if (!mbar_wait(&acc_full[buf], (tl >> 1) & 1, abort_flag)) break;
       tc_fence_after();
-      const int64_t row = (int64_t)mt * BM + ew * 32 + lane;
-      const bool row_ok = row < job.mrows;
       const bool has_k = kblocks(split) > 0;
 #pragma unroll 1
-      for (int c = half; c < BN / 32; c += kEpiWarps / 4) {
+      for (int q = half; q < MP * kChunks; q += kEpiWarps / 4) {
+        const int m = q / kChunks, c = q % kChunks;
+        const int64_t row = (int64_t)(mt + m) * BM + ew * 32 + lane;
+        const bool row_ok = row < job.mrows;
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
+        tmem_ld32(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)((buf * MP + m) * BN + c * 32), v);
         if (!has_k)
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = 0.f;
@@ -754,29 +776,46 @@ cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-template <bool BF, int STAGES, int NA, int NB>
+template <bool BF, int STAGES, int NA, int NB, int MP = 1>
 cudaError_t launch_gemm(const TcMaps& maps, const TcJob& job, int max_ctas, cudaStream_t st, bool pdl) {
-  using S = Smem<STAGES, NA, NB>;
-  const void* fn = (const void*)k_tc_gemm<BF, STAGES, NA, NB>;
+  using S = Smem<STAGES, NA, NB, MP>;
+  const void* fn = (const void*)k_tc_gemm<BF, STAGES, NA, NB, MP>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kTotal);
   if (e != cudaSuccess) return e;
-  const int tiles = job.m_tiles * job.n_tiles * job.splits;
+  const int tiles = job.m_tiles / MP * job.n_tiles * job.splits;
   const int grid = std::max(1, std::min(tiles, max_ctas));
-  return launch_k(k_tc_gemm<BF, STAGES, NA, NB>, dim3(grid), dim3(kThreads), S::kTotal, st, pdl, maps, job);
+  return launch_k(k_tc_gemm<BF, STAGES, NA, NB, MP>, dim3(grid), dim3(kThreads), S::kTotal, st, pdl,
+                  maps, job);
+}
+
+// GEMM1-shaped launches (B raw and split in shared memory, 3xTF32) take pairs of M tiles when
+// the panel spans an even number of them (b = 256): the B tile is then loaded and split once
+// for both halves of the panel, which halves the B traffic into shared memory per flop.
+// CQR_GEMM_PAIR=0 keeps one M tile per work unit.
+bool pair_m_tiles(bool three, bool bf, bool split, int m_tiles) {
+  static const int env = [] {
+    const char* e = getenv("CQR_GEMM_PAIR");
+    return e ? atoi(e) : 1;
+  }();
+  return env != 0 && three && !bf && split && m_tiles % 2 == 0;
 }
 
 // One launch of the tensor-core kernel in the variant of the handle's mode.  split: B arrives
 // as raw FP32 and is split in shared memory (GEMM1 and the first block-reorthogonalisation
-// product); otherwise B comes from planes.  Stages: 3 x 64 KB (two products), 6 x 32 KB
-// (one product), 4 x 48 KB (BF16, one product, raw FP32 B of 64 K elements).
+// product); otherwise B comes from planes.  Stages: 3 x 64 KB (two products), 2 x 96 KB (two
+// products on pairs of M tiles), 6 x 32 KB (one product), 4 x 48 KB (BF16, one product, raw
+// FP32 B of 64 K elements).
 cudaError_t launch_mode(const TcGemm* t, bool split, const TcMaps& maps, const TcJob& job,
                         cudaStream_t st, int max_ctas = 0) {
   const bool three = t->nplanes == 2;
   const int mc = max_ctas > 0 ? std::min(max_ctas, t->num_sms) : t->num_sms;
   const bool pdl = st == t->pdl_st && st != nullptr;
-  if (!t->bf)
+  if (!t->bf) {
+    if (pair_m_tiles(three, false, split, job.m_tiles))
+      return launch_gemm<false, 2, 2, 2, 2>(maps, job, mc, st, pdl);
     return three ? launch_gemm<false, 3, 2, 2>(maps, job, mc, st, pdl)
                  : launch_gemm<false, 6, 1, 1>(maps, job, mc, st, pdl);
+  }
   if (three) return launch_gemm<true, 3, 2, 2>(maps, job, mc, st, pdl);
   return split ? launch_gemm<true, 4, 1, 2>(maps, job, mc, st, pdl)
                : launch_gemm<true, 6, 1, 1>(maps, job, mc, st, pdl);
@@ -917,7 +956,10 @@ int64_t best_kchunk(int64_t tiles, int64_t kblocks, int ctas, int max_splits) {
 int tc_splits(const TcGemm* t, int m1, int n1, int64_t* kchunk, int max_ctas = 0) {
   const int ctas = max_ctas > 0 ? std::min(max_ctas, t->num_sms) : t->num_sms;
   const int64_t kblocks = (t->M + t->KE - 1) / t->KE;
-  *kchunk = best_kchunk((int64_t)m1 * n1, kblocks, ctas, kMaxSplits) * t->KE;
+  // work units of the GEMM1-shaped launch (pairs of M tiles where launch_mode pairs them)
+  const bool three = t->nplanes == 2;
+  const int units_m = pair_m_tiles(three, t->bf, three || t->bf, m1) ? m1 / 2 : m1;
+  *kchunk = best_kchunk((int64_t)units_m * n1, kblocks, ctas, kMaxSplits) * t->KE;
   return (int)((t->M + *kchunk - 1) / *kchunk);
 }
 }  // namespace
