@@ -1068,11 +1068,21 @@ cqr_status coded_qr_run(cqr_handle h, const void* A, int64_t lda, const void* y,
   void* xd = x;
   int64_t ldxd = ldx;
   if (host) {
-    // host -> device: A straight into the systematic block of the encoded matrix (encode then
-    // runs in place), y into the handle's workspace; x comes back from the workspace.
-    CK(cudaMemcpy2DAsync(h->B.Q, g.ldq * es, A, lda * es, g.m * es, g.n, cudaMemcpyHostToDevice, h->st));
-    Ad = h->B.Q;
-    ldad = g.ldq;
+    // host -> device: A as one contiguous copy into the R buffer when it fits there (encode
+    // reads it before it clears R; one large copy instead of n rows of a pitched copy), else
+    // pitched straight into the systematic block of the encoded matrix (encode then runs in
+    // place); y into the handle's workspace; x comes back from the workspace.
+    const size_t a_bytes = (size_t)lda * (size_t)(g.n - 1) * es + (size_t)g.m * es;
+    if (a_bytes <= (size_t)g.ldr * (size_t)g.N * es) {
+      CK(cudaMemcpyAsync(h->B.R, A, a_bytes, cudaMemcpyHostToDevice, h->st));
+      Ad = h->B.R;
+      ldad = lda;
+    } else {
+      CK(cudaMemcpy2DAsync(h->B.Q, g.ldq * es, A, lda * es, g.m * es, g.n, cudaMemcpyHostToDevice,
+                           h->st));
+      Ad = h->B.Q;
+      ldad = g.ldq;
+    }
     if (y) {
       CK(cudaMemcpy2DAsync(h->B.xw, g.m * es, y, ldy * es, g.m * es, nrhs, cudaMemcpyHostToDevice, h->st));
       yd = h->B.xw;
