@@ -43,9 +43,9 @@ namespace {
 
 constexpr int BM = 128;       // UMMA M (TMEM lanes)
 constexpr int BN = 128;       // UMMA N (TMEM columns)
-// TMEM columns: two accumulator buffers of MP 128 x 128 accumulators (a power of two, <= 512)
-template <int MP>
-constexpr int tmem_cols() { return 2 * MP * BN; }
+// TMEM columns: two accumulator buffers of U 128 x 128 accumulators (a power of two, <= 512)
+template <int U>
+constexpr int tmem_cols() { return 2 * U * BN; }
 constexpr int kEpiWarps = 8;  // two per TMEM lane quarter, each draining half the columns
 constexpr int kThreads = 32 * (4 + kEpiWarps);
 constexpr int kMaxSplits = 16;
@@ -209,6 +209,7 @@ struct TcJob {
   int split_b_smem;   // 1: B arrives raw and is split in shared memory
   int epi;            // 0: store partial P[s] ; 1: C -= D
   int prefetch_c;     // epi 1: prefetch each output tile into L2 when its loads start
+  int pair_n;         // B from planes: work units of two N tiles when n_tiles is even
   int64_t c_col0;     // epi 1: column of `out` in the tensor map of C
   int m_tiles, n_tiles, splits;
   int64_t a_row0;     // A tile y coordinate offset (rows of the MMA M dimension)
@@ -224,11 +225,11 @@ struct TcJob {
   int* status;
 };
 
-template <int STAGES, int NA, int NB, int MP = 1>
+template <int STAGES, int NA, int NB, int MP = 1, int NP = 1>
 struct Smem {
-  // per stage: NA A tiles for each of the MP M tiles, then NB B tiles (each 1024-byte aligned,
-  // 16 KB)
-  static constexpr uint32_t kStageBytes = MP * NA * kTileBytesA + NB * kTileBytesB;
+  // per stage: NA A tiles for each of the MP M tiles, then NB B tiles for each of the NP N
+  // tiles (each 1024-byte aligned, 16 KB)
+  static constexpr uint32_t kStageBytes = MP * NA * kTileBytesA + NP * NB * kTileBytesB;
   static constexpr uint32_t kTiles = STAGES * kStageBytes;
   static constexpr uint32_t kTotal = kTiles + 1024 /*alignment*/ + 256 /*barriers*/;
   // full/ready/empty per stage, acc_full[2], acc_empty[2], TMEM slot, abort flag
@@ -244,11 +245,15 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 
 // MP = 2: a work unit is a pair of vertically adjacent M tiles on the same N tile (m_tiles
 // even): the B tile is loaded (and split) once for both, and two accumulators are formed.
-template <bool BF, int STAGES, int NA, int NB, int MP>
+// NP = 2: a pair of adjacent N tiles on the same M tile (n_tiles even, B from planes): the A
+// tiles are loaded once for both.  MP NP <= 2.
+template <bool BF, int STAGES, int NA, int NB, int MP, int NP>
 __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__ TcMaps maps,
                                                           const TcJob job) {
-  using S = Smem<STAGES, NA, NB, MP>;
-  constexpr int kTmemCols = tmem_cols<MP>();
+  static_assert(MP * NP <= 2, "at most two accumulators per buffer");
+  using S = Smem<STAGES, NA, NB, MP, NP>;
+  constexpr int kAcc = MP * NP;  // accumulators per work unit
+  constexpr int kTmemCols = tmem_cols<kAcc>();
   constexpr int BK = Op<BF>::KE;
   constexpr int UMMA_K = Op<BF>::UK;
   extern __shared__ __align__(1024) unsigned char smraw[];
@@ -267,9 +272,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
   // the output tiles stay inside `out` (uniform over the launch: before any barrier or TMEM
   // allocation)
   CQR_CHECK(job.ldo >= job.mrows && (int64_t)job.m_tiles * BM >= job.mrows &&
-                (int64_t)job.n_tiles * BN >= job.ncols && job.m_tiles % MP == 0, 401);
+                (int64_t)job.n_tiles * BN >= job.ncols && job.m_tiles % MP == 0 &&
+                job.n_tiles % NP == 0 && (NP == 1 || !job.split_b_smem), 401);
   const int mu = job.m_tiles / MP;  // work units along M
-  const int total_tiles = mu * job.n_tiles * job.splits;
+  const int total_tiles = mu * (job.n_tiles / NP) * job.splits;
   const int nkb_full = (int)(job.kchunk / BK);
 
   if (threadIdx.x == 0) {
@@ -316,14 +322,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
       for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x) {
         const int split = t % job.splits;
         const int mn = t / job.splits;
-        const int mt = (mn % mu) * MP, nt = mn / mu;  // first M tile of the unit
+        const int mt = (mn % mu) * MP, nt = (mn / mu) * NP;  // first M and N tiles of the unit
         const int nk = kblocks(split);
         const int64_t kbase = job.k0 + (int64_t)split * job.kchunk;
         if (job.prefetch_c) {
-          // the output tile (BM rows x BN columns of C) is read by the epilogue once this
-          // tile's products are done: start bringing it into L2 now
-          const int y = (int)(job.c_col0 + (int64_t)nt * BN);
-          for (int r = 0; r < BM; r += 32) tma_prefetch_l2(&maps.c, mt * BM + r, y);
+          // the output tiles (BM rows x BN columns of C) are read by the epilogue once this
+          // unit's products are done: start bringing them into L2 now
+          for (int n = 0; n < NP; ++n) {
+            const int y = (int)(job.c_col0 + (int64_t)(nt + n) * BN);
+            for (int r = 0; r < BM; r += 32) tma_prefetch_l2(&maps.c, mt * BM + r, y);
+          }
         }
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = it % STAGES;
@@ -335,16 +343,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
           // raw FP32 B for the in-smem split: one 32-element box (TF32) or two (BF16: 64
           // elements of K, split in place into the BF16 hi and lo tiles)
           const int nb_load = job.split_b_smem ? (BF ? 2 : 1) : NB;
-          mbar_expect_tx(&full[s], MP * NA * kTileBytesA + nb_load * kTileBytesB);
+          mbar_expect_tx(&full[s], MP * NA * kTileBytesA + NP * nb_load * kTileBytesB);
 #pragma unroll
           for (int m = 0; m < MP; ++m)
             for (int p = 0; p < NA; ++p)
               tma_load_2d(st + (m * NA + p) * kTileBytesA, &maps.a[p], x, ya + m * BM, &full[s]);
-          for (int p = 0; p < nb_load; ++p) {
-            const bool raw = job.split_b_smem;
-            tma_load_2d(st + MP * NA * kTileBytesA + p * kTileBytesB, raw ? &maps.b[0] : &maps.b[p],
-                        raw ? x + 32 * p : x, yb, &full[s]);
-          }
+#pragma unroll
+          for (int n = 0; n < NP; ++n)
+            for (int p = 0; p < nb_load; ++p) {
+              const bool raw = job.split_b_smem;
+              tma_load_2d(st + MP * NA * kTileBytesA + (n * NB + p) * kTileBytesB,
+                          raw ? &maps.b[0] : &maps.b[p], raw ? x + 32 * p : x, yb + n * BN,
+                          &full[s]);
+            }
         }
       }
       // the last load issued into each stage has landed before the CTA may exit (bounded)
@@ -363,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
         // two accumulator buffers: the epilogue drains unit tl-1 while unit tl accumulates;
         // a buffer holds MP accumulators of BN columns
         const int buf = tl & 1;
-        const uint32_t acc = tmem + (uint32_t)(buf * MP * BN);
+        const uint32_t acc = tmem + (uint32_t)(buf * kAcc * BN);
         if (!mbar_wait(&acc_empty[buf], ((tl >> 1) & 1) ^ 1, abort_flag)) break;
         tc_fence_after();
         bool ok = true;
@@ -373,21 +384,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
           if (!mbar_wait(gate, (it / STAGES) & 1, abort_flag)) { ok = false; break; }
           tc_fence_after();
           const uint32_t st = tiles_u + s * S::kStageBytes;
-          const uint32_t b_hi = st + MP * NA * kTileBytesA, b_lo = b_hi + kTileBytesB;
 #pragma unroll
           for (int ks = 0; ks < BK / UMMA_K; ++ks) {
             const uint32_t off = ks * 32;  // 32 bytes of K per instruction
             const uint32_t acc0 = (kb > 0 || ks > 0) ? 1u : 0u;
 #pragma unroll
-            for (int m = 0; m < MP; ++m) {
-              const uint32_t am = acc + (uint32_t)(m * BN);
-              const uint32_t a_hi = st + m * NA * kTileBytesA, a_lo = a_hi + kTileBytesA;
-              mma_op<BF>(am, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
-              if (job.nprod == 3) {
-                mma_op<BF>(am, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
-                mma_op<BF>(am, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
+            for (int m = 0; m < MP; ++m)
+#pragma unroll
+              for (int n = 0; n < NP; ++n) {
+                const uint32_t am = acc + (uint32_t)((m * NP + n) * BN);
+                const uint32_t a_hi = st + m * NA * kTileBytesA, a_lo = a_hi + kTileBytesA;
+                const uint32_t b_hi = st + MP * NA * kTileBytesA + n * NB * kTileBytesB;
+                const uint32_t b_lo = b_hi + kTileBytesB;
+                mma_op<BF>(am, sdesc(a_hi + off), sdesc(b_hi + off), acc0);
+                if (job.nprod == 3) {
+                  mma_op<BF>(am, sdesc(a_hi + off), sdesc(b_lo + off), 1u);
+                  mma_op<BF>(am, sdesc(a_lo + off), sdesc(b_hi + off), 1u);
+                }
               }
-            }
           }
           mma_commit(&empty[s]);
         }
@@ -467,22 +481,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
     for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x, ++tl) {
       const int split = t % job.splits;
       const int mn = t / job.splits;
-      const int mt = (mn % mu) * MP, nt = mn / mu;
+      const int mt = (mn % mu) * MP, nt = (mn / mu) * NP;
       const int buf = tl & 1;
       if (!mbar_wait(&acc_full[buf], (tl >> 1) & 1, abort_flag)) break;
       tc_fence_after();
       const bool has_k = kblocks(split) > 0;
 #pragma unroll 1
-      for (int q = half; q < MP * kChunks; q += kEpiWarps / 4) {
-        const int m = q / kChunks, c = q % kChunks;
+      for (int q = half; q < kAcc * kChunks; q += kEpiWarps / 4) {
+        const int a = q / kChunks, c = q % kChunks;  // accumulator a = m NP + n
+        const int m = a / NP, n = a % NP;
         const int64_t row = (int64_t)(mt + m) * BM + ew * 32 + lane;
         const bool row_ok = row < job.mrows;
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)((buf * MP + m) * BN + c * 32), v);
+        tmem_ld32(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)((buf * kAcc + a) * BN + c * 32), v);
         if (!has_k)
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = 0.f;
-        const int64_t col0 = (int64_t)nt * BN + c * 32;
+        const int64_t col0 = (int64_t)(nt + n) * BN + c * 32;
         if (job.epi == 0) {
           float* o = job.out + (int64_t)split * job.split_stride;
 #pragma unroll
@@ -776,16 +791,16 @@ cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-template <bool BF, int STAGES, int NA, int NB, int MP = 1>
+template <bool BF, int STAGES, int NA, int NB, int MP = 1, int NP = 1>
 cudaError_t launch_gemm(const TcMaps& maps, const TcJob& job, int max_ctas, cudaStream_t st, bool pdl) {
-  using S = Smem<STAGES, NA, NB, MP>;
-  const void* fn = (const void*)k_tc_gemm<BF, STAGES, NA, NB, MP>;
+  using S = Smem<STAGES, NA, NB, MP, NP>;
+  const void* fn = (const void*)k_tc_gemm<BF, STAGES, NA, NB, MP, NP>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kTotal);
   if (e != cudaSuccess) return e;
-  const int tiles = job.m_tiles / MP * job.n_tiles * job.splits;
+  const int tiles = job.m_tiles / MP * (job.n_tiles / NP) * job.splits;
   const int grid = std::max(1, std::min(tiles, max_ctas));
-  return launch_k(k_tc_gemm<BF, STAGES, NA, NB, MP>, dim3(grid), dim3(kThreads), S::kTotal, st, pdl,
-                  maps, job);
+  return launch_k(k_tc_gemm<BF, STAGES, NA, NB, MP, NP>, dim3(grid), dim3(kThreads), S::kTotal, st,
+                  pdl, maps, job);
 }
 
 // GEMM1-shaped launches (B raw and split in shared memory, 3xTF32) take pairs of M tiles when
@@ -798,6 +813,21 @@ bool pair_m_tiles(bool three, bool bf, bool split, int m_tiles) {
     return e ? atoi(e) : 1;
   }();
   return env != 0 && three && !bf && split && m_tiles % 2 == 0;
+}
+
+// Launches whose B comes from planes (GEMM2 and the block pass's second product) take pairs of
+// N tiles when the job asks for it (TcJob::pair_n) and n_tiles is even: the A tiles are then
+// loaded once for both.  CQR_GEMM_NPAIR: 0 never, 1 the block pass's second product only
+// (the default), 2 also GEMM2.
+int npair_level() {
+  static const int env = [] {
+    const char* e = getenv("CQR_GEMM_NPAIR");
+    return e ? atoi(e) : 1;
+  }();
+  return env;
+}
+bool pair_n_tiles(bool three, bool bf, bool split, const TcJob& job) {
+  return job.pair_n && three && !bf && !split && job.n_tiles % 2 == 0;
 }
 
 // One launch of the tensor-core kernel in the variant of the handle's mode.  split: B arrives
@@ -813,6 +843,8 @@ cudaError_t launch_mode(const TcGemm* t, bool split, const TcMaps& maps, const T
   if (!t->bf) {
     if (pair_m_tiles(three, false, split, job.m_tiles))
       return launch_gemm<false, 2, 2, 2, 2>(maps, job, mc, st, pdl);
+    if (pair_n_tiles(three, false, split, job))
+      return launch_gemm<false, 2, 2, 2, 1, 2>(maps, job, mc, st, pdl);
     return three ? launch_gemm<false, 3, 2, 2>(maps, job, mc, st, pdl)
                  : launch_gemm<false, 6, 1, 1>(maps, job, mc, st, pdl);
   }
@@ -1093,6 +1125,7 @@ cudaError_t tc_gemm_update(TcGemm* t, int bk, int64_t j0, int64_t w, int buf, in
   maps.c = t->tm_q_b;
   job.prefetch_c = 1;
   job.c_col0 = j0;
+  job.pair_n = npair_level() >= 2 ? 1 : 0;
   return launch_mode(t, false, maps, job, st, max_ctas);
 }
 
@@ -1145,7 +1178,9 @@ cudaError_t tc_block_reorth(TcGemm* t, int64_t kb, int bk, float* R, int64_t ldr
   // kMaxSplits * bkp * N floats) and are subtracted in a fixed order, so the result does not
   // depend on the schedule.
   const int64_t kblk = kbp / KE;
-  const int tiles2 = job.m_tiles * job.n_tiles;
+  job.pair_n = npair_level() >= 1 ? 1 : 0;
+  const bool np2 = pair_n_tiles(t->nplanes == 2, t->bf, false, job);
+  const int tiles2 = job.m_tiles * (job.n_tiles / (np2 ? 2 : 1));
   const int64_t cap = std::min<int64_t>(kMaxSplits, (int64_t)kMaxSplits * t->bkp * t->N /
                                                         (t->M * (int64_t)bk));
   const int64_t kchunk2 = best_kchunk(tiles2, kblk, t->num_sms, (int)std::max<int64_t>(1, cap)) * KE;
