@@ -329,13 +329,17 @@ __device__ bool b_panel(BCtx<G>& c, float* P, int64_t cs, int nr, int bk, float*
   // step 0: v_a = p_a^T p_0 and eta_a = p_a^T p_a
   cta_start_sums<G, RPT>(c, P, cs, nr, bk, loc);
   cluster_sum<G>(c, loc, 2 * bk, tmp);
+  // eta_a is kept as the ICGS threshold: the FP64 product tau^2 eta_a rounded up to FP32, so
+  // that the FP32 test v_j < eta_j decides exactly as the FP64 one, with one FP64 product per
+  // column instead of one per thread and column
+  const bool icgs = tau2 > 0.0;
   for (int a = c.tid; a < bk; a += kBT) {
     v[a] = tmp[a];
-    eta[a] = tmp[bk + a];
+    eta[a] = icgs ? __double2float_ru(tau2 * (double)tmp[bk + a]) : tmp[bk + a];
   }
   __syncthreads();
   for (int j = 0; j < bk; ++j) {
-    if (j > 0 && tau2 > 0.0 && (double)v[j] < tau2 * (double)eta[j]) {
+    if (j > 0 && icgs && v[j] < eta[j]) {
       // ICGS: project p_j once more on q_0 .. q_{j-1}
       cta_colsums<G>(c, j, nr, loc, [&](int a, int r) { return P[r + a * cs] * P[r + j * cs]; });
       cluster_sum<G>(c, loc, j, sv);

@@ -88,6 +88,14 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
   return s_ok != 0;
 }
 
+// t rounded towards +infinity to T (the FP32 threshold of the ICGS test; exact for double)
+template <typename T>
+__device__ __forceinline__ T round_up_to(double t);
+template <>
+__device__ __forceinline__ float round_up_to<float>(double t) { return __double2float_ru(t); }
+template <>
+__device__ __forceinline__ double round_up_to<double>(double t) { return t; }
+
 template <typename T>
 struct Ctx {
   T* base;       // slice, column 0, first row of this CTA
@@ -493,9 +501,17 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
     }
     if (!sync_reduce<T, CL, HIER>(c, 0, 2 * pld, v, step++, 1)) { leave(); return; }
   }
+  // The ICGS test of column j, v_j < tau^2 eta_j with the product in FP64, is taken in T
+  // against eta_j replaced by the FP64 product rounded up to T: for a T value v and a double
+  // t, (double)v < t exactly when v < t rounded up to T, so the decision is the same, with
+  // one FP64 product per column and CTA instead of one per thread and column.  The first
+  // use (j = 1) comes after the next reduction's barriers.
+  const bool icgs = tau2 > 0.0;
+  if (icgs)
+    for (int a = tid; a < bk; a += kNT) eta[a] = round_up_to<T>(tau2 * (double)eta[a]);
 
   for (int j = 0; j < bk; ++j) {
-    if (j > 0 && tau2 > 0.0 && (double)v[j] < tau2 * (double)eta[j]) {
+    if (j > 0 && icgs && v[j] < eta[j]) {
       // ICGS: one more projection of p_j on the computed columns 0 .. j-1
       const T* pj = c.base + j * c.cs;
 #pragma unroll

@@ -275,11 +275,18 @@ __global__ void __launch_bounds__(kNT, 1) k_panel_reg(float* __restrict__ Q, int
   gather(par, 256, 256 + bk, v);
   __syncthreads();
   par ^= 1;
+  // The ICGS test v_j < tau^2 eta_j (product in FP64) in FP32 against the FP64 product
+  // rounded up to FP32: the same decision for every FP32 v, with one FP64 product per column
+  // and CTA instead of one per thread and column.  First used at j = 1, after the next
+  // exchange's barriers.
+  const bool icgs = tau2 > 0.0;
+  if (icgs)
+    for (int a = tid; a < bk; a += kNT) eta[a] = __double2float_ru(tau2 * (double)eta[a]);
 
   for (int j = 0; j < bk && !aborted; ++j) {
     float* st_cur = stage + (size_t)(j & 1) * 2 * RPC;   // p_j, p_{j+1}
     float* st_nxt = stage + (size_t)((j + 1) & 1) * 2 * RPC;
-    if (j > 0 && tau2 > 0.0 && (double)v[j] < tau2 * (double)eta[j]) {
+    if (j > 0 && icgs && v[j] < eta[j]) {
       // ICGS reorthogonalisation of p_j against columns 0 .. j-1 (held by their owners)
       uint64_t pj[NP];
 #pragma unroll
