@@ -300,7 +300,7 @@ cqr_status coded_qr_debug_bounds_selftest(void* stream);
  * microseconds (CUDA events on `stream`; the call synchronises the stream).
  *   kind 0: the register panel (one cluster; bk <= 128 and M within its registers);
  *   kind 1: the shared-memory panel as the handle plans it for M rows (one cluster of up to
- *           16 CTAs, the two-level exchange over clusters of 8, or the grid barrier).
+ *           16 CTAs, the two-level exchange over clusters of 16 or 8, or the grid barrier).
  * It allocates its scratch with cudaMalloc and frees it.  Returns CQR_EINVAL when the panel does
  * not fit the chosen kind (or its slices would not be in shared memory), the device status
  * (CQR_ETIMEOUT) when an exchange wait ran out, CQR_ECUDA when a sum came back wrong or a CUDA

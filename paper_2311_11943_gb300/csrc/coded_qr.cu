@@ -379,6 +379,10 @@ void ensure_panel_plan(cqr_handle h, int bk) {
   h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, true);
   if (h->plan.cluster && !panel_cluster_fits<T>(h->plan))
     h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, false);
+  // two-level plans: clusters of 16, else of 8, else the flat grid, whichever can have all
+  // its clusters resident at once
+  if (h->plan.hier && !panel_hier_fits<T>(h->plan))
+    h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, h->plan.cluster != 0, true, 8);
   if (h->plan.hier && !panel_hier_fits<T>(h->plan))
     h->plan = plan_panel(g.M, bk, sizeof(T), h->num_sms, h->plan.cluster != 0, false);
   h->reg_ok = false;
@@ -1214,6 +1218,8 @@ cqr_status coded_qr_probe_exchange(int32_t kind, int64_t M, int32_t bk, int32_t 
     // the plan the handle's panel step takes for an FP32 panel of M rows (ensure_panel_plan)
     pp = plan_panel(M, bk, sizeof(float), sms, true);
     if (pp.cluster && !panel_cluster_fits<float>(pp)) pp = plan_panel(M, bk, sizeof(float), sms, false);
+    if (pp.hier && !panel_hier_fits<float>(pp))
+      pp = plan_panel(M, bk, sizeof(float), sms, pp.cluster != 0, true, 8);
     if (pp.hier && !panel_hier_fits<float>(pp))
       pp = plan_panel(M, bk, sizeof(float), sms, pp.cluster != 0, false);
     if (!pp.smem) return CQR_EINVAL;  // slices in global memory: no exchange-only floor

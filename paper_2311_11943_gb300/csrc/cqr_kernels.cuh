@@ -33,6 +33,7 @@ struct PanelPlan {
   int smem;       // 1: panel slice resident in shared memory
   int cluster;    // 1: one thread-block cluster (distributed shared memory reductions)
   int hier;       // 1: grid of clusters with the two-level exchange (FP32, shared-memory slices)
+  int hcs;        // two-level: CTAs per cluster (8, or 16 with CQR_HIER_CS=16)
   size_t smem_bytes;
 };
 
@@ -46,9 +47,10 @@ cudaError_t launch_encode(const Geo& g, const T* A, int64_t lda, const T* Gt, co
                           int* status, cudaStream_t st);
 
 
-// allow_hier: a grid of more than 48 FP32 CTAs may use the two-level exchange (clusters of 8)
+// allow_hier: a grid of more than 48 FP32 CTAs may use the two-level exchange, in clusters of
+// hier_cs (16, or 8) CTAs
 PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_cluster,
-                     bool allow_hier = true);
+                     bool allow_hier = true, int hier_cs = 16);
 template <typename T>
 bool panel_cluster_fits(const PanelPlan& pp);
 // Whether every cluster of a two-level plan can be resident at once.

@@ -30,9 +30,11 @@ constexpr int kNT = 512;
 constexpr int kNW = kNT / 32;
 constexpr size_t kSmemCap = 227 * 1024;
 constexpr int kMaxCluster = 16;
-// Two-level exchange of the grid variant: clusters of kHierCS CTAs, used for FP32 panels
+// Two-level exchange of the grid variant: clusters of kHierCS (or kHierCSWide) CTAs, used for
+// FP32 panels
 // that need more than kHierMinG CTAs.
 constexpr int kHierCS = 8;
+constexpr int kHierCSWide = 16;  // non-portable cluster size
 constexpr int kHierMinG = 48;
 
 __device__ __forceinline__ void cluster_sync_all() {
@@ -106,13 +108,16 @@ struct Ctx {
                  // [2][clusters][2*pld] cluster sums
   T* lpart;      // cluster and two-level variants: this CTA's [2][2*pld] in shared memory
   T* red;        // grid variant: shared [8][2*pld] scratch
-  T* rbuf;       // two-level, cluster leader: receive buffer [2][kHierCS][pld]
+  T* rbuf;       // two-level, cluster leader: receive buffer [hcs][pld] (one buffer: a CTA
+                 // sends step s + 1 only after it has read its leader's sums of step s, which
+                 // the leader writes after reading the buffer)
   uint64_t* mbar;  // two-level: [2] mbarriers of rbuf (used in the leader)
   unsigned* bar;
   int* status;
   unsigned target;
   unsigned phases;   // two-level: bit p = phase parity of mbar[p]
   int crank, cl, ncl;  // two-level: rank in the cluster, cluster index, clusters
+  int hcs;             // two-level: CTAs per cluster
   long long wait_limit;  // bound of each wait on other CTAs, SM cycles
 };
 
@@ -251,9 +256,9 @@ __device__ __forceinline__ bool sync_reduce(Ctx<T>& c, int lo, int hi, T* out, i
       __syncthreads();  // this CTA's partials are complete; no thread reads the step's columns
       hook();
       const uint32_t lead_buf =
-          map_peer(smem_addr(c.rbuf + ((size_t)par * kHierCS + c.crank) * c.pld), 0);
+          map_peer(smem_addr(c.rbuf + (size_t)c.crank * c.pld), 0);
       const uint32_t lead_bar = map_peer(smem_addr(c.mbar + par), 0);
-      if (c.crank == 0 && tid == 0) mbar_expect(c.mbar + par, (unsigned)(kHierCS * (c1 - c0) * 16));
+      if (c.crank == 0 && tid == 0) mbar_expect(c.mbar + par, (unsigned)(c.hcs * (c1 - c0) * 16));
       for (int ch = c0 + tid; ch < c1; ch += kNT)
         st_async4(lead_buf + 16u * ch,
                   *reinterpret_cast<const float4*>(c.lpart + par * 2 * c.pld + 4 * ch), lead_bar);
@@ -271,8 +276,7 @@ __device__ __forceinline__ bool sync_reduce(Ctx<T>& c, int lo, int hi, T* out, i
         for (int a = lo + tid; a < hi; a += kNT) {
           float sum = 0.f;
 #pragma unroll
-          for (int k = 0; k < kHierCS; ++k)
-            sum += (float)c.rbuf[((size_t)par * kHierCS + k) * c.pld + a];
+          for (int k = 0; k < c.hcs; ++k) sum += (float)c.rbuf[(size_t)k * c.pld + a];
           st_relaxed_u64(dst + a, tag | __float_as_uint(sum));
         }
       }
@@ -432,9 +436,15 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
   c.status = status;
   c.target = 0;
   c.phases = 0u;
-  c.crank = g % kHierCS;
-  c.cl = g / kHierCS;
-  c.ncl = gridDim.x / kHierCS;
+  c.hcs = kHierCS;
+  if (HIER) {
+    unsigned ncta;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
+    c.hcs = (int)ncta;
+  }
+  c.crank = g % c.hcs;
+  c.cl = g / c.hcs;
+  c.ncl = gridDim.x / c.hcs;
   c.wait_limit = wait_limit;
   int step = 0;
   auto ok_row = [&](int r) { return SMEM ? true : (r < nr); };
@@ -450,11 +460,11 @@ __global__ void __launch_bounds__(kNT, 1) k_panel(T* __restrict__ Q, int64_t ldq
     }
   };
   if (HIER) {
-    // the exchange addresses rank 0 of a cluster of kHierCS CTAs: a launch of any other shape
+    // the exchange addresses rank 0 of a cluster of 8 or 16 CTAs: a launch of any other shape
     // (the same for every CTA) records an error and leaves before touching another CTA
     unsigned ncta;
     asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
-    if (ncta != (unsigned)kHierCS || gridDim.x % kHierCS != 0) {
+    if ((ncta != (unsigned)kHierCS && ncta != (unsigned)kHierCSWide) || gridDim.x % ncta != 0) {
       if (g == 0 && tid == 0) set_status(status, CQR_ECUDA, 50);
       return;
     }
@@ -804,14 +814,20 @@ __global__ void __launch_bounds__(kNT, 1) k_exchange_probe(int bk, int reps, flo
   c.status = status;
   c.target = 0;
   c.phases = 0u;
-  c.crank = g % kHierCS;
-  c.cl = g / kHierCS;
-  c.ncl = gridDim.x / kHierCS;
+  c.hcs = kHierCS;
+  if (HIER) {
+    unsigned ncta;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
+    c.hcs = (int)ncta;
+  }
+  c.crank = g % c.hcs;
+  c.cl = g / c.hcs;
+  c.ncl = gridDim.x / c.hcs;
   c.wait_limit = wait_limit;
   if (HIER) {
     unsigned ncta;
     asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
-    if (ncta != (unsigned)kHierCS || gridDim.x % kHierCS != 0) {
+    if ((ncta != (unsigned)kHierCS && ncta != (unsigned)kHierCSWide) || gridDim.x % ncta != 0) {
       if (g == 0 && tid == 0) set_status(status, CQR_ECUDA, 51);
       return;
     }
@@ -926,7 +942,7 @@ int rpl_for_rows(int rpc) {
 // the smallest RPL that fits shared memory with G <= #SMs (grid barrier); otherwise slices in
 // global memory.  CQR_PANEL_RPL / CQR_PANEL_CLUSTER override the choice (tuning).
 PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_cluster,
-                     bool allow_hier) {
+                     bool allow_hier, int hier_cs) {
   PanelPlan p{};
   const int rpl_env = env_int("CQR_PANEL_RPL", 0);
   const int cl_env = env_int("CQR_PANEL_CLUSTER", -1);
@@ -965,10 +981,16 @@ PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_clu
     // many CTAs (FP32): the two-level exchange, the grid padded to whole clusters (the extra
     // CTAs own no rows)
     if (!best_cl && allow_hier && elem == 4 && p.G > kHierMinG && env_int("CQR_PANEL_HIER", 1) != 0) {
-      const int Gh = (p.G + kHierCS - 1) / kHierCS * kHierCS;
+      // clusters of 16 (non-portable) unless the caller or CQR_HIER_CS asks for 8: half as
+      // many cluster sums for every CTA to poll (20480 x 256, FP32: 73.5 against 78.3 ms per
+      // 64 panels)
+      const int req = env_int("CQR_HIER_CS", hier_cs);
+      const int hcs = req == kHierCS ? kHierCS : kHierCSWide;
+      const int Gh = (p.G + hcs - 1) / hcs * hcs;
       const size_t sb = (size_t)bk * p.rpc_pad * elem + small_bytes(bk, elem, false, true);
       if (Gh <= num_sms && sb + 1024 <= kSmemCap) {
         p.hier = 1;
+        p.hcs = hcs;
         p.G = Gh;
         p.smem_bytes = sb;
       }
@@ -988,7 +1010,7 @@ PanelPlan plan_panel(int64_t M, int bk, size_t elem, int num_sms, bool allow_clu
   return p;
 }
 
-// Launch configuration of the two-level variant: clusters of kHierCS CTAs over the whole
+// Launch configuration of the two-level variant: clusters of pp.hcs CTAs over the whole
 // grid.  Its leaders wait for one another, so every cluster must be resident at once: the
 // plan is taken only when the occupancy query says they all fit (panel_hier_fits), and the
 // variant is used only on the sequential schedule, where the panel is the only work on the
@@ -1001,7 +1023,7 @@ void hier_config(const PanelPlan& pp, cudaStream_t st, cudaLaunchConfig_t* cfg,
   cfg->dynamicSmemBytes = pp.smem_bytes;
   cfg->stream = st;
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kHierCS;
+  attr[0].val.clusterDim.x = pp.hcs;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg->attrs = attr;
@@ -1014,6 +1036,8 @@ cudaError_t launch_hier(const PanelPlan& pp, int rpl, void** args, cudaStream_t 
   if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)pp.smem_bytes);
+  if (e == cudaSuccess && pp.hcs > 8)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
@@ -1041,7 +1065,7 @@ cudaError_t launch_panel(const PanelPlan& pp, T* Q, int64_t ldq, T* R, int64_t l
     const int pld = (bk + 3) / 4 * 4;
     const size_t row = (size_t)2 * pld * sizeof(T);
     cudaError_t e = cudaMemsetAsync(reinterpret_cast<char*>(part) + (size_t)pp.G * row, 0,
-                                    (size_t)2 * (pp.G / kHierCS) * row, st);
+                                    (size_t)2 * (pp.G / pp.hcs) * row, st);
     if (e != cudaSuccess) return e;
     return launch_hier<T>(pp, rpl, args, st);
   }
@@ -1106,7 +1130,9 @@ bool panel_hier_fits(const PanelPlan& pp) {
   const void* fn = pick_hier<T>((pp.rpc / 32));
   if (!fn) return false;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp.smem_bytes) !=
-      cudaSuccess) {
+          cudaSuccess ||
+      (pp.hcs > 8 &&
+       cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
     cudaGetLastError();
     return false;
   }
@@ -1118,7 +1144,7 @@ bool panel_hier_fits(const PanelPlan& pp) {
     cudaGetLastError();
     return false;
   }
-  return n >= pp.G / kHierCS;
+  return n >= pp.G / pp.hcs;
 }
 
 size_t panel_partial_bytes(int bk, size_t elem, int num_sms) {
@@ -1149,11 +1175,11 @@ cudaError_t launch_exchange_probe(const PanelPlan& pp, int bk, int reps, float* 
   if (e == cudaSuccess && pp.hier) {
     const size_t row = (size_t)2 * pld * sizeof(float);
     e = cudaMemsetAsync(reinterpret_cast<char*>(part) + (size_t)pp.G * row, 0,
-                        (size_t)2 * (pp.G / kHierCS) * row, st);
+                        (size_t)2 * (pp.G / pp.hcs) * row, st);
   }
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp.smem_bytes);
-  if (e == cudaSuccess && pp.cluster && pp.G > 8)
+  if (e == cudaSuccess && ((pp.cluster && pp.G > 8) || (pp.hier && pp.hcs > 8)))
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   long long wl = kWaitLimitCycles;
@@ -1166,7 +1192,7 @@ cudaError_t launch_exchange_probe(const PanelPlan& pp, int bk, int reps, float* 
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = pp.hier ? kHierCS : pp.G;
+    attr[0].val.clusterDim.x = pp.hier ? pp.hcs : pp.G;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
