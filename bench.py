@@ -417,8 +417,8 @@ def run_reference(args, cfg):
 # ------------------------------------------------------------------------ GPU leg
 def measure_peaks_here(torch):
     """TF32 and FP64 dense matmul rates of this GPU, measured in the run by the same torch
-    method as the driver's bf16 figures: torch.matmul, best of 10 (burst) and back to back for
-    about two seconds (sustained, TF32 only), CUDA events."""
+    method as the measured BF16 peaks file: torch.matmul, best of 10 (burst) and back to back
+    for about two seconds (sustained, TF32 only), CUDA events."""
     out = {}
     prev = torch.backends.cuda.matmul.allow_tf32
     try:
