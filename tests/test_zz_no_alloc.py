@@ -1,9 +1,11 @@
 """coded_qr_panel_icgs_noalloc: the panel factorisation for callers that cannot allocate device
 memory (caching allocators that must not be re-entered, hosts that gave all device memory to
-another framework, latency-critical paths that must not take the allocation lock).  Its scratch is a fixed array inside the
-library, so these tests check that two calls in a row -- the second one seeing the array as
-the first left it -- give the same panel as the allocating path (coded_qr_factor's first
-panel step), within the parity tolerance of the other GPU tests.  This file is collected last.
+another framework, latency-critical paths that must not take the allocation lock).  Its
+scratch is a fixed array inside the library, so these tests check that two calls in a row --
+the second one seeing the array as the first left it -- give the same panel as the allocating
+path (coded_qr_factor's first panel step), within the parity tolerance of the other GPU tests,
+and that the largest panel it accepts is one 1024-row slice per co-resident CTA,
+min(160, #SMs) of them.  This file is collected last.
 """
 import ctypes as C
 
@@ -72,3 +74,24 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert B.coded_qr_panel_icgs_noalloc(B.CQR_F64, 10_000_000, 64, x.data_ptr(), 10_000_000,
                                          x.data_ptr(), 64) == B.CQR_EINVAL
     assert B.coded_qr_panel_icgs_noalloc(7, 64, 8, x.data_ptr(), 64, x.data_ptr(), 8) == B.CQR_EINVAL
+
+
+def test_noalloc_row_limit_is_one_slice_per_resident_cta():
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    lim = min(160, sms) * 1024
+    bk = 8
+    Q = B.colmajor_empty(lim + 1, bk, torch.float32)
+    Q.copy_(torch.randn(bk, lim + 1, device="cuda", generator=torch.Generator("cuda").manual_seed(5)).t())
+    R = B.colmajor_empty(bk, bk, torch.float32)
+    R.zero_()
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")
+    # at the limit: accepted and factored (an orthonormal panel)
+    assert B.coded_qr_panel_icgs_noalloc(B.CQR_F32, lim, bk, Q.data_ptr(), lim + 1, R.data_ptr(), bk,
+                                         0.0, st.data_ptr()) == B.CQR_OK
+    torch.cuda.synchronize()
+    assert int(st[0].item()) == 0
+    Qd = Q[:lim].double()
+    assert (Qd.t() @ Qd - torch.eye(bk, dtype=torch.float64, device="cuda")).abs().max().item() < 1e-4
+    # one row more: rejected without a launch
+    assert B.coded_qr_panel_icgs_noalloc(B.CQR_F32, lim + 1, bk, Q.data_ptr(), lim + 1, R.data_ptr(),
+                                         bk, 0.0, st.data_ptr()) == B.CQR_EINVAL
