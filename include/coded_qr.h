@@ -363,7 +363,7 @@ cqr_status coded_qr_panel_icgs_noalloc(int32_t dtype, int64_t M, int32_t bk, voi
  * Per-instance arrays (m, n, A, lda, panel_end) are host arrays of length count. */
 typedef struct cqr_batched_s* cqr_batched;
 
-enum { CQR_BATCH_GRAPH = 1, CQR_BATCH_POST_ORTH = 2 };
+enum { CQR_BATCH_GRAPH = 1, CQR_BATCH_POST_ORTH = 2, CQR_BATCH_HOST_BUFFERS = 4 };
 
 /* Allocate the batch (cudaMalloc on the current device) and compute the shared generator.
  * Every instance must satisfy the single-instance rules (m_i >= n_i, p_c | n_i, ...). */
@@ -390,7 +390,13 @@ cqr_status coded_qr_batched_post_orth(cqr_batched bh);
  * holds count quadruples (instance, panel t, grid row, grid column): the tiles are lost at
  * the start of panel t (every tile of one instance at the same t, CQR_ENOTSUP otherwise).
  * With CQR_BATCH_GRAPH the launches are recorded into a CUDA graph on the first call and the
- * graph is replayed while the erasure list, the inputs and the tuning stay the same. */
+ * graph is replayed while the erasure list, the inputs and the tuning stay the same.
+ * With CQR_BATCH_HOST_BUFFERS, A[i] are host pointers (pinned memory gives full copy speed):
+ * each instance's A is copied on the batch's stream (one 2-D copy per instance) straight into
+ * the systematic block of its own encoded matrix, and the encode then runs in place there.
+ * The call returns once everything is enqueued, so the host arrays must stay untouched until
+ * the stream has passed the copies (coded_qr_batched_sync_status synchronises it).  The
+ * recorded graph does not depend on the host pointers. */
 cqr_status coded_qr_batched_run(cqr_batched bh, const void* const* A, const int64_t* lda,
                                 const int32_t* erasures, int32_t count, int32_t flags);
 /* Autotuner: times coded_qr_batched_run on A with the given erasure list (CUDA events, best
@@ -416,6 +422,19 @@ cqr_status coded_qr_batched_get_decode_sets(cqr_batched bh, int32_t i, int32_t* 
 /* Synchronise; the status of the first instance whose device status word is set (CQR_OK if
  * none), *first_bad its index or -1, *reorth the reorthogonalisations of all instances. */
 cqr_status coded_qr_batched_sync_status(cqr_batched bh, int32_t* first_bad, int64_t* reorth);
+
+/* Phase clocks of the persistent factor launch (instrumentation, no counterpart in the paper).
+ * With enable != 0 every later factor launch of the batch (direct, or recorded into a new
+ * graph) adds, for each CTA, the SM clock cycles it spent in each phase to counters of the
+ * batch (allocated on the first enable): in-launch recovery, panel, the product Qbar^T B,
+ * its reduction into Rbar, the update B -= Qbar Rbar, and the rest (work queue, the wait at
+ * the end).  Thread 0 of the CTA reads the clock at the phase boundaries, so the cost when on
+ * is a few instructions per panel and update chunk; when off, one test per boundary.
+ * coded_qr_batched_phases synchronises the stream and writes cycles[0..5] (host, summed over
+ * the CTAs, in the order above) and cycles[6] (the number of CTAs that added theirs); with
+ * reset != 0 it then zeroes the counters.  CQR_ESTATE if the clocks were never enabled. */
+cqr_status coded_qr_batched_profile(cqr_batched bh, int32_t enable);
+cqr_status coded_qr_batched_phases(cqr_batched bh, int64_t* cycles, int32_t reset);
 
 /* Name of the last CUDA error behind a CQR_ECUDA of a batch entry point on this host thread. */
 const char* coded_qr_batched_last_error(void);

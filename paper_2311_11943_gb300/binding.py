@@ -44,10 +44,11 @@ EXPORTS = ["coded_qr_workspace_size", "coded_qr_create", "coded_qr_create_in", "
            "coded_qr_batched_set_tuning", "coded_qr_batched_get_tuning",
            "coded_qr_batched_get_factors", "coded_qr_batched_get_decode_sets",
            "coded_qr_batched_sync_status", "coded_qr_batched_last_error",
+           "coded_qr_batched_profile", "coded_qr_batched_phases",
            "coded_qr_adjoint_qr", "coded_qr_adjoint_lstsq", "coded_qr_mds_stats",
            "coded_qr_inject_node_failure", "coded_qr_set_wait_limit", "coded_qr_debug_bounds",
            "coded_qr_debug_bounds_selftest", "coded_qr_probe_exchange"]
-CQR_BATCH_GRAPH, CQR_BATCH_POST_ORTH = 1, 2
+CQR_BATCH_GRAPH, CQR_BATCH_POST_ORTH, CQR_BATCH_HOST_BUFFERS = 1, 2, 4
 PROF_CLASSES = 17
 
 
@@ -131,6 +132,8 @@ def lib():
                                              C.POINTER(vp), C.POINTER(i64)],
             "coded_qr_batched_get_decode_sets": [vp, i32, C.POINTER(i32), i32, C.POINTER(i32)],
             "coded_qr_batched_sync_status": [vp, C.POINTER(i32), C.POINTER(i64)],
+            "coded_qr_batched_profile": [vp, i32],
+            "coded_qr_batched_phases": [vp, C.POINTER(i64), i32],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -666,9 +669,18 @@ class CodedQRBatch:
     def post_orth(self):
         _bcheck(coded_qr_batched_post_orth(self.h), "coded_qr_batched_post_orth")
 
-    def run(self, As, erasures=(), graph=True, post_orth=False):
+    def run(self, As, erasures=(), graph=True, post_orth=False, host=False):
+        """The whole sequence; with host=True, As are Fortran-ordered host arrays (numpy
+        views of pinned memory copy at full speed), copied by the library on its stream."""
         flags = (CQR_BATCH_GRAPH if graph else 0) | (CQR_BATCH_POST_ORTH if post_orth else 0)
-        _bcheck(coded_qr_batched_run(self.h, *self._args(As), list(erasures), flags),
+        if host:
+            for a in As:
+                assert a.flags.f_contiguous, "host A must be Fortran-ordered"
+            args = ([a.ctypes.data for a in As], [a.shape[0] for a in As])
+            flags |= CQR_BATCH_HOST_BUFFERS
+        else:
+            args = self._args(As)
+        _bcheck(coded_qr_batched_run(self.h, *args, list(erasures), flags),
               "coded_qr_batched_run")
 
     def autotune(self, As, erasures=(), reps=2):
@@ -697,6 +709,19 @@ class CodedQRBatch:
 
     def sync_status(self):
         return coded_qr_batched_sync_status(self.h)
+
+    BATCH_PHASES = ("recover", "panel", "s_product", "rbar_reduce", "update", "other")
+
+    def profile(self, on=True):
+        """Phase clocks of the later factor launches (coded_qr_batched_profile)."""
+        _bcheck(lib().coded_qr_batched_profile(self.h, 1 if on else 0), "coded_qr_batched_profile")
+
+    def phases(self, reset=True):
+        """SM cycles per phase summed over the CTAs, and the number of CTAs."""
+        buf = (C.c_int64 * 7)()
+        _bcheck(lib().coded_qr_batched_phases(self.h, buf, 1 if reset else 0),
+                "coded_qr_batched_phases")
+        return dict(zip(self.BATCH_PHASES, buf[:6])), buf[6]
 
 
 def debug_bounds():

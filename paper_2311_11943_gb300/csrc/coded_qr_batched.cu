@@ -83,6 +83,9 @@ struct cqr_batched_s {
   BatchTile* d_tiles = nullptr;
   int tile_cap = 0;
   int64_t max_tile_elems = 0;
+  // phase clocks of the factor launch (instrumentation)
+  unsigned long long* d_prof = nullptr;
+  bool prof_on = false;
   // recorded sequence
   cudaGraphExec_t gexec = nullptr;
   std::vector<int64_t> gkey;
@@ -151,6 +154,7 @@ cqr_status enqueue_factor(cqr_batched bh, const int* d_range, int queue_slot,
   L.plans = bh->d_plans;
   L.Gt = bh->d_Gt;
   L.Gh = bh->d_Gh;
+  L.prof = bh->prof_on ? bh->d_prof : nullptr;
   BK(launch_b_factor(L, bh->st));
   return CQR_OK;
 }
@@ -418,6 +422,7 @@ cqr_status coded_qr_batched_destroy(cqr_batched bh) {
   cudaStreamSynchronize(bh->st);
   if (bh->gexec) cudaGraphExecDestroy(bh->gexec);
   if (bh->mem) cudaFree(bh->mem);
+  if (bh->d_prof) cudaFree(bh->d_prof);
   if (bh->cap_st) cudaStreamDestroy(bh->cap_st);
   cudaGetLastError();
   delete bh;
@@ -539,7 +544,7 @@ cqr_status coded_qr_batched_post_orth(cqr_batched bh) {
 cqr_status coded_qr_batched_run(cqr_batched bh, const void* const* A, const int64_t* lda,
                                 const int32_t* erasures, int32_t count, int32_t flags) {
   if (!bh || count < 0 || (count > 0 && !erasures)) return CQR_EINVAL;
-  if (flags & ~(CQR_BATCH_GRAPH | CQR_BATCH_POST_ORTH)) return CQR_EINVAL;
+  if (flags & ~(CQR_BATCH_GRAPH | CQR_BATCH_POST_ORTH | CQR_BATCH_HOST_BUFFERS)) return CQR_EINVAL;
   // one erasure event per instance: every tile of instance k is lost at the same panel
   std::vector<int> t_of(bh->count, -1);
   for (int e = 0; e < count; ++e) {
@@ -552,9 +557,35 @@ cqr_status coded_qr_batched_run(cqr_batched bh, const void* const* A, const int6
     if (t_of[k] >= 0 && t_of[k] != t) return CQR_ENOTSUP;
     t_of[k] = t;
   }
-  cqr_status s = check_inputs(bh, A, lda);
+  // host buffers: the encode reads each A from the systematic block of the instance's own
+  // encoded matrix, where copy_in puts it (in place: every position is read and rewritten
+  // with the same value by one thread); the device addresses also key the recorded graph
+  const bool host = (flags & CQR_BATCH_HOST_BUFFERS) != 0;
+  std::vector<const void*> a_dev;
+  std::vector<int64_t> ld_dev;
+  if (host) {
+    if (!A || !lda) return CQR_EINVAL;
+    for (int k = 0; k < bh->count; ++k) {
+      if (!A[k] || lda[k] < bh->geo[k].m) return CQR_EINVAL;
+      a_dev.push_back(bh->h_inst[k].Q);
+      ld_dev.push_back(bh->geo[k].ldq);
+    }
+  }
+  const void* const* Ause = host ? a_dev.data() : A;
+  const int64_t* lduse = host ? ld_dev.data() : lda;
+  cqr_status s = check_inputs(bh, Ause, lduse);
   if (s != CQR_OK) return s;
   reset_state(bh);
+  auto copy_in = [&]() -> cqr_status {
+    if (!host) return CQR_OK;
+    for (int k = 0; k < bh->count; ++k) {
+      const Geo& g = bh->geo[k];
+      BK(cudaMemcpy2DAsync(bh->h_inst[k].Q, (size_t)g.ldq * sizeof(float), A[k],
+                           (size_t)lda[k] * sizeof(float), (size_t)g.m * sizeof(float),
+                           (size_t)g.n, cudaMemcpyHostToDevice, bh->st));
+    }
+    return CQR_OK;
+  };
   // host planning (before anything is enqueued, so that an unrecoverable pattern launches
   // nothing): panel ranges of the two factor phases, poisoned tiles, decode plans
   std::vector<int> ra(2 * bh->count), rb(2 * bh->count);
@@ -636,10 +667,11 @@ cqr_status coded_qr_batched_run(cqr_batched bh, const void* const* A, const int6
   std::vector<int64_t> key;
   key.push_back(flags);
   key.push_back(fused ? 1 : 0);
+  key.push_back(bh->prof_on ? 1 : 0);
   for (int e = 0; e < 4 * count; ++e) key.push_back(erasures[e]);
   for (int k = 0; k < bh->count; ++k) {
-    key.push_back(reinterpret_cast<int64_t>(A[k]));
-    key.push_back(lda[k]);
+    key.push_back(reinterpret_cast<int64_t>(Ause[k]));
+    key.push_back(lduse[k]);
   }
   const bool replay = (flags & CQR_BATCH_GRAPH) && bh->gexec && key == bh->gkey;
   int64_t dec_total = 0;
@@ -702,9 +734,12 @@ cqr_status coded_qr_batched_run(cqr_batched bh, const void* const* A, const int6
       }
       bh->gkey = key;
     }
+    s = copy_in();
+    if (s != CQR_OK) return s;
     BK(cudaGraphLaunch(bh->gexec, bh->st));
   } else {
-    s = sequence();
+    s = copy_in();
+    if (s == CQR_OK) s = sequence();
     if (s != CQR_OK) return s;
   }
   for (int k = 0; k < bh->count; ++k) bh->next_panel[k] = bh->geo[k].panels;
@@ -875,6 +910,30 @@ cqr_status coded_qr_batched_sync_status(cqr_batched bh, int32_t* first_bad, int6
   if (first_bad) *first_bad = bad;
   if (reorth) *reorth = nre;
   return bad < 0 ? CQR_OK : (cqr_status)st[4 * bad];
+}
+
+cqr_status coded_qr_batched_profile(cqr_batched bh, int32_t enable) {
+  if (!bh) return CQR_EINVAL;
+  if (enable && !bh->d_prof) {
+    BK(cudaMalloc(&bh->d_prof, sizeof(unsigned long long) * (kPhases + 1)));
+    BK(cudaMemsetAsync(bh->d_prof, 0, sizeof(unsigned long long) * (kPhases + 1), bh->st));
+  }
+  bh->prof_on = enable != 0;
+  return CQR_OK;
+}
+
+cqr_status coded_qr_batched_phases(cqr_batched bh, int64_t* cycles, int32_t reset) {
+  if (!bh || !cycles) return CQR_EINVAL;
+  if (!bh->d_prof) return CQR_ESTATE;
+  unsigned long long h[kPhases + 1];
+  BK(cudaStreamSynchronize(bh->st));
+  BK(cudaMemcpy(h, bh->d_prof, sizeof(h), cudaMemcpyDeviceToHost));
+  for (int k = 0; k <= kPhases; ++k) cycles[k] = (int64_t)h[k];
+  if (reset) {
+    BK(cudaMemsetAsync(bh->d_prof, 0, sizeof(h), bh->st));
+    BK(cudaStreamSynchronize(bh->st));
+  }
+  return CQR_OK;
 }
 
 const char* coded_qr_batched_last_error(void) { return cudaGetErrorString(g_last_cuda); }

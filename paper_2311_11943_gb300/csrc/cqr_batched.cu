@@ -61,6 +61,45 @@ __device__ __forceinline__ int ld_cl_i32(uint32_t local_addr, uint32_t rank) {
   return v;
 }
 
+// Phase clocks (instrumentation, off unless the launch is given a counter array): thread 0 of
+// each CTA adds the SM cycles between consecutive marks to the phase that just ended, in
+// shared memory, and adds its totals to the launch's array when the CTA leaves.  The slots
+// live in shared memory so that the other threads carry no extra registers.
+//   slots [0, kPhases): cycles per phase; [kPhases]: last mark; [kPhases + 1]: the array
+__device__ __forceinline__ long long* ph_slots() {
+  __shared__ long long s_ph[kPhases + 2];
+  return s_ph;
+}
+__device__ __forceinline__ void ph_begin(unsigned long long* prof) {
+  if (threadIdx.x == 0) {
+    long long* s = ph_slots();
+    for (int k = 0; k < kPhases; ++k) s[k] = 0;
+    s[kPhases] = clock64();
+    s[kPhases + 1] = (long long)reinterpret_cast<uintptr_t>(prof);
+  }
+}
+__device__ __forceinline__ void ph_mark(int phase) {
+  if (threadIdx.x == 0) {
+    long long* s = ph_slots();
+    if (s[kPhases + 1] != 0) {
+      const long long now = clock64();
+      s[phase] += now - s[kPhases];
+      s[kPhases] = now;
+    }
+  }
+}
+__device__ __forceinline__ void ph_end() {
+  if (threadIdx.x == 0) {
+    long long* s = ph_slots();
+    unsigned long long* prof = reinterpret_cast<unsigned long long*>((uintptr_t)s[kPhases + 1]);
+    if (prof) {
+      ph_mark(PH_OTHER);
+      for (int k = 0; k < kPhases; ++k) atomicAdd(prof + k, (unsigned long long)s[k]);
+      atomicAdd(prof + kPhases, 1ull);
+    }
+  }
+}
+
 // Shared-memory layout (in floats), the same for every CTA of a launch.
 //   small : v, eta, sv [kBMax each], warp partials [256]
 //   cpart : cluster partials, two buffers of kBMax * kWC (G > 1)
@@ -485,6 +524,7 @@ __device__ void b_update(BCtx<G>& c, const float* P, int64_t cs, int nr, int bk,
     }
     cp_wait<0>();
     __syncthreads();
+    ph_mark(PH_SPROD);
     // K-split partials -> spart[ks][a][j] (ld kWC), then a fixed-order sum
     if (active)
 #pragma unroll
@@ -523,6 +563,7 @@ __device__ void b_update(BCtx<G>& c, const float* P, int64_t cs, int nr, int bk,
         const int a = e / wc, j = e % wc;
         R[(kb + a) + (c0 + j) * ldr] = rbar[a * kWC + j];
       }
+    ph_mark(PH_RBAR);
     // ---------------------------------------------------------------- B -= Qbar Rbar
     for (int t = 0; t < depth; ++t) issue(t);
     for (int t = 0; t < nkt; ++t) {
@@ -563,6 +604,7 @@ __device__ void b_update(BCtx<G>& c, const float* P, int64_t cs, int nr, int bk,
       }
     }
     cp_wait<0>();
+    ph_mark(PH_UPDATE);
   }
   __syncthreads();
 }
@@ -608,7 +650,8 @@ __global__ void __launch_bounds__(kBT, 1) k_b_factor(BatchInst<float>* __restric
                                                      const BatchTile* __restrict__ tiles,
                                                      const BatchPlan* __restrict__ plans,
                                                      const double* __restrict__ Gt,
-                                                     const double* __restrict__ Gh) {
+                                                     const double* __restrict__ Gh,
+                                                     unsigned long long* prof) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int s_item;
   BCtx<G> c;
@@ -619,6 +662,7 @@ __global__ void __launch_bounds__(kBT, 1) k_b_factor(BatchInst<float>* __restric
   c.warp = threadIdx.x >> 5;
   c.rank = (G > 1) ? cl_rank() : 0;
   c.step = 0;
+  ph_begin(prof);
   for (;;) {
     if (c.rank == 0 && c.tid == 0) s_item = atomicAdd(queue, 1);
     int item;
@@ -631,6 +675,7 @@ __global__ void __launch_bounds__(kBT, 1) k_b_factor(BatchInst<float>* __restric
       item = s_item;
       __syncthreads();
     }
+    ph_mark(PH_OTHER);
     if (item >= count) break;
     const int idx = order[item];
     BatchInst<float>& I = inst[idx];
@@ -643,7 +688,10 @@ __global__ void __launch_bounds__(kBT, 1) k_b_factor(BatchInst<float>* __restric
     float* Qs = I.Q + row0;
     bool ok = true;
     for (int k = pb; k < pe && ok; ++k) {
-      if (k == I.rec_at - 1) b_recover<G>(c, I, tiles, plans, Gt, Gh);
+      if (k == I.rec_at - 1) {
+        b_recover<G>(c, I, tiles, plans, Gt, Gh);
+        ph_mark(PH_RECOVER);
+      }
       const int kb = k * I.b;
       const int bk = (int)std::min<int64_t>(I.b, g.n - kb);
       // ICGS on the panel slice: in the shared-memory pool (after the panel's scratch) when it
@@ -673,10 +721,12 @@ __global__ void __launch_bounds__(kBT, 1) k_b_factor(BatchInst<float>* __restric
           if (r < nr) Pg[r + (int64_t)a * g.ldq] = P[e];
         }
       __syncthreads();
+      ph_mark(PH_PANEL);
       b_update<G>(c, Pg, g.ldq, nr, bk, Qs, g.ldq, kb + bk, g.N, I.R, g.ldr, kb, panel_cap);
     }
   }
   if (G > 1) cl_sync();  // peers may still read this CTA's shared memory
+  ph_end();
 }
 
 template <int G>
@@ -697,7 +747,7 @@ cudaError_t launch_g(const BFactorLaunch& L, cudaStream_t st) {
   cfg.attrs = attr;
   cfg.numAttrs = G > 1 ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, fn, L.inst, L.count, L.order, L.range, L.queue, L.tau2,
-                            L.panel_cap, L.tiles, L.plans, L.Gt, L.Gh);
+                            L.panel_cap, L.tiles, L.plans, L.Gt, L.Gh, L.prof);
 }
 
 template <int G>

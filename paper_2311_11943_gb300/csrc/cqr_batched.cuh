@@ -10,6 +10,12 @@ namespace cqr {
 constexpr int kBMax = 64;  // widest panel of the batched kernel
 constexpr int kWC = 64;    // trailing columns per update chunk
 
+// Phases of the factor launch's clocks (BFactorLaunch::prof): in-launch recovery; the panel
+// (ICGS column steps, the slice's copies); the product S = Qbar^T B; its reduction into Rbar
+// (K-split sum, cluster sum, store into R); the update B -= Qbar Rbar; everything else (the
+// work queue, the wait at the end).  prof[kPhases] counts the CTAs that added their clocks.
+enum { PH_RECOVER = 0, PH_PANEL, PH_SPROD, PH_RBAR, PH_UPDATE, PH_OTHER, kPhases };
+
 struct BFactorLaunch {
   int G;                    // CTAs per instance (thread-block cluster size): 1, 2, 4 or 8
   int grid;                 // CTAs in the launch (a multiple of G)
@@ -26,6 +32,9 @@ struct BFactorLaunch {
   const BatchPlan* plans = nullptr;
   const double* Gt = nullptr;
   const double* Gh = nullptr;
+  // phase clocks (instrumentation): device array of kPhases + 1 counters that each CTA adds
+  // its SM cycles per phase to; nullptr turns them off
+  unsigned long long* prof = nullptr;
 };
 
 // Shared-memory floats left for the panel slice when the CTAs form clusters of G.

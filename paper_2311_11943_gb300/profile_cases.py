@@ -8,6 +8,7 @@ library's public API.  Each case runs twice (the first run warms up the handle).
   python -m paper_2311_11943_gb300.profile_cases bandwidth8192  # encode / decode / post-orth
   python -m paper_2311_11943_gb300.profile_cases c3_tall    # the 16384^2 workload's panel shape
   python -m paper_2311_11943_gb300.profile_cases exchange_floor  # per-column exchange floor
+  python -m paper_2311_11943_gb300.profile_cases bfactor_phases  # batched factor phase clocks
 
 Launch order per run (for ncu's --launch-skip; filter by kernel name with -k, as the commands
 in profiles/ do, since two streams interleave):
@@ -175,9 +176,79 @@ def case_exchange_floor(reps=8):
         print(json.dumps(r))
 
 
+def case_bfactor_phases(count=512):
+    """Phase clocks (coded_qr_batched_profile) of the persistent batched factor on the batch
+    recipe of 512 instances: m ~ U[256, 8192], n ~ U[32, 256] (m >= 4 n), grid 8 x 4, f = 2,
+    shapes from seed 4, N(0,1) entries drawn on the device, cluster size and widths picked by
+    the autotuner.  Two launch kinds, each timed with CUDA events after a warm-up: the factor
+    launch alone (encode, then factor, no erasure), and the whole run with one tile of every
+    instance lost at its middle panel and recovered inside the launch.  One JSON line each:
+    kernel (or run) ms, SM cycles per CTA in each phase and the phases' shares."""
+    import json
+
+    import torch
+    from . import binding as B
+    from . import synth
+    shapes = synth.batched_shapes(count, 4)
+    gen = torch.Generator(device="cuda").manual_seed(4000)
+    As = [torch.randn(n, m, device="cuda", dtype=torch.float32, generator=gen).t()
+          for (m, n) in shapes]
+    bt = B.CodedQRBatch(shapes, 8, 4, 2, b=0, seed=4)
+    bt.autotune(As, [], reps=1)
+    quads = []
+    for i, g in enumerate(bt.geo):
+        (r, c), = synth.random_erasures(g["grid_rows"], g["grid_cols"], 2, 1, 11 + i)
+        quads.append((i, g["panels"] // 2, r, c))
+    stream = torch.cuda.current_stream()
+
+    def timed(prep, fn, warm=True):
+        if warm:
+            prep()
+            fn()
+        prep()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    kinds = [("factor launch alone, no erasure (encode outside the events)",
+              lambda: bt.encode(As), lambda: bt.factor()),
+             ("whole run (encode, factor with one tile per instance recovered in the launch)",
+              lambda: None, lambda: bt.run(As, quads, graph=False))]
+    runs = [(name, prep, fn) for (name, prep, fn) in kinds]
+    # the factor launch again at the widest cluster (8 CTAs per instance, an eighth of the rows
+    # each, widths by the shape rule)
+    runs.append(("factor launch alone at clusters of 8, no erasure", "cluster8",
+                 lambda: bt.factor()))
+    for name, prep, fn in runs:
+        if prep == "cluster8":
+            bt.set_tuning(8)
+            prep = lambda: bt.encode(As)  # noqa: E731
+        cl, widths = bt.tuning()
+        ms_plain = timed(prep, fn)
+        bt.profile(True)
+        prep()
+        fn()
+        bt.phases(reset=True)
+        ms_prof = timed(prep, fn, warm=False)
+        ph, ctas = bt.phases(reset=True)
+        bt.profile(False)
+        assert bt.sync_status()[0] == 0
+        tot = sum(ph.values())
+        per_cta = {k: v / max(1, ctas) for k, v in ph.items()}
+        print(json.dumps({"launch": name, "instances": count, "cluster": cl,
+                          "widths": sorted(set(widths)), "ms": ms_plain, "ms_clocked": ms_prof,
+                          "ctas": ctas, "cycles_per_cta": per_cta,
+                          "share": {k: v / tot for k, v in ph.items()} if tot else None}))
+    bt.close()
+
+
 CASES = {"tc_c2": case_c2, "panel_c2": case_c2, "bfactor64": case_bfactor, "adjoint": case_adjoint,
          "bandwidth8192": case_bandwidth, "c3_tall": case_c3_tall,
-         "exchange_floor": case_exchange_floor}
+         "exchange_floor": case_exchange_floor, "bfactor_phases": case_bfactor_phases}
 
 if __name__ == "__main__":
     CASES[sys.argv[1]]()

@@ -41,6 +41,18 @@ def test_binding_names_match_header(libpath):
     binding.lib()
 
 
+def test_binding_flag_values_match_header():
+    """Every CQR_BATCH_* / CQR_RUN_* flag the binding passes has the header's value."""
+    with open(os.path.join(ROOT, "include", "coded_qr.h")) as fh:
+        text = fh.read()
+    vals = {k: int(v) for k, v in re.findall(r"\b(CQR_BATCH_\w+)\s*=\s*(\d+)", text)}
+    vals.update({k: int(v) for k, v in re.findall(r"#define\s+(CQR_RUN_\w+)\s+(\d+)u?", text)})
+    from paper_2311_11943_gb300 import binding
+    for name in ("CQR_BATCH_GRAPH", "CQR_BATCH_POST_ORTH", "CQR_BATCH_HOST_BUFFERS",
+                 "CQR_RUN_HOST_BUFFERS"):
+        assert getattr(binding, name) == vals[name], name
+
+
 def test_solve_ls_validates_like_solve_without_gpu(libpath):
     # the least-squares verb under the problem statement's name takes the same arguments and
     # rejects the same null handle before touching the device

@@ -131,6 +131,72 @@ def test_graph_replay_and_stepwise_verbs_reproduce_the_run_bitwise(small_batch):
         assert torch.equal(Q, first[i][0]) and torch.equal(R, first[i][1])
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_host_buffer_run_reproduces_the_device_run_bitwise(small_batch, graph):
+    """CQR_BATCH_HOST_BUFFERS: the library copies every A from host memory into the systematic
+    block of its encoded matrix and encodes in place there; the factors are those of the run
+    on device buffers, bit for bit, for pinned and for pageable host arrays, and when the
+    recorded graph is replayed with other host arrays."""
+    bt, As, Ad = small_batch
+    quads = erasure_plan(bt, 8)
+    bt.run(Ad, quads, graph=graph)
+    torch.cuda.synchronize()
+    first = [tuple(t.clone() for t in bt.factors(i)) for i in range(bt.count)]
+
+    def same():
+        st, bad, _ = bt.sync_status()
+        assert st == 0 and bad == -1
+        for i in range(bt.count):
+            Q, R = bt.factors(i)
+            assert torch.equal(Q, first[i][0]) and torch.equal(R, first[i][1]), i
+
+    pinned = []
+    for A in As:
+        h = torch.empty((A.shape[1], A.shape[0]), dtype=torch.float32, pin_memory=True)
+        h.copy_(torch.from_numpy(np.ascontiguousarray(A.T.astype(np.float32))))
+        pinned.append(h)
+    for _ in range(2):
+        bt.run([h.numpy().T for h in pinned], quads, graph=graph, host=True)
+        same()
+    plain = [np.asfortranarray(A.astype(np.float32)) for A in As]
+    bt.run(plain, quads, graph=graph, host=True)
+    same()
+    with pytest.raises(AssertionError):
+        bt.run([np.ascontiguousarray(a) for a in plain], quads, graph=graph, host=True)
+
+
+def test_phase_clocks_count_every_cta_and_leave_the_factors_unchanged(small_batch):
+    """coded_qr_batched_profile: every CTA of the launch adds its cycles per phase once; the
+    run with the clocks on gives the same factors bit for bit."""
+    bt, As, Ad = small_batch
+    quads = erasure_plan(bt, 9)
+    assert len(quads) > 0
+    bt.run(Ad, quads, graph=False)
+    torch.cuda.synchronize()
+    first = [tuple(t.clone() for t in bt.factors(i)) for i in range(bt.count)]
+    bt.profile(True)
+    try:
+        bt.phases(reset=True)
+        for graph in (False, True):
+            bt.run(Ad, quads, graph=graph)
+            ph, ctas = bt.phases(reset=True)
+            assert ctas > 0
+            for k in ("panel", "s_product", "rbar_reduce", "update", "recover"):
+                assert ph[k] > 0, (graph, k, ph)
+            assert all(v >= 0 for v in ph.values())
+            for i in range(bt.count):
+                Q, R = bt.factors(i)
+                assert torch.equal(Q, first[i][0]) and torch.equal(R, first[i][1]), i
+        ph, ctas = bt.phases(reset=False)
+        assert ctas == 0 and sum(ph.values()) == 0
+    finally:
+        bt.profile(False)
+    bt.run(Ad, quads, graph=True)   # clocks off again: a new recording without them
+    bt.sync_status()
+    ph, ctas = bt.phases(reset=False)
+    assert ctas == 0
+
+
 @pytest.mark.parametrize("G", [1, 2, 4, 8])
 @pytest.mark.parametrize("width", [16, 32, 64])
 def test_every_cluster_size_and_width(small_batch, G, width):
