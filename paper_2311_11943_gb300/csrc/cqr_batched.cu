@@ -232,13 +232,47 @@ __device__ __forceinline__ void cta_colsums(BCtx<G>& c, int nv, int nr, float* l
 }
 
 // Rows of the slice per thread and block: thread t owns rows blk*RPT*kBT + t + k*kBT, k < RPT
-// (RPT = 4, 8 or 20 by the slice height, so that short slices run short loops).
+// (RPT = 4, 8 or 10 by the slice height, so that short slices run short loops).
 
 // Sum of one value per thread over the CTA for each of nv columns: warp shuffles, then a
 // fixed-order sum over the warps (wp: [kBW][nv] scratch) into loc (accumulate when add).
 __device__ __forceinline__ void warp_part(float s, int a, int nv, float* wp, int warp, int lane) {
   s = warp_sum(s);
   if (lane == 0) wp[warp * nv + a] = s;
+}
+
+// Columns a = j + 1 + a1 + u (u < CW) of the fused column step: every load of the CW columns
+// first, then per column the update p_a -= q (v_a / r_jj), its store and the warp's part of
+// p_a^T p'.  The arithmetic of each column is that of a group of one.
+template <int kRPT, int CW>
+__device__ __forceinline__ void update_cols(float* P, int64_t cs, int nr, int rb, int j, int a1,
+                                            int nv, float inv, const float* v,
+                                            const float (&q)[kRPT], const float (&p1)[kRPT],
+                                            float* wp, int warp, int lane) {
+  float x[CW][kRPT];
+#pragma unroll
+  for (int u = 0; u < CW; ++u) {
+    const float* pa = P + (j + 1 + a1 + u) * cs;
+#pragma unroll
+    for (int k = 0; k < kRPT; ++k) {
+      const int r = rb + k * kBT;
+      x[u][k] = (r < nr) ? pa[r] : 0.f;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < CW; ++u) {
+    float* pa = P + (j + 1 + a1 + u) * cs;
+    const float ca = v[j + 1 + a1 + u] * inv;
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kRPT; ++k) {
+      const int r = rb + k * kBT;
+      x[u][k] = fmaf(-q[k], ca, x[u][k]);
+      if (r < nr) pa[r] = x[u][k];
+      s = fmaf(x[u][k], p1[k], s);
+    }
+    warp_part(s, a1 + u, nv, wp, warp, lane);
+  }
 }
 
 // The fused column step of the panel, row-split: with q = p_j / r_jj and p' = p_{j+1} - q c1
@@ -283,25 +317,14 @@ __device__ __forceinline__ void cta_update_sums(BCtx<G>& c, float* P, int64_t cs
       for (int k = 0; k < kRPT; ++k) s = fmaf(p1[k], p1[k], s);
       warp_part(s, 0, nv, wp, c.warp, c.lane);
     }
-    for (int a1 = 1; a1 < nv; ++a1) {
-      float* pa = P + (j + 1 + a1) * cs;
-      const float ca = v[j + 1 + a1] * inv;
-      float x[kRPT];
-#pragma unroll
-      for (int k = 0; k < kRPT; ++k) {
-        const int r = rb + k * kBT;
-        x[k] = (r < nr) ? pa[r] : 0.f;
-      }
-      float s = 0.f;
-#pragma unroll
-      for (int k = 0; k < kRPT; ++k) {
-        const int r = rb + k * kBT;
-        x[k] = fmaf(-q[k], ca, x[k]);
-        if (r < nr) pa[r] = x[k];
-        s = fmaf(x[k], p1[k], s);
-      }
-      warp_part(s, a1, nv, wp, c.warp, c.lane);
-    }
+    // columns in groups of kCW: with the slice in L2 every group costs one round trip, since
+    // the loads of a column cannot move above the stores of the one before it
+    constexpr int kCW = 4;
+    int a1 = 1;
+    for (; a1 + kCW <= nv; a1 += kCW)
+      update_cols<kRPT, kCW>(P, cs, nr, rb, j, a1, nv, inv, v, q, p1, wp, c.warp, c.lane);
+    for (; a1 < nv; ++a1)
+      update_cols<kRPT, 1>(P, cs, nr, rb, j, a1, nv, inv, v, q, p1, wp, c.warp, c.lane);
     __syncthreads();
     for (int a = c.tid; a < nv; a += kBT) {
       float t = 0.f;
@@ -328,7 +351,31 @@ __device__ __forceinline__ void cta_start_sums(BCtx<G>& c, const float* P, int64
       const int r = rb + k * kBT;
       p0[k] = (r < nr) ? P[r] : 0.f;
     }
-    for (int a = 0; a < bk; ++a) {
+    // columns in groups of four: the loads of a group go out together (the shared-memory
+    // stores of the warp partials keep later loads from moving above them)
+    int a = 0;
+    for (; a + 4 <= bk; a += 4) {
+      float x[4][kRPT];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < kRPT; ++k) {
+          const int r = rb + k * kBT;
+          x[u][k] = (r < nr) ? P[(a + u) * cs + r] : 0.f;
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int k = 0; k < kRPT; ++k) {
+          s0 = fmaf(x[u][k], p0[k], s0);
+          s1 = fmaf(x[u][k], x[u][k], s1);
+        }
+        warp_part(s0, a + u, 2 * bk, wp, c.warp, c.lane);
+        warp_part(s1, bk + a + u, 2 * bk, wp, c.warp, c.lane);
+      }
+    }
+    for (; a < bk; ++a) {
       const float* pa = P + a * cs;
       float x[kRPT];
 #pragma unroll
@@ -713,7 +760,7 @@ __global__ void __launch_bounds__(kBT, 1) k_b_factor(BatchInst<float>* __restric
       else if (nr <= 8 * kBT)
         ok = b_panel<G, 8>(c, P, cs, nr, bk, I.R, g.ldr, kb, tau2, I.status);
       else
-        ok = b_panel<G, 20>(c, P, cs, nr, bk, I.R, g.ldr, kb, tau2, I.status);
+        ok = b_panel<G, 10>(c, P, cs, nr, bk, I.R, g.ldr, kb, tau2, I.status);
       if (!ok) break;
       if (in_smem)
         for (int e = c.tid; e < rpad * bk; e += kBT) {
