@@ -427,12 +427,14 @@ cqr_status coded_qr_batched_sync_status(cqr_batched bh, int32_t* first_bad, int6
  * With enable != 0 every later factor launch of the batch (direct, or recorded into a new
  * graph) adds, for each CTA, the SM clock cycles it spent in each phase to counters of the
  * batch (allocated on the first enable): in-launch recovery, panel, the product Qbar^T B,
- * its reduction into Rbar, the update B -= Qbar Rbar, and the rest (work queue, the wait at
- * the end).  Thread 0 of the CTA reads the clock at the phase boundaries, so the cost when on
- * is a few instructions per panel and update chunk; when off, one test per boundary.
- * coded_qr_batched_phases synchronises the stream and writes cycles[0..5] (host, summed over
- * the CTAs, in the order above) and cycles[6] (the number of CTAs that added theirs); with
- * reset != 0 it then zeroes the counters.  CQR_ESTATE if the clocks were never enabled. */
+ * its reduction into Rbar, the update B -= Qbar Rbar, the rest (work queue, the wait at the
+ * end), and the parts of the two products spent at the top of each pipeline stage waiting for
+ * its copies and the CTA barrier.  Thread 0 of the CTA reads the clock at the phase
+ * boundaries, so the cost when on is a few instructions per pipeline stage; when off, one
+ * test per boundary.  coded_qr_batched_phases synchronises the stream and writes
+ * cycles[0..7] (host, summed over the CTAs, in the order above) and cycles[8] (the number of
+ * CTAs that added theirs); with reset != 0 it then zeroes the counters.  CQR_ESTATE if the
+ * clocks were never enabled. */
 cqr_status coded_qr_batched_profile(cqr_batched bh, int32_t enable);
 cqr_status coded_qr_batched_phases(cqr_batched bh, int64_t* cycles, int32_t reset);
 

@@ -710,7 +710,8 @@ class CodedQRBatch:
     def sync_status(self):
         return coded_qr_batched_sync_status(self.h)
 
-    BATCH_PHASES = ("recover", "panel", "s_product", "rbar_reduce", "update", "other")
+    BATCH_PHASES = ("recover", "panel", "s_product", "rbar_reduce", "update", "other",
+                    "s_product_wait", "update_wait")
 
     def profile(self, on=True):
         """Phase clocks of the later factor launches (coded_qr_batched_profile)."""
@@ -718,10 +719,11 @@ class CodedQRBatch:
 
     def phases(self, reset=True):
         """SM cycles per phase summed over the CTAs, and the number of CTAs."""
-        buf = (C.c_int64 * 7)()
+        n = len(self.BATCH_PHASES)
+        buf = (C.c_int64 * (n + 1))()
         _bcheck(lib().coded_qr_batched_phases(self.h, buf, 1 if reset else 0),
                 "coded_qr_batched_phases")
-        return dict(zip(self.BATCH_PHASES, buf[:6])), buf[6]
+        return dict(zip(self.BATCH_PHASES, buf[:n])), buf[n]
 
 
 def debug_bounds():

@@ -536,8 +536,10 @@ __device__ void b_update(BCtx<G>& c, const float* P, int64_t cs, int nr, int bk,
     __syncthreads();  // the previous readers of the pool are done
     for (int t = 0; t < depth; ++t) issue(t);
     for (int t = 0; t < nkt; ++t) {
+      ph_mark(PH_SPROD);
       cp_wait_dyn(depth - 1);
       __syncthreads();
+      ph_mark(PH_SPROD_WAIT);
       issue(t + depth);
       const int r0 = t * kKT;
       const int kr = (nr - r0) < kKT ? (nr - r0) : kKT;
@@ -614,8 +616,10 @@ __device__ void b_update(BCtx<G>& c, const float* P, int64_t cs, int nr, int bk,
     // ---------------------------------------------------------------- B -= Qbar Rbar
     for (int t = 0; t < depth; ++t) issue(t);
     for (int t = 0; t < nkt; ++t) {
+      ph_mark(PH_UPDATE);
       cp_wait_dyn(depth - 1);
       __syncthreads();
+      ph_mark(PH_UPDATE_WAIT);
       issue(t + depth);
       const int r = t * kKT + 4 * rq4;
       const int j = 2 * cp;

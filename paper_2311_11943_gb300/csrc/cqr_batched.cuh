@@ -13,8 +13,11 @@ constexpr int kWC = 64;    // trailing columns per update chunk
 // Phases of the factor launch's clocks (BFactorLaunch::prof): in-launch recovery; the panel
 // (ICGS column steps, the slice's copies); the product S = Qbar^T B; its reduction into Rbar
 // (K-split sum, cluster sum, store into R); the update B -= Qbar Rbar; everything else (the
-// work queue, the wait at the end).  prof[kPhases] counts the CTAs that added their clocks.
-enum { PH_RECOVER = 0, PH_PANEL, PH_SPROD, PH_RBAR, PH_UPDATE, PH_OTHER, kPhases };
+// work queue, the wait at the end); and, split off the two products, the time spent at the
+// top of each pipeline stage waiting for its copies and for the CTA's barrier.
+// prof[kPhases] counts the CTAs that added their clocks.
+enum { PH_RECOVER = 0, PH_PANEL, PH_SPROD, PH_RBAR, PH_UPDATE, PH_OTHER, PH_SPROD_WAIT,
+       PH_UPDATE_WAIT, kPhases };
 
 struct BFactorLaunch {
   int G;                    // CTAs per instance (thread-block cluster size): 1, 2, 4 or 8
