@@ -488,7 +488,10 @@ __device__ void b_update(BCtx<G>& c, const float* P, int64_t cs, int nr, int bk,
   const int sf = stage_floats(bk);
   int nst = pool_floats / sf;
   if (nst > kMaxStages) nst = kMaxStages;
-  const int depth = nst - 1;       // stages in flight ahead of the one being consumed
+  // two stages per CTA barrier when at least four fit (one otherwise); `depth` stages are in
+  // flight ahead of the ones being consumed
+  const int spb = nst >= 4 ? 2 : 1;
+  const int depth = nst - spb;
   const int bkq = (bk + 3) / 4;
   const int tiles = bkq * (kWC / 4);
   int ks_n = kBT / tiles;
@@ -534,13 +537,8 @@ __device__ void b_update(BCtx<G>& c, const float* P, int64_t cs, int nr, int bk,
 #pragma unroll
       for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
     __syncthreads();  // the previous readers of the pool are done
-    for (int t = 0; t < depth; ++t) issue(t);
-    for (int t = 0; t < nkt; ++t) {
-      ph_mark(PH_SPROD);
-      cp_wait_dyn(depth - 1);
-      __syncthreads();
-      ph_mark(PH_SPROD_WAIT);
-      issue(t + depth);
+    // one stage of S: this thread's 4 x 4 tile over its K-split share of the four-row groups
+    auto s_stage = [&](int t) {
       const int r0 = t * kKT;
       const int kr = (nr - r0) < kKT ? (nr - r0) : kKT;
       const int ng = (kr + 3) / 4;
@@ -570,6 +568,16 @@ __device__ void b_update(BCtx<G>& c, const float* P, int64_t cs, int nr, int bk,
             }
         }
       }
+    };
+    for (int t = 0; t < depth; ++t) issue(t);
+    for (int t = 0; t < nkt; t += spb) {
+      ph_mark(PH_SPROD);
+      cp_wait_dyn(depth - spb);
+      __syncthreads();
+      ph_mark(PH_SPROD_WAIT);
+      for (int u = 0; u < spb; ++u) issue(t + depth + u);
+      for (int u = 0; u < spb; ++u)
+        if (t + u < nkt) s_stage(t + u);
     }
     cp_wait<0>();
     __syncthreads();
@@ -614,13 +622,8 @@ __device__ void b_update(BCtx<G>& c, const float* P, int64_t cs, int nr, int bk,
       }
     ph_mark(PH_RBAR);
     // ---------------------------------------------------------------- B -= Qbar Rbar
-    for (int t = 0; t < depth; ++t) issue(t);
-    for (int t = 0; t < nkt; ++t) {
-      ph_mark(PH_UPDATE);
-      cp_wait_dyn(depth - 1);
-      __syncthreads();
-      ph_mark(PH_UPDATE_WAIT);
-      issue(t + depth);
+    // one stage of the update: four rows x two columns of B per thread, stored to global
+    auto u_stage = [&](int t) {
       const int r = t * kKT + 4 * rq4;
       const int j = 2 * cp;
       if (r < nr && j < wc) {
@@ -653,6 +656,16 @@ __device__ void b_update(BCtx<G>& c, const float* P, int64_t cs, int nr, int bk,
           }
         }
       }
+    };
+    for (int t = 0; t < depth; ++t) issue(t);
+    for (int t = 0; t < nkt; t += spb) {
+      ph_mark(PH_UPDATE);
+      cp_wait_dyn(depth - spb);
+      __syncthreads();
+      ph_mark(PH_UPDATE_WAIT);
+      for (int u = 0; u < spb; ++u) issue(t + depth + u);
+      for (int u = 0; u < spb; ++u)
+        if (t + u < nkt) u_stage(t + u);
     }
     cp_wait<0>();
     ph_mark(PH_UPDATE);
