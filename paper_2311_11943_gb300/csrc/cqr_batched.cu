@@ -472,8 +472,9 @@ __device__ bool b_panel(BCtx<G>& c, float* P, int64_t cs, int nr, int bk, float*
 
 // Trailing update of one panel on this CTA's rows, in chunks of kWC columns:
 //   S = Qbar^T B over this CTA's rows: stages of kKT rows of B and of Qbar stream in through
-//       a cp.async pipeline as deep as the shared-memory pool allows (up to kMaxStages); each
-//       thread accumulates a 4 x 4 tile of S over a K-split share of four-row groups;
+//       a cp.async pipeline as deep as the shared-memory pool allows (up to kMaxStages),
+//       two stages per CTA barrier; each thread accumulates a 4 x 4 tile of S over a K-split
+//       share of four-row groups;
 //   Rbar = cluster sum of S (fixed order);  R[kb.., col] = Rbar (rank 0);
 //   B -= Qbar Rbar: the same stages stream in again, each thread updates four rows x two
 //       columns and stores them straight to global memory.
