@@ -1244,7 +1244,9 @@ def run_autograd(args):
     rank = int(os.environ.get("RANK", "0"))
     torch.cuda.set_device(local)
     bs, m, n = cfg["batch"], cfg["m"], cfg["n"]
-    gen = torch.Generator(device="cuda").manual_seed(cfg["seed"])
+    from paper_2311_11943_gb300 import replicas
+    # every rank draws its own problems of the recipe (rank 0: the seed itself)
+    gen = torch.Generator(device="cuda").manual_seed(replicas.rank_seed(cfg["seed"], rank))
     # A = U diag(sigma) V^T with Haar U (m x n), V (n x n), sigma geometric to kappa (data
     # generation on the device, not timed)
     A = torch.empty((bs, m, n), device="cuda", dtype=torch.float32)
